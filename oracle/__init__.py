@@ -1,0 +1,224 @@
+"""FP64 CPU reference STA (test infrastructure only).
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the ``cpu_baseline`` /
+``--impl reference`` legs of ``bench.py`` may import this package.  It shares
+no code with the CUDA library: ``sta_oracle.c`` is compiled on its own with
+gcc into ``liboracle.so`` and driven through ctypes here.
+
+Every function follows the textbook reading of the terms HeteroSTA
+(arXiv 2511.11660) uses without formulas: NLDM tables (Sec. IV-A), Elmore
+delay on RC trees (Sec. III, "Delay models"), RC from positions and unit R/C
+(Sec. III, "Parasitics (RC) inputs"), pin slacks and WNS/TNS (Sec. III,
+"Report options").  ``sta_oracle.c`` states each formula.
+
+A design is a plain ``dict`` of numpy arrays and scalars (the layout that
+``paper_2511_11660_b300.synth`` writes); see ``_Design`` for the keys.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "sta_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+ERRORS = {0: "ok", 1: "invalid input", 2: "combinational cycle", 3: "out of memory"}
+
+
+def build(force: bool = False) -> str:
+    """Compile ``sta_oracle.c`` into ``liboracle.so`` (gcc -O2, plain C)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".tmp%d" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        _lib = C.CDLL(build())
+        P = C.c_void_p
+        _lib.orc_lut_eval.argtypes = [P, P, P, C.c_double, C.c_double, P]
+        _lib.orc_rc_tree.argtypes = [C.c_int32, P, P, P, P, P, P, P]
+        _lib.orc_net_delays.argtypes = [P, C.c_int32, P, P, P]
+        _lib.orc_topo_order.argtypes = [P, P]
+        _lib.orc_sta.argtypes = [P, P, P, P, P, P, P, P]
+        _lib.orc_objective_grad.argtypes = [P, C.c_double, C.c_double, P, P, P]
+        _lib.orc_objective.argtypes = [P, C.c_double, C.c_double, P]
+        for f in ("orc_lut_eval", "orc_rc_tree", "orc_net_delays", "orc_topo_order", "orc_sta",
+                  "orc_objective_grad", "orc_objective"):
+            getattr(_lib, f).restype = C.c_int
+    return _lib
+
+
+class _Design(C.Structure):
+    _fields_ = [
+        ("n_types", C.c_int32), ("type_nin", C.c_void_p), ("type_kind", C.c_void_p),
+        ("arc_sense", C.c_void_p), ("lut_idx1", C.c_void_p), ("lut_idx2", C.c_void_p),
+        ("lut_val", C.c_void_p), ("pin_cap", C.c_void_p),
+        ("setup_ns", C.c_double), ("hold_ns", C.c_double), ("po_cap_pf", C.c_double),
+        ("n_cells", C.c_int32), ("cell_type", C.c_void_p), ("cell_pin_ptr", C.c_void_p),
+        ("cell_pin", C.c_void_p), ("n_pins", C.c_int32), ("pin_role", C.c_void_p),
+        ("n_nets", C.c_int32), ("net_pin_ptr", C.c_void_p), ("net_pin", C.c_void_p),
+        ("rc_ptr", C.c_void_p), ("rc_parent", C.c_void_p), ("rc_pin_node", C.c_void_p),
+        ("rc_R", C.c_void_p), ("rc_C", C.c_void_p), ("cell_xy", C.c_void_p), ("port_xy", C.c_void_p),
+        ("r_per_um", C.c_double), ("c_per_um", C.c_double),
+        ("period_ns", C.c_double), ("clk_slew_ns", C.c_double), ("pi_at_ns", C.c_double),
+        ("pi_slew_ns", C.c_double), ("n_corners", C.c_int32), ("lut_scale", C.c_void_p),
+        ("rc_scale", C.c_void_p), ("gamma_ns", C.c_double),
+    ]
+
+
+_ARRAYS = {
+    "type_nin": np.int32, "type_kind": np.int32, "arc_sense": np.int32, "lut_idx1": np.float32,
+    "lut_idx2": np.float32, "lut_val": np.float32, "pin_cap": np.float32, "cell_type": np.int32,
+    "cell_pin_ptr": np.int32, "cell_pin": np.int32, "pin_role": np.int8, "net_pin_ptr": np.int32,
+    "net_pin": np.int32, "rc_ptr": np.int32, "rc_parent": np.int32, "rc_pin_node": np.int32,
+    "rc_R": np.float32, "rc_C": np.float32, "cell_xy": np.float32, "port_xy": np.float32,
+    "lut_scale": np.float32, "rc_scale": np.float32,
+}
+_SCALARS = ("setup_ns", "hold_ns", "po_cap_pf", "r_per_um", "c_per_um", "period_ns", "clk_slew_ns",
+            "pi_at_ns", "pi_slew_ns", "gamma_ns")
+
+
+def _marshal(d: dict, use_rc: bool | None = None):
+    """Build the ctypes struct; returns (struct, keep-alive list)."""
+    keep = []
+    s = _Design()
+    if use_rc is None:
+        use_rc = d.get("rc_ptr") is not None
+    for k, dt in _ARRAYS.items():
+        v = d.get(k)
+        if k.startswith("rc_") and k not in ("rc_scale",) and not use_rc:
+            v = None
+        if v is None:
+            setattr(s, k, None)
+            continue
+        a = np.ascontiguousarray(np.asarray(v), dtype=dt)
+        keep.append(a)
+        setattr(s, k, a.ctypes.data)
+    for k in _SCALARS:
+        setattr(s, k, float(d.get(k, 0.0)))
+    s.n_types = int(d["n_types"])
+    s.n_cells = int(d["n_cells"])
+    s.n_pins = int(d["n_pins"])
+    s.n_nets = int(d["n_nets"])
+    s.n_corners = int(d.get("n_corners", 1))
+    if d.get("lut_scale") is None:
+        a = np.ones(s.n_corners, np.float32); keep.append(a); s.lut_scale = a.ctypes.data
+    if d.get("rc_scale") is None:
+        a = np.ones(s.n_corners, np.float32); keep.append(a); s.rc_scale = a.ctypes.data
+    return s, keep
+
+
+def _check(rc: int, what: str):
+    if rc != 0:
+        raise RuntimeError("oracle %s failed: %s" % (what, ERRORS.get(rc, rc)))
+
+
+def _ptr(a: np.ndarray):
+    return a.ctypes.data
+
+
+def lut_eval(idx1, idx2, val, s: float, l: float):
+    """O1: bilinear lookup -> (value, d/d slew, d/d load)."""
+    lib = _load()
+    i1 = np.ascontiguousarray(idx1, np.float32)
+    i2 = np.ascontiguousarray(idx2, np.float32)
+    v = np.ascontiguousarray(val, np.float32).reshape(-1)
+    out = np.zeros(3, np.float64)
+    _check(lib.orc_lut_eval(_ptr(i1), _ptr(i2), _ptr(v), float(s), float(l), _ptr(out)), "lut_eval")
+    return float(out[0]), float(out[1]), float(out[2])
+
+
+def rc_tree(parent, R, C_):
+    """O3 on one tree (double inputs): returns (Cdown, D, beta, var)."""
+    lib = _load()
+    par = np.ascontiguousarray(parent, np.int32)
+    r = np.ascontiguousarray(R, np.float64)
+    c = np.ascontiguousarray(C_, np.float64)
+    n = len(par)
+    outs = [np.zeros(n, np.float64) for _ in range(4)]
+    _check(lib.orc_rc_tree(n, _ptr(par), _ptr(r), _ptr(c), *[_ptr(o) for o in outs]), "rc_tree")
+    return tuple(outs)
+
+
+def net_delays(d: dict, corner: int = 0, use_rc: bool | None = None):
+    """Per pin: driver load (pF), sink Elmore delay (ns), sink variance (ns^2)."""
+    lib = _load()
+    s, keep = _marshal(d, use_rc)
+    P = int(d["n_pins"])
+    outs = [np.zeros(max(P, 1), np.float64) for _ in range(3)]
+    _check(lib.orc_net_delays(C.byref(s), int(corner), *[_ptr(o) for o in outs]), "net_delays")
+    return tuple(o[:P] for o in outs)
+
+
+def topo_order(d: dict):
+    lib = _load()
+    s, keep = _marshal(d)
+    out = np.zeros(max(int(d["n_pins"]), 1), np.int32)
+    _check(lib.orc_topo_order(C.byref(s), _ptr(out)), "topo_order")
+    return out[: int(d["n_pins"])]
+
+
+def endpoints(d: dict) -> np.ndarray:
+    """Endpoint pins (DFF D and PO) in ascending pin id, the oracle's order."""
+    role = np.asarray(d["pin_role"])
+    return np.nonzero((role == 4) | (role == 1))[0].astype(np.int32)
+
+
+def sta(d: dict, use_rc: bool | None = None) -> dict:
+    """Full FP64 analysis; see ``orc_sta`` for the array layouts."""
+    lib = _load()
+    s, keep = _marshal(d, use_rc)
+    P, K = int(d["n_pins"]), int(d.get("n_corners", 1))
+    E = len(endpoints(d))
+    arr = {k: np.zeros((max(P, 1), K, 4), np.float64) for k in ("at", "slew", "rat", "slack")}
+    eps = np.zeros((max(E, 1), K), np.float64)
+    eph = np.zeros((max(E, 1), K), np.float64)
+    summ = np.zeros((K, 8), np.float64)
+    rc = lib.orc_sta(C.byref(s), _ptr(arr["at"]), _ptr(arr["slew"]), _ptr(arr["rat"]),
+                     _ptr(arr["slack"]), _ptr(eps), _ptr(eph), _ptr(summ))
+    _check(rc, "sta")
+    out = {k: v[:P] for k, v in arr.items()}
+    out["ep_setup"] = eps[:E]
+    out["ep_hold"] = eph[:E]
+    out["endpoints"] = endpoints(d)
+    out["wns_setup"] = summ[:, 0].copy()
+    out["tns_setup"] = summ[:, 1].copy()
+    out["wns_hold"] = summ[:, 2].copy()
+    out["tns_hold"] = summ[:, 3].copy()
+    out["worst_setup"] = summ[:, 4].copy()
+    out["worst_hold"] = summ[:, 5].copy()
+    out["n_viol_setup"] = summ[:, 6].astype(np.int64)
+    out["n_viol_hold"] = summ[:, 7].astype(np.int64)
+    return out
+
+
+def objective_grad(d: dict, w_tns: float = 1.0, w_wns: float = 1.0):
+    """O6: smoothed J, per-corner (TNS_g, WNS_g) and dJ/d(cell x, y) in FP64."""
+    lib = _load()
+    s, keep = _marshal(d, use_rc=False)
+    K = int(d.get("n_corners", 1))
+    J = np.zeros(1, np.float64)
+    terms = np.zeros((K, 2), np.float64)
+    g = np.zeros((max(int(d["n_cells"]), 1), 2), np.float64)
+    _check(lib.orc_objective_grad(C.byref(s), float(w_tns), float(w_wns), _ptr(J), _ptr(terms), _ptr(g)),
+           "objective_grad")
+    return float(J[0]), terms, g[: int(d["n_cells"])]
+
+
+def objective(d: dict, w_tns: float = 1.0, w_wns: float = 1.0) -> float:
+    lib = _load()
+    s, keep = _marshal(d, use_rc=False)
+    J = np.zeros(1, np.float64)
+    _check(lib.orc_objective(C.byref(s), float(w_tns), float(w_wns), _ptr(J)), "objective")
+    return float(J[0])

@@ -1,0 +1,739 @@
+/*
+ * sta_oracle.c -- plain, slow, FP64 reference static timing analysis.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Nothing in the product path may link, load or
+ * call this file: it exists so that tests/, the smoke check and the CPU
+ * baseline leg of the benchmark can compare the GPU library against an
+ * independent computation.  It shares no code, header, table or constant
+ * with the CUDA library.
+ *
+ * What it computes (HeteroSTA, arXiv 2511.11660): the graph-based part of
+ * the STA engine the paper accelerates -- delay calculation followed by
+ * graph propagation (Sec. I lists these among the engine's steps), with the
+ * Elmore net delay calculator (Sec. III, "Delay models"), NLDM cell tables
+ * (Sec. IV-A names the NLDM delay model), RC supplied as a
+ * flattened tree or built from pin positions and unit R/C (Sec. III,
+ * "Parasitics (RC) inputs") and WNS/TNS plus pin slacks as reports (Sec. III,
+ * "Report options").  The paper prints no formula; it defers the STA
+ * definitions to the textbook it cites (Bhasker & Chadha, "Static Timing
+ * Analysis for Nanometer Designs").  Every formula below is therefore the
+ * textbook / TAU-contest reading of those terms:
+ *
+ *   O1  NLDM bilinear interpolation, linear extrapolation off the table edge;
+ *   O2  cell arcs with unateness, rise/fall x early/late, worst-slew merge;
+ *   O3  Elmore delay and second moment on RC trees, slew = sqrt(s^2 + var);
+ *   O4  endpoint required times, back-propagated required times, slack,
+ *       WNS = min(0, worst endpoint slack), TNS = sum of negative slacks;
+ *   O6  log-sum-exp smoothed objective and its hand-written FP64 adjoint
+ *       with respect to cell (x, y) (not in the paper; it feeds a placer the
+ *       way the paper's DREAMPlace integration consumes pin slacks, Sec. IV-C).
+ *
+ * Order of evaluation is a memoised depth-first topological order of the pin
+ * graph (no levelisation), single threaded, every value in double.
+ *
+ * Units: ns, pF for library tables and loads; Ohm and fF for RC
+ * (Ohm * fF = 1e-6 ns); um for positions.
+ *
+ * Parity pins (tests/test_oracle_*.py) fix: hand-worked LUT values, exact
+ * reproduction of noise-free bilinear tables, closed-form Elmore / second
+ * moment on single RC, uniform chains and star trees, brute-force path
+ * enumeration on tiny DAGs, the GBA >= PBA invariant, slack = RAT - AT,
+ * early <= late, WNS/TNS definitions, and the adjoint against central finite
+ * differences of this file's own smoothed forward pass.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* pin roles (the netlist description uses the same integer codes) */
+enum { R_PI = 0, R_PO = 1, R_IN = 2, R_OUT = 3, R_D = 4, R_CK = 5, R_Q = 6 };
+/* arc sense per (cell type, input slot) */
+enum { S_NONE = -1, S_POS = 0, S_NEG = 1, S_NON = 2, S_RISE = 3 };
+/* table order inside one arc: delay rise, delay fall, slew rise, slew fall */
+enum { TB_DR = 0, TB_DF = 1, TB_SR = 2, TB_SF = 3 };
+
+#define NLDM 7          /* 7 x 7 tables */
+#define MAXSLOT 3       /* at most three inputs per cell */
+
+enum { OK = 0, ERR_INVAL = 1, ERR_CYCLE = 2, ERR_NOMEM = 3 };
+
+typedef struct {
+    /* cell library */
+    int32_t n_types;
+    const int32_t *type_nin;   /* input pins per type (a DFF has D and CK) */
+    const int32_t *type_kind;  /* 0 combinational, 1 flip-flop */
+    const int32_t *arc_sense;  /* [n_types * 3] */
+    const float *lut_idx1;     /* [n_types][3][4][7] input slew, ns */
+    const float *lut_idx2;     /* [n_types][3][4][7] load, pF */
+    const float *lut_val;      /* [n_types][3][4][49] value[i_slew * 7 + j_load] */
+    const float *pin_cap;      /* [n_types * 4] pF by pin slot */
+    double setup_ns, hold_ns, po_cap_pf;
+    /* netlist */
+    int32_t n_cells;
+    const int32_t *cell_type;
+    const int32_t *cell_pin_ptr; /* [n_cells + 1] */
+    const int32_t *cell_pin;     /* pins of each cell, slot order, output last */
+    int32_t n_pins;
+    const int8_t *pin_role;
+    int32_t n_nets;
+    const int32_t *net_pin_ptr;  /* [n_nets + 1] */
+    const int32_t *net_pin;      /* driver first, then sinks */
+    /* parasitics: an RC tree per net, or positions (star tree) */
+    const int32_t *rc_ptr;       /* [n_nets + 1] node ranges */
+    const int32_t *rc_parent;    /* local parent index, -1 at the root (node 0) */
+    const int32_t *rc_pin_node;  /* per net_pin entry: local node it sits on */
+    const float *rc_R;           /* Ohm, per node (root ignored) */
+    const float *rc_C;           /* fF wire capacitance, per node */
+    const float *cell_xy;        /* [n_cells * 2] um; used when rc_ptr == NULL */
+    const float *port_xy;        /* [n_pins * 2] um; read for PI/PO pins only */
+    double r_per_um, c_per_um;   /* Ohm/um, fF/um */
+    /* constraints */
+    double period_ns, clk_slew_ns, pi_at_ns, pi_slew_ns;
+    int32_t n_corners;
+    const float *lut_scale;      /* [n_corners] */
+    const float *rc_scale;       /* [n_corners] */
+    double gamma_ns;             /* 0: hard max/min merges; > 0: log-sum-exp */
+} orc_design;
+
+/* ------------------------------------------------------------------ O1 */
+
+/* Bilinear NLDM lookup at (s, l) with partial derivatives.
+ * Segment i = largest index with idx1[i] <= s, clamped to [0, 5]; t is not
+ * clamped, so inputs off the table extrapolate linearly from the edge
+ * segment.  Same for the load axis. */
+int orc_lut_eval(const float *idx1, const float *idx2, const float *val,
+                 double s, double l, double *out3)
+{
+    int i = 0, j = 0;
+    for (int k = 1; k <= NLDM - 2; ++k) {
+        if ((double)idx1[k] <= s) i = k;
+        if ((double)idx2[k] <= l) j = k;
+    }
+    double x0 = idx1[i], x1 = idx1[i + 1], y0 = idx2[j], y1 = idx2[j + 1];
+    double t = (s - x0) / (x1 - x0);
+    double u = (l - y0) / (y1 - y0);
+    double v00 = val[i * NLDM + j], v10 = val[(i + 1) * NLDM + j];
+    double v01 = val[i * NLDM + j + 1], v11 = val[(i + 1) * NLDM + j + 1];
+    out3[0] = (1 - t) * (1 - u) * v00 + t * (1 - u) * v10 + (1 - t) * u * v01 + t * u * v11;
+    out3[1] = ((1 - u) * (v10 - v00) + u * (v11 - v01)) / (x1 - x0);
+    out3[2] = ((1 - t) * (v01 - v00) + t * (v11 - v10)) / (y1 - y0);
+    return OK;
+}
+
+/* ------------------------------------------------------------------ O3 */
+
+/* Elmore delay and second moment of one RC tree whose nodes are listed
+ * parent before child (parent[0] = -1, R[0] ignored).
+ *   Cdown_i = C_i + sum over children Cdown
+ *   D_i     = D_parent + R_i Cdown_i
+ *   M_i     = C_i D_i + sum over children M
+ *   beta_i  = beta_parent + R_i M_i
+ *   var_i   = 2 beta_i - D_i^2 */
+int orc_rc_tree(int32_t n, const int32_t *parent, const double *R, const double *C,
+                double *cdown, double *D, double *beta, double *var)
+{
+    if (n <= 0 || parent[0] != -1) return ERR_INVAL;
+    for (int32_t i = 1; i < n; ++i)
+        if (parent[i] < 0 || parent[i] >= i) return ERR_INVAL;
+    double *M = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!M) return ERR_NOMEM;
+    for (int32_t i = 0; i < n; ++i) cdown[i] = C[i];
+    for (int32_t i = n - 1; i >= 1; --i) cdown[parent[i]] += cdown[i];
+    D[0] = 0.0;
+    for (int32_t i = 1; i < n; ++i) D[i] = D[parent[i]] + R[i] * cdown[i];
+    for (int32_t i = 0; i < n; ++i) M[i] = C[i] * D[i];
+    for (int32_t i = n - 1; i >= 1; --i) M[parent[i]] += M[i];
+    beta[0] = 0.0;
+    for (int32_t i = 1; i < n; ++i) beta[i] = beta[parent[i]] + R[i] * M[i];
+    for (int32_t i = 0; i < n; ++i) var[i] = 2.0 * beta[i] - D[i] * D[i];
+    free(M);
+    return OK;
+}
+
+/* --------------------------------------------------------- helpers */
+
+typedef struct {
+    int32_t *cell, *slot;     /* per pin: owning cell (-1 for ports) and slot */
+    int32_t *drv_net;         /* per pin: net it drives, -1 */
+    int32_t *sink_net;        /* per pin: net it is a sink of, -1 */
+    int32_t *sink_entry;      /* per pin: index into net_pin of that sink entry */
+} pin_info;
+
+static void free_info(pin_info *pi)
+{
+    free(pi->cell); free(pi->slot); free(pi->drv_net); free(pi->sink_net); free(pi->sink_entry);
+}
+
+static int build_info_checked(const orc_design *d, pin_info *pi);
+
+static int build_info(const orc_design *d, pin_info *pi)
+{
+    memset(pi, 0, sizeof(*pi));
+    int rc = build_info_checked(d, pi);
+    if (rc) free_info(pi);
+    return rc;
+}
+
+static int build_info_checked(const orc_design *d, pin_info *pi)
+{
+    size_t P = (size_t)d->n_pins;
+    pi->cell = (int32_t *)malloc(P * 4); pi->slot = (int32_t *)malloc(P * 4);
+    pi->drv_net = (int32_t *)malloc(P * 4); pi->sink_net = (int32_t *)malloc(P * 4);
+    pi->sink_entry = (int32_t *)malloc(P * 4);
+    if (!pi->cell || !pi->slot || !pi->drv_net || !pi->sink_net || !pi->sink_entry) return ERR_NOMEM;
+    for (size_t p = 0; p < P; ++p) {
+        pi->cell[p] = -1; pi->slot[p] = -1; pi->drv_net[p] = -1;
+        pi->sink_net[p] = -1; pi->sink_entry[p] = -1;
+    }
+    for (int32_t c = 0; c < d->n_cells; ++c) {
+        int32_t t = d->cell_type[c];
+        if (t < 0 || t >= d->n_types) return ERR_INVAL;
+        if (d->cell_pin_ptr[c + 1] - d->cell_pin_ptr[c] != d->type_nin[t] + 1) return ERR_INVAL;
+        for (int32_t k = d->cell_pin_ptr[c]; k < d->cell_pin_ptr[c + 1]; ++k) {
+            int32_t p = d->cell_pin[k];
+            if (p < 0 || p >= d->n_pins || pi->cell[p] != -1) return ERR_INVAL;
+            pi->cell[p] = c; pi->slot[p] = k - d->cell_pin_ptr[c];
+        }
+    }
+    for (int32_t n = 0; n < d->n_nets; ++n) {
+        int32_t b = d->net_pin_ptr[n], e = d->net_pin_ptr[n + 1];
+        if (e - b < 1) return ERR_INVAL;
+        int32_t drv = d->net_pin[b];
+        if (drv < 0 || drv >= d->n_pins || pi->drv_net[drv] != -1) return ERR_INVAL;
+        int r = d->pin_role[drv];
+        if (r != R_PI && r != R_OUT && r != R_Q) return ERR_INVAL;
+        pi->drv_net[drv] = n;
+        for (int32_t k = b + 1; k < e; ++k) {
+            int32_t s = d->net_pin[k];
+            if (s < 0 || s >= d->n_pins || pi->sink_net[s] != -1) return ERR_INVAL;
+            int rs = d->pin_role[s];
+            if (rs != R_IN && rs != R_D && rs != R_PO) return ERR_INVAL;
+            pi->sink_net[s] = n; pi->sink_entry[s] = k;
+        }
+    }
+    /* every pin that needs a driver has one */
+    for (int32_t p = 0; p < d->n_pins; ++p) {
+        int r = d->pin_role[p];
+        if ((r == R_IN || r == R_D || r == R_PO) && pi->sink_net[p] < 0) return ERR_INVAL;
+    }
+    return OK;
+}
+
+static const float *tab_base(const float *arr, int32_t t, int32_t slot, int tb, int per)
+{
+    return arr + (((size_t)t * MAXSLOT + (size_t)slot) * 4 + (size_t)tb) * (size_t)per;
+}
+
+static double lut(const orc_design *d, int32_t t, int32_t slot, int tb, double s, double l,
+                  double *ds, double *dl)
+{
+    double o[3];
+    orc_lut_eval(tab_base(d->lut_idx1, t, slot, tb, NLDM), tab_base(d->lut_idx2, t, slot, tb, NLDM),
+                 tab_base(d->lut_val, t, slot, tb, NLDM * NLDM), s, l, o);
+    if (ds) *ds = o[1];
+    if (dl) *dl = o[2];
+    return o[0];
+}
+
+/* rf_in values that reach rf_out through an arc of the given sense */
+static int rf_inputs(int sense, int rf_out, int *rf_in)
+{
+    switch (sense) {
+    case S_POS: rf_in[0] = rf_out; return 1;
+    case S_NEG: rf_in[0] = 1 - rf_out; return 1;
+    case S_NON: rf_in[0] = 0; rf_in[1] = 1; return 2;
+    case S_RISE: rf_in[0] = 0; return 1;
+    default: return 0;
+    }
+}
+
+/* merge: late = max, early = min; gamma > 0 replaces them by
+ * gamma * log sum exp(x / gamma) (and its mirror for min). */
+static double merge(const double *x, int n, int late, double gamma)
+{
+    if (n == 0) return late ? -INFINITY : INFINITY;
+    double m = x[0];
+    for (int i = 1; i < n; ++i) m = late ? fmax(m, x[i]) : fmin(m, x[i]);
+    if (gamma <= 0.0) return m;
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s += exp((late ? (x[i] - m) : (m - x[i])) / gamma);
+    return late ? m + gamma * log(s) : m - gamma * log(s);
+}
+
+static double pin_cap_of(const orc_design *d, const pin_info *pi, int32_t p)
+{
+    if (d->pin_role[p] == R_PO) return d->po_cap_pf;
+    int32_t c = pi->cell[p];
+    return d->pin_cap[(size_t)d->cell_type[c] * 4 + (size_t)pi->slot[p]];
+}
+
+static void pin_xy(const orc_design *d, const pin_info *pi, int32_t p, double *x, double *y)
+{
+    int32_t c = pi->cell[p];
+    if (c >= 0) { *x = d->cell_xy[2 * (size_t)c]; *y = d->cell_xy[2 * (size_t)c + 1]; }
+    else if (d->port_xy) { *x = d->port_xy[2 * (size_t)p]; *y = d->port_xy[2 * (size_t)p + 1]; }
+    else { *x = 0.0; *y = 0.0; }
+}
+
+/* Per-corner net quantities: load (pF) at each driver pin, Elmore delay (ns)
+ * and variance (ns^2) at each sink pin.  With rc_ptr == NULL the tree is the
+ * star of O3/A8: root at the driver, one segment per sink of Manhattan length
+ * L with R = r L and C = c L split half at each end, plus the sink pin cap. */
+int orc_net_delays(const orc_design *d, int32_t corner, double *load_pf, double *D_ns, double *V_ns2)
+{
+    pin_info pi;
+    int rc = build_info(d, &pi);
+    if (rc) return rc;
+    for (int32_t p = 0; p < d->n_pins; ++p) { load_pf[p] = 0.0; D_ns[p] = 0.0; V_ns2[p] = 0.0; }
+    double f = d->rc_scale ? d->rc_scale[corner] : 1.0;
+    for (int32_t n = 0; n < d->n_nets; ++n) {
+        int32_t b = d->net_pin_ptr[n], e = d->net_pin_ptr[n + 1];
+        int32_t nn;
+        if (d->rc_ptr) nn = d->rc_ptr[n + 1] - d->rc_ptr[n];
+        else nn = e - b;             /* root + one node per sink */
+        int32_t *par = (int32_t *)malloc(sizeof(int32_t) * (size_t)nn);
+        double *R = (double *)malloc(sizeof(double) * (size_t)nn);
+        double *C = (double *)malloc(sizeof(double) * (size_t)nn);
+        double *cd = (double *)malloc(sizeof(double) * (size_t)nn);
+        double *Dd = (double *)malloc(sizeof(double) * (size_t)nn);
+        double *be = (double *)malloc(sizeof(double) * (size_t)nn);
+        double *va = (double *)malloc(sizeof(double) * (size_t)nn);
+        if (!par || !R || !C || !cd || !Dd || !be || !va) { rc = ERR_NOMEM; goto next; }
+        if (d->rc_ptr) {
+            int32_t o = d->rc_ptr[n];
+            for (int32_t i = 0; i < nn; ++i) {
+                par[i] = d->rc_parent[o + i];
+                R[i] = i ? f * (double)d->rc_R[o + i] : 0.0;
+                C[i] = f * (double)d->rc_C[o + i];
+            }
+            for (int32_t k = b + 1; k < e; ++k) {
+                int32_t node = d->rc_pin_node[k];
+                if (node < 0 || node >= nn) { rc = ERR_INVAL; goto next; }
+                C[node] += 1e3 * pin_cap_of(d, &pi, d->net_pin[k]);   /* pF -> fF */
+            }
+        } else {
+            double xd, yd;
+            pin_xy(d, &pi, d->net_pin[b], &xd, &yd);
+            par[0] = -1; R[0] = 0.0; C[0] = 0.0;
+            for (int32_t k = b + 1; k < e; ++k) {
+                double xs, ys;
+                pin_xy(d, &pi, d->net_pin[k], &xs, &ys);
+                double L = fabs(xd - xs) + fabs(yd - ys);
+                int32_t i = k - b;
+                par[i] = 0;
+                R[i] = f * d->r_per_um * L;
+                C[i] = 0.5 * f * d->c_per_um * L + 1e3 * pin_cap_of(d, &pi, d->net_pin[k]);
+                C[0] += 0.5 * f * d->c_per_um * L;
+            }
+        }
+        rc = orc_rc_tree(nn, par, R, C, cd, Dd, be, va);
+        if (rc) goto next;
+        load_pf[d->net_pin[b]] = 1e-3 * cd[0];
+        for (int32_t k = b + 1; k < e; ++k) {
+            int32_t node = d->rc_ptr ? d->rc_pin_node[k] : k - b;
+            D_ns[d->net_pin[k]] = 1e-6 * Dd[node];
+            V_ns2[d->net_pin[k]] = 1e-12 * va[node];
+        }
+    next:
+        free(par); free(R); free(C); free(cd); free(Dd); free(be); free(va);
+        if (rc) { free_info(&pi); return rc; }
+    }
+    free_info(&pi);
+    return OK;
+}
+
+/* ------------------------------------------------------ topological order */
+
+/* Fan-in pins of p in the timing graph: net sink <- driver, cell output <-
+ * the cell's arc inputs, flip-flop Q <- CK.  PI and CK are sources. */
+static int fanins(const orc_design *d, const pin_info *pi, int32_t p, int32_t *out)
+{
+    int r = d->pin_role[p];
+    if (r == R_IN || r == R_D || r == R_PO) {
+        out[0] = d->net_pin[d->net_pin_ptr[pi->sink_net[p]]];
+        return 1;
+    }
+    if (r == R_OUT || r == R_Q) {
+        int32_t c = pi->cell[p], t = d->cell_type[c], n = 0;
+        for (int32_t s = 0; s < d->type_nin[t]; ++s)
+            if (d->arc_sense[t * MAXSLOT + s] != S_NONE) out[n++] = d->cell_pin[d->cell_pin_ptr[c] + s];
+        return n;
+    }
+    return 0;
+}
+
+/* Memoised depth-first search; order[] receives every pin after all of its
+ * fan-ins.  Returns ERR_CYCLE on a combinational loop. */
+static int topo_order(const orc_design *d, const pin_info *pi, int32_t *order)
+{
+    int32_t P = d->n_pins;
+    int8_t *mark = (int8_t *)calloc((size_t)P, 1);    /* 0 new, 1 on stack, 2 done */
+    int32_t *stk = (int32_t *)malloc(sizeof(int32_t) * (size_t)P);
+    int32_t *it = (int32_t *)malloc(sizeof(int32_t) * (size_t)P);
+    if (!mark || !stk || !it) { free(mark); free(stk); free(it); return ERR_NOMEM; }
+    int32_t nout = 0;
+    for (int32_t root = 0; root < P; ++root) {
+        if (mark[root]) continue;
+        int32_t sp = 0;
+        stk[sp] = root; it[sp] = 0; mark[root] = 1;
+        while (sp >= 0) {
+            int32_t p = stk[sp], fi[MAXSLOT + 1];
+            int nf = fanins(d, pi, p, fi);
+            if (it[sp] < nf) {
+                int32_t q = fi[it[sp]++];
+                if (mark[q] == 1) { free(mark); free(stk); free(it); return ERR_CYCLE; }
+                if (mark[q] == 0) { ++sp; stk[sp] = q; it[sp] = 0; mark[q] = 1; }
+            } else {
+                mark[p] = 2; order[nout++] = p; --sp;
+            }
+        }
+    }
+    free(mark); free(stk); free(it);
+    return OK;
+}
+
+int orc_topo_order(const orc_design *d, int32_t *order)
+{
+    pin_info pi;
+    int rc = build_info(d, &pi);
+    if (rc) return rc;
+    rc = topo_order(d, &pi, order);
+    free_info(&pi);
+    return rc;
+}
+
+/* ------------------------------------------------------- O2: forward */
+
+#define IX(p, k, j) ((((size_t)(p)) * (size_t)K + (size_t)(k)) * 4 + (size_t)(j))
+#define JJ(el, rf) ((el) * 2 + (rf))   /* el 0 early, 1 late; rf 0 rise, 1 fall */
+
+static void forward_corner(const orc_design *d, const pin_info *pi, const int32_t *order, int32_t k,
+                           const double *load, const double *Dn, const double *Vn,
+                           double *at, double *slew)
+{
+    int32_t K = d->n_corners;
+    double sc = d->lut_scale ? d->lut_scale[k] : 1.0;
+    for (int32_t oi = 0; oi < d->n_pins; ++oi) {
+        int32_t p = order[oi];
+        int r = d->pin_role[p];
+        if (r == R_PI || r == R_CK) {
+            double a = (r == R_PI) ? d->pi_at_ns : 0.0;
+            double s = (r == R_PI) ? d->pi_slew_ns : d->clk_slew_ns;
+            for (int j = 0; j < 4; ++j) { at[IX(p, k, j)] = a; slew[IX(p, k, j)] = s; }
+        } else if (r == R_IN || r == R_D || r == R_PO) {
+            int32_t drv = d->net_pin[d->net_pin_ptr[pi->sink_net[p]]];
+            for (int j = 0; j < 4; ++j) {
+                double sd = slew[IX(drv, k, j)];
+                at[IX(p, k, j)] = at[IX(drv, k, j)] + Dn[p];
+                slew[IX(p, k, j)] = sqrt(sd * sd + Vn[p]);
+            }
+        } else { /* R_OUT or R_Q */
+            int32_t c = pi->cell[p], t = d->cell_type[c];
+            double l = load[p];
+            for (int el = 0; el < 2; ++el)
+                for (int rfo = 0; rfo < 2; ++rfo) {
+                    double ca[2 * MAXSLOT], cs[2 * MAXSLOT];
+                    int n = 0;
+                    for (int32_t s = 0; s < d->type_nin[t]; ++s) {
+                        int sense = d->arc_sense[t * MAXSLOT + s], rfi[2];
+                        int m = rf_inputs(sense, rfo, rfi);
+                        int32_t a = d->cell_pin[d->cell_pin_ptr[c] + s];
+                        for (int q = 0; q < m; ++q) {
+                            double si = slew[IX(a, k, JJ(el, rfi[q]))];
+                            ca[n] = at[IX(a, k, JJ(el, rfi[q]))] +
+                                    sc * lut(d, t, s, rfo ? TB_DF : TB_DR, si, l, 0, 0);
+                            cs[n] = sc * lut(d, t, s, rfo ? TB_SF : TB_SR, si, l, 0, 0);
+                            ++n;
+                        }
+                    }
+                    at[IX(p, k, JJ(el, rfo))] = merge(ca, n, el, d->gamma_ns);
+                    slew[IX(p, k, JJ(el, rfo))] = merge(cs, n, el, d->gamma_ns);
+                }
+        }
+    }
+}
+
+/* ----------------------------------------------- O4: required times, slack */
+
+static void backward_corner(const orc_design *d, const pin_info *pi, const int32_t *order, int32_t k,
+                            const double *load, const double *Dn, const double *slew, double *rat)
+{
+    int32_t K = d->n_corners;
+    double sc = d->lut_scale ? d->lut_scale[k] : 1.0;
+    for (int32_t oi = d->n_pins - 1; oi >= 0; --oi) {
+        int32_t p = order[oi];
+        int r = d->pin_role[p];
+        double rl[2] = {INFINITY, INFINITY}, re[2] = {-INFINITY, -INFINITY};
+        if (r == R_D) {
+            rl[0] = rl[1] = d->period_ns - d->setup_ns;
+            re[0] = re[1] = d->hold_ns;
+        } else if (r == R_PO) {
+            rl[0] = rl[1] = d->period_ns;
+            re[0] = re[1] = 0.0;
+        } else {
+            if (pi->drv_net[p] >= 0) {
+                int32_t n = pi->drv_net[p];
+                for (int32_t q = d->net_pin_ptr[n] + 1; q < d->net_pin_ptr[n + 1]; ++q) {
+                    int32_t s = d->net_pin[q];
+                    for (int rf = 0; rf < 2; ++rf) {
+                        rl[rf] = fmin(rl[rf], rat[IX(s, k, JJ(1, rf))] - Dn[s]);
+                        re[rf] = fmax(re[rf], rat[IX(s, k, JJ(0, rf))] - Dn[s]);
+                    }
+                }
+            }
+            if ((r == R_IN || r == R_CK) && pi->cell[p] >= 0) {
+                int32_t c = pi->cell[p], t = d->cell_type[c], s = pi->slot[p];
+                int sense = d->arc_sense[t * MAXSLOT + s];
+                int32_t z = d->cell_pin[d->cell_pin_ptr[c] + d->type_nin[t]];
+                for (int rfo = 0; rfo < 2; ++rfo) {
+                    int rfi[2];
+                    int m = rf_inputs(sense, rfo, rfi);
+                    for (int q = 0; q < m; ++q) {
+                        int ri = rfi[q];
+                        double dl = sc * lut(d, t, s, rfo ? TB_DF : TB_DR, slew[IX(p, k, JJ(1, ri))], load[z], 0, 0);
+                        double de = sc * lut(d, t, s, rfo ? TB_DF : TB_DR, slew[IX(p, k, JJ(0, ri))], load[z], 0, 0);
+                        rl[ri] = fmin(rl[ri], rat[IX(z, k, JJ(1, rfo))] - dl);
+                        re[ri] = fmax(re[ri], rat[IX(z, k, JJ(0, rfo))] - de);
+                    }
+                }
+            }
+        }
+        rat[IX(p, k, JJ(0, 0))] = re[0]; rat[IX(p, k, JJ(0, 1))] = re[1];
+        rat[IX(p, k, JJ(1, 0))] = rl[0]; rat[IX(p, k, JJ(1, 1))] = rl[1];
+    }
+}
+
+/* Full analysis.  Arrays at/slew/rat/slack are [n_pins][n_corners][4] with
+ * the inner index el * 2 + rf (el 0 early / hold, 1 late / setup).
+ * Endpoints are the DFF D pins and POs in ascending pin id; ep_setup and
+ * ep_hold are [n_endpoints][n_corners] (min over rise/fall).  summary is
+ * [n_corners][8]: WNS setup, TNS setup, WNS hold, TNS hold, worst setup
+ * slack, worst hold slack, setup violations, hold violations. */
+int orc_sta(const orc_design *d, double *at, double *slew, double *rat, double *slack,
+            double *ep_setup, double *ep_hold, double *summary)
+{
+    pin_info pi;
+    int rc = build_info(d, &pi);
+    if (rc) { return rc; }
+    int32_t P = d->n_pins, K = d->n_corners;
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(P ? P : 1));
+    double *load = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    double *Dn = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    double *Vn = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    if (!order || !load || !Dn || !Vn) { rc = ERR_NOMEM; goto done; }
+    rc = topo_order(d, &pi, order);
+    if (rc) goto done;
+    for (int32_t k = 0; k < K; ++k) {
+        rc = orc_net_delays(d, k, load, Dn, Vn);
+        if (rc) goto done;
+        forward_corner(d, &pi, order, k, load, Dn, Vn, at, slew);
+        backward_corner(d, &pi, order, k, load, Dn, slew, rat);
+        for (int32_t p = 0; p < P; ++p)
+            for (int rf = 0; rf < 2; ++rf) {
+                slack[IX(p, k, JJ(0, rf))] = at[IX(p, k, JJ(0, rf))] - rat[IX(p, k, JJ(0, rf))];
+                slack[IX(p, k, JJ(1, rf))] = rat[IX(p, k, JJ(1, rf))] - at[IX(p, k, JJ(1, rf))];
+            }
+        double *sm = summary + (size_t)k * 8;
+        double wns_s = 0, tns_s = 0, wns_h = 0, tns_h = 0, worst_s = INFINITY, worst_h = INFINITY;
+        double nv_s = 0, nv_h = 0;
+        int32_t e = 0;
+        for (int32_t p = 0; p < P; ++p) {
+            int r = d->pin_role[p];
+            if (r != R_D && r != R_PO) continue;
+            double ss = fmin(slack[IX(p, k, JJ(1, 0))], slack[IX(p, k, JJ(1, 1))]);
+            double hs = fmin(slack[IX(p, k, JJ(0, 0))], slack[IX(p, k, JJ(0, 1))]);
+            ep_setup[(size_t)e * K + k] = ss;
+            ep_hold[(size_t)e * K + k] = hs;
+            ++e;
+            worst_s = fmin(worst_s, ss); worst_h = fmin(worst_h, hs);
+            if (ss < 0) { tns_s += ss; nv_s += 1; wns_s = fmin(wns_s, ss); }
+            if (hs < 0) { tns_h += hs; nv_h += 1; wns_h = fmin(wns_h, hs); }
+        }
+        sm[0] = wns_s; sm[1] = tns_s; sm[2] = wns_h; sm[3] = tns_h;
+        sm[4] = worst_s; sm[5] = worst_h; sm[6] = nv_s; sm[7] = nv_h;
+    }
+done:
+    free(order); free(load); free(Dn); free(Vn);
+    free_info(&pi);
+    return rc;
+}
+
+/* ---------------------------------------------- O6: objective and adjoint */
+
+static double softplus(double z) { return (z > 0 ? z : 0) + log1p(exp(-fabs(z))); }
+static double sigmoid(double z)
+{
+    if (z >= 0) return 1.0 / (1.0 + exp(-z));
+    double e = exp(z);
+    return e / (1.0 + e);
+}
+
+/* Smoothed objective J = w_tns * TNS_g + w_wns * WNS_g summed over corners,
+ * with per endpoint setup slack s_e = smin_g over rise/fall of (RAT - AT_late)
+ *   TNS_g = - sum_e g * softplus(-s_e / g)
+ *   WNS_g = - g * log sum_e exp(-s_e / g)
+ * and its gradient with respect to every cell (x, y) (ports are fixed).  The
+ * forward merges are the log-sum-exp ones of merge() with the same gamma.
+ * Requires the position (star tree) parasitics and gamma_ns > 0.
+ * terms[k*2 + 0] = TNS_g, terms[k*2 + 1] = WNS_g of corner k (may be NULL). */
+int orc_objective_grad(const orc_design *d, double w_tns, double w_wns, double *J_out,
+                       double *terms, double *grad_xy)
+{
+    if (d->rc_ptr || !d->cell_xy || d->gamma_ns <= 0.0) return ERR_INVAL;
+    pin_info pi;
+    int rc = build_info(d, &pi);
+    if (rc) return rc;
+    int32_t P = d->n_pins, K = d->n_corners;
+    double g = d->gamma_ns;
+    size_t PK4 = (size_t)(P ? P : 1) * (size_t)K * 4;
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(P ? P : 1));
+    double *load = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    double *Dn = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    double *Vn = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    double *at = (double *)malloc(sizeof(double) * PK4);
+    double *sl = (double *)malloc(sizeof(double) * PK4);
+    double *aat = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1) * 2);
+    double *asl = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1) * 2);
+    double *aload = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    double *aD = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    double *aV = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    double *seed = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    double J = 0.0;
+    if (!order || !load || !Dn || !Vn || !at || !sl || !aat || !asl || !aload || !aD || !aV || !seed) {
+        rc = ERR_NOMEM; goto done;
+    }
+    for (int32_t c = 0; c < 2 * d->n_cells; ++c) grad_xy[c] = 0.0;
+    rc = topo_order(d, &pi, order);
+    if (rc) goto done;
+    for (int32_t k = 0; k < K; ++k) {
+        double sc = d->lut_scale ? d->lut_scale[k] : 1.0;
+        double f = d->rc_scale ? d->rc_scale[k] : 1.0;
+        rc = orc_net_delays(d, k, load, Dn, Vn);
+        if (rc) goto done;
+        forward_corner(d, &pi, order, k, load, Dn, Vn, at, sl);
+        /* endpoint slacks and the objective */
+        double mx = -INFINITY;
+        for (int32_t p = 0; p < P; ++p) {
+            int r = d->pin_role[p];
+            if (r != R_D && r != R_PO) continue;
+            double req = (r == R_D) ? d->period_ns - d->setup_ns : d->period_ns;
+            double y[2] = {req - at[IX(p, k, JJ(1, 0))], req - at[IX(p, k, JJ(1, 1))]};
+            seed[p] = merge(y, 2, 0, g);              /* smooth min over rise/fall */
+            mx = fmax(mx, -seed[p] / g);
+        }
+        double tns = 0.0, lse = 0.0;
+        for (int32_t p = 0; p < P; ++p) {
+            int r = d->pin_role[p];
+            if (r != R_D && r != R_PO) continue;
+            tns += -g * softplus(-seed[p] / g);
+            lse += exp(-seed[p] / g - mx);
+        }
+        double wns = (lse > 0) ? -g * (mx + log(lse)) : 0.0;
+        if (terms) { terms[2 * k] = tns; terms[2 * k + 1] = wns; }
+        J += w_tns * tns + w_wns * wns;
+        /* seed the adjoint: dJ/dAT_late at each endpoint */
+        for (int32_t p = 0; p < P; ++p) {
+            aat[2 * p] = aat[2 * p + 1] = 0.0; asl[2 * p] = asl[2 * p + 1] = 0.0;
+            aload[p] = 0.0; aD[p] = 0.0; aV[p] = 0.0;
+        }
+        for (int32_t p = 0; p < P; ++p) {
+            int r = d->pin_role[p];
+            if (r != R_D && r != R_PO) continue;
+            double s = seed[p];
+            double dj = w_tns * sigmoid(-s / g) + w_wns * exp(-s / g - mx) / lse;
+            double req = (r == R_D) ? d->period_ns - d->setup_ns : d->period_ns;
+            for (int rf = 0; rf < 2; ++rf) {
+                double y = req - at[IX(p, k, JJ(1, rf))];
+                double om = exp(-(y - s) / g);          /* d smin / d y_rf */
+                aat[2 * p + rf] += -dj * om;            /* d y / d AT = -1 */
+            }
+        }
+        /* reverse topological sweep, late quantities only */
+        for (int32_t oi = P - 1; oi >= 0; --oi) {
+            int32_t p = order[oi];
+            int r = d->pin_role[p];
+            if (r == R_IN || r == R_D || r == R_PO) {
+                int32_t drv = d->net_pin[d->net_pin_ptr[pi.sink_net[p]]];
+                for (int rf = 0; rf < 2; ++rf) {
+                    double sp = sl[IX(p, k, JJ(1, rf))], sd = sl[IX(drv, k, JJ(1, rf))];
+                    aat[2 * drv + rf] += aat[2 * p + rf];
+                    asl[2 * drv + rf] += asl[2 * p + rf] * sd / sp;
+                    aD[p] += aat[2 * p + rf];
+                    aV[p] += asl[2 * p + rf] / (2.0 * sp);
+                }
+            } else if (r == R_OUT || r == R_Q) {
+                int32_t c = pi.cell[p], t = d->cell_type[c];
+                double l = load[p];
+                for (int rfo = 0; rfo < 2; ++rfo) {
+                    double ca[2 * MAXSLOT], cs[2 * MAXSLOT], dds[2 * MAXSLOT], ddl[2 * MAXSLOT];
+                    double sds[2 * MAXSLOT], sdl[2 * MAXSLOT];
+                    int32_t src[2 * MAXSLOT], srf[2 * MAXSLOT];
+                    int n = 0;
+                    for (int32_t s = 0; s < d->type_nin[t]; ++s) {
+                        int sense = d->arc_sense[t * MAXSLOT + s], rfi[2];
+                        int m = rf_inputs(sense, rfo, rfi);
+                        int32_t a = d->cell_pin[d->cell_pin_ptr[c] + s];
+                        for (int q = 0; q < m; ++q) {
+                            double si = sl[IX(a, k, JJ(1, rfi[q]))];
+                            ca[n] = at[IX(a, k, JJ(1, rfi[q]))] +
+                                    sc * lut(d, t, s, rfo ? TB_DF : TB_DR, si, l, &dds[n], &ddl[n]);
+                            cs[n] = sc * lut(d, t, s, rfo ? TB_SF : TB_SR, si, l, &sds[n], &sdl[n]);
+                            src[n] = a; srf[n] = rfi[q];
+                            ++n;
+                        }
+                    }
+                    double ma = merge(ca, n, 1, g), ms = merge(cs, n, 1, g);
+                    double Aa = aat[2 * p + rfo], As = asl[2 * p + rfo];
+                    for (int i = 0; i < n; ++i) {
+                        double wa = exp((ca[i] - ma) / g), ws = exp((cs[i] - ms) / g);
+                        int32_t a = src[i];
+                        int rf = srf[i];
+                        aload[p] += Aa * wa * sc * ddl[i] + As * ws * sc * sdl[i];
+                        if (d->pin_role[a] == R_CK) continue;   /* ideal clock: fixed */
+                        aat[2 * a + rf] += Aa * wa;
+                        asl[2 * a + rf] += Aa * wa * sc * dds[i] + As * ws * sc * sds[i];
+                    }
+                }
+            }
+        }
+        /* star-tree partials: D = R (C/2 + Cp), var = D^2, load = sum (cL + Cp) */
+        for (int32_t n = 0; n < d->n_nets; ++n) {
+            int32_t b = d->net_pin_ptr[n], e = d->net_pin_ptr[n + 1];
+            int32_t drv = d->net_pin[b];
+            double xd, yd;
+            pin_xy(d, &pi, drv, &xd, &yd);
+            for (int32_t q = b + 1; q < e; ++q) {
+                int32_t s = d->net_pin[q];
+                double xs, ys;
+                pin_xy(d, &pi, s, &xs, &ys);
+                double L = fabs(xd - xs) + fabs(yd - ys);
+                double cp = 1e3 * pin_cap_of(d, &pi, s);
+                double r = f * d->r_per_um, cc = f * d->c_per_um;
+                double Draw = r * L * (0.5 * cc * L + cp);
+                double dDdL = r * (cc * L + cp);
+                double dJdL = aD[s] * 1e-6 * dDdL + aV[s] * 1e-12 * 2.0 * Draw * dDdL + aload[drv] * 1e-3 * cc;
+                double sx = (xd > xs) - (xd < xs), sy = (yd > ys) - (yd < ys);
+                int32_t cd = pi.cell[drv], cs = pi.cell[s];
+                if (cd >= 0) { grad_xy[2 * cd] += dJdL * sx; grad_xy[2 * cd + 1] += dJdL * sy; }
+                if (cs >= 0) { grad_xy[2 * cs] -= dJdL * sx; grad_xy[2 * cs + 1] -= dJdL * sy; }
+            }
+        }
+    }
+    *J_out = J;
+done:
+    free(order); free(load); free(Dn); free(Vn); free(at); free(sl);
+    free(aat); free(asl); free(aload); free(aD); free(aV); free(seed);
+    free_info(&pi);
+    return rc;
+}
+
+/* Smoothed objective only (for finite differences in the tests). */
+int orc_objective(const orc_design *d, double w_tns, double w_wns, double *J_out)
+{
+    double *gx = (double *)malloc(sizeof(double) * (size_t)(2 * d->n_cells + 2));
+    if (!gx) return ERR_NOMEM;
+    int rc = orc_objective_grad(d, w_tns, w_wns, J_out, NULL, gx);
+    free(gx);
+    return rc;
+}

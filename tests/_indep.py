@@ -1,0 +1,168 @@
+"""Independent re-derivations used to pin the oracle (tests only).
+
+Nothing here calls the oracle or the GPU library.  Each routine computes a
+quantity from a different formula than the oracle uses:
+
+* Elmore delay and second moment from shared-path resistances
+  (D_i = sum_j R_ij C_j, beta_i = sum_j R_ij C_j D_j, R_ij = resistance of the
+  common part of the root->i and root->j paths) instead of the oracle's
+  two-sweep recurrences;
+* loads as plain sums of capacitances;
+* NLDM values by direct bilinear interpolation written out here;
+* arrival times by enumerating every path (no max/min merge until the end).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+PI, PO, IN, OUT, D, CK, Q = 0, 1, 2, 3, 4, 5, 6
+NONE, POS, NEG, NON, RISE = -1, 0, 1, 2, 3
+
+
+def shared_path_moments(parent, R, C):
+    """Elmore D and beta of every node by the shared-resistance sums."""
+    n = len(parent)
+    anc = []
+    for i in range(n):
+        path, k = set(), i
+        while k > 0:
+            path.add(k)
+            k = parent[k]
+        anc.append(path)
+    Rsh = np.zeros((n, n))
+    for i in range(n):
+        for j in range(n):
+            Rsh[i, j] = sum(R[k] for k in anc[i] & anc[j])
+    Dm = Rsh @ np.asarray(C, float)
+    beta = Rsh @ (np.asarray(C, float) * Dm)
+    return Dm, beta
+
+
+def bilinear(idx1, idx2, val, s, l):
+    idx1 = np.asarray(idx1, float)
+    idx2 = np.asarray(idx2, float)
+    v = np.asarray(val, float).reshape(7, 7)
+    i = int(np.clip(np.searchsorted(idx1, s, side="right") - 1, 0, 5))
+    j = int(np.clip(np.searchsorted(idx2, l, side="right") - 1, 0, 5))
+    t = (s - idx1[i]) / (idx1[i + 1] - idx1[i])
+    u = (l - idx2[j]) / (idx2[j + 1] - idx2[j])
+    return ((1 - t) * (1 - u) * v[i, j] + t * (1 - u) * v[i + 1, j]
+            + (1 - t) * u * v[i, j + 1] + t * u * v[i + 1, j + 1])
+
+
+class Net:
+    """Per-net parasitic quantities computed independently."""
+
+    def __init__(self, d, corner=0):
+        f = float(np.asarray(d["rc_scale"])[corner])
+        role = np.asarray(d["pin_role"])
+        cell_of = -np.ones(d["n_pins"], int)
+        slot_of = -np.ones(d["n_pins"], int)
+        cpp = np.asarray(d["cell_pin_ptr"])
+        cp = np.asarray(d["cell_pin"])
+        for c in range(d["n_cells"]):
+            for k in range(cpp[c], cpp[c + 1]):
+                cell_of[cp[k]] = c
+                slot_of[cp[k]] = k - cpp[c]
+        self.cell_of, self.slot_of = cell_of, slot_of
+        pin_cap = np.asarray(d["pin_cap"]).reshape(-1, 4)
+        ctype = np.asarray(d["cell_type"])
+
+        def cap(p):
+            if role[p] == PO:
+                return float(d["po_cap_pf"])
+            return float(pin_cap[ctype[cell_of[p]], slot_of[p]])
+
+        self.load, self.Dns, self.Vns, self.driver = {}, {}, {}, {}
+        npp = np.asarray(d["net_pin_ptr"])
+        npn = np.asarray(d["net_pin"])
+        for n in range(d["n_nets"]):
+            b, e = npp[n], npp[n + 1]
+            drv = int(npn[b])
+            sinks = [int(s) for s in npn[b + 1:e]]
+            if d.get("rc_ptr") is not None:
+                r0, r1 = d["rc_ptr"][n], d["rc_ptr"][n + 1]
+                par = [int(x) for x in d["rc_parent"][r0:r1]]
+                R = [0.0] + [f * float(x) for x in d["rc_R"][r0 + 1:r1]]
+                Cn = [f * float(x) for x in d["rc_C"][r0:r1]]
+                node = {s: int(d["rc_pin_node"][b + 1 + k]) for k, s in enumerate(sinks)}
+                for s in sinks:
+                    Cn[node[s]] += 1e3 * cap(s)
+            else:
+                xy = np.asarray(d["cell_xy"]).reshape(-1, 2)
+                pxy = np.asarray(d["port_xy"]).reshape(-1, 2)
+
+                def pos(p):
+                    return xy[cell_of[p]] if cell_of[p] >= 0 else pxy[p]
+
+                par, R, Cn, node = [-1], [0.0], [0.0], {}
+                for k, s in enumerate(sinks):
+                    L = float(np.abs(pos(drv).astype(float) - pos(s).astype(float)).sum())
+                    par.append(0)
+                    R.append(f * d["r_per_um"] * L)
+                    Cn.append(0.5 * f * d["c_per_um"] * L + 1e3 * cap(s))
+                    Cn[0] += 0.5 * f * d["c_per_um"] * L
+                    node[s] = k + 1
+            Dm, beta = shared_path_moments(par, R, Cn)
+            self.load[drv] = 1e-3 * sum(Cn)
+            for s in sinks:
+                self.Dns[s] = 1e-6 * Dm[node[s]]
+                self.Vns[s] = 1e-12 * (2 * beta[node[s]] - Dm[node[s]] ** 2)
+                self.driver[s] = drv
+
+
+def rf_in_of(sense, rf_out):
+    return {POS: [rf_out], NEG: [1 - rf_out], NON: [0, 1], RISE: [0]}.get(sense, [])
+
+
+def enumerate_paths(d, corner=0, with_slew=False):
+    """All (arrival, slew, rf) path values at every pin, by exhaustive
+    enumeration.  Cell delays are evaluated per path at the path's own slew
+    (path-based analysis)."""
+    net = Net(d, corner)
+    sc = float(np.asarray(d["lut_scale"])[corner])
+    role = np.asarray(d["pin_role"])
+    ctype = np.asarray(d["cell_type"])
+    cpp = np.asarray(d["cell_pin_ptr"])
+    cp = np.asarray(d["cell_pin"])
+    sense = np.asarray(d["arc_sense"]).reshape(-1, 3)
+    nin = np.asarray(d["type_nin"])
+    i1 = np.asarray(d["lut_idx1"]).reshape(-1, 3, 4, 7)
+    i2 = np.asarray(d["lut_idx2"]).reshape(-1, 3, 4, 7)
+    vv = np.asarray(d["lut_val"]).reshape(-1, 3, 4, 49)
+    memo = {}
+
+    def paths(p):
+        if p in memo:
+            return memo[p]
+        r = role[p]
+        if r == PI:
+            out = [(float(d["pi_at_ns"]), float(d["pi_slew_ns"]), rf) for rf in (0, 1)]
+        elif r == CK:
+            out = [(0.0, float(d["clk_slew_ns"]), rf) for rf in (0, 1)]
+        elif r in (IN, D, PO):
+            drv = net.driver[p]
+            out = [(a + net.Dns[p], np.sqrt(s * s + net.Vns[p]), rf) for a, s, rf in paths(drv)]
+        else:
+            c = net.cell_of[p]
+            t = ctype[c]
+            l = net.load.get(p, 0.0)
+            out = []
+            for slot in range(nin[t]):
+                se = sense[t, slot]
+                if se == NONE:
+                    continue
+                a_pin = cp[cpp[c] + slot]
+                for a, s, rf in paths(a_pin):
+                    if r == Q and rf != 0:
+                        continue
+                    for rfo in (0, 1):
+                        if rf not in rf_in_of(se, rfo):
+                            continue
+                        dl = sc * bilinear(i1[t, slot, rfo], i2[t, slot, rfo], vv[t, slot, rfo], s, l)
+                        sl = sc * bilinear(i1[t, slot, 2 + rfo], i2[t, slot, 2 + rfo], vv[t, slot, 2 + rfo], s, l)
+                        out.append((a + dl, sl, rfo))
+        memo[p] = out
+        return out
+
+    return {p: paths(p) for p in range(d["n_pins"])}
