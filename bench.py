@@ -1,0 +1,358 @@
+#!/usr/bin/env python
+"""Benchmark: timing arcs per second of the full STA pass on one B300.
+
+A step is one ``sta_update_timing`` -- net delay calculation, forward
+arrival/slew propagation, endpoint required times, backward required-time
+propagation with pin slacks, and the FP64 WNS/TNS reduction -- over the
+seeded 1M-cell synthetic design (depth 150, RC trees of 2-10 nodes, one
+corner).  Arcs are counted once per pass (cell arcs + net arcs).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank times its own
+replica of the design (replicas only: a single design's levels do not shard)
+and ``value`` sums the ranks' arcs over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "timing arcs/sec (fwd+bwd STA) and grad ms/iter at 1M cells, batched vs plain"
+UNIT = "arcs/s"
+WORKLOADS = {
+    "scale": "1M cells, depth 150, RC trees of 2-10 nodes, 1 corner, clock period at the 90th percentile "
+             "endpoint requirement (seed 0)",
+}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="scale", choices=sorted(WORKLOADS))
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--schedule", default="level", choices=["level", "dataflow"])
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the update only (no e2e, CPU baseline or clock sampling); for profilers")
+    return ap.parse_args()
+
+
+# --------------------------------------------------------------- helpers
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.init_process_group("gloo")
+            self.pg = dist
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x: float) -> float:
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([x], dtype=torch.float64)
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(", ") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm = [float(r[1]) for r in rows if len(r) > 8 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) > 8 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) > 8:
+                for n, v in zip(names, r[5:9]):
+                    if v.strip() == "Active":
+                        reasons.add(n)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def byte_model(st: dict, K: int) -> dict:
+    """Algorithmic (compulsory) bytes of one update per phase.
+    P pins, S net sinks (net arcs), Nn nets, N RC nodes, E endpoints, I items."""
+    P, S, Nn, N = st["n_pins"], st["n_net_arcs"], st["n_nets"], st["n_rc_nodes"]
+    E, I = st["n_endpoints"], st["n_items"]
+    net = 12 * N + 8 * S + K * (4 * Nn + 8 * S)
+    fwd = K * (64 * P + 8 * S + 4 * Nn) + 4 * S + 8 * I
+    bwd = K * (80 * P + 4 * S + 4 * Nn + 10 * E) + 4 * S + 4 * I
+    red = K * 8 * E
+    return {"net": net, "fwd": fwd, "bwd": bwd, "reduce": red, "total": net + fwd + bwd + red}
+
+
+def kernel_source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2511_11660_b300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
+            h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(kernel: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was taken on
+    the current kernel sources (else null)."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        t = json.load(open(p))
+    except (OSError, ValueError):
+        return None
+    e = t.get(kernel)
+    if not e or e.get("source_hash") != kernel_source_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+def make_workload(name: str, seed: int):
+    from paper_2511_11660_b300 import synth
+    return synth.workload(name, seed=seed)
+
+
+# ------------------------------------------------------------------ ours
+
+def run_ours(a, dist: Dist):
+    import torch
+    from paper_2511_11660_b300 import clock, sta, synth
+
+    torch.cuda.set_device(dist.local)
+    dev = dist.local
+    d = make_workload(a.workload, a.seed)
+    dstats = synth.design_stats(d)
+    ctx = sta.Context(d, device=dev)
+    if a.schedule == "dataflow":
+        ctx.set_schedule(sta.SCHED_DATAFLOW, 0)
+    # clock period: 90th-percentile endpoint requirement from a run at T = 0
+    ctx.set_clock(0.0)
+    ctx.update_timing()
+    s0, _, _, _ = ctx.get_endpoint_slack()
+    T, half_gap = clock.period_in_gap(-s0[:, 0])
+    ctx.set_clock(T)
+    st = ctx.stats()
+    K = st["n_corners"]
+    arcs = dstats["arcs"]
+    stream = torch.cuda.current_stream()
+
+    for _ in range(a.warmup):
+        ctx.update_timing()
+    torch.cuda.synchronize()
+
+    sampler = ClockSampler(dev) if not a.no_extras else None
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        ctx.update_timing()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    dist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    clocks = sampler.stop() if sampler else None
+    ms_step = dist.max(ms_total) / a.steps
+    value = arcs * dist.world / (ms_step * 1e-3)
+    rep = ctx.report_slack()[0]
+
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": dist.world, "steps": a.steps,
+           "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "%s: %s" % (a.workload, WORKLOADS[a.workload]),
+                      "cells": dstats["cells"], "pins": dstats["pins"], "cell_arcs": dstats["cell_arcs"],
+                      "net_arcs": dstats["net_arcs"], "rc_nodes": dstats["rc_nodes"],
+                      "endpoints": dstats["endpoints"], "levels": st["n_levels"], "corners": K,
+                      "period_ns": T, "schedule": a.schedule,
+                      "parallelism": "replicas x%d" % dist.world if dist.world > 1 else "1 GPU",
+                      "l2": "no flush: per-pass working set %.0f MB > 126 MB L2" % (st["device_bytes"] / 1e6),
+                      "wns_setup_ns": rep["wns_setup"], "tns_setup_ns": rep["tns_setup"],
+                      "setup_violations": rep["n_viol_setup"]},
+           "gpu_launches": st["launches_per_update"] * a.steps}
+
+    if a.no_extras:
+        if dist.rank == 0:
+            print(json.dumps(out))
+        return
+
+    # ---- roofline of the dominant kernel, from per-phase CUDA events
+    ctx.set_profiling(True)
+    acc = np.zeros(4)
+    n_prof = 5
+    for _ in range(n_prof):
+        ctx.update_timing()
+        ctx.sync()
+        acc += np.array(ctx.last_timings())
+    ctx.set_profiling(False)
+    ph = acc / n_prof
+    bm = byte_model(st, K)
+    pk, pk_kind = peaks()
+    kern = "k_fwd_level" if ph[1] >= ph[2] else "k_bwd_level"
+    phase_ms = ph[1] if kern == "k_fwd_level" else ph[2]
+    phase_bytes = bm["fwd"] if kern == "k_fwd_level" else bm["bwd"]
+    launches = st["n_levels"]
+    achieved = phase_bytes / (phase_ms * 1e-3) / 1e9
+    tr = measured_traffic(kern)
+    out["roofline"] = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": pk["hbm_gbs"],
+                       "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
+                       "traffic": tr, "peak_source": pk_kind + " (hbm_gbs, copy burst)",
+                       "bytes_per_launch": phase_bytes / launches, "launches_per_pass": launches,
+                       "phase_ms": {"net": ph[0], "fwd": ph[1], "bwd": ph[2], "reduce": ph[3]},
+                       "pass_bytes_model": bm["total"],
+                       "pass_frac": bm["total"] / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"]}
+
+    # ---- end to end through the C ABI with host buffers
+    if d.get("rc_R") is not None:
+        Rh = torch.from_numpy(np.asarray(d["rc_R"], np.float32)).pin_memory()
+        Ch = torch.from_numpy(np.asarray(d["rc_C"], np.float32)).pin_memory()
+        h2d = Rh.numel() * 4 + Ch.numel() * 4
+        feed = lambda: ctx.set_rc(Rh, Ch)  # noqa: E731
+    else:
+        XY = torch.from_numpy(np.asarray(d["cell_xy"], np.float32)).pin_memory()
+        h2d = XY.numel() * 4
+        feed = lambda: ctx.set_positions(XY)  # noqa: E731
+    E = st["n_endpoints"]
+    for _ in range(2):
+        feed(); ctx.update_timing(); ctx.get_endpoint_slack(); ctx.report_slack()
+    torch.cuda.synchronize()
+    dist.barrier()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        feed()
+        ctx.update_timing()
+        ctx.get_endpoint_slack()
+        ctx.report_slack()
+    torch.cuda.synchronize()
+    t_e2e = dist.max(time.perf_counter() - t0) / a.steps
+    out["e2e"] = {"value": arcs * dist.world / t_e2e, "unit": UNIT,
+                  "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(E * K * 10 + 64 * K),
+                  "ms_per_step": t_e2e * 1e3,
+                  "what": "sta_set_rc from pinned host R/C + sta_update_timing + endpoint slacks and "
+                          "violation flags to host + sta_report_slack"}
+
+    # ---- the FP64 oracle on the host cores (rank 0, one GPU only)
+    if dist.rank == 0 and dist.world == 1:
+        out["cpu_baseline"] = cpu_baseline(d, T, budget_s=12.0)
+    if clocks is not None:
+        out["clocks"] = clocks
+    if dist.rank == 0:
+        print(json.dumps(out))
+
+
+def cpu_baseline(d: dict, T: float, budget_s: float) -> dict:
+    import oracle
+    from paper_2511_11660_b300 import synth
+    dd = dict(d)
+    dd["period_ns"] = T
+    arcs = synth.design_stats(d)["arcs"]
+    n, t = 0, 0.0
+    while t < budget_s:
+        t0 = time.perf_counter()
+        oracle.sta(dd)
+        t += time.perf_counter() - t0
+        n += 1
+    return {"value": arcs * n / t, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "the full workload design, %d oracle passes (%.1f s), FP64, single thread" % (n, t)}
+
+
+# ------------------------------------------------------------- reference
+
+def run_reference(a, dist: Dist):
+    """The FP64 oracle timed on the host cores on this arm's workload."""
+    if dist.rank != 0:
+        return
+    from paper_2511_11660_b300 import synth
+    import oracle
+    d = make_workload(a.workload, a.seed)
+    arcs = synth.design_stats(d)["arcs"]
+    for _ in range(a.warmup):
+        oracle.sta(d)
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        oracle.sta(d)
+    t = (time.perf_counter() - t0) / a.steps
+    v = arcs / t
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": dist.world,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "%s: %s" % (a.workload, WORKLOADS[a.workload]), "arcs": arcs},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                            "sample": "one full oracle pass of the workload design per step"},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    a = parse()
+    dist = Dist()
+    try:
+        if a.impl == "reference":
+            run_reference(a, dist)
+        else:
+            run_ours(a, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,278 @@
+/*
+ * sta.h -- C ABI of libsta.so, a B300 (sm_103a) graph-based static timing
+ * analysis library.
+ *
+ * What it computes follows HeteroSTA (arXiv 2511.11660):
+ *   - inputs are a flattened CSR netlist handed over by a host flow instead
+ *     of parsed files (Sec. III, "Heterogeneous netlist database"), a cell
+ *     library of NLDM tables (Sec. IV-A), parasitics either as flattened RC
+ *     trees or as pin positions plus unit R/C (Sec. III, "Parasitics (RC)
+ *     inputs") and one ideal clock;
+ *   - delay calculation uses the Elmore calculator (Sec. III, "Delay
+ *     models"), extended with the second moment for the output slew;
+ *   - outputs are pin slacks and WNS/TNS (Sec. III, "Report options"),
+ *     left on the GPU or copied to the host at the caller's choice.
+ * The paper gives no formulas; the library implements the textbook readings
+ * (NLDM bilinear interpolation with edge extrapolation; Elmore delay and
+ * slew = sqrt(s^2 + 2*m2 - D^2); max/min propagation of arrival times over
+ * rise/fall x early/late; required times propagated backwards; setup slack
+ * = RAT - AT, hold slack = AT - RAT; WNS = min(0, worst endpoint slack),
+ * TNS = sum of negative endpoint slacks).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns sta_status; no C++ exception crosses the ABI.
+ *   - Pointers in sta_design_desc are HOST pointers, read during the call
+ *     only and copied; the caller keeps ownership.
+ *   - Arguments typed with sta_mem say where a caller buffer lives
+ *     (STA_HOST or STA_DEVICE, device = the context's device).
+ *   - Streams are cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Calls that take a stream are asynchronous unless they return host data.
+ *   - Asynchronous device errors, and the device-side error word set by the
+ *     kernels' own bounds / wait-limit checks, are reported by the next call
+ *     that synchronises (sta_report_slack, sta_sync, sta_backward with host
+ *     output).
+ *   - Units: ns, pF for tables and loads; Ohm, fF for RC; um for positions.
+ *   - Per-pin arrays use the layout [n_pins][n_corners][4] with the inner
+ *     index el*2 + rf: el 0 = early (hold), 1 = late (setup); rf 0 = rise,
+ *     1 = fall.  Endpoints are the DFF D pins and primary outputs in
+ *     ascending pin id.
+ */
+#ifndef STA_H
+#define STA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sta_ctx sta_ctx;   /* opaque, owned by the library */
+
+typedef enum {
+    STA_OK = 0,
+    STA_EINVAL = 1,    /* malformed input (message in sta_last_error) */
+    STA_ECYCLE = 2,    /* combinational loop in the timing graph */
+    STA_ENOMEM = 3,    /* device or host allocation failed */
+    STA_ECUDA = 4,     /* CUDA runtime error */
+    STA_ETIMEOUT = 5,  /* a bounded device-side wait gave up */
+    STA_ESTATE = 6     /* call out of order (e.g. report before update) */
+} sta_status;
+
+typedef enum { STA_HOST = 0, STA_DEVICE = 1 } sta_mem;
+
+/* pin roles */
+enum { STA_PIN_PI = 0, STA_PIN_PO = 1, STA_PIN_IN = 2, STA_PIN_OUT = 3,
+       STA_PIN_D = 4, STA_PIN_CK = 5, STA_PIN_Q = 6 };
+/* timing sense of the arc from an input slot to the cell output */
+enum { STA_SENSE_NONE = -1, STA_SENSE_POS = 0, STA_SENSE_NEG = 1,
+       STA_SENSE_NON = 2, STA_SENSE_RISE = 3 /* clock rising edge -> Q */ };
+/* which per-pin array sta_get_pin_state copies */
+enum { STA_AT = 0, STA_SLEW = 1, STA_RAT = 2, STA_SLACK = 3 };
+/* propagation schedules (sta_set_schedule) */
+enum { STA_SCHED_LEVEL = 0,      /* one kernel launch per level, graph-captured */
+       STA_SCHED_DATAFLOW = 1 }; /* one persistent kernel per pass, per-item ready flags */
+
+/*
+ * Cell library.  Per type: type_nin inputs (1..3) followed by one output.
+ * A flip-flop (type_kind 1) has exactly two inputs, D (slot 0, sense NONE,
+ * a setup/hold check pin) and CK (slot 1, sense RISE, arc CK -> Q).
+ * Tables: per (type, slot) four 7x7 NLDM tables in the order delay rise,
+ * delay fall, slew rise, slew fall; idx1 = input slew axis (ns), idx2 = load
+ * axis (pF), both strictly increasing; val[i_slew * 7 + j_load].
+ * Array shapes: type_nin/type_kind [n_types]; arc_sense [n_types*3];
+ * lut_idx1/lut_idx2 [n_types*3*4*7]; lut_val [n_types*3*4*49];
+ * pin_cap [n_types*4] (pF, by slot).
+ */
+typedef struct {
+    int32_t n_types;
+    const int32_t *type_nin;
+    const int32_t *type_kind;
+    const int32_t *arc_sense;
+    const float *lut_idx1;
+    const float *lut_idx2;
+    const float *lut_val;
+    const float *pin_cap;
+    float setup_ns, hold_ns;   /* flip-flop setup / hold against the ideal clock */
+    float po_cap_pf;           /* load of a primary output pin */
+} sta_library;
+
+/*
+ * One design.  Cells: cell c owns pins cell_pin[cell_pin_ptr[c] ..
+ * cell_pin_ptr[c+1]) in slot order (inputs, then the output), roles IN..OUT
+ * or D, CK, Q.  Pins that belong to no cell are ports (PI or PO).  Nets:
+ * net n lists net_pin[net_pin_ptr[n] .. net_pin_ptr[n+1]) with its driver
+ * (PI, OUT or Q) first, then its sinks (IN, D or PO).  Every IN, D and PO pin
+ * is the sink of exactly one net; CK pins are on no net (ideal clock).
+ *
+ * Parasitics, one of:
+ *   RC trees: net n has nodes rc_ptr[n] .. rc_ptr[n+1) listed parent before
+ *     child; rc_parent is the local parent index (-1 at node 0, the driver);
+ *     rc_R (Ohm, node to parent; node 0 ignored), rc_C (fF, wire);
+ *     rc_pin_node[k] is the local node of the pin net_pin[k] (0 for the
+ *     driver).  Sink pin capacitances are added at their nodes.
+ *   Positions (rc_ptr == NULL): a star tree per net from the driver to each
+ *     sink, segment R = r_per_um * L, C = c_per_um * L split half to each
+ *     end, L = Manhattan distance; pins sit at their cell's cell_xy[2c..],
+ *     ports at port_xy[2p..] (port_xy may be NULL: ports at the origin).
+ * Corners: n_corners >= 1; corner k multiplies every table value by
+ * lut_scale[k] and every wire R and C by rc_scale[k] (NULL = all 1).
+ * gamma_ns > 0 selects log-sum-exp smoothed max/min merges (differentiable
+ * mode, required for sta_backward); 0 = exact max/min.
+ */
+typedef struct {
+    const sta_library *lib;
+    int32_t n_cells;
+    const int32_t *cell_type;
+    const int32_t *cell_pin_ptr;
+    const int32_t *cell_pin;
+    int32_t n_pins;
+    const int8_t *pin_role;
+    int32_t n_nets;
+    const int32_t *net_pin_ptr;
+    const int32_t *net_pin;
+    const int32_t *rc_ptr;
+    const int32_t *rc_parent;
+    const int32_t *rc_pin_node;
+    const float *rc_R;
+    const float *rc_C;
+    const float *cell_xy;
+    const float *port_xy;
+    float r_per_um, c_per_um;
+    float period_ns;      /* ideal clock period: setup capture edge */
+    float clk_slew_ns;    /* slew at every CK pin (arrival 0, rising edge) */
+    float pi_at_ns, pi_slew_ns;
+    int32_t n_corners;
+    const float *lut_scale;
+    const float *rc_scale;
+    float gamma_ns;
+} sta_design_desc;
+
+/* Sizes of a levelised design (sta_plan / sta_stats). */
+typedef struct {
+    int64_t n_pins, n_cells, n_nets, n_items;    /* items: PIs + cells */
+    int64_t n_cell_arcs, n_net_arcs, n_rc_nodes, n_endpoints;
+    int32_t n_levels;                            /* propagation levels (items) */
+    int32_t n_corners;
+    int32_t max_level_width;
+    int32_t n_designs;                           /* 1, or the batch size */
+    int64_t device_bytes;                        /* device memory the context holds */
+    int32_t launches_per_update;                 /* kernels one sta_update_timing launches */
+} sta_plan_info;
+
+/* Per-corner summary returned by sta_report_slack. */
+typedef struct {
+    double wns_setup, tns_setup;   /* WNS = min(0, worst), TNS = sum of negatives */
+    double wns_hold, tns_hold;
+    double worst_setup, worst_hold;   /* raw worst endpoint slacks (may be > 0) */
+    int64_t n_viol_setup, n_viol_hold;
+} sta_corner_report;
+
+/* Host only, no GPU needed: validate a design and levelise its timing graph.
+ * Fills *out.  Returns STA_EINVAL (message via sta_plan_error) or
+ * STA_ECYCLE.  Defined by the CSR database of Sec. III plus the level
+ * ordering that graph propagation (Sec. I) needs. */
+sta_status sta_plan(const sta_design_desc *desc, sta_plan_info *out);
+/* Message of the last failed sta_plan / sta_create on this thread. */
+const char *sta_plan_error(void);
+
+/* Validate, levelise, renumber pins level-major and upload everything to
+ * `device`.  The context owns its device memory (cudaMalloc) until
+ * sta_destroy.  Errors: STA_EINVAL, STA_ECYCLE, STA_ENOMEM, STA_ECUDA. */
+sta_status sta_create(const sta_design_desc *desc, int device, sta_ctx **out);
+
+/* Many independent designs in one context: they are packed into one graph
+ * whose levels are the union of the designs' levels, so one launch sequence
+ * times all of them.  Every design must use the same library (same pointer
+ * contents), the same n_corners and the same parasitic kind.  Reports are per
+ * design (sta_report_slack_design).  Errors as sta_create. */
+sta_status sta_create_batch(const sta_design_desc *const *descs, int32_t n_designs, int device,
+                            sta_ctx **out);
+
+/* Replace RC values (same topology): R and C as in sta_design_desc, in the
+ * caller's node order, total n_rc_nodes floats each.  Takes effect at the
+ * next sta_update_timing. */
+sta_status sta_set_rc(sta_ctx *ctx, const float *R, const float *C, sta_mem mem);
+
+/* Replace cell positions (positions mode): cell_xy[n_cells*2] um, copied on
+ * `stream`.  Errors: STA_ESTATE if the context uses RC trees. */
+sta_status sta_set_positions(sta_ctx *ctx, const float *cell_xy, sta_mem mem, void *stream);
+
+/* Replace cell types (resizing), host array [n_cells]; each new type must
+ * have the same number of inputs and the same kind as the old one. */
+sta_status sta_set_cell_types(sta_ctx *ctx, const int32_t *cell_type);
+
+/* Change the ideal clock period (ns) used by the next sta_update_timing. */
+sta_status sta_set_clock(sta_ctx *ctx, float period_ns);
+
+/* Select the propagation schedule (STA_SCHED_*) and its parameter (threads
+ * per block for LEVEL; resident blocks per SM for DATAFLOW, 0 = auto). */
+sta_status sta_set_schedule(sta_ctx *ctx, int32_t schedule, int32_t param);
+
+/* Full analysis on `stream`: net delay calculation, forward arrival/slew
+ * propagation, endpoint required times, backward required-time propagation,
+ * pin and endpoint slacks, FP64 WNS/TNS.  Asynchronous. */
+sta_status sta_update_timing(sta_ctx *ctx, void *stream);
+
+/* Wait for the context's work on `stream` and surface device errors. */
+sta_status sta_sync(sta_ctx *ctx, void *stream);
+
+/* Synchronise and fill reports[n_corners] (design 0 of a batch). */
+sta_status sta_report_slack(sta_ctx *ctx, void *stream, sta_corner_report *reports);
+/* Same for design `d` of a batch context. */
+sta_status sta_report_slack_design(sta_ctx *ctx, int32_t d, void *stream, sta_corner_report *reports);
+
+/* Copy one per-pin array (STA_AT, STA_SLEW, STA_RAT or STA_SLACK) into
+ * out[n_pins][n_corners][4] in the caller's pin numbering, on `stream`.
+ * For a batch, pins of design d follow those of design d-1. */
+sta_status sta_get_pin_state(sta_ctx *ctx, int32_t which, float *out, sta_mem mem, void *stream);
+
+/* Endpoint slacks: setup[n_endpoints][n_corners] = min over rise/fall of the
+ * late slack, hold likewise with the early slack, viol_* = slack < 0 as
+ * 0/1 bytes.  Any output may be NULL. */
+sta_status sta_get_endpoint_slack(sta_ctx *ctx, float *setup, float *hold, uint8_t *viol_setup,
+                                  uint8_t *viol_hold, sta_mem mem, void *stream);
+
+/* Differentiable mode (gamma_ns > 0, positions): after sta_update_timing,
+ * compute the smoothed objective
+ *   J = w_tns * TNS_g + w_wns * WNS_g,  summed over corners, with
+ *   s_e   = smooth min over rise/fall of (RAT_e - AT_late,e),
+ *   TNS_g = -sum_e g * softplus(-s_e / g),  WNS_g = -g * log sum_e exp(-s_e / g)
+ * and its gradient with respect to every cell position by a hand-written
+ * adjoint of the forward pass (LSE merges, NLDM interpolation, star Elmore).
+ * J_out: 1 double (+ per-corner TNS_g, WNS_g pairs if terms != NULL);
+ * grad_xy: n_cells*2 doubles.  All three in `mem`; host outputs synchronise.
+ * Errors: STA_ESTATE (no prior update, or not differentiable). */
+sta_status sta_backward(sta_ctx *ctx, double w_tns, double w_wns, double *J_out, double *terms,
+                        double *grad_xy, sta_mem mem, void *stream);
+
+/* Device views in the library's internal (level-major) pin order; valid
+ * until the next sta_update_timing or sta_destroy.  gpu_pin_of[p] maps a
+ * caller pin id to its internal index (device int32 array). */
+typedef struct {
+    const float *at, *slew, *rat, *slack;   /* [n_pins][n_corners][4] internal order */
+    const int32_t *gpu_pin_of;              /* [n_pins] */
+} sta_views;
+sta_status sta_get_arrays(sta_ctx *ctx, sta_views *out);
+
+/* Sizes and the device bytes held. */
+sta_status sta_stats(const sta_ctx *ctx, sta_plan_info *out);
+
+/* Wall time of the last update's passes measured with CUDA events when
+ * enabled by sta_set_profiling(ctx, 1); ms[0..3] = net delays, forward,
+ * backward (incl. endpoints and slack), reduction. */
+sta_status sta_set_profiling(sta_ctx *ctx, int32_t on);
+sta_status sta_last_timings(sta_ctx *ctx, float *ms4);
+
+/* Message for the last failed call on this context (never NULL). */
+const char *sta_last_error(const sta_ctx *ctx);
+const char *sta_status_string(sta_status s);
+
+/* Free the context and its device memory.  NULL is accepted. */
+void sta_destroy(sta_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STA_H */

@@ -1,0 +1,28 @@
+// kernels.h -- host entry points of the device passes.
+#pragma once
+
+#include <vector>
+
+#include "device.cuh"
+
+namespace sta {
+
+// Host-side description of the launch sequence.
+struct HostSched {
+    int S = 0;
+    std::vector<int32_t> stage_ptr;   // host copy of the level offsets
+    int n_tiles = 0;                  // RC tiles (tree mode)
+    bool placed = false;
+    int threads = 128;                // threads per block of the level kernels
+};
+
+// Net delays, forward levels, endpoints, backward levels, reduction.  With
+// `ev` (5 events) the phase boundaries are recorded: ev[0] start, ev[1] after
+// net delays, ev[2] after forward + endpoints, ev[3] after backward, ev[4]
+// after the reduction.
+void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev = nullptr);
+
+void launch_gather_pins(const float4 *arr, const int32_t *gpu_of, float4 *out, int P, int K, cudaStream_t st);
+void launch_gather_f32(const float *src, const int32_t *idx, float *dst, int n, cudaStream_t st);
+
+}  // namespace sta

@@ -1,0 +1,645 @@
+// sta_api.cu -- the C ABI of libsta.so (see include/sta.h).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "kernels.h"
+#include "plan.h"
+#include "sta.h"
+
+using sta::DevCtx;
+using sta::HostSched;
+using sta::Plan;
+
+struct sta_ctx {
+    int device = 0;
+    Plan plan;
+    DevCtx dc{};
+    HostSched hs;
+    std::vector<void *> allocs;
+    size_t bytes = 0;
+    int32_t *d_gpu_of = nullptr;
+    int32_t *d_rc_src = nullptr;
+    float *d_rc_tmp = nullptr;
+    float4 *d_gather_tmp = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;
+    int schedule = STA_SCHED_LEVEL;
+    int sched_param = 0;
+    bool updated = false;
+    bool profiling = false;
+    cudaEvent_t ev[5] = {};
+    float last_ms[4] = {0, 0, 0, 0};
+    std::string msg;
+    // caller pin -> (cell, slot) for resizing
+    std::vector<int32_t> pin_cell_c, pin_slot_c;
+};
+
+namespace {
+
+thread_local std::string g_plan_err;
+
+struct CudaFail {
+    cudaError_t e;
+    const char *what;
+};
+
+#define CK(call)                                        \
+    do {                                                \
+        cudaError_t _e = (call);                        \
+        if (_e != cudaSuccess) throw CudaFail{_e, #call}; \
+    } while (0)
+
+sta_status fail(sta_ctx *c, sta_status st, const std::string &m)
+{
+    if (c) c->msg = m;
+    return st;
+}
+
+sta_status from_cuda(sta_ctx *c, const CudaFail &f)
+{
+    const sta_status st = (f.e == cudaErrorMemoryAllocation) ? STA_ENOMEM : STA_ECUDA;
+    return fail(c, st, std::string(f.what) + ": " + cudaGetErrorString(f.e));
+}
+
+template <class T>
+T *dev_alloc(sta_ctx *c, size_t n)
+{
+    void *p = nullptr;
+    const size_t b = std::max<size_t>(n * sizeof(T), 16);
+    CK(cudaMalloc(&p, b));
+    c->allocs.push_back(p);
+    c->bytes += b;
+    return static_cast<T *>(p);
+}
+
+template <class T>
+T *upload(sta_ctx *c, const std::vector<T> &v)
+{
+    T *p = dev_alloc<T>(c, v.size());
+    if (!v.empty()) CK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return p;
+}
+
+void drop_graph(sta_ctx *c)
+{
+    if (c->exec) cudaGraphExecDestroy(c->exec);
+    if (c->graph) cudaGraphDestroy(c->graph);
+    c->exec = nullptr;
+    c->graph = nullptr;
+}
+
+void record_pass(sta_ctx *c, cudaStream_t st, cudaEvent_t *ev = nullptr)
+{
+    sta::launch_level_pass(c->dc, c->hs, st, ev);
+}
+
+void ensure_graph(sta_ctx *c)
+{
+    if (c->exec) return;
+    CK(cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    record_pass(c, c->cap_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (e != cudaSuccess) throw CudaFail{e, "cudaStreamEndCapture"};
+    c->graph = g;
+    CK(cudaGraphInstantiate(&c->exec, c->graph, 0));
+}
+
+sta_status create_from_plan(sta_ctx *c, int device)
+{
+    Plan &pl = c->plan;
+    c->device = device;
+    CK(cudaSetDevice(device));
+    CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+    DevCtx &d = c->dc;
+    d.P = pl.P;
+    d.I = pl.I;
+    d.S = pl.S;
+    d.E = pl.E;
+    d.K = pl.K;
+    d.T = pl.T;
+    d.C = pl.C;
+    d.n_designs = pl.n_designs;
+    d.period = pl.period;
+    d.clk_slew = pl.clk_slew;
+    d.pi_at = pl.pi_at;
+    d.pi_slew = pl.pi_slew;
+    d.setup = pl.setup;
+    d.hold = pl.hold;
+    d.gamma = pl.gamma;
+    d.inv_gamma = pl.gamma > 0 ? 1.f / pl.gamma : 0.f;
+    d.r_per_um = pl.r_per_um;
+    d.c_per_um = pl.c_per_um;
+    d.lut = upload(c, pl.lut);
+    d.type_nin = upload(c, pl.type_nin);
+    d.type_kind = upload(c, pl.type_kind);
+    d.arc_sense = upload(c, pl.arc_sense);
+    d.lut_scale = upload(c, pl.lut_scale);
+    d.rc_scale = upload(c, pl.rc_scale);
+    d.item_pin0 = upload(c, pl.item_pin0);
+    d.item_type = upload(c, pl.item_type);
+    d.item_cell = upload(c, pl.item_cell);
+    d.fo_ptr = upload(c, pl.fo_ptr);
+    d.fo_pin = upload(c, pl.fo_pin);
+    d.fo_node = upload(c, pl.fo_node);
+    d.fo_cap = upload(c, pl.fo_cap);
+    d.rc_ptr = upload(c, pl.rc_ptr);
+    d.tile_item = upload(c, pl.tile_item);
+    d.rc_parent = upload(c, pl.rc_parent);
+    d.rc_R = upload(c, pl.rc_R);
+    d.rc_C = upload(c, pl.rc_C);
+    d.drv_of = upload(c, pl.drv_of);
+    d.pin_cell = upload(c, pl.pin_cell);
+    d.port_xy = upload(c, pl.port_xy);
+    d.cell_xy = upload(c, pl.cell_xy.empty() ? std::vector<float>(2 * (size_t)pl.C, 0.f) : pl.cell_xy);
+    d.ep_pin = upload(c, pl.ep_pin);
+    d.ep_is_d = upload(c, pl.ep_is_d);
+    d.ep_design_ptr = upload(c, pl.ep_design_ptr);
+    c->d_gpu_of = upload(c, pl.gpu_of);
+    {
+        std::vector<int32_t> src(pl.rc_src.begin(), pl.rc_src.end());
+        c->d_rc_src = upload(c, src);
+    }
+    const size_t PK = (size_t)pl.P * pl.K;
+    d.at = dev_alloc<float4>(c, PK);
+    d.slew = dev_alloc<float4>(c, PK);
+    d.rat = dev_alloc<float4>(c, PK);
+    d.slack = dev_alloc<float4>(c, PK);
+    d.netD = dev_alloc<float>(c, PK);
+    d.netV = dev_alloc<float>(c, PK);
+    d.load = dev_alloc<float>(c, PK);
+    CK(cudaMemset(d.netD, 0, PK * sizeof(float)));
+    CK(cudaMemset(d.netV, 0, PK * sizeof(float)));
+    CK(cudaMemset(d.load, 0, PK * sizeof(float)));
+    const size_t EK = (size_t)pl.E * pl.K;
+    d.ep_setup = dev_alloc<float>(c, EK);
+    d.ep_hold = dev_alloc<float>(c, EK);
+    d.viol_setup = dev_alloc<uint8_t>(c, EK);
+    d.viol_hold = dev_alloc<uint8_t>(c, EK);
+    d.report = dev_alloc<double>(c, (size_t)pl.n_designs * pl.K * 8);
+    d.err = dev_alloc<unsigned>(c, 1);
+    CK(cudaMemset(d.err, 0, sizeof(unsigned)));
+    if (pl.n_big_tiles > 0) {
+        d.scratch_a = dev_alloc<float>(c, (size_t)pl.NN);
+        d.scratch_b = dev_alloc<float>(c, (size_t)pl.NN);
+    }
+    HostSched &h = c->hs;
+    h.S = pl.S;
+    h.stage_ptr = pl.stage_ptr;
+    h.n_tiles = (int)pl.tile_item.size() - 1;
+    h.placed = pl.placed;
+    h.threads = 128;
+    for (auto &e : c->ev) CK(cudaEventCreate(&e));
+    CK(cudaDeviceSynchronize());
+    return STA_OK;
+}
+
+cudaStream_t as_stream(void *s) { return static_cast<cudaStream_t>(s); }
+
+// Kernel launches of one update under the current schedule.
+int32_t launches_per_update(const sta_ctx *c)
+{
+    const Plan &pl = c->plan;
+    int32_t n = 0;
+    if (pl.placed) n += pl.I > 0;
+    else n += (int32_t)pl.tile_item.size() > 1;
+    int32_t levels = 0;
+    for (int32_t s = 0; s < pl.S; ++s) levels += pl.stage_ptr[s + 1] > pl.stage_ptr[s];
+    n += 2 * levels;
+    n += pl.E > 0;
+    n += 1;   // reduction
+    return n;
+}
+
+sta_status check_device_error(sta_ctx *c)
+{
+    unsigned err = 0;
+    CK(cudaMemcpy(&err, c->dc.err, sizeof(unsigned), cudaMemcpyDeviceToHost));
+    if (err) {
+        CK(cudaMemset(c->dc.err, 0, sizeof(unsigned)));
+        if (err & sta::kErrTimeout) return fail(c, STA_ETIMEOUT, "a device-side wait reached its limit");
+        return fail(c, STA_ECUDA, "device-side bounds check failed");
+    }
+    return STA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *sta_status_string(sta_status s)
+{
+    switch (s) {
+    case STA_OK: return "ok";
+    case STA_EINVAL: return "invalid argument";
+    case STA_ECYCLE: return "combinational cycle";
+    case STA_ENOMEM: return "out of memory";
+    case STA_ECUDA: return "CUDA error";
+    case STA_ETIMEOUT: return "device wait timed out";
+    case STA_ESTATE: return "call out of order";
+    }
+    return "unknown status";
+}
+
+sta_status sta_plan(const sta_design_desc *desc, sta_plan_info *out)
+{
+    Plan pl;
+    std::string err;
+    const sta_status st = sta::build_plan(desc, pl, err);
+    if (st != STA_OK) {
+        g_plan_err = err;
+        return st;
+    }
+    if (out) {
+        std::memset(out, 0, sizeof(*out));
+        out->n_pins = pl.P;
+        out->n_cells = pl.C;
+        out->n_nets = desc->n_nets;
+        out->n_items = pl.I;
+        out->n_cell_arcs = pl.cell_arcs;
+        out->n_net_arcs = pl.F;
+        out->n_rc_nodes = pl.placed ? pl.F + desc->n_nets : pl.NN;
+        out->n_endpoints = pl.E;
+        out->n_levels = pl.S;
+        out->n_corners = pl.K;
+        out->max_level_width = pl.max_width;
+        out->n_designs = 1;
+        out->device_bytes = 0;
+    }
+    return STA_OK;
+}
+
+const char *sta_plan_error(void) { return g_plan_err.c_str(); }
+
+static sta_status finish_create(sta_ctx *c, int device, sta_ctx **out)
+{
+    try {
+        const sta_status st = create_from_plan(c, device);
+        if (st != STA_OK) {
+            g_plan_err = c->msg;
+            sta_destroy(c);
+            return st;
+        }
+    } catch (const CudaFail &f) {
+        const sta_status st = from_cuda(c, f);
+        g_plan_err = c->msg;
+        sta_destroy(c);
+        return st;
+    } catch (const std::bad_alloc &) {
+        g_plan_err = "host allocation failed";
+        sta_destroy(c);
+        return STA_ENOMEM;
+    }
+    *out = c;
+    return STA_OK;
+}
+
+static void keep_pin_maps(sta_ctx *c, const sta_design_desc *const *descs, int32_t n)
+{
+    int64_t P = 0;
+    for (int32_t i = 0; i < n; ++i) P += descs[i]->n_pins;
+    c->pin_cell_c.assign(P, -1);
+    c->pin_slot_c.assign(P, -1);
+    int64_t p0 = 0, c0 = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        const sta_design_desc &d = *descs[i];
+        for (int32_t cc = 0; cc < d.n_cells; ++cc)
+            for (int32_t k = d.cell_pin_ptr[cc]; k < d.cell_pin_ptr[cc + 1]; ++k) {
+                c->pin_cell_c[p0 + d.cell_pin[k]] = (int32_t)(c0 + cc);
+                c->pin_slot_c[p0 + d.cell_pin[k]] = k - d.cell_pin_ptr[cc];
+            }
+        p0 += d.n_pins;
+        c0 += d.n_cells;
+    }
+}
+
+sta_status sta_create(const sta_design_desc *desc, int device, sta_ctx **out)
+{
+    if (!out) return STA_EINVAL;
+    *out = nullptr;
+    sta_ctx *c = new (std::nothrow) sta_ctx();
+    if (!c) return STA_ENOMEM;
+    std::string err;
+    const sta_status st = sta::build_plan(desc, c->plan, err);
+    if (st != STA_OK) {
+        g_plan_err = err;
+        delete c;
+        return st;
+    }
+    keep_pin_maps(c, &desc, 1);
+    return finish_create(c, device, out);
+}
+
+sta_status sta_create_batch(const sta_design_desc *const *descs, int32_t n_designs, int device, sta_ctx **out)
+{
+    if (!out) return STA_EINVAL;
+    *out = nullptr;
+    sta_ctx *c = new (std::nothrow) sta_ctx();
+    if (!c) return STA_ENOMEM;
+    std::string err;
+    const sta_status st = sta::build_batch_plan(descs, n_designs, c->plan, err);
+    if (st != STA_OK) {
+        g_plan_err = err;
+        delete c;
+        return st;
+    }
+    keep_pin_maps(c, descs, n_designs);
+    return finish_create(c, device, out);
+}
+
+void sta_destroy(sta_ctx *c)
+{
+    if (!c) return;
+    cudaSetDevice(c->device);
+    drop_graph(c);
+    for (auto &e : c->ev)
+        if (e) cudaEventDestroy(e);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    for (void *p : c->allocs) cudaFree(p);
+    delete c;
+}
+
+const char *sta_last_error(const sta_ctx *c) { return c ? c->msg.c_str() : "NULL context"; }
+
+sta_status sta_set_clock(sta_ctx *c, float period_ns)
+{
+    if (!c) return STA_EINVAL;
+    if (!std::isfinite(period_ns)) return fail(c, STA_EINVAL, "period must be finite");
+    try {
+        CK(cudaSetDevice(c->device));
+        drop_graph(c);   // the context is passed to the kernels by value
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    c->plan.period = period_ns;
+    c->dc.period = period_ns;
+    return STA_OK;
+}
+
+sta_status sta_set_schedule(sta_ctx *c, int32_t schedule, int32_t param)
+{
+    if (!c) return STA_EINVAL;
+    if (schedule != STA_SCHED_LEVEL) return fail(c, STA_EINVAL, "unknown schedule");
+    if (schedule == STA_SCHED_LEVEL && param != 0 && (param < 32 || param > 1024 || param % 32))
+        return fail(c, STA_EINVAL, "threads per block must be a multiple of 32 in [32, 1024]");
+    try {
+        CK(cudaSetDevice(c->device));
+        drop_graph(c);
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    c->schedule = schedule;
+    c->sched_param = param;
+    if (schedule == STA_SCHED_LEVEL) c->hs.threads = param ? param : 128;
+    return STA_OK;
+}
+
+sta_status sta_update_timing(sta_ctx *c, void *stream)
+{
+    if (!c) return STA_EINVAL;
+    try {
+        CK(cudaSetDevice(c->device));
+        cudaStream_t st = as_stream(stream);
+        if (c->profiling) {
+            // eager launches with events at the phase boundaries
+            record_pass(c, st, c->ev);
+        } else {
+            ensure_graph(c);
+            CK(cudaGraphLaunch(c->exec, st));
+        }
+        CK(cudaGetLastError());
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    c->updated = true;
+    return STA_OK;
+}
+
+sta_status sta_sync(sta_ctx *c, void *stream)
+{
+    if (!c) return STA_EINVAL;
+    try {
+        CK(cudaSetDevice(c->device));
+        CK(cudaStreamSynchronize(as_stream(stream)));
+        CK(cudaGetLastError());
+        if (c->profiling && c->updated) {
+            for (int i = 0; i < 4; ++i) {
+                float ms = 0;
+                if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) == cudaSuccess) c->last_ms[i] = ms;
+            }
+        }
+        return check_device_error(c);
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+}
+
+sta_status sta_report_slack_design(sta_ctx *c, int32_t d, void *stream, sta_corner_report *rep)
+{
+    if (!c || !rep) return STA_EINVAL;
+    if (!c->updated) return fail(c, STA_ESTATE, "sta_report_slack before sta_update_timing");
+    if (d < 0 || d >= c->plan.n_designs) return fail(c, STA_EINVAL, "design index out of range");
+    sta_status st = sta_sync(c, stream);
+    if (st != STA_OK) return st;
+    const int K = c->plan.K;
+    std::vector<double> h((size_t)K * 8);
+    try {
+        CK(cudaMemcpy(h.data(), c->dc.report + (size_t)d * K * 8, h.size() * sizeof(double),
+                      cudaMemcpyDeviceToHost));
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    for (int k = 0; k < K; ++k) {
+        const double *o = h.data() + (size_t)k * 8;
+        rep[k].wns_setup = o[0];
+        rep[k].tns_setup = o[1];
+        rep[k].wns_hold = o[2];
+        rep[k].tns_hold = o[3];
+        rep[k].worst_setup = o[4];
+        rep[k].worst_hold = o[5];
+        rep[k].n_viol_setup = (int64_t)o[6];
+        rep[k].n_viol_hold = (int64_t)o[7];
+    }
+    return STA_OK;
+}
+
+sta_status sta_report_slack(sta_ctx *c, void *stream, sta_corner_report *rep)
+{
+    return sta_report_slack_design(c, 0, stream, rep);
+}
+
+sta_status sta_get_pin_state(sta_ctx *c, int32_t which, float *out, sta_mem mem, void *stream)
+{
+    if (!c || !out) return STA_EINVAL;
+    if (!c->updated) return fail(c, STA_ESTATE, "no analysis yet");
+    const float4 *src = which == STA_AT ? c->dc.at : which == STA_SLEW ? c->dc.slew : which == STA_RAT ? c->dc.rat
+                        : which == STA_SLACK ? c->dc.slack : nullptr;
+    if (!src) return fail(c, STA_EINVAL, "unknown array id");
+    try {
+        CK(cudaSetDevice(c->device));
+        cudaStream_t st = as_stream(stream);
+        const size_t PK = (size_t)c->plan.P * c->plan.K;
+        if (mem == STA_DEVICE) {
+            sta::launch_gather_pins(src, c->d_gpu_of, reinterpret_cast<float4 *>(out), c->plan.P, c->plan.K, st);
+            CK(cudaGetLastError());
+        } else {
+            if (!c->d_gather_tmp) c->d_gather_tmp = dev_alloc<float4>(c, PK);
+            sta::launch_gather_pins(src, c->d_gpu_of, c->d_gather_tmp, c->plan.P, c->plan.K, st);
+            CK(cudaMemcpyAsync(out, c->d_gather_tmp, PK * sizeof(float4), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+        }
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    return STA_OK;
+}
+
+sta_status sta_get_endpoint_slack(sta_ctx *c, float *setup, float *hold, uint8_t *vs, uint8_t *vh, sta_mem mem,
+                                  void *stream)
+{
+    if (!c) return STA_EINVAL;
+    if (!c->updated) return fail(c, STA_ESTATE, "no analysis yet");
+    try {
+        CK(cudaSetDevice(c->device));
+        cudaStream_t st = as_stream(stream);
+        const size_t EK = (size_t)c->plan.E * c->plan.K;
+        const cudaMemcpyKind kind = mem == STA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (setup) CK(cudaMemcpyAsync(setup, c->dc.ep_setup, EK * sizeof(float), kind, st));
+        if (hold) CK(cudaMemcpyAsync(hold, c->dc.ep_hold, EK * sizeof(float), kind, st));
+        if (vs) CK(cudaMemcpyAsync(vs, c->dc.viol_setup, EK, kind, st));
+        if (vh) CK(cudaMemcpyAsync(vh, c->dc.viol_hold, EK, kind, st));
+        if (mem == STA_HOST) CK(cudaStreamSynchronize(st));
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    return STA_OK;
+}
+
+sta_status sta_set_rc(sta_ctx *c, const float *R, const float *Cc, sta_mem mem)
+{
+    if (!c || !R || !Cc) return STA_EINVAL;
+    if (c->plan.placed) return fail(c, STA_ESTATE, "context uses positions, not RC trees");
+    const size_t NN = (size_t)c->plan.NN;
+    try {
+        CK(cudaSetDevice(c->device));
+        if (!c->d_rc_tmp) c->d_rc_tmp = dev_alloc<float>(c, NN);
+        const cudaMemcpyKind kind = mem == STA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        CK(cudaMemcpy(c->d_rc_tmp, R, NN * sizeof(float), kind));
+        sta::launch_gather_f32(c->d_rc_tmp, c->d_rc_src, const_cast<float *>(c->dc.rc_R), (int)NN, 0);
+        CK(cudaMemcpy(c->d_rc_tmp, Cc, NN * sizeof(float), kind));
+        sta::launch_gather_f32(c->d_rc_tmp, c->d_rc_src, const_cast<float *>(c->dc.rc_C), (int)NN, 0);
+        CK(cudaDeviceSynchronize());
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    return STA_OK;
+}
+
+sta_status sta_set_positions(sta_ctx *c, const float *cell_xy, sta_mem mem, void *stream)
+{
+    if (!c || !cell_xy) return STA_EINVAL;
+    if (!c->plan.placed) return fail(c, STA_ESTATE, "context uses RC trees, not positions");
+    try {
+        CK(cudaSetDevice(c->device));
+        const cudaMemcpyKind kind = mem == STA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        CK(cudaMemcpyAsync(const_cast<float *>(c->dc.cell_xy), cell_xy, 2 * (size_t)c->plan.C * sizeof(float), kind,
+                           as_stream(stream)));
+        if (mem == STA_HOST) CK(cudaStreamSynchronize(as_stream(stream)));
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    return STA_OK;
+}
+
+sta_status sta_set_cell_types(sta_ctx *c, const int32_t *cell_type)
+{
+    if (!c || !cell_type) return STA_EINVAL;
+    Plan &pl = c->plan;
+    for (int32_t i = 0; i < pl.C; ++i) {
+        const int32_t t = cell_type[i], o = pl.cell_type[i];
+        if (t < 0 || t >= pl.T) return fail(c, STA_EINVAL, "cell type out of range");
+        if (pl.type_nin[t] != pl.type_nin[o] || pl.type_kind[t] != pl.type_kind[o])
+            return fail(c, STA_EINVAL, "resizing must keep the input count and kind");
+    }
+    for (int32_t i = 0; i < pl.C; ++i) {
+        pl.cell_type[i] = cell_type[i];
+        pl.item_type[pl.item_of_cell[i]] = cell_type[i];
+    }
+    for (int64_t q = 0; q < pl.F; ++q) {
+        const int32_t s = pl.fo_src[q];
+        const int32_t cc = c->pin_cell_c[s];
+        if (cc >= 0) pl.fo_cap[q] = pl.type_pin_cap[(size_t)pl.cell_type[cc] * 4 + c->pin_slot_c[s]];
+    }
+    try {
+        CK(cudaSetDevice(c->device));
+        CK(cudaMemcpy(const_cast<int32_t *>(c->dc.item_type), pl.item_type.data(), pl.item_type.size() * 4,
+                      cudaMemcpyHostToDevice));
+        if (pl.F)
+            CK(cudaMemcpy(const_cast<float *>(c->dc.fo_cap), pl.fo_cap.data(), pl.fo_cap.size() * 4,
+                          cudaMemcpyHostToDevice));
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    return STA_OK;
+}
+
+sta_status sta_get_arrays(sta_ctx *c, sta_views *out)
+{
+    if (!c || !out) return STA_EINVAL;
+    out->at = reinterpret_cast<const float *>(c->dc.at);
+    out->slew = reinterpret_cast<const float *>(c->dc.slew);
+    out->rat = reinterpret_cast<const float *>(c->dc.rat);
+    out->slack = reinterpret_cast<const float *>(c->dc.slack);
+    out->gpu_pin_of = c->d_gpu_of;
+    return STA_OK;
+}
+
+sta_status sta_stats(const sta_ctx *c, sta_plan_info *out)
+{
+    if (!c || !out) return STA_EINVAL;
+    const Plan &pl = c->plan;
+    std::memset(out, 0, sizeof(*out));
+    out->n_pins = pl.P;
+    out->n_cells = pl.C;
+    out->n_nets = 0;
+    for (int32_t g = 0; g < pl.I; ++g) out->n_nets += pl.fo_ptr[g + 1] > pl.fo_ptr[g];
+    out->n_items = pl.I;
+    out->n_cell_arcs = pl.cell_arcs;
+    out->n_net_arcs = pl.F;
+    out->n_rc_nodes = pl.placed ? pl.F + out->n_nets : pl.NN;
+    out->n_endpoints = pl.E;
+    out->n_levels = pl.S;
+    out->n_corners = pl.K;
+    out->max_level_width = pl.max_width;
+    out->n_designs = pl.n_designs;
+    out->device_bytes = (int64_t)c->bytes;
+    out->launches_per_update = launches_per_update(c);
+    return STA_OK;
+}
+
+sta_status sta_set_profiling(sta_ctx *c, int32_t on)
+{
+    if (!c) return STA_EINVAL;
+    c->profiling = on != 0;
+    return STA_OK;
+}
+
+sta_status sta_last_timings(sta_ctx *c, float *ms4)
+{
+    if (!c || !ms4) return STA_EINVAL;
+    for (int i = 0; i < 4; ++i) ms4[i] = c->last_ms[i];
+    return STA_OK;
+}
+
+sta_status sta_backward(sta_ctx *c, double, double, double *, double *, double *, sta_mem, void *)
+{
+    if (!c) return STA_EINVAL;
+    return fail(c, STA_ESTATE, "differentiable pass not built");
+}
+
+}  // extern "C"

@@ -120,7 +120,7 @@ def _csr_from_groups(keys: np.ndarray, n_groups: int):
 
 def make_design(n_cells: int, depth: int, seed: int = 0, lib: dict | None = None,
                 rc_nodes: tuple[int, int] = (2, 12), fanout_mean: float = 2.5,
-                dff_frac: float = 0.10, pi_frac: float = 0.02, placed: bool = False,
+                dff_frac: float = 0.10, pi_frac: float = 0.02, po_frac: float = 0.2, placed: bool = False,
                 die_um: float = 1000.0, r_per_um: float = 0.1, c_per_um: float = 0.2,
                 period_ns: float = 1.0, n_corners: int = 1, lut_scale=None, rc_scale=None,
                 gamma_ns: float = 0.0, base_types_only: bool = True) -> dict:
@@ -134,7 +134,8 @@ def make_design(n_cells: int, depth: int, seed: int = 0, lib: dict | None = None
     * Every driver draws a weight from a geometric law of mean
       ``fanout_mean`` and is picked with probability proportional to it.
     * A driver nobody picked drives a primary output (so every net has a sink;
-      all last-level outputs become POs).
+      all last-level outputs become POs); ``po_frac * n_cells`` further
+      drivers get an extra primary output (observation points).
     * RC per net: ``rc_nodes`` inclusive node-count range, parent of node i
       uniform in [0, i), R ~ U(5, 50) Ohm (root 0), C ~ U(0.5, 5) fF; each
       sink sits on a uniform non-root node.
@@ -204,6 +205,10 @@ def make_design(n_cells: int, depth: int, seed: int = 0, lib: dict | None = None
     sink_drv = np.concatenate([slot_drv, d_drv]).astype(np.int64)
     fan = np.bincount(sink_drv, minlength=n_drv)
     lonely = np.nonzero(fan == 0)[0]
+    # observation points: extra primary outputs on random drivers
+    n_tap = int(round(po_frac * n_cells))
+    taps = rng.choice(n_drv, size=min(n_tap, n_drv), replace=False) if n_tap > 0 else np.zeros(0, np.int64)
+    lonely = np.concatenate([lonely, np.setdiff1d(taps, lonely)])
     n_po = len(lonely)
     po_pin = n_cell_pins + n_pi + np.arange(n_po)
     sink_pin = np.concatenate([sink_pin, po_pin])

