@@ -173,6 +173,11 @@ typedef struct {
  * STA_ECYCLE.  Defined by the CSR database of Sec. III plus the level
  * ordering that graph propagation (Sec. I) needs. */
 sta_status sta_plan(const sta_design_desc *desc, sta_plan_info *out);
+/* Host only: the propagation level of every cell, cell_level[n_cells]
+ * (flip-flops 0; a gate 1 + the highest level among the cells driving its
+ * inputs, primary inputs counting as level 0).  Errors as sta_plan. */
+sta_status sta_plan_levels(const sta_design_desc *desc, int32_t *cell_level);
+
 /* Message of the last failed sta_plan / sta_create on this thread. */
 const char *sta_plan_error(void);
 

@@ -12,6 +12,8 @@ namespace sta {
 constexpr int kLutStride = 80;   // floats per packed table, see plan.cpp
 constexpr int kRcTileNodes = 2048;
 constexpr int kRcTileNets = 128;
+constexpr int kRedThreads = 256;   // threads of the reduction kernels
+constexpr int kRedChunk = 4096;    // endpoints per first-stage reduction block
 
 // device error word bits (sta_sync maps them to sta_status)
 constexpr unsigned kErrTimeout = 1u;
@@ -38,6 +40,9 @@ struct DevCtx {
     float *ep_setup, *ep_hold;                  // [E*K]
     uint8_t *viol_setup, *viol_hold;            // [E*K]
     double *report;                             // [n_designs][K][8]
+    const int32_t *red_chunk_ptr;               // [n_red_chunks+1] endpoint ranges
+    const int32_t *red_design_chunk;            // [n_designs+1] chunk ranges per design
+    double *red_partial;                        // [n_red_chunks][K][6] scratch
     unsigned *err;
     float *scratch_a, *scratch_b;               // RC sweeps of nets larger than a tile
 };

@@ -12,6 +12,8 @@
 
 namespace sta {
 
+static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
+
 // ------------------------------------------------------------------ nets
 
 // RC trees.  One block per tile of consecutive items whose nodes fit in
@@ -313,30 +315,19 @@ __global__ void k_bwd_level(const DevCtx c, int i0, int i1)
 
 // ------------------------------------------------------------- reduction
 
-// One block per (design, corner): WNS = min(0, worst), TNS = sum of
-// negatives, in FP64, fixed summation order (deterministic).
-__global__ void __launch_bounds__(256) k_reduce(const DevCtx c)
+// Two-stage FP64 reduction of the endpoint slacks, deterministic (fixed
+// thread-to-element assignment and fixed tree order).  Stage 1: block b of
+// corner k reduces endpoint chunk b (chunks never straddle designs) into six
+// partials (TNS setup, TNS hold, worst setup, worst hold, violation counts).
+// Stage 2: one block per (design, corner) folds that design's chunks into
+// WNS = min(0, worst), TNS = sum of negatives.
+template <int NT>
+__device__ __forceinline__ void block_fold6(double v[6], double (*sh)[NT])
 {
-    const int d = blockIdx.x / c.K, k = blockIdx.x % c.K;
-    const int e0 = c.ep_design_ptr[d], e1 = c.ep_design_ptr[d + 1];
-    const int K = c.K;
-    double tns_s = 0, tns_h = 0, wst_s = INFINITY, wst_h = INFINITY, nv_s = 0, nv_h = 0;
-    for (int e = e0 + threadIdx.x; e < e1; e += blockDim.x) {
-        const double ss = c.ep_setup[(size_t)e * K + k], hs = c.ep_hold[(size_t)e * K + k];
-        wst_s = fmin(wst_s, ss);
-        wst_h = fmin(wst_h, hs);
-        if (ss < 0) { tns_s += ss; nv_s += 1; }
-        if (hs < 0) { tns_h += hs; nv_h += 1; }
-    }
-    __shared__ double sh[6][256];
-    sh[0][threadIdx.x] = tns_s;
-    sh[1][threadIdx.x] = tns_h;
-    sh[2][threadIdx.x] = wst_s;
-    sh[3][threadIdx.x] = wst_h;
-    sh[4][threadIdx.x] = nv_s;
-    sh[5][threadIdx.x] = nv_h;
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] = v[q];
     __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    for (int w = NT / 2; w > 0; w >>= 1) {
         if (threadIdx.x < w) {
             sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
             sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
@@ -347,6 +338,41 @@ __global__ void __launch_bounds__(256) k_reduce(const DevCtx c)
         }
         __syncthreads();
     }
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce_chunks(const DevCtx c)
+{
+    __shared__ double sh[6][kRedThreads];
+    const int b = blockIdx.x, k = blockIdx.y, K = c.K;
+    const int e0 = c.red_chunk_ptr[b], e1 = c.red_chunk_ptr[b + 1];
+    double v[6] = {0, 0, INFINITY, INFINITY, 0, 0};
+    for (int e = e0 + threadIdx.x; e < e1; e += kRedThreads) {
+        const double ss = c.ep_setup[(size_t)e * K + k], hs = c.ep_hold[(size_t)e * K + k];
+        v[2] = fmin(v[2], ss);
+        v[3] = fmin(v[3], hs);
+        if (ss < 0) { v[0] += ss; v[4] += 1; }
+        if (hs < 0) { v[1] += hs; v[5] += 1; }
+    }
+    block_fold6<kRedThreads>(v, sh);
+    if (threadIdx.x < 6) c.red_partial[((size_t)b * K + k) * 6 + threadIdx.x] = sh[threadIdx.x][0];
+}
+
+__global__ void __launch_bounds__(kRedThreads) k_reduce_final(const DevCtx c)
+{
+    __shared__ double sh[6][kRedThreads];
+    const int d = blockIdx.x / c.K, k = blockIdx.x % c.K, K = c.K;
+    const int b0 = c.red_design_chunk[d], b1 = c.red_design_chunk[d + 1];
+    double v[6] = {0, 0, INFINITY, INFINITY, 0, 0};
+    for (int b = b0 + threadIdx.x; b < b1; b += kRedThreads) {
+        const double *p = c.red_partial + ((size_t)b * K + k) * 6;
+        v[0] += p[0];
+        v[1] += p[1];
+        v[2] = fmin(v[2], p[2]);
+        v[3] = fmin(v[3], p[3]);
+        v[4] += p[4];
+        v[5] += p[5];
+    }
+    block_fold6<kRedThreads>(v, sh);
     if (threadIdx.x == 0) {
         double *o = c.report + ((size_t)d * K + k) * 8;
         o[0] = fmin(0.0, sh[2][0]);
@@ -358,6 +384,12 @@ __global__ void __launch_bounds__(256) k_reduce(const DevCtx c)
         o[6] = sh[4][0];
         o[7] = sh[5][0];
     }
+}
+
+void launch_reduce(const DevCtx &c, const HostSched &h, cudaStream_t st)
+{
+    if (h.n_red_chunks > 0) k_reduce_chunks<<<dim3(h.n_red_chunks, c.K), kRedThreads, 0, st>>>(c);
+    k_reduce_final<<<c.n_designs * c.K, kRedThreads, 0, st>>>(c);
 }
 
 // ------------------------------------------------------------- gathers
@@ -380,8 +412,6 @@ __global__ void k_gather_f32(const float *__restrict__ src, const int32_t *__res
 }
 
 // ------------------------------------------------------------- launchers
-
-static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
 void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev)
 {
@@ -407,7 +437,7 @@ void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cud
         k_bwd_level<<<nblk(i1 - i0, tpb), tpb, 0, st>>>(c, i0, i1);
     }
     if (ev) cudaEventRecord(ev[3], st);
-    k_reduce<<<c.n_designs * c.K, 256, 0, st>>>(c);
+    launch_reduce(c, h, st);
     if (ev) cudaEventRecord(ev[4], st);
 }
 

@@ -14,6 +14,7 @@ struct HostSched {
     int n_tiles = 0;                  // RC tiles (tree mode)
     bool placed = false;
     int threads = 128;                // threads per block of the level kernels
+    int n_red_chunks = 0;             // first-stage reduction blocks
 };
 
 // Net delays, forward levels, endpoints, backward levels, reduction.  With
@@ -21,6 +22,9 @@ struct HostSched {
 // net delays, ev[2] after forward + endpoints, ev[3] after backward, ev[4]
 // after the reduction.
 void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev = nullptr);
+
+// The two-stage FP64 WNS/TNS reduction.
+void launch_reduce(const DevCtx &c, const HostSched &h, cudaStream_t st);
 
 void launch_gather_pins(const float4 *arr, const int32_t *gpu_of, float4 *out, int P, int K, cudaStream_t st);
 void launch_gather_f32(const float *src, const int32_t *idx, float *dst, int n, cudaStream_t st);

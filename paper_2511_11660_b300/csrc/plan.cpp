@@ -266,7 +266,7 @@ void build(const sta_design_desc *d, Plan &pl)
                 if (--indeg[v] == 0) { level[v] = lv + 1; order.push_back(v); }
             }
         }
-        pl.stage_ptr.push_back((int32_t)order.size());
+        pl.stage_ptr.push_back((int32_t)layer_end);
     }
     if ((int32_t)order.size() != I) {
         int32_t bad = -1;
@@ -323,6 +323,11 @@ void build(const sta_design_desc *d, Plan &pl)
     }
     REQUIRE(next == P, STA_EINVAL, "internal: numbered %d of %d pins", next, P);
     pl.E = (int32_t)pl.ep_pin.size();
+    // level of each cell as the launch schedule sees it (the stage holding its item)
+    pl.cell_level.assign(C, -1);
+    for (int32_t s = 0; s < pl.S; ++s)
+        for (int32_t g = pl.stage_ptr[s]; g < pl.stage_ptr[s + 1]; ++g)
+            if (pl.item_cell[g] >= 0) pl.cell_level[pl.item_cell[g]] = s;
     pl.ep_design_ptr = {0, pl.E};
 
     // ---- per-pin maps

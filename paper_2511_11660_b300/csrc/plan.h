@@ -74,6 +74,7 @@ struct Plan {
     // caller cell types (for resizing) and the item of each cell
     std::vector<int32_t> cell_type;          // [C]
     std::vector<int32_t> item_of_cell;       // [C]
+    std::vector<int32_t> cell_level;         // [C] propagation level of each cell
 };
 
 // Validate `desc` and fill `plan`.  On failure returns the status and sets

@@ -1,4 +1,5 @@
 // sta_api.cu -- the C ABI of libsta.so (see include/sta.h).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -182,6 +183,19 @@ sta_status create_from_plan(sta_ctx *c, int device)
     d.viol_setup = dev_alloc<uint8_t>(c, EK);
     d.viol_hold = dev_alloc<uint8_t>(c, EK);
     d.report = dev_alloc<double>(c, (size_t)pl.n_designs * pl.K * 8);
+    {
+        // reduction chunks: <= kRedChunk endpoints, never straddling designs
+        std::vector<int32_t> cp{0}, dc{0};
+        for (int32_t dd = 0; dd < pl.n_designs; ++dd) {
+            for (int32_t e = pl.ep_design_ptr[dd]; e < pl.ep_design_ptr[dd + 1]; e += sta::kRedChunk)
+                cp.push_back(std::min(e + sta::kRedChunk, pl.ep_design_ptr[dd + 1]));
+            dc.push_back((int32_t)cp.size() - 1);
+        }
+        c->hs.n_red_chunks = (int)cp.size() - 1;
+        d.red_chunk_ptr = upload(c, cp);
+        d.red_design_chunk = upload(c, dc);
+        d.red_partial = dev_alloc<double>(c, std::max<size_t>(1, cp.size() - 1) * pl.K * 6);
+    }
     d.err = dev_alloc<unsigned>(c, 1);
     CK(cudaMemset(d.err, 0, sizeof(unsigned)));
     if (pl.n_big_tiles > 0) {
@@ -212,7 +226,7 @@ int32_t launches_per_update(const sta_ctx *c)
     for (int32_t s = 0; s < pl.S; ++s) levels += pl.stage_ptr[s + 1] > pl.stage_ptr[s];
     n += 2 * levels;
     n += pl.E > 0;
-    n += 1;   // reduction
+    n += (c->hs.n_red_chunks > 0) + 1;   // two-stage reduction
     return n;
 }
 
@@ -275,6 +289,20 @@ sta_status sta_plan(const sta_design_desc *desc, sta_plan_info *out)
 }
 
 const char *sta_plan_error(void) { return g_plan_err.c_str(); }
+
+sta_status sta_plan_levels(const sta_design_desc *desc, int32_t *cell_level)
+{
+    if (!cell_level) return STA_EINVAL;
+    Plan pl;
+    std::string err;
+    const sta_status st = sta::build_plan(desc, pl, err);
+    if (st != STA_OK) {
+        g_plan_err = err;
+        return st;
+    }
+    for (int32_t c = 0; c < pl.C; ++c) cell_level[c] = pl.cell_level[c];
+    return STA_OK;
+}
 
 static sta_status finish_create(sta_ctx *c, int device, sta_ctx **out)
 {

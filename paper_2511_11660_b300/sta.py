@@ -78,6 +78,7 @@ _V, _P = C.c_void_p, C.c_void_p
 SIGNATURES = {
     "sta_plan": (C.c_int, [_P, C.POINTER(sta_plan_info)]),
     "sta_plan_error": (C.c_char_p, []),
+    "sta_plan_levels": (C.c_int, [_P, _P]),
     "sta_create": (C.c_int, [_P, C.c_int, C.POINTER(C.c_void_p)]),
     "sta_create_batch": (C.c_int, [_P, C.c_int32, C.c_int, C.POINTER(C.c_void_p)]),
     "sta_set_rc": (C.c_int, [_V, _P, _P, C.c_int]),
@@ -195,6 +196,17 @@ def sta_plan(design) -> dict:
     if st != OK:
         raise StaError(st, lib.sta_plan_error().decode())
     return info.as_dict()
+
+
+def sta_plan_levels(design) -> np.ndarray:
+    """Host-only: propagation level of every cell."""
+    lib = load()
+    dd = design if isinstance(design, Design) else Design(design)
+    out = np.zeros(max(int(dd.src["n_cells"]), 1), np.int32)
+    st = lib.sta_plan_levels(C.byref(dd.desc), _ptr(out))
+    if st != OK:
+        raise StaError(st, lib.sta_plan_error().decode())
+    return out[: int(dd.src["n_cells"])]
 
 
 class Context:

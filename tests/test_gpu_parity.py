@@ -109,8 +109,14 @@ def test_smoothed_merges_parity():
 
 
 def test_large_rc_trees_use_global_sweeps():
-    """Nets above the shared-memory tile (2048 RC nodes) take the global path."""
+    """Nets above the shared-memory tile (2048 RC nodes) take the global path.
+    R and C are scaled down so that loads stay inside the tables (2,500 nodes
+    of the default values would put 7 pF on 0.5 pF tables, where extrapolated
+    slews double per stage and the comparison measures conditioning, not the
+    kernel)."""
     d = synth.make_design(400, 6, seed=9, rc_nodes=(2000, 3000))
+    d["rc_R"] = (d["rc_R"] * 0.1).astype(np.float32)
+    d["rc_C"] = (d["rc_C"] * 0.01).astype(np.float32)
     g, ref = run_both(d)
     check_all(d, g, ref, exact_viol=False)
 

@@ -169,3 +169,45 @@ def test_batch_plan_merges_designs(lib):
     # a batch is created on a device, but its host merge is exercised by the
     # equality of summed sizes of the parts
     assert sum(i["n_pins"] for i in infos) == sum(d["n_pins"] for d in ds)
+
+
+def _levels_by_dfs(d):
+    """Longest-path level of every cell, computed independently (memoised
+    recursion over cell inputs; PIs and flip-flops are level 0)."""
+    import sys
+    sys.setrecursionlimit(100000)
+    role = d["pin_role"]
+    cpp, cp = d["cell_pin_ptr"], d["cell_pin"]
+    npp, npn = d["net_pin_ptr"], d["net_pin"]
+    driver_of = {}
+    for n in range(d["n_nets"]):
+        for s in npn[npp[n] + 1:npp[n + 1]]:
+            driver_of[int(s)] = int(npn[npp[n]])
+    cell_of = {}
+    for c in range(d["n_cells"]):
+        for p in cp[cpp[c]:cpp[c + 1]]:
+            cell_of[int(p)] = c
+    memo = {}
+
+    def lev(c):
+        if c in memo:
+            return memo[c]
+        t = d["cell_type"][c]
+        if d["type_kind"][t] == 1:
+            memo[c] = 0
+            return 0
+        best = 0
+        for p in cp[cpp[c]:cpp[c + 1] - 1]:
+            drv = driver_of[int(p)]
+            best = max(best, 0 if role[drv] == synth.PI else lev(cell_of[drv]))
+        memo[c] = best + 1
+        return best + 1
+    return np.array([lev(c) for c in range(d["n_cells"])])
+
+
+@pytest.mark.parametrize("seed", [0, 1])
+def test_levels_are_longest_path_levels(lib, seed):
+    d = synth.make_design(2500, 17, seed=seed)
+    got = sta.sta_plan_levels(d)
+    np.testing.assert_array_equal(got, _levels_by_dfs(d))
+    assert got.max() == 17
