@@ -269,6 +269,27 @@ sta_status sta_stats(const sta_ctx *ctx, sta_plan_info *out);
 sta_status sta_set_profiling(sta_ctx *ctx, int32_t on);
 sta_status sta_last_timings(sta_ctx *ctx, float *ms4);
 
+/* WNS/TNS of endpoint slacks without allocating anything.  The paper has no
+ * counterpart: this is for callers that cannot call cudaMalloc -- a flow whose
+ * device memory is already reserved by another allocator, or a loop that must
+ * not pay cudaMalloc's implicit synchronisation -- and so cannot create the
+ * partial-sums buffer the regular reduction uses.  It computes what
+ * sta_report_slack reports for a single design, from device arrays
+ * setup[n_endpoints][n_corners] and hold[...] (as sta_get_endpoint_slack writes
+ * them), into device out[n_corners][8] doubles in sta_corner_report field
+ * order (violation counts as doubles), asynchronously on `stream`.
+ * Its partial sums live in one fixed 384 KiB device array inside the library,
+ * held on every GPU that loads it until the process exits; the limit is
+ * ceil(n_endpoints / 4096) * n_corners <= 8192 (about 33.5 million
+ * endpoint-corners), larger inputs return STA_EINVAL with a message on
+ * stderr.  The first call on a device looks the array's address up
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array: calls whose
+ * kernels overlap on the GPU race, so serialise them (one stream).  Errors:
+ * STA_EINVAL (NULL pointer, bad size), STA_ECUDA. */
+sta_status sta_reduce_slack_noalloc(const float *setup, const float *hold, int64_t n_endpoints,
+                                    int32_t n_corners, double *out, void *stream);
+
 /* Message for the last failed call on this context (never NULL). */
 const char *sta_last_error(const sta_ctx *ctx);
 const char *sta_status_string(sta_status s);

@@ -100,6 +100,7 @@ SIGNATURES = {
     "sta_last_error": (C.c_char_p, [_V]),
     "sta_status_string": (C.c_char_p, [C.c_int]),
     "sta_destroy": (None, [_V]),
+    "sta_reduce_slack_noalloc": (C.c_int, [_P, _P, C.c_int64, C.c_int32, _P, _V]),
 }
 
 _lib = None
@@ -333,3 +334,15 @@ class Context:
         v = sta_views()
         self._chk(self.lib.sta_get_arrays(self.h, C.byref(v)))
         return {k: getattr(v, k) for k, _ in v._fields_}
+
+
+def reduce_slack_noalloc(setup, hold, out, stream=None):
+    """WNS/TNS of device endpoint slacks ``setup``/``hold`` ([E, K] float32
+    CUDA tensors) into ``out`` ([K, 8] float64 CUDA tensor) without any device
+    allocation (``sta_reduce_slack_noalloc``)."""
+    lib = load()
+    E, K = int(setup.shape[0]), int(setup.shape[1])
+    st = lib.sta_reduce_slack_noalloc(_ptr(setup), _ptr(hold), E, K, _ptr(out), _stream(stream))
+    if st != OK:
+        raise StaError(st, "sta_reduce_slack_noalloc failed")
+    return out
