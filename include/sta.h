@@ -214,6 +214,17 @@ sta_status sta_set_clock(sta_ctx *ctx, float period_ns);
  * per block for LEVEL; resident blocks per SM for DATAFLOW, 0 = auto). */
 sta_status sta_set_schedule(sta_ctx *ctx, int32_t schedule, int32_t param);
 
+/* Dataflow schedule: polls a wait may spend on a ready flag before the pass
+ * gives up and the next synchronising call returns STA_ETIMEOUT (default
+ * 2^23, seconds of waiting; a real wait ends in microseconds). */
+sta_status sta_set_wait_limit(sta_ctx *ctx, int64_t polls);
+
+/* Failure-detection test hook (dataflow schedule): while `cell` >= 0, the
+ * forward pass of that cell never publishes its ready flag, so its fan-out
+ * waits run out and the update reports STA_ETIMEOUT with the context still
+ * usable; -1 restores normal operation. */
+sta_status sta_debug_hold_cell(sta_ctx *ctx, int32_t cell);
+
 /* Full analysis on `stream`: net delay calculation, forward arrival/slew
  * propagation, endpoint required times, backward required-time propagation,
  * pin and endpoint slacks, FP64 WNS/TNS.  Asynchronous. */

@@ -1,0 +1,206 @@
+// dataflow.cu -- persistent dataflow schedule of the timing pass.
+//
+// Instead of one launch per level, each pass is one persistent kernel.  Its
+// warps take chunks of at most 8 items of one level (four lanes per item), in level order (the
+// backward pass in reverse level order), from an atomic counter; an item
+// runs as soon as the flags of the items it reads carry this pass's epoch
+// (acquire loads, polled by the whole warp with a bounded number of idle
+// rounds), and publishes its own flag with a release store after writing its
+// results.  Chunks are handed out in increasing order and an item only waits
+// for items handed out earlier, whose warps are already running, so the
+// oldest unfinished item can always proceed: no grid barrier and no
+// co-residency assumption.  Flags hold the epoch of the update that set them
+// (driver pins in the forward pass, gate input pins in the backward pass), so
+// nothing is cleared between updates.  The cell library (tables and per-type
+// data) is copied into shared memory once per block.
+#include <algorithm>
+
+#include "item.cuh"
+#include "kernels.h"
+
+namespace sta {
+
+constexpr int kDfThreads = 256;
+
+static inline size_t df_smem_bytes(int T) { return (size_t)T * 3 * 4 * kLutStride * sizeof(float) + (size_t)T * 5 * sizeof(int); }
+
+// New epoch, chunk counters at zero, abort cleared.
+__global__ void k_df_begin(const DevCtx c)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        c.df_state[0] = c.df_state[0] + 1u;
+        c.df_state[1] = 0u;
+        c.df_state[2] = 0u;
+        c.df_state[3] = 0u;
+    }
+}
+
+struct SmemLib {
+    LutShared lut;
+    const int *nin, *kind, *sense;
+};
+
+__device__ __forceinline__ SmemLib stage_library(const DevCtx &c, float *smem)
+{
+    const int nl = c.T * 3 * 4 * kLutStride;
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) smem[i] = __ldg(c.lut + i);
+    int *ti = reinterpret_cast<int *>(smem + nl);
+    for (int i = threadIdx.x; i < c.T; i += blockDim.x) {
+        ti[i] = __ldg(c.type_nin + i);
+        ti[c.T + i] = __ldg(c.type_kind + i);
+    }
+    for (int i = threadIdx.x; i < 3 * c.T; i += blockDim.x) ti[2 * c.T + i] = __ldg(c.arc_sense + i);
+    __syncthreads();
+    return SmemLib{LutShared{smem}, ti, ti + c.T, ti + 2 * c.T};
+}
+
+// Next chunk for this warp (lane 0 takes it, all lanes get it); -1 when the
+// queue is empty or the pass was aborted.
+__device__ __forceinline__ int next_chunk(const DevCtx &c, int counter, int n_chunks)
+{
+    int ch = 0;
+    if ((threadIdx.x & 31) == 0) ch = (int)atomicAdd(c.df_state + counter, 1u);
+    ch = __shfl_sync(0xffffffffu, ch, 0);
+    if (ch >= n_chunks) return -1;
+    if (ld_volatile(c.df_state + 3)) return -1;
+    return ch;
+}
+
+// The warp's polling loop.  Every pending item of the chunk probes its
+// inputs' flags without blocking; items whose inputs are all published run
+// at once, so one late input holds back only its own item.  A warp gives up
+// after c.spin_limit idle rounds (timeout bit + abort word), or as soon as
+// another warp has aborted.
+__device__ __forceinline__ bool warp_idle_round(const DevCtx &c, long long &spins)
+{
+    if (++spins >= c.spin_limit) {
+        if ((threadIdx.x & 31) == 0) {
+            atomicOr(c.err, kErrTimeout);
+            atomicExch(c.df_state + 3, 1u);
+        }
+        return false;
+    }
+    if ((spins & 31) == 0 && __any_sync(0xffffffffu, ld_volatile(c.df_state + 3) != 0u)) return false;
+    __nanosleep(32);
+    return true;
+}
+
+template <bool SMOOTH, bool UNIFORM>
+__global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
+{
+    extern __shared__ float smem[];
+    const SmemLib L = stage_library(c, smem);
+    const unsigned epoch = ld_volatile(c.df_state);
+    const int lane = threadIdx.x & 31, q = lane & 3;
+    for (;;) {
+        const int ch = next_chunk(c, 1, c.n_fwd_chunks);
+        if (ch < 0) break;
+        const int x = c.fwd_chunk_lo[ch] + (lane >> 2);
+        bool pending = x < c.fwd_chunk_hi[ch];
+        const bool is_item = x < c.I;   // endpoint chunks follow all item chunks
+        FwdItem f{};
+        EpItem e{};
+        if (pending) {
+            if (is_item) f = fwd_prep(c, L.nin, L.kind, L.sense, x);
+            else e = ep_prep(c, x - c.I);
+        }
+        long long spins = 0;
+        while (__any_sync(0xffffffffu, pending)) {
+            if (pending) {
+                const bool ready = quad_all(is_item ? fwd_probe(c, f, epoch) : ep_probe(c, e, epoch));
+                if (ready) {
+                    if (is_item) fwd_run<SMOOTH, UNIFORM, true>(c, L.lut, f, x, q, epoch);
+                    else ep_run<true>(c, e, x - c.I, q);
+                    pending = false;
+                }
+            }
+            if (__any_sync(0xffffffffu, pending) && !warp_idle_round(c, spins)) break;
+        }
+    }
+}
+
+template <bool UNIFORM>
+__global__ void __launch_bounds__(kDfThreads) k_df_backward(const DevCtx c)
+{
+    extern __shared__ float smem[];
+    const SmemLib L = stage_library(c, smem);
+    const unsigned epoch = ld_volatile(c.df_state);
+    const int lane = threadIdx.x & 31, q = lane & 3;
+    for (;;) {
+        const int ch = next_chunk(c, 2, c.n_bwd_chunks);
+        if (ch < 0) break;
+        const int x = c.bwd_chunk_lo[ch] + (lane >> 2);
+        bool pending = x < c.bwd_chunk_hi[ch];
+        BwdItem b{};
+        if (pending) b = bwd_prep(c, L.nin, L.kind, x);
+        long long spins = 0;
+        while (__any_sync(0xffffffffu, pending)) {
+            if (pending && quad_all(bwd_probe(c, b, epoch))) {
+                bwd_run<UNIFORM, true>(c, L.lut, L.sense, b, q, epoch);
+                pending = false;
+            }
+            if (__any_sync(0xffffffffu, pending) && !warp_idle_round(c, spins)) break;
+        }
+    }
+}
+
+template <class F>
+static cudaError_t occupancy_blocks(F kernel, size_t smem, int *blocks)
+{
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kDfThreads, smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    *blocks = per_sm * sms;
+    return cudaSuccess;
+}
+
+size_t dataflow_smem_bytes(int T) { return df_smem_bytes(T); }
+
+// Shared-memory attribute and persistent grid sizes, computed outside any
+// stream capture.  `requested` > 0 fixes the grid size.
+cudaError_t dataflow_prepare(HostSched &h, bool smooth, int requested)
+{
+    const size_t smem = df_smem_bytes(h.T);
+    auto kf = smooth ? (h.uniform ? k_df_forward<true, true> : k_df_forward<true, false>)
+                     : (h.uniform ? k_df_forward<false, true> : k_df_forward<false, false>);
+    auto kb = h.uniform ? k_df_backward<true> : k_df_backward<false>;
+    int bf = 0, bb = 0;
+    cudaError_t e = occupancy_blocks(kf, smem, &bf);
+    if (e == cudaSuccess) e = occupancy_blocks(kb, smem, &bb);
+    if (e != cudaSuccess) return e;
+    h.df_blocks_fwd = requested > 0 ? std::min(requested, bf) : bf;
+    h.df_blocks_bwd = requested > 0 ? std::min(requested, bb) : bb;
+    return cudaSuccess;
+}
+
+void launch_dataflow_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev)
+{
+    const size_t smem = df_smem_bytes(h.T);
+    if (ev) cudaEventRecord(ev[0], st);
+    k_df_begin<<<1, 32, 0, st>>>(c);
+    if (h.placed) {
+        if (c.I > 0) launch_net_star(c, st);
+    } else if (h.n_tiles > 0) {
+        launch_net_tree(c, h, st);
+    }
+    if (ev) cudaEventRecord(ev[1], st);
+    if (c.n_fwd_chunks > 0) {
+        auto kf = c.gamma > 0.f ? (h.uniform ? k_df_forward<true, true> : k_df_forward<true, false>)
+                                : (h.uniform ? k_df_forward<false, true> : k_df_forward<false, false>);
+        kf<<<h.df_blocks_fwd, kDfThreads, smem, st>>>(c);
+    }
+    if (ev) cudaEventRecord(ev[2], st);
+    if (c.n_bwd_chunks > 0) {
+        auto kb = h.uniform ? k_df_backward<true> : k_df_backward<false>;
+        kb<<<h.df_blocks_bwd, kDfThreads, smem, st>>>(c);
+    }
+    if (ev) cudaEventRecord(ev[3], st);
+    launch_reduce(c, h, st);
+    if (ev) cudaEventRecord(ev[4], st);
+}
+
+}  // namespace sta

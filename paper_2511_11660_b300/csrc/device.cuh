@@ -45,86 +45,52 @@ struct DevCtx {
     double *red_partial;                        // [n_red_chunks][K][6] scratch
     unsigned *err;
     float *scratch_a, *scratch_b;               // RC sweeps of nets larger than a tile
+    // dataflow schedule
+    unsigned *flag;                             // [P] ready epoch per pin (drivers: forward, gate inputs: backward)
+    unsigned *df_state;                         // [0] epoch, [1] forward chunk counter, [2] backward counter, [3] abort
+    int32_t ep_begin;                           // first endpoint pin (endpoints are the last E pins)
+    int32_t hold_item;                          // test hook: item whose forward flag is never published (-1 none)
+    long long spin_limit;                       // polls before a wait gives up
+    int32_t n_fwd_chunks, n_bwd_chunks;
+    const int32_t *fwd_chunk_lo, *fwd_chunk_hi;   // forward work: items by level, then endpoints (index I + e)
+    const int32_t *bwd_chunk_lo, *bwd_chunk_hi;   // backward work: items by level, deepest first
+    // shared table axes (valid when every table has the same ones): slew and
+    // load breakpoints and reciprocal segment widths
+    float ax1[7], ax2[7], iw1[6], iw2[6];
 };
+
+// arc senses as the kernels see them
+constexpr int kSensePosC = 0, kSenseNegC = 1, kSenseNonC = 2, kSenseRiseC = 3;
 
 __device__ __forceinline__ float comp(const float4 &v, int i)
 {
     return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w;
 }
 
-// NLDM bilinear lookup (segment = number of interior breakpoints <= query,
-// so queries off the table extrapolate from the edge segment).  Packed table:
-// idx1[0..6] idx2[7..13] 1/width1[14..19] 1/width2[20..25] val[26..74].
-__device__ __forceinline__ float lut_eval(const float *__restrict__ tb, float s, float l)
-{
-    const int i = (s >= __ldg(tb + 1)) + (s >= __ldg(tb + 2)) + (s >= __ldg(tb + 3)) + (s >= __ldg(tb + 4)) +
-                  (s >= __ldg(tb + 5));
-    const int j = (l >= __ldg(tb + 8)) + (l >= __ldg(tb + 9)) + (l >= __ldg(tb + 10)) + (l >= __ldg(tb + 11)) +
-                  (l >= __ldg(tb + 12));
-    const float t = (s - __ldg(tb + i)) * __ldg(tb + 14 + i);
-    const float u = (l - __ldg(tb + 7 + j)) * __ldg(tb + 20 + j);
-    const float *v = tb + 26 + i * 7 + j;
-    const float v00 = __ldg(v), v01 = __ldg(v + 1), v10 = __ldg(v + 7), v11 = __ldg(v + 8);
-    const float a = fmaf(u, v01 - v00, v00);
-    const float b = fmaf(u, v11 - v10, v10);
-    return fmaf(t, b - a, a);
-}
-
-// Same lookup, also returning d/ds and d/dl.
-__device__ __forceinline__ float lut_eval_d(const float *__restrict__ tb, float s, float l, float &ds, float &dl)
-{
-    const int i = (s >= __ldg(tb + 1)) + (s >= __ldg(tb + 2)) + (s >= __ldg(tb + 3)) + (s >= __ldg(tb + 4)) +
-                  (s >= __ldg(tb + 5));
-    const int j = (l >= __ldg(tb + 8)) + (l >= __ldg(tb + 9)) + (l >= __ldg(tb + 10)) + (l >= __ldg(tb + 11)) +
-                  (l >= __ldg(tb + 12));
-    const float w1 = __ldg(tb + 14 + i), w2 = __ldg(tb + 20 + j);
-    const float t = (s - __ldg(tb + i)) * w1;
-    const float u = (l - __ldg(tb + 7 + j)) * w2;
-    const float *v = tb + 26 + i * 7 + j;
-    const float v00 = __ldg(v), v01 = __ldg(v + 1), v10 = __ldg(v + 7), v11 = __ldg(v + 8);
-    const float a = fmaf(u, v01 - v00, v00);
-    const float b = fmaf(u, v11 - v10, v10);
-    ds = (b - a) * w1;
-    dl = ((1.f - t) * (v01 - v00) + t * (v11 - v10)) * w2;
-    return fmaf(t, b - a, a);
-}
-
-// Running merge of candidates: LATE keeps the max, early the min; SMOOTH
-// replaces both by gamma * log-sum-exp (max-shifted).
-template <bool LATE, bool SMOOTH>
-struct Merge {
-    float m, s;
-    __device__ __forceinline__ Merge() : m(LATE ? -INFINITY : INFINITY), s(0.f) {}
-    __device__ __forceinline__ void add(float x, float inv_g)
+// Running max of candidates y (callers pass y = x for a late max and y = -x
+// for an early min, and negate the result back).  SMOOTH replaces the max by
+// gamma * log-sum-exp(y / gamma), accumulated max-shifted.
+template <bool SMOOTH>
+struct MaxMerge {
+    float m = -INFINITY, s = 0.f;
+    __device__ __forceinline__ void add(float y, float inv_g)
     {
         if (!SMOOTH) {
-            m = LATE ? fmaxf(m, x) : fminf(m, x);
+            m = fmaxf(m, y);
+        } else if (y > m) {
+            s = s * expf((m - y) * inv_g) + 1.f;
+            m = y;
         } else {
-            const float y = LATE ? x : -x, mm = LATE ? m : -m;
-            if (y > mm) {
-                s = s * expf((mm - y) * inv_g) + 1.f;
-                m = x;
-            } else {
-                s += expf((y - mm) * inv_g);
-            }
+            s += expf((y - m) * inv_g);
         }
     }
-    __device__ __forceinline__ float get(float g) const
-    {
-        if (!SMOOTH) return m;
-        return LATE ? m + g * logf(s) : m - g * logf(s);
-    }
+    __device__ __forceinline__ float get(float g) const { return SMOOTH ? m + g * logf(s) : m; }
 };
 
 __device__ __forceinline__ int item_out_pin(const DevCtx &c, int t, int pin0)
 {
     if (t < 0) return pin0;
     return __ldg(c.type_kind + t) == 1 ? pin0 + 1 : pin0 + __ldg(c.type_nin + t);
-}
-
-__device__ __forceinline__ const float *table(const DevCtx &c, int t, int slot, int tb)
-{
-    return c.lut + ((size_t)(t * 3 + slot) * 4 + tb) * kLutStride;
 }
 
 }  // namespace sta

@@ -1,0 +1,448 @@
+// item.cuh -- the per-item timing math shared by the level kernels and the
+// persistent dataflow kernels.
+//
+// An item is a primary input, a flip-flop (CK -> Q) or a gate with its input
+// pins and output pin.  Forward: the gate's input pins take the driver's
+// arrival + Elmore delay and slew sqrt(s^2 + var) (net arcs); the output
+// merges every arc candidate: arrival = input arrival + NLDM delay(input
+// slew, load), slew = NLDM slew(input slew, load), max for late, min for
+// early (log-sum-exp when smoothed).  Backward: the output's required time
+// is the min (late) / max (early) over its net sinks of RAT - Elmore delay;
+// each input's is the min/max over its arcs of output RAT - arc delay.
+//
+// Four lanes (a "quad") work on one item: lane q owns state component q =
+// el*2 + rf (early-rise, early-fall, late-rise, late-fall), so a thread's
+// serial chain is a quarter of the item and the four lanes write 16
+// contiguous bytes of every float4.
+//
+// WAIT = true reads values produced by other items of the same launch at
+// L2 (the dataflow schedule acquires their ready flags first, see
+// dataflow.cu) and publishes the item's own flags; WAIT = false relies on
+// launch boundaries (level schedule).
+#pragma once
+
+#include "device.cuh"
+
+namespace sta {
+
+// ---------------------------------------------------------------- tables
+
+// Table reads: from global memory through the read-only cache, or from a
+// shared-memory copy of the packed library.
+struct LutGlobal {
+    const float *base;
+    __device__ __forceinline__ float operator[](int off) const { return __ldg(base + off); }
+};
+struct LutShared {
+    const float *base;   // points into shared memory
+    __device__ __forceinline__ float operator[](int off) const { return base[off]; }
+};
+
+struct Seg {
+    int o;     // offset of the segment's first value (i*7 on the slew axis, j on the load axis)
+    float t;   // position inside the segment (outside [0, 1] when extrapolating)
+};
+
+// Segment = number of interior breakpoints <= x (off-table queries use the
+// edge segment); weight = (x - x_i) / (x_{i+1} - x_i) via a stored reciprocal.
+template <class L>
+__device__ __forceinline__ Seg seg_slew_t(const L &lut, int tb, float s)
+{
+    const int i = (s >= lut[tb + 1]) + (s >= lut[tb + 2]) + (s >= lut[tb + 3]) + (s >= lut[tb + 4]) +
+                  (s >= lut[tb + 5]);
+    return Seg{i * 7, (s - lut[tb + i]) * lut[tb + 14 + i]};
+}
+template <class L>
+__device__ __forceinline__ Seg seg_load_t(const L &lut, int tb, float l)
+{
+    const int j = (l >= lut[tb + 8]) + (l >= lut[tb + 9]) + (l >= lut[tb + 10]) + (l >= lut[tb + 11]) +
+                  (l >= lut[tb + 12]);
+    return Seg{j, (l - lut[tb + 7 + j]) * lut[tb + 20 + j]};
+}
+
+// The same segment rule on the shared axes held in the kernel parameters:
+// comparisons and selects only, no memory access.
+__device__ __forceinline__ Seg seg_axes(const float *ax, const float *iw, int stride, float x)
+{
+    const bool b1 = x >= ax[1], b2 = x >= ax[2], b3 = x >= ax[3], b4 = x >= ax[4], b5 = x >= ax[5];
+    const int i = b1 + b2 + b3 + b4 + b5;
+    const float x0 = b5 ? ax[5] : b4 ? ax[4] : b3 ? ax[3] : b2 ? ax[2] : b1 ? ax[1] : ax[0];
+    const float w = b5 ? iw[5] : b4 ? iw[4] : b3 ? iw[3] : b2 ? iw[2] : b1 ? iw[1] : iw[0];
+    return Seg{i * stride, (x - x0) * w};
+}
+
+template <bool UNIFORM, class L>
+__device__ __forceinline__ Seg seg_slew(const DevCtx &c, const L &lut, int tb, float s)
+{
+    if (UNIFORM) return seg_axes(c.ax1, c.iw1, 7, s);
+    return seg_slew_t(lut, tb, s);
+}
+template <bool UNIFORM, class L>
+__device__ __forceinline__ Seg seg_load(const DevCtx &c, const L &lut, int tb, float l)
+{
+    if (UNIFORM) return seg_axes(c.ax2, c.iw2, 1, l);
+    return seg_load_t(lut, tb, l);
+}
+
+template <class L>
+__device__ __forceinline__ float interp(const L &lut, int tb, Seg a, Seg b)
+{
+    const int v = tb + 26 + a.o + b.o;
+    const float v00 = lut[v], v01 = lut[v + 1], v10 = lut[v + 7], v11 = lut[v + 8];
+    const float x = fmaf(b.t, v01 - v00, v00);
+    const float y = fmaf(b.t, v11 - v10, v10);
+    return fmaf(a.t, y - x, x);
+}
+// The same bilinear form with its partials: d/ds (per ns) and d/dl (per pF).
+template <class L>
+__device__ __forceinline__ float interp_d(const L &lut, int tb, Seg a, Seg b, float &ds, float &dl)
+{
+    const int v = tb + 26 + a.o + b.o;
+    const float v00 = lut[v], v01 = lut[v + 1], v10 = lut[v + 7], v11 = lut[v + 8];
+    const float x = fmaf(b.t, v01 - v00, v00);
+    const float y = fmaf(b.t, v11 - v10, v10);
+    ds = (y - x) * lut[tb + 14 + a.o / 7];
+    dl = fmaf(a.t, (v11 - v10) - (v01 - v00), v01 - v00) * lut[tb + 20 + b.o];
+    return fmaf(a.t, y - x, x);
+}
+
+__device__ __forceinline__ int tab_off(int t, int slot, int tb) { return ((t * 3 + slot) * 4 + tb) * kLutStride; }
+
+// value of table tq at (s, l): shared segments when every table has the same
+// axes (UNIFORM), else the table's own segments
+template <bool UNIFORM, class L>
+__device__ __forceinline__ float lookup(const L &lut, int tq, Seg as, Seg bl, float s, float l)
+{
+    if (UNIFORM) return interp(lut, tq, as, bl);
+    return interp(lut, tq, seg_slew_t(lut, tq, s), seg_load_t(lut, tq, l));
+}
+
+// ------------------------------------------------------ flags and loads
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+{
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+{
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_volatile(const unsigned *p) { return *(const volatile unsigned *)p; }
+
+// State written by another item of the same launch is read at L2 (after the
+// acquire that ordered it).
+template <bool WAIT>
+__device__ __forceinline__ float4 ld_state(const float4 *p)
+{
+    if (WAIT) return __ldcg(p);
+    return *p;
+}
+template <bool WAIT>
+__device__ __forceinline__ float ld_comp(const float4 *p, int q)
+{
+    const float *f = reinterpret_cast<const float *>(p) + q;
+    if (WAIT) return __ldcg(f);
+    return *f;
+}
+__device__ __forceinline__ void st_comp(float4 *p, int q, float v) { reinterpret_cast<float *>(p)[q] = v; }
+
+__device__ __forceinline__ bool arc_on(int sense, int rfi, int rfo)
+{
+    return sense == kSenseNonC || (sense == kSensePosC && rfi == rfo) || (sense == kSenseNegC && rfi != rfo);
+}
+
+// lanes of the quad that owns this lane
+__device__ __forceinline__ unsigned quad_mask() { return 0xFu << (threadIdx.x & 28); }
+
+// every lane of the quad agrees
+__device__ __forceinline__ bool quad_all(bool ok) { return __all_sync(quad_mask(), ok); }
+
+// Publish a ready flag for the quad's writes: the warp barrier orders the
+// four lanes' stores before lane 0's release store, which carries them to
+// any reader that acquires the flag.
+__device__ __forceinline__ void quad_publish(unsigned *f, unsigned epoch, int q)
+{
+    __syncwarp(quad_mask());
+    if (q == 0) st_release(f, epoch);
+}
+
+// ------------------------------------------------------------- forward
+//
+// Each item is processed in three steps: prep (loads that do not depend on
+// this pass's results), probe (are the drivers' results published?  only in
+// the dataflow schedule) and run (the arithmetic, the stores and, in the
+// dataflow schedule, the publication of the item's own flag).
+
+struct FwdItem {
+    int t, pin0, nin, kind;
+    int sense[3], drv[3];
+    float Dn0[3], V0[3], ld0;   // corner 0 net values, loaded ahead
+};
+
+__device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, const int *tkind, const int *tsense,
+                                            int g)
+{
+    FwdItem f;
+    f.t = c.item_type[g];
+    f.pin0 = c.item_pin0[g];
+    f.kind = f.t >= 0 ? tkind[f.t] : -1;
+    f.nin = f.kind == 0 ? tnin[f.t] : 0;
+    const int K = c.K;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const bool on = j < f.nin;
+        f.sense[j] = on ? tsense[f.t * 3 + j] : -1;
+        f.drv[j] = on ? c.drv_of[f.pin0 + j] : 0;
+        f.Dn0[j] = on ? c.netD[(size_t)(f.pin0 + j) * K] : 0.f;
+        f.V0[j] = on ? c.netV[(size_t)(f.pin0 + j) * K] : 0.f;
+    }
+    const int zl = f.kind == 1 ? f.pin0 + 1 : f.pin0 + f.nin;
+    f.ld0 = f.t >= 0 ? c.load[(size_t)zl * K] : 0.f;
+    return f;
+}
+
+// all drivers of the item published in this pass (acquire)
+__device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, unsigned epoch)
+{
+    bool ok = true;
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        if (j < f.nin) ok = (ld_acquire(c.flag + f.drv[j]) == epoch) && ok;
+    return ok;
+}
+
+// Lane q of the quad computes component q = el*2 + rf of the item's states.
+template <bool SMOOTH, bool UNIFORM, bool WAIT, class L>
+__device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const FwdItem &f, int g, int q,
+                                        unsigned epoch)
+{
+    const int K = c.K, t = f.t, pin0 = f.pin0, nin = f.nin;
+    const int el = q >> 1, rfo = q & 1;
+    if (t < 0) {   // primary input
+        for (int k = 0; k < K; ++k) {
+            st_comp(c.at + (size_t)pin0 * K + k, q, c.pi_at);
+            st_comp(c.slew + (size_t)pin0 * K + k, q, c.pi_slew);
+        }
+        if (WAIT && g != c.hold_item) quad_publish(c.flag + pin0, epoch, q);
+        return;
+    }
+    if (f.kind == 1) {   // flip-flop: ideal clock at CK, arc CK(rise) -> Q for both edges of Q
+        const int ck = pin0, qp = pin0 + 1;
+        const float cs = c.clk_slew;
+        const int tb = tab_off(t, 1, 0);
+        for (int k = 0; k < K; ++k) {
+            const float sc = __ldg(c.lut_scale + k);
+            const float ld = k ? c.load[(size_t)qp * K + k] : f.ld0;
+            st_comp(c.at + (size_t)ck * K + k, q, 0.f);
+            st_comp(c.slew + (size_t)ck * K + k, q, cs);
+            const Seg as = seg_slew<UNIFORM>(c, lut, tb, cs), bl = seg_load<UNIFORM>(c, lut, tb, ld);
+            st_comp(c.at + (size_t)qp * K + k, q, sc * lookup<UNIFORM>(lut, tb + rfo * kLutStride, as, bl, cs, ld));
+            st_comp(c.slew + (size_t)qp * K + k, q,
+                    sc * lookup<UNIFORM>(lut, tb + (2 + rfo) * kLutStride, as, bl, cs, ld));
+        }
+        if (WAIT && g != c.hold_item) quad_publish(c.flag + qp, epoch, q);
+        return;
+    }
+    const int z = pin0 + nin;
+    const float sgn = el ? 1.f : -1.f;   // early merges are mins: max of the negated candidates
+    for (int k = 0; k < K; ++k) {
+        // net arcs into the input pins: this lane needs components el*2 + {0, 1}
+        float ain[3][2], sin[3][2];
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (j < nin) {
+                const int a = pin0 + j;
+                const float4 ad = ld_state<WAIT>(c.at + (size_t)f.drv[j] * K + k);
+                const float4 sd = ld_state<WAIT>(c.slew + (size_t)f.drv[j] * K + k);
+                const float Dn = k ? c.netD[(size_t)a * K + k] : f.Dn0[j];
+                const float V = k ? c.netV[(size_t)a * K + k] : f.V0[j];
+                ain[j][0] = (el ? ad.z : ad.x) + Dn;
+                ain[j][1] = (el ? ad.w : ad.y) + Dn;
+                const float s0 = el ? sd.z : sd.x, s1 = el ? sd.w : sd.y;
+                sin[j][0] = sqrtf(fmaf(s0, s0, V));
+                sin[j][1] = sqrtf(fmaf(s1, s1, V));
+                // lane q stores component q of the input pin: (el, rf = q & 1)
+                st_comp(c.at + (size_t)a * K + k, q, rfo ? ain[j][1] : ain[j][0]);
+                st_comp(c.slew + (size_t)a * K + k, q, rfo ? sin[j][1] : sin[j][0]);
+            }
+        }
+        const float sc = __ldg(c.lut_scale + k);
+        const float ld = k ? c.load[(size_t)z * K + k] : f.ld0;
+        const Seg bl = seg_load<UNIFORM>(c, lut, tab_off(t, 0, 0), ld);
+        MaxMerge<SMOOTH> ma, ms;
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (j >= nin) continue;
+            const int tbj = tab_off(t, j, 0);
+#pragma unroll
+            for (int rfi = 0; rfi < 2; ++rfi) {
+                if (!arc_on(f.sense[j], rfi, rfo)) continue;
+                const float s = sin[j][rfi];
+                const Seg as = seg_slew<UNIFORM>(c, lut, tbj, s);
+                const float dv = lookup<UNIFORM>(lut, tbj + rfo * kLutStride, as, bl, s, ld);
+                const float sv = lookup<UNIFORM>(lut, tbj + (2 + rfo) * kLutStride, as, bl, s, ld);
+                ma.add(sgn * fmaf(sc, dv, ain[j][rfi]), c.inv_gamma);
+                ms.add(sgn * (sc * sv), c.inv_gamma);
+            }
+        }
+        st_comp(c.at + (size_t)z * K + k, q, sgn * ma.get(c.gamma));
+        st_comp(c.slew + (size_t)z * K + k, q, sgn * ms.get(c.gamma));
+    }
+    if (WAIT && g != c.hold_item) quad_publish(c.flag + z, epoch, q);
+}
+
+// ------------------------------------------------------------ endpoints
+
+struct EpItem {
+    int p, d;
+    bool isD;
+    float Dn0, V0;
+};
+
+__device__ __forceinline__ EpItem ep_prep(const DevCtx &c, int e)
+{
+    EpItem x;
+    x.p = c.ep_pin[e];
+    x.d = c.drv_of[x.p];
+    x.isD = c.ep_is_d[e] != 0;
+    x.Dn0 = c.netD[(size_t)x.p * c.K];
+    x.V0 = c.netV[(size_t)x.p * c.K];
+    return x;
+}
+
+__device__ __forceinline__ bool ep_probe(const DevCtx &c, const EpItem &x, unsigned epoch)
+{
+    return ld_acquire(c.flag + x.d) == epoch;
+}
+
+// Arrival through the net, required times of the ideal clock (D: setup
+// capture edge T - setup, hold 0 + hold; PO: T and 0), pin and endpoint
+// slacks (min over rise/fall) and violation flags.  Lane q: component q.
+template <bool WAIT>
+__device__ __forceinline__ void ep_run(const DevCtx &c, const EpItem &x, int e, int q)
+{
+    const int K = c.K, p = x.p, d = x.d;
+    const float req = q >= 2 ? (x.isD ? c.period - c.setup : c.period) : (x.isD ? c.hold : 0.f);
+    const unsigned m = quad_mask();
+    const int base = threadIdx.x & 28;   // first lane of the quad
+    for (int k = 0; k < K; ++k) {
+        const float ad = ld_comp<WAIT>(c.at + (size_t)d * K + k, q), sd = ld_comp<WAIT>(c.slew + (size_t)d * K + k, q);
+        const float Dn = k ? c.netD[(size_t)p * K + k] : x.Dn0, V = k ? c.netV[(size_t)p * K + k] : x.V0;
+        const float A = ad + Dn;
+        st_comp(c.at + (size_t)p * K + k, q, A);
+        st_comp(c.slew + (size_t)p * K + k, q, sqrtf(fmaf(sd, sd, V)));
+        st_comp(c.rat + (size_t)p * K + k, q, req);
+        const float sk = q >= 2 ? req - A : A - req;
+        st_comp(c.slack + (size_t)p * K + k, q, sk);
+        const float worst = fminf(sk, __shfl_xor_sync(m, sk, 1));   // min over the two edges
+        const float ss = __shfl_sync(m, worst, base + 2), hs = __shfl_sync(m, worst, base);
+        if (q == 0) {
+            c.ep_setup[(size_t)e * K + k] = ss;
+            c.ep_hold[(size_t)e * K + k] = hs;
+            c.viol_setup[(size_t)e * K + k] = ss < 0.f;
+            c.viol_hold[(size_t)e * K + k] = hs < 0.f;
+        }
+    }
+}
+
+// ------------------------------------------------------------- backward
+
+struct BwdItem {
+    int t, pin0, nin, kind, z, f0, f1;
+    float ld0;
+};
+
+__device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, const int *tkind, int g)
+{
+    BwdItem b;
+    b.t = c.item_type[g];
+    b.pin0 = c.item_pin0[g];
+    b.kind = b.t >= 0 ? tkind[b.t] : -1;
+    b.nin = b.t >= 0 ? tnin[b.t] : 0;
+    b.z = b.t < 0 ? b.pin0 : (b.kind == 1 ? b.pin0 + 1 : b.pin0 + b.nin);
+    b.f0 = c.fo_ptr[g];
+    b.f1 = c.fo_ptr[g + 1];
+    b.ld0 = b.t >= 0 ? c.load[(size_t)b.z * c.K] : 0.f;
+    return b;
+}
+
+// every gate-input sink of the item's net has its required time (acquire);
+// endpoint sinks were set by the forward pass
+__device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, unsigned epoch)
+{
+    bool ok = true;
+    for (int p = b.f0; p < b.f1; ++p) {
+        const int s = c.fo_pin[p];
+        if (s < c.ep_begin) ok = (ld_acquire(c.flag + s) == epoch) && ok;
+    }
+    return ok;
+}
+
+template <bool UNIFORM, bool WAIT, class L>
+__device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int *tsense, const BwdItem &b, int q,
+                                        unsigned epoch)
+{
+    const int t = b.t, pin0 = b.pin0, z = b.z, K = c.K;
+    const int el = q >> 1, rfi = q & 1;
+    const unsigned m = quad_mask();
+    const int base = threadIdx.x & 28;
+    for (int k = 0; k < K; ++k) {
+        // required time of the output, component q, over its net sinks
+        float R = el ? INFINITY : -INFINITY;
+        for (int p = b.f0; p < b.f1; ++p) {
+            const int s = c.fo_pin[p];
+            const float r = ld_comp<WAIT>(c.rat + (size_t)s * K + k, q) - c.netD[(size_t)s * K + k];
+            R = el ? fminf(R, r) : fmaxf(R, r);
+        }
+        st_comp(c.rat + (size_t)z * K + k, q, R);
+        const float Az = reinterpret_cast<const float *>(c.at + (size_t)z * K + k)[q];
+        st_comp(c.slack + (size_t)z * K + k, q, el ? R - Az : Az - R);
+        if (t < 0) continue;
+        // the output's required times of both edges at this lane's el
+        const float R0 = __shfl_sync(m, R, base + el * 2), R1 = __shfl_sync(m, R, base + el * 2 + 1);
+        const float sc = __ldg(c.lut_scale + k);
+        const float ld = k ? c.load[(size_t)z * K + k] : b.ld0;
+        if (b.kind == 1) {   // CK: only the rising edge has an arc (to both edges of Q)
+            const int ck = pin0;
+            const float s = reinterpret_cast<const float *>(c.slew + (size_t)ck * K + k)[el * 2];
+            const int tb = tab_off(t, 1, 0);
+            const Seg as = seg_slew<UNIFORM>(c, lut, tb, s), bl = seg_load<UNIFORM>(c, lut, tb, ld);
+            const float d0 = sc * lookup<UNIFORM>(lut, tb, as, bl, s, ld);
+            const float d1 = sc * lookup<UNIFORM>(lut, tb + kLutStride, as, bl, s, ld);
+            float Rc = el ? fminf(R0 - d0, R1 - d1) : fmaxf(R0 - d0, R1 - d1);
+            if (rfi == 1) Rc = el ? INFINITY : -INFINITY;
+            st_comp(c.rat + (size_t)ck * K + k, q, Rc);
+            const float Ac = reinterpret_cast<const float *>(c.at + (size_t)ck * K + k)[q];
+            st_comp(c.slack + (size_t)ck * K + k, q, el ? Rc - Ac : Ac - Rc);
+            continue;
+        }
+        const Seg bl = seg_load<UNIFORM>(c, lut, tab_off(t, 0, 0), ld);
+        for (int j = 0; j < b.nin; ++j) {
+            const int a = pin0 + j;
+            const int se = tsense[t * 3 + j];
+            const int tbj = tab_off(t, j, 0);
+            const float s = reinterpret_cast<const float *>(c.slew + (size_t)a * K + k)[q];
+            const Seg as = seg_slew<UNIFORM>(c, lut, tbj, s);
+            float acc = el ? INFINITY : -INFINITY;
+#pragma unroll
+            for (int rfo = 0; rfo < 2; ++rfo) {
+                if (!arc_on(se, rfi, rfo)) continue;
+                const float dv = lookup<UNIFORM>(lut, tbj + rfo * kLutStride, as, bl, s, ld);
+                const float cand = (rfo ? R1 : R0) - sc * dv;
+                acc = el ? fminf(acc, cand) : fmaxf(acc, cand);
+            }
+            st_comp(c.rat + (size_t)a * K + k, q, acc);
+            const float Aa = reinterpret_cast<const float *>(c.at + (size_t)a * K + k)[q];
+            st_comp(c.slack + (size_t)a * K + k, q, el ? acc - Aa : Aa - acc);
+        }
+    }
+    if (WAIT && b.kind == 0) {
+        __syncwarp(m);
+        if (q == 0)
+            for (int j = 0; j < b.nin; ++j) st_release(c.flag + pin0 + j, epoch);
+    }
+}
+
+}  // namespace sta

@@ -8,6 +8,7 @@
 // propagation, Sec. I; Elmore delay, Sec. III "Delay models"; WNS/TNS and
 // pin slacks, Sec. III "Report options") without formulas; the formulas are
 // the textbook ones stated in include/sta.h.
+#include "item.cuh"
 #include "kernels.h"
 
 namespace sta {
@@ -110,207 +111,35 @@ __global__ void k_net_star(const DevCtx c)
     }
 }
 
-// --------------------------------------------------------------- forward
+// ------------------------------------------------- level-schedule passes
 
-template <bool SMOOTH>
-__device__ __forceinline__ void fwd_item(const DevCtx &c, int g)
-{
-    const int t = c.item_type[g];
-    const int pin0 = c.item_pin0[g];
-    const int K = c.K;
-    if (t < 0) {   // primary input
-        const float4 a = make_float4(c.pi_at, c.pi_at, c.pi_at, c.pi_at);
-        const float4 s = make_float4(c.pi_slew, c.pi_slew, c.pi_slew, c.pi_slew);
-        for (int k = 0; k < K; ++k) {
-            c.at[(size_t)pin0 * K + k] = a;
-            c.slew[(size_t)pin0 * K + k] = s;
-        }
-        return;
-    }
-    if (__ldg(c.type_kind + t) == 1) {   // flip-flop: ideal clock at CK, arc CK(rise) -> Q
-        const int ck = pin0, q = pin0 + 1;
-        const float cs = c.clk_slew;
-        const float *tb = table(c, t, 1, 0);
-        for (int k = 0; k < K; ++k) {
-            const float sc = __ldg(c.lut_scale + k);
-            const float ld = c.load[(size_t)q * K + k];
-            c.at[(size_t)ck * K + k] = make_float4(0.f, 0.f, 0.f, 0.f);
-            c.slew[(size_t)ck * K + k] = make_float4(cs, cs, cs, cs);
-            const float dr = sc * lut_eval(tb, cs, ld), df = sc * lut_eval(tb + kLutStride, cs, ld);
-            const float sr = sc * lut_eval(tb + 2 * kLutStride, cs, ld), sf = sc * lut_eval(tb + 3 * kLutStride, cs, ld);
-            c.at[(size_t)q * K + k] = make_float4(dr, df, dr, df);
-            c.slew[(size_t)q * K + k] = make_float4(sr, sf, sr, sf);
-        }
-        return;
-    }
-    const int nin = __ldg(c.type_nin + t);
-    const int z = pin0 + nin;
-    int sense[3];
-#pragma unroll
-    for (int j = 0; j < 3; ++j) sense[j] = j < nin ? __ldg(c.arc_sense + t * 3 + j) : -1;
-    for (int k = 0; k < K; ++k) {
-        float4 A[3], S[3];
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-            if (j < nin) {
-                const int a = pin0 + j;
-                const int d = c.drv_of[a];
-                const float4 ad = c.at[(size_t)d * K + k], sd = c.slew[(size_t)d * K + k];
-                const float Dn = c.netD[(size_t)a * K + k], V = c.netV[(size_t)a * K + k];
-                A[j] = make_float4(ad.x + Dn, ad.y + Dn, ad.z + Dn, ad.w + Dn);
-                S[j] = make_float4(sqrtf(fmaf(sd.x, sd.x, V)), sqrtf(fmaf(sd.y, sd.y, V)), sqrtf(fmaf(sd.z, sd.z, V)),
-                                   sqrtf(fmaf(sd.w, sd.w, V)));
-                c.at[(size_t)a * K + k] = A[j];
-                c.slew[(size_t)a * K + k] = S[j];
-            }
-        }
-        const float sc = __ldg(c.lut_scale + k);
-        const float ld = c.load[(size_t)z * K + k];
-        float oa[4], os[4];
-#pragma unroll
-        for (int rfo = 0; rfo < 2; ++rfo) {
-            Merge<true, SMOOTH> la, ls;
-            Merge<false, SMOOTH> ea, es;
-#pragma unroll
-            for (int j = 0; j < 3; ++j) {
-                if (j >= nin) continue;
-                const float *td = table(c, t, j, rfo), *ts = table(c, t, j, 2 + rfo);
-#pragma unroll
-                for (int rfi = 0; rfi < 2; ++rfi) {
-                    const bool on = sense[j] == 2 || (sense[j] == 0 && rfi == rfo) || (sense[j] == 1 && rfi != rfo);
-                    if (!on) continue;
-                    const float se = comp(S[j], rfi), sl = comp(S[j], 2 + rfi);
-                    ea.add(comp(A[j], rfi) + sc * lut_eval(td, se, ld), c.inv_gamma);
-                    es.add(sc * lut_eval(ts, se, ld), c.inv_gamma);
-                    la.add(comp(A[j], 2 + rfi) + sc * lut_eval(td, sl, ld), c.inv_gamma);
-                    ls.add(sc * lut_eval(ts, sl, ld), c.inv_gamma);
-                }
-            }
-            oa[rfo] = ea.get(c.gamma);
-            os[rfo] = es.get(c.gamma);
-            oa[2 + rfo] = la.get(c.gamma);
-            os[2 + rfo] = ls.get(c.gamma);
-        }
-        c.at[(size_t)z * K + k] = make_float4(oa[0], oa[1], oa[2], oa[3]);
-        c.slew[(size_t)z * K + k] = make_float4(os[0], os[1], os[2], os[3]);
-    }
-}
-
-template <bool SMOOTH>
+// One launch per level: four lanes per item run fwd_item / bwd_item
+// (item.cuh), reading tables through the read-only cache.
+template <bool SMOOTH, bool UNIFORM>
 __global__ void k_fwd_level(const DevCtx c, int i0, int i1)
 {
-    const int g = i0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < i1) fwd_item<SMOOTH>(c, g);
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = i0 + (tid >> 2);
+    if (g < i1) {
+        const FwdItem f = fwd_prep(c, c.type_nin, c.type_kind, c.arc_sense, g);
+        fwd_run<SMOOTH, UNIFORM, false>(c, LutGlobal{c.lut}, f, g, tid & 3, 0u);
+    }
 }
 
-// ------------------------------------------------------------- endpoints
-
-// Arrival at the endpoint through its net, the required times of the ideal
-// clock (D: setup capture edge T - setup, hold edge 0 + hold; PO: T and 0),
-// pin slack, and the endpoint slacks (min over rise/fall) with violation
-// flags.
 __global__ void k_endpoints(const DevCtx c)
 {
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= c.E) return;
-    const int p = c.ep_pin[e];
-    const int d = c.drv_of[p];
-    const bool isD = c.ep_is_d[e] != 0;
-    const int K = c.K;
-    const float rl = isD ? c.period - c.setup : c.period;
-    const float re = isD ? c.hold : 0.f;
-    for (int k = 0; k < K; ++k) {
-        const float4 ad = c.at[(size_t)d * K + k], sd = c.slew[(size_t)d * K + k];
-        const float Dn = c.netD[(size_t)p * K + k], V = c.netV[(size_t)p * K + k];
-        const float4 A = make_float4(ad.x + Dn, ad.y + Dn, ad.z + Dn, ad.w + Dn);
-        const float4 S = make_float4(sqrtf(fmaf(sd.x, sd.x, V)), sqrtf(fmaf(sd.y, sd.y, V)),
-                                     sqrtf(fmaf(sd.z, sd.z, V)), sqrtf(fmaf(sd.w, sd.w, V)));
-        c.at[(size_t)p * K + k] = A;
-        c.slew[(size_t)p * K + k] = S;
-        c.rat[(size_t)p * K + k] = make_float4(re, re, rl, rl);
-        const float4 sk = make_float4(A.x - re, A.y - re, rl - A.z, rl - A.w);
-        c.slack[(size_t)p * K + k] = sk;
-        const float ss = fminf(sk.z, sk.w), hs = fminf(sk.x, sk.y);
-        c.ep_setup[(size_t)e * K + k] = ss;
-        c.ep_hold[(size_t)e * K + k] = hs;
-        c.viol_setup[(size_t)e * K + k] = ss < 0.f;
-        c.viol_hold[(size_t)e * K + k] = hs < 0.f;
-    }
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int e = tid >> 2;
+    if (e < c.E) ep_run<false>(c, ep_prep(c, e), e, tid & 3);
 }
 
-// -------------------------------------------------------------- backward
-
-__device__ __forceinline__ void bwd_item(const DevCtx &c, int g)
-{
-    const int t = c.item_type[g];
-    const int pin0 = c.item_pin0[g];
-    const int z = item_out_pin(c, t, pin0);
-    const int f0 = c.fo_ptr[g], f1 = c.fo_ptr[g + 1];
-    const int K = c.K;
-    const int kind = t >= 0 ? __ldg(c.type_kind + t) : -1;
-    const int nin = t >= 0 ? __ldg(c.type_nin + t) : 0;
-    for (int k = 0; k < K; ++k) {
-        float4 R = make_float4(-INFINITY, -INFINITY, INFINITY, INFINITY);
-        for (int q = f0; q < f1; ++q) {
-            const int s = c.fo_pin[q];
-            const float4 r = c.rat[(size_t)s * K + k];
-            const float Dn = c.netD[(size_t)s * K + k];
-            R.x = fmaxf(R.x, r.x - Dn);
-            R.y = fmaxf(R.y, r.y - Dn);
-            R.z = fminf(R.z, r.z - Dn);
-            R.w = fminf(R.w, r.w - Dn);
-        }
-        const float4 Az = c.at[(size_t)z * K + k];
-        c.rat[(size_t)z * K + k] = R;
-        c.slack[(size_t)z * K + k] = make_float4(Az.x - R.x, Az.y - R.y, R.z - Az.z, R.w - Az.w);
-        if (t < 0) continue;
-        const float sc = __ldg(c.lut_scale + k);
-        const float ld = c.load[(size_t)z * K + k];
-        if (kind == 1) {
-            const int ck = pin0;
-            const float4 S = c.slew[(size_t)ck * K + k];
-            const float *tb = table(c, t, 1, 0);
-            const float er = fmaxf(R.x - sc * lut_eval(tb, S.x, ld), R.y - sc * lut_eval(tb + kLutStride, S.x, ld));
-            const float lr = fminf(R.z - sc * lut_eval(tb, S.z, ld), R.w - sc * lut_eval(tb + kLutStride, S.z, ld));
-            const float4 Rc = make_float4(er, -INFINITY, lr, INFINITY);
-            const float4 Ac = c.at[(size_t)ck * K + k];
-            c.rat[(size_t)ck * K + k] = Rc;
-            c.slack[(size_t)ck * K + k] = make_float4(Ac.x - Rc.x, Ac.y - Rc.y, Rc.z - Ac.z, Rc.w - Ac.w);
-            continue;
-        }
-        for (int j = 0; j < nin; ++j) {
-            const int a = pin0 + j;
-            const int se = __ldg(c.arc_sense + t * 3 + j);
-            const float4 S = c.slew[(size_t)a * K + k];
-            float r[4];
-#pragma unroll
-            for (int el = 0; el < 2; ++el) {
-#pragma unroll
-                for (int rfi = 0; rfi < 2; ++rfi) {
-                    float acc = el ? INFINITY : -INFINITY;
-                    const float s_in = comp(S, el * 2 + rfi);
-#pragma unroll
-                    for (int rfo = 0; rfo < 2; ++rfo) {
-                        const bool on = se == 2 || (se == 0 && rfi == rfo) || (se == 1 && rfi != rfo);
-                        if (!on) continue;
-                        const float cand = comp(R, el * 2 + rfo) - sc * lut_eval(table(c, t, j, rfo), s_in, ld);
-                        acc = el ? fminf(acc, cand) : fmaxf(acc, cand);
-                    }
-                    r[el * 2 + rfi] = acc;
-                }
-            }
-            const float4 Ra = make_float4(r[0], r[1], r[2], r[3]);
-            const float4 Aa = c.at[(size_t)a * K + k];
-            c.rat[(size_t)a * K + k] = Ra;
-            c.slack[(size_t)a * K + k] = make_float4(Aa.x - Ra.x, Aa.y - Ra.y, Ra.z - Aa.z, Ra.w - Aa.w);
-        }
-    }
-}
-
+template <bool UNIFORM>
 __global__ void k_bwd_level(const DevCtx c, int i0, int i1)
 {
-    const int g = i0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < i1) bwd_item(c, g);
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = i0 + (tid >> 2);
+    if (g < i1) bwd_run<UNIFORM, false>(c, LutGlobal{c.lut}, c.arc_sense, bwd_prep(c, c.type_nin, c.type_kind, g),
+                                        tid & 3, 0u);
 }
 
 // ------------------------------------------------------------- reduction
@@ -413,28 +242,42 @@ __global__ void k_gather_f32(const float *__restrict__ src, const int32_t *__res
 
 // ------------------------------------------------------------- launchers
 
+void launch_net_star(const DevCtx &c, cudaStream_t st) { k_net_star<<<nblk(c.I, 128), 128, 0, st>>>(c); }
+
+void launch_net_tree(const DevCtx &c, const HostSched &h, cudaStream_t st)
+{
+    k_net_tree<<<h.n_tiles, kRcTileNets, 0, st>>>(c);
+}
+
 void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev)
 {
     if (ev) cudaEventRecord(ev[0], st);
     if (h.placed) {
-        if (c.I > 0) k_net_star<<<nblk(c.I, 128), 128, 0, st>>>(c);
+        if (c.I > 0) launch_net_star(c, st);
     } else if (h.n_tiles > 0) {
-        k_net_tree<<<h.n_tiles, kRcTileNets, 0, st>>>(c);
+        launch_net_tree(c, h, st);
     }
     if (ev) cudaEventRecord(ev[1], st);
     const int tpb = h.threads > 0 ? h.threads : 128;
     for (int s = 0; s < h.S; ++s) {
         const int i0 = h.stage_ptr[s], i1 = h.stage_ptr[s + 1];
         if (i1 <= i0) continue;
-        if (c.gamma > 0.f) k_fwd_level<true><<<nblk(i1 - i0, tpb), tpb, 0, st>>>(c, i0, i1);
-        else k_fwd_level<false><<<nblk(i1 - i0, tpb), tpb, 0, st>>>(c, i0, i1);
+        const dim3 grid(nblk(4LL * (i1 - i0), tpb));
+        if (c.gamma > 0.f) {
+            if (h.uniform) k_fwd_level<true, true><<<grid, tpb, 0, st>>>(c, i0, i1);
+            else k_fwd_level<true, false><<<grid, tpb, 0, st>>>(c, i0, i1);
+        } else {
+            if (h.uniform) k_fwd_level<false, true><<<grid, tpb, 0, st>>>(c, i0, i1);
+            else k_fwd_level<false, false><<<grid, tpb, 0, st>>>(c, i0, i1);
+        }
     }
-    if (c.E > 0) k_endpoints<<<nblk(c.E, 256), 256, 0, st>>>(c);
+    if (c.E > 0) k_endpoints<<<nblk(4LL * c.E, 256), 256, 0, st>>>(c);
     if (ev) cudaEventRecord(ev[2], st);
     for (int s = h.S - 1; s >= 0; --s) {
         const int i0 = h.stage_ptr[s], i1 = h.stage_ptr[s + 1];
         if (i1 <= i0) continue;
-        k_bwd_level<<<nblk(i1 - i0, tpb), tpb, 0, st>>>(c, i0, i1);
+        if (h.uniform) k_bwd_level<true><<<nblk(4LL * (i1 - i0), tpb), tpb, 0, st>>>(c, i0, i1);
+        else k_bwd_level<false><<<nblk(4LL * (i1 - i0), tpb), tpb, 0, st>>>(c, i0, i1);
     }
     if (ev) cudaEventRecord(ev[3], st);
     launch_reduce(c, h, st);

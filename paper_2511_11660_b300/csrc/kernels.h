@@ -15,6 +15,10 @@ struct HostSched {
     bool placed = false;
     int threads = 128;                // threads per block of the level kernels
     int n_red_chunks = 0;             // first-stage reduction blocks
+    bool uniform = false;             // every table shares the same slew and load axes
+    int T = 0;                        // cell types (shared-memory table size)
+    int df_blocks_fwd = 0;            // persistent grids of the dataflow kernels
+    int df_blocks_bwd = 0;
 };
 
 // Net delays, forward levels, endpoints, backward levels, reduction.  With
@@ -22,6 +26,18 @@ struct HostSched {
 // net delays, ev[2] after forward + endpoints, ev[3] after backward, ev[4]
 // after the reduction.
 void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev = nullptr);
+
+// Net delay calculation: RC trees (tiles in shared memory) or star trees.
+void launch_net_tree(const DevCtx &c, const HostSched &h, cudaStream_t st);
+void launch_net_star(const DevCtx &c, cudaStream_t st);
+
+// Dataflow schedule: one persistent kernel per pass (see dataflow.cu).
+// dataflow_prepare sizes the persistent grids (at most `requested` blocks
+// when > 0, else every block the occupancy allows) and must run before the
+// first launch and outside stream capture.
+size_t dataflow_smem_bytes(int T);
+cudaError_t dataflow_prepare(HostSched &h, bool smooth, int requested);
+void launch_dataflow_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev = nullptr);
 
 // The two-stage FP64 WNS/TNS reduction.
 void launch_reduce(const DevCtx &c, const HostSched &h, cudaStream_t st);

@@ -81,6 +81,22 @@ void pack_library(const sta_library *L, Plan &pl)
             }
         }
     }
+    // do all active tables share the same axes?  Then one segment search per
+    // (slew, load) query serves every table.
+    pl.uniform_axes = true;
+    const float *ref = nullptr;
+    for (int t = 0; t < T && pl.uniform_axes; ++t)
+        for (int s = 0; s < pl.type_nin[t] && pl.uniform_axes; ++s) {
+            if (pl.arc_sense[(size_t)t * 3 + s] == kSenseNone) continue;
+            for (int tb = 0; tb < 4; ++tb) {
+                const float *o = pl.lut.data() + (((size_t)t * 3 + s) * 4 + tb) * kTabStride;
+                if (!ref) {
+                    ref = o;
+                    std::memcpy(pl.axes, o, sizeof(pl.axes));
+                }
+                else if (std::memcmp(o, ref, 26 * sizeof(float)) != 0) { pl.uniform_axes = false; break; }
+            }
+        }
     pl.setup = L->setup_ns;
     pl.hold = L->hold_ns;
     pl.po_cap = L->po_cap_pf;

@@ -75,6 +75,8 @@ struct Plan {
     std::vector<int32_t> cell_type;          // [C]
     std::vector<int32_t> item_of_cell;       // [C]
     std::vector<int32_t> cell_level;         // [C] propagation level of each cell
+    bool uniform_axes = false;               // all tables share one slew axis and one load axis
+    float axes[26] = {};                     // those axes: idx1[7] idx2[7] 1/width1[6] 1/width2[6]
 };
 
 // Validate `desc` and fill `plan`.  On failure returns the status and sets

@@ -96,7 +96,8 @@ void drop_graph(sta_ctx *c)
 
 void record_pass(sta_ctx *c, cudaStream_t st, cudaEvent_t *ev = nullptr)
 {
-    sta::launch_level_pass(c->dc, c->hs, st, ev);
+    if (c->schedule == STA_SCHED_DATAFLOW) sta::launch_dataflow_pass(c->dc, c->hs, st, ev);
+    else sta::launch_level_pass(c->dc, c->hs, st, ev);
 }
 
 void ensure_graph(sta_ctx *c)
@@ -208,6 +209,50 @@ sta_status create_from_plan(sta_ctx *c, int device)
     h.n_tiles = (int)pl.tile_item.size() - 1;
     h.placed = pl.placed;
     h.threads = 128;
+    h.uniform = pl.uniform_axes;
+    if (pl.uniform_axes) {
+        for (int i = 0; i < 7; ++i) {
+            d.ax1[i] = pl.axes[i];
+            d.ax2[i] = pl.axes[7 + i];
+        }
+        for (int i = 0; i < 6; ++i) {
+            d.iw1[i] = pl.axes[14 + i];
+            d.iw2[i] = pl.axes[20 + i];
+        }
+    }
+    h.T = pl.T;
+    // dataflow schedule: ready flags, epoch state and work chunks
+    d.flag = dev_alloc<unsigned>(c, (size_t)pl.P);
+    CK(cudaMemset(d.flag, 0, std::max<size_t>(1, (size_t)pl.P) * sizeof(unsigned)));
+    d.df_state = dev_alloc<unsigned>(c, 4);
+    CK(cudaMemset(d.df_state, 0, 4 * sizeof(unsigned)));
+    d.ep_begin = pl.P - pl.E;
+    d.hold_item = -1;
+    d.spin_limit = 1LL << 23;
+    {
+        constexpr int32_t kChunkItems = 8;   // a warp works on 8 items, four lanes each
+        std::vector<int32_t> flo, fhi, blo, bhi;
+        for (int32_t s = 0; s < pl.S; ++s)
+            for (int32_t g = pl.stage_ptr[s]; g < pl.stage_ptr[s + 1]; g += kChunkItems) {
+                flo.push_back(g);
+                fhi.push_back(std::min(g + kChunkItems, pl.stage_ptr[s + 1]));
+            }
+        for (int32_t e = 0; e < pl.E; e += kChunkItems) {
+            flo.push_back(pl.I + e);
+            fhi.push_back(pl.I + std::min(e + kChunkItems, pl.E));
+        }
+        for (int32_t s = pl.S - 1; s >= 0; --s)
+            for (int32_t g = pl.stage_ptr[s]; g < pl.stage_ptr[s + 1]; g += kChunkItems) {
+                blo.push_back(g);
+                bhi.push_back(std::min(g + kChunkItems, pl.stage_ptr[s + 1]));
+            }
+        d.n_fwd_chunks = (int32_t)flo.size();
+        d.n_bwd_chunks = (int32_t)blo.size();
+        d.fwd_chunk_lo = upload(c, flo);
+        d.fwd_chunk_hi = upload(c, fhi);
+        d.bwd_chunk_lo = upload(c, blo);
+        d.bwd_chunk_hi = upload(c, bhi);
+    }
     for (auto &e : c->ev) CK(cudaEventCreate(&e));
     CK(cudaDeviceSynchronize());
     return STA_OK;
@@ -222,6 +267,13 @@ int32_t launches_per_update(const sta_ctx *c)
     int32_t n = 0;
     if (pl.placed) n += pl.I > 0;
     else n += (int32_t)pl.tile_item.size() > 1;
+    if (c->schedule == STA_SCHED_DATAFLOW) {
+        n += 1;                                  // epoch / counter reset
+        n += c->dc.n_fwd_chunks > 0;
+        n += c->dc.n_bwd_chunks > 0;
+        n += (c->hs.n_red_chunks > 0) + 1;       // two-stage reduction
+        return n;
+    }
     int32_t levels = 0;
     for (int32_t s = 0; s < pl.S; ++s) levels += pl.stage_ptr[s + 1] > pl.stage_ptr[s];
     n += 2 * levels;
@@ -412,9 +464,14 @@ sta_status sta_set_clock(sta_ctx *c, float period_ns)
 sta_status sta_set_schedule(sta_ctx *c, int32_t schedule, int32_t param)
 {
     if (!c) return STA_EINVAL;
-    if (schedule != STA_SCHED_LEVEL) return fail(c, STA_EINVAL, "unknown schedule");
+    if (schedule != STA_SCHED_LEVEL && schedule != STA_SCHED_DATAFLOW)
+        return fail(c, STA_EINVAL, "unknown schedule");
     if (schedule == STA_SCHED_LEVEL && param != 0 && (param < 32 || param > 1024 || param % 32))
         return fail(c, STA_EINVAL, "threads per block must be a multiple of 32 in [32, 1024]");
+    if (schedule == STA_SCHED_DATAFLOW && (param < 0 || param > 65535))
+        return fail(c, STA_EINVAL, "persistent grid size must be in [0, 65535] (0 = from occupancy)");
+    if (schedule == STA_SCHED_DATAFLOW && sta::dataflow_smem_bytes(c->plan.T) > 200 * 1024)
+        return fail(c, STA_EINVAL, "cell library too large for the dataflow schedule's shared-memory copy");
     try {
         CK(cudaSetDevice(c->device));
         drop_graph(c);
@@ -423,7 +480,43 @@ sta_status sta_set_schedule(sta_ctx *c, int32_t schedule, int32_t param)
     }
     c->schedule = schedule;
     c->sched_param = param;
-    if (schedule == STA_SCHED_LEVEL) c->hs.threads = param ? param : 128;
+    if (schedule == STA_SCHED_LEVEL) {
+        c->hs.threads = param ? param : 128;
+    } else {
+        const cudaError_t e = sta::dataflow_prepare(c->hs, c->dc.gamma > 0.f, param);
+        if (e != cudaSuccess) {
+            c->schedule = STA_SCHED_LEVEL;
+            return fail(c, STA_ECUDA, std::string("dataflow set-up: ") + cudaGetErrorString(e));
+        }
+    }
+    return STA_OK;
+}
+
+sta_status sta_set_wait_limit(sta_ctx *c, int64_t polls)
+{
+    if (!c) return STA_EINVAL;
+    if (polls < 1) return fail(c, STA_EINVAL, "wait limit must be >= 1 poll");
+    try {
+        CK(cudaSetDevice(c->device));
+        drop_graph(c);
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    c->dc.spin_limit = polls;
+    return STA_OK;
+}
+
+sta_status sta_debug_hold_cell(sta_ctx *c, int32_t cell)
+{
+    if (!c) return STA_EINVAL;
+    if (cell < -1 || cell >= c->plan.C) return fail(c, STA_EINVAL, "cell index out of range");
+    try {
+        CK(cudaSetDevice(c->device));
+        drop_graph(c);
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    c->dc.hold_item = cell < 0 ? -1 : c->plan.item_of_cell[cell];
     return STA_OK;
 }
 

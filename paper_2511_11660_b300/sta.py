@@ -86,6 +86,8 @@ SIGNATURES = {
     "sta_set_cell_types": (C.c_int, [_V, _P]),
     "sta_set_clock": (C.c_int, [_V, C.c_float]),
     "sta_set_schedule": (C.c_int, [_V, C.c_int32, C.c_int32]),
+    "sta_set_wait_limit": (C.c_int, [_V, C.c_int64]),
+    "sta_debug_hold_cell": (C.c_int, [_V, C.c_int32]),
     "sta_update_timing": (C.c_int, [_V, _V]),
     "sta_sync": (C.c_int, [_V, _V]),
     "sta_report_slack": (C.c_int, [_V, _V, _P]),
@@ -252,6 +254,12 @@ class Context:
 
     def set_schedule(self, schedule: int, param: int = 0):
         self._chk(self.lib.sta_set_schedule(self.h, schedule, param))
+
+    def set_wait_limit(self, polls: int):
+        self._chk(self.lib.sta_set_wait_limit(self.h, int(polls)))
+
+    def debug_hold_cell(self, cell: int):
+        self._chk(self.lib.sta_debug_hold_cell(self.h, int(cell)))
 
     def set_clock(self, period_ns: float):
         self._chk(self.lib.sta_set_clock(self.h, float(period_ns)))
