@@ -220,9 +220,10 @@ sta_status sta_set_schedule(sta_ctx *ctx, int32_t schedule, int32_t param);
 sta_status sta_set_wait_limit(sta_ctx *ctx, int64_t polls);
 
 /* Failure-detection test hook (dataflow schedule): while `cell` >= 0, the
- * forward pass of that cell never publishes its ready flag, so its fan-out
- * waits run out and the update reports STA_ETIMEOUT with the context still
- * usable; -1 restores normal operation. */
+ * forward pass of that cell never publishes its results to the items that
+ * read them, so their bounded waits run out and the update reports
+ * STA_ETIMEOUT with the context still usable; -1 restores normal
+ * operation. */
 sta_status sta_debug_hold_cell(sta_ctx *ctx, int32_t cell);
 
 /* Full analysis on `stream`: net delay calculation, forward arrival/slew

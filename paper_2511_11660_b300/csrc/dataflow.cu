@@ -1,17 +1,15 @@
 // dataflow.cu -- persistent dataflow schedule of the timing pass.
 //
 // Instead of one launch per level, each pass is one persistent kernel.  Its
-// warps take chunks of at most 8 items of one level (four lanes per item), in level order (the
-// backward pass in reverse level order), from an atomic counter; an item
-// runs as soon as the flags of the items it reads carry this pass's epoch
-// (acquire loads, polled by the whole warp with a bounded number of idle
-// rounds), and publishes its own flag with a release store after writing its
-// results.  Chunks are handed out in increasing order and an item only waits
-// for items handed out earlier, whose warps are already running, so the
-// oldest unfinished item can always proceed: no grid barrier and no
-// co-residency assumption.  Flags hold the epoch of the update that set them
-// (driver pins in the forward pass, gate input pins in the backward pass), so
-// nothing is cleared between updates.  The cell library (tables and per-type
+// warps take chunks of at most 8 items of one level (four lanes per item) in
+// level order (the backward pass in reverse level order) from an atomic
+// counter.  An item runs as soon as the mailbox entries of the items it
+// reads are complete -- polled by the whole warp, with a bounded number of
+// idle rounds -- and publishes its own results to the mailbox of this pass's
+// epoch parity (item.cuh).  Chunks are handed out in increasing order and an
+// item only waits for items handed out earlier, whose warps are already
+// running, so the oldest unfinished item can always proceed: no grid barrier
+// and no co-residency assumption.  The cell library (tables and per-type
 // data) is copied into shared memory once per block.
 #include <algorithm>
 
@@ -23,6 +21,18 @@ namespace sta {
 constexpr int kDfThreads = 256;
 
 static inline size_t df_smem_bytes(int T) { return (size_t)T * 3 * 4 * kLutStride * sizeof(float) + (size_t)T * 5 * sizeof(int); }
+
+// After an aborted pass the mailboxes hold a mix of parities: reset them
+// all to NaN.  (A completed pass leaves the next parity all NaN.)
+__global__ void k_df_recover(const DevCtx c)
+{
+    if (ld_volatile(c.df_state + 3) == 0u) return;
+    const float4 nan4 = make_float4(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff),
+                                    __int_as_float(0x7fffffff), __int_as_float(0x7fffffff));
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.fbox_len; i += stride) c.fbox[i] = nan4;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.rbox_len; i += stride) c.rbox[i] = nan4;
+}
 
 // New epoch, chunk counters at zero, abort cleared.
 __global__ void k_df_begin(const DevCtx c)
@@ -67,10 +77,10 @@ __device__ __forceinline__ int next_chunk(const DevCtx &c, int counter, int n_ch
 }
 
 // The warp's polling loop.  Every pending item of the chunk probes its
-// inputs' flags without blocking; items whose inputs are all published run
-// at once, so one late input holds back only its own item.  A warp gives up
-// after c.spin_limit idle rounds (timeout bit + abort word), or as soon as
-// another warp has aborted.
+// inputs' mailbox entries without blocking; items whose inputs are complete
+// run at once, so one late input holds back only its own item.  A warp
+// gives up after c.spin_limit idle rounds (timeout bit + abort word), or as
+// soon as another warp has aborted.
 __device__ __forceinline__ bool warp_idle_round(const DevCtx &c, long long &spins)
 {
     if (++spins >= c.spin_limit) {
@@ -90,7 +100,7 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
 {
     extern __shared__ float smem[];
     const SmemLib L = stage_library(c, smem);
-    const unsigned epoch = ld_volatile(c.df_state);
+    const int par = (int)(ld_volatile(c.df_state) & 1u);
     const int lane = threadIdx.x & 31, q = lane & 3;
     for (;;) {
         const int ch = next_chunk(c, 1, c.n_fwd_chunks);
@@ -107,10 +117,14 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
             if (pending) {
-                const bool ready = quad_all(is_item ? fwd_probe(c, f, epoch) : ep_probe(c, e, epoch));
-                if (ready) {
-                    if (is_item) fwd_run<SMOOTH, UNIFORM, true>(c, L.lut, f, x, q, epoch);
-                    else ep_run<true>(c, e, x - c.I, q);
+                FwdIn in;
+                if (is_item) {
+                    if (quad_all(fwd_probe(c, f, par, in))) {
+                        fwd_run<SMOOTH, UNIFORM, true>(c, L.lut, f, in, x, q, par);
+                        pending = false;
+                    }
+                } else if (quad_all(ep_probe(c, e, par, in.at[0], in.sl[0]))) {
+                    ep_run<true>(c, e, in.at[0], in.sl[0], x - c.I, q, par);
                     pending = false;
                 }
             }
@@ -124,7 +138,7 @@ __global__ void __launch_bounds__(kDfThreads) k_df_backward(const DevCtx c)
 {
     extern __shared__ float smem[];
     const SmemLib L = stage_library(c, smem);
-    const unsigned epoch = ld_volatile(c.df_state);
+    const int par = (int)(ld_volatile(c.df_state) & 1u);
     const int lane = threadIdx.x & 31, q = lane & 3;
     for (;;) {
         const int ch = next_chunk(c, 2, c.n_bwd_chunks);
@@ -135,8 +149,8 @@ __global__ void __launch_bounds__(kDfThreads) k_df_backward(const DevCtx c)
         if (pending) b = bwd_prep(c, L.nin, L.kind, x);
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
-            if (pending && quad_all(bwd_probe(c, b, epoch))) {
-                bwd_run<UNIFORM, true>(c, L.lut, L.sense, b, q, epoch);
+            if (pending && quad_all(bwd_probe(c, b, par))) {
+                bwd_run<UNIFORM, true>(c, L.lut, L.sense, b, q, par);
                 pending = false;
             }
             if (__any_sync(0xffffffffu, pending) && !warp_idle_round(c, spins)) break;
@@ -181,6 +195,7 @@ void launch_dataflow_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, 
 {
     const size_t smem = df_smem_bytes(h.T);
     if (ev) cudaEventRecord(ev[0], st);
+    k_df_recover<<<h.df_blocks_fwd > 0 ? h.df_blocks_fwd : 1, kDfThreads, 0, st>>>(c);
     k_df_begin<<<1, 32, 0, st>>>(c);
     if (h.placed) {
         if (c.I > 0) launch_net_star(c, st);

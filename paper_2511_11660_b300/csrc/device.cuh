@@ -45,8 +45,10 @@ struct DevCtx {
     double *red_partial;                        // [n_red_chunks][K][6] scratch
     unsigned *err;
     float *scratch_a, *scratch_b;               // RC sweeps of nets larger than a tile
-    // dataflow schedule
-    unsigned *flag;                             // [P] ready epoch per pin (drivers: forward, gate inputs: backward)
+    // dataflow schedule: mailboxes by epoch parity, NaN until published
+    float4 *fbox;                               // [2][P][K][2] arrival, slew of driver pins
+    float4 *rbox;                               // [2][P][K]    required time of gate input pins
+    size_t fbox_len, rbox_len;                  // float4 elements of each
     unsigned *df_state;                         // [0] epoch, [1] forward chunk counter, [2] backward counter, [3] abort
     int32_t ep_begin;                           // first endpoint pin (endpoints are the last E pins)
     int32_t hold_item;                          // test hook: item whose forward flag is never published (-1 none)

@@ -15,10 +15,19 @@
 // serial chain is a quarter of the item and the four lanes write 16
 // contiguous bytes of every float4.
 //
-// WAIT = true reads values produced by other items of the same launch at
-// L2 (the dataflow schedule acquires their ready flags first, see
-// dataflow.cu) and publishes the item's own flags; WAIT = false relies on
-// launch boundaries (level schedule).
+// WAIT = true is the dataflow schedule: values produced by other items of
+// the same launch are taken from the parity mailboxes once they are
+// complete (see below and dataflow.cu) and the item publishes its own
+// results there; WAIT = false relies on launch boundaries (level schedule).
+//
+// Mailboxes.  For epoch parity p, fbox[p] holds each driver pin's arrival
+// and slew and rbox[p] each gate input pin's required time.  Every float is
+// NaN until its producer stores the final value with a relaxed store, and a
+// real result is never NaN, so a reader that sees all the floats it needs
+// non-NaN has the final values: each 32-bit store is single-copy atomic, no
+// fence or flag is needed, and the poll is the data load itself.  While it
+// publishes parity p, a producer resets its own entries of parity p ^ 1 to
+// NaN for the next pass.
 #pragma once
 
 #include "device.cuh"
@@ -117,34 +126,55 @@ __device__ __forceinline__ float lookup(const L &lut, int tq, Seg as, Seg bl, fl
     return interp(lut, tq, seg_slew_t(lut, tq, s), seg_load_t(lut, tq, l));
 }
 
-// ------------------------------------------------------ flags and loads
+// ------------------------------------------------------ mailbox access
 
-__device__ __forceinline__ unsigned ld_acquire(const unsigned *p)
+__device__ __forceinline__ float4 ld_relaxed4(const float4 *p)
 {
-    unsigned v;
-    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    float4 v;
+    asm volatile("ld.relaxed.gpu.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "l"(p)
+                 : "memory");
     return v;
 }
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v)
+__device__ __forceinline__ void st_relaxed(float *p, float v)
 {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+    asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
 __device__ __forceinline__ unsigned ld_volatile(const unsigned *p) { return *(const volatile unsigned *)p; }
+__device__ __forceinline__ bool complete(float4 v) { return v.x == v.x && v.y == v.y && v.z == v.z && v.w == v.w; }
 
-// State written by another item of the same launch is read at L2 (after the
-// acquire that ordered it).
-template <bool WAIT>
-__device__ __forceinline__ float4 ld_state(const float4 *p)
+// mailbox records
+__device__ __forceinline__ float4 *fbox_at(const DevCtx &c, int par, int pin, int k)
 {
-    if (WAIT) return __ldcg(p);
-    return *p;
+    return c.fbox + (((size_t)par * c.P + pin) * c.K + k) * 2;
 }
+__device__ __forceinline__ float4 *rbox_at(const DevCtx &c, int par, int pin, int k)
+{
+    return c.rbox + ((size_t)par * c.P + pin) * c.K + k;
+}
+
+// Lane q publishes component q of pin's arrival and slew for parity par and
+// clears the same component of parity par ^ 1.
+__device__ __forceinline__ void publish_fwd(const DevCtx &c, int par, int pin, int k, int q, float at, float sl)
+{
+    float *n = reinterpret_cast<float *>(fbox_at(c, par, pin, k));
+    float *o = reinterpret_cast<float *>(fbox_at(c, par ^ 1, pin, k));
+    st_relaxed(n + q, at);
+    st_relaxed(n + 4 + q, sl);
+    o[q] = __int_as_float(0x7fffffff);
+    o[4 + q] = __int_as_float(0x7fffffff);
+}
+__device__ __forceinline__ void publish_rat(const DevCtx &c, int par, int pin, int k, int q, float r)
+{
+    st_relaxed(reinterpret_cast<float *>(rbox_at(c, par, pin, k)) + q, r);
+    reinterpret_cast<float *>(rbox_at(c, par ^ 1, pin, k))[q] = __int_as_float(0x7fffffff);
+}
+
 template <bool WAIT>
 __device__ __forceinline__ float ld_comp(const float4 *p, int q)
 {
-    const float *f = reinterpret_cast<const float *>(p) + q;
-    if (WAIT) return __ldcg(f);
-    return *f;
+    return reinterpret_cast<const float *>(p)[q];
 }
 __device__ __forceinline__ void st_comp(float4 *p, int q, float v) { reinterpret_cast<float *>(p)[q] = v; }
 
@@ -159,26 +189,22 @@ __device__ __forceinline__ unsigned quad_mask() { return 0xFu << (threadIdx.x & 
 // every lane of the quad agrees
 __device__ __forceinline__ bool quad_all(bool ok) { return __all_sync(quad_mask(), ok); }
 
-// Publish a ready flag for the quad's writes: the warp barrier orders the
-// four lanes' stores before lane 0's release store, which carries them to
-// any reader that acquires the flag.
-__device__ __forceinline__ void quad_publish(unsigned *f, unsigned epoch, int q)
-{
-    __syncwarp(quad_mask());
-    if (q == 0) st_release(f, epoch);
-}
-
 // ------------------------------------------------------------- forward
 //
 // Each item is processed in three steps: prep (loads that do not depend on
-// this pass's results), probe (are the drivers' results published?  only in
-// the dataflow schedule) and run (the arithmetic, the stores and, in the
-// dataflow schedule, the publication of the item's own flag).
+// this pass's results), probe (are the inputs' results complete?  only in
+// the dataflow schedule; it returns them) and run (the arithmetic, the
+// stores and, in the dataflow schedule, the publication to the mailbox).
 
 struct FwdItem {
     int t, pin0, nin, kind;
     int sense[3], drv[3];
     float Dn0[3], V0[3], ld0;   // corner 0 net values, loaded ahead
+};
+
+// driver arrival and slew of corner 0, as probed
+struct FwdIn {
+    float4 at[3], sl[3];
 };
 
 __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, const int *tkind, const int *tsense,
@@ -203,29 +229,39 @@ __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, co
     return f;
 }
 
-// all drivers of the item published in this pass (acquire)
-__device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, unsigned epoch)
+// Are the drivers' arrivals and slews of every corner complete?  Corner 0's
+// are returned in `in`.
+__device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int par, FwdIn &in)
 {
     bool ok = true;
 #pragma unroll
-    for (int j = 0; j < 3; ++j)
-        if (j < f.nin) ok = (ld_acquire(c.flag + f.drv[j]) == epoch) && ok;
+    for (int j = 0; j < 3; ++j) {
+        if (j < f.nin) {
+            in.at[j] = ld_relaxed4(fbox_at(c, par, f.drv[j], 0));
+            in.sl[j] = ld_relaxed4(fbox_at(c, par, f.drv[j], 0) + 1);
+            ok = ok && complete(in.at[j]) && complete(in.sl[j]);
+            for (int k = 1; k < c.K && ok; ++k)
+                ok = complete(ld_relaxed4(fbox_at(c, par, f.drv[j], k))) &&
+                     complete(ld_relaxed4(fbox_at(c, par, f.drv[j], k) + 1));
+        }
+    }
     return ok;
 }
 
 // Lane q of the quad computes component q = el*2 + rf of the item's states.
 template <bool SMOOTH, bool UNIFORM, bool WAIT, class L>
-__device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const FwdItem &f, int g, int q,
-                                        unsigned epoch)
+__device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const FwdItem &f, const FwdIn &in, int g,
+                                        int q, int par)
 {
     const int K = c.K, t = f.t, pin0 = f.pin0, nin = f.nin;
     const int el = q >> 1, rfo = q & 1;
+    const bool pub = WAIT && g != c.hold_item;
     if (t < 0) {   // primary input
         for (int k = 0; k < K; ++k) {
             st_comp(c.at + (size_t)pin0 * K + k, q, c.pi_at);
             st_comp(c.slew + (size_t)pin0 * K + k, q, c.pi_slew);
+            if (pub) publish_fwd(c, par, pin0, k, q, c.pi_at, c.pi_slew);
         }
-        if (WAIT && g != c.hold_item) quad_publish(c.flag + pin0, epoch, q);
         return;
     }
     if (f.kind == 1) {   // flip-flop: ideal clock at CK, arc CK(rise) -> Q for both edges of Q
@@ -238,11 +274,12 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
             st_comp(c.at + (size_t)ck * K + k, q, 0.f);
             st_comp(c.slew + (size_t)ck * K + k, q, cs);
             const Seg as = seg_slew<UNIFORM>(c, lut, tb, cs), bl = seg_load<UNIFORM>(c, lut, tb, ld);
-            st_comp(c.at + (size_t)qp * K + k, q, sc * lookup<UNIFORM>(lut, tb + rfo * kLutStride, as, bl, cs, ld));
-            st_comp(c.slew + (size_t)qp * K + k, q,
-                    sc * lookup<UNIFORM>(lut, tb + (2 + rfo) * kLutStride, as, bl, cs, ld));
+            const float a = sc * lookup<UNIFORM>(lut, tb + rfo * kLutStride, as, bl, cs, ld);
+            const float sl = sc * lookup<UNIFORM>(lut, tb + (2 + rfo) * kLutStride, as, bl, cs, ld);
+            st_comp(c.at + (size_t)qp * K + k, q, a);
+            st_comp(c.slew + (size_t)qp * K + k, q, sl);
+            if (pub) publish_fwd(c, par, qp, k, q, a, sl);
         }
-        if (WAIT && g != c.hold_item) quad_publish(c.flag + qp, epoch, q);
         return;
     }
     const int z = pin0 + nin;
@@ -254,8 +291,17 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
         for (int j = 0; j < 3; ++j) {
             if (j < nin) {
                 const int a = pin0 + j;
-                const float4 ad = ld_state<WAIT>(c.at + (size_t)f.drv[j] * K + k);
-                const float4 sd = ld_state<WAIT>(c.slew + (size_t)f.drv[j] * K + k);
+                float4 ad, sd;
+                if (!WAIT) {
+                    ad = c.at[(size_t)f.drv[j] * K + k];
+                    sd = c.slew[(size_t)f.drv[j] * K + k];
+                } else if (k == 0) {
+                    ad = in.at[j];
+                    sd = in.sl[j];
+                } else {
+                    ad = ld_relaxed4(fbox_at(c, par, f.drv[j], k));
+                    sd = ld_relaxed4(fbox_at(c, par, f.drv[j], k) + 1);
+                }
                 const float Dn = k ? c.netD[(size_t)a * K + k] : f.Dn0[j];
                 const float V = k ? c.netV[(size_t)a * K + k] : f.V0[j];
                 ain[j][0] = (el ? ad.z : ad.x) + Dn;
@@ -287,10 +333,11 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
                 ms.add(sgn * (sc * sv), c.inv_gamma);
             }
         }
-        st_comp(c.at + (size_t)z * K + k, q, sgn * ma.get(c.gamma));
-        st_comp(c.slew + (size_t)z * K + k, q, sgn * ms.get(c.gamma));
+        const float oa = sgn * ma.get(c.gamma), os = sgn * ms.get(c.gamma);
+        st_comp(c.at + (size_t)z * K + k, q, oa);
+        st_comp(c.slew + (size_t)z * K + k, q, os);
+        if (pub) publish_fwd(c, par, z, k, q, oa, os);
     }
-    if (WAIT && g != c.hold_item) quad_publish(c.flag + z, epoch, q);
 }
 
 // ------------------------------------------------------------ endpoints
@@ -312,23 +359,41 @@ __device__ __forceinline__ EpItem ep_prep(const DevCtx &c, int e)
     return x;
 }
 
-__device__ __forceinline__ bool ep_probe(const DevCtx &c, const EpItem &x, unsigned epoch)
+// the driver's arrival and slew of every corner are complete; corner 0's
+// are returned
+__device__ __forceinline__ bool ep_probe(const DevCtx &c, const EpItem &x, int par, float4 &at0, float4 &sl0)
 {
-    return ld_acquire(c.flag + x.d) == epoch;
+    at0 = ld_relaxed4(fbox_at(c, par, x.d, 0));
+    sl0 = ld_relaxed4(fbox_at(c, par, x.d, 0) + 1);
+    bool ok = complete(at0) && complete(sl0);
+    for (int k = 1; k < c.K && ok; ++k)
+        ok = complete(ld_relaxed4(fbox_at(c, par, x.d, k))) && complete(ld_relaxed4(fbox_at(c, par, x.d, k) + 1));
+    return ok;
 }
 
 // Arrival through the net, required times of the ideal clock (D: setup
 // capture edge T - setup, hold 0 + hold; PO: T and 0), pin and endpoint
 // slacks (min over rise/fall) and violation flags.  Lane q: component q.
 template <bool WAIT>
-__device__ __forceinline__ void ep_run(const DevCtx &c, const EpItem &x, int e, int q)
+__device__ __forceinline__ void ep_run(const DevCtx &c, const EpItem &x, float4 at0, float4 sl0, int e, int q,
+                                       int par)
 {
     const int K = c.K, p = x.p, d = x.d;
     const float req = q >= 2 ? (x.isD ? c.period - c.setup : c.period) : (x.isD ? c.hold : 0.f);
     const unsigned m = quad_mask();
     const int base = threadIdx.x & 28;   // first lane of the quad
     for (int k = 0; k < K; ++k) {
-        const float ad = ld_comp<WAIT>(c.at + (size_t)d * K + k, q), sd = ld_comp<WAIT>(c.slew + (size_t)d * K + k, q);
+        float ad, sd;
+        if (!WAIT) {
+            ad = reinterpret_cast<const float *>(c.at + (size_t)d * K + k)[q];
+            sd = reinterpret_cast<const float *>(c.slew + (size_t)d * K + k)[q];
+        } else if (k == 0) {
+            ad = comp(at0, q);
+            sd = comp(sl0, q);
+        } else {
+            ad = comp(ld_relaxed4(fbox_at(c, par, d, k)), q);
+            sd = comp(ld_relaxed4(fbox_at(c, par, d, k) + 1), q);
+        }
         const float Dn = k ? c.netD[(size_t)p * K + k] : x.Dn0, V = k ? c.netV[(size_t)p * K + k] : x.V0;
         const float A = ad + Dn;
         st_comp(c.at + (size_t)p * K + k, q, A);
@@ -368,21 +433,22 @@ __device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, co
     return b;
 }
 
-// every gate-input sink of the item's net has its required time (acquire);
-// endpoint sinks were set by the forward pass
-__device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, unsigned epoch)
+// every gate-input sink of the item's net has its required times (all
+// corners); endpoint sinks were set by the forward pass
+__device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int par)
 {
     bool ok = true;
-    for (int p = b.f0; p < b.f1; ++p) {
+    for (int p = b.f0; p < b.f1 && ok; ++p) {
         const int s = c.fo_pin[p];
-        if (s < c.ep_begin) ok = (ld_acquire(c.flag + s) == epoch) && ok;
+        if (s < c.ep_begin)
+            for (int k = 0; k < c.K && ok; ++k) ok = complete(ld_relaxed4(rbox_at(c, par, s, k)));
     }
     return ok;
 }
 
 template <bool UNIFORM, bool WAIT, class L>
 __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int *tsense, const BwdItem &b, int q,
-                                        unsigned epoch)
+                                        int par)
 {
     const int t = b.t, pin0 = b.pin0, z = b.z, K = c.K;
     const int el = q >> 1, rfi = q & 1;
@@ -393,7 +459,9 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
         float R = el ? INFINITY : -INFINITY;
         for (int p = b.f0; p < b.f1; ++p) {
             const int s = c.fo_pin[p];
-            const float r = ld_comp<WAIT>(c.rat + (size_t)s * K + k, q) - c.netD[(size_t)s * K + k];
+            const float rs = (WAIT && s < c.ep_begin) ? comp(ld_relaxed4(rbox_at(c, par, s, k)), q)
+                                                      : reinterpret_cast<const float *>(c.rat + (size_t)s * K + k)[q];
+            const float r = rs - c.netD[(size_t)s * K + k];
             R = el ? fminf(R, r) : fmaxf(R, r);
         }
         st_comp(c.rat + (size_t)z * K + k, q, R);
@@ -436,12 +504,8 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
             st_comp(c.rat + (size_t)a * K + k, q, acc);
             const float Aa = reinterpret_cast<const float *>(c.at + (size_t)a * K + k)[q];
             st_comp(c.slack + (size_t)a * K + k, q, el ? acc - Aa : Aa - acc);
+            if (WAIT) publish_rat(c, par, a, k, q, acc);
         }
-    }
-    if (WAIT && b.kind == 0) {
-        __syncwarp(m);
-        if (q == 0)
-            for (int j = 0; j < b.nin; ++j) st_release(c.flag + pin0 + j, epoch);
     }
 }
 

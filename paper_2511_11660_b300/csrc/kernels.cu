@@ -122,7 +122,7 @@ __global__ void k_fwd_level(const DevCtx c, int i0, int i1)
     const int g = i0 + (tid >> 2);
     if (g < i1) {
         const FwdItem f = fwd_prep(c, c.type_nin, c.type_kind, c.arc_sense, g);
-        fwd_run<SMOOTH, UNIFORM, false>(c, LutGlobal{c.lut}, f, g, tid & 3, 0u);
+        fwd_run<SMOOTH, UNIFORM, false>(c, LutGlobal{c.lut}, f, FwdIn{}, g, tid & 3, 0);
     }
 }
 
@@ -130,7 +130,7 @@ __global__ void k_endpoints(const DevCtx c)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int e = tid >> 2;
-    if (e < c.E) ep_run<false>(c, ep_prep(c, e), e, tid & 3);
+    if (e < c.E) ep_run<false>(c, ep_prep(c, e), float4{}, float4{}, e, tid & 3, 0);
 }
 
 template <bool UNIFORM>
@@ -139,7 +139,7 @@ __global__ void k_bwd_level(const DevCtx c, int i0, int i1)
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int g = i0 + (tid >> 2);
     if (g < i1) bwd_run<UNIFORM, false>(c, LutGlobal{c.lut}, c.arc_sense, bwd_prep(c, c.type_nin, c.type_kind, g),
-                                        tid & 3, 0u);
+                                        tid & 3, 0);
 }
 
 // ------------------------------------------------------------- reduction

@@ -221,9 +221,13 @@ sta_status create_from_plan(sta_ctx *c, int device)
         }
     }
     h.T = pl.T;
-    // dataflow schedule: ready flags, epoch state and work chunks
-    d.flag = dev_alloc<unsigned>(c, (size_t)pl.P);
-    CK(cudaMemset(d.flag, 0, std::max<size_t>(1, (size_t)pl.P) * sizeof(unsigned)));
+    // dataflow schedule: parity mailboxes (all NaN), epoch state, work chunks
+    d.fbox_len = 2 * 2 * (size_t)pl.P * pl.K;
+    d.rbox_len = 2 * (size_t)pl.P * pl.K;
+    d.fbox = dev_alloc<float4>(c, d.fbox_len);
+    d.rbox = dev_alloc<float4>(c, d.rbox_len);
+    CK(cudaMemset(d.fbox, 0xFF, std::max<size_t>(1, d.fbox_len) * sizeof(float4)));
+    CK(cudaMemset(d.rbox, 0xFF, std::max<size_t>(1, d.rbox_len) * sizeof(float4)));
     d.df_state = dev_alloc<unsigned>(c, 4);
     CK(cudaMemset(d.df_state, 0, 4 * sizeof(unsigned)));
     d.ep_begin = pl.P - pl.E;
