@@ -1,7 +1,8 @@
 #!/usr/bin/env python
 """Benchmark: timing arcs per second of the full STA pass on one B300.
 
-A step is one ``sta_update_timing`` -- net delay calculation, forward
+A step is one ``sta_update_timing`` (dataflow schedule by default) -- net
+delay calculation, forward
 arrival/slew propagation, endpoint required times, backward required-time
 propagation with pin slacks, and the FP64 WNS/TNS reduction -- over the
 seeded 1M-cell synthetic design (depth 150, RC trees of 2-10 nodes, one
@@ -45,7 +46,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scale", choices=sorted(WORKLOADS))
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--schedule", default="level", choices=["level", "dataflow"])
+    ap.add_argument("--schedule", default="dataflow", choices=["level", "dataflow"])
     ap.add_argument("--no-extras", action="store_true",
                     help="time the update only (no e2e, CPU baseline or clock sampling); for profilers")
     return ap.parse_args()
@@ -247,10 +248,15 @@ def run_ours(a, dist: Dist):
     ph = acc / n_prof
     bm = byte_model(st, K)
     pk, pk_kind = peaks()
-    kern = "k_fwd_level" if ph[1] >= ph[2] else "k_bwd_level"
-    phase_ms = ph[1] if kern == "k_fwd_level" else ph[2]
-    phase_bytes = bm["fwd"] if kern == "k_fwd_level" else bm["bwd"]
-    launches = st["n_levels"]
+    fwd_dominant = ph[1] >= ph[2]
+    if a.schedule == "dataflow":
+        kern = "k_df_forward" if fwd_dominant else "k_df_backward"
+        launches = 1
+    else:
+        kern = "k_fwd_level" if fwd_dominant else "k_bwd_level"
+        launches = st["n_levels"]
+    phase_ms = ph[1] if fwd_dominant else ph[2]
+    phase_bytes = bm["fwd"] if fwd_dominant else bm["bwd"]
     achieved = phase_bytes / (phase_ms * 1e-3) / 1e9
     tr = measured_traffic(kern)
     out["roofline"] = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": pk["hbm_gbs"],
