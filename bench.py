@@ -35,6 +35,7 @@ UNIT = "arcs/s"
 WORKLOADS = {
     "scale": "1M cells, depth 150, RC trees of 2-10 nodes, 1 corner, clock period at the 90th percentile "
              "endpoint requirement (seed 0)",
+    "mid": "200k cells, depth 150, RC trees of 2-10 nodes, 1 corner (profiler-sized; seed 0)",
 }
 
 
@@ -145,17 +146,18 @@ def kernel_source_hash() -> str:
 
 
 def measured_traffic(kernel: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was taken on
-    the current kernel sources (else null)."""
-    p = os.path.join(ROOT, "profiles", "traffic.json")
+    """DRAM bytes per launch from the committed ncu summary (profiles/traffic.txt),
+    if it was taken on the current kernel sources (else null)."""
+    p = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
-        t = json.load(open(p))
-    except (OSError, ValueError):
+        lines = open(p).read().splitlines()
+    except OSError:
         return None
-    e = t.get(kernel)
-    if not e or e.get("source_hash") != kernel_source_hash():
-        return None
-    return e.get("dram_bytes_per_launch")
+    for ln in lines:
+        f = ln.split()
+        if len(f) == 3 and not ln.startswith("#") and f[0] == kernel and f[1] == kernel_source_hash():
+            return float(f[2])
+    return None
 
 
 def peaks():

@@ -315,13 +315,16 @@ def lut_corners():
 
 def workload(name: str, seed: int = 0, **over) -> dict:
     """Named workloads: 'tiny' (2,000 cells, depth 30, RC trees of 2-12
-    nodes), 'scale' (1M cells, depth 150, 2-10 nodes), 'diff' (200k cells
+    nodes), 'scale' (1M cells, depth 150, 2-10 nodes), 'mid' (the same at
+    200k cells, for profiler captures), 'diff' (200k cells
     placed in a 1000 um die, star RC from positions, gamma 0.01 ns) and
     'large' (10M cells, depth 400, placed, 4 corners, 2 drive strengths)."""
     if name == "tiny":
         kw = dict(n_cells=2000, depth=30, rc_nodes=(2, 12))
     elif name == "scale":
         kw = dict(n_cells=1_000_000, depth=150, rc_nodes=(2, 10))
+    elif name == "mid":
+        kw = dict(n_cells=200_000, depth=150, rc_nodes=(2, 10))
     elif name == "diff":
         kw = dict(n_cells=200_000, depth=150, rc_nodes=(2, 10), placed=True, gamma_ns=0.01)
     elif name == "large":
