@@ -56,6 +56,11 @@ struct DevCtx {
     int32_t n_fwd_chunks, n_bwd_chunks;
     const int32_t *fwd_chunk_lo, *fwd_chunk_hi;   // forward work: items by level, then endpoints (index I + e)
     const int32_t *bwd_chunk_lo, *bwd_chunk_hi;   // backward work: items by level, deepest first
+    // differentiable pass (sta_backward)
+    float4 *adj;                                // [P][K] late adjoints: dJ/dAT rise, fall, dJ/dslew rise, fall
+    double *obj;                                // [K][4] max(-s/g), sum exp(-s/g - max), TNS_g, WNS_g; [4K] J
+    double *grad;                               // [C][2] dJ/d(x, y)
+    double w_tns, w_wns;
     // shared table axes (valid when every table has the same ones): slew and
     // load breakpoints and reciprocal segment widths
     float ax1[7], ax2[7], iw1[6], iw2[6];

@@ -1,6 +1,7 @@
 // kernels.h -- host entry points of the device passes.
 #pragma once
 
+#include <algorithm>
 #include <vector>
 
 #include "device.cuh"
@@ -38,6 +39,9 @@ void launch_net_star(const DevCtx &c, cudaStream_t st);
 size_t dataflow_smem_bytes(int T);
 cudaError_t dataflow_prepare(HostSched &h, bool smooth, int requested);
 void launch_dataflow_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev = nullptr);
+
+// Smoothed objective and its reverse sweep to cell positions (adjoint.cu).
+void launch_adjoint(const DevCtx &c, const HostSched &h, cudaStream_t st);
 
 // The two-stage FP64 WNS/TNS reduction.
 void launch_reduce(const DevCtx &c, const HostSched &h, cudaStream_t st);

@@ -761,10 +761,43 @@ sta_status sta_last_timings(sta_ctx *c, float *ms4)
     return STA_OK;
 }
 
-sta_status sta_backward(sta_ctx *c, double, double, double *, double *, double *, sta_mem, void *)
+sta_status sta_backward(sta_ctx *c, double w_tns, double w_wns, double *J_out, double *terms, double *grad_xy,
+                        sta_mem mem, void *stream)
 {
     if (!c) return STA_EINVAL;
-    return fail(c, STA_ESTATE, "differentiable pass not built");
+    if (!c->updated) return fail(c, STA_ESTATE, "sta_backward before sta_update_timing");
+    if (!(c->plan.gamma > 0.f) || !c->plan.placed)
+        return fail(c, STA_ESTATE, "sta_backward needs a differentiable context (gamma_ns > 0, positions)");
+    if (!std::isfinite(w_tns) || !std::isfinite(w_wns)) return fail(c, STA_EINVAL, "weights must be finite");
+    try {
+        CK(cudaSetDevice(c->device));
+        cudaStream_t st = as_stream(stream);
+        DevCtx &d = c->dc;
+        const int K = c->plan.K;
+        if (!d.adj) {
+            d.adj = dev_alloc<float4>(c, (size_t)c->plan.P * K);
+            d.obj = dev_alloc<double>(c, 4 * (size_t)K + 1);
+            d.grad = dev_alloc<double>(c, 2 * (size_t)c->plan.C);
+        }
+        d.w_tns = w_tns;
+        d.w_wns = w_wns;
+        sta::launch_adjoint(d, c->hs, st);
+        CK(cudaGetLastError());
+        const cudaMemcpyKind kind = mem == STA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (J_out) CK(cudaMemcpyAsync(J_out, d.obj + 4 * K, sizeof(double), kind, st));
+        if (terms)
+            CK(cudaMemcpy2DAsync(terms, 2 * sizeof(double), d.obj + 2, 4 * sizeof(double), 2 * sizeof(double), K,
+                                 kind, st));
+        if (grad_xy && c->plan.C > 0)
+            CK(cudaMemcpyAsync(grad_xy, d.grad, 2 * (size_t)c->plan.C * sizeof(double), kind, st));
+        if (mem == STA_HOST) {
+            CK(cudaStreamSynchronize(st));
+            return check_device_error(c);
+        }
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    return STA_OK;
 }
 
 }  // extern "C"

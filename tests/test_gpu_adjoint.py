@@ -1,0 +1,136 @@
+"""GPU differentiable timing: the smoothed objective and its adjoint
+(sta_backward) against the FP64 oracle (orc_objective_grad), whose adjoint is
+itself pinned to central finite differences (tests/test_oracle_pins.py).
+
+Tolerances (the adjoint runs in FP32, its sums in FP64): J within 1e-5
+relative; every gradient component within 1e-3 * max|g*| + 1e-3 * |g*|."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2511_11660_b300 import sta, synth
+from tests._parity import tune_period
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    sta.load()
+
+
+def gpu_grad(d, w=(1.0, 1.0), schedule=sta.SCHED_DATAFLOW):
+    ctx = sta.Context(d)
+    ctx.set_schedule(schedule)
+    ctx.update_timing()
+    J, terms, g = ctx.backward(*w)
+    ctx.close()
+    return J, terms, g
+
+
+def check_grad(g, ref, tol=1e-3):
+    scale = np.abs(ref).max()
+    err = np.abs(g - ref)
+    bad = err > tol * scale + tol * np.abs(ref)
+    assert not bad.any(), "max err %.3g (scale %.3g) at %s" % (err.max(), scale, np.argwhere(bad)[:3].tolist())
+    return float(err.max() / scale)
+
+
+def placed(n, depth, seed, **kw):
+    d = synth.make_design(n, depth, seed=seed, placed=True, gamma_ns=0.01, **kw)
+    d["period_ns"], _ = tune_period(d, min_half_gap=0.0)
+    return d
+
+
+@pytest.mark.parametrize("w", [(1.0, 1.0), (1.0, 0.0), (0.0, 1.0)])
+def test_objective_and_gradient_small(w):
+    d = placed(3000, 20, 3)
+    J, terms, g = gpu_grad(d, w)
+    J0, terms0, g0 = oracle.objective_grad(d, *w)
+    assert J == pytest.approx(J0, rel=1e-5)
+    np.testing.assert_allclose(terms, terms0, rtol=1e-5)
+    check_grad(g, g0)
+
+
+def test_level_and_dataflow_forward_give_the_same_gradient():
+    d = placed(2000, 15, 4)
+    a = gpu_grad(d, schedule=sta.SCHED_DATAFLOW)
+    b = gpu_grad(d, schedule=sta.SCHED_LEVEL)
+    assert a[0] == b[0]
+    np.testing.assert_allclose(a[2], b[2], rtol=1e-9, atol=1e-12 * np.abs(b[2]).max())
+
+
+def test_four_corner_objective_and_gradient():
+    ls, rs = synth.lut_corners()
+    d = placed(2000, 15, 5, n_corners=4, lut_scale=ls, rc_scale=rs)
+    J, terms, g = gpu_grad(d)
+    J0, terms0, g0 = oracle.objective_grad(d)
+    assert J == pytest.approx(J0, rel=1e-5)
+    np.testing.assert_allclose(terms, terms0, rtol=1e-5)
+    check_grad(g, g0)
+
+
+def test_device_outputs_and_autograd():
+    import torch
+    from paper_2511_11660_b300.autograd import smoothed_objective
+    d = placed(1500, 12, 6)
+    ctx = sta.Context(d)
+    ctx.set_schedule(sta.SCHED_DATAFLOW)
+    xy = torch.tensor(d["cell_xy"], dtype=torch.float32, device="cuda", requires_grad=True)
+    J = smoothed_objective(xy, ctx)
+    J.backward()
+    J0, _, g0 = oracle.objective_grad(d)
+    assert float(J.detach()) == pytest.approx(J0, rel=1e-5)
+    check_grad(xy.grad.double().cpu().numpy().reshape(-1, 2), g0)
+    ctx.close()
+
+
+def test_backward_state_errors():
+    d = synth.make_design(300, 5, seed=1)              # RC trees: not differentiable
+    ctx = sta.Context(d)
+    with pytest.raises(sta.StaError) as ei:
+        ctx.backward()
+    assert ei.value.status == sta.ESTATE
+    ctx.close()
+    d = placed(300, 5, 1)
+    ctx = sta.Context(d)
+    with pytest.raises(sta.StaError) as ei:
+        ctx.backward()                                  # before any update
+    assert ei.value.status == sta.ESTATE
+    ctx.close()
+
+
+def test_diff_workload_200k_against_oracle_and_differences():
+    """The 200k-cell placed workload (star RC, gamma 0.01 ns): J and every
+    gradient component against the FP64 oracle, and central differences
+    (h = 1e-3 um) of the oracle's objective on sampled cells against the GPU
+    gradient."""
+    d = synth.workload("diff", seed=0)
+    d["period_ns"], _ = tune_period(d, min_half_gap=0.0)
+    J, terms, g = gpu_grad(d)
+    J0, terms0, g0 = oracle.objective_grad(d)
+    assert J == pytest.approx(J0, rel=1e-5)
+    rel = check_grad(g, g0)
+    rng = np.random.default_rng(0)
+    big = np.argsort(-np.abs(g0).max(1))[:200]
+    cells = rng.choice(big, 6, replace=False)
+    h = 1e-3
+    scale = np.abs(g0).max()
+    for cidx in cells:
+        for ax in (0, 1):
+            xy = d["cell_xy"].astype(np.float64)
+            vals = []
+            for sgn in (1, -1):
+                dd = dict(d)
+                x2 = xy.copy()
+                x2[2 * cidx + ax] += sgn * h
+                dd["cell_xy"] = x2.astype(np.float32)
+                vals.append(oracle.objective(dd))
+            v0 = float(d["cell_xy"][2 * cidx + ax])
+            step = float(np.float32(v0 + h)) - float(np.float32(v0 - h))
+            fd = (vals[0] - vals[1]) / step
+            assert abs(fd - g[cidx, ax]) <= 1e-3 * scale + 1e-2 * abs(fd), (cidx, ax, fd, g[cidx, ax])
+    print("200k gradient: max error / max|g| = %.2e" % rel)
