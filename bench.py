@@ -49,7 +49,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--schedule", default="dataflow", choices=["level", "dataflow"])
     ap.add_argument("--no-extras", action="store_true",
-                    help="time the update only (no e2e, CPU baseline or clock sampling); for profilers")
+                    help="time the update only (no e2e, CPU baseline, batch, gradient or clock sampling); for profilers")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
+    ap.add_argument("--no-grad", action="store_true", help="skip the gradient timing")
     return ap.parse_args()
 
 
@@ -298,6 +300,13 @@ def run_ours(a, dist: Dist):
                   "what": "sta_set_rc from pinned host R/C + sta_update_timing + endpoint slacks and "
                           "violation flags to host + sta_report_slack"}
 
+    del ctx
+    torch.cuda.empty_cache()
+    if not a.no_grad:
+        out["grad"] = run_grad(a, dev)
+    if not a.no_batch:
+        out["batched"] = run_batched(a, dev)
+
     # ---- the FP64 oracle on the host cores (rank 0, one GPU only)
     if dist.rank == 0 and dist.world == 1:
         out["cpu_baseline"] = cpu_baseline(d, T, budget_s=12.0)
@@ -305,6 +314,83 @@ def run_ours(a, dist: Dist):
         out["clocks"] = clocks
     if dist.rank == 0:
         print(json.dumps(out))
+
+
+def _events_ms(fn, n: int) -> float:
+    import torch
+    st = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(n):
+        fn()
+    e1.record(st)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / n
+
+
+def run_grad(a, dev: int) -> dict:
+    """ms per gradient iteration = sta_set_positions (device) + sta_update_timing
+    + sta_backward (device outputs), on placed designs with gamma = 0.01 ns."""
+    import torch
+    from paper_2511_11660_b300 import clock, sta, synth
+    res = {}
+    for name, d in (("diff_200k", synth.workload("diff", seed=a.seed)),
+                    ("placed_1M", synth.make_design(1_000_000, 150, seed=a.seed, rc_nodes=(2, 10), placed=True,
+                                                    gamma_ns=0.01))):
+        ctx = sta.Context(d, device=dev)
+        ctx.set_schedule(sta.SCHED_DATAFLOW, 0)
+        ctx.set_clock(0.0)
+        ctx.update_timing()
+        s0, _, _, _ = ctx.get_endpoint_slack()
+        ctx.set_clock(clock.period_in_gap(-s0[:, 0], min_half_gap=0.0)[0])
+        xy = torch.tensor(np.asarray(d["cell_xy"], np.float32), device="cuda")
+        grad = torch.empty((d["n_cells"], 2), dtype=torch.float64, device="cuda")
+
+        def it():
+            ctx.set_positions(xy)
+            ctx.update_timing()
+            ctx.backward(1.0, 1.0, grad_out=grad)
+        for _ in range(3):
+            it()
+        ms = _events_ms(it, 10)
+        res[name] = {"ms_per_iter": ms, "cells": d["n_cells"], "pins": d["n_pins"],
+                     "what": "set_positions + update_timing (dataflow) + sta_backward, all on the device"}
+        ctx.close()
+    return res
+
+
+def run_batched(a, dev: int) -> dict:
+    """One batched context (64 designs, cells log-uniform in 5k-500k, depth
+    150, 4 corners) against 256 sequential plain passes (one design, one
+    corner each), device time."""
+    from paper_2511_11660_b300 import sta, synth
+    ds = synth.batch_workload(seed=a.seed)
+    arcs = sum(synth.design_stats(d)["arcs"] for d in ds)
+    K = ds[0]["n_corners"]
+    b = sta.Context(None, batch=ds, device=dev)
+    b.set_schedule(sta.SCHED_DATAFLOW, 0)
+    for _ in range(3):
+        b.update_timing()
+    ms_batch = _events_ms(b.update_timing, 10)
+    b.close()
+    del b
+    ls, rs = synth.lut_corners()
+    ms_plain = 0.0
+    for d in ds:
+        d1 = dict(d)
+        d1.update(n_corners=1, lut_scale=np.array([ls[0]], np.float32), rc_scale=np.array([rs[0]], np.float32))
+        c = sta.Context(d1, device=dev)
+        c.set_schedule(sta.SCHED_DATAFLOW, 0)
+        for k in range(K):
+            c.set_corners([ls[k]], [rs[k]])
+            c.update_timing()
+            ms_plain += _events_ms(c.update_timing, 3)
+        c.close()
+    return {"designs": len(ds), "corners": K, "cells": int(sum(d["n_cells"] for d in ds)), "arcs": int(arcs),
+            "batched_ms_per_pass": ms_batch, "plain_ms_256_passes": ms_plain,
+            "batched_arcs_corners_per_s": arcs * K / (ms_batch * 1e-3),
+            "plain_arcs_corners_per_s": arcs * K / (ms_plain * 1e-3), "speedup": ms_plain / ms_batch}
 
 
 def cpu_baseline(d: dict, T: float, budget_s: float) -> dict:

@@ -207,6 +207,10 @@ sta_status sta_set_positions(sta_ctx *ctx, const float *cell_xy, sta_mem mem, vo
  * have the same number of inputs and the same kind as the old one. */
 sta_status sta_set_cell_types(sta_ctx *ctx, const int32_t *cell_type);
 
+/* Replace the corner scale factors (n_corners host floats each; see
+ * sta_design_desc).  Takes effect at the next sta_update_timing. */
+sta_status sta_set_corners(sta_ctx *ctx, const float *lut_scale, const float *rc_scale);
+
 /* Change the ideal clock period (ns) used by the next sta_update_timing. */
 sta_status sta_set_clock(sta_ctx *ctx, float period_ns);
 

@@ -450,6 +450,25 @@ void sta_destroy(sta_ctx *c)
 
 const char *sta_last_error(const sta_ctx *c) { return c ? c->msg.c_str() : "NULL context"; }
 
+sta_status sta_set_corners(sta_ctx *c, const float *lut_scale, const float *rc_scale)
+{
+    if (!c || !lut_scale || !rc_scale) return STA_EINVAL;
+    const int K = c->plan.K;
+    for (int k = 0; k < K; ++k)
+        if (!std::isfinite(lut_scale[k]) || !(lut_scale[k] > 0) || !std::isfinite(rc_scale[k]) || !(rc_scale[k] > 0))
+            return fail(c, STA_EINVAL, "corner scales must be finite and > 0");
+    try {
+        CK(cudaSetDevice(c->device));
+        CK(cudaMemcpy(const_cast<float *>(c->dc.lut_scale), lut_scale, K * sizeof(float), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(const_cast<float *>(c->dc.rc_scale), rc_scale, K * sizeof(float), cudaMemcpyHostToDevice));
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    c->plan.lut_scale.assign(lut_scale, lut_scale + K);
+    c->plan.rc_scale.assign(rc_scale, rc_scale + K);
+    return STA_OK;
+}
+
 sta_status sta_set_clock(sta_ctx *c, float period_ns)
 {
     if (!c) return STA_EINVAL;

@@ -85,6 +85,7 @@ SIGNATURES = {
     "sta_set_positions": (C.c_int, [_V, _P, C.c_int, _V]),
     "sta_set_cell_types": (C.c_int, [_V, _P]),
     "sta_set_clock": (C.c_int, [_V, C.c_float]),
+    "sta_set_corners": (C.c_int, [_V, _P, _P]),
     "sta_set_schedule": (C.c_int, [_V, C.c_int32, C.c_int32]),
     "sta_set_wait_limit": (C.c_int, [_V, C.c_int64]),
     "sta_debug_hold_cell": (C.c_int, [_V, C.c_int32]),
@@ -260,6 +261,12 @@ class Context:
 
     def debug_hold_cell(self, cell: int):
         self._chk(self.lib.sta_debug_hold_cell(self.h, int(cell)))
+
+    def set_corners(self, lut_scale, rc_scale):
+        a = np.ascontiguousarray(lut_scale, np.float32)
+        b = np.ascontiguousarray(rc_scale, np.float32)
+        assert len(a) == self.K and len(b) == self.K
+        self._chk(self.lib.sta_set_corners(self.h, _ptr(a), _ptr(b)))
 
     def set_clock(self, period_ns: float):
         self._chk(self.lib.sta_set_clock(self.h, float(period_ns)))

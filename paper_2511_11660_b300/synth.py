@@ -337,6 +337,19 @@ def workload(name: str, seed: int = 0, **over) -> dict:
     return make_design(seed=seed, **kw)
 
 
+def batch_workload(seed: int = 0, n_designs: int = 64, lo: int = 5_000, hi: int = 500_000, depth: int = 150,
+                   n_corners: int = 4, period_ns: float = 11.0) -> list:
+    """Independent designs with cell counts log-uniform in [lo, hi], all on
+    one library, with the four corners of ``lut_corners`` and one clock."""
+    rng = np.random.default_rng(seed)
+    sizes = np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_designs)).astype(np.int64)
+    lib = make_library(seed)
+    ls, rs = lut_corners()
+    ls, rs = ls[:n_corners], rs[:n_corners]
+    return [make_design(int(n), depth, seed=seed * 1000 + i + 1, lib=lib, rc_nodes=(2, 10), n_corners=n_corners,
+                        lut_scale=ls, rc_scale=rs, period_ns=period_ns) for i, n in enumerate(sizes)]
+
+
 class Builder:
     """Hand-built netlists for small exact cases.
 
