@@ -25,6 +25,8 @@ namespace sta {
 
 static inline int nblk2(long long n, int t) { return (int)((n + t - 1) / t); }
 
+constexpr int kDfThreadsA = 256;
+
 // smooth min of the two edges' setup margins of endpoint e at corner k (FP64)
 __device__ __forceinline__ double ep_smooth_slack(const DevCtx &c, int e, int k, double y[2])
 {
@@ -165,30 +167,71 @@ __device__ __forceinline__ float2 pos_of(const DevCtx &c, int p)
     return make_float2(c.port_xy[2 * (size_t)q], c.port_xy[2 * (size_t)q + 1]);
 }
 
-// One item of the reverse sweep (one thread per item, all corners).
-template <bool UNIFORM>
-__device__ void adj_item(const DevCtx &c, int g)
+__device__ __forceinline__ float4 *abox_at(const DevCtx &c, int par, int pin, int k)
 {
-    const LutGlobal lut{c.lut};
-    const int t = c.item_type[g];
-    const int pin0 = c.item_pin0[g];
-    const int kind = t >= 0 ? __ldg(c.type_kind + t) : -1;
-    const int nin = kind == 0 ? __ldg(c.type_nin + t) : 0;
-    const int z = t < 0 ? pin0 : (kind == 1 ? pin0 + 1 : pin0 + nin);
-    const int f0 = c.fo_ptr[g], f1 = c.fo_ptr[g + 1];
-    const int K = c.K;
+    return c.abox + ((size_t)par * c.P + pin) * c.K + k;
+}
+
+struct AdjItem {
+    int t, pin0, kind, nin, z, f0, f1;
+};
+
+__device__ __forceinline__ AdjItem adj_prep(const DevCtx &c, const int *tnin, const int *tkind, int g)
+{
+    AdjItem a;
+    a.t = c.item_type[g];
+    a.pin0 = c.item_pin0[g];
+    a.kind = a.t >= 0 ? tkind[a.t] : -1;
+    a.nin = a.kind == 0 ? tnin[a.t] : 0;
+    a.z = a.t < 0 ? a.pin0 : (a.kind == 1 ? a.pin0 + 1 : a.pin0 + a.nin);
+    a.f0 = c.fo_ptr[g];
+    a.f1 = c.fo_ptr[g + 1];
+    return a;
+}
+
+// the adjoints of every gate-input sink of the item's net are complete
+// (endpoint sinks were seeded by an earlier launch)
+__device__ __forceinline__ bool adj_probe(const DevCtx &c, const AdjItem &a, int par)
+{
+    bool ok = true;
+    for (int p = a.f0; p < a.f1 && ok; ++p) {
+        const int s = c.fo_pin[p];
+        if (s < c.ep_begin)
+            for (int k = 0; k < c.K && ok; ++k) ok = complete(ld_relaxed4(abox_at(c, par, s, k)));
+    }
+    return ok;
+}
+
+__device__ __forceinline__ float quad_sum(float v)
+{
+    const unsigned m = quad_mask();
+    v += __shfl_xor_sync(m, v, 1);
+    v += __shfl_xor_sync(m, v, 2);
+    return v;
+}
+
+// One item of the reverse sweep; lane q of the quad differentiates the merge
+// of output edge rf = q >> 1, of the arrivals (q & 1 == 0, delay tables) or
+// of the slews (q & 1 == 1, slew tables); the quad then sums the partials.
+template <bool UNIFORM, bool WAIT, class Lut>
+__device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const int *tsense, const AdjItem &a, int q,
+                                        int par)
+{
+    const int t = a.t, pin0 = a.pin0, z = a.z, K = c.K, nin = a.nin;
     const float ig = c.inv_gamma;
+    const int rfo = q >> 1;
+    const bool slew_lane = (q & 1) != 0;
     const float2 pz = pos_of(c, z);
     const int cz = c.pin_cell[z];
     for (int k = 0; k < K; ++k) {
         const float fk = __ldg(c.rc_scale + k);
         const float r = fk * c.r_per_um, cc = fk * c.c_per_um;
         const float4 Sz = c.slew[(size_t)z * K + k];
-        // gather the sinks' adjoints through the net arcs
+        // gather the sinks' adjoints through the net arcs (every lane)
         float aA[2] = {0.f, 0.f}, aS[2] = {0.f, 0.f};
-        for (int q = f0; q < f1; ++q) {
-            const int s = c.fo_pin[q];
-            const float4 as = c.adj[(size_t)s * K + k];
+        for (int p = a.f0; p < a.f1; ++p) {
+            const int s = c.fo_pin[p];
+            const float4 as = (WAIT && s < c.ep_begin) ? ld_relaxed4(abox_at(c, par, s, k)) : c.adj[(size_t)s * K + k];
             const float4 Ss = c.slew[(size_t)s * K + k];
             aA[0] += as.x;
             aA[1] += as.y;
@@ -197,98 +240,88 @@ __device__ void adj_item(const DevCtx &c, int g)
         }
         // through the output merges and the NLDM lookups
         float aload = 0.f;
+        float aAin[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, aSin[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (t >= 0) {
             const float sc = __ldg(c.lut_scale + k);
             const float ld = c.load[(size_t)z * K + k];
-            if (kind == 1) {
+            const float abar = slew_lane ? aS[rfo] : aA[rfo];
+            if (a.kind == 1) {
                 const float cs = c.slew[(size_t)pin0 * K + k].z;
-                const int tb = tab_off(t, 1, 0);
-                for (int rfo = 0; rfo < 2; ++rfo) {
-                    float dds, ddl, sds, sdl;
-                    const int td = tb + rfo * kLutStride, ts = tb + (2 + rfo) * kLutStride;
-                    interp_d(lut, td, seg_slew<UNIFORM>(c, lut, td, cs), seg_load<UNIFORM>(c, lut, td, ld), dds, ddl);
-                    interp_d(lut, ts, seg_slew<UNIFORM>(c, lut, ts, cs), seg_load<UNIFORM>(c, lut, ts, ld), sds, sdl);
-                    aload += aA[rfo] * sc * ddl + aS[rfo] * sc * sdl;
-                }
+                const int tq = tab_off(t, 1, slew_lane ? 2 + rfo : rfo);
+                float ds, dl;
+                interp_d(lut, tq, seg_slew<UNIFORM>(c, lut, tq, cs), seg_load<UNIFORM>(c, lut, tq, ld), ds, dl);
+                aload = abar * sc * dl;
             } else {
-                float aAin[3][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-                float aSin[3][2] = {{0.f, 0.f}, {0.f, 0.f}, {0.f, 0.f}};
-                float4 Ain[3], Sin[3];
-                int sense[3];
+                float x[6], dds[6], ddl[6];
+#pragma unroll
+                for (int i = 0; i < 6; ++i) {
+                    x[i] = -INFINITY;
+                    dds[i] = ddl[i] = 0.f;
+                }
 #pragma unroll
                 for (int j = 0; j < 3; ++j) {
-                    if (j < nin) {
-                        Ain[j] = c.at[(size_t)(pin0 + j) * K + k];
-                        Sin[j] = c.slew[(size_t)(pin0 + j) * K + k];
-                        sense[j] = __ldg(c.arc_sense + t * 3 + j);
+                    if (j >= nin) continue;
+                    const int se = tsense[t * 3 + j];
+                    const int tq = tab_off(t, j, slew_lane ? 2 + rfo : rfo);
+                    const float4 Ain = c.at[(size_t)(pin0 + j) * K + k];
+                    const float4 Sin = c.slew[(size_t)(pin0 + j) * K + k];
+#pragma unroll
+                    for (int rfi = 0; rfi < 2; ++rfi) {
+                        if (!arc_on(se, rfi, rfo)) continue;
+                        const float s = rfi ? Sin.w : Sin.z;
+                        float ds, dl;
+                        const float v = interp_d(lut, tq, seg_slew<UNIFORM>(c, lut, tq, s),
+                                                 seg_load<UNIFORM>(c, lut, tq, ld), ds, dl);
+                        x[j * 2 + rfi] = slew_lane ? sc * v : (rfi ? Ain.w : Ain.z) + sc * v;
+                        dds[j * 2 + rfi] = ds;
+                        ddl[j * 2 + rfi] = dl;
                     }
                 }
+                // softmax weights of the log-sum-exp merge
+                float m = -INFINITY;
 #pragma unroll
-                for (int rfo = 0; rfo < 2; ++rfo) {
-                    float xa[6], xs[6], dds[6], ddl[6], sds[6], sdl[6];
+                for (int i = 0; i < 6; ++i) m = fmaxf(m, x[i]);
+                float zsum = 0.f;
 #pragma unroll
-                    for (int i = 0; i < 6; ++i) {
-                        xa[i] = xs[i] = -INFINITY;
-                        dds[i] = ddl[i] = sds[i] = sdl[i] = 0.f;
-                    }
+                for (int i = 0; i < 6; ++i) zsum += x[i] > -INFINITY ? expf((x[i] - m) * ig) : 0.f;
 #pragma unroll
-                    for (int j = 0; j < 3; ++j) {
-                        if (j >= nin) continue;
-                        const int tbj = tab_off(t, j, 0);
-#pragma unroll
-                        for (int rfi = 0; rfi < 2; ++rfi) {
-                            const bool on = arc_on(sense[j], rfi, rfo);
-                            const float s = comp(Sin[j], 2 + rfi);
-                            const int td = tbj + rfo * kLutStride, ts = tbj + (2 + rfo) * kLutStride;
-                            float dv = 0.f, sv = 0.f, a = 0.f, b = 0.f, e2 = 0.f, f2 = 0.f;
-                            if (on) {
-                                dv = interp_d(lut, td, seg_slew<UNIFORM>(c, lut, td, s), seg_load<UNIFORM>(c, lut, td, ld), a, b);
-                                sv = interp_d(lut, ts, seg_slew<UNIFORM>(c, lut, ts, s), seg_load<UNIFORM>(c, lut, ts, ld), e2, f2);
-                            }
-                            const int i = j * 2 + rfi;
-                            xa[i] = on ? comp(Ain[j], 2 + rfi) + sc * dv : -INFINITY;
-                            xs[i] = on ? sc * sv : -INFINITY;
-                            dds[i] = a;
-                            ddl[i] = b;
-                            sds[i] = e2;
-                            sdl[i] = f2;
-                        }
-                    }
-                    // softmax weights of the log-sum-exp merges
-                    float ma = -INFINITY, ms = -INFINITY;
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) { ma = fmaxf(ma, xa[i]); ms = fmaxf(ms, xs[i]); }
-                    float za = 0.f, zs = 0.f;
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) {
-                        za += xa[i] > -INFINITY ? expf((xa[i] - ma) * ig) : 0.f;
-                        zs += xs[i] > -INFINITY ? expf((xs[i] - ms) * ig) : 0.f;
-                    }
-#pragma unroll
-                    for (int i = 0; i < 6; ++i) {
-                        if (!(xa[i] > -INFINITY)) continue;
-                        const float wa = expf((xa[i] - ma) * ig) / za, ws = expf((xs[i] - ms) * ig) / zs;
-                        const int j = i >> 1, rfi = i & 1;
-                        aAin[j][rfi] += aA[rfo] * wa;
-                        aSin[j][rfi] += aA[rfo] * wa * sc * dds[i] + aS[rfo] * ws * sc * sds[i];
-                        aload += aA[rfo] * wa * sc * ddl[i] + aS[rfo] * ws * sc * sdl[i];
-                    }
+                for (int i = 0; i < 6; ++i) {
+                    if (!(x[i] > -INFINITY)) continue;
+                    const float w = abar * expf((x[i] - m) * ig) / zsum;
+                    if (!slew_lane) aAin[i] = w;
+                    aSin[i] = w * sc * dds[i];
+                    aload += w * sc * ddl[i];
                 }
-#pragma unroll
-                for (int j = 0; j < 3; ++j)
-                    if (j < nin)
-                        c.adj[(size_t)(pin0 + j) * K + k] = make_float4(aAin[j][0], aAin[j][1], aSin[j][0], aSin[j][1]);
             }
         }
-        // star segments of the item's net: dJ/dL to the cells at both ends
-        for (int q = f0; q < f1; ++q) {
-            const int s = c.fo_pin[q];
-            const float4 as = c.adj[(size_t)s * K + k];
+        aload = quad_sum(aload);
+        if (a.kind == 0) {
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                aAin[i] = quad_sum(aAin[i]);
+                aSin[i] = quad_sum(aSin[i]);
+            }
+            for (int j = 0; j < nin; ++j) {
+                const float v = q == 0 ? aAin[j * 2] : q == 1 ? aAin[j * 2 + 1] : q == 2 ? aSin[j * 2] : aSin[j * 2 + 1];
+                reinterpret_cast<float *>(c.adj + (size_t)(pin0 + j) * K + k)[q] = v;
+                if (WAIT) {
+                    float *n = reinterpret_cast<float *>(abox_at(c, par, pin0 + j, k));
+                    float *o = reinterpret_cast<float *>(abox_at(c, par ^ 1, pin0 + j, k));
+                    st_relaxed(n + q, v);
+                    o[q] = __int_as_float(0x7fffffff);
+                }
+            }
+        }
+        // star segments of the item's net, split over the quad's lanes:
+        // dJ/dL to the cells at both ends
+        for (int p = a.f0 + q; p < a.f1; p += 4) {
+            const int s = c.fo_pin[p];
+            const float4 as = (WAIT && s < c.ep_begin) ? ld_relaxed4(abox_at(c, par, s, k)) : c.adj[(size_t)s * K + k];
             const float4 Ss = c.slew[(size_t)s * K + k];
             const float2 ps = pos_of(c, s);
             const float dx = pz.x - ps.x, dy = pz.y - ps.y;
             const float L = fabsf(dx) + fabsf(dy);
-            const float cp = 1e3f * c.fo_cap[q];
+            const float cp = 1e3f * c.fo_cap[p];
             const double Draw = (double)r * L * (0.5 * cc * L + cp);
             const double dDdL = (double)r * (cc * L + cp);
             const double Dbar = (double)as.x + as.y;
@@ -311,8 +344,77 @@ __device__ void adj_item(const DevCtx &c, int g)
 template <bool UNIFORM>
 __global__ void k_adj_level(const DevCtx c, int i0, int i1)
 {
-    const int g = i0 + blockIdx.x * blockDim.x + threadIdx.x;
-    if (g < i1) adj_item<UNIFORM>(c, g);
+    const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+    const int g = i0 + (tid >> 2);
+    if (g < i1)
+        adj_run<UNIFORM, false>(c, LutGlobal{c.lut}, c.arc_sense, adj_prep(c, c.type_nin, c.type_kind, g), tid & 3, 0);
+}
+
+// ----------------------------------------------------- dataflow adjoint
+
+// After an aborted adjoint pass: reset its mailbox to NaN.
+__global__ void k_adj_recover(const DevCtx c)
+{
+    if (ld_volatile(c.df_state + 6) == 0u) return;
+    const float4 nan4 = make_float4(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff),
+                                    __int_as_float(0x7fffffff), __int_as_float(0x7fffffff));
+    const size_t stride = (size_t)gridDim.x * blockDim.x;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.abox_len; i += stride) c.abox[i] = nan4;
+}
+
+__global__ void k_adj_begin(const DevCtx c)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        c.df_state[4] = c.df_state[4] + 1u;
+        c.df_state[5] = 0u;
+        c.df_state[6] = 0u;
+    }
+}
+
+template <bool UNIFORM>
+__global__ void __launch_bounds__(kDfThreadsA) k_df_adjoint(const DevCtx c)
+{
+    extern __shared__ float smem[];
+    const int nl = c.T * 3 * 4 * kLutStride;
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) smem[i] = __ldg(c.lut + i);
+    int *ti = reinterpret_cast<int *>(smem + nl);
+    for (int i = threadIdx.x; i < c.T; i += blockDim.x) {
+        ti[i] = __ldg(c.type_nin + i);
+        ti[c.T + i] = __ldg(c.type_kind + i);
+    }
+    for (int i = threadIdx.x; i < 3 * c.T; i += blockDim.x) ti[2 * c.T + i] = __ldg(c.arc_sense + i);
+    __syncthreads();
+    const LutShared lut{smem};
+    const int par = (int)(ld_volatile(c.df_state + 4) & 1u);
+    const int lane = threadIdx.x & 31, q = lane & 3;
+    for (;;) {
+        int ch = 0;
+        if (lane == 0) ch = (int)atomicAdd(c.df_state + 5, 1u);
+        ch = __shfl_sync(0xffffffffu, ch, 0);
+        if (ch >= c.n_bwd_chunks || ld_volatile(c.df_state + 6)) break;
+        const int x = c.bwd_chunk_lo[ch] + (lane >> 2);
+        bool pending = x < c.bwd_chunk_hi[ch];
+        AdjItem it{};
+        if (pending) it = adj_prep(c, ti, ti + c.T, x);
+        long long spins = 0;
+        while (__any_sync(0xffffffffu, pending)) {
+            if (pending && quad_all(adj_probe(c, it, par))) {
+                adj_run<UNIFORM, true>(c, lut, ti + 2 * c.T, it, q, par);
+                pending = false;
+            }
+            if (__any_sync(0xffffffffu, pending)) {
+                if (++spins >= c.spin_limit) {
+                    if (lane == 0) {
+                        atomicOr(c.err, kErrTimeout);
+                        atomicExch(c.df_state + 6, 1u);
+                    }
+                    break;
+                }
+                if ((spins & 31) == 0 && __any_sync(0xffffffffu, ld_volatile(c.df_state + 6) != 0u)) break;
+                __nanosleep(32);
+            }
+        }
+    }
 }
 
 void launch_adjoint(const DevCtx &c, const HostSched &h, cudaStream_t st)
@@ -327,12 +429,40 @@ void launch_adjoint(const DevCtx &c, const HostSched &h, cudaStream_t st)
     k_obj_total<<<1, 32, 0, st>>>(c);
     cudaMemsetAsync(c.grad, 0, std::max<size_t>(1, 2 * (size_t)c.C) * sizeof(double), st);
     if (c.E > 0) k_adj_seed<<<nblk2(c.E, 128), 128, 0, st>>>(c);
+    if (h.adj_blocks > 0) {
+        k_adj_recover<<<h.adj_blocks, kDfThreadsA, 0, st>>>(c);
+        k_adj_begin<<<1, 32, 0, st>>>(c);
+        const size_t smem = adjoint_smem_bytes(h.T);
+        if (h.uniform) k_df_adjoint<true><<<h.adj_blocks, kDfThreadsA, smem, st>>>(c);
+        else k_df_adjoint<false><<<h.adj_blocks, kDfThreadsA, smem, st>>>(c);
+        return;
+    }
     for (int s = h.S - 1; s >= 0; --s) {
         const int i0 = h.stage_ptr[s], i1 = h.stage_ptr[s + 1];
         if (i1 <= i0) continue;
-        if (h.uniform) k_adj_level<true><<<nblk2(i1 - i0, 128), 128, 0, st>>>(c, i0, i1);
-        else k_adj_level<false><<<nblk2(i1 - i0, 128), 128, 0, st>>>(c, i0, i1);
+        if (h.uniform) k_adj_level<true><<<nblk2(4LL * (i1 - i0), 128), 128, 0, st>>>(c, i0, i1);
+        else k_adj_level<false><<<nblk2(4LL * (i1 - i0), 128), 128, 0, st>>>(c, i0, i1);
     }
+}
+
+size_t adjoint_smem_bytes(int T) { return (size_t)T * 3 * 4 * kLutStride * sizeof(float) + (size_t)T * 5 * sizeof(int); }
+
+cudaError_t adjoint_prepare(HostSched &h)
+{
+    const size_t smem = adjoint_smem_bytes(h.T);
+    if (smem > 200 * 1024) {   // library too large for the shared copy: level sweep
+        h.adj_blocks = 0;
+        return cudaSuccess;
+    }
+    auto k = h.uniform ? k_df_adjoint<true> : k_df_adjoint<false>;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kDfThreadsA, smem);
+    if (e != cudaSuccess) return e;
+    h.adj_blocks = std::max(1, per_sm) * sms;
+    return cudaSuccess;
 }
 
 }  // namespace sta

@@ -49,7 +49,8 @@ struct DevCtx {
     float4 *fbox;                               // [2][P][K][2] arrival, slew of driver pins
     float4 *rbox;                               // [2][P][K]    required time of gate input pins
     size_t fbox_len, rbox_len;                  // float4 elements of each
-    unsigned *df_state;                         // [0] epoch, [1] forward chunk counter, [2] backward counter, [3] abort
+    unsigned *df_state;                         // [0] epoch, [1] forward chunk counter, [2] backward counter,
+                                                // [3] abort; adjoint: [4] epoch, [5] chunk counter, [6] abort
     int32_t ep_begin;                           // first endpoint pin (endpoints are the last E pins)
     int32_t hold_item;                          // test hook: item whose forward flag is never published (-1 none)
     long long spin_limit;                       // polls before a wait gives up
@@ -58,6 +59,8 @@ struct DevCtx {
     const int32_t *bwd_chunk_lo, *bwd_chunk_hi;   // backward work: items by level, deepest first
     // differentiable pass (sta_backward)
     float4 *adj;                                // [P][K] late adjoints: dJ/dAT rise, fall, dJ/dslew rise, fall
+    float4 *abox;                               // [2][P][K] the same for gate input pins, parity mailbox
+    size_t abox_len;
     double *obj;                                // [K][4] max(-s/g), sum exp(-s/g - max), TNS_g, WNS_g; [4K] J
     double *grad;                               // [C][2] dJ/d(x, y)
     double w_tns, w_wns;

@@ -20,6 +20,7 @@ struct HostSched {
     int T = 0;                        // cell types (shared-memory table size)
     int df_blocks_fwd = 0;            // persistent grids of the dataflow kernels
     int df_blocks_bwd = 0;
+    int adj_blocks = 0;               // persistent grid of the dataflow adjoint (0 = level sweep)
 };
 
 // Net delays, forward levels, endpoints, backward levels, reduction.  With
@@ -40,8 +41,12 @@ size_t dataflow_smem_bytes(int T);
 cudaError_t dataflow_prepare(HostSched &h, bool smooth, int requested);
 void launch_dataflow_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev = nullptr);
 
-// Smoothed objective and its reverse sweep to cell positions (adjoint.cu).
+// Smoothed objective and its reverse sweep to cell positions (adjoint.cu):
+// a persistent dataflow sweep when adjoint_prepare gave it a grid
+// (h.adj_blocks > 0), else one launch per level.
 void launch_adjoint(const DevCtx &c, const HostSched &h, cudaStream_t st);
+size_t adjoint_smem_bytes(int T);
+cudaError_t adjoint_prepare(HostSched &h);
 
 // The two-stage FP64 WNS/TNS reduction.
 void launch_reduce(const DevCtx &c, const HostSched &h, cudaStream_t st);

@@ -134,3 +134,26 @@ def test_diff_workload_200k_against_oracle_and_differences():
             fd = (vals[0] - vals[1]) / step
             assert abs(fd - g[cidx, ax]) <= 1e-3 * scale + 1e-2 * abs(fd), (cidx, ax, fd, g[cidx, ax])
     print("200k gradient: max error / max|g| = %.2e" % rel)
+
+
+def test_large_library_uses_level_sweeps():
+    """A 64-type library does not fit the dataflow kernels' shared-memory copy:
+    the dataflow schedule is refused and the adjoint falls back to one launch
+    per level; results still match the oracle."""
+    lib = synth.make_library(9, strengths=8)
+    d = synth.make_design(1500, 12, seed=9, lib=lib, placed=True, gamma_ns=0.01)
+    rng = np.random.default_rng(1)
+    ct = d["cell_type"].copy()
+    ct += 8 * rng.integers(0, 8, size=len(ct))        # spread cells over the drive strengths
+    d["cell_type"] = ct.astype(np.int32)
+    d["period_ns"], _ = tune_period(d, min_half_gap=0.0)
+    ctx = sta.Context(d)
+    with pytest.raises(sta.StaError) as ei:
+        ctx.set_schedule(sta.SCHED_DATAFLOW)
+    assert ei.value.status == sta.EINVAL
+    ctx.update_timing()
+    J, terms, g = ctx.backward()
+    J0, terms0, g0 = oracle.objective_grad(d)
+    assert J == pytest.approx(J0, rel=1e-5)
+    check_grad(g, g0)
+    ctx.close()
