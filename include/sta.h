@@ -211,8 +211,28 @@ sta_status sta_set_cell_types(sta_ctx *ctx, const int32_t *cell_type);
  * sta_design_desc).  Takes effect at the next sta_update_timing. */
 sta_status sta_set_corners(sta_ctx *ctx, const float *lut_scale, const float *rc_scale);
 
+/* Pick the fastest schedule for this context: times `trials` graph launches
+ * of each candidate (level schedule with 64, 128 and 256 threads per block;
+ * dataflow schedule with a persistent grid from occupancy, one block per SM
+ * and two per SM) on `stream`, keeps the best and selects it.  Choices are
+ * cached per (device, graph shape); a cached choice is reused unless `force`.
+ * Outputs (nullable): the chosen schedule, its parameter and its ms per
+ * update.  Runs full timing updates (the context's results are those of the
+ * last one). */
+sta_status sta_autotune(sta_ctx *ctx, void *stream, int32_t trials, int32_t force, int32_t *schedule,
+                        int32_t *param, float *ms);
+
 /* Change the ideal clock period (ns) used by the next sta_update_timing. */
 sta_status sta_set_clock(sta_ctx *ctx, float period_ns);
+
+/* Resize n cells: cell_type of cells[i] becomes types[i] (both arrays in
+ * `mem`, int32).  Each new type must keep the cell's input count and kind
+ * (checked on the device; a violation sets the device error word, reported
+ * as STA_EINVAL by the next synchronising call, and leaves that cell
+ * unchanged).  Updates the cell's type and the capacitance its input pins
+ * present to their nets, on `stream`, without touching other cells. */
+sta_status sta_resize_cells(sta_ctx *ctx, const int32_t *cells, const int32_t *types, int32_t n, sta_mem mem,
+                            void *stream);
 
 /* Select the propagation schedule (STA_SCHED_*) and its parameter (threads
  * per block for LEVEL; resident blocks per SM for DATAFLOW, 0 = auto). */

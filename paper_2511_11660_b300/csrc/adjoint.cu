@@ -189,15 +189,15 @@ __device__ __forceinline__ AdjItem adj_prep(const DevCtx &c, const int *tnin, co
     return a;
 }
 
-// the adjoints of every gate-input sink of the item's net are complete
-// (endpoint sinks were seeded by an earlier launch)
+// the adjoints of the lane's corners of every gate-input sink of the item's
+// net are complete (endpoint sinks were seeded by an earlier launch)
 __device__ __forceinline__ bool adj_probe(const DevCtx &c, const AdjItem &a, int par)
 {
     bool ok = true;
     for (int p = a.f0; p < a.f1 && ok; ++p) {
         const int s = c.fo_pin[p];
         if (s < c.ep_begin)
-            for (int k = 0; k < c.K && ok; ++k) ok = complete(ld_relaxed4(abox_at(c, par, s, k)));
+            for (int k = corner_lane(c); k < c.K && ok; k += c.KL) ok = complete(ld_relaxed4(abox_at(c, par, s, k)));
     }
     return ok;
 }
@@ -210,22 +210,25 @@ __device__ __forceinline__ float quad_sum(float v)
     return v;
 }
 
-// One item of the reverse sweep; lane q of the quad differentiates the merge
+constexpr int kMaxCornersPerLane = 16;
+
+// One item of the reverse sweep.  Lane q of a quad differentiates the merge
 // of output edge rf = q >> 1, of the arrivals (q & 1 == 0, delay tables) or
-// of the slews (q & 1 == 1, slew tables); the quad then sums the partials.
+// of the slews (q & 1 == 1, slew tables), for the quad's corners; the quad
+// sums the partials.  The segment gradients are summed over corners (and the
+// driver's over all its segments) before the FP64 atomics.
 template <bool UNIFORM, bool WAIT, class Lut>
 __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const int *tsense, const AdjItem &a, int q,
                                         int par)
 {
     const int t = a.t, pin0 = a.pin0, z = a.z, K = c.K, nin = a.nin;
+    const int kq = corner_lane(c), KL = c.KL;
     const float ig = c.inv_gamma;
     const int rfo = q >> 1;
     const bool slew_lane = (q & 1) != 0;
-    const float2 pz = pos_of(c, z);
-    const int cz = c.pin_cell[z];
-    for (int k = 0; k < K; ++k) {
-        const float fk = __ldg(c.rc_scale + k);
-        const float r = fk * c.r_per_um, cc = fk * c.c_per_um;
+    float aload_k[kMaxCornersPerLane];
+    int nk = 0;
+    for (int k = kq; k < K; k += KL, ++nk) {
         const float4 Sz = c.slew[(size_t)z * K + k];
         // gather the sinks' adjoints through the net arcs (every lane)
         float aA[2] = {0.f, 0.f}, aS[2] = {0.f, 0.f};
@@ -294,7 +297,7 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
                 }
             }
         }
-        aload = quad_sum(aload);
+        aload_k[nk] = quad_sum(aload);
         if (a.kind == 0) {
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
@@ -312,32 +315,53 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
                 }
             }
         }
-        // star segments of the item's net, split over the quad's lanes:
-        // dJ/dL to the cells at both ends
-        for (int p = a.f0 + q; p < a.f1; p += 4) {
-            const int s = c.fo_pin[p];
+    }
+    // star segments of the item's net: lane q takes segments q, q + 4, ...;
+    // each lane sums its corners, the KL lanes sharing q sum the rest
+    const float2 pz = pos_of(c, z);
+    const int cz = c.pin_cell[z];
+    const int base = (threadIdx.x & 31) & ~(4 * KL - 1);
+    unsigned mq = 0;
+    for (int j = 0; j < KL; ++j) mq |= 1u << (base + q + 4 * j);
+    double gdx = 0.0, gdy = 0.0;
+    for (int p = a.f0 + q; p < a.f1; p += 4) {
+        const int s = c.fo_pin[p];
+        const float2 ps = pos_of(c, s);
+        const float dx = pz.x - ps.x, dy = pz.y - ps.y;
+        const float L = fabsf(dx) + fabsf(dy);
+        const float cp = 1e3f * c.fo_cap[p];
+        double dJdL = 0.0;
+        int i = 0;
+        for (int k = kq; k < K; k += KL, ++i) {
+            const float fk = __ldg(c.rc_scale + k);
+            const float r = fk * c.r_per_um, cc = fk * c.c_per_um;
             const float4 as = (WAIT && s < c.ep_begin) ? ld_relaxed4(abox_at(c, par, s, k)) : c.adj[(size_t)s * K + k];
             const float4 Ss = c.slew[(size_t)s * K + k];
-            const float2 ps = pos_of(c, s);
-            const float dx = pz.x - ps.x, dy = pz.y - ps.y;
-            const float L = fabsf(dx) + fabsf(dy);
-            const float cp = 1e3f * c.fo_cap[p];
             const double Draw = (double)r * L * (0.5 * cc * L + cp);
             const double dDdL = (double)r * (cc * L + cp);
             const double Dbar = (double)as.x + as.y;
             const double Vbar = (double)as.z / (2.0 * Ss.z) + (double)as.w / (2.0 * Ss.w);
-            const double dJdL = Dbar * 1e-6 * dDdL + Vbar * 1e-12 * 2.0 * Draw * dDdL + (double)aload * 1e-3 * cc;
-            const double gx = dJdL * (double)((dx > 0.f) - (dx < 0.f)), gy = dJdL * (double)((dy > 0.f) - (dy < 0.f));
-            const int cs = c.pin_cell[s];
-            if (cz >= 0) {
-                atomicAdd(c.grad + 2 * (size_t)cz, gx);
-                atomicAdd(c.grad + 2 * (size_t)cz + 1, gy);
-            }
-            if (cs >= 0) {
-                atomicAdd(c.grad + 2 * (size_t)cs, -gx);
-                atomicAdd(c.grad + 2 * (size_t)cs + 1, -gy);
-            }
+            dJdL += Dbar * 1e-6 * dDdL + Vbar * 1e-12 * 2.0 * Draw * dDdL + (double)aload_k[i] * 1e-3 * cc;
         }
+        for (int off = 4; off < 4 * KL; off <<= 1) dJdL += __shfl_xor_sync(mq, dJdL, off);
+        const double gx = dJdL * (double)((dx > 0.f) - (dx < 0.f)), gy = dJdL * (double)((dy > 0.f) - (dy < 0.f));
+        gdx += gx;
+        gdy += gy;
+        const int cs = c.pin_cell[s];
+        if (kq == 0 && cs >= 0) {
+            atomicAdd(c.grad + 2 * (size_t)cs, -gx);
+            atomicAdd(c.grad + 2 * (size_t)cs + 1, -gy);
+        }
+    }
+    // the driver cell: sum over the quad's segments, one atomic pair per item
+    const unsigned m4 = quad_mask();
+    gdx += __shfl_xor_sync(m4, gdx, 1);
+    gdx += __shfl_xor_sync(m4, gdx, 2);
+    gdy += __shfl_xor_sync(m4, gdy, 1);
+    gdy += __shfl_xor_sync(m4, gdy, 2);
+    if (kq == 0 && q == 0 && cz >= 0 && a.f1 > a.f0) {
+        atomicAdd(c.grad + 2 * (size_t)cz, gdx);
+        atomicAdd(c.grad + 2 * (size_t)cz + 1, gdy);
     }
 }
 
@@ -345,7 +369,7 @@ template <bool UNIFORM>
 __global__ void k_adj_level(const DevCtx c, int i0, int i1)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int g = i0 + (tid >> 2);
+    const int g = i0 + tid / (4 * c.KL);
     if (g < i1)
         adj_run<UNIFORM, false>(c, LutGlobal{c.lut}, c.arc_sense, adj_prep(c, c.type_nin, c.type_kind, g), tid & 3, 0);
 }
@@ -392,13 +416,13 @@ __global__ void __launch_bounds__(kDfThreadsA) k_df_adjoint(const DevCtx c)
         if (lane == 0) ch = (int)atomicAdd(c.df_state + 5, 1u);
         ch = __shfl_sync(0xffffffffu, ch, 0);
         if (ch >= c.n_bwd_chunks || ld_volatile(c.df_state + 6)) break;
-        const int x = c.bwd_chunk_lo[ch] + (lane >> 2);
+        const int x = c.bwd_chunk_lo[ch] + lane / (4 * c.KL);
         bool pending = x < c.bwd_chunk_hi[ch];
         AdjItem it{};
         if (pending) it = adj_prep(c, ti, ti + c.T, x);
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
-            if (pending && quad_all(adj_probe(c, it, par))) {
+            if (pending && group_all(c, adj_probe(c, it, par))) {
                 adj_run<UNIFORM, true>(c, lut, ti + 2 * c.T, it, q, par);
                 pending = false;
             }
@@ -440,8 +464,8 @@ void launch_adjoint(const DevCtx &c, const HostSched &h, cudaStream_t st)
     for (int s = h.S - 1; s >= 0; --s) {
         const int i0 = h.stage_ptr[s], i1 = h.stage_ptr[s + 1];
         if (i1 <= i0) continue;
-        if (h.uniform) k_adj_level<true><<<nblk2(4LL * (i1 - i0), 128), 128, 0, st>>>(c, i0, i1);
-        else k_adj_level<false><<<nblk2(4LL * (i1 - i0), 128), 128, 0, st>>>(c, i0, i1);
+        if (h.uniform) k_adj_level<true><<<nblk2(4LL * c.KL * (i1 - i0), 128), 128, 0, st>>>(c, i0, i1);
+        else k_adj_level<false><<<nblk2(4LL * c.KL * (i1 - i0), 128), 128, 0, st>>>(c, i0, i1);
     }
 }
 

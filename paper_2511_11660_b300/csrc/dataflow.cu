@@ -1,7 +1,8 @@
 // dataflow.cu -- persistent dataflow schedule of the timing pass.
 //
 // Instead of one launch per level, each pass is one persistent kernel.  Its
-// warps take chunks of at most 8 items of one level (four lanes per item) in
+// warps take chunks of at most 8 / KL items of one level (4 * KL lanes per
+// item, KL = corners side by side) in
 // level order (the backward pass in reverse level order) from an atomic
 // counter.  An item runs as soon as the mailbox entries of the items it
 // reads are complete -- polled by the whole warp, with a bounded number of
@@ -105,7 +106,7 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
     for (;;) {
         const int ch = next_chunk(c, 1, c.n_fwd_chunks);
         if (ch < 0) break;
-        const int x = c.fwd_chunk_lo[ch] + (lane >> 2);
+        const int x = c.fwd_chunk_lo[ch] + lane / (4 * c.KL);
         bool pending = x < c.fwd_chunk_hi[ch];
         const bool is_item = x < c.I;   // endpoint chunks follow all item chunks
         FwdItem f{};
@@ -119,11 +120,11 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
             if (pending) {
                 FwdIn in;
                 if (is_item) {
-                    if (quad_all(fwd_probe(c, f, par, in))) {
+                    if (group_all(c, fwd_probe(c, f, par, in))) {
                         fwd_run<SMOOTH, UNIFORM, true>(c, L.lut, f, in, x, q, par);
                         pending = false;
                     }
-                } else if (quad_all(ep_probe(c, e, par, in.at[0], in.sl[0]))) {
+                } else if (group_all(c, ep_probe(c, e, par, in.at[0], in.sl[0]))) {
                     ep_run<true>(c, e, in.at[0], in.sl[0], x - c.I, q, par);
                     pending = false;
                 }
@@ -143,13 +144,13 @@ __global__ void __launch_bounds__(kDfThreads) k_df_backward(const DevCtx c)
     for (;;) {
         const int ch = next_chunk(c, 2, c.n_bwd_chunks);
         if (ch < 0) break;
-        const int x = c.bwd_chunk_lo[ch] + (lane >> 2);
+        const int x = c.bwd_chunk_lo[ch] + lane / (4 * c.KL);
         bool pending = x < c.bwd_chunk_hi[ch];
         BwdItem b{};
         if (pending) b = bwd_prep(c, L.nin, L.kind, x);
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
-            if (pending && quad_all(bwd_probe(c, b, par))) {
+            if (pending && group_all(c, bwd_probe(c, b, par))) {
                 bwd_run<UNIFORM, true>(c, L.lut, L.sense, b, q, par);
                 pending = false;
             }

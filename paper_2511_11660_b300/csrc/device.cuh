@@ -18,9 +18,11 @@ constexpr int kRedChunk = 4096;    // endpoints per first-stage reduction block
 // device error word bits (sta_sync maps them to sta_status)
 constexpr unsigned kErrTimeout = 1u;
 constexpr unsigned kErrBounds = 2u;
+constexpr unsigned kErrResize = 4u;
 
 struct DevCtx {
     int32_t P, I, S, E, K, T, C, n_designs;
+    int32_t KL;                                 // quads per item: corners handled side by side (1, 2, 4 or 8)
     float period, clk_slew, pi_at, pi_slew, setup, hold, gamma, inv_gamma;
     float r_per_um, c_per_um;
     const float *lut;          // [T][3][4][80]

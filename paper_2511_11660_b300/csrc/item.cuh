@@ -10,10 +10,11 @@
 // is the min (late) / max (early) over its net sinks of RAT - Elmore delay;
 // each input's is the min/max over its arcs of output RAT - arc delay.
 //
-// Four lanes (a "quad") work on one item: lane q owns state component q =
-// el*2 + rf (early-rise, early-fall, late-rise, late-fall), so a thread's
-// serial chain is a quarter of the item and the four lanes write 16
-// contiguous bytes of every float4.
+// Four lanes (a "quad") work on one item and corner: lane q owns state
+// component q = el*2 + rf (early-rise, early-fall, late-rise, late-fall), so
+// a thread's serial chain is a quarter of the item and the four lanes write
+// 16 contiguous bytes of every float4.  With several corners, KL quads (a
+// power of two, at most 8) share an item, one corner each in turn.
 //
 // WAIT = true is the dataflow schedule: values produced by other items of
 // the same launch are taken from the parity mailboxes once they are
@@ -189,6 +190,18 @@ __device__ __forceinline__ unsigned quad_mask() { return 0xFu << (threadIdx.x & 
 // every lane of the quad agrees
 __device__ __forceinline__ bool quad_all(bool ok) { return __all_sync(quad_mask(), ok); }
 
+// Corners are spread over c.KL quads: an item owns 4 * KL consecutive lanes,
+// and the quad with corner offset kq handles corners kq, kq + KL, ...
+__device__ __forceinline__ int corner_lane(const DevCtx &c) { return (threadIdx.x >> 2) & (c.KL - 1); }
+__device__ __forceinline__ unsigned group_mask(const DevCtx &c)
+{
+    const int w = 4 * c.KL;
+    if (w >= 32) return 0xffffffffu;
+    return ((1u << w) - 1u) << ((threadIdx.x & 31) & ~(w - 1));
+}
+// every lane of the item's group agrees
+__device__ __forceinline__ bool group_all(const DevCtx &c, bool ok) { return __all_sync(group_mask(c), ok); }
+
 // ------------------------------------------------------------- forward
 //
 // Each item is processed in three steps: prep (loads that do not depend on
@@ -199,7 +212,7 @@ __device__ __forceinline__ bool quad_all(bool ok) { return __all_sync(quad_mask(
 struct FwdItem {
     int t, pin0, nin, kind;
     int sense[3], drv[3];
-    float Dn0[3], V0[3], ld0;   // corner 0 net values, loaded ahead
+    float Dn0[3], V0[3], ld0;   // net values of the lane's first corner, loaded ahead
 };
 
 // driver arrival and slew of corner 0, as probed
@@ -215,32 +228,33 @@ __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, co
     f.pin0 = c.item_pin0[g];
     f.kind = f.t >= 0 ? tkind[f.t] : -1;
     f.nin = f.kind == 0 ? tnin[f.t] : 0;
-    const int K = c.K;
+    const int K = c.K, kq = corner_lane(c);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const bool on = j < f.nin;
         f.sense[j] = on ? tsense[f.t * 3 + j] : -1;
         f.drv[j] = on ? c.drv_of[f.pin0 + j] : 0;
-        f.Dn0[j] = on ? c.netD[(size_t)(f.pin0 + j) * K] : 0.f;
-        f.V0[j] = on ? c.netV[(size_t)(f.pin0 + j) * K] : 0.f;
+        f.Dn0[j] = on ? c.netD[(size_t)(f.pin0 + j) * K + kq] : 0.f;
+        f.V0[j] = on ? c.netV[(size_t)(f.pin0 + j) * K + kq] : 0.f;
     }
     const int zl = f.kind == 1 ? f.pin0 + 1 : f.pin0 + f.nin;
-    f.ld0 = f.t >= 0 ? c.load[(size_t)zl * K] : 0.f;
+    f.ld0 = f.t >= 0 ? c.load[(size_t)zl * K + kq] : 0.f;
     return f;
 }
 
-// Are the drivers' arrivals and slews of every corner complete?  Corner 0's
-// are returned in `in`.
+// Are the drivers' arrivals and slews of the lane's corners complete?  Those
+// of its first corner are returned in `in`.
 __device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int par, FwdIn &in)
 {
     bool ok = true;
+    const int kq = corner_lane(c);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         if (j < f.nin) {
-            in.at[j] = ld_relaxed4(fbox_at(c, par, f.drv[j], 0));
-            in.sl[j] = ld_relaxed4(fbox_at(c, par, f.drv[j], 0) + 1);
+            in.at[j] = ld_relaxed4(fbox_at(c, par, f.drv[j], kq));
+            in.sl[j] = ld_relaxed4(fbox_at(c, par, f.drv[j], kq) + 1);
             ok = ok && complete(in.at[j]) && complete(in.sl[j]);
-            for (int k = 1; k < c.K && ok; ++k)
+            for (int k = kq + c.KL; k < c.K && ok; k += c.KL)
                 ok = complete(ld_relaxed4(fbox_at(c, par, f.drv[j], k))) &&
                      complete(ld_relaxed4(fbox_at(c, par, f.drv[j], k) + 1));
         }
@@ -255,9 +269,10 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
 {
     const int K = c.K, t = f.t, pin0 = f.pin0, nin = f.nin;
     const int el = q >> 1, rfo = q & 1;
+    const int kq = corner_lane(c), KL = c.KL;
     const bool pub = WAIT && g != c.hold_item;
     if (t < 0) {   // primary input
-        for (int k = 0; k < K; ++k) {
+        for (int k = kq; k < K; k += KL) {
             st_comp(c.at + (size_t)pin0 * K + k, q, c.pi_at);
             st_comp(c.slew + (size_t)pin0 * K + k, q, c.pi_slew);
             if (pub) publish_fwd(c, par, pin0, k, q, c.pi_at, c.pi_slew);
@@ -268,9 +283,9 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
         const int ck = pin0, qp = pin0 + 1;
         const float cs = c.clk_slew;
         const int tb = tab_off(t, 1, 0);
-        for (int k = 0; k < K; ++k) {
+        for (int k = kq; k < K; k += KL) {
             const float sc = __ldg(c.lut_scale + k);
-            const float ld = k ? c.load[(size_t)qp * K + k] : f.ld0;
+            const float ld = k != kq ? c.load[(size_t)qp * K + k] : f.ld0;
             st_comp(c.at + (size_t)ck * K + k, q, 0.f);
             st_comp(c.slew + (size_t)ck * K + k, q, cs);
             const Seg as = seg_slew<UNIFORM>(c, lut, tb, cs), bl = seg_load<UNIFORM>(c, lut, tb, ld);
@@ -284,7 +299,7 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
     }
     const int z = pin0 + nin;
     const float sgn = el ? 1.f : -1.f;   // early merges are mins: max of the negated candidates
-    for (int k = 0; k < K; ++k) {
+    for (int k = kq; k < K; k += KL) {
         // net arcs into the input pins: this lane needs components el*2 + {0, 1}
         float ain[3][2], sin[3][2];
 #pragma unroll
@@ -295,15 +310,15 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
                 if (!WAIT) {
                     ad = c.at[(size_t)f.drv[j] * K + k];
                     sd = c.slew[(size_t)f.drv[j] * K + k];
-                } else if (k == 0) {
+                } else if (k == kq) {
                     ad = in.at[j];
                     sd = in.sl[j];
                 } else {
                     ad = ld_relaxed4(fbox_at(c, par, f.drv[j], k));
                     sd = ld_relaxed4(fbox_at(c, par, f.drv[j], k) + 1);
                 }
-                const float Dn = k ? c.netD[(size_t)a * K + k] : f.Dn0[j];
-                const float V = k ? c.netV[(size_t)a * K + k] : f.V0[j];
+                const float Dn = k != kq ? c.netD[(size_t)a * K + k] : f.Dn0[j];
+                const float V = k != kq ? c.netV[(size_t)a * K + k] : f.V0[j];
                 ain[j][0] = (el ? ad.z : ad.x) + Dn;
                 ain[j][1] = (el ? ad.w : ad.y) + Dn;
                 const float s0 = el ? sd.z : sd.x, s1 = el ? sd.w : sd.y;
@@ -315,7 +330,7 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
             }
         }
         const float sc = __ldg(c.lut_scale + k);
-        const float ld = k ? c.load[(size_t)z * K + k] : f.ld0;
+        const float ld = k != kq ? c.load[(size_t)z * K + k] : f.ld0;
         const Seg bl = seg_load<UNIFORM>(c, lut, tab_off(t, 0, 0), ld);
         MaxMerge<SMOOTH> ma, ms;
 #pragma unroll
@@ -354,19 +369,20 @@ __device__ __forceinline__ EpItem ep_prep(const DevCtx &c, int e)
     x.p = c.ep_pin[e];
     x.d = c.drv_of[x.p];
     x.isD = c.ep_is_d[e] != 0;
-    x.Dn0 = c.netD[(size_t)x.p * c.K];
-    x.V0 = c.netV[(size_t)x.p * c.K];
+    x.Dn0 = c.netD[(size_t)x.p * c.K + corner_lane(c)];
+    x.V0 = c.netV[(size_t)x.p * c.K + corner_lane(c)];
     return x;
 }
 
-// the driver's arrival and slew of every corner are complete; corner 0's
-// are returned
+// the driver's arrival and slew of the lane's corners are complete; those of
+// its first corner are returned
 __device__ __forceinline__ bool ep_probe(const DevCtx &c, const EpItem &x, int par, float4 &at0, float4 &sl0)
 {
-    at0 = ld_relaxed4(fbox_at(c, par, x.d, 0));
-    sl0 = ld_relaxed4(fbox_at(c, par, x.d, 0) + 1);
+    const int kq = corner_lane(c);
+    at0 = ld_relaxed4(fbox_at(c, par, x.d, kq));
+    sl0 = ld_relaxed4(fbox_at(c, par, x.d, kq) + 1);
     bool ok = complete(at0) && complete(sl0);
-    for (int k = 1; k < c.K && ok; ++k)
+    for (int k = kq + c.KL; k < c.K && ok; k += c.KL)
         ok = complete(ld_relaxed4(fbox_at(c, par, x.d, k))) && complete(ld_relaxed4(fbox_at(c, par, x.d, k) + 1));
     return ok;
 }
@@ -382,19 +398,20 @@ __device__ __forceinline__ void ep_run(const DevCtx &c, const EpItem &x, float4 
     const float req = q >= 2 ? (x.isD ? c.period - c.setup : c.period) : (x.isD ? c.hold : 0.f);
     const unsigned m = quad_mask();
     const int base = threadIdx.x & 28;   // first lane of the quad
-    for (int k = 0; k < K; ++k) {
+    const int kq = corner_lane(c);
+    for (int k = kq; k < K; k += c.KL) {
         float ad, sd;
         if (!WAIT) {
             ad = reinterpret_cast<const float *>(c.at + (size_t)d * K + k)[q];
             sd = reinterpret_cast<const float *>(c.slew + (size_t)d * K + k)[q];
-        } else if (k == 0) {
+        } else if (k == kq) {
             ad = comp(at0, q);
             sd = comp(sl0, q);
         } else {
             ad = comp(ld_relaxed4(fbox_at(c, par, d, k)), q);
             sd = comp(ld_relaxed4(fbox_at(c, par, d, k) + 1), q);
         }
-        const float Dn = k ? c.netD[(size_t)p * K + k] : x.Dn0, V = k ? c.netV[(size_t)p * K + k] : x.V0;
+        const float Dn = k != kq ? c.netD[(size_t)p * K + k] : x.Dn0, V = k != kq ? c.netV[(size_t)p * K + k] : x.V0;
         const float A = ad + Dn;
         st_comp(c.at + (size_t)p * K + k, q, A);
         st_comp(c.slew + (size_t)p * K + k, q, sqrtf(fmaf(sd, sd, V)));
@@ -429,7 +446,7 @@ __device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, co
     b.z = b.t < 0 ? b.pin0 : (b.kind == 1 ? b.pin0 + 1 : b.pin0 + b.nin);
     b.f0 = c.fo_ptr[g];
     b.f1 = c.fo_ptr[g + 1];
-    b.ld0 = b.t >= 0 ? c.load[(size_t)b.z * c.K] : 0.f;
+    b.ld0 = b.t >= 0 ? c.load[(size_t)b.z * c.K + corner_lane(c)] : 0.f;
     return b;
 }
 
@@ -441,7 +458,7 @@ __device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int
     for (int p = b.f0; p < b.f1 && ok; ++p) {
         const int s = c.fo_pin[p];
         if (s < c.ep_begin)
-            for (int k = 0; k < c.K && ok; ++k) ok = complete(ld_relaxed4(rbox_at(c, par, s, k)));
+            for (int k = corner_lane(c); k < c.K && ok; k += c.KL) ok = complete(ld_relaxed4(rbox_at(c, par, s, k)));
     }
     return ok;
 }
@@ -454,7 +471,8 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
     const int el = q >> 1, rfi = q & 1;
     const unsigned m = quad_mask();
     const int base = threadIdx.x & 28;
-    for (int k = 0; k < K; ++k) {
+    const int kq = corner_lane(c);
+    for (int k = kq; k < K; k += c.KL) {
         // required time of the output, component q, over its net sinks
         float R = el ? INFINITY : -INFINITY;
         for (int p = b.f0; p < b.f1; ++p) {
@@ -471,7 +489,7 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
         // the output's required times of both edges at this lane's el
         const float R0 = __shfl_sync(m, R, base + el * 2), R1 = __shfl_sync(m, R, base + el * 2 + 1);
         const float sc = __ldg(c.lut_scale + k);
-        const float ld = k ? c.load[(size_t)z * K + k] : b.ld0;
+        const float ld = k != kq ? c.load[(size_t)z * K + k] : b.ld0;
         if (b.kind == 1) {   // CK: only the rising edge has an arc (to both edges of Q)
             const int ck = pin0;
             const float s = reinterpret_cast<const float *>(c.slew + (size_t)ck * K + k)[el * 2];

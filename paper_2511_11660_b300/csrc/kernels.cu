@@ -119,7 +119,7 @@ template <bool SMOOTH, bool UNIFORM>
 __global__ void k_fwd_level(const DevCtx c, int i0, int i1)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int g = i0 + (tid >> 2);
+    const int g = i0 + tid / (4 * c.KL);
     if (g < i1) {
         const FwdItem f = fwd_prep(c, c.type_nin, c.type_kind, c.arc_sense, g);
         fwd_run<SMOOTH, UNIFORM, false>(c, LutGlobal{c.lut}, f, FwdIn{}, g, tid & 3, 0);
@@ -129,7 +129,7 @@ __global__ void k_fwd_level(const DevCtx c, int i0, int i1)
 __global__ void k_endpoints(const DevCtx c)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int e = tid >> 2;
+    const int e = tid / (4 * c.KL);
     if (e < c.E) ep_run<false>(c, ep_prep(c, e), float4{}, float4{}, e, tid & 3, 0);
 }
 
@@ -137,7 +137,7 @@ template <bool UNIFORM>
 __global__ void k_bwd_level(const DevCtx c, int i0, int i1)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-    const int g = i0 + (tid >> 2);
+    const int g = i0 + tid / (4 * c.KL);
     if (g < i1) bwd_run<UNIFORM, false>(c, LutGlobal{c.lut}, c.arc_sense, bwd_prep(c, c.type_nin, c.type_kind, g),
                                         tid & 3, 0);
 }
@@ -233,6 +233,61 @@ __global__ void k_gather_pins(const float4 *__restrict__ arr, const int32_t *__r
     out[i] = arr[(size_t)gpu_of[p] * K + k];
 }
 
+// Resize cells: new type per cell (same input count and kind), and the pin
+// capacitance of its input pins in the fan-out lists of their nets.
+__global__ void k_resize(const DevCtx c, const int32_t *__restrict__ item_of_cell, const int32_t *__restrict__ fo_of_pin,
+                         const float *__restrict__ type_pin_cap, const int32_t *__restrict__ cells,
+                         const int32_t *__restrict__ types, int n, int32_t *item_type)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int cell = cells[i], t = types[i];
+    if (cell < 0 || cell >= c.C || t < 0 || t >= c.T) {
+        atomicOr(c.err, kErrResize);
+        return;
+    }
+    const int g = item_of_cell[cell];
+    const int old = item_type[g];
+    if (c.type_nin[t] != c.type_nin[old] || c.type_kind[t] != c.type_kind[old]) {
+        atomicOr(c.err, kErrResize);
+        return;
+    }
+    item_type[g] = t;
+    const int pin0 = c.item_pin0[g];
+    if (c.type_kind[t] == 1) return;   // a flip-flop's D pin: see the endpoint entry below
+    for (int s = 0; s < c.type_nin[t]; ++s) {
+        const int q = fo_of_pin[pin0 + s];
+        if (q >= 0) const_cast<float *>(c.fo_cap)[q] = type_pin_cap[t * 4 + s];
+    }
+}
+
+// Flip-flops: the D pin lives in the endpoint region; its fan-out entry is
+// found through the caller pin map.
+__global__ void k_resize_dff(const DevCtx c, const int32_t *__restrict__ item_of_cell,
+                             const int32_t *__restrict__ d_pin_of_cell, const int32_t *__restrict__ fo_of_pin,
+                             const float *__restrict__ type_pin_cap, const int32_t *__restrict__ cells,
+                             const int32_t *__restrict__ types, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int cell = cells[i], t = types[i];
+    if (cell < 0 || cell >= c.C || t < 0 || t >= c.T || c.type_kind[t] != 1) return;
+    const int dp = d_pin_of_cell[cell];
+    if (dp < 0) return;
+    const int q = fo_of_pin[dp];
+    if (q >= 0) const_cast<float *>(c.fo_cap)[q] = type_pin_cap[t * 4];
+}
+
+void launch_resize(const DevCtx &c, const int32_t *item_of_cell, const int32_t *d_pin_of_cell,
+                   const int32_t *fo_of_pin, const float *type_pin_cap, const int32_t *cells, const int32_t *types,
+                   int n, int32_t *item_type, cudaStream_t st)
+{
+    if (n <= 0) return;
+    k_resize<<<nblk(n, 256), 256, 0, st>>>(c, item_of_cell, fo_of_pin, type_pin_cap, cells, types, n, item_type);
+    k_resize_dff<<<nblk(n, 256), 256, 0, st>>>(c, item_of_cell, d_pin_of_cell, fo_of_pin, type_pin_cap, cells,
+                                               types, n);
+}
+
 // dst[r] = src[idx[r]]
 __global__ void k_gather_f32(const float *__restrict__ src, const int32_t *__restrict__ idx, float *dst, int n)
 {
@@ -262,7 +317,7 @@ void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cud
     for (int s = 0; s < h.S; ++s) {
         const int i0 = h.stage_ptr[s], i1 = h.stage_ptr[s + 1];
         if (i1 <= i0) continue;
-        const dim3 grid(nblk(4LL * (i1 - i0), tpb));
+        const dim3 grid(nblk(4LL * c.KL * (i1 - i0), tpb));
         if (c.gamma > 0.f) {
             if (h.uniform) k_fwd_level<true, true><<<grid, tpb, 0, st>>>(c, i0, i1);
             else k_fwd_level<true, false><<<grid, tpb, 0, st>>>(c, i0, i1);
@@ -271,13 +326,13 @@ void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cud
             else k_fwd_level<false, false><<<grid, tpb, 0, st>>>(c, i0, i1);
         }
     }
-    if (c.E > 0) k_endpoints<<<nblk(4LL * c.E, 256), 256, 0, st>>>(c);
+    if (c.E > 0) k_endpoints<<<nblk(4LL * c.KL * c.E, 256), 256, 0, st>>>(c);
     if (ev) cudaEventRecord(ev[2], st);
     for (int s = h.S - 1; s >= 0; --s) {
         const int i0 = h.stage_ptr[s], i1 = h.stage_ptr[s + 1];
         if (i1 <= i0) continue;
-        if (h.uniform) k_bwd_level<true><<<nblk(4LL * (i1 - i0), tpb), tpb, 0, st>>>(c, i0, i1);
-        else k_bwd_level<false><<<nblk(4LL * (i1 - i0), tpb), tpb, 0, st>>>(c, i0, i1);
+        if (h.uniform) k_bwd_level<true><<<nblk(4LL * c.KL * (i1 - i0), tpb), tpb, 0, st>>>(c, i0, i1);
+        else k_bwd_level<false><<<nblk(4LL * c.KL * (i1 - i0), tpb), tpb, 0, st>>>(c, i0, i1);
     }
     if (ev) cudaEventRecord(ev[3], st);
     launch_reduce(c, h, st);

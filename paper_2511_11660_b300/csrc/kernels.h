@@ -51,6 +51,11 @@ cudaError_t adjoint_prepare(HostSched &h);
 // The two-stage FP64 WNS/TNS reduction.
 void launch_reduce(const DevCtx &c, const HostSched &h, cudaStream_t st);
 
+// Device-side resizing (sta_resize_cells).
+void launch_resize(const DevCtx &c, const int32_t *item_of_cell, const int32_t *d_pin_of_cell,
+                   const int32_t *fo_of_pin, const float *type_pin_cap, const int32_t *cells, const int32_t *types,
+                   int n, int32_t *item_type, cudaStream_t st);
+
 void launch_gather_pins(const float4 *arr, const int32_t *gpu_of, float4 *out, int P, int K, cudaStream_t st);
 void launch_gather_f32(const float *src, const int32_t *idx, float *dst, int n, cudaStream_t st);
 

@@ -1,5 +1,8 @@
 // sta_api.cu -- the C ABI of libsta.so (see include/sta.h).
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -23,6 +26,11 @@ struct sta_ctx {
     std::vector<void *> allocs;
     size_t bytes = 0;
     int32_t *d_gpu_of = nullptr;
+    // device-side resizing (allocated at the first sta_resize_cells)
+    int32_t *d_item_of_cell = nullptr, *d_d_pin_of_cell = nullptr, *d_fo_of_pin = nullptr;
+    float *d_type_pin_cap = nullptr;
+    int32_t *d_resize_tmp = nullptr;
+    int32_t resize_cap = 0;
     int32_t *d_rc_src = nullptr;
     float *d_rc_tmp = nullptr;
     float4 *d_gather_tmp = nullptr;
@@ -234,7 +242,9 @@ sta_status create_from_plan(sta_ctx *c, int device)
     d.hold_item = -1;
     d.spin_limit = 1LL << 23;
     {
-        constexpr int32_t kChunkItems = 8;   // a warp works on 8 items, four lanes each
+        // a warp works on 8 / KL items, 4 * KL lanes each (KL corners side by side)
+        d.KL = pl.K >= 8 ? 8 : pl.K >= 4 ? 4 : pl.K >= 2 ? 2 : 1;
+        const int32_t kChunkItems = 8 / d.KL;
         std::vector<int32_t> flo, fhi, blo, bhi;
         for (int32_t s = 0; s < pl.S; ++s)
             for (int32_t g = pl.stage_ptr[s]; g < pl.stage_ptr[s + 1]; g += kChunkItems) {
@@ -293,6 +303,9 @@ sta_status check_device_error(sta_ctx *c)
     if (err) {
         CK(cudaMemset(c->dc.err, 0, sizeof(unsigned)));
         if (err & sta::kErrTimeout) return fail(c, STA_ETIMEOUT, "a device-side wait reached its limit");
+        if (err & sta::kErrResize)
+            return fail(c, STA_EINVAL, "sta_resize_cells: a cell index or type was out of range, or a new type "
+                                       "changes the input count or kind (those cells were left unchanged)");
         return fail(c, STA_ECUDA, "device-side bounds check failed");
     }
     return STA_OK;
@@ -543,6 +556,83 @@ sta_status sta_debug_hold_cell(sta_ctx *c, int32_t cell)
     return STA_OK;
 }
 
+namespace {
+struct TuneKey {
+    int device;
+    int64_t P, I, S, K, T, E;
+    bool uniform, placed, smooth;
+    bool operator<(const TuneKey &o) const
+    {
+        return std::tie(device, P, I, S, K, T, E, uniform, placed, smooth) <
+               std::tie(o.device, o.P, o.I, o.S, o.K, o.T, o.E, o.uniform, o.placed, o.smooth);
+    }
+};
+struct TuneChoice {
+    int schedule, param;
+    float ms;
+};
+std::mutex g_tune_mu;
+std::map<TuneKey, TuneChoice> g_tune_cache;
+}  // namespace
+
+sta_status sta_autotune(sta_ctx *c, void *stream, int32_t trials, int32_t force, int32_t *schedule_out,
+                        int32_t *param_out, float *ms_out)
+{
+    if (!c) return STA_EINVAL;
+    if (trials < 1) trials = 1;
+    const Plan &pl = c->plan;
+    const TuneKey key{c->device, pl.P, pl.I, pl.S, pl.K, pl.T, pl.E, pl.uniform_axes, pl.placed, pl.gamma > 0.f};
+    TuneChoice best{-1, 0, 0.f};
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (!force && it != g_tune_cache.end()) best = it->second;
+    }
+    try {
+        CK(cudaSetDevice(c->device));
+        cudaStream_t st = as_stream(stream);
+        if (best.schedule < 0) {
+            int sms = 0;
+            CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
+            std::vector<std::pair<int, int>> cand = {{STA_SCHED_LEVEL, 64}, {STA_SCHED_LEVEL, 128},
+                                                     {STA_SCHED_LEVEL, 256}, {STA_SCHED_DATAFLOW, 0},
+                                                     {STA_SCHED_DATAFLOW, sms}, {STA_SCHED_DATAFLOW, 2 * sms}};
+            cudaEvent_t e0, e1;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            for (auto &cs : cand) {
+                if (sta_set_schedule(c, cs.first, cs.second) != STA_OK) continue;   // e.g. library too large
+                CK(cudaSetDevice(c->device));
+                if (sta_update_timing(c, stream) != STA_OK) continue;            // warm-up, captures the graph
+                CK(cudaEventRecord(e0, st));
+                for (int i = 0; i < trials; ++i) sta_update_timing(c, stream);
+                CK(cudaEventRecord(e1, st));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                ms /= trials;
+                if (check_device_error(c) != STA_OK) continue;
+                if (best.schedule < 0 || ms < best.ms) best = TuneChoice{cs.first, cs.second, ms};
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            if (best.schedule < 0) return fail(c, STA_ECUDA, "no schedule could run");
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tune_cache[key] = best;
+        }
+        const sta_status st2 = sta_set_schedule(c, best.schedule, best.param);
+        if (st2 != STA_OK) return st2;
+        const sta_status st3 = sta_update_timing(c, stream);
+        if (st3 != STA_OK) return st3;
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    if (schedule_out) *schedule_out = best.schedule;
+    if (param_out) *param_out = best.param;
+    if (ms_out) *ms_out = best.ms;
+    return STA_OK;
+}
+
 sta_status sta_update_timing(sta_ctx *c, void *stream)
 {
     if (!c) return STA_EINVAL;
@@ -726,6 +816,49 @@ sta_status sta_set_cell_types(sta_ctx *c, const int32_t *cell_type)
         if (pl.F)
             CK(cudaMemcpy(const_cast<float *>(c->dc.fo_cap), pl.fo_cap.data(), pl.fo_cap.size() * 4,
                           cudaMemcpyHostToDevice));
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    return STA_OK;
+}
+
+sta_status sta_resize_cells(sta_ctx *c, const int32_t *cells, const int32_t *types, int32_t n, sta_mem mem,
+                            void *stream)
+{
+    if (!c) return STA_EINVAL;
+    if (n < 0 || (n > 0 && (!cells || !types))) return fail(c, STA_EINVAL, "bad resize arguments");
+    if (n == 0) return STA_OK;
+    Plan &pl = c->plan;
+    try {
+        CK(cudaSetDevice(c->device));
+        cudaStream_t st = as_stream(stream);
+        if (!c->d_item_of_cell) {
+            c->d_item_of_cell = upload(c, pl.item_of_cell);
+            std::vector<int32_t> fo_of_pin(pl.P, -1), dpin(pl.C, -1);
+            for (int64_t q = 0; q < pl.F; ++q) fo_of_pin[pl.fo_pin[q]] = (int32_t)q;
+            for (size_t p = 0; p < c->pin_cell_c.size(); ++p) {
+                const int32_t cc = c->pin_cell_c[p];
+                if (cc >= 0 && c->pin_slot_c[p] == 0 && pl.type_kind[pl.cell_type[cc]] == 1) dpin[cc] = pl.gpu_of[p];
+            }
+            c->d_fo_of_pin = upload(c, fo_of_pin);
+            c->d_d_pin_of_cell = upload(c, dpin);
+            c->d_type_pin_cap = upload(c, pl.type_pin_cap);
+        }
+        const int32_t *dc = cells, *dt = types;
+        if (mem == STA_HOST) {
+            if (n > c->resize_cap) {
+                c->d_resize_tmp = dev_alloc<int32_t>(c, 2 * (size_t)n);
+                c->resize_cap = n;
+            }
+            CK(cudaMemcpyAsync(c->d_resize_tmp, cells, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            CK(cudaMemcpyAsync(c->d_resize_tmp + n, types, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+            dc = c->d_resize_tmp;
+            dt = c->d_resize_tmp + n;
+        }
+        sta::launch_resize(c->dc, c->d_item_of_cell, c->d_d_pin_of_cell, c->d_fo_of_pin, c->d_type_pin_cap, dc, dt,
+                           n, const_cast<int32_t *>(c->dc.item_type), st);
+        CK(cudaGetLastError());
+        if (mem == STA_HOST) CK(cudaStreamSynchronize(st));
     } catch (const CudaFail &f) {
         return from_cuda(c, f);
     }

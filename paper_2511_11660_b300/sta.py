@@ -85,8 +85,10 @@ SIGNATURES = {
     "sta_set_positions": (C.c_int, [_V, _P, C.c_int, _V]),
     "sta_set_cell_types": (C.c_int, [_V, _P]),
     "sta_set_clock": (C.c_int, [_V, C.c_float]),
+    "sta_resize_cells": (C.c_int, [_V, _P, _P, C.c_int32, C.c_int, _V]),
     "sta_set_corners": (C.c_int, [_V, _P, _P]),
     "sta_set_schedule": (C.c_int, [_V, C.c_int32, C.c_int32]),
+    "sta_autotune": (C.c_int, [_V, _V, C.c_int32, C.c_int32, _P, _P, _P]),
     "sta_set_wait_limit": (C.c_int, [_V, C.c_int64]),
     "sta_debug_hold_cell": (C.c_int, [_V, C.c_int32]),
     "sta_update_timing": (C.c_int, [_V, _V]),
@@ -256,6 +258,14 @@ class Context:
     def set_schedule(self, schedule: int, param: int = 0):
         self._chk(self.lib.sta_set_schedule(self.h, schedule, param))
 
+    def autotune(self, trials: int = 5, force: bool = False, stream=None):
+        """Time the candidate schedules, select the fastest; returns
+        (schedule, param, ms per update)."""
+        sch, par, ms = C.c_int32(), C.c_int32(), C.c_float()
+        self._chk(self.lib.sta_autotune(self.h, _stream(stream), int(trials), int(force), C.byref(sch),
+                                        C.byref(par), C.byref(ms)))
+        return sch.value, par.value, ms.value
+
     def set_wait_limit(self, polls: int):
         self._chk(self.lib.sta_set_wait_limit(self.h, int(polls)))
 
@@ -291,6 +301,16 @@ class Context:
     def set_cell_types(self, cell_type):
         a = np.ascontiguousarray(cell_type, np.int32)
         self._chk(self.lib.sta_set_cell_types(self.h, _ptr(a)))
+
+    def resize_cells(self, cells, types, stream=None):
+        """Give cells[i] the type types[i] (int32; torch CUDA tensors stay on
+        the device, numpy arrays are copied)."""
+        mem = _mem_of(cells)
+        if mem == HOST:
+            cells = np.ascontiguousarray(cells, np.int32)
+            types = np.ascontiguousarray(types, np.int32)
+        self._chk(self.lib.sta_resize_cells(self.h, _ptr(cells), _ptr(types), int(len(cells)), mem,
+                                            _stream(stream)))
 
     def update_timing(self, stream=None):
         self._chk(self.lib.sta_update_timing(self.h, _stream(stream)))

@@ -2,8 +2,8 @@
 
 The dataflow kernels run the same per-item arithmetic as the level kernels
 (item.cuh), so the two schedules must agree bit for bit; both are also held to
-the FP64 oracle.  The failure-detection test makes a ready flag that nothing
-sets (a test hook withholds one cell's flag), lets the bounded waits run out,
+the FP64 oracle.  The failure-detection test makes a result that nothing
+sets (a test hook withholds one cell's results), lets the bounded waits run out,
 and checks that the host gets STA_ETIMEOUT and that the context still works."""
 import numpy as np
 import pytest
@@ -149,3 +149,18 @@ def test_scale_design_dataflow_full_size():
     same(g, run(d, sta.SCHED_LEVEL))
     ref = oracle.sta(d)
     check_all(d, g, ref, exact_viol=_hold_margin_ok(ref))
+
+
+def test_autotune_selects_a_schedule_and_keeps_results():
+    import time
+    d = synth.make_design(20000, 40, seed=13, period_ns=3.0)
+    ref = oracle.sta(d)
+    ctx = sta.Context(d)
+    sch, par, ms = ctx.autotune(trials=3)
+    assert sch in (sta.SCHED_LEVEL, sta.SCHED_DATAFLOW) and ms > 0
+    assert_close("at", ctx.get_pin_state(sta.AT), ref["at"])
+    assert_close("slack", ctx.get_pin_state(sta.SLACK), ref["slack"])
+    t0 = time.perf_counter()
+    again = ctx.autotune(trials=3)            # cached choice for this shape
+    assert again[:2] == (sch, par) and time.perf_counter() - t0 < 1.0
+    ctx.close()
