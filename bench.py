@@ -36,6 +36,8 @@ WORKLOADS = {
     "scale": "1M cells, depth 150, RC trees of 2-10 nodes, 1 corner, clock period at the 90th percentile "
              "endpoint requirement (seed 0)",
     "mid": "200k cells, depth 150, RC trees of 2-10 nodes, 1 corner (profiler-sized; seed 0)",
+    "batch": "64 designs, cells log-uniform in 5k-500k, depth 150, 4 corners, one batched context against 256 "
+             "sequential plain passes (seed 0)",
     "large": "10M cells, depth 400, placed in a 1000 um die (star RC), 4 corners, 2 drive strengths, "
              "gamma 0.01 ns; 20 iterations of 1% moves + 1% resizes + timing + gradient (seed 0)",
 }
@@ -53,6 +55,8 @@ def parse():
     ap.add_argument("--no-extras", action="store_true",
                     help="time the update only (no e2e, CPU baseline, batch, gradient or clock sampling); for profilers")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
+    ap.add_argument("--batch-designs", type=int, default=64)
+    ap.add_argument("--batch-hi", type=int, default=500_000, help="largest design of the batch (cells)")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient timing")
     return ap.parse_args()
 
@@ -362,12 +366,12 @@ def run_grad(a, dev: int) -> dict:
     return res
 
 
-def run_batched(a, dev: int) -> dict:
+def run_batched(a, dev: int, plain: bool = True) -> dict:
     """One batched context (64 designs, cells log-uniform in 5k-500k, depth
     150, 4 corners) against 256 sequential plain passes (one design, one
     corner each), device time."""
     from paper_2511_11660_b300 import sta, synth
-    ds = synth.batch_workload(seed=a.seed)
+    ds = synth.batch_workload(seed=a.seed, n_designs=a.batch_designs, hi=a.batch_hi)
     arcs = sum(synth.design_stats(d)["arcs"] for d in ds)
     K = ds[0]["n_corners"]
     b = sta.Context(None, batch=ds, device=dev)
@@ -379,7 +383,7 @@ def run_batched(a, dev: int) -> dict:
     del b
     ls, rs = synth.lut_corners()
     ms_plain = 0.0
-    for d in ds:
+    for d in (ds if plain else []):
         d1 = dict(d)
         d1.update(n_corners=1, lut_scale=np.array([ls[0]], np.float32), rc_scale=np.array([rs[0]], np.float32))
         c = sta.Context(d1, device=dev)
@@ -392,7 +396,21 @@ def run_batched(a, dev: int) -> dict:
     return {"designs": len(ds), "corners": K, "cells": int(sum(d["n_cells"] for d in ds)), "arcs": int(arcs),
             "batched_ms_per_pass": ms_batch, "plain_ms_256_passes": ms_plain,
             "batched_arcs_corners_per_s": arcs * K / (ms_batch * 1e-3),
-            "plain_arcs_corners_per_s": arcs * K / (ms_plain * 1e-3), "speedup": ms_plain / ms_batch}
+            "plain_arcs_corners_per_s": arcs * K / (ms_plain * 1e-3) if plain else None,
+            "speedup": ms_plain / ms_batch if plain else None}
+
+
+def run_batch_only(a, dist: Dist):
+    import torch
+    torch.cuda.set_device(dist.local)
+    r = run_batched(a, dist.local, plain=not a.no_extras)
+    v = r["batched_arcs_corners_per_s"]
+    out = {"metric": "arc-corners/s, batched designs x corners in one launch sequence", "value": v,
+           "unit": "arc-corners/s", "n_gpus": 1, "steps": 10, "warmup": 3, "ms_per_step": r["batched_ms_per_pass"],
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": "batch: %d designs, cells log-uniform in 5k-%d, depth 150, 4 corners"
+                                  % (a.batch_designs, a.batch_hi)}, "batched": r}
+    print(json.dumps(out))
 
 
 def cpu_baseline(d: dict, T: float, budget_s: float) -> dict:
@@ -517,6 +535,8 @@ def main():
             run_reference(a, dist)
         elif a.workload == "large":
             run_incremental(a, dist)
+        elif a.workload == "batch":
+            run_batch_only(a, dist)
         else:
             run_ours(a, dist)
     finally:

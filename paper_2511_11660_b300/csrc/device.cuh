@@ -10,7 +10,8 @@
 namespace sta {
 
 constexpr int kLutStride = 80;   // floats per packed table, see plan.cpp
-constexpr int kRcTileNodes = 2048;
+constexpr int kRcTileNodes = 1024;
+constexpr int kRcTileSinks = 1024;
 constexpr int kRcTileNets = 128;
 constexpr int kRedThreads = 256;   // threads of the reduction kernels
 constexpr int kRedChunk = 4096;    // endpoints per first-stage reduction block

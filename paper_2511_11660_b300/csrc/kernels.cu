@@ -17,23 +17,32 @@ static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
 // ------------------------------------------------------------------ nets
 
-// RC trees.  One block per tile of consecutive items whose nodes fit in
-// shared memory (one thread per net); a tile holding a single larger net
-// sweeps it in global scratch instead.  Per corner: Cdown (reverse sweep),
-// Elmore D (forward), M = C*D summed over the subtree (reverse), beta
-// (forward), var = 2*beta - D^2.  Units: Ohm*fF -> 1e-6 ns.
+// RC trees.  One block per tile of consecutive items whose RC nodes and
+// sinks fit in shared memory (one thread per net); a tile holding a single
+// larger net sweeps it in global scratch instead.  Per corner: Cdown
+// (reverse sweep), Elmore D (forward), M = C*D summed over the subtree
+// (reverse), beta (forward), var = 2*beta - D^2.  Units: Ohm*fF -> 1e-6 ns.
 __global__ void __launch_bounds__(kRcTileNets) k_net_tree(const DevCtx c)
 {
-    __shared__ int32_t s_par[kRcTileNodes];
+    __shared__ int16_t s_par[kRcTileNodes];
     __shared__ float s_R[kRcTileNodes], s_C[kRcTileNodes], s_A[kRcTileNodes], s_B[kRcTileNodes];
+    __shared__ int16_t s_fnode[kRcTileSinks];
+    __shared__ float s_fcap[kRcTileSinks];
+    __shared__ int32_t s_fpin[kRcTileSinks];
     const int g0 = c.tile_item[blockIdx.x], g1 = c.tile_item[blockIdx.x + 1];
     const int n0 = c.rc_ptr[g0], nn = c.rc_ptr[g1] - n0;
-    const bool big = nn > kRcTileNodes;
+    const int s0 = c.fo_ptr[g0], ns = c.fo_ptr[g1] - s0;
+    const bool big = nn > kRcTileNodes || ns > kRcTileSinks;
     if (!big) {
         for (int i = threadIdx.x; i < nn; i += blockDim.x) {
-            s_par[i] = c.rc_parent[n0 + i];
+            s_par[i] = (int16_t)c.rc_parent[n0 + i];
             s_R[i] = c.rc_R[n0 + i];
             s_C[i] = c.rc_C[n0 + i];
+        }
+        for (int i = threadIdx.x; i < ns; i += blockDim.x) {
+            s_fnode[i] = (int16_t)c.fo_node[s0 + i];
+            s_fcap[i] = c.fo_cap[s0 + i];
+            s_fpin[i] = c.fo_pin[s0 + i];
         }
     }
     __syncthreads();
@@ -41,31 +50,34 @@ __global__ void __launch_bounds__(kRcTileNets) k_net_tree(const DevCtx c)
     if (g >= g1) return;
     const int b = c.rc_ptr[g] - n0, e = c.rc_ptr[g + 1] - n0;
     if (e == b) return;
-    const int32_t *par = big ? c.rc_parent + n0 : s_par;
-    const float *R = big ? c.rc_R + n0 : s_R;
-    const float *Cw = big ? c.rc_C + n0 : s_C;
+    const int f0 = c.fo_ptr[g] - s0, f1 = c.fo_ptr[g + 1] - s0;
     float *A = big ? c.scratch_a + n0 : s_A;
     float *B = big ? c.scratch_b + n0 : s_B;
+    auto par = [&](int i) -> int { return big ? c.rc_parent[n0 + i] : s_par[i]; };
+    auto Rv = [&](int i) -> float { return big ? c.rc_R[n0 + i] : s_R[i]; };
+    auto Cv = [&](int i) -> float { return big ? c.rc_C[n0 + i] : s_C[i]; };
+    auto fnode = [&](int q) -> int { return big ? c.fo_node[s0 + q] : s_fnode[q]; };
+    auto fcap = [&](int q) -> float { return big ? c.fo_cap[s0 + q] : s_fcap[q]; };
+    auto fpin = [&](int q) -> int { return big ? c.fo_pin[s0 + q] : s_fpin[q]; };
     const int t = c.item_type[g];
     const int z = item_out_pin(c, t, c.item_pin0[g]);
-    const int f0 = c.fo_ptr[g], f1 = c.fo_ptr[g + 1];
     const int K = c.K;
     for (int k = 0; k < K; ++k) {
         const float f = __ldg(c.rc_scale + k);
-        for (int i = b; i < e; ++i) A[i] = f * Cw[i];
-        for (int q = f0; q < f1; ++q) A[b + c.fo_node[q]] += 1e3f * c.fo_cap[q];
+        for (int i = b; i < e; ++i) A[i] = f * Cv(i);
+        for (int q = f0; q < f1; ++q) A[b + fnode(q)] += 1e3f * fcap(q);
         for (int i = b; i < e; ++i) B[i] = A[i];                       // node capacitance
-        for (int i = e - 1; i > b; --i) A[b + par[i]] += A[i];          // Cdown
+        for (int i = e - 1; i > b; --i) A[b + par(i)] += A[i];          // Cdown
         c.load[(size_t)z * K + k] = 1e-3f * A[b];
         A[b] = 0.f;
-        for (int i = b + 1; i < e; ++i) A[i] = A[b + par[i]] + f * R[i] * A[i];   // Elmore D
+        for (int i = b + 1; i < e; ++i) A[i] = A[b + par(i)] + f * Rv(i) * A[i];   // Elmore D
         for (int i = b; i < e; ++i) B[i] *= A[i];                      // C_i D_i
-        for (int i = e - 1; i > b; --i) B[b + par[i]] += B[i];          // M
+        for (int i = e - 1; i > b; --i) B[b + par(i)] += B[i];          // M
         B[b] = 0.f;
-        for (int i = b + 1; i < e; ++i) B[i] = B[b + par[i]] + f * R[i] * B[i];   // beta
+        for (int i = b + 1; i < e; ++i) B[i] = B[b + par(i)] + f * Rv(i) * B[i];   // beta
         for (int q = f0; q < f1; ++q) {
-            const int node = b + c.fo_node[q];
-            const int s = c.fo_pin[q];
+            const int node = b + fnode(q);
+            const int s = fpin(q);
             const float Dn = A[node];
             c.netD[(size_t)s * K + k] = 1e-6f * Dn;
             c.netV[(size_t)s * K + k] = 1e-12f * fmaxf(2.f * B[node] - Dn * Dn, 0.f);

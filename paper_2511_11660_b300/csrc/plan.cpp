@@ -418,13 +418,15 @@ void build(const sta_design_desc *d, Plan &pl)
     if (!pl.placed) {
         int32_t g = 0;
         while (g < I) {
-            int32_t h = g, nodes = 0;
+            int32_t h = g, nodes = 0, sinks = 0;
             while (h < I && h - g < kTileNets) {
                 const int32_t nn = pl.rc_ptr[h + 1] - pl.rc_ptr[h];
-                if (nodes + nn > kTileNodes && h > g) break;
+                const int32_t ns = pl.fo_ptr[h + 1] - pl.fo_ptr[h];
+                if ((nodes + nn > kTileNodes || sinks + ns > kTileSinks) && h > g) break;
                 nodes += nn;
+                sinks += ns;
                 ++h;
-                if (nodes > kTileNodes) { ++pl.n_big_tiles; break; }
+                if (nodes > kTileNodes || sinks > kTileSinks) { ++pl.n_big_tiles; break; }
             }
             pl.tile_item.push_back(h);
             g = h;

@@ -214,3 +214,26 @@ def test_scale_design_sampled_full_size():
     frac = ref["n_viol_setup"][0] / len(ref["endpoints"])
     assert 0.05 < frac < 0.15
     print("1M parity max abs err", {k: v[0] for k, v in errs.items()})
+
+
+@pytest.mark.parametrize("schedule", [sta.SCHED_LEVEL, sta.SCHED_DATAFLOW])
+def test_high_fanout_net(schedule):
+    """One primary input drives 1,500 gates (more sinks than a shared-memory
+    RC tile holds, so its net is swept in global scratch) and a long fan-out
+    list in the backward pass."""
+    lib = synth.make_library(4)
+    b = synth.Builder(lib)
+    a = b.pi()
+    outs = [b.cell("INV", [a]) for _ in range(1500)]
+    z = b.cell("NAND2", [outs[0], outs[1]])
+    b.po(z)
+    for o in outs[2:40]:
+        b.po(o)
+    d = b.design(period_ns=0.4, default_R=2.0, default_C=0.05)
+    ref = oracle.sta(d)
+    ctx = sta.Context(d)
+    ctx.set_schedule(schedule)
+    ctx.update_timing()
+    for k, w in (("at", sta.AT), ("slew", sta.SLEW), ("rat", sta.RAT), ("slack", sta.SLACK)):
+        assert_close(k, ctx.get_pin_state(w), ref[k])
+    ctx.close()
