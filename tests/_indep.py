@@ -166,3 +166,51 @@ def enumerate_paths(d, corner=0, with_slew=False):
         return out
 
     return {p: paths(p) for p in range(d["n_pins"])}
+
+
+def enumerate_suffixes(d, corner=0):
+    """Every path from each pin to an endpoint, for slew-independent cell
+    delays: {pin: [(delay to the endpoint, rf at the pin, endpoint pin)]}.
+    Cell delays are read at the driven net's load (the tables do not depend
+    on slew); net delays are the independent Elmore sums of ``Net``."""
+    net = Net(d, corner)
+    sc = float(np.asarray(d["lut_scale"])[corner])
+    role = np.asarray(d["pin_role"])
+    ctype = np.asarray(d["cell_type"])
+    cpp = np.asarray(d["cell_pin_ptr"])
+    cp = np.asarray(d["cell_pin"])
+    sense = np.asarray(d["arc_sense"]).reshape(-1, 3)
+    nin = np.asarray(d["type_nin"])
+    i1 = np.asarray(d["lut_idx1"]).reshape(-1, 3, 4, 7)
+    i2 = np.asarray(d["lut_idx2"]).reshape(-1, 3, 4, 7)
+    vv = np.asarray(d["lut_val"]).reshape(-1, 3, 4, 49)
+    sinks_of = {}
+    for s, drv in net.driver.items():
+        sinks_of.setdefault(drv, []).append(s)
+    memo = {}
+
+    def suf(p):
+        if p in memo:
+            return memo[p]
+        r = role[p]
+        out = []
+        if r in (D, PO):
+            out = [(0.0, rf, p) for rf in (0, 1)]
+        elif r in (PI, OUT, Q):
+            for s in sinks_of.get(p, []):
+                out += [(dl + net.Dns[s], rf, e) for dl, rf, e in suf(s)]
+        elif r in (IN, CK):
+            c = net.cell_of[p]
+            t = ctype[c]
+            slot = net.slot_of[p]
+            se = sense[t, slot]
+            z = cp[cpp[c] + nin[t]]
+            l = net.load.get(int(z), 0.0)
+            for dl, rfo, e in suf(int(z)):
+                dc = sc * bilinear(i1[t, slot, rfo], i2[t, slot, rfo], vv[t, slot, rfo], 0.0, l)
+                for rf in rf_in_of(se, rfo):
+                    out.append((dl + dc, rf, e))
+        memo[p] = out
+        return out
+
+    return {p: suf(p) for p in range(d["n_pins"])}

@@ -196,24 +196,62 @@ def test_brute_force_paths_fixed_delay(seed):
     assert checked > 20
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_brute_force_required_times_fixed_delay(seed):
+    """With slew-independent delays, the late required time of a pin is the
+    minimum over every path from it to an endpoint of (endpoint requirement
+    - path delay) and the early one the maximum (setup requirement T - t_setup
+    at a D pin and T at a PO; hold requirement t_hold at a D pin and 0 at a
+    PO); pins with no path to an endpoint have +-inf."""
+    d = _fixed_design(seed)
+    d["period_ns"] = 0.7
+    r = oracle.sta(d)
+    role = np.asarray(d["pin_role"])
+    req_late = {synth.D: d["period_ns"] - d["setup_ns"], synth.PO: d["period_ns"]}
+    req_early = {synth.D: d["hold_ns"], synth.PO: 0.0}
+    checked = 0
+    for p, lst in _indep.enumerate_suffixes(d).items():
+        for rf in (0, 1):
+            late = [req_late[role[e]] - dl for dl, f, e in lst if f == rf]
+            early = [req_early[role[e]] - dl for dl, f, e in lst if f == rf]
+            want_l = min(late) if late else np.inf
+            want_e = max(early) if early else -np.inf
+            assert r["rat"][p, 0, 2 + rf] == pytest.approx(want_l, abs=1e-12), (p, rf)
+            assert r["rat"][p, 0, rf] == pytest.approx(want_e, abs=1e-12), (p, rf)
+            checked += bool(late)
+    assert checked > 20
+
+
 @pytest.mark.parametrize("seed", range(4))
 def test_gba_bounds_pba(seed):
     """Slew-dependent mode with monotone tables: graph-based late arrival is
-    no smaller than any path-based arrival, early no larger."""
+    no smaller than any path-based arrival, early no larger, and equal to it
+    where a pin is reached by a single path (every Q pin: its CK source, at
+    the clock slew).  The clock slew and the PI arrival/slew differ so that
+    each source's own value is the one that propagates."""
     lib = synth.make_library(seed, noise=0.0)
     d = synth.make_design(10, 4, seed=seed, lib=lib, rc_nodes=(2, 6), pi_frac=0.3)
+    d.update(clk_slew_ns=0.07, pi_slew_ns=0.02, pi_at_ns=0.013)
     r = oracle.sta(d)
     allp = _indep.enumerate_paths(d)
-    n_tight = 0
+    role = np.asarray(d["pin_role"])
+    n_tight = n_single = 0
     for p, lst in allp.items():
         for rf in (0, 1):
             vals = [a for a, _, f in lst if f == rf]
+            slews = [s for _, s, f in lst if f == rf]
             if not vals:
                 continue
             assert r["at"][p, 0, 2 + rf] >= max(vals) - 1e-12
             assert r["at"][p, 0, rf] <= min(vals) + 1e-12
             n_tight += abs(r["at"][p, 0, 2 + rf] - max(vals)) < 1e-12
-    assert n_tight > 0
+            if len(vals) == 1:
+                n_single += 1
+                for el in (0, 2):
+                    assert r["at"][p, 0, el + rf] == pytest.approx(vals[0], abs=1e-12), (p, rf)
+                    assert r["slew"][p, 0, el + rf] == pytest.approx(slews[0], abs=1e-12), (p, rf)
+    assert n_tight > 0 and n_single > 0
+    assert np.any(role == synth.Q)
 
 
 def test_single_gate_hand_case():
@@ -360,6 +398,33 @@ def test_corner_scaling_is_per_corner():
     assert not np.allclose(r4["at"][:, 1], r1["at"][:, 0])
 
 
+@pytest.mark.parametrize("placed", [False, True])
+def test_corner_equals_prescaled_single_corner(placed):
+    """Corner k with LUT scale s_k and RC scale f_k equals a single-corner
+    design whose table values are multiplied by s_k and whose wire R and C
+    (tree values, or per-um values for positions) are multiplied by f_k.
+    Powers of two keep the pre-scaled fp32 inputs exact."""
+    d = synth.make_design(300, 9, seed=12, placed=placed, period_ns=0.8)
+    ls, rs = [1.0, 0.5, 2.0], [1.0, 2.0, 0.5]
+    dk = dict(d)
+    dk.update(n_corners=3, lut_scale=np.array(ls, np.float32), rc_scale=np.array(rs, np.float32))
+    rk = oracle.sta(dk)
+    for k in range(3):
+        d1 = dict(d)
+        d1["lut_val"] = (np.asarray(d["lut_val"], np.float32) * np.float32(ls[k])).astype(np.float32)
+        if placed:
+            d1["r_per_um"] = d["r_per_um"] * rs[k]
+            d1["c_per_um"] = d["c_per_um"] * rs[k]
+        else:
+            d1["rc_R"] = (np.asarray(d["rc_R"], np.float32) * np.float32(rs[k])).astype(np.float32)
+            d1["rc_C"] = (np.asarray(d["rc_C"], np.float32) * np.float32(rs[k])).astype(np.float32)
+        r1 = oracle.sta(d1)
+        for key in ("at", "slew", "rat", "slack"):
+            np.testing.assert_allclose(rk[key][:, k], r1[key][:, 0], rtol=1e-13, atol=1e-15, err_msg=key)
+        assert rk["tns_setup"][k] == pytest.approx(r1["tns_setup"][0], rel=1e-12)
+        assert rk["tns_hold"][k] == pytest.approx(r1["tns_hold"][0], rel=1e-12)
+
+
 # ----------------------------------------------------------- O6 the adjoint
 
 def _single_path_design(x, y, gamma):
@@ -407,10 +472,21 @@ def test_adjoint_single_path_closed_form():
     assert grad[0, 0] == pytest.approx(fd, rel=1e-6)
 
 
-def test_adjoint_matches_central_differences():
+@pytest.mark.parametrize("resistive", [False, True])
+def test_adjoint_matches_central_differences(resistive):
     """dJ/d(x, y) of the oracle's adjoint against central differences of its
-    own smoothed objective, h = 1e-3 um, on random cells of a placed design."""
+    own smoothed objective, h = 1e-3 um, on random cells of a placed design.
+    With resistive wires (R per um raised 10x) the wire variance is
+    comparable to the slews, so the wire-slew terms of the adjoint carry a
+    visible share of the gradient."""
     d = synth.make_design(400, 12, seed=21, placed=True, gamma_ns=0.01, period_ns=0.6)
+    if resistive:
+        d["r_per_um"] = 1.0
+        d["gamma_ns"] = 0.0
+        d["period_ns"] = 0.0
+        req = -oracle.sta(d)["ep_setup"][:, 0]
+        d["period_ns"] = float(np.quantile(req, 0.7))
+        d["gamma_ns"] = 0.01
     J, _, g = oracle.objective_grad(d)
     rng = np.random.default_rng(0)
     cells = rng.choice(d["n_cells"], 40, replace=False)
