@@ -51,7 +51,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scale", choices=sorted(WORKLOADS))
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--schedule", default="dataflow", choices=["level", "dataflow"])
+    ap.add_argument("--schedule", default="dataflow", choices=["level", "dataflow", "coop", "auto"],
+                    help="propagation schedule; auto = sta_autotune's choice")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the update only (no e2e, CPU baseline, batch, gradient or clock sampling); for profilers")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
@@ -199,8 +200,13 @@ def run_ours(a, dist: Dist):
     d = make_workload(a.workload, a.seed)
     dstats = synth.design_stats(d)
     ctx = sta.Context(d, device=dev)
-    if a.schedule == "dataflow":
-        ctx.set_schedule(sta.SCHED_DATAFLOW, 0)
+    sched_names = {sta.SCHED_LEVEL: "level", sta.SCHED_DATAFLOW: "dataflow", sta.SCHED_COOP: "coop"}
+    if a.schedule == "auto":
+        sch, par, _ = ctx.autotune(trials=5)
+        schedule = sched_names[sch]
+    else:
+        schedule = a.schedule
+        ctx.set_schedule({v: k for k, v in sched_names.items()}[schedule], 0)
     # clock period: 90th-percentile endpoint requirement from a run at T = 0
     ctx.set_clock(0.0)
     ctx.update_timing()
@@ -242,7 +248,7 @@ def run_ours(a, dist: Dist):
                       "cells": dstats["cells"], "pins": dstats["pins"], "cell_arcs": dstats["cell_arcs"],
                       "net_arcs": dstats["net_arcs"], "rc_nodes": dstats["rc_nodes"],
                       "endpoints": dstats["endpoints"], "levels": st["n_levels"], "corners": K,
-                      "period_ns": T, "schedule": a.schedule,
+                      "period_ns": T, "schedule": schedule,
                       "parallelism": "replicas x%d" % dist.world if dist.world > 1 else "1 GPU",
                       "l2": "no flush: per-pass working set %.0f MB > 126 MB L2" % (st["device_bytes"] / 1e6),
                       "wns_setup_ns": rep["wns_setup"], "tns_setup_ns": rep["tns_setup"],
@@ -267,14 +273,18 @@ def run_ours(a, dist: Dist):
     bm = byte_model(st, K)
     pk, pk_kind = peaks()
     fwd_dominant = ph[1] >= ph[2]
-    if a.schedule == "dataflow":
+    phase_ms = ph[1] if fwd_dominant else ph[2]
+    phase_bytes = bm["fwd"] if fwd_dominant else bm["bwd"]
+    if schedule == "dataflow":
         kern = "k_df_forward" if fwd_dominant else "k_df_backward"
         launches = 1
+    elif schedule == "coop":
+        # one launch runs both passes: its time is the forward slot
+        kern, launches = "k_coop_pass", 1
+        phase_ms, phase_bytes = ph[1] + ph[2], bm["fwd"] + bm["bwd"]
     else:
         kern = "k_fwd_level" if fwd_dominant else "k_bwd_level"
         launches = st["n_levels"]
-    phase_ms = ph[1] if fwd_dominant else ph[2]
-    phase_bytes = bm["fwd"] if fwd_dominant else bm["bwd"]
     achieved = phase_bytes / (phase_ms * 1e-3) / 1e9
     tr = measured_traffic(kern)
     out["roofline"] = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": pk["hbm_gbs"],

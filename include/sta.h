@@ -71,7 +71,8 @@ enum { STA_SENSE_NONE = -1, STA_SENSE_POS = 0, STA_SENSE_NEG = 1,
 enum { STA_AT = 0, STA_SLEW = 1, STA_RAT = 2, STA_SLACK = 3 };
 /* propagation schedules (sta_set_schedule) */
 enum { STA_SCHED_LEVEL = 0,      /* one kernel launch per level, graph-captured */
-       STA_SCHED_DATAFLOW = 1 }; /* one persistent kernel per pass, per-item ready flags */
+       STA_SCHED_DATAFLOW = 1,   /* one persistent kernel per pass, per-item ready flags */
+       STA_SCHED_COOP = 2 };     /* one co-resident launch for both passes, a grid barrier per level */
 
 /*
  * Cell library.  Per type: type_nin inputs (1..3) followed by one output.
@@ -214,7 +215,8 @@ sta_status sta_set_corners(sta_ctx *ctx, const float *lut_scale, const float *rc
 /* Pick the fastest schedule for this context: times `trials` graph launches
  * of each candidate (level schedule with 64, 128 and 256 threads per block;
  * dataflow schedule with a persistent grid from occupancy, one block per SM
- * and two per SM) on `stream`, keeps the best and selects it.  Choices are
+ * and two per SM; cooperative schedule with a grid from occupancy and one
+ * block per SM) on `stream`, keeps the best and selects it.  Choices are
  * cached per (device, graph shape); a cached choice is reused unless `force`.
  * Outputs (nullable): the chosen schedule, its parameter and its ms per
  * update.  Runs full timing updates (the context's results are those of the
@@ -234,13 +236,15 @@ sta_status sta_set_clock(sta_ctx *ctx, float period_ns);
 sta_status sta_resize_cells(sta_ctx *ctx, const int32_t *cells, const int32_t *types, int32_t n, sta_mem mem,
                             void *stream);
 
-/* Select the propagation schedule (STA_SCHED_*) and its parameter (threads
- * per block for LEVEL; resident blocks per SM for DATAFLOW, 0 = auto). */
+/* Select the propagation schedule (STA_SCHED_*) and its parameter: threads
+ * per block for LEVEL (0 = 128); for DATAFLOW and COOP the persistent grid
+ * size in blocks (0 = every block the occupancy allows on this device). */
 sta_status sta_set_schedule(sta_ctx *ctx, int32_t schedule, int32_t param);
 
-/* Dataflow schedule: polls a wait may spend on a ready flag before the pass
- * gives up and the next synchronising call returns STA_ETIMEOUT (default
- * 2^23, seconds of waiting; a real wait ends in microseconds). */
+/* Dataflow and cooperative schedules: polls a wait (on a ready flag, or on
+ * the grid barrier between levels) may spend before the pass gives up and
+ * the next synchronising call returns STA_ETIMEOUT (default 2^23, seconds of
+ * waiting; a real wait ends in microseconds). */
 sta_status sta_set_wait_limit(sta_ctx *ctx, int64_t polls);
 
 /* Failure-detection test hook (dataflow schedule): while `cell` >= 0, the

@@ -1,16 +1,15 @@
 // dataflow.cu -- persistent dataflow schedule of the timing pass.
 //
 // Instead of one launch per level, each pass is one persistent kernel.  Its
-// warps take chunks of at most 8 / KL items of one level (4 * KL lanes per
-// item, KL = corners side by side) in
-// level order (the backward pass in reverse level order) from an atomic
-// counter.  An item runs as soon as the mailbox entries of the items it
-// reads are complete -- polled by the whole warp, with a bounded number of
-// idle rounds -- and publishes its own results to the mailbox of this pass's
-// epoch parity (item.cuh).  Chunks are handed out in increasing order and an
-// item only waits for items handed out earlier, whose warps are already
-// running, so the oldest unfinished item can always proceed: no grid barrier
-// and no co-residency assumption.  The cell library (tables and per-type
+// warps take chunks of at most 8 / KL items of one level in level order (the
+// backward pass in reverse level order) from an atomic counter and run each
+// item in a slot of 4 * KL lanes (KL = corners side by side) as soon as the
+// mailbox entries of the items it reads are complete -- polled without
+// blocking, with a bounded number of idle rounds -- and publish its results
+// to the mailbox of this pass's epoch parity (item.cuh).  Items are handed
+// out in increasing order and an item only waits for earlier ones, so the
+// oldest unfinished item can always proceed: no grid barrier and no
+// co-residency assumption.  The cell library (tables and per-type
 // data) is copied into shared memory once per block.
 #include <algorithm>
 
@@ -108,24 +107,24 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
         if (ch < 0) break;
         const int x = c.fwd_chunk_lo[ch] + lane / (4 * c.KL);
         bool pending = x < c.fwd_chunk_hi[ch];
-        const bool is_item = x < c.I;   // endpoint chunks follow all item chunks
+        const bool is_item = x < c.I;   // else position x - I of the endpoint order
         FwdItem f{};
         EpItem e{};
         if (pending) {
             if (is_item) f = fwd_prep(c, L.nin, L.kind, L.sense, x);
-            else e = ep_prep(c, x - c.I);
+            else e = ep_prep(c, c.ep_order[x - c.I]);
         }
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
             if (pending) {
                 FwdIn in;
                 if (is_item) {
-                    if (group_all(c, fwd_probe(c, f, par, in))) {
+                    if (group_all(c, fwd_probe(c, f, par, q, in))) {
                         fwd_run<SMOOTH, UNIFORM, true>(c, L.lut, f, in, x, q, par);
                         pending = false;
                     }
-                } else if (group_all(c, ep_probe(c, e, par, in.at[0], in.sl[0]))) {
-                    ep_run<true>(c, e, in.at[0], in.sl[0], x - c.I, q, par);
+                } else if (group_all(c, ep_probe(c, e, par, q, in.at[0], in.sl[0]))) {
+                    ep_run<true>(c, e, in.at[0], in.sl[0], c.ep_order[x - c.I], q, par);
                     pending = false;
                 }
             }
@@ -147,11 +146,12 @@ __global__ void __launch_bounds__(kDfThreads) k_df_backward(const DevCtx c)
         const int x = c.bwd_chunk_lo[ch] + lane / (4 * c.KL);
         bool pending = x < c.bwd_chunk_hi[ch];
         BwdItem b{};
-        if (pending) b = bwd_prep(c, L.nin, L.kind, x);
+        if (pending) b = bwd_prep(c, L.nin, L.kind, x, q);
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
-            if (pending && group_all(c, bwd_probe(c, b, par))) {
-                bwd_run<UNIFORM, true>(c, L.lut, L.sense, b, q, par);
+            float R;
+            if (pending && group_all(c, bwd_probe(c, b, par, q, R))) {
+                bwd_run<UNIFORM, true>(c, L.lut, L.sense, b, q, par, R);
                 pending = false;
             }
             if (__any_sync(0xffffffffu, pending) && !warp_idle_round(c, spins)) break;
@@ -190,6 +190,147 @@ cudaError_t dataflow_prepare(HostSched &h, bool smooth, int requested)
     h.df_blocks_fwd = requested > 0 ? std::min(requested, bf) : bf;
     h.df_blocks_bwd = requested > 0 ? std::min(requested, bb) : bb;
     return cudaSuccess;
+}
+
+// ------------------------------------------------------- cooperative schedule
+//
+// Level-synchronous, but without a kernel boundary per level: one launch
+// whose blocks are all resident (cooperative launch) walks the forward
+// levels, the endpoints and the backward levels, and a grid-wide barrier
+// separates consecutive levels.  Inside a level, warp w of W takes items
+// (w + r W) * 8/KL + lane / (4 KL), r = 0, 1, ...; the per-item arithmetic is
+// that of the level kernels (item.cuh, pin states read from L2).
+
+// Barrier arrivals accumulate in df_state[7] (reset before the launch), so
+// the n-th barrier of a pass completes at n * gridDim.x arrivals.  One thread
+// per block arrives (after a device-scope fence over the block's writes)
+// and polls; the poll is bounded and any block that gives up, or sees that
+// another one gave up, raises the abort word and leaves the kernel.
+__device__ __forceinline__ bool grid_barrier(const DevCtx &c, unsigned &target, int *abort_flag)
+{
+    __syncthreads();
+    target += gridDim.x;
+    if (threadIdx.x == 0) {
+        int ab = 0;
+        __threadfence();
+        atomicAdd(c.df_state + 7, 1u);
+        long long spins = 0;
+        while (ld_volatile(c.df_state + 7) < target) {
+            if (++spins >= c.spin_limit) {
+                atomicOr(c.err, kErrTimeout);
+                atomicExch(c.df_state + 3, 1u);
+                ab = 1;
+                break;
+            }
+            if ((spins & 15) == 0 && ld_volatile(c.df_state + 3) != 0u) {
+                ab = 1;
+                break;
+            }
+        }
+        __threadfence();
+        *abort_flag = ab;
+    }
+    __syncthreads();
+    return *abort_flag == 0;
+}
+
+// Barrier count and abort word at zero.  (The dataflow epoch is left alone:
+// its mailbox parities stay consistent across schedule changes.)
+__global__ void k_coop_begin(const DevCtx c)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        c.df_state[3] = 0u;
+        c.df_state[7] = 0u;
+    }
+}
+
+template <bool SMOOTH, bool UNIFORM>
+__global__ void __launch_bounds__(kDfThreads) k_coop_pass(const DevCtx c)
+{
+    extern __shared__ float smem[];
+    __shared__ int abort_flag;
+    const SmemLib L = stage_library(c, smem);
+    const int lane = threadIdx.x & 31, q = lane & 3;
+    const int per = 8 / c.KL;                          // items per warp
+    const int sub = lane / (4 * c.KL);                 // this lane's item inside the warp's group
+    const int W = gridDim.x * (kDfThreads / 32);
+    const int w = blockIdx.x * (kDfThreads / 32) + (threadIdx.x >> 5);
+    unsigned target = 0;
+    for (int s = 0; s < c.S; ++s) {
+        const int i0 = __ldg(c.stage_ptr + s), i1 = __ldg(c.stage_ptr + s + 1);
+        for (int g = i0 + w * per + sub; g < i1; g += W * per) {
+            const FwdItem f = fwd_prep(c, L.nin, L.kind, L.sense, g);
+            fwd_run<SMOOTH, UNIFORM, false>(c, L.lut, f, FwdIn{}, g, q, 0);
+        }
+        if (!grid_barrier(c, target, &abort_flag)) return;
+    }
+    for (int e = w * per + sub; e < c.E; e += W * per) ep_run<false>(c, ep_prep(c, e), 0.f, 0.f, e, q, 0);
+    if (!grid_barrier(c, target, &abort_flag)) return;
+    for (int s = c.S - 1; s >= 0; --s) {
+        const int i0 = __ldg(c.stage_ptr + s), i1 = __ldg(c.stage_ptr + s + 1);
+        for (int g = i0 + w * per + sub; g < i1; g += W * per)
+            bwd_run<UNIFORM, false>(c, L.lut, L.sense, bwd_prep(c, L.nin, L.kind, g, q), q, 0, 0.f);
+        if (s > 0 && !grid_barrier(c, target, &abort_flag)) return;
+    }
+}
+
+template <bool SMOOTH, bool UNIFORM>
+static cudaError_t coop_launch(const DevCtx &c, int blocks, size_t smem, cudaStream_t st)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(kDfThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_coop_pass<SMOOTH, UNIFORM>, c);
+}
+
+cudaError_t coop_prepare(HostSched &h, bool smooth, int requested)
+{
+    const size_t smem = df_smem_bytes(h.T);
+    auto k = smooth ? (h.uniform ? k_coop_pass<true, true> : k_coop_pass<true, false>)
+                    : (h.uniform ? k_coop_pass<false, true> : k_coop_pass<false, false>);
+    int dev = 0, coop = 0, blocks = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (e == cudaSuccess && !coop) e = cudaErrorNotSupported;
+    if (e == cudaSuccess) e = occupancy_blocks(k, smem, &blocks);
+    if (e != cudaSuccess) return e;
+    h.coop_blocks = requested > 0 ? std::min(requested, blocks) : blocks;
+    return cudaSuccess;
+}
+
+void launch_coop_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev)
+{
+    const size_t smem = df_smem_bytes(h.T);
+    if (ev) cudaEventRecord(ev[0], st);
+    k_coop_begin<<<1, 32, 0, st>>>(c);
+    if (h.placed) {
+        if (c.I > 0) launch_net_star(c, st);
+    } else if (h.n_tiles > 0) {
+        launch_net_tree(c, h, st);
+    }
+    if (ev) cudaEventRecord(ev[1], st);
+    if (c.I > 0 || c.E > 0) {
+        if (c.gamma > 0.f) {
+            if (h.uniform) coop_launch<true, true>(c, h.coop_blocks, smem, st);
+            else coop_launch<true, false>(c, h.coop_blocks, smem, st);
+        } else {
+            if (h.uniform) coop_launch<false, true>(c, h.coop_blocks, smem, st);
+            else coop_launch<false, false>(c, h.coop_blocks, smem, st);
+        }
+    }
+    // forward and backward share one launch: the phase events after it
+    // coincide (the profile attributes the whole launch to the forward slot)
+    if (ev) cudaEventRecord(ev[2], st);
+    if (ev) cudaEventRecord(ev[3], st);
+    launch_reduce(c, h, st);
+    if (ev) cudaEventRecord(ev[4], st);
 }
 
 void launch_dataflow_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev)

@@ -14,6 +14,7 @@ constexpr int kRcTileNodes = 1024;
 constexpr int kRcTileSinks = 1024;
 constexpr int kRcTileNets = 128;
 constexpr int kRedThreads = 256;   // threads of the reduction kernels
+constexpr int kDfStateWords = 16;  // schedule state words (see DevCtx::df_state)
 constexpr int kRedChunk = 4096;    // endpoints per first-stage reduction block
 
 // device error word bits (sta_sync maps them to sta_status)
@@ -52,12 +53,15 @@ struct DevCtx {
     float4 *fbox;                               // [2][P][K][2] arrival, slew of driver pins
     float4 *rbox;                               // [2][P][K]    required time of gate input pins
     size_t fbox_len, rbox_len;                  // float4 elements of each
-    unsigned *df_state;                         // [0] epoch, [1] forward chunk counter, [2] backward counter,
-                                                // [3] abort; adjoint: [4] epoch, [5] chunk counter, [6] abort
+    unsigned *df_state;                         // [kDfStateWords] [0] epoch, [1] forward chunk counter,
+                                                // [2] backward counter, [3] abort; adjoint: [4] epoch,
+                                                // [5] chunk counter, [6] abort; [7] grid-barrier arrivals
     int32_t ep_begin;                           // first endpoint pin (endpoints are the last E pins)
     int32_t hold_item;                          // test hook: item whose forward flag is never published (-1 none)
     long long spin_limit;                       // polls before a wait gives up
     int32_t n_fwd_chunks, n_bwd_chunks;
+    const int32_t *stage_ptr;                   // [S+1] item offsets of the levels (cooperative schedule)
+    const int32_t *ep_order;                    // [E] endpoints by driver level (dataflow forward work list)
     const int32_t *fwd_chunk_lo, *fwd_chunk_hi;   // forward work: items by level, then endpoints (index I + e)
     const int32_t *bwd_chunk_lo, *bwd_chunk_hi;   // backward work: items by level, deepest first
     // differentiable pass (sta_backward)

@@ -138,6 +138,12 @@ __device__ __forceinline__ float4 ld_relaxed4(const float4 *p)
                  : "memory");
     return v;
 }
+__device__ __forceinline__ float ld_relaxed1(const float *p)
+{
+    float v;
+    asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+    return v;
+}
 __device__ __forceinline__ void st_relaxed(float *p, float v)
 {
     asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
@@ -172,10 +178,15 @@ __device__ __forceinline__ void publish_rat(const DevCtx &c, int par, int pin, i
     reinterpret_cast<float *>(rbox_at(c, par ^ 1, pin, k))[q] = __int_as_float(0x7fffffff);
 }
 
-template <bool WAIT>
-__device__ __forceinline__ float ld_comp(const float4 *p, int q)
+// Reads of pin states (arrival, slew, required time) that another item
+// produced: L2 only (ld.global.cg), never a line an earlier read left in
+// this SM's L1.  Across kernel boundaries plain loads would do; inside one
+// persistent launch (the cooperative schedule) the value may have been
+// written by another SM after this SM's L1 cached the line.
+__device__ __forceinline__ float4 ld_state4(const float4 *p) { return __ldcg(p); }
+__device__ __forceinline__ float ld_state(const float4 *p, int q)
 {
-    return reinterpret_cast<const float *>(p)[q];
+    return __ldcg(reinterpret_cast<const float *>(p) + q);
 }
 __device__ __forceinline__ void st_comp(float4 *p, int q, float v) { reinterpret_cast<float *>(p)[q] = v; }
 
@@ -215,9 +226,10 @@ struct FwdItem {
     float Dn0[3], V0[3], ld0;   // net values of the lane's first corner, loaded ahead
 };
 
-// driver arrival and slew of corner 0, as probed
+// the drivers' arrival and slew, component q of the lane's first corner, as
+// probed (the other edge comes from the partner lane q ^ 1)
 struct FwdIn {
-    float4 at[3], sl[3];
+    float at[3], sl[3];
 };
 
 __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, const int *tkind, const int *tsense,
@@ -242,18 +254,20 @@ __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, co
     return f;
 }
 
-// Are the drivers' arrivals and slews of the lane's corners complete?  Those
-// of its first corner are returned in `in`.
-__device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int par, FwdIn &in)
+// Are the drivers' arrivals and slews of the lane's corners complete?  Lane
+// q reads component q of its first corner (returned in `in`); the caller's
+// group_all over the quad covers the four components.
+__device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int par, int q, FwdIn &in)
 {
     bool ok = true;
     const int kq = corner_lane(c);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         if (j < f.nin) {
-            in.at[j] = ld_relaxed4(fbox_at(c, par, f.drv[j], kq));
-            in.sl[j] = ld_relaxed4(fbox_at(c, par, f.drv[j], kq) + 1);
-            ok = ok && complete(in.at[j]) && complete(in.sl[j]);
+            const float *r = reinterpret_cast<const float *>(fbox_at(c, par, f.drv[j], kq));
+            in.at[j] = ld_relaxed1(r + q);
+            in.sl[j] = ld_relaxed1(r + 4 + q);
+            ok = ok && in.at[j] == in.at[j] && in.sl[j] == in.sl[j];
             for (int k = kq + c.KL; k < c.K && ok; k += c.KL)
                 ok = complete(ld_relaxed4(fbox_at(c, par, f.drv[j], k))) &&
                      complete(ld_relaxed4(fbox_at(c, par, f.drv[j], k) + 1));
@@ -299,6 +313,7 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
     }
     const int z = pin0 + nin;
     const float sgn = el ? 1.f : -1.f;   // early merges are mins: max of the negated candidates
+    const unsigned qm = quad_mask();
     for (int k = kq; k < K; k += KL) {
         // net arcs into the input pins: this lane needs components el*2 + {0, 1}
         float ain[3][2], sin[3][2];
@@ -306,22 +321,31 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
         for (int j = 0; j < 3; ++j) {
             if (j < nin) {
                 const int a = pin0 + j;
-                float4 ad, sd;
-                if (!WAIT) {
-                    ad = c.at[(size_t)f.drv[j] * K + k];
-                    sd = c.slew[(size_t)f.drv[j] * K + k];
-                } else if (k == kq) {
-                    ad = in.at[j];
-                    sd = in.sl[j];
+                float a0, a1, s0, s1;   // the driver's rise / fall arrival and slew at this lane's el
+                if (WAIT && k == kq) {
+                    const float ap = __shfl_xor_sync(qm, in.at[j], 1), sp = __shfl_xor_sync(qm, in.sl[j], 1);
+                    a0 = rfo ? ap : in.at[j];
+                    a1 = rfo ? in.at[j] : ap;
+                    s0 = rfo ? sp : in.sl[j];
+                    s1 = rfo ? in.sl[j] : sp;
                 } else {
-                    ad = ld_relaxed4(fbox_at(c, par, f.drv[j], k));
-                    sd = ld_relaxed4(fbox_at(c, par, f.drv[j], k) + 1);
+                    float4 ad, sd;
+                    if (!WAIT) {
+                        ad = ld_state4(c.at + (size_t)f.drv[j] * K + k);
+                        sd = ld_state4(c.slew + (size_t)f.drv[j] * K + k);
+                    } else {
+                        ad = ld_relaxed4(fbox_at(c, par, f.drv[j], k));
+                        sd = ld_relaxed4(fbox_at(c, par, f.drv[j], k) + 1);
+                    }
+                    a0 = el ? ad.z : ad.x;
+                    a1 = el ? ad.w : ad.y;
+                    s0 = el ? sd.z : sd.x;
+                    s1 = el ? sd.w : sd.y;
                 }
                 const float Dn = k != kq ? c.netD[(size_t)a * K + k] : f.Dn0[j];
                 const float V = k != kq ? c.netV[(size_t)a * K + k] : f.V0[j];
-                ain[j][0] = (el ? ad.z : ad.x) + Dn;
-                ain[j][1] = (el ? ad.w : ad.y) + Dn;
-                const float s0 = el ? sd.z : sd.x, s1 = el ? sd.w : sd.y;
+                ain[j][0] = a0 + Dn;
+                ain[j][1] = a1 + Dn;
                 sin[j][0] = sqrtf(fmaf(s0, s0, V));
                 sin[j][1] = sqrtf(fmaf(s1, s1, V));
                 // lane q stores component q of the input pin: (el, rf = q & 1)
@@ -374,14 +398,16 @@ __device__ __forceinline__ EpItem ep_prep(const DevCtx &c, int e)
     return x;
 }
 
-// the driver's arrival and slew of the lane's corners are complete; those of
-// its first corner are returned
-__device__ __forceinline__ bool ep_probe(const DevCtx &c, const EpItem &x, int par, float4 &at0, float4 &sl0)
+// the driver's arrival and slew of the lane's corners are complete; lane q
+// reads component q of its first corner (returned; the caller's group_all
+// covers the quad)
+__device__ __forceinline__ bool ep_probe(const DevCtx &c, const EpItem &x, int par, int q, float &at0, float &sl0)
 {
     const int kq = corner_lane(c);
-    at0 = ld_relaxed4(fbox_at(c, par, x.d, kq));
-    sl0 = ld_relaxed4(fbox_at(c, par, x.d, kq) + 1);
-    bool ok = complete(at0) && complete(sl0);
+    const float *r = reinterpret_cast<const float *>(fbox_at(c, par, x.d, kq));
+    at0 = ld_relaxed1(r + q);
+    sl0 = ld_relaxed1(r + 4 + q);
+    bool ok = at0 == at0 && sl0 == sl0;
     for (int k = kq + c.KL; k < c.K && ok; k += c.KL)
         ok = complete(ld_relaxed4(fbox_at(c, par, x.d, k))) && complete(ld_relaxed4(fbox_at(c, par, x.d, k) + 1));
     return ok;
@@ -391,7 +417,7 @@ __device__ __forceinline__ bool ep_probe(const DevCtx &c, const EpItem &x, int p
 // capture edge T - setup, hold 0 + hold; PO: T and 0), pin and endpoint
 // slacks (min over rise/fall) and violation flags.  Lane q: component q.
 template <bool WAIT>
-__device__ __forceinline__ void ep_run(const DevCtx &c, const EpItem &x, float4 at0, float4 sl0, int e, int q,
+__device__ __forceinline__ void ep_run(const DevCtx &c, const EpItem &x, float at0, float sl0, int e, int q,
                                        int par)
 {
     const int K = c.K, p = x.p, d = x.d;
@@ -402,11 +428,11 @@ __device__ __forceinline__ void ep_run(const DevCtx &c, const EpItem &x, float4 
     for (int k = kq; k < K; k += c.KL) {
         float ad, sd;
         if (!WAIT) {
-            ad = reinterpret_cast<const float *>(c.at + (size_t)d * K + k)[q];
-            sd = reinterpret_cast<const float *>(c.slew + (size_t)d * K + k)[q];
+            ad = ld_state(c.at + (size_t)d * K + k, q);
+            sd = ld_state(c.slew + (size_t)d * K + k, q);
         } else if (k == kq) {
-            ad = comp(at0, q);
-            sd = comp(sl0, q);
+            ad = at0;
+            sd = sl0;
         } else {
             ad = comp(ld_relaxed4(fbox_at(c, par, d, k)), q);
             sd = comp(ld_relaxed4(fbox_at(c, par, d, k) + 1), q);
@@ -434,11 +460,16 @@ __device__ __forceinline__ void ep_run(const DevCtx &c, const EpItem &x, float4 
 struct BwdItem {
     int t, pin0, nin, kind, z, f0, f1;
     float ld0;
+    // states of the lane's first corner, component q, loaded ahead (written
+    // by the forward pass): arrival of the output, slew and arrival of each
+    // input pin (CK: the slew of the rising component of this lane's el)
+    float az0, s0[3], a0[3];
 };
 
-__device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, const int *tkind, int g)
+__device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, const int *tkind, int g, int q)
 {
     BwdItem b;
+    const int K = c.K, kq = corner_lane(c);
     b.t = c.item_type[g];
     b.pin0 = c.item_pin0[g];
     b.kind = b.t >= 0 ? tkind[b.t] : -1;
@@ -446,26 +477,67 @@ __device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, co
     b.z = b.t < 0 ? b.pin0 : (b.kind == 1 ? b.pin0 + 1 : b.pin0 + b.nin);
     b.f0 = c.fo_ptr[g];
     b.f1 = c.fo_ptr[g + 1];
-    b.ld0 = b.t >= 0 ? c.load[(size_t)b.z * c.K + corner_lane(c)] : 0.f;
+    b.ld0 = b.t >= 0 ? c.load[(size_t)b.z * K + kq] : 0.f;
+    b.az0 = ld_state(c.at + (size_t)b.z * K + kq, q);
+    const int nread = b.kind == 1 ? 1 : b.kind == 0 ? b.nin : 0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const bool on = j < nread;
+        const size_t o = (size_t)(b.pin0 + j) * K + kq;
+        b.s0[j] = on ? ld_state(c.slew + o, b.kind == 1 ? (q & 2) : q) : 0.f;
+        b.a0[j] = on ? ld_state(c.at + o, q) : 0.f;
+    }
     return b;
 }
 
-// every gate-input sink of the item's net has its required times (all
-// corners); endpoint sinks were set by the forward pass
-__device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int par)
+// Are the required times of every sink of the item's net complete (all the
+// lane's corners)?  Lane q reads component q only: the caller's group_all
+// over the quad covers the four.  Sinks are read four at a time, their
+// loads in flight together.  For the lane's first corner the same pass
+// folds them: R = min (late) / max (early) over the sinks of RAT - Elmore
+// delay, component q -- the output's required time, ready for bwd_run.
+// Endpoint sinks were set by the forward pass.
+__device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int par, int q, float &R)
 {
+    const int K = c.K, kq = corner_lane(c);
+    const bool late = q >= 2;
     bool ok = true;
-    for (int p = b.f0; p < b.f1 && ok; ++p) {
-        const int s = c.fo_pin[p];
-        if (s < c.ep_begin)
-            for (int k = corner_lane(c); k < c.K && ok; k += c.KL) ok = complete(ld_relaxed4(rbox_at(c, par, s, k)));
+    float r = late ? INFINITY : -INFINITY;
+    for (int p0 = b.f0; p0 < b.f1; p0 += 4) {
+        int s[4];
+        float m[4], nd[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] = p0 + u < b.f1 ? __ldg(c.fo_pin + p0 + u) : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (s[u] < 0) continue;
+            m[u] = s[u] < c.ep_begin ? ld_relaxed1(reinterpret_cast<const float *>(rbox_at(c, par, s[u], kq)) + q)
+                                     : ld_state(c.rat + (size_t)s[u] * K + kq, q);
+            nd[u] = __ldg(c.netD + (size_t)s[u] * K + kq);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (s[u] < 0) continue;
+            ok = ok && m[u] == m[u];
+            const float v = m[u] - nd[u];
+            r = late ? fminf(r, v) : fmaxf(r, v);
+        }
     }
+    for (int p = b.f0; p < b.f1 && ok; ++p) {
+        const int s = __ldg(c.fo_pin + p);
+        if (s < c.ep_begin)
+            for (int k = kq + c.KL; k < K && ok; k += c.KL) ok = complete(ld_relaxed4(rbox_at(c, par, s, k)));
+    }
+    R = r;
     return ok;
 }
 
+// Lane q = el*2 + rfi: the output's required time (component q) over its
+// net sinks, then each input pin's over its arcs, and pin slacks.  With WAIT
+// the first corner's output required time comes folded from bwd_probe (Rpre).
 template <bool UNIFORM, bool WAIT, class L>
 __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int *tsense, const BwdItem &b, int q,
-                                        int par)
+                                        int par, float Rpre)
 {
     const int t = b.t, pin0 = b.pin0, z = b.z, K = c.K;
     const int el = q >> 1, rfi = q & 1;
@@ -473,26 +545,31 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
     const int base = threadIdx.x & 28;
     const int kq = corner_lane(c);
     for (int k = kq; k < K; k += c.KL) {
+        const bool first = k == kq;
         // required time of the output, component q, over its net sinks
         float R = el ? INFINITY : -INFINITY;
-        for (int p = b.f0; p < b.f1; ++p) {
-            const int s = c.fo_pin[p];
-            const float rs = (WAIT && s < c.ep_begin) ? comp(ld_relaxed4(rbox_at(c, par, s, k)), q)
-                                                      : reinterpret_cast<const float *>(c.rat + (size_t)s * K + k)[q];
-            const float r = rs - c.netD[(size_t)s * K + k];
-            R = el ? fminf(R, r) : fmaxf(R, r);
+        if (WAIT && first) {
+            R = Rpre;
+        } else {
+            for (int p = b.f0; p < b.f1; ++p) {
+                const int s = c.fo_pin[p];
+                const float rs = (WAIT && s < c.ep_begin) ? comp(ld_relaxed4(rbox_at(c, par, s, k)), q)
+                                                          : ld_state(c.rat + (size_t)s * K + k, q);
+                const float r = rs - c.netD[(size_t)s * K + k];
+                R = el ? fminf(R, r) : fmaxf(R, r);
+            }
         }
         st_comp(c.rat + (size_t)z * K + k, q, R);
-        const float Az = reinterpret_cast<const float *>(c.at + (size_t)z * K + k)[q];
+        const float Az = first ? b.az0 : ld_state(c.at + (size_t)z * K + k, q);
         st_comp(c.slack + (size_t)z * K + k, q, el ? R - Az : Az - R);
         if (t < 0) continue;
         // the output's required times of both edges at this lane's el
         const float R0 = __shfl_sync(m, R, base + el * 2), R1 = __shfl_sync(m, R, base + el * 2 + 1);
         const float sc = __ldg(c.lut_scale + k);
-        const float ld = k != kq ? c.load[(size_t)z * K + k] : b.ld0;
+        const float ld = first ? b.ld0 : c.load[(size_t)z * K + k];
         if (b.kind == 1) {   // CK: only the rising edge has an arc (to both edges of Q)
             const int ck = pin0;
-            const float s = reinterpret_cast<const float *>(c.slew + (size_t)ck * K + k)[el * 2];
+            const float s = first ? b.s0[0] : ld_state(c.slew + (size_t)ck * K + k, el * 2);
             const int tb = tab_off(t, 1, 0);
             const Seg as = seg_slew<UNIFORM>(c, lut, tb, s), bl = seg_load<UNIFORM>(c, lut, tb, ld);
             const float d0 = sc * lookup<UNIFORM>(lut, tb, as, bl, s, ld);
@@ -500,16 +577,18 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
             float Rc = el ? fminf(R0 - d0, R1 - d1) : fmaxf(R0 - d0, R1 - d1);
             if (rfi == 1) Rc = el ? INFINITY : -INFINITY;
             st_comp(c.rat + (size_t)ck * K + k, q, Rc);
-            const float Ac = reinterpret_cast<const float *>(c.at + (size_t)ck * K + k)[q];
+            const float Ac = first ? b.a0[0] : ld_state(c.at + (size_t)ck * K + k, q);
             st_comp(c.slack + (size_t)ck * K + k, q, el ? Rc - Ac : Ac - Rc);
             continue;
         }
         const Seg bl = seg_load<UNIFORM>(c, lut, tab_off(t, 0, 0), ld);
-        for (int j = 0; j < b.nin; ++j) {
+#pragma unroll
+        for (int j = 0; j < 3; ++j) {
+            if (j >= b.nin) continue;
             const int a = pin0 + j;
             const int se = tsense[t * 3 + j];
             const int tbj = tab_off(t, j, 0);
-            const float s = reinterpret_cast<const float *>(c.slew + (size_t)a * K + k)[q];
+            const float s = first ? b.s0[j] : ld_state(c.slew + (size_t)a * K + k, q);
             const Seg as = seg_slew<UNIFORM>(c, lut, tbj, s);
             float acc = el ? INFINITY : -INFINITY;
 #pragma unroll
@@ -520,7 +599,7 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
                 acc = el ? fminf(acc, cand) : fmaxf(acc, cand);
             }
             st_comp(c.rat + (size_t)a * K + k, q, acc);
-            const float Aa = reinterpret_cast<const float *>(c.at + (size_t)a * K + k)[q];
+            const float Aa = first ? b.a0[j] : ld_state(c.at + (size_t)a * K + k, q);
             st_comp(c.slack + (size_t)a * K + k, q, el ? acc - Aa : Aa - acc);
             if (WAIT) publish_rat(c, par, a, k, q, acc);
         }

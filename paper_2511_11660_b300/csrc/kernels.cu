@@ -142,7 +142,7 @@ __global__ void k_endpoints(const DevCtx c)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int e = tid / (4 * c.KL);
-    if (e < c.E) ep_run<false>(c, ep_prep(c, e), float4{}, float4{}, e, tid & 3, 0);
+    if (e < c.E) ep_run<false>(c, ep_prep(c, e), 0.f, 0.f, e, tid & 3, 0);
 }
 
 template <bool UNIFORM>
@@ -150,8 +150,8 @@ __global__ void k_bwd_level(const DevCtx c, int i0, int i1)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int g = i0 + tid / (4 * c.KL);
-    if (g < i1) bwd_run<UNIFORM, false>(c, LutGlobal{c.lut}, c.arc_sense, bwd_prep(c, c.type_nin, c.type_kind, g),
-                                        tid & 3, 0);
+    if (g < i1) bwd_run<UNIFORM, false>(c, LutGlobal{c.lut}, c.arc_sense,
+                                        bwd_prep(c, c.type_nin, c.type_kind, g, tid & 3), tid & 3, 0, 0.f);
 }
 
 // ------------------------------------------------------------- reduction

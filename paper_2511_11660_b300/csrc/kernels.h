@@ -21,6 +21,7 @@ struct HostSched {
     int df_blocks_fwd = 0;            // persistent grids of the dataflow kernels
     int df_blocks_bwd = 0;
     int adj_blocks = 0;               // persistent grid of the dataflow adjoint (0 = level sweep)
+    int coop_blocks = 0;              // co-resident grid of the cooperative schedule
 };
 
 // Net delays, forward levels, endpoints, backward levels, reduction.  With
@@ -40,6 +41,13 @@ void launch_net_star(const DevCtx &c, cudaStream_t st);
 size_t dataflow_smem_bytes(int T);
 cudaError_t dataflow_prepare(HostSched &h, bool smooth, int requested);
 void launch_dataflow_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev = nullptr);
+
+// Cooperative schedule: one co-resident launch runs every forward level,
+// the endpoints and every backward level, with a grid-wide barrier between
+// levels (see dataflow.cu).  coop_prepare sizes the grid (at most `requested`
+// blocks when > 0) outside stream capture.
+cudaError_t coop_prepare(HostSched &h, bool smooth, int requested);
+void launch_coop_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev = nullptr);
 
 // Smoothed objective and its reverse sweep to cell positions (adjoint.cu):
 // a persistent dataflow sweep when adjoint_prepare gave it a grid

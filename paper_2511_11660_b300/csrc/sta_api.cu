@@ -105,6 +105,7 @@ void drop_graph(sta_ctx *c)
 void record_pass(sta_ctx *c, cudaStream_t st, cudaEvent_t *ev = nullptr)
 {
     if (c->schedule == STA_SCHED_DATAFLOW) sta::launch_dataflow_pass(c->dc, c->hs, st, ev);
+    else if (c->schedule == STA_SCHED_COOP) sta::launch_coop_pass(c->dc, c->hs, st, ev);
     else sta::launch_level_pass(c->dc, c->hs, st, ev);
 }
 
@@ -236,8 +237,9 @@ sta_status create_from_plan(sta_ctx *c, int device)
     d.rbox = dev_alloc<float4>(c, d.rbox_len);
     CK(cudaMemset(d.fbox, 0xFF, std::max<size_t>(1, d.fbox_len) * sizeof(float4)));
     CK(cudaMemset(d.rbox, 0xFF, std::max<size_t>(1, d.rbox_len) * sizeof(float4)));
-    d.df_state = dev_alloc<unsigned>(c, 4);
-    CK(cudaMemset(d.df_state, 0, 4 * sizeof(unsigned)));
+    d.df_state = dev_alloc<unsigned>(c, sta::kDfStateWords);
+    CK(cudaMemset(d.df_state, 0, sta::kDfStateWords * sizeof(unsigned)));
+    d.stage_ptr = upload(c, pl.stage_ptr);
     d.ep_begin = pl.P - pl.E;
     d.hold_item = -1;
     d.spin_limit = 1LL << 23;
@@ -245,16 +247,47 @@ sta_status create_from_plan(sta_ctx *c, int device)
         // a warp works on 8 / KL items, 4 * KL lanes each (KL corners side by side)
         d.KL = pl.K >= 8 ? 8 : pl.K >= 4 ? 4 : pl.K >= 2 ? 2 : 1;
         const int32_t kChunkItems = 8 / d.KL;
-        std::vector<int32_t> flo, fhi, blo, bhi;
+        // Forward work list: the item chunks of each level, and after the
+        // chunks of level s the endpoints whose driver sits at level
+        // s - kEpLag (so an endpoint is taken once its driver is about done,
+        // not after every level).  Endpoint chunks hold positions I + i of
+        // ep_order, the endpoints stably sorted by driver level.
+        constexpr int32_t kEpLag = 3;
+        std::vector<int32_t> item_level(pl.I), out_item(pl.P, -1);
         for (int32_t s = 0; s < pl.S; ++s)
+            for (int32_t g = pl.stage_ptr[s]; g < pl.stage_ptr[s + 1]; ++g) item_level[g] = s;
+        for (int32_t g = 0; g < pl.I; ++g) {
+            const int32_t t = pl.item_type[g], p0 = pl.item_pin0[g];
+            out_item[t < 0 ? p0 : (pl.type_kind[t] == 1 ? p0 + 1 : p0 + pl.type_nin[t])] = g;
+        }
+        std::vector<int32_t> ep_level(pl.E), ep_order(pl.E);
+        for (int32_t e = 0; e < pl.E; ++e) {
+            const int32_t drv = pl.drv_of[pl.ep_pin[e]];
+            ep_level[e] = drv >= 0 && out_item[drv] >= 0 ? item_level[out_item[drv]] : 0;
+            ep_order[e] = e;
+        }
+        std::stable_sort(ep_order.begin(), ep_order.end(),
+                         [&](int32_t a, int32_t b) { return ep_level[a] < ep_level[b]; });
+        std::vector<int32_t> flo, fhi, blo, bhi;
+        int32_t ep_pos = 0;
+        auto push_eps = [&](int32_t max_level) {
+            int32_t end = ep_pos;
+            while (end < pl.E && ep_level[ep_order[end]] <= max_level) ++end;
+            for (int32_t e = ep_pos; e < end; e += kChunkItems) {
+                flo.push_back(pl.I + e);
+                fhi.push_back(pl.I + std::min(e + kChunkItems, end));
+            }
+            ep_pos = end;
+        };
+        for (int32_t s = 0; s < pl.S; ++s) {
             for (int32_t g = pl.stage_ptr[s]; g < pl.stage_ptr[s + 1]; g += kChunkItems) {
                 flo.push_back(g);
                 fhi.push_back(std::min(g + kChunkItems, pl.stage_ptr[s + 1]));
             }
-        for (int32_t e = 0; e < pl.E; e += kChunkItems) {
-            flo.push_back(pl.I + e);
-            fhi.push_back(pl.I + std::min(e + kChunkItems, pl.E));
+            push_eps(s - kEpLag);
         }
+        push_eps(pl.S);
+        d.ep_order = upload(c, ep_order);
         for (int32_t s = pl.S - 1; s >= 0; --s)
             for (int32_t g = pl.stage_ptr[s]; g < pl.stage_ptr[s + 1]; g += kChunkItems) {
                 blo.push_back(g);
@@ -285,6 +318,11 @@ int32_t launches_per_update(const sta_ctx *c)
         n += 1;                                  // epoch / counter reset
         n += c->dc.n_fwd_chunks > 0;
         n += c->dc.n_bwd_chunks > 0;
+        n += (c->hs.n_red_chunks > 0) + 1;       // two-stage reduction
+        return n;
+    }
+    if (c->schedule == STA_SCHED_COOP) {
+        n += 2;                                  // barrier reset, all levels in one launch
         n += (c->hs.n_red_chunks > 0) + 1;       // two-stage reduction
         return n;
     }
@@ -500,14 +538,14 @@ sta_status sta_set_clock(sta_ctx *c, float period_ns)
 sta_status sta_set_schedule(sta_ctx *c, int32_t schedule, int32_t param)
 {
     if (!c) return STA_EINVAL;
-    if (schedule != STA_SCHED_LEVEL && schedule != STA_SCHED_DATAFLOW)
+    if (schedule != STA_SCHED_LEVEL && schedule != STA_SCHED_DATAFLOW && schedule != STA_SCHED_COOP)
         return fail(c, STA_EINVAL, "unknown schedule");
     if (schedule == STA_SCHED_LEVEL && param != 0 && (param < 32 || param > 1024 || param % 32))
         return fail(c, STA_EINVAL, "threads per block must be a multiple of 32 in [32, 1024]");
-    if (schedule == STA_SCHED_DATAFLOW && (param < 0 || param > 65535))
+    if (schedule != STA_SCHED_LEVEL && (param < 0 || param > 65535))
         return fail(c, STA_EINVAL, "persistent grid size must be in [0, 65535] (0 = from occupancy)");
-    if (schedule == STA_SCHED_DATAFLOW && sta::dataflow_smem_bytes(c->plan.T) > 200 * 1024)
-        return fail(c, STA_EINVAL, "cell library too large for the dataflow schedule's shared-memory copy");
+    if (schedule != STA_SCHED_LEVEL && sta::dataflow_smem_bytes(c->plan.T) > 200 * 1024)
+        return fail(c, STA_EINVAL, "cell library too large for the persistent schedules' shared-memory copy");
     try {
         CK(cudaSetDevice(c->device));
         drop_graph(c);
@@ -518,6 +556,12 @@ sta_status sta_set_schedule(sta_ctx *c, int32_t schedule, int32_t param)
     c->sched_param = param;
     if (schedule == STA_SCHED_LEVEL) {
         c->hs.threads = param ? param : 128;
+    } else if (schedule == STA_SCHED_COOP) {
+        const cudaError_t e = sta::coop_prepare(c->hs, c->dc.gamma > 0.f, param);
+        if (e != cudaSuccess) {
+            c->schedule = STA_SCHED_LEVEL;
+            return fail(c, STA_ECUDA, std::string("cooperative set-up: ") + cudaGetErrorString(e));
+        }
     } else {
         const cudaError_t e = sta::dataflow_prepare(c->hs, c->dc.gamma > 0.f, param);
         if (e != cudaSuccess) {
@@ -596,7 +640,8 @@ sta_status sta_autotune(sta_ctx *c, void *stream, int32_t trials, int32_t force,
             CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device));
             std::vector<std::pair<int, int>> cand = {{STA_SCHED_LEVEL, 64}, {STA_SCHED_LEVEL, 128},
                                                      {STA_SCHED_LEVEL, 256}, {STA_SCHED_DATAFLOW, 0},
-                                                     {STA_SCHED_DATAFLOW, sms}, {STA_SCHED_DATAFLOW, 2 * sms}};
+                                                     {STA_SCHED_DATAFLOW, sms}, {STA_SCHED_DATAFLOW, 2 * sms},
+                                                     {STA_SCHED_COOP, 0}, {STA_SCHED_COOP, sms}};
             cudaEvent_t e0, e1;
             CK(cudaEventCreate(&e0));
             CK(cudaEventCreate(&e1));

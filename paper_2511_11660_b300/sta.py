@@ -20,7 +20,7 @@ from .build import LIB
 OK, EINVAL, ECYCLE, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(7)
 HOST, DEVICE = 0, 1
 AT, SLEW, RAT, SLACK = 0, 1, 2, 3
-SCHED_LEVEL, SCHED_DATAFLOW = 0, 1
+SCHED_LEVEL, SCHED_DATAFLOW, SCHED_COOP = 0, 1, 2
 
 
 class StaError(RuntimeError):

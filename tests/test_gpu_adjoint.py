@@ -55,9 +55,10 @@ def test_objective_and_gradient_small(w):
     check_grad(g, g0)
 
 
-def test_level_and_dataflow_forward_give_the_same_gradient():
+@pytest.mark.parametrize("schedule", [sta.SCHED_DATAFLOW, sta.SCHED_COOP], ids=["dataflow", "coop"])
+def test_every_forward_schedule_gives_the_same_gradient(schedule):
     d = placed(2000, 15, 4)
-    a = gpu_grad(d, schedule=sta.SCHED_DATAFLOW)
+    a = gpu_grad(d, schedule=schedule)
     b = gpu_grad(d, schedule=sta.SCHED_LEVEL)
     assert a[0] == b[0]
     np.testing.assert_allclose(a[2], b[2], rtol=1e-9, atol=1e-12 * np.abs(b[2]).max())

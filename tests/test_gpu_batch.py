@@ -30,7 +30,7 @@ def designs(corners=2):
             for i, (n, dep) in enumerate([(300, 8), (2000, 25), (800, 12), (5000, 30), (40, 3)])]
 
 
-@pytest.mark.parametrize("schedule", [sta.SCHED_LEVEL, sta.SCHED_DATAFLOW])
+@pytest.mark.parametrize("schedule", [sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP])
 def test_batch_equals_separate_contexts(schedule):
     ds = designs()
     bctx = sta.Context(None, batch=ds)

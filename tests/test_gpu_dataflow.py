@@ -46,8 +46,7 @@ def same(a, b):
     assert a["report"] == b["report"]
 
 
-@pytest.mark.parametrize("case", ["tiny", "corners", "star", "smooth", "fixed", "big_rc"])
-def test_dataflow_matches_level_and_oracle(case):
+def _case(case):
     if case == "tiny":
         d = synth.workload("tiny", seed=1)
         d["period_ns"], _ = tune_period(d)
@@ -66,26 +65,39 @@ def test_dataflow_matches_level_and_oracle(case):
         d = synth.make_design(400, 6, seed=9, rc_nodes=(2000, 3000))
         d["rc_R"] = (d["rc_R"] * 0.1).astype(np.float32)
         d["rc_C"] = (d["rc_C"] * 0.01).astype(np.float32)
-    g = run(d, sta.SCHED_DATAFLOW)
+    return d
+
+
+CASES = ["tiny", "corners", "star", "smooth", "fixed", "big_rc"]
+
+
+@pytest.mark.parametrize("schedule", [sta.SCHED_DATAFLOW, sta.SCHED_COOP], ids=["dataflow", "coop"])
+@pytest.mark.parametrize("case", CASES)
+def test_persistent_schedules_match_level_and_oracle(case, schedule):
+    d = _case(case)
+    g = run(d, schedule)
     same(g, run(d, sta.SCHED_LEVEL))
     ref = oracle.sta(d)
     check_all(d, g, ref, exact_viol=case in ("tiny", "star", "smooth") and _hold_margin_ok(ref))
 
 
+@pytest.mark.parametrize("schedule", [sta.SCHED_DATAFLOW, sta.SCHED_COOP], ids=["dataflow", "coop"])
 @pytest.mark.parametrize("blocks", [1, 3, 148])
-def test_small_persistent_grids_make_progress(blocks):
-    """One resident block (8 warps) must still finish: chunks are taken in
-    order and only wait for earlier chunks."""
+def test_small_persistent_grids_make_progress(blocks, schedule):
+    """One resident block (8 warps) must still finish: dataflow chunks are
+    taken in order and only wait for earlier chunks; the cooperative grid
+    strides over every level whatever its size."""
     d = synth.make_design(5000, 40, seed=11, period_ns=2.5)
-    same(run(d, sta.SCHED_DATAFLOW, blocks), run(d, sta.SCHED_LEVEL))
+    same(run(d, schedule, blocks), run(d, sta.SCHED_LEVEL))
 
 
-def test_degenerate_designs_dataflow():
+@pytest.mark.parametrize("schedule", [sta.SCHED_DATAFLOW, sta.SCHED_COOP], ids=["dataflow", "coop"])
+def test_degenerate_designs_persistent(schedule):
     lib = synth.make_library(1)
     b = synth.Builder(lib)
     b.po(b.pi())
     d = b.design(period_ns=0.3)
-    same(run(d, sta.SCHED_DATAFLOW), run(d, sta.SCHED_LEVEL))
+    same(run(d, schedule), run(d, sta.SCHED_LEVEL))
     b = synth.Builder(lib)
     x = b.pi()
     q = b.cell("DFF", [x])
@@ -94,11 +106,11 @@ def test_degenerate_designs_dataflow():
     b.cell("BUF", [q2])
     b.po(q2)
     d = b.design(period_ns=0.2)
-    g = run(d, sta.SCHED_DATAFLOW)
+    g = run(d, schedule)
     same(g, run(d, sta.SCHED_LEVEL))
     check_all(d, g, oracle.sta(d), exact_viol=False)
     d = synth.make_design(1, 1, seed=3)
-    same(run(d, sta.SCHED_DATAFLOW), run(d, sta.SCHED_LEVEL))
+    same(run(d, schedule), run(d, sta.SCHED_LEVEL))
 
 
 def test_repeated_dataflow_updates_are_identical():
@@ -140,15 +152,40 @@ def test_wait_limit_reports_timeout_and_context_recovers():
     ctx.close()
 
 
-def test_scale_design_dataflow_full_size():
-    """The 1M-cell workload under the dataflow schedule, against the oracle
-    and bit-identical to the level schedule."""
+def test_coop_barrier_wait_limit_reports_timeout_and_context_recovers():
+    """A one-poll limit on the grid barrier: blocks that reach a barrier
+    before the last one arrives give up at once, the update reports
+    STA_ETIMEOUT, and the same context then runs a normal, correct pass."""
+    d = synth.make_design(20000, 60, seed=5, period_ns=2.5)
+    ref = oracle.sta(d)
+    ctx = sta.Context(d)
+    ctx.set_schedule(sta.SCHED_COOP)
+    ctx.update_timing()
+    ctx.sync()
+    ctx.set_wait_limit(1)
+    ctx.update_timing()
+    with pytest.raises(sta.StaError) as ei:
+        ctx.sync()
+    assert ei.value.status == sta.ETIMEOUT
+    ctx.set_wait_limit(1 << 23)
+    ctx.update_timing()
+    ctx.sync()
+    assert_close("at", ctx.get_pin_state(sta.AT), ref["at"])
+    assert_close("slack", ctx.get_pin_state(sta.SLACK), ref["slack"])
+    ctx.close()
+
+
+def test_scale_design_persistent_full_size():
+    """The 1M-cell workload under the dataflow and cooperative schedules,
+    against the oracle and bit-identical to the level schedule."""
     d = synth.workload("scale", seed=0)
     d["period_ns"], _ = tune_period(d)
-    g = run(d, sta.SCHED_DATAFLOW)
-    same(g, run(d, sta.SCHED_LEVEL))
+    lv = run(d, sta.SCHED_LEVEL)
     ref = oracle.sta(d)
-    check_all(d, g, ref, exact_viol=_hold_margin_ok(ref))
+    for schedule in (sta.SCHED_DATAFLOW, sta.SCHED_COOP):
+        g = run(d, schedule)
+        same(g, lv)
+        check_all(d, g, ref, exact_viol=_hold_margin_ok(ref))
 
 
 def test_autotune_selects_a_schedule_and_keeps_results():
@@ -157,7 +194,7 @@ def test_autotune_selects_a_schedule_and_keeps_results():
     ref = oracle.sta(d)
     ctx = sta.Context(d)
     sch, par, ms = ctx.autotune(trials=3)
-    assert sch in (sta.SCHED_LEVEL, sta.SCHED_DATAFLOW) and ms > 0
+    assert sch in (sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP) and ms > 0
     assert_close("at", ctx.get_pin_state(sta.AT), ref["at"])
     assert_close("slack", ctx.get_pin_state(sta.SLACK), ref["slack"])
     t0 = time.perf_counter()
