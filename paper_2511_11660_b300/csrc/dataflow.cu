@@ -312,8 +312,8 @@ void launch_coop_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cuda
     k_coop_begin<<<1, 32, 0, st>>>(c);
     if (h.placed) {
         if (c.I > 0) launch_net_star(c, st);
-    } else if (h.n_tiles > 0) {
-        launch_net_tree(c, h, st);
+    } else if (h.rc) {
+        launch_net_tree(c, st);
     }
     if (ev) cudaEventRecord(ev[1], st);
     if (c.I > 0 || c.E > 0) {
@@ -341,8 +341,8 @@ void launch_dataflow_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, 
     k_df_begin<<<1, 32, 0, st>>>(c);
     if (h.placed) {
         if (c.I > 0) launch_net_star(c, st);
-    } else if (h.n_tiles > 0) {
-        launch_net_tree(c, h, st);
+    } else if (h.rc) {
+        launch_net_tree(c, st);
     }
     if (ev) cudaEventRecord(ev[1], st);
     if (c.n_fwd_chunks > 0) {

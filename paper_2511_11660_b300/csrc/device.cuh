@@ -10,9 +10,8 @@
 namespace sta {
 
 constexpr int kLutStride = 80;   // floats per packed table, see plan.cpp
-constexpr int kRcTileNodes = 1024;
-constexpr int kRcTileSinks = 1024;
-constexpr int kRcTileNets = 128;
+constexpr int kRcColNodes = 16;    // RC nets up to this size are swept in shared memory (as plan.h)
+constexpr int kRcThreads = 128;    // threads (nets) per block of the RC sweep
 constexpr int kRedThreads = 256;   // threads of the reduction kernels
 constexpr int kDfStateWords = 16;  // schedule state words (see DevCtx::df_state)
 constexpr int kRedChunk = 4096;    // endpoints per first-stage reduction block
@@ -33,7 +32,7 @@ struct DevCtx {
     const int32_t *item_pin0, *item_type, *item_cell;
     const int32_t *fo_ptr, *fo_pin, *fo_node;   // sinks of each item's output net
     const float *fo_cap;
-    const int32_t *rc_ptr, *rc_parent, *tile_item;
+    const int32_t *rc_ptr, *rc_parent;
     const float *rc_R, *rc_C;
     const int32_t *drv_of, *pin_cell;
     const float *port_xy, *cell_xy;
@@ -48,7 +47,7 @@ struct DevCtx {
     const int32_t *red_design_chunk;            // [n_designs+1] chunk ranges per design
     double *red_partial;                        // [n_red_chunks][K][6] scratch
     unsigned *err;
-    float *scratch_a, *scratch_b;               // RC sweeps of nets larger than a tile
+    float *scratch_a, *scratch_b;               // [NN] RC sweeps of nets larger than kRcColNodes
     // dataflow schedule: mailboxes by epoch parity, NaN until published
     float4 *fbox;                               // [2][P][K][2] arrival, slew of driver pins
     float4 *rbox;                               // [2][P][K]    required time of gate input pins

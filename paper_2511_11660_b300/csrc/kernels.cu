@@ -17,70 +17,111 @@ static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
 // ------------------------------------------------------------------ nets
 
-// RC trees.  One block per tile of consecutive items whose RC nodes and
-// sinks fit in shared memory (one thread per net); a tile holding a single
-// larger net sweeps it in global scratch instead.  Per corner: Cdown
-// (reverse sweep), Elmore D (forward), M = C*D summed over the subtree
-// (reverse), beta (forward), var = 2*beta - D^2.  Units: Ohm*fF -> 1e-6 ns.
-__global__ void __launch_bounds__(kRcTileNets) k_net_tree(const DevCtx c)
+// RC trees, one thread per item's net.  A net of at most kRcColNodes nodes
+// lives in a shared-memory column of its thread: node i at [i * kRcThreads +
+// thread], so every access of the sweeps -- the parent's entry included --
+// falls in the thread's own bank.  The loads that fill the column are
+// unrolled over the column height (predicated on the net size), so all of a
+// thread's loads are in flight together.  Larger nets sweep the same way in
+// global scratch at their node offsets.  Per corner (node capacitance =
+// scaled wire C + sink pin caps, Ohm * fF -> 1e-6 ns):
+//   Cdown (reverse sweep), load = Cdown at the root;
+//   D_i = D_parent + R_i Cdown_i and, in the same sweep, C_i D_i;
+//   M = subtree sums of C D (reverse sweep);
+//   beta_i = beta_parent + R_i M_i; var = 2 beta - D^2 at the sinks.
+struct ColRef {
+    float *base;
+    int stride;
+    __device__ __forceinline__ float &operator[](int i) const { return base[i * stride]; }
+};
+
+__global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
 {
-    __shared__ int16_t s_par[kRcTileNodes];
-    __shared__ float s_R[kRcTileNodes], s_C[kRcTileNodes], s_A[kRcTileNodes], s_B[kRcTileNodes];
-    __shared__ int16_t s_fnode[kRcTileSinks];
-    __shared__ float s_fcap[kRcTileSinks];
-    __shared__ int32_t s_fpin[kRcTileSinks];
-    const int g0 = c.tile_item[blockIdx.x], g1 = c.tile_item[blockIdx.x + 1];
-    const int n0 = c.rc_ptr[g0], nn = c.rc_ptr[g1] - n0;
-    const int s0 = c.fo_ptr[g0], ns = c.fo_ptr[g1] - s0;
-    const bool big = nn > kRcTileNodes || ns > kRcTileSinks;
-    if (!big) {
-        for (int i = threadIdx.x; i < nn; i += blockDim.x) {
-            s_par[i] = (int16_t)c.rc_parent[n0 + i];
-            s_R[i] = c.rc_R[n0 + i];
-            s_C[i] = c.rc_C[n0 + i];
-        }
-        for (int i = threadIdx.x; i < ns; i += blockDim.x) {
-            s_fnode[i] = (int16_t)c.fo_node[s0 + i];
-            s_fcap[i] = c.fo_cap[s0 + i];
-            s_fpin[i] = c.fo_pin[s0 + i];
-        }
+    __shared__ int8_t s_par[kRcColNodes * kRcThreads];
+    __shared__ float s_R[kRcColNodes * kRcThreads], s_C[kRcColNodes * kRcThreads];
+    __shared__ float s_A[kRcColNodes * kRcThreads], s_B[kRcColNodes * kRcThreads];
+    const int t = threadIdx.x;
+    const int g = blockIdx.x * kRcThreads + t;
+    if (g >= c.I) return;
+    const int n0 = c.rc_ptr[g], n = c.rc_ptr[g + 1] - n0;
+    const int f0 = c.fo_ptr[g], f1 = c.fo_ptr[g + 1];
+    if (n == 0) return;
+    const bool col = n <= kRcColNodes;
+    if (col) {
+        int8_t pv[kRcColNodes];
+        float rv[kRcColNodes], cv[kRcColNodes];
+#pragma unroll
+        for (int i = 0; i < kRcColNodes; ++i)
+            if (i < n) {
+                pv[i] = (int8_t)__ldg(c.rc_parent + n0 + i);
+                rv[i] = __ldg(c.rc_R + n0 + i);
+                cv[i] = __ldg(c.rc_C + n0 + i);
+            }
+#pragma unroll
+        for (int i = 0; i < kRcColNodes; ++i)
+            if (i < n) {
+                s_par[i * kRcThreads + t] = pv[i];
+                s_R[i * kRcThreads + t] = rv[i];
+                s_C[i * kRcThreads + t] = cv[i];
+            }
     }
-    __syncthreads();
-    const int g = g0 + threadIdx.x;
-    if (g >= g1) return;
-    const int b = c.rc_ptr[g] - n0, e = c.rc_ptr[g + 1] - n0;
-    if (e == b) return;
-    const int f0 = c.fo_ptr[g] - s0, f1 = c.fo_ptr[g + 1] - s0;
-    float *A = big ? c.scratch_a + n0 : s_A;
-    float *B = big ? c.scratch_b + n0 : s_B;
-    auto par = [&](int i) -> int { return big ? c.rc_parent[n0 + i] : s_par[i]; };
-    auto Rv = [&](int i) -> float { return big ? c.rc_R[n0 + i] : s_R[i]; };
-    auto Cv = [&](int i) -> float { return big ? c.rc_C[n0 + i] : s_C[i]; };
-    auto fnode = [&](int q) -> int { return big ? c.fo_node[s0 + q] : s_fnode[q]; };
-    auto fcap = [&](int q) -> float { return big ? c.fo_cap[s0 + q] : s_fcap[q]; };
-    auto fpin = [&](int q) -> int { return big ? c.fo_pin[s0 + q] : s_fpin[q]; };
-    const int t = c.item_type[g];
-    const int z = item_out_pin(c, t, c.item_pin0[g]);
+    const ColRef A = col ? ColRef{s_A + t, kRcThreads} : ColRef{c.scratch_a + n0, 1};
+    const ColRef B = col ? ColRef{s_B + t, kRcThreads} : ColRef{c.scratch_b + n0, 1};
+    auto par = [&](int i) -> int { return col ? s_par[i * kRcThreads + t] : __ldg(c.rc_parent + n0 + i); };
+    auto Rv = [&](int i) -> float { return col ? s_R[i * kRcThreads + t] : __ldg(c.rc_R + n0 + i); };
+    auto Cv = [&](int i) -> float { return col ? s_C[i * kRcThreads + t] : __ldg(c.rc_C + n0 + i); };
+    const int z = item_out_pin(c, c.item_type[g], c.item_pin0[g]);
     const int K = c.K;
     for (int k = 0; k < K; ++k) {
         const float f = __ldg(c.rc_scale + k);
-        for (int i = b; i < e; ++i) A[i] = f * Cv(i);
-        for (int q = f0; q < f1; ++q) A[b + fnode(q)] += 1e3f * fcap(q);
-        for (int i = b; i < e; ++i) B[i] = A[i];                       // node capacitance
-        for (int i = e - 1; i > b; --i) A[b + par(i)] += A[i];          // Cdown
-        c.load[(size_t)z * K + k] = 1e-3f * A[b];
-        A[b] = 0.f;
-        for (int i = b + 1; i < e; ++i) A[i] = A[b + par(i)] + f * Rv(i) * A[i];   // Elmore D
-        for (int i = b; i < e; ++i) B[i] *= A[i];                      // C_i D_i
-        for (int i = e - 1; i > b; --i) B[b + par(i)] += B[i];          // M
-        B[b] = 0.f;
-        for (int i = b + 1; i < e; ++i) B[i] = B[b + par(i)] + f * Rv(i) * B[i];   // beta
-        for (int q = f0; q < f1; ++q) {
-            const int node = b + fnode(q);
-            const int s = fpin(q);
-            const float Dn = A[node];
-            c.netD[(size_t)s * K + k] = 1e-6f * Dn;
-            c.netV[(size_t)s * K + k] = 1e-12f * fmaxf(2.f * B[node] - Dn * Dn, 0.f);
+        for (int i = 0; i < n; ++i) {
+            const float ci = f * Cv(i);
+            A[i] = ci;
+            B[i] = ci;
+        }
+        for (int q0 = f0; q0 < f1; q0 += 4) {
+            int nd[4];
+            float cp[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (q0 + u < f1) {
+                    nd[u] = __ldg(c.fo_node + q0 + u);
+                    cp[u] = 1e3f * __ldg(c.fo_cap + q0 + u);
+                }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (q0 + u < f1) {
+                    A[nd[u]] += cp[u];
+                    B[nd[u]] += cp[u];                                   // node capacitance
+                }
+        }
+        for (int i = n - 1; i > 0; --i) A[par(i)] += A[i];              // Cdown
+        c.load[(size_t)z * K + k] = 1e-3f * A[0];
+        A[0] = 0.f;
+        B[0] = 0.f;
+        for (int i = 1; i < n; ++i) {
+            const float d = A[par(i)] + f * Rv(i) * A[i];               // Elmore D
+            A[i] = d;
+            B[i] *= d;                                                   // C_i D_i
+        }
+        for (int i = n - 1; i > 0; --i) B[par(i)] += B[i];              // M
+        B[0] = 0.f;
+        for (int i = 1; i < n; ++i) B[i] = B[par(i)] + f * Rv(i) * B[i];   // beta
+        for (int q0 = f0; q0 < f1; q0 += 4) {
+            int nd[4], sp[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (q0 + u < f1) {
+                    nd[u] = __ldg(c.fo_node + q0 + u);
+                    sp[u] = __ldg(c.fo_pin + q0 + u);
+                }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                if (q0 + u < f1) {
+                    const float Dn = A[nd[u]];
+                    c.netD[(size_t)sp[u] * K + k] = 1e-6f * Dn;
+                    c.netV[(size_t)sp[u] * K + k] = 1e-12f * fmaxf(2.f * B[nd[u]] - Dn * Dn, 0.f);
+                }
         }
     }
 }
@@ -311,9 +352,9 @@ __global__ void k_gather_f32(const float *__restrict__ src, const int32_t *__res
 
 void launch_net_star(const DevCtx &c, cudaStream_t st) { k_net_star<<<nblk(c.I, 128), 128, 0, st>>>(c); }
 
-void launch_net_tree(const DevCtx &c, const HostSched &h, cudaStream_t st)
+void launch_net_tree(const DevCtx &c, cudaStream_t st)
 {
-    k_net_tree<<<h.n_tiles, kRcTileNets, 0, st>>>(c);
+    if (c.I > 0) k_net_tree<<<nblk(c.I, kRcThreads), kRcThreads, 0, st>>>(c);
 }
 
 void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev)
@@ -321,8 +362,8 @@ void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cud
     if (ev) cudaEventRecord(ev[0], st);
     if (h.placed) {
         if (c.I > 0) launch_net_star(c, st);
-    } else if (h.n_tiles > 0) {
-        launch_net_tree(c, h, st);
+    } else if (h.rc) {
+        launch_net_tree(c, st);
     }
     if (ev) cudaEventRecord(ev[1], st);
     const int tpb = h.threads > 0 ? h.threads : 128;

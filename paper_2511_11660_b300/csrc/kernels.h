@@ -12,7 +12,7 @@ namespace sta {
 struct HostSched {
     int S = 0;
     std::vector<int32_t> stage_ptr;   // host copy of the level offsets
-    int n_tiles = 0;                  // RC tiles (tree mode)
+    bool rc = false;                  // RC trees to sweep (tree mode with nodes)
     bool placed = false;
     int threads = 128;                // threads per block of the level kernels
     int n_red_chunks = 0;             // first-stage reduction blocks
@@ -30,8 +30,8 @@ struct HostSched {
 // after the reduction.
 void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev = nullptr);
 
-// Net delay calculation: RC trees (tiles in shared memory) or star trees.
-void launch_net_tree(const DevCtx &c, const HostSched &h, cudaStream_t st);
+// Net delay calculation: RC trees (one thread per net) or star trees.
+void launch_net_tree(const DevCtx &c, cudaStream_t st);
 void launch_net_star(const DevCtx &c, cudaStream_t st);
 
 // Dataflow schedule: one persistent kernel per pass (see dataflow.cu).

@@ -412,28 +412,10 @@ void build(const sta_design_desc *d, Plan &pl)
             }
         }
     }
-    // ---- RC tiles: consecutive items, <= kTileNets items and <= kTileNodes nodes
-    pl.tile_item.assign(1, 0);
-    pl.n_big_tiles = 0;
-    if (!pl.placed) {
-        int32_t g = 0;
-        while (g < I) {
-            int32_t h = g, nodes = 0, sinks = 0;
-            while (h < I && h - g < kTileNets) {
-                const int32_t nn = pl.rc_ptr[h + 1] - pl.rc_ptr[h];
-                const int32_t ns = pl.fo_ptr[h + 1] - pl.fo_ptr[h];
-                if ((nodes + nn > kTileNodes || sinks + ns > kTileSinks) && h > g) break;
-                nodes += nn;
-                sinks += ns;
-                ++h;
-                if (nodes > kTileNodes || sinks > kTileSinks) { ++pl.n_big_tiles; break; }
-            }
-            pl.tile_item.push_back(h);
-            g = h;
-        }
-    } else {
-        for (int32_t g = 0; g < I; g += kTileNets) pl.tile_item.push_back(std::min(I, g + kTileNets));
-    }
+    // ---- RC nets too large for the shared-memory sweep
+    pl.n_big_nets = 0;
+    if (!pl.placed)
+        for (int32_t g = 0; g < I; ++g) pl.n_big_nets += pl.rc_ptr[g + 1] - pl.rc_ptr[g] > kColNodes;
     // ---- arc count
     pl.cell_arcs = 0;
     for (int32_t c = 0; c < C; ++c) {

@@ -19,9 +19,7 @@ namespace sta {
 constexpr int kNldm = 7;          // 7x7 NLDM tables
 constexpr int kMaxSlot = 3;       // at most three inputs per cell
 constexpr int kTabStride = 80;    // floats per packed table (see packLut)
-constexpr int kTileNets = 128;    // nets per RC tile (one thread each)
-constexpr int kTileNodes = 1024;  // RC nodes staged in shared memory per tile
-constexpr int kTileSinks = 1024;  // net sinks staged in shared memory per tile
+constexpr int kColNodes = 16;     // RC nets up to this many nodes are swept in shared memory
 
 enum { kPinPI = 0, kPinPO = 1, kPinIN = 2, kPinOUT = 3, kPinD = 4, kPinCK = 5, kPinQ = 6 };
 enum { kSenseNone = -1, kSensePos = 0, kSenseNeg = 1, kSenseNon = 2, kSenseRise = 3 };
@@ -60,8 +58,7 @@ struct Plan {
     std::vector<int32_t> rc_parent;          // [NN] local parent
     std::vector<float> rc_R, rc_C;           // [NN]
     std::vector<int64_t> rc_src;             // [NN] caller node index
-    std::vector<int32_t> tile_item;          // [n_tiles+1] RC tiles over items
-    int32_t n_big_tiles = 0;                 // tiles holding one net larger than a shared-memory tile
+    int32_t n_big_nets = 0;                  // RC nets of more than kColNodes nodes (swept in global scratch)
     // pins
     std::vector<int32_t> drv_of;             // [P] internal driver of a sink pin, -1
     std::vector<int32_t> gpu_of;             // [P] caller pin -> internal pin

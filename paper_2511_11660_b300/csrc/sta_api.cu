@@ -160,7 +160,6 @@ sta_status create_from_plan(sta_ctx *c, int device)
     d.fo_node = upload(c, pl.fo_node);
     d.fo_cap = upload(c, pl.fo_cap);
     d.rc_ptr = upload(c, pl.rc_ptr);
-    d.tile_item = upload(c, pl.tile_item);
     d.rc_parent = upload(c, pl.rc_parent);
     d.rc_R = upload(c, pl.rc_R);
     d.rc_C = upload(c, pl.rc_C);
@@ -208,14 +207,14 @@ sta_status create_from_plan(sta_ctx *c, int device)
     }
     d.err = dev_alloc<unsigned>(c, 1);
     CK(cudaMemset(d.err, 0, sizeof(unsigned)));
-    if (pl.n_big_tiles > 0) {
+    if (pl.n_big_nets > 0) {
         d.scratch_a = dev_alloc<float>(c, (size_t)pl.NN);
         d.scratch_b = dev_alloc<float>(c, (size_t)pl.NN);
     }
     HostSched &h = c->hs;
     h.S = pl.S;
     h.stage_ptr = pl.stage_ptr;
-    h.n_tiles = (int)pl.tile_item.size() - 1;
+    h.rc = !pl.placed && pl.NN > 0;
     h.placed = pl.placed;
     h.threads = 128;
     h.uniform = pl.uniform_axes;
@@ -313,7 +312,7 @@ int32_t launches_per_update(const sta_ctx *c)
     const Plan &pl = c->plan;
     int32_t n = 0;
     if (pl.placed) n += pl.I > 0;
-    else n += (int32_t)pl.tile_item.size() > 1;
+    else n += pl.NN > 0 && pl.I > 0;
     if (c->schedule == STA_SCHED_DATAFLOW) {
         n += 1;                                  // epoch / counter reset
         n += c->dc.n_fwd_chunks > 0;
