@@ -153,26 +153,34 @@ def byte_model(st: dict, K: int) -> dict:
     return {"net": net, "fwd": fwd, "bwd": bwd, "reduce": red, "total": net + fwd + bwd + red}
 
 
-def kernel_source_hash() -> str:
+# the source files that define each measured kernel (its code and everything it inlines)
+_PERSISTENT = ("dataflow.cu", "item.cuh", "device.cuh", "kernels.h")
+_LEVEL = ("kernels.cu", "item.cuh", "device.cuh", "kernels.h")
+KERNEL_SOURCES = {"k_df_forward": _PERSISTENT, "k_df_backward": _PERSISTENT, "k_coop_pass": _PERSISTENT,
+                  "k_net_tree": _LEVEL, "k_fwd_level": _LEVEL, "k_bwd_level": _LEVEL}
+
+
+def kernel_source_hash(kernel: str) -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2511_11660_b300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        if f.endswith((".cu", ".cuh", ".h", ".cpp")):
-            h.update(open(os.path.join(csrc, f), "rb").read())
+    for f in KERNEL_SOURCES[kernel]:
+        h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
 
 
 def measured_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary (profiles/traffic.txt),
-    if it was taken on the current kernel sources (else null)."""
+    if it was taken on the kernel's current sources (else null)."""
     p = os.path.join(ROOT, "profiles", "traffic.txt")
     try:
         lines = open(p).read().splitlines()
     except OSError:
         return None
+    if kernel not in KERNEL_SOURCES:
+        return None
     for ln in lines:
         f = ln.split()
-        if len(f) == 3 and not ln.startswith("#") and f[0] == kernel and f[1] == kernel_source_hash():
+        if len(f) == 3 and not ln.startswith("#") and f[0] == kernel and f[1] == kernel_source_hash(kernel):
             return float(f[2])
     return None
 
