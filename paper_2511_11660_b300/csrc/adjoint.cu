@@ -14,7 +14,8 @@
 // segment length L = |dx| + |dy| to the two cells it joins:
 //   dJ/dL = D_bar 1e-6 dD/dL + var_bar 1e-12 2 D dD/dL + load_bar 1e-3 c,
 //   D = r L (c L / 2 + Cpin) [Ohm fF], dD/dL = r (c L + Cpin).
-// The objective sums are FP64; the gradient accumulates with FP64 atomics.
+// Per-endpoint and per-segment terms are FP32; the objective sums are FP64
+// and the gradient accumulates with FP64 atomics.
 // Placement-driven timing optimisation consumes such gradients (the paper's
 // DREAMPlace integration uses pin slacks, Sec. IV-C); the paper itself has
 // no differentiable mode.
@@ -27,17 +28,22 @@ static inline int nblk2(long long n, int t) { return (int)((n + t - 1) / t); }
 
 constexpr int kDfThreadsA = 256;
 
-// smooth min of the two edges' setup margins of endpoint e at corner k (FP64)
-__device__ __forceinline__ double ep_smooth_slack(const DevCtx &c, int e, int k, double y[2])
+// Smooth min of the two edges' setup margins of endpoint e at corner k.
+// Per-endpoint terms are FP32 (the arrivals they start from are FP32); the
+// sums over endpoints and over the gradient are FP64.
+__device__ __forceinline__ float ep_smooth_slack(const DevCtx &c, int e, int k, float y[2])
 {
     const int p = c.ep_pin[e];
-    const double req = c.ep_is_d[e] ? (double)c.period - c.setup : (double)c.period;
+    const float req = c.ep_is_d[e] ? c.period - c.setup : c.period;
     const float4 a = c.at[(size_t)p * c.K + k];
     y[0] = req - a.z;
     y[1] = req - a.w;
-    const double g = c.gamma, m = fmin(y[0], y[1]);
-    return m - g * log(exp((m - y[0]) / g) + exp((m - y[1]) / g));
+    const float m = fminf(y[0], y[1]);
+    return m - c.gamma * logf(expf((m - y[0]) * c.inv_gamma) + expf((m - y[1]) * c.inv_gamma));
 }
+
+// softplus(z) = max(z, 0) + log1p(exp(-|z|))
+__device__ __forceinline__ float softplus_f(float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); }
 
 template <int NT>
 __device__ __forceinline__ double block_sum(double v, double *sh)
@@ -71,13 +77,13 @@ __global__ void __launch_bounds__(kRedThreads) k_obj_max_chunks(const DevCtx c)
 {
     __shared__ double sh[kRedThreads];
     const int b = blockIdx.x, k = blockIdx.y;
-    double v = -INFINITY;
+    float v = -INFINITY;
     for (int e = c.red_chunk_ptr[b] + threadIdx.x; e < c.red_chunk_ptr[b + 1]; e += kRedThreads) {
-        double y[2];
-        v = fmax(v, -ep_smooth_slack(c, e, k, y) / c.gamma);
+        float y[2];
+        v = fmaxf(v, -ep_smooth_slack(c, e, k, y) * c.inv_gamma);
     }
-    v = block_max<kRedThreads>(v, sh);
-    if (threadIdx.x == 0) c.red_partial[((size_t)b * c.K + k) * 6] = v;
+    const double vm = block_max<kRedThreads>((double)v, sh);
+    if (threadIdx.x == 0) c.red_partial[((size_t)b * c.K + k) * 6] = vm;
 }
 
 // stage 2: per corner, the global max
@@ -96,14 +102,13 @@ __global__ void __launch_bounds__(kRedThreads) k_obj_sum_chunks(const DevCtx c)
 {
     __shared__ double sh[kRedThreads];
     const int b = blockIdx.x, k = blockIdx.y;
-    const double mx = c.obj[k * 4 + 0], g = c.gamma;
+    const float mx = (float)c.obj[k * 4 + 0], g = c.gamma;
     double se = 0, st = 0;
     for (int e = c.red_chunk_ptr[b] + threadIdx.x; e < c.red_chunk_ptr[b + 1]; e += kRedThreads) {
-        double y[2];
-        const double s = ep_smooth_slack(c, e, k, y);
-        se += exp(-s / g - mx);
-        const double z = -s / g;   // softplus(z) = max(z, 0) + log1p(exp(-|z|))
-        st += -g * (fmax(z, 0.0) + log1p(exp(-fabs(z))));
+        float y[2];
+        const float z = -ep_smooth_slack(c, e, k, y) * c.inv_gamma;
+        se += (double)expf(z - mx);
+        st += (double)(-g * softplus_f(z));
     }
     se = block_sum<kRedThreads>(se, sh);
     st = block_sum<kRedThreads>(st, sh);
@@ -147,15 +152,16 @@ __global__ void k_adj_seed(const DevCtx c)
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= c.E) return;
     const int p = c.ep_pin[e];
-    const double g = c.gamma;
+    const float ig = c.inv_gamma;
+    const float wt = (float)c.w_tns, ww = (float)c.w_wns;
     for (int k = 0; k < c.K; ++k) {
-        double y[2];
-        const double s = ep_smooth_slack(c, e, k, y);
-        const double z = -s / g;
-        const double sig = z >= 0 ? 1.0 / (1.0 + exp(-z)) : exp(z) / (1.0 + exp(z));
-        const double dj = c.w_tns * sig + c.w_wns * exp(-s / g - c.obj[k * 4 + 0]) / c.obj[k * 4 + 1];
-        const double w0 = exp((s - y[0]) / g), w1 = exp((s - y[1]) / g);
-        c.adj[(size_t)p * c.K + k] = make_float4((float)(-dj * w0), (float)(-dj * w1), 0.f, 0.f);
+        float y[2];
+        const float s = ep_smooth_slack(c, e, k, y);
+        const float z = -s * ig;
+        const float sig = z >= 0.f ? 1.f / (1.f + expf(-z)) : expf(z) / (1.f + expf(z));
+        const float dj = wt * sig + ww * expf(z - (float)c.obj[k * 4 + 0]) / (float)c.obj[k * 4 + 1];
+        const float w0 = expf((s - y[0]) * ig), w1 = expf((s - y[1]) * ig);
+        c.adj[(size_t)p * c.K + k] = make_float4(-dj * w0, -dj * w1, 0.f, 0.f);
     }
 }
 
@@ -174,11 +180,16 @@ __device__ __forceinline__ float4 *abox_at(const DevCtx &c, int par, int pin, in
 
 struct AdjItem {
     int t, pin0, kind, nin, z, f0, f1;
+    // the lane's first corner, loaded ahead (written by the forward pass):
+    // the output's late slew of this lane's edge, its load, the clock slew
+    // (flip-flop) or the late arrival and slew of each input pin
+    float sz0, ld0, ain0[3][2], sin0[3][2];
 };
 
-__device__ __forceinline__ AdjItem adj_prep(const DevCtx &c, const int *tnin, const int *tkind, int g)
+__device__ __forceinline__ AdjItem adj_prep(const DevCtx &c, const int *tnin, const int *tkind, int g, int q)
 {
     AdjItem a;
+    const int K = c.K, kq = corner_lane(c);
     a.t = c.item_type[g];
     a.pin0 = c.item_pin0[g];
     a.kind = a.t >= 0 ? tkind[a.t] : -1;
@@ -186,19 +197,62 @@ __device__ __forceinline__ AdjItem adj_prep(const DevCtx &c, const int *tnin, co
     a.z = a.t < 0 ? a.pin0 : (a.kind == 1 ? a.pin0 + 1 : a.pin0 + a.nin);
     a.f0 = c.fo_ptr[g];
     a.f1 = c.fo_ptr[g + 1];
+    a.sz0 = ld_state(c.slew + (size_t)a.z * K + kq, 2 + (q >> 1));
+    a.ld0 = a.t >= 0 ? c.load[(size_t)a.z * K + kq] : 0.f;
+    const int nread = a.kind == 1 ? 1 : a.nin;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        const bool on = j < nread;
+        const size_t o = (size_t)(a.pin0 + j) * K + kq;
+        a.ain0[j][0] = on ? ld_state(c.at + o, 2) : 0.f;
+        a.ain0[j][1] = on ? ld_state(c.at + o, 3) : 0.f;
+        a.sin0[j][0] = on ? ld_state(c.slew + o, 2) : 0.f;
+        a.sin0[j][1] = on ? ld_state(c.slew + o, 3) : 0.f;
+    }
     return a;
 }
 
-// the adjoints of the lane's corners of every gate-input sink of the item's
-// net are complete (endpoint sinks were seeded by an earlier launch)
-__device__ __forceinline__ bool adj_probe(const DevCtx &c, const AdjItem &a, int par)
+// Lane q of a quad works on output edge rf = q >> 1, arrivals (q & 1 == 0)
+// or slews (q & 1 == 1).  Are the adjoints of every gate-input sink of the
+// item's net complete (all the lane's corners)?  For the lane's first corner
+// the same pass gathers the lane's adjoint of the output: the sum over the
+// sinks of dJ/dAT (arrival lanes) or of dJ/dslew * slew_z / slew_sink (slew
+// lanes, through slew_sink = sqrt(slew_z^2 + var)).  Sinks are read four at a
+// time, one component each; the caller's group_all covers the quad.
+// Endpoint sinks were seeded by an earlier launch.
+__device__ __forceinline__ bool adj_probe(const DevCtx &c, const AdjItem &a, int par, int q, float &abar)
 {
+    const int K = c.K, kq = corner_lane(c);
+    const int rf = q >> 1;
+    const bool slew_lane = (q & 1) != 0;
+    const int comp_q = slew_lane ? 2 + rf : rf;   // dJ/dAT rise, fall; dJ/dslew rise, fall
     bool ok = true;
-    for (int p = a.f0; p < a.f1 && ok; ++p) {
-        const int s = c.fo_pin[p];
-        if (s < c.ep_begin)
-            for (int k = corner_lane(c); k < c.K && ok; k += c.KL) ok = complete(ld_relaxed4(abox_at(c, par, s, k)));
+    float acc = 0.f;
+    for (int p0 = a.f0; p0 < a.f1; p0 += 4) {
+        int s[4];
+        float v[4], ss[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) s[u] = p0 + u < a.f1 ? __ldg(c.fo_pin + p0 + u) : -1;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (s[u] < 0) continue;
+            v[u] = s[u] < c.ep_begin ? ld_relaxed1(reinterpret_cast<const float *>(abox_at(c, par, s[u], kq)) + comp_q)
+                                     : ld_state(c.adj + (size_t)s[u] * K + kq, comp_q);
+            ss[u] = slew_lane ? ld_state(c.slew + (size_t)s[u] * K + kq, 2 + rf) : 1.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (s[u] < 0) continue;
+            ok = ok && v[u] == v[u];
+            acc += slew_lane ? v[u] * a.sz0 / ss[u] : v[u];
+        }
     }
+    for (int p = a.f0; p < a.f1 && ok; ++p) {
+        const int s = __ldg(c.fo_pin + p);
+        if (s < c.ep_begin)
+            for (int k = kq + c.KL; k < K && ok; k += c.KL) ok = complete(ld_relaxed4(abox_at(c, par, s, k)));
+    }
+    abar = acc;
     return ok;
 }
 
@@ -210,46 +264,45 @@ __device__ __forceinline__ float quad_sum(float v)
     return v;
 }
 
-constexpr int kMaxCornersPerLane = 16;
-
 // One item of the reverse sweep.  Lane q of a quad differentiates the merge
 // of output edge rf = q >> 1, of the arrivals (q & 1 == 0, delay tables) or
 // of the slews (q & 1 == 1, slew tables), for the quad's corners; the quad
 // sums the partials.  The segment gradients are summed over corners (and the
 // driver's over all its segments) before the FP64 atomics.
 template <bool UNIFORM, bool WAIT, class Lut>
-__device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const int *tsense, const AdjItem &a, int q,
-                                        int par)
+__device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const int *tsense, const AdjItem &a, int g,
+                                        int q, int par, float abar0)
 {
     const int t = a.t, pin0 = a.pin0, z = a.z, K = c.K, nin = a.nin;
     const int kq = corner_lane(c), KL = c.KL;
     const float ig = c.inv_gamma;
     const int rfo = q >> 1;
     const bool slew_lane = (q & 1) != 0;
-    float aload_k[kMaxCornersPerLane];
-    int nk = 0;
-    for (int k = kq; k < K; k += KL, ++nk) {
-        const float4 Sz = c.slew[(size_t)z * K + k];
-        // gather the sinks' adjoints through the net arcs (every lane)
-        float aA[2] = {0.f, 0.f}, aS[2] = {0.f, 0.f};
-        for (int p = a.f0; p < a.f1; ++p) {
-            const int s = c.fo_pin[p];
-            const float4 as = (WAIT && s < c.ep_begin) ? ld_relaxed4(abox_at(c, par, s, k)) : c.adj[(size_t)s * K + k];
-            const float4 Ss = c.slew[(size_t)s * K + k];
-            aA[0] += as.x;
-            aA[1] += as.y;
-            aS[0] += as.z * Sz.z / Ss.z;
-            aS[1] += as.w * Sz.w / Ss.w;
+    for (int k = kq; k < K; k += KL) {
+        const bool first = k == kq;
+        // the lane's adjoint of the output, gathered from the sinks through
+        // the net arcs (folded by adj_probe for the first corner when WAIT)
+        float abar;
+        if (WAIT && first) {
+            abar = abar0;
+        } else {
+            const float szq = first ? a.sz0 : ld_state(c.slew + (size_t)z * K + k, 2 + rfo);
+            abar = 0.f;
+            for (int p = a.f0; p < a.f1; ++p) {
+                const int s = c.fo_pin[p];
+                const float4 as = (WAIT && s < c.ep_begin) ? ld_relaxed4(abox_at(c, par, s, k)) : c.adj[(size_t)s * K + k];
+                if (slew_lane) abar += (rfo ? as.w : as.z) * szq / ld_state(c.slew + (size_t)s * K + k, 2 + rfo);
+                else abar += rfo ? as.y : as.x;
+            }
         }
         // through the output merges and the NLDM lookups
         float aload = 0.f;
         float aAin[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, aSin[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         if (t >= 0) {
             const float sc = __ldg(c.lut_scale + k);
-            const float ld = c.load[(size_t)z * K + k];
-            const float abar = slew_lane ? aS[rfo] : aA[rfo];
+            const float ld = first ? a.ld0 : c.load[(size_t)z * K + k];
             if (a.kind == 1) {
-                const float cs = c.slew[(size_t)pin0 * K + k].z;
+                const float cs = first ? a.sin0[0][0] : ld_state(c.slew + (size_t)pin0 * K + k, 2);
                 const int tq = tab_off(t, 1, slew_lane ? 2 + rfo : rfo);
                 float ds, dl;
                 interp_d(lut, tq, seg_slew<UNIFORM>(c, lut, tq, cs), seg_load<UNIFORM>(c, lut, tq, ld), ds, dl);
@@ -266,16 +319,27 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
                     if (j >= nin) continue;
                     const int se = tsense[t * 3 + j];
                     const int tq = tab_off(t, j, slew_lane ? 2 + rfo : rfo);
-                    const float4 Ain = c.at[(size_t)(pin0 + j) * K + k];
-                    const float4 Sin = c.slew[(size_t)(pin0 + j) * K + k];
+                    float Ain[2], Sin[2];
+                    if (first) {
+                        Ain[0] = a.ain0[j][0];
+                        Ain[1] = a.ain0[j][1];
+                        Sin[0] = a.sin0[j][0];
+                        Sin[1] = a.sin0[j][1];
+                    } else {
+                        const size_t o = (size_t)(pin0 + j) * K + k;
+                        Ain[0] = ld_state(c.at + o, 2);
+                        Ain[1] = ld_state(c.at + o, 3);
+                        Sin[0] = ld_state(c.slew + o, 2);
+                        Sin[1] = ld_state(c.slew + o, 3);
+                    }
 #pragma unroll
                     for (int rfi = 0; rfi < 2; ++rfi) {
                         if (!arc_on(se, rfi, rfo)) continue;
-                        const float s = rfi ? Sin.w : Sin.z;
+                        const float s = Sin[rfi];
                         float ds, dl;
                         const float v = interp_d(lut, tq, seg_slew<UNIFORM>(c, lut, tq, s),
                                                  seg_load<UNIFORM>(c, lut, tq, ld), ds, dl);
-                        x[j * 2 + rfi] = slew_lane ? sc * v : (rfi ? Ain.w : Ain.z) + sc * v;
+                        x[j * 2 + rfi] = slew_lane ? sc * v : Ain[rfi] + sc * v;
                         dds[j * 2 + rfi] = ds;
                         ddl[j * 2 + rfi] = dl;
                     }
@@ -297,7 +361,8 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
                 }
             }
         }
-        aload_k[nk] = quad_sum(aload);
+        aload = quad_sum(aload);
+        if (q == 0) c.aload[(size_t)g * K + k] = aload;
         if (a.kind == 0) {
 #pragma unroll
             for (int i = 0; i < 6; ++i) {
@@ -316,50 +381,54 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
             }
         }
     }
-    // star segments of the item's net: lane q takes segments q, q + 4, ...;
-    // each lane sums its corners, the KL lanes sharing q sum the rest
+}
+
+// Star segments, after the sweep: dJ/dL of every driver-sink segment from
+// the sink's adjoints (arrival and slew, through the segment's Elmore delay
+// D = r L (c L / 2 + Cpin) and variance D^2) and the driver's load adjoint
+// (load = sum of c L + Cpin), summed over corners, then to the two cells'
+// positions through L = |dx| + |dy| (sign 0 at dx = 0).  One thread per
+// item's net; the driver cell gets one atomic pair per net.
+__global__ void k_adj_star(const DevCtx c)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= c.I) return;
+    const int f0 = c.fo_ptr[g], f1 = c.fo_ptr[g + 1];
+    if (f0 == f1) return;
+    const int K = c.K;
+    const int z = item_out_pin(c, c.item_type[g], c.item_pin0[g]);
     const float2 pz = pos_of(c, z);
     const int cz = c.pin_cell[z];
-    const int base = (threadIdx.x & 31) & ~(4 * KL - 1);
-    unsigned mq = 0;
-    for (int j = 0; j < KL; ++j) mq |= 1u << (base + q + 4 * j);
     double gdx = 0.0, gdy = 0.0;
-    for (int p = a.f0 + q; p < a.f1; p += 4) {
+    for (int p = f0; p < f1; ++p) {
         const int s = c.fo_pin[p];
         const float2 ps = pos_of(c, s);
         const float dx = pz.x - ps.x, dy = pz.y - ps.y;
         const float L = fabsf(dx) + fabsf(dy);
         const float cp = 1e3f * c.fo_cap[p];
-        double dJdL = 0.0;
-        int i = 0;
-        for (int k = kq; k < K; k += KL, ++i) {
+        float dJdL = 0.f;
+        for (int k = 0; k < K; ++k) {
             const float fk = __ldg(c.rc_scale + k);
             const float r = fk * c.r_per_um, cc = fk * c.c_per_um;
-            const float4 as = (WAIT && s < c.ep_begin) ? ld_relaxed4(abox_at(c, par, s, k)) : c.adj[(size_t)s * K + k];
+            const float4 as = c.adj[(size_t)s * K + k];
             const float4 Ss = c.slew[(size_t)s * K + k];
-            const double Draw = (double)r * L * (0.5 * cc * L + cp);
-            const double dDdL = (double)r * (cc * L + cp);
-            const double Dbar = (double)as.x + as.y;
-            const double Vbar = (double)as.z / (2.0 * Ss.z) + (double)as.w / (2.0 * Ss.w);
-            dJdL += Dbar * 1e-6 * dDdL + Vbar * 1e-12 * 2.0 * Draw * dDdL + (double)aload_k[i] * 1e-3 * cc;
+            const float Draw = r * L * (0.5f * cc * L + cp);
+            const float dDdL = r * (cc * L + cp);
+            const float Dbar = as.x + as.y;
+            const float Vbar = as.z / (2.f * Ss.z) + as.w / (2.f * Ss.w);
+            dJdL += Dbar * 1e-6f * dDdL + Vbar * 1e-12f * 2.f * Draw * dDdL + c.aload[(size_t)g * K + k] * 1e-3f * cc;
         }
-        for (int off = 4; off < 4 * KL; off <<= 1) dJdL += __shfl_xor_sync(mq, dJdL, off);
-        const double gx = dJdL * (double)((dx > 0.f) - (dx < 0.f)), gy = dJdL * (double)((dy > 0.f) - (dy < 0.f));
+        const double gx = (double)dJdL * (double)((dx > 0.f) - (dx < 0.f));
+        const double gy = (double)dJdL * (double)((dy > 0.f) - (dy < 0.f));
         gdx += gx;
         gdy += gy;
         const int cs = c.pin_cell[s];
-        if (kq == 0 && cs >= 0) {
+        if (cs >= 0) {
             atomicAdd(c.grad + 2 * (size_t)cs, -gx);
             atomicAdd(c.grad + 2 * (size_t)cs + 1, -gy);
         }
     }
-    // the driver cell: sum over the quad's segments, one atomic pair per item
-    const unsigned m4 = quad_mask();
-    gdx += __shfl_xor_sync(m4, gdx, 1);
-    gdx += __shfl_xor_sync(m4, gdx, 2);
-    gdy += __shfl_xor_sync(m4, gdy, 1);
-    gdy += __shfl_xor_sync(m4, gdy, 2);
-    if (kq == 0 && q == 0 && cz >= 0 && a.f1 > a.f0) {
+    if (cz >= 0) {
         atomicAdd(c.grad + 2 * (size_t)cz, gdx);
         atomicAdd(c.grad + 2 * (size_t)cz + 1, gdy);
     }
@@ -371,7 +440,8 @@ __global__ void k_adj_level(const DevCtx c, int i0, int i1)
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int g = i0 + tid / (4 * c.KL);
     if (g < i1)
-        adj_run<UNIFORM, false>(c, LutGlobal{c.lut}, c.arc_sense, adj_prep(c, c.type_nin, c.type_kind, g), tid & 3, 0);
+        adj_run<UNIFORM, false>(c, LutGlobal{c.lut}, c.arc_sense, adj_prep(c, c.type_nin, c.type_kind, g, tid & 3), g,
+                                tid & 3, 0, 0.f);
 }
 
 // ----------------------------------------------------- dataflow adjoint
@@ -419,11 +489,12 @@ __global__ void __launch_bounds__(kDfThreadsA) k_df_adjoint(const DevCtx c)
         const int x = c.bwd_chunk_lo[ch] + lane / (4 * c.KL);
         bool pending = x < c.bwd_chunk_hi[ch];
         AdjItem it{};
-        if (pending) it = adj_prep(c, ti, ti + c.T, x);
+        if (pending) it = adj_prep(c, ti, ti + c.T, x, q);
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
-            if (pending && group_all(c, adj_probe(c, it, par))) {
-                adj_run<UNIFORM, true>(c, lut, ti + 2 * c.T, it, q, par);
+            float abar;
+            if (pending && group_all(c, adj_probe(c, it, par, q, abar))) {
+                adj_run<UNIFORM, true>(c, lut, ti + 2 * c.T, it, x, q, par, abar);
                 pending = false;
             }
             if (__any_sync(0xffffffffu, pending)) {
@@ -459,14 +530,15 @@ void launch_adjoint(const DevCtx &c, const HostSched &h, cudaStream_t st)
         const size_t smem = adjoint_smem_bytes(h.T);
         if (h.uniform) k_df_adjoint<true><<<h.adj_blocks, kDfThreadsA, smem, st>>>(c);
         else k_df_adjoint<false><<<h.adj_blocks, kDfThreadsA, smem, st>>>(c);
-        return;
+    } else {
+        for (int s = h.S - 1; s >= 0; --s) {
+            const int i0 = h.stage_ptr[s], i1 = h.stage_ptr[s + 1];
+            if (i1 <= i0) continue;
+            if (h.uniform) k_adj_level<true><<<nblk2(4LL * c.KL * (i1 - i0), 128), 128, 0, st>>>(c, i0, i1);
+            else k_adj_level<false><<<nblk2(4LL * c.KL * (i1 - i0), 128), 128, 0, st>>>(c, i0, i1);
+        }
     }
-    for (int s = h.S - 1; s >= 0; --s) {
-        const int i0 = h.stage_ptr[s], i1 = h.stage_ptr[s + 1];
-        if (i1 <= i0) continue;
-        if (h.uniform) k_adj_level<true><<<nblk2(4LL * c.KL * (i1 - i0), 128), 128, 0, st>>>(c, i0, i1);
-        else k_adj_level<false><<<nblk2(4LL * c.KL * (i1 - i0), 128), 128, 0, st>>>(c, i0, i1);
-    }
+    if (c.I > 0) k_adj_star<<<nblk2(c.I, 128), 128, 0, st>>>(c);
 }
 
 size_t adjoint_smem_bytes(int T) { return (size_t)T * 3 * 4 * kLutStride * sizeof(float) + (size_t)T * 5 * sizeof(int); }

@@ -68,6 +68,7 @@ struct DevCtx {
     float4 *abox;                               // [2][P][K] the same for gate input pins, parity mailbox
     size_t abox_len;
     double *obj;                                // [K][4] max(-s/g), sum exp(-s/g - max), TNS_g, WNS_g; [4K] J
+    float *aload;                               // [I][K] dJ/dload of each item's output net
     double *grad;                               // [C][2] dJ/d(x, y)
     double w_tns, w_wns;
     // shared table axes (valid when every table has the same ones): slew and

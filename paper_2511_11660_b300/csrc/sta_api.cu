@@ -974,6 +974,7 @@ sta_status sta_backward(sta_ctx *c, double w_tns, double w_wns, double *J_out, d
             d.adj = dev_alloc<float4>(c, (size_t)c->plan.P * K);
             d.obj = dev_alloc<double>(c, 4 * (size_t)K + 1);
             d.grad = dev_alloc<double>(c, 2 * (size_t)c->plan.C);
+            d.aload = dev_alloc<float>(c, (size_t)c->plan.I * K);
             d.abox_len = 2 * (size_t)c->plan.P * K;
             d.abox = dev_alloc<float4>(c, d.abox_len);
             CK(cudaMemset(d.abox, 0xFF, std::max<size_t>(1, d.abox_len) * sizeof(float4)));
