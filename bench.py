@@ -17,6 +17,7 @@ and ``value`` sums the ranks' arcs over the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import collections
 import hashlib
 import json
 import os
@@ -407,8 +408,9 @@ def run_batched(a, dev: int, plain: bool = True, dist: Dist = None) -> dict:
         ds = [ds[i] for i in part]
     arcs = sum(synth.design_stats(d)["arcs"] for d in ds)
     K = ds[0]["n_corners"]
+    names = {sta.SCHED_LEVEL: "level", sta.SCHED_DATAFLOW: "dataflow", sta.SCHED_COOP: "coop"}
     b = sta.Context(None, batch=ds, device=dev)
-    b.set_schedule(sta.SCHED_DATAFLOW, 0)
+    sch, par, _ = b.autotune(trials=3)
     for _ in range(3):
         b.update_timing()
     if dist is not None:
@@ -423,11 +425,12 @@ def run_batched(a, dev: int, plain: bool = True, dist: Dist = None) -> dict:
     del b
     ls, rs = synth.lut_corners()
     ms_plain = 0.0
+    plain_sched = collections.Counter()
     for d in (ds if plain else []):
         d1 = dict(d)
         d1.update(n_corners=1, lut_scale=np.array([ls[0]], np.float32), rc_scale=np.array([rs[0]], np.float32))
         c = sta.Context(d1, device=dev)
-        c.set_schedule(sta.SCHED_DATAFLOW, 0)
+        plain_sched[names[c.autotune(trials=2)[0]]] += 1   # each plain pass on its own best schedule
         for k in range(K):
             c.set_corners([ls[k]], [rs[k]])
             c.update_timing()
@@ -437,7 +440,10 @@ def run_batched(a, dev: int, plain: bool = True, dist: Dist = None) -> dict:
             "batched_ms_per_pass": ms_batch, "plain_ms_256_passes": ms_plain,
             "batched_arcs_corners_per_s": arcs * K / (ms_batch * 1e-3),
             "plain_arcs_corners_per_s": arcs * K / (ms_plain * 1e-3) if plain else None,
-            "speedup": ms_plain / ms_batch if plain else None, "designs_reported": len(reports)}
+            "speedup": ms_plain / ms_batch if plain else None, "designs_reported": len(reports),
+            "batched_schedule": "%s (%d)" % (names[sch], par), "plain_schedules": dict(plain_sched),
+            "what": "device time of one update of the batched context (schedule from sta_autotune) vs the sum of "
+                    "256 plain single-design single-corner updates, each context on its own autotuned schedule"}
 
 
 def run_batch_only(a, dist: Dist):
@@ -490,12 +496,12 @@ def run_incremental(a, dist: Dist):
     t0 = time.perf_counter()
     ctx = sta.Context(d, device=dist.local)
     t_create = time.perf_counter() - t0
-    ctx.set_schedule(sta.SCHED_DATAFLOW, 0)
     ctx.set_clock(0.0)
     ctx.update_timing()
     s0, _, _, _ = ctx.get_endpoint_slack()
     T = clock.period_in_gap(-s0[:, 1], min_half_gap=0.0)[0]   # corner 1 (scale 1.0)
     ctx.set_clock(T)
+    sched = {sta.SCHED_LEVEL: "level", sta.SCHED_DATAFLOW: "dataflow", sta.SCHED_COOP: "coop"}[ctx.autotune(trials=2)[0]]
     K = ctx.K
     C = d["n_cells"]
     rng = np.random.default_rng(a.seed)
@@ -539,6 +545,7 @@ def run_incremental(a, dist: Dist):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
            "config": {"workload": "large: " + WORKLOADS["large"], "cells": st_d["cells"], "pins": st_d["pins"],
                       "arcs": st_d["arcs"], "corners": K, "levels": stats["n_levels"], "period_ns": T,
+                      "schedule": sched,
                       "device_bytes": stats["device_bytes"], "generate_s": t_gen, "create_s": t_create,
                       "wns_setup_ns_by_corner": [r["wns_setup"] for r in rep]},
            "device_ms_per_iter": float(np.median(devs)), "ms_by_call": parts,

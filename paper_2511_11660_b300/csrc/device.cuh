@@ -24,6 +24,7 @@ constexpr unsigned kErrResize = 4u;
 struct DevCtx {
     int32_t P, I, S, E, K, T, C, n_designs;
     int32_t KL;                                 // quads per item: corners handled side by side (1, 2, 4 or 8)
+    int64_t NN;                                 // RC nodes
     float period, clk_slew, pi_at, pi_slew, setup, hold, gamma, inv_gamma;
     float r_per_um, c_per_um;
     const float *lut;          // [T][3][4][80]
@@ -47,7 +48,7 @@ struct DevCtx {
     const int32_t *red_design_chunk;            // [n_designs+1] chunk ranges per design
     double *red_partial;                        // [n_red_chunks][K][6] scratch
     unsigned *err;
-    float *scratch_a, *scratch_b;               // [NN] RC sweeps of nets larger than kRcColNodes
+    float *scratch_a, *scratch_b;               // [K][NN] RC sweeps of nets larger than kRcColNodes
     // dataflow schedule: mailboxes by epoch parity, NaN until published
     float4 *fbox;                               // [2][P][K][2] arrival, slew of driver pins
     float4 *rbox;                               // [2][P][K]    required time of gate input pins

@@ -17,13 +17,15 @@ static inline int nblk(long long n, int t) { return (int)((n + t - 1) / t); }
 
 // ------------------------------------------------------------------ nets
 
-// RC trees, one thread per item's net.  A net of at most kRcColNodes nodes
+// RC trees, one thread per (item's net, corner): the K threads of a net are
+// adjacent, so their per-sink outputs (corner innermost) are written side by
+// side.  A net of at most kRcColNodes nodes
 // lives in a shared-memory column of its thread: node i at [i * kRcThreads +
 // thread], so every access of the sweeps -- the parent's entry included --
 // falls in the thread's own bank.  The loads that fill the column are
 // unrolled over the column height (predicated on the net size), so all of a
 // thread's loads are in flight together.  Larger nets sweep the same way in
-// global scratch at their node offsets.  Per corner (node capacitance =
+// global scratch at their node offsets (one copy of the scratch per corner).  Per corner (node capacitance =
 // scaled wire C + sink pin caps, Ohm * fF -> 1e-6 ns):
 //   Cdown (reverse sweep), load = Cdown at the root;
 //   D_i = D_parent + R_i Cdown_i and, in the same sweep, C_i D_i;
@@ -41,8 +43,10 @@ __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
     __shared__ float s_R[kRcColNodes * kRcThreads], s_C[kRcColNodes * kRcThreads];
     __shared__ float s_A[kRcColNodes * kRcThreads], s_B[kRcColNodes * kRcThreads];
     const int t = threadIdx.x;
-    const int g = blockIdx.x * kRcThreads + t;
-    if (g >= c.I) return;
+    const int K = c.K;
+    const long long gk = (long long)blockIdx.x * kRcThreads + t;
+    if (gk >= (long long)c.I * K) return;
+    const int g = (int)(gk / K), k = (int)(gk % K);
     const int n0 = c.rc_ptr[g], n = c.rc_ptr[g + 1] - n0;
     const int f0 = c.fo_ptr[g], f1 = c.fo_ptr[g + 1];
     if (n == 0) return;
@@ -65,14 +69,14 @@ __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
                 s_C[i * kRcThreads + t] = cv[i];
             }
     }
-    const ColRef A = col ? ColRef{s_A + t, kRcThreads} : ColRef{c.scratch_a + n0, 1};
-    const ColRef B = col ? ColRef{s_B + t, kRcThreads} : ColRef{c.scratch_b + n0, 1};
+    const size_t so = (size_t)k * c.NN + n0;   // global scratch: one copy per corner
+    const ColRef A = col ? ColRef{s_A + t, kRcThreads} : ColRef{c.scratch_a + so, 1};
+    const ColRef B = col ? ColRef{s_B + t, kRcThreads} : ColRef{c.scratch_b + so, 1};
     auto par = [&](int i) -> int { return col ? s_par[i * kRcThreads + t] : __ldg(c.rc_parent + n0 + i); };
     auto Rv = [&](int i) -> float { return col ? s_R[i * kRcThreads + t] : __ldg(c.rc_R + n0 + i); };
     auto Cv = [&](int i) -> float { return col ? s_C[i * kRcThreads + t] : __ldg(c.rc_C + n0 + i); };
     const int z = item_out_pin(c, c.item_type[g], c.item_pin0[g]);
-    const int K = c.K;
-    for (int k = 0; k < K; ++k) {
+    {
         const float f = __ldg(c.rc_scale + k);
         for (int i = 0; i < n; ++i) {
             const float ci = f * Cv(i);
@@ -354,7 +358,7 @@ void launch_net_star(const DevCtx &c, cudaStream_t st) { k_net_star<<<nblk(c.I, 
 
 void launch_net_tree(const DevCtx &c, cudaStream_t st)
 {
-    if (c.I > 0) k_net_tree<<<nblk(c.I, kRcThreads), kRcThreads, 0, st>>>(c);
+    if (c.I > 0) k_net_tree<<<nblk((long long)c.I * c.K, kRcThreads), kRcThreads, 0, st>>>(c);
 }
 
 void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev)

@@ -133,6 +133,7 @@ sta_status create_from_plan(sta_ctx *c, int device)
     d.S = pl.S;
     d.E = pl.E;
     d.K = pl.K;
+    d.NN = pl.NN;
     d.T = pl.T;
     d.C = pl.C;
     d.n_designs = pl.n_designs;
@@ -208,8 +209,8 @@ sta_status create_from_plan(sta_ctx *c, int device)
     d.err = dev_alloc<unsigned>(c, 1);
     CK(cudaMemset(d.err, 0, sizeof(unsigned)));
     if (pl.n_big_nets > 0) {
-        d.scratch_a = dev_alloc<float>(c, (size_t)pl.NN);
-        d.scratch_b = dev_alloc<float>(c, (size_t)pl.NN);
+        d.scratch_a = dev_alloc<float>(c, (size_t)pl.NN * pl.K);
+        d.scratch_b = dev_alloc<float>(c, (size_t)pl.NN * pl.K);
     }
     HostSched &h = c->hs;
     h.S = pl.S;
