@@ -216,7 +216,9 @@ sta_status sta_set_corners(sta_ctx *ctx, const float *lut_scale, const float *rc
  * of each candidate (level schedule with 64, 128 and 256 threads per block;
  * dataflow schedule with a persistent grid from occupancy, one block per SM
  * and two per SM; cooperative schedule with a grid from occupancy and one
- * block per SM) on `stream`, keeps the best and selects it.  Choices are
+ * block per SM) on `stream`, keeps the best and selects it.  In a
+ * differentiable context it also times sta_backward with each reverse-sweep
+ * schedule (sta_set_adjoint_schedule) and selects the faster.  Choices are
  * cached per (device, graph shape); a cached choice is reused unless `force`.
  * Outputs (nullable): the chosen schedule, its parameter and its ms per
  * update.  Runs full timing updates (the context's results are those of the
@@ -240,6 +242,12 @@ sta_status sta_resize_cells(sta_ctx *ctx, const int32_t *cells, const int32_t *t
  * per block for LEVEL (0 = 128); for DATAFLOW and COOP the persistent grid
  * size in blocks (0 = every block the occupancy allows on this device). */
 sta_status sta_set_schedule(sta_ctx *ctx, int32_t schedule, int32_t param);
+
+/* Reverse sweep of sta_backward: STA_SCHED_DATAFLOW (one persistent kernel,
+ * the default; used only when the cell library fits its shared-memory copy)
+ * or STA_SCHED_LEVEL (one launch per level).  Both compute the same
+ * gradient. */
+sta_status sta_set_adjoint_schedule(sta_ctx *ctx, int32_t schedule);
 
 /* Dataflow and cooperative schedules: polls a wait (on a ready flag, or on
  * the grid barrier between levels) may spend before the pass gives up and

@@ -33,7 +33,7 @@ constexpr int kDfThreadsA = 256;
 // sums over endpoints and over the gradient are FP64.
 __device__ __forceinline__ float ep_smooth_slack(const DevCtx &c, int e, int k, float y[2])
 {
-    const int p = c.ep_pin[e];
+    const int p = chk(c, c.ep_pin[e], c.P);
     const float req = c.ep_is_d[e] ? c.period - c.setup : c.period;
     const float4 a = c.at[(size_t)p * c.K + k];
     y[0] = req - a.z;
@@ -151,7 +151,7 @@ __global__ void k_adj_seed(const DevCtx c)
 {
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= c.E) return;
-    const int p = c.ep_pin[e];
+    const int p = chk(c, c.ep_pin[e], c.P);
     const float ig = c.inv_gamma;
     const float wt = (float)c.w_tns, ww = (float)c.w_wns;
     for (int k = 0; k < c.K; ++k) {
@@ -167,8 +167,11 @@ __global__ void k_adj_seed(const DevCtx c)
 
 __device__ __forceinline__ float2 pos_of(const DevCtx &c, int p)
 {
-    const int pc = c.pin_cell[p];
-    if (pc >= 0) return make_float2(c.cell_xy[2 * (size_t)pc], c.cell_xy[2 * (size_t)pc + 1]);
+    const int pc = c.pin_cell[chk(c, p, c.P)];
+    if (pc >= 0) {
+        const int cc = chk(c, pc, c.C);
+        return make_float2(c.cell_xy[2 * (size_t)cc], c.cell_xy[2 * (size_t)cc + 1]);
+    }
     const int q = -pc - 1;
     return make_float2(c.port_xy[2 * (size_t)q], c.port_xy[2 * (size_t)q + 1]);
 }
@@ -190,13 +193,15 @@ __device__ __forceinline__ AdjItem adj_prep(const DevCtx &c, const int *tnin, co
 {
     AdjItem a;
     const int K = c.K, kq = corner_lane(c);
-    a.t = c.item_type[g];
-    a.pin0 = c.item_pin0[g];
+    g = chk(c, g, c.I);
+    a.t = chk_type(c, c.item_type[g]);
+    a.pin0 = chk(c, c.item_pin0[g], c.P);
     a.kind = a.t >= 0 ? tkind[a.t] : -1;
     a.nin = a.kind == 0 ? tnin[a.t] : 0;
     a.z = a.t < 0 ? a.pin0 : (a.kind == 1 ? a.pin0 + 1 : a.pin0 + a.nin);
-    a.f0 = c.fo_ptr[g];
-    a.f1 = c.fo_ptr[g + 1];
+    a.z = chk(c, a.z, c.P);
+    a.f0 = chk(c, c.fo_ptr[g], (long long)c.F + 1);
+    a.f1 = chk(c, c.fo_ptr[g + 1], (long long)c.F + 1);
     a.sz0 = ld_state(c.slew + (size_t)a.z * K + kq, 2 + (q >> 1));
     a.ld0 = a.t >= 0 ? c.load[(size_t)a.z * K + kq] : 0.f;
     const int nread = a.kind == 1 ? 1 : a.nin;
@@ -232,7 +237,7 @@ __device__ __forceinline__ bool adj_probe(const DevCtx &c, const AdjItem &a, int
         int s[4];
         float v[4], ss[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) s[u] = p0 + u < a.f1 ? __ldg(c.fo_pin + p0 + u) : -1;
+        for (int u = 0; u < 4; ++u) s[u] = p0 + u < a.f1 ? chk(c, __ldg(c.fo_pin + p0 + u), c.P) : -1;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (s[u] < 0) continue;
@@ -248,7 +253,7 @@ __device__ __forceinline__ bool adj_probe(const DevCtx &c, const AdjItem &a, int
         }
     }
     for (int p = a.f0; p < a.f1 && ok; ++p) {
-        const int s = __ldg(c.fo_pin + p);
+        const int s = chk(c, __ldg(c.fo_pin + p), c.P);
         if (s < c.ep_begin)
             for (int k = kq + c.KL; k < K && ok; k += c.KL) ok = complete(ld_relaxed4(abox_at(c, par, s, k)));
     }
@@ -289,7 +294,7 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
             const float szq = first ? a.sz0 : ld_state(c.slew + (size_t)z * K + k, 2 + rfo);
             abar = 0.f;
             for (int p = a.f0; p < a.f1; ++p) {
-                const int s = c.fo_pin[p];
+                const int s = chk(c, c.fo_pin[p], c.P);
                 const float4 as = (WAIT && s < c.ep_begin) ? ld_relaxed4(abox_at(c, par, s, k)) : c.adj[(size_t)s * K + k];
                 if (slew_lane) abar += (rfo ? as.w : as.z) * szq / ld_state(c.slew + (size_t)s * K + k, 2 + rfo);
                 else abar += rfo ? as.y : as.x;
@@ -393,15 +398,15 @@ __global__ void k_adj_star(const DevCtx c)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= c.I) return;
-    const int f0 = c.fo_ptr[g], f1 = c.fo_ptr[g + 1];
-    if (f0 == f1) return;
+    const int f0 = chk(c, c.fo_ptr[g], (long long)c.F + 1), f1 = chk(c, c.fo_ptr[g + 1], (long long)c.F + 1);
+    if (f0 >= f1) return;
     const int K = c.K;
-    const int z = item_out_pin(c, c.item_type[g], c.item_pin0[g]);
+    const int z = chk(c, item_out_pin(c, chk_type(c, c.item_type[g]), c.item_pin0[g]), c.P);
     const float2 pz = pos_of(c, z);
     const int cz = c.pin_cell[z];
     double gdx = 0.0, gdy = 0.0;
     for (int p = f0; p < f1; ++p) {
-        const int s = c.fo_pin[p];
+        const int s = chk(c, c.fo_pin[p], c.P);
         const float2 ps = pos_of(c, s);
         const float dx = pz.x - ps.x, dy = pz.y - ps.y;
         const float L = fabsf(dx) + fabsf(dy);
@@ -422,7 +427,7 @@ __global__ void k_adj_star(const DevCtx c)
         const double gy = (double)dJdL * (double)((dy > 0.f) - (dy < 0.f));
         gdx += gx;
         gdy += gy;
-        const int cs = c.pin_cell[s];
+        const int cs = c.pin_cell[s] >= 0 ? chk(c, c.pin_cell[s], c.C) : -1;
         if (cs >= 0) {
             atomicAdd(c.grad + 2 * (size_t)cs, -gx);
             atomicAdd(c.grad + 2 * (size_t)cs + 1, -gy);
@@ -546,7 +551,7 @@ size_t adjoint_smem_bytes(int T) { return (size_t)T * 3 * 4 * kLutStride * sizeo
 cudaError_t adjoint_prepare(HostSched &h)
 {
     const size_t smem = adjoint_smem_bytes(h.T);
-    if (smem > 200 * 1024) {   // library too large for the shared copy: level sweep
+    if (h.adj_level || smem > 200 * 1024) {   // chosen, or the library is too large for the shared copy
         h.adj_blocks = 0;
         return cudaSuccess;
     }

@@ -112,7 +112,7 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
         EpItem e{};
         if (pending) {
             if (is_item) f = fwd_prep(c, L.nin, L.kind, L.sense, x);
-            else e = ep_prep(c, c.ep_order[x - c.I]);
+            else e = ep_prep(c, c.ep_order[chk(c, x - c.I, c.E)]);
         }
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
@@ -124,7 +124,7 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
                         pending = false;
                     }
                 } else if (group_all(c, ep_probe(c, e, par, q, in.at[0], in.sl[0]))) {
-                    ep_run<true>(c, e, in.at[0], in.sl[0], c.ep_order[x - c.I], q, par);
+                    ep_run<true>(c, e, in.at[0], in.sl[0], c.ep_order[chk(c, x - c.I, c.E)], q, par);
                     pending = false;
                 }
             }

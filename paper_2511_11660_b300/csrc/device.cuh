@@ -25,6 +25,7 @@ struct DevCtx {
     int32_t P, I, S, E, K, T, C, n_designs;
     int32_t KL;                                 // quads per item: corners handled side by side (1, 2, 4 or 8)
     int64_t NN;                                 // RC nodes
+    int32_t F;                                  // net sinks (fan-out entries)
     float period, clk_slew, pi_at, pi_slew, setup, hold, gamma, inv_gamma;
     float r_per_um, c_per_um;
     const float *lut;          // [T][3][4][80]
@@ -76,6 +77,31 @@ struct DevCtx {
     // load breakpoints and reciprocal segment widths
     float ax1[7], ax2[7], iw1[6], iw2[6];
 };
+
+// Debug builds (-DSTA_CHECKS) range-check every index a kernel derives from
+// plan data: out of range records kErrBounds in the device error word and
+// yields 0 (or -1 for a cell type), so the access that follows stays in
+// bounds.  In normal builds both are the identity.
+__device__ __forceinline__ int chk(const DevCtx &c, long long i, long long n)
+{
+#ifdef STA_CHECKS
+    if (i < 0 || i >= n) {
+        atomicOr(c.err, kErrBounds);
+        return 0;
+    }
+#endif
+    return (int)i;
+}
+__device__ __forceinline__ int chk_type(const DevCtx &c, int t)
+{
+#ifdef STA_CHECKS
+    if (t < -1 || t >= c.T) {
+        atomicOr(c.err, kErrBounds);
+        return -1;
+    }
+#endif
+    return t;
+}
 
 // arc senses as the kernels see them
 constexpr int kSensePosC = 0, kSenseNegC = 1, kSenseNonC = 2, kSenseRiseC = 3;

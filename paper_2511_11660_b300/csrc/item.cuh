@@ -236,8 +236,9 @@ __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, co
                                             int g)
 {
     FwdItem f;
-    f.t = c.item_type[g];
-    f.pin0 = c.item_pin0[g];
+    g = chk(c, g, c.I);
+    f.t = chk_type(c, c.item_type[g]);
+    f.pin0 = chk(c, c.item_pin0[g], c.P);
     f.kind = f.t >= 0 ? tkind[f.t] : -1;
     f.nin = f.kind == 0 ? tnin[f.t] : 0;
     const int K = c.K, kq = corner_lane(c);
@@ -245,11 +246,12 @@ __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, co
     for (int j = 0; j < 3; ++j) {
         const bool on = j < f.nin;
         f.sense[j] = on ? tsense[f.t * 3 + j] : -1;
-        f.drv[j] = on ? c.drv_of[f.pin0 + j] : 0;
-        f.Dn0[j] = on ? c.netD[(size_t)(f.pin0 + j) * K + kq] : 0.f;
-        f.V0[j] = on ? c.netV[(size_t)(f.pin0 + j) * K + kq] : 0.f;
+        const int a = on ? chk(c, f.pin0 + j, c.P) : 0;
+        f.drv[j] = on ? chk(c, c.drv_of[a], c.P) : 0;
+        f.Dn0[j] = on ? c.netD[(size_t)a * K + kq] : 0.f;
+        f.V0[j] = on ? c.netV[(size_t)a * K + kq] : 0.f;
     }
-    const int zl = f.kind == 1 ? f.pin0 + 1 : f.pin0 + f.nin;
+    const int zl = chk(c, f.kind == 1 ? f.pin0 + 1 : f.pin0 + f.nin, c.P);
     f.ld0 = f.t >= 0 ? c.load[(size_t)zl * K + kq] : 0.f;
     return f;
 }
@@ -390,8 +392,9 @@ struct EpItem {
 __device__ __forceinline__ EpItem ep_prep(const DevCtx &c, int e)
 {
     EpItem x;
-    x.p = c.ep_pin[e];
-    x.d = c.drv_of[x.p];
+    e = chk(c, e, c.E);
+    x.p = chk(c, c.ep_pin[e], c.P);
+    x.d = chk(c, c.drv_of[x.p], c.P);
     x.isD = c.ep_is_d[e] != 0;
     x.Dn0 = c.netD[(size_t)x.p * c.K + corner_lane(c)];
     x.V0 = c.netV[(size_t)x.p * c.K + corner_lane(c)];
@@ -470,13 +473,14 @@ __device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, co
 {
     BwdItem b;
     const int K = c.K, kq = corner_lane(c);
-    b.t = c.item_type[g];
-    b.pin0 = c.item_pin0[g];
+    g = chk(c, g, c.I);
+    b.t = chk_type(c, c.item_type[g]);
+    b.pin0 = chk(c, c.item_pin0[g], c.P);
     b.kind = b.t >= 0 ? tkind[b.t] : -1;
     b.nin = b.t >= 0 ? tnin[b.t] : 0;
-    b.z = b.t < 0 ? b.pin0 : (b.kind == 1 ? b.pin0 + 1 : b.pin0 + b.nin);
-    b.f0 = c.fo_ptr[g];
-    b.f1 = c.fo_ptr[g + 1];
+    b.z = chk(c, b.t < 0 ? b.pin0 : (b.kind == 1 ? b.pin0 + 1 : b.pin0 + b.nin), c.P);
+    b.f0 = chk(c, c.fo_ptr[g], (long long)c.F + 1);
+    b.f1 = chk(c, c.fo_ptr[g + 1], (long long)c.F + 1);
     b.ld0 = b.t >= 0 ? c.load[(size_t)b.z * K + kq] : 0.f;
     b.az0 = ld_state(c.at + (size_t)b.z * K + kq, q);
     const int nread = b.kind == 1 ? 1 : b.kind == 0 ? b.nin : 0;
@@ -507,7 +511,7 @@ __device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int
         int s[4];
         float m[4], nd[4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) s[u] = p0 + u < b.f1 ? __ldg(c.fo_pin + p0 + u) : -1;
+        for (int u = 0; u < 4; ++u) s[u] = p0 + u < b.f1 ? chk(c, __ldg(c.fo_pin + p0 + u), c.P) : -1;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (s[u] < 0) continue;
@@ -524,7 +528,7 @@ __device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int
         }
     }
     for (int p = b.f0; p < b.f1 && ok; ++p) {
-        const int s = __ldg(c.fo_pin + p);
+        const int s = chk(c, __ldg(c.fo_pin + p), c.P);
         if (s < c.ep_begin)
             for (int k = kq + c.KL; k < K && ok; k += c.KL) ok = complete(ld_relaxed4(rbox_at(c, par, s, k)));
     }
@@ -552,7 +556,7 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
             R = Rpre;
         } else {
             for (int p = b.f0; p < b.f1; ++p) {
-                const int s = c.fo_pin[p];
+                const int s = chk(c, c.fo_pin[p], c.P);
                 const float rs = (WAIT && s < c.ep_begin) ? comp(ld_relaxed4(rbox_at(c, par, s, k)), q)
                                                           : ld_state(c.rat + (size_t)s * K + k, q);
                 const float r = rs - c.netD[(size_t)s * K + k];

@@ -47,9 +47,9 @@ __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
     const long long gk = (long long)blockIdx.x * kRcThreads + t;
     if (gk >= (long long)c.I * K) return;
     const int g = (int)(gk / K), k = (int)(gk % K);
-    const int n0 = c.rc_ptr[g], n = c.rc_ptr[g + 1] - n0;
-    const int f0 = c.fo_ptr[g], f1 = c.fo_ptr[g + 1];
-    if (n == 0) return;
+    const int n0 = chk(c, c.rc_ptr[g], c.NN + 1), n = chk(c, c.rc_ptr[g + 1], c.NN + 1) - n0;
+    const int f0 = chk(c, c.fo_ptr[g], (long long)c.F + 1), f1 = chk(c, c.fo_ptr[g + 1], (long long)c.F + 1);
+    if (n <= 0) return;
     const bool col = n <= kRcColNodes;
     if (col) {
         int8_t pv[kRcColNodes];
@@ -57,7 +57,7 @@ __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
 #pragma unroll
         for (int i = 0; i < kRcColNodes; ++i)
             if (i < n) {
-                pv[i] = (int8_t)__ldg(c.rc_parent + n0 + i);
+                pv[i] = (int8_t)(i ? chk(c, __ldg(c.rc_parent + n0 + i), i) : 0);
                 rv[i] = __ldg(c.rc_R + n0 + i);
                 cv[i] = __ldg(c.rc_C + n0 + i);
             }
@@ -72,10 +72,10 @@ __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
     const size_t so = (size_t)k * c.NN + n0;   // global scratch: one copy per corner
     const ColRef A = col ? ColRef{s_A + t, kRcThreads} : ColRef{c.scratch_a + so, 1};
     const ColRef B = col ? ColRef{s_B + t, kRcThreads} : ColRef{c.scratch_b + so, 1};
-    auto par = [&](int i) -> int { return col ? s_par[i * kRcThreads + t] : __ldg(c.rc_parent + n0 + i); };
+    auto par = [&](int i) -> int { return col ? s_par[i * kRcThreads + t] : chk(c, __ldg(c.rc_parent + n0 + i), i); };
     auto Rv = [&](int i) -> float { return col ? s_R[i * kRcThreads + t] : __ldg(c.rc_R + n0 + i); };
     auto Cv = [&](int i) -> float { return col ? s_C[i * kRcThreads + t] : __ldg(c.rc_C + n0 + i); };
-    const int z = item_out_pin(c, c.item_type[g], c.item_pin0[g]);
+    const int z = chk(c, item_out_pin(c, chk_type(c, c.item_type[g]), c.item_pin0[g]), c.P);
     {
         const float f = __ldg(c.rc_scale + k);
         for (int i = 0; i < n; ++i) {
@@ -89,7 +89,7 @@ __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 if (q0 + u < f1) {
-                    nd[u] = __ldg(c.fo_node + q0 + u);
+                    nd[u] = chk(c, __ldg(c.fo_node + q0 + u), n);
                     cp[u] = 1e3f * __ldg(c.fo_cap + q0 + u);
                 }
 #pragma unroll
@@ -116,8 +116,8 @@ __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
 #pragma unroll
             for (int u = 0; u < 4; ++u)
                 if (q0 + u < f1) {
-                    nd[u] = __ldg(c.fo_node + q0 + u);
-                    sp[u] = __ldg(c.fo_pin + q0 + u);
+                    nd[u] = chk(c, __ldg(c.fo_node + q0 + u), n);
+                    sp[u] = chk(c, __ldg(c.fo_pin + q0 + u), c.P);
                 }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
@@ -132,8 +132,11 @@ __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
 
 __device__ __forceinline__ float2 pin_pos(const DevCtx &c, int p)
 {
-    const int pc = c.pin_cell[p];
-    if (pc >= 0) return make_float2(c.cell_xy[2 * (size_t)pc], c.cell_xy[2 * (size_t)pc + 1]);
+    const int pc = c.pin_cell[chk(c, p, c.P)];
+    if (pc >= 0) {
+        const int cc = chk(c, pc, c.C);
+        return make_float2(c.cell_xy[2 * (size_t)cc], c.cell_xy[2 * (size_t)cc + 1]);
+    }
     const int q = -pc - 1;
     return make_float2(c.port_xy[2 * (size_t)q], c.port_xy[2 * (size_t)q + 1]);
 }
@@ -144,9 +147,9 @@ __global__ void k_net_star(const DevCtx c)
 {
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= c.I) return;
-    const int f0 = c.fo_ptr[g], f1 = c.fo_ptr[g + 1];
-    if (f0 == f1) return;
-    const int z = item_out_pin(c, c.item_type[g], c.item_pin0[g]);
+    const int f0 = chk(c, c.fo_ptr[g], (long long)c.F + 1), f1 = chk(c, c.fo_ptr[g + 1], (long long)c.F + 1);
+    if (f0 >= f1) return;
+    const int z = chk(c, item_out_pin(c, chk_type(c, c.item_type[g]), c.item_pin0[g]), c.P);
     const float2 pz = pin_pos(c, z);
     const int K = c.K;
     for (int k = 0; k < K; ++k) {
@@ -154,7 +157,7 @@ __global__ void k_net_star(const DevCtx c)
         const float r = f * c.r_per_um, cc = f * c.c_per_um;
         float ld = 0.f;
         for (int q = f0; q < f1; ++q) {
-            const int s = c.fo_pin[q];
+            const int s = chk(c, c.fo_pin[q], c.P);
             const float2 ps = pin_pos(c, s);
             const float L = fabsf(pz.x - ps.x) + fabsf(pz.y - ps.y);
             const float cp = 1e3f * c.fo_cap[q];

@@ -21,6 +21,8 @@ struct HostSched {
     int df_blocks_fwd = 0;            // persistent grids of the dataflow kernels
     int df_blocks_bwd = 0;
     int adj_blocks = 0;               // persistent grid of the dataflow adjoint (0 = level sweep)
+    bool adj_level = false;           // reverse sweep forced to one launch per level
+    bool adj_ready = false;           // adjoint_prepare has run for the current choice
     int coop_blocks = 0;              // co-resident grid of the cooperative schedule
 };
 

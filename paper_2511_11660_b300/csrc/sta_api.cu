@@ -134,6 +134,7 @@ sta_status create_from_plan(sta_ctx *c, int device)
     d.E = pl.E;
     d.K = pl.K;
     d.NN = pl.NN;
+    d.F = (int32_t)pl.F;
     d.T = pl.T;
     d.C = pl.C;
     d.n_designs = pl.n_designs;
@@ -572,6 +573,16 @@ sta_status sta_set_schedule(sta_ctx *c, int32_t schedule, int32_t param)
     return STA_OK;
 }
 
+sta_status sta_set_adjoint_schedule(sta_ctx *c, int32_t schedule)
+{
+    if (!c) return STA_EINVAL;
+    if (schedule != STA_SCHED_LEVEL && schedule != STA_SCHED_DATAFLOW)
+        return fail(c, STA_EINVAL, "adjoint schedule must be STA_SCHED_LEVEL or STA_SCHED_DATAFLOW");
+    c->hs.adj_level = schedule == STA_SCHED_LEVEL;
+    c->hs.adj_ready = false;
+    return STA_OK;
+}
+
 sta_status sta_set_wait_limit(sta_ctx *c, int64_t polls)
 {
     if (!c) return STA_EINVAL;
@@ -614,6 +625,7 @@ struct TuneKey {
 struct TuneChoice {
     int schedule, param;
     float ms;
+    int adj_schedule;   // reverse sweep of sta_backward (differentiable contexts), -1 = not tuned
 };
 std::mutex g_tune_mu;
 std::map<TuneKey, TuneChoice> g_tune_cache;
@@ -626,7 +638,7 @@ sta_status sta_autotune(sta_ctx *c, void *stream, int32_t trials, int32_t force,
     if (trials < 1) trials = 1;
     const Plan &pl = c->plan;
     const TuneKey key{c->device, pl.P, pl.I, pl.S, pl.K, pl.T, pl.E, pl.uniform_axes, pl.placed, pl.gamma > 0.f};
-    TuneChoice best{-1, 0, 0.f};
+    TuneChoice best{-1, 0, 0.f, -1};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         auto it = g_tune_cache.find(key);
@@ -657,16 +669,50 @@ sta_status sta_autotune(sta_ctx *c, void *stream, int32_t trials, int32_t force,
                 CK(cudaEventElapsedTime(&ms, e0, e1));
                 ms /= trials;
                 if (check_device_error(c) != STA_OK) continue;
-                if (best.schedule < 0 || ms < best.ms) best = TuneChoice{cs.first, cs.second, ms};
+                if (best.schedule < 0 || ms < best.ms) best = TuneChoice{cs.first, cs.second, ms, -1};
+            }
+            if (best.schedule < 0) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return fail(c, STA_ECUDA, "no schedule could run");
+            }
+            // differentiable contexts: the reverse sweep of sta_backward too
+            if (pl.gamma > 0.f && pl.placed) {
+                float best_adj = 0.f;
+                if (sta_set_schedule(c, best.schedule, best.param) != STA_OK || sta_update_timing(c, stream) != STA_OK) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return fail(c, STA_ECUDA, "the chosen schedule failed to run again");
+                }
+                for (int as : {STA_SCHED_DATAFLOW, STA_SCHED_LEVEL}) {
+                    if (sta_set_adjoint_schedule(c, as) != STA_OK) continue;
+                    if (sta_backward(c, 1.0, 1.0, nullptr, nullptr, nullptr, STA_DEVICE, stream) != STA_OK) continue;
+                    CK(cudaSetDevice(c->device));
+                    CK(cudaEventRecord(e0, st));
+                    for (int i = 0; i < trials; ++i) sta_backward(c, 1.0, 1.0, nullptr, nullptr, nullptr, STA_DEVICE, stream);
+                    CK(cudaEventRecord(e1, st));
+                    CK(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, e0, e1));
+                    ms /= trials;
+                    if (check_device_error(c) != STA_OK) continue;
+                    if (best.adj_schedule < 0 || ms < best_adj) {
+                        best.adj_schedule = as;
+                        best_adj = ms;
+                    }
+                }
             }
             cudaEventDestroy(e0);
             cudaEventDestroy(e1);
-            if (best.schedule < 0) return fail(c, STA_ECUDA, "no schedule could run");
             std::lock_guard<std::mutex> lk(g_tune_mu);
             g_tune_cache[key] = best;
         }
         const sta_status st2 = sta_set_schedule(c, best.schedule, best.param);
         if (st2 != STA_OK) return st2;
+        if (best.adj_schedule >= 0) {
+            const sta_status st4 = sta_set_adjoint_schedule(c, best.adj_schedule);
+            if (st4 != STA_OK) return st4;
+        }
         const sta_status st3 = sta_update_timing(c, stream);
         if (st3 != STA_OK) return st3;
     } catch (const CudaFail &f) {
@@ -979,8 +1025,11 @@ sta_status sta_backward(sta_ctx *c, double w_tns, double w_wns, double *J_out, d
             d.abox_len = 2 * (size_t)c->plan.P * K;
             d.abox = dev_alloc<float4>(c, d.abox_len);
             CK(cudaMemset(d.abox, 0xFF, std::max<size_t>(1, d.abox_len) * sizeof(float4)));
+        }
+        if (!c->hs.adj_ready) {
             const cudaError_t e = sta::adjoint_prepare(c->hs);
             if (e != cudaSuccess) throw CudaFail{e, "adjoint set-up"};
+            c->hs.adj_ready = true;
         }
         d.w_tns = w_tns;
         d.w_wns = w_wns;

@@ -90,6 +90,7 @@ SIGNATURES = {
     "sta_set_schedule": (C.c_int, [_V, C.c_int32, C.c_int32]),
     "sta_autotune": (C.c_int, [_V, _V, C.c_int32, C.c_int32, _P, _P, _P]),
     "sta_set_wait_limit": (C.c_int, [_V, C.c_int64]),
+    "sta_set_adjoint_schedule": (C.c_int, [_V, C.c_int32]),
     "sta_debug_hold_cell": (C.c_int, [_V, C.c_int32]),
     "sta_update_timing": (C.c_int, [_V, _V]),
     "sta_sync": (C.c_int, [_V, _V]),
@@ -268,6 +269,10 @@ class Context:
 
     def set_wait_limit(self, polls: int):
         self._chk(self.lib.sta_set_wait_limit(self.h, int(polls)))
+
+    def set_adjoint_schedule(self, schedule: int):
+        """Reverse sweep of backward(): SCHED_DATAFLOW (default) or SCHED_LEVEL."""
+        self._chk(self.lib.sta_set_adjoint_schedule(self.h, schedule))
 
     def debug_hold_cell(self, cell: int):
         self._chk(self.lib.sta_debug_hold_cell(self.h, int(cell)))

@@ -64,6 +64,22 @@ def test_every_forward_schedule_gives_the_same_gradient(schedule):
     np.testing.assert_allclose(a[2], b[2], rtol=1e-9, atol=1e-12 * np.abs(b[2]).max())
 
 
+def test_adjoint_schedules_give_the_same_gradient():
+    """The reverse sweep as one persistent kernel or one launch per level:
+    the same objective, and gradients equal up to the order of the FP64
+    atomic sums."""
+    d = placed(2000, 15, 5)
+    out = []
+    for sch in (sta.SCHED_DATAFLOW, sta.SCHED_LEVEL):
+        ctx = sta.Context(d)
+        ctx.set_adjoint_schedule(sch)
+        ctx.update_timing()
+        out.append(ctx.backward(1.0, 1.0))
+        ctx.close()
+    assert out[0][0] == out[1][0]
+    np.testing.assert_allclose(out[0][2], out[1][2], rtol=1e-9, atol=1e-12 * np.abs(out[1][2]).max())
+
+
 def test_four_corner_objective_and_gradient():
     ls, rs = synth.lut_corners()
     d = placed(2000, 15, 5, n_corners=4, lut_scale=ls, rc_scale=rs)
