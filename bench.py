@@ -550,7 +550,8 @@ def run_incremental(a, dist: Dist):
                       "wns_setup_ns_by_corner": [r["wns_setup"] for r in rep]},
            "device_ms_per_iter": float(np.median(devs)), "ms_by_call": parts,
            "arc_corners_per_s": st_d["arcs"] * K / np.median(walls),
-           "gpu_launches": None}
+           # per iteration: update + backward + the two resize kernels (set_positions is a copy)
+           "gpu_launches": n_iter * (stats["launches_per_update"] + stats["launches_per_backward"] + 2)}
     print(json.dumps(out))
 
 

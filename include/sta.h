@@ -159,6 +159,8 @@ typedef struct {
     int32_t n_designs;                           /* 1, or the batch size */
     int64_t device_bytes;                        /* device memory the context holds */
     int32_t launches_per_update;                 /* kernels one sta_update_timing launches */
+    int32_t launches_per_backward;               /* kernels one sta_backward launches (differentiable
+                                                    contexts, current reverse-sweep schedule; else 0) */
 } sta_plan_info;
 
 /* Per-corner summary returned by sta_report_slack. */

@@ -335,6 +335,25 @@ int32_t launches_per_update(const sta_ctx *c)
     return n;
 }
 
+// Kernel launches of one sta_backward under the current reverse-sweep schedule.
+int32_t launches_per_backward(const sta_ctx *c)
+{
+    const Plan &pl = c->plan;
+    if (!(pl.gamma > 0.f) || !pl.placed) return 0;
+    int32_t n = 0;
+    n += c->hs.n_red_chunks > 0 ? 4 : 0;        // objective: max and sums, two stages each
+    n += 1;                                      // objective total
+    n += pl.E > 0;                               // endpoint seed
+    const bool dataflow = !c->hs.adj_level && sta::adjoint_smem_bytes(pl.T) <= 200 * 1024;
+    if (dataflow) {
+        n += 3;                                  // mailbox recovery, epoch, persistent sweep
+    } else {
+        for (int32_t s = 0; s < pl.S; ++s) n += pl.stage_ptr[s + 1] > pl.stage_ptr[s];
+    }
+    n += pl.I > 0;                               // star segments
+    return n;
+}
+
 sta_status check_device_error(sta_ctx *c)
 {
     unsigned err = 0;
@@ -987,6 +1006,7 @@ sta_status sta_stats(const sta_ctx *c, sta_plan_info *out)
     out->n_designs = pl.n_designs;
     out->device_bytes = (int64_t)c->bytes;
     out->launches_per_update = launches_per_update(c);
+    out->launches_per_backward = launches_per_backward(c);
     return STA_OK;
 }
 

@@ -53,7 +53,7 @@ class sta_plan_info(C.Structure):
                 ("n_cell_arcs", C.c_int64), ("n_net_arcs", C.c_int64), ("n_rc_nodes", C.c_int64),
                 ("n_endpoints", C.c_int64), ("n_levels", C.c_int32), ("n_corners", C.c_int32),
                 ("max_level_width", C.c_int32), ("n_designs", C.c_int32), ("device_bytes", C.c_int64),
-                ("launches_per_update", C.c_int32)]
+                ("launches_per_update", C.c_int32), ("launches_per_backward", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
