@@ -48,12 +48,13 @@ def _load():
         P = C.c_void_p
         _lib.orc_lut_eval.argtypes = [P, P, P, C.c_double, C.c_double, P]
         _lib.orc_rc_tree.argtypes = [C.c_int32, P, P, P, P, P, P, P]
+        _lib.orc_arnoldi_t50.argtypes = [C.c_int32, P, P, P, C.c_int32, P]
         _lib.orc_net_delays.argtypes = [P, C.c_int32, P, P, P]
         _lib.orc_topo_order.argtypes = [P, P]
         _lib.orc_sta.argtypes = [P, P, P, P, P, P, P, P]
         _lib.orc_objective_grad.argtypes = [P, C.c_double, C.c_double, P, P, P]
         _lib.orc_objective.argtypes = [P, C.c_double, C.c_double, P]
-        for f in ("orc_lut_eval", "orc_rc_tree", "orc_net_delays", "orc_topo_order", "orc_sta",
+        for f in ("orc_lut_eval", "orc_rc_tree", "orc_arnoldi_t50", "orc_net_delays", "orc_topo_order", "orc_sta",
                   "orc_objective_grad", "orc_objective"):
             getattr(_lib, f).restype = C.c_int
     return _lib
@@ -74,6 +75,7 @@ class _Design(C.Structure):
         ("period_ns", C.c_double), ("clk_slew_ns", C.c_double), ("pi_at_ns", C.c_double),
         ("pi_slew_ns", C.c_double), ("n_corners", C.c_int32), ("lut_scale", C.c_void_p),
         ("rc_scale", C.c_void_p), ("gamma_ns", C.c_double),
+        ("net_model", C.c_int32), ("arnoldi_order", C.c_int32),
     ]
 
 
@@ -112,6 +114,8 @@ def _marshal(d: dict, use_rc: bool | None = None):
     s.n_pins = int(d["n_pins"])
     s.n_nets = int(d["n_nets"])
     s.n_corners = int(d.get("n_corners", 1))
+    s.net_model = int(d.get("net_model", 0))
+    s.arnoldi_order = int(d.get("arnoldi_order", 3))
     if d.get("lut_scale") is None:
         a = np.ones(s.n_corners, np.float32); keep.append(a); s.lut_scale = a.ctypes.data
     if d.get("rc_scale") is None:
@@ -149,6 +153,18 @@ def rc_tree(parent, R, C_):
     outs = [np.zeros(n, np.float64) for _ in range(4)]
     _check(lib.orc_rc_tree(n, _ptr(par), _ptr(r), _ptr(c), *[_ptr(o) for o in outs]), "rc_tree")
     return tuple(outs)
+
+
+def arnoldi_t50(parent, R, C_, q: int):
+    """O7 on one tree (double inputs, Ohm and fF): the 50% step-response delay
+    of every node under an order-q Arnoldi reduced model (node 0: 0)."""
+    lib = _load()
+    par = np.ascontiguousarray(parent, np.int32)
+    r = np.ascontiguousarray(R, np.float64)
+    c = np.ascontiguousarray(C_, np.float64)
+    out = np.zeros(len(par), np.float64)
+    _check(lib.orc_arnoldi_t50(len(par), _ptr(par), _ptr(r), _ptr(c), int(q), _ptr(out)), "arnoldi_t50")
+    return out
 
 
 def net_delays(d: dict, corner: int = 0, use_rc: bool | None = None):

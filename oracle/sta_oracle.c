@@ -24,6 +24,10 @@
  *   O3  Elmore delay and second moment on RC trees, slew = sqrt(s^2 + var);
  *   O4  endpoint required times, back-propagated required times, slack,
  *       WNS = min(0, worst endpoint slack), TNS = sum of negative slacks;
+ *   O7  Arnoldi reduced-order net model (the paper's second delay
+ *       calculator, Sec. III "Delay models"): sink delay = 50% crossing of
+ *       the step response of an order-q congruence-projected model of the
+ *       RC tree; the slew law of O3 is kept;
  *   O6  log-sum-exp smoothed objective and its hand-written FP64 adjoint
  *       with respect to cell (x, y) (not in the paper; it feeds a placer the
  *       way the paper's DREAMPlace integration consumes pin slacks, Sec. IV-C).
@@ -94,6 +98,8 @@ typedef struct {
     const float *lut_scale;      /* [n_corners] */
     const float *rc_scale;       /* [n_corners] */
     double gamma_ns;             /* 0: hard max/min merges; > 0: log-sum-exp */
+    int32_t net_model;           /* 0 Elmore; 1 Arnoldi reduced order (O7, RC trees only) */
+    int32_t arnoldi_order;       /* Krylov dimension q of O7 (>= 1) */
 } orc_design;
 
 /* ------------------------------------------------------------------ O1 */
@@ -149,6 +155,210 @@ int orc_rc_tree(int32_t n, const int32_t *parent, const double *R, const double 
     for (int32_t i = 0; i < n; ++i) var[i] = 2.0 * beta[i] - D[i] * D[i];
     free(M);
     return OK;
+}
+
+/* ------------------------------------------------------------------ O7 */
+
+/* Solve G x = y for an RC tree whose root (node 0) is held at 0 V: G is the
+ * nodal conductance matrix of nodes 1..n-1.  The current through the edge
+ * above node i is the sum of y over i's subtree, so x_i = x_parent + R_i *
+ * (subtree sum of y).  x[0] = 0; y[0] is ignored. */
+static void tree_solve(int32_t n, const int32_t *parent, const double *R, const double *y, double *x)
+{
+    for (int32_t i = 0; i < n; ++i) x[i] = i ? y[i] : 0.0;
+    for (int32_t i = n - 1; i >= 1; --i) if (parent[i] > 0) x[parent[i]] += x[i];
+    x[0] = 0.0;
+    for (int32_t i = 1; i < n; ++i) x[i] = x[parent[i]] + R[i] * x[i];
+}
+
+/* Symmetric eigen-decomposition by cyclic Jacobi rotations: a (q x q, row
+ * major) is overwritten, eigenvalues in w, eigenvectors in the columns of v. */
+static void jacobi_eig(int q, double *a, double *w, double *v)
+{
+    for (int i = 0; i < q; ++i)
+        for (int j = 0; j < q; ++j) v[i * q + j] = i == j;
+    for (int sweep = 0; sweep < 100; ++sweep) {
+        double off = 0.0;
+        for (int i = 0; i < q; ++i)
+            for (int j = i + 1; j < q; ++j) off += a[i * q + j] * a[i * q + j];
+        if (off < 1e-30) break;
+        for (int p = 0; p < q; ++p)
+            for (int r = p + 1; r < q; ++r) {
+                const double apr = a[p * q + r];
+                if (fabs(apr) < 1e-300) continue;
+                const double theta = (a[r * q + r] - a[p * q + p]) / (2.0 * apr);
+                const double t = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int k = 0; k < q; ++k) {   /* A <- A J (columns p, r) */
+                    const double akp = a[k * q + p], akr = a[k * q + r];
+                    a[k * q + p] = c * akp - s * akr;
+                    a[k * q + r] = s * akp + c * akr;
+                }
+                for (int k = 0; k < q; ++k) {   /* A <- J^T A (rows p, r) */
+                    const double apk = a[p * q + k], ark = a[r * q + k];
+                    a[p * q + k] = c * apk - s * ark;
+                    a[r * q + k] = s * apk + c * ark;
+                }
+                for (int k = 0; k < q; ++k) {   /* V <- V J */
+                    const double vkp = v[k * q + p], vkr = v[k * q + r];
+                    v[k * q + p] = c * vkp - s * vkr;
+                    v[k * q + r] = s * vkp + c * vkr;
+                }
+            }
+    }
+    for (int i = 0; i < q; ++i) w[i] = a[i * q + i];
+}
+
+/* Arnoldi reduced-order model of an RC tree driven by a unit step at node 0
+ * (R in Ohm, C in fF, nodes parent before child; C[0] ignored).  The node
+ * voltages v of nodes 1..m (m = n - 1) obey C v' + G v = b u, u the root
+ * voltage, so the DC solution is v = 1.  The order-q Krylov space of
+ * A = G^-1 C started at G^-1 b = 1 is spanned by an orthonormal basis V
+ * (modified Gram-Schmidt, each new direction A v_j by one tree solve); the
+ * congruence projection G_r = V^T G V, C_r = V^T C V, b_r = V^T b keeps a
+ * passive model whose sink voltage is v_s(t) = sum_k a_sk (1 - exp(-l_k t))
+ * with l_k the eigenvalues of C_r^-1 G_r (through the Cholesky factor of
+ * C_r and a symmetric eigensolve).  t50[i] = the time v_i(t) first reaches
+ * half its final value (bisection), for every node (t50[0] = 0).  q is
+ * capped at m; q = m reproduces the unreduced response. */
+int orc_arnoldi_t50(int32_t n, const int32_t *parent, const double *R, const double *C, int32_t q_in, double *t50)
+{
+    if (n <= 0 || parent[0] != -1 || q_in < 1) return ERR_INVAL;
+    for (int32_t i = 1; i < n; ++i)
+        if (parent[i] < 0 || parent[i] >= i) return ERR_INVAL;
+    t50[0] = 0.0;
+    const int32_t m = n - 1;
+    if (m == 0) return OK;
+    const int q = q_in < m ? q_in : m;
+    double *V = (double *)calloc((size_t)q * n, sizeof(double));   /* V[j*n + i], entries 1..m used */
+    double *y = (double *)malloc(sizeof(double) * (size_t)n);
+    double *x = (double *)malloc(sizeof(double) * (size_t)n);
+    double *Gr = (double *)calloc((size_t)q * q, sizeof(double)), *Cr = (double *)calloc((size_t)q * q, sizeof(double));
+    double *L = (double *)calloc((size_t)q * q, sizeof(double)), *M = (double *)calloc((size_t)q * q, sizeof(double));
+    double *T = (double *)calloc((size_t)q * q, sizeof(double)), *W = (double *)calloc((size_t)q * q, sizeof(double));
+    double *lam = (double *)calloc((size_t)q, sizeof(double)), *br = (double *)calloc((size_t)q, sizeof(double));
+    double *c = (double *)calloc((size_t)q, sizeof(double)), *yinf = (double *)calloc((size_t)q, sizeof(double));
+    double *h = (double *)calloc((size_t)q, sizeof(double)), *a = (double *)calloc((size_t)q, sizeof(double));
+    int rc = OK;
+    if (!V || !y || !x || !Gr || !Cr || !L || !M || !T || !W || !lam || !br || !c || !yinf || !h || !a) {
+        rc = ERR_NOMEM;
+        goto done;
+    }
+    /* Krylov basis */
+    for (int32_t i = 1; i < n; ++i) V[i] = 1.0 / sqrt((double)m);
+    int qq = 1;
+    for (int j = 1; j < q; ++j) {
+        for (int32_t i = 0; i < n; ++i) y[i] = i ? C[i] * V[(j - 1) * n + i] : 0.0;
+        tree_solve(n, parent, R, y, x);
+        for (int p = 0; p < j; ++p) {   /* modified Gram-Schmidt */
+            double dot = 0.0;
+            for (int32_t i = 1; i < n; ++i) dot += V[p * n + i] * x[i];
+            for (int32_t i = 1; i < n; ++i) x[i] -= dot * V[p * n + i];
+        }
+        double nrm = 0.0;
+        for (int32_t i = 1; i < n; ++i) nrm += x[i] * x[i];
+        nrm = sqrt(nrm);
+        if (!(nrm > 1e-300)) break;   /* the Krylov space is exhausted */
+        for (int32_t i = 1; i < n; ++i) V[j * n + i] = x[i] / nrm;
+        qq = j + 1;
+    }
+    /* projected matrices: v^T G w = sum over edges of dv dw / R (root at 0 V);
+     * b = G * 1, so b_r = V^T G 1 = sum over the root's edges of v / R */
+    for (int p = 0; p < qq; ++p)
+        for (int r = 0; r < qq; ++r) {
+            double g = 0.0, cc = 0.0;
+            for (int32_t i = 1; i < n; ++i) {
+                const double dp = V[p * n + i] - (parent[i] ? V[p * n + parent[i]] : 0.0);
+                const double dr = V[r * n + i] - (parent[i] ? V[r * n + parent[i]] : 0.0);
+                g += dp * dr / R[i];
+                cc += C[i] * V[p * n + i] * V[r * n + i];
+            }
+            Gr[p * qq + r] = g;
+            Cr[p * qq + r] = cc;
+        }
+    for (int p = 0; p < qq; ++p) {
+        double s = 0.0;
+        for (int32_t i = 1; i < n; ++i) if (parent[i] == 0) s += V[p * n + i] / R[i];
+        br[p] = s;
+    }
+    /* Cholesky C_r = L L^T */
+    for (int i = 0; i < qq; ++i)
+        for (int j = 0; j <= i; ++j) {
+            double s = Cr[i * qq + j];
+            for (int k = 0; k < j; ++k) s -= L[i * qq + k] * L[j * qq + k];
+            if (i == j) {
+                if (!(s > 0.0)) { rc = ERR_INVAL; goto done; }   /* a zero-capacitance subspace */
+                L[i * qq + i] = sqrt(s);
+            } else {
+                L[i * qq + j] = s / L[j * qq + j];
+            }
+        }
+    /* M = L^-1 G_r L^-T: T = L^-1 G_r (forward substitution per column), M = T L^-T */
+    for (int col = 0; col < qq; ++col)
+        for (int i = 0; i < qq; ++i) {
+            double s = Gr[i * qq + col];
+            for (int k = 0; k < i; ++k) s -= L[i * qq + k] * T[k * qq + col];
+            T[i * qq + col] = s / L[i * qq + i];
+        }
+    for (int row = 0; row < qq; ++row)
+        for (int i = 0; i < qq; ++i) {
+            double s = T[row * qq + i];
+            for (int k = 0; k < i; ++k) s -= L[i * qq + k] * M[row * qq + k];
+            M[row * qq + i] = s / L[i * qq + i];
+        }
+    for (int i = 0; i < qq; ++i)   /* symmetrise rounding */
+        for (int j = i + 1; j < qq; ++j) M[i * qq + j] = M[j * qq + i] = 0.5 * (M[i * qq + j] + M[j * qq + i]);
+    jacobi_eig(qq, M, lam, W);
+    /* y' + M y = c with c = L^-1 b_r, y = L^T z; y_inf = M^-1 c = W diag(1/l) W^T c */
+    for (int i = 0; i < qq; ++i) {
+        double s = br[i];
+        for (int k = 0; k < i; ++k) s -= L[i * qq + k] * c[k];
+        c[i] = s / L[i * qq + i];
+    }
+    for (int k = 0; k < qq; ++k) {
+        double s = 0.0;
+        for (int i = 0; i < qq; ++i) s += W[i * qq + k] * c[i];
+        yinf[k] = s / lam[k];   /* modal coordinates of y_inf */
+    }
+    for (int32_t node = 1; node < n; ++node) {
+        /* v_node = e^T V z = h^T y with h = L^-1 V^T e_node; in modal form
+         * v(t) = sum_k (h^T w_k) yinf_k (1 - exp(-l_k t)) */
+        for (int i = 0; i < qq; ++i) {
+            double s = V[i * n + node];
+            for (int k = 0; k < i; ++k) s -= L[i * qq + k] * h[k];
+            h[i] = s / L[i * qq + i];
+        }
+        double vinf = 0.0;
+        for (int k = 0; k < qq; ++k) {
+            double s = 0.0;
+            for (int i = 0; i < qq; ++i) s += h[i] * W[i * qq + k];
+            a[k] = s * yinf[k];
+            vinf += a[k];
+        }
+        /* bracket the first time v reaches vinf / 2, then bisect */
+        double lmin = lam[0];
+        for (int k = 1; k < qq; ++k) lmin = fmin(lmin, lam[k]);
+        double hi = 1.0 / lmin, lo = 0.0;
+        for (int it = 0; it < 200; ++it) {
+            double v = 0.0;
+            for (int k = 0; k < qq; ++k) v += a[k] * (1.0 - exp(-lam[k] * hi));
+            if (v >= 0.5 * vinf) break;
+            lo = hi;
+            hi *= 2.0;
+        }
+        for (int it = 0; it < 200; ++it) {
+            const double mid = 0.5 * (lo + hi);
+            double v = 0.0;
+            for (int k = 0; k < qq; ++k) v += a[k] * (1.0 - exp(-lam[k] * mid));
+            if (v >= 0.5 * vinf) hi = mid;
+            else lo = mid;
+        }
+        t50[node] = 0.5 * (lo + hi);
+    }
+done:
+    free(V); free(y); free(x); free(Gr); free(Cr); free(L); free(M); free(T); free(W);
+    free(lam); free(br); free(c); free(yinf); free(h); free(a);
+    return rc;
 }
 
 /* --------------------------------------------------------- helpers */
@@ -329,6 +539,10 @@ int orc_net_delays(const orc_design *d, int32_t corner, double *load_pf, double 
         }
         rc = orc_rc_tree(nn, par, R, C, cd, Dd, be, va);
         if (rc) goto next;
+        if (d->net_model == 1 && d->rc_ptr) {
+            rc = orc_arnoldi_t50(nn, par, R, C, d->arnoldi_order, Dd);   /* O7 delays replace Elmore's */
+            if (rc) goto next;
+        }
         load_pf[d->net_pin[b]] = 1e-3 * cd[0];
         for (int32_t k = b + 1; k < e; ++k) {
             int32_t node = d->rc_ptr ? d->rc_pin_node[k] : k - b;

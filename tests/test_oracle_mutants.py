@@ -56,6 +56,20 @@ MUTANTS = [
     ("endpoint_best_edge", "double ss = fmin(slack[IX(p, k, JJ(1, 0))], slack[IX(p, k, JJ(1, 1))]);",
      "double ss = fmax(slack[IX(p, k, JJ(1, 0))], slack[IX(p, k, JJ(1, 1))]);", 0),
     ("cycle_not_detected", "if (mark[q] == 1) {", "if (mark[q] == 3) {", 0),
+    # O7 Arnoldi reduced-order net model
+    ("arn_tree_solve_path", "for (int32_t i = 1; i < n; ++i) x[i] = x[parent[i]] + R[i] * x[i];",
+     "for (int32_t i = 1; i < n; ++i) x[i] = R[i] * x[i];", 0),
+    ("arn_start_vector", "for (int32_t i = 1; i < n; ++i) V[i] = 1.0 / sqrt((double)m);",
+     "for (int32_t i = 1; i < n; ++i) V[i] = (double)i / m;", 0),
+    ("arn_gram_schmidt_sign", "for (int32_t i = 1; i < n; ++i) x[i] -= dot * V[p * n + i];",
+     "for (int32_t i = 1; i < n; ++i) x[i] += dot * V[p * n + i];", 0),
+    ("arn_edge_conductance", "g += dp * dr / R[i];", "g += dp * dr * R[i];", 0),
+    ("arn_cap_weight", "cc += C[i] * V[p * n + i] * V[r * n + i];", "cc += V[p * n + i] * V[r * n + i];", 0),
+    ("arn_root_conductance", "if (parent[i] == 0) s += V[p * n + i] / R[i];", "if (parent[i] == 0) s += V[p * n + i] * R[i];", 0),
+    ("arn_cholesky_diag", "L[i * qq + i] = sqrt(s);", "L[i * qq + i] = s;", 0),
+    ("arn_modal_inverse", "yinf[k] = s / lam[k];", "yinf[k] = s * lam[k];", 0),
+    ("arn_half_threshold", "if (v >= 0.5 * vinf) hi = mid;", "if (v >= 0.4 * vinf) hi = mid;", 0),
+    ("arn_model_switch", "if (d->net_model == 1 && d->rc_ptr) {", "if (d->net_model == 2 && d->rc_ptr) {", 0),
     # O6 smoothed objective and its adjoint
     ("tns_softplus_sign", "tns += -g * softplus(-seed[p] / g);", "tns += -g * softplus(seed[p] / g);", 0),
     ("seed_sigmoid_sign", "w_tns * sigmoid(-s / g)", "w_tns * sigmoid(s / g)", 0),
