@@ -220,7 +220,10 @@ static void jacobi_eig(int q, double *a, double *w, double *v)
  * with l_k the eigenvalues of C_r^-1 G_r (through the Cholesky factor of
  * C_r and a symmetric eigensolve).  t50[i] = the time v_i(t) first reaches
  * half its final value (bisection), for every node (t50[0] = 0).  q is
- * capped at m; q = m reproduces the unreduced response. */
+ * capped at m; q = m reproduces the unreduced response.  The basis stops
+ * growing when a new direction's part orthogonal to the basis is below
+ * 1e-5 of its length (the Krylov space is exhausted, e.g. by symmetric
+ * branches): what is left is rounding, not a direction. */
 int orc_arnoldi_t50(int32_t n, const int32_t *parent, const double *R, const double *C, int32_t q_in, double *t50)
 {
     if (n <= 0 || parent[0] != -1 || q_in < 1) return ERR_INVAL;
@@ -250,6 +253,9 @@ int orc_arnoldi_t50(int32_t n, const int32_t *parent, const double *R, const dou
     for (int j = 1; j < q; ++j) {
         for (int32_t i = 0; i < n; ++i) y[i] = i ? C[i] * V[(j - 1) * n + i] : 0.0;
         tree_solve(n, parent, R, y, x);
+        double len = 0.0;
+        for (int32_t i = 1; i < n; ++i) len += x[i] * x[i];
+        len = sqrt(len);
         for (int p = 0; p < j; ++p) {   /* modified Gram-Schmidt */
             double dot = 0.0;
             for (int32_t i = 1; i < n; ++i) dot += V[p * n + i] * x[i];
@@ -258,7 +264,7 @@ int orc_arnoldi_t50(int32_t n, const int32_t *parent, const double *R, const dou
         double nrm = 0.0;
         for (int32_t i = 1; i < n; ++i) nrm += x[i] * x[i];
         nrm = sqrt(nrm);
-        if (!(nrm > 1e-300)) break;   /* the Krylov space is exhausted */
+        if (!(nrm > 1e-5 * len)) break;   /* the Krylov space is exhausted (to 1e-5 of the new direction) */
         for (int32_t i = 1; i < n; ++i) V[j * n + i] = x[i] / nrm;
         qq = j + 1;
     }

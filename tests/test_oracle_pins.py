@@ -562,6 +562,10 @@ def test_arnoldi_single_rc_closed_form():
     for q in (1, 2, 3):
         t = oracle.arnoldi_t50([-1, 0], [0.0, 12.5], [0.0, 3.2], q)
         assert t[1] == pytest.approx(12.5 * 3.2 * np.log(2), rel=1e-12)
+    # identical branches off the driver: each is that single RC, and the
+    # Krylov space stops at one direction (the exhausted-space path)
+    t = oracle.arnoldi_t50([-1, 0, 0, 0], [0.0, 12.5, 12.5, 12.5], [0.0, 3.2, 3.2, 3.2], 3)
+    np.testing.assert_allclose(t[1:], 12.5 * 3.2 * np.log(2), rtol=1e-12)
 
 
 def test_arnoldi_first_order_is_the_lumped_pole():
