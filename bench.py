@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--seed", type=int, default=0)
     ap.add_argument("--schedule", default="dataflow", choices=["level", "dataflow", "coop", "auto"],
                     help="propagation schedule; auto = sta_autotune's choice")
+    ap.add_argument("--net-model", default="elmore", choices=["elmore", "arnoldi"],
+                    help="net delay calculator of the scale/mid workloads (arnoldi: order-3 reduced model)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the update only (no e2e, CPU baseline, batch, gradient or clock sampling); for profilers")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched-vs-plain comparison")
@@ -207,6 +209,8 @@ def run_ours(a, dist: Dist):
     torch.cuda.set_device(dist.local)
     dev = dist.local
     d = make_workload(a.workload, a.seed)
+    if a.net_model == "arnoldi":
+        d.update(net_model=sta.NET_ARNOLDI, arnoldi_order=3)
     dstats = synth.design_stats(d)
     ctx = sta.Context(d, device=dev)
     sched_names = {sta.SCHED_LEVEL: "level", sta.SCHED_DATAFLOW: "dataflow", sta.SCHED_COOP: "coop"}
@@ -257,7 +261,7 @@ def run_ours(a, dist: Dist):
                       "cells": dstats["cells"], "pins": dstats["pins"], "cell_arcs": dstats["cell_arcs"],
                       "net_arcs": dstats["net_arcs"], "rc_nodes": dstats["rc_nodes"],
                       "endpoints": dstats["endpoints"], "levels": st["n_levels"], "corners": K,
-                      "period_ns": T, "schedule": schedule,
+                      "period_ns": T, "schedule": schedule, "net_model": a.net_model,
                       "parallelism": "replicas x%d" % dist.world if dist.world > 1 else "1 GPU",
                       "l2": "no flush: per-pass working set %.0f MB > 126 MB L2" % (st["device_bytes"] / 1e6),
                       "wns_setup_ns": rep["wns_setup"], "tns_setup_ns": rep["tns_setup"],

@@ -120,6 +120,18 @@ typedef struct {
  * lut_scale[k] and every wire R and C by rc_scale[k] (NULL = all 1).
  * gamma_ns > 0 selects log-sum-exp smoothed max/min merges (differentiable
  * mode, required for sta_backward); 0 = exact max/min.
+ * Net delay calculator (Sec. III "Delay models": an Elmore calculator and
+ * an Arnoldi-based reduced-order model), RC trees only for the latter:
+ *   STA_NET_ELMORE:  sink delay = Elmore delay (first moment of the impulse
+ *     response);
+ *   STA_NET_ARNOLDI: sink delay = the time the step response of an
+ *     order-q reduced model reaches 50%.  The model projects the tree's
+ *     nodal equations C v' + G v = b u (driver node held at u) onto an
+ *     orthonormal basis of the Krylov space of G^-1 C started at the DC
+ *     solution (congruence, so it stays passive); q = arnoldi_order (1..3,
+ *     0 = 3), capped by the number of non-driver nodes.
+ *   Both keep the slew law slew_sink = sqrt(slew_drv^2 + 2 beta - D^2) with
+ *   the tree's second moment (an order >= 2 model matches it exactly).
  */
 typedef struct {
     const sta_library *lib;
@@ -147,7 +159,12 @@ typedef struct {
     const float *lut_scale;
     const float *rc_scale;
     float gamma_ns;
+    int32_t net_model;      /* STA_NET_ELMORE (0) or STA_NET_ARNOLDI (1) */
+    int32_t arnoldi_order;  /* q of STA_NET_ARNOLDI: 1..3, 0 = 3 */
 } sta_design_desc;
+
+/* net delay calculators (sta_design_desc.net_model) */
+enum { STA_NET_ELMORE = 0, STA_NET_ARNOLDI = 1 };
 
 /* Sizes of a levelised design (sta_plan / sta_stats). */
 typedef struct {

@@ -10,6 +10,7 @@
 namespace sta {
 
 constexpr int kLutStride = 80;   // floats per packed table, see plan.cpp
+constexpr int kNetArnoldi = 1;     // DevCtx::net_model of the reduced-order calculator (STA_NET_ARNOLDI)
 constexpr int kRcColNodes = 16;    // RC nets up to this size are swept in shared memory (as plan.h)
 constexpr int kRcThreads = 128;    // threads (nets) per block of the RC sweep
 constexpr int kRedThreads = 256;   // threads of the reduction kernels
@@ -26,6 +27,7 @@ struct DevCtx {
     int32_t KL;                                 // quads per item: corners handled side by side (1, 2, 4 or 8)
     int64_t NN;                                 // RC nodes
     int32_t F;                                  // net sinks (fan-out entries)
+    int32_t net_model, arnoldi_q;               // STA_NET_ELMORE / STA_NET_ARNOLDI and its order
     float period, clk_slew, pi_at, pi_slew, setup, hold, gamma, inv_gamma;
     float r_per_um, c_per_um;
     const float *lut;          // [T][3][4][80]
@@ -49,7 +51,7 @@ struct DevCtx {
     const int32_t *red_design_chunk;            // [n_designs+1] chunk ranges per design
     double *red_partial;                        // [n_red_chunks][K][6] scratch
     unsigned *err;
-    float *scratch_a, *scratch_b;               // [K][NN] RC sweeps of nets larger than kRcColNodes
+    float *scratch_a, *scratch_b, *scratch_c;   // [K][NN] RC sweeps of nets larger than kRcColNodes
     // dataflow schedule: mailboxes by epoch parity, NaN until published
     float4 *fbox;                               // [2][P][K][2] arrival, slew of driver pins
     float4 *rbox;                               // [2][P][K]    required time of gate input pins

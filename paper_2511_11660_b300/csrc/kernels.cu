@@ -37,6 +37,235 @@ struct ColRef {
     __device__ __forceinline__ float &operator[](int i) const { return base[i * stride]; }
 };
 
+// Symmetric 3x3 (or smaller) eigen-decomposition by cyclic Jacobi rotations
+// (a row-major, overwritten; eigenvectors in the columns of v).
+__device__ __forceinline__ void jacobi3(int q, float a[9], float lam[3], float v[9])
+{
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = (i % 4 == 0) ? 1.f : 0.f;
+    for (int sweep = 0; sweep < 8; ++sweep) {
+        const float off = fabsf(a[1]) + fabsf(a[2]) + fabsf(a[5]);
+        if (!(off > 1e-7f * (fabsf(a[0]) + fabsf(a[4]) + fabsf(a[8])))) break;
+#pragma unroll
+        for (int p = 0; p < 3; ++p)
+#pragma unroll
+            for (int r = p + 1; r < 3; ++r) {
+                if (r >= q) continue;
+                const float apr = a[p * 3 + r];
+                if (fabsf(apr) < 1e-30f) continue;
+                const float theta = (a[r * 3 + r] - a[p * 3 + p]) / (2.f * apr);
+                const float tt = copysignf(1.f, theta) / (fabsf(theta) + sqrtf(theta * theta + 1.f));
+                const float cs = rsqrtf(tt * tt + 1.f), sn = tt * cs;
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float akp = a[k * 3 + p], akr = a[k * 3 + r];
+                    a[k * 3 + p] = cs * akp - sn * akr;
+                    a[k * 3 + r] = sn * akp + cs * akr;
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float apk = a[p * 3 + k], ark = a[r * 3 + k];
+                    a[p * 3 + k] = cs * apk - sn * ark;
+                    a[r * 3 + k] = sn * apk + cs * ark;
+                }
+#pragma unroll
+                for (int k = 0; k < 3; ++k) {
+                    const float vkp = v[k * 3 + p], vkr = v[k * 3 + r];
+                    v[k * 3 + p] = cs * vkp - sn * vkr;
+                    v[k * 3 + r] = sn * vkp + cs * vkr;
+                }
+            }
+    }
+#pragma unroll
+    for (int i = 0; i < 3; ++i) lam[i] = a[i * 4];
+}
+
+// The Arnoldi reduced-order delays of one net at one corner (STA_NET_ARNOLDI),
+// the same steps as the FP64 reference in FP32 with q <= 3:
+//   Krylov basis of G^-1 Cn from v1 = 1/sqrt(m) (implicit) -- each new
+//   direction by one tree solve (subtree sums, then path sums of R times
+//   them), modified Gram-Schmidt, and the basis stops when the orthogonal
+//   part is below 1e-5 of the direction (space exhausted); v2 in A, v3 in B;
+//   G_r = sum over edges of dv dv / R, C_r = sum Cn v v, b_r = sum over the
+//   driver's edges of v / R; C_r = L L^T, M = L^-1 G_r L^-T = W diag(l) W^T;
+//   sink s: v_s(t) = sum_k a_k (1 - exp(-l_k t)) with a_k = (h^T w_k)
+//   (w_k^T M^-1 L^-1 b_r), h = L^-1 V^T e_s; netD = the 50% crossing,
+//   bracketed by doubling, then safeguarded Newton steps inside the bracket
+//   (bisection wherever a step would leave it) to FP32 resolution.
+template <class Par, class Rf>
+__device__ void arnoldi_delays(const DevCtx &c, int n, float f, int q_req, const ColRef &A, const ColRef &B,
+                               const ColRef &Cn, Par par, Rf Rv, int f0, int f1, int K, int k)
+{
+    const int m = n - 1;
+    const int qmax = min(q_req, m);
+    const float c1 = rsqrtf((float)m);
+    int qq = 1;
+    // direction 2 from v1, direction 3 from v2
+    for (int j = 1; j < qmax; ++j) {
+        const ColRef &X = j == 1 ? A : B;   // the new direction's column
+        for (int i = 1; i < n; ++i) X[i] = Cn[i] * (j == 1 ? c1 : A[i]);
+        X[0] = 0.f;
+        for (int i = n - 1; i > 0; --i) {
+            const int p = par(i);
+            if (p > 0) X[p] += X[i];
+        }
+        for (int i = 1; i < n; ++i) X[i] = (par(i) > 0 ? X[par(i)] : 0.f) + f * Rv(i) * X[i];
+        float len = 0.f, d1 = 0.f;
+        for (int i = 1; i < n; ++i) {
+            len += X[i] * X[i];
+            d1 += c1 * X[i];
+        }
+        len = sqrtf(len);
+        for (int i = 1; i < n; ++i) X[i] -= d1 * c1;
+        if (j == 2) {
+            float d2 = 0.f;
+            for (int i = 1; i < n; ++i) d2 += A[i] * X[i];
+            for (int i = 1; i < n; ++i) X[i] -= d2 * A[i];
+        }
+        float nrm = 0.f;
+        for (int i = 1; i < n; ++i) nrm += X[i] * X[i];
+        nrm = sqrtf(nrm);
+        if (!(nrm > 1e-5f * len)) break;
+        const float inv = 1.f / nrm;
+        for (int i = 1; i < n; ++i) X[i] *= inv;
+        qq = j + 1;
+    }
+    // projected matrices
+    float Gr[9] = {}, Cr[9] = {}, br[3] = {};
+    for (int i = 1; i < n; ++i) {
+        const int p = par(i);
+        const float g = 1.f / (f * Rv(i));
+        const float v[3] = {c1, qq > 1 ? A[i] : 0.f, qq > 2 ? B[i] : 0.f};
+        const float vp[3] = {p > 0 ? c1 : 0.f, (qq > 1 && p > 0) ? A[p] : 0.f, (qq > 2 && p > 0) ? B[p] : 0.f};
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            if (p == 0) br[a] += v[a] * g;
+#pragma unroll
+            for (int b = 0; b < 3; ++b) {
+                Gr[a * 3 + b] += (v[a] - vp[a]) * (v[b] - vp[b]) * g;
+                Cr[a * 3 + b] += Cn[i] * v[a] * v[b];
+            }
+        }
+    }
+    // Cholesky of C_r, M = L^-1 G_r L^-T, eigen-decomposition, modal steady state
+    float L[9] = {}, T[9] = {}, M[9] = {}, W[9], lam[3], cc[3] = {}, yinf[3] = {};
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = 0; j <= i; ++j) {
+            if (i >= qq) continue;
+            float s = Cr[i * 3 + j];
+#pragma unroll
+            for (int t = 0; t < j; ++t) s -= L[i * 3 + t] * L[j * 3 + t];
+            if (i == j) L[i * 4] = sqrtf(fmaxf(s, 1e-30f));
+            else L[i * 3 + j] = s / L[j * 4];
+        }
+#pragma unroll
+    for (int col = 0; col < 3; ++col)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (i >= qq || col >= qq) continue;
+            float s = Gr[i * 3 + col];
+#pragma unroll
+            for (int t = 0; t < i; ++t) s -= L[i * 3 + t] * T[t * 3 + col];
+            T[i * 3 + col] = s / L[i * 4];
+        }
+#pragma unroll
+    for (int row = 0; row < 3; ++row)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            if (i >= qq || row >= qq) continue;
+            float s = T[row * 3 + i];
+#pragma unroll
+            for (int t = 0; t < i; ++t) s -= L[i * 3 + t] * M[row * 3 + t];
+            M[row * 3 + i] = s / L[i * 4];
+        }
+#pragma unroll
+    for (int i = 0; i < 3; ++i)
+#pragma unroll
+        for (int j = i + 1; j < 3; ++j) M[i * 3 + j] = M[j * 3 + i] = 0.5f * (M[i * 3 + j] + M[j * 3 + i]);
+    jacobi3(qq, M, lam, W);
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        if (i >= qq) continue;
+        float s = br[i];
+#pragma unroll
+        for (int t = 0; t < i; ++t) s -= L[i * 3 + t] * cc[t];
+        cc[i] = s / L[i * 4];
+    }
+    float lmin = INFINITY;
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk) {
+        if (kk >= qq) continue;
+        float s = 0.f;
+#pragma unroll
+        for (int i = 0; i < 3; ++i)
+            if (i < qq) s += W[i * 3 + kk] * cc[i];
+        yinf[kk] = s / lam[kk];
+        lmin = fminf(lmin, lam[kk]);
+    }
+    // every sink: its modal weights and its 50% crossing
+    for (int q = f0; q < f1; ++q) {
+        const int node = chk(c, __ldg(c.fo_node + q), n);
+        const int s = chk(c, __ldg(c.fo_pin + q), c.P);
+        float t50 = 0.f;
+        if (node > 0) {
+            const float e[3] = {c1, qq > 1 ? A[node] : 0.f, qq > 2 ? B[node] : 0.f};
+            float h[3] = {}, a[3] = {};
+            float vinf = 0.f;
+#pragma unroll
+            for (int i = 0; i < 3; ++i) {
+                if (i >= qq) continue;
+                float sum = e[i];
+#pragma unroll
+                for (int t = 0; t < i; ++t) sum -= L[i * 3 + t] * h[t];
+                h[i] = sum / L[i * 4];
+            }
+#pragma unroll
+            for (int kk = 0; kk < 3; ++kk) {
+                if (kk >= qq) continue;
+                float sum = 0.f;
+#pragma unroll
+                for (int i = 0; i < 3; ++i)
+                    if (i < qq) sum += h[i] * W[i * 3 + kk];
+                a[kk] = sum * yinf[kk];
+                vinf += a[kk];
+            }
+            // v(t) - vinf/2 and its derivative (one exponential per pole)
+            auto resp = [&](float t, float &dv) {
+                float v = -0.5f * vinf;
+                dv = 0.f;
+#pragma unroll
+                for (int kk = 0; kk < 3; ++kk)
+                    if (kk < qq) {
+                        const float ex = expf(-lam[kk] * t);
+                        v += a[kk] * (1.f - ex);
+                        dv += a[kk] * lam[kk] * ex;
+                    }
+                return v;
+            };
+            float dv;
+            float lo = 0.f, hi = 1.f / lmin;
+            for (int it = 0; it < 64 && resp(hi, dv) < 0.f; ++it) {
+                lo = hi;
+                hi *= 2.f;
+            }
+            // safeguarded Newton inside [lo, hi], from the dominant pole's ln 2 / l
+            float t = fminf(fmaxf(0.69314718f / lmin, lo), hi);
+            for (int it = 0; it < 24 && hi - lo > 1e-7f * hi; ++it) {
+                const float v = resp(t, dv);
+                if (v >= 0.f) hi = t;
+                else lo = t;
+                float tn = t - v / dv;
+                if (!(dv > 0.f) || !(tn > lo && tn < hi)) tn = 0.5f * (lo + hi);
+                t = tn;
+            }
+            t50 = t;
+        }
+        c.netD[(size_t)s * K + k] = 1e-6f * t50;
+    }
+}
+
 __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
 {
     __shared__ int8_t s_par[kRcColNodes * kRcThreads];
@@ -126,6 +355,13 @@ __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
                     c.netD[(size_t)sp[u] * K + k] = 1e-6f * Dn;
                     c.netV[(size_t)sp[u] * K + k] = 1e-12f * fmaxf(2.f * B[nd[u]] - Dn * Dn, 0.f);
                 }
+        }
+        if (c.net_model == kNetArnoldi && n > 1) {
+            // node capacitance again (wire * f + sink pins), in the C column
+            const ColRef Cn = col ? ColRef{s_C + t, kRcThreads} : ColRef{c.scratch_c + so, 1};
+            for (int i = 0; i < n; ++i) Cn[i] = f * Cv(i);
+            for (int q = f0; q < f1; ++q) Cn[chk(c, __ldg(c.fo_node + q), n)] += 1e3f * __ldg(c.fo_cap + q);
+            arnoldi_delays(c, n, f, c.arnoldi_q, A, B, Cn, par, Rv, f0, f1, K, k);
         }
     }
 }

@@ -125,6 +125,13 @@ void build(const sta_design_desc *d, Plan &pl)
                 finite(d->pi_slew_ns) && d->pi_slew_ns >= 0,
             STA_EINVAL, "clock / input constraints not finite or negative slew");
     REQUIRE(finite(d->gamma_ns) && d->gamma_ns >= 0, STA_EINVAL, "gamma_ns must be finite and >= 0");
+    REQUIRE(d->net_model == STA_NET_ELMORE || d->net_model == STA_NET_ARNOLDI, STA_EINVAL,
+            "net_model must be STA_NET_ELMORE or STA_NET_ARNOLDI");
+    REQUIRE(d->net_model == STA_NET_ELMORE || d->rc_ptr, STA_EINVAL, "STA_NET_ARNOLDI needs RC trees (rc_ptr)");
+    REQUIRE(d->net_model == STA_NET_ELMORE || (d->arnoldi_order >= 0 && d->arnoldi_order <= 3), STA_EINVAL,
+            "arnoldi_order must be in 0..3");
+    pl.net_model = d->net_model;
+    pl.arnoldi_q = d->arnoldi_order > 0 ? d->arnoldi_order : 3;
     pl.period = d->period_ns;
     pl.clk_slew = d->clk_slew_ns;
     pl.pi_at = d->pi_at_ns;
@@ -479,10 +486,12 @@ sta_status build_batch_plan(const sta_design_desc *const *descs, int32_t n, Plan
                         di.period_ns == d0.period_ns && di.clk_slew_ns == d0.clk_slew_ns &&
                         di.pi_at_ns == d0.pi_at_ns && di.pi_slew_ns == d0.pi_slew_ns &&
                         di.gamma_ns == d0.gamma_ns && di.r_per_um == d0.r_per_um && di.c_per_um == d0.c_per_um &&
+                        di.net_model == d0.net_model && di.arnoldi_order == d0.arnoldi_order &&
                         (K < 1 || K > 16 || (same_array(di.lut_scale, d0.lut_scale, (size_t)K) &&
                                              same_array(di.rc_scale, d0.rc_scale, (size_t)K)));
         if (!ok) {
-            err = "design " + std::to_string(i) + " differs from design 0 in library, corners, clock or parasitic kind";
+            err = "design " + std::to_string(i) +
+                  " differs from design 0 in library, corners, clock, parasitic kind or net model";
             return STA_EINVAL;
         }
         if (di.n_cells < 0 || di.n_pins < 0 || di.n_nets < 0) { err = "negative size"; return STA_EINVAL; }

@@ -34,6 +34,8 @@ struct Plan {
     int32_t n_designs = 1;
     bool placed = false;
     float gamma = 0.f;
+    int32_t net_model = STA_NET_ELMORE;      // net delay calculator
+    int32_t arnoldi_q = 3;                   // order of STA_NET_ARNOLDI
     // constraints
     float period = 1.f, clk_slew = 0.02f, pi_at = 0.f, pi_slew = 0.02f;
     float setup = 0.f, hold = 0.f, po_cap = 0.f;

@@ -135,6 +135,8 @@ sta_status create_from_plan(sta_ctx *c, int device)
     d.K = pl.K;
     d.NN = pl.NN;
     d.F = (int32_t)pl.F;
+    d.net_model = pl.net_model;
+    d.arnoldi_q = pl.arnoldi_q;
     d.T = pl.T;
     d.C = pl.C;
     d.n_designs = pl.n_designs;
@@ -212,6 +214,7 @@ sta_status create_from_plan(sta_ctx *c, int device)
     if (pl.n_big_nets > 0) {
         d.scratch_a = dev_alloc<float>(c, (size_t)pl.NN * pl.K);
         d.scratch_b = dev_alloc<float>(c, (size_t)pl.NN * pl.K);
+        if (pl.net_model == STA_NET_ARNOLDI) d.scratch_c = dev_alloc<float>(c, (size_t)pl.NN * pl.K);
     }
     HostSched &h = c->hs;
     h.S = pl.S;

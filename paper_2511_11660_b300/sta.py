@@ -21,6 +21,7 @@ OK, EINVAL, ECYCLE, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(7)
 HOST, DEVICE = 0, 1
 AT, SLEW, RAT, SLACK = 0, 1, 2, 3
 SCHED_LEVEL, SCHED_DATAFLOW, SCHED_COOP = 0, 1, 2
+NET_ELMORE, NET_ARNOLDI = 0, 1
 
 
 class StaError(RuntimeError):
@@ -45,7 +46,8 @@ class sta_design_desc(C.Structure):
                 ("cell_xy", C.c_void_p), ("port_xy", C.c_void_p), ("r_per_um", C.c_float),
                 ("c_per_um", C.c_float), ("period_ns", C.c_float), ("clk_slew_ns", C.c_float),
                 ("pi_at_ns", C.c_float), ("pi_slew_ns", C.c_float), ("n_corners", C.c_int32),
-                ("lut_scale", C.c_void_p), ("rc_scale", C.c_void_p), ("gamma_ns", C.c_float)]
+                ("lut_scale", C.c_void_p), ("rc_scale", C.c_void_p), ("gamma_ns", C.c_float),
+                ("net_model", C.c_int32), ("arnoldi_order", C.c_int32)]
 
 
 class sta_plan_info(C.Structure):
@@ -183,7 +185,8 @@ class Design:
             None if placed else _ptr(a["rc_C"]), _ptr(a["cell_xy"]), _ptr(a["port_xy"]),
             float(d.get("r_per_um", 0.0)), float(d.get("c_per_um", 0.0)), float(d["period_ns"]),
             float(d["clk_slew_ns"]), float(d["pi_at_ns"]), float(d["pi_slew_ns"]), int(d.get("n_corners", 1)),
-            _ptr(a["lut_scale"]), _ptr(a["rc_scale"]), float(d.get("gamma_ns", 0.0)))
+            _ptr(a["lut_scale"]), _ptr(a["rc_scale"]), float(d.get("gamma_ns", 0.0)),
+            int(d.get("net_model", 0)), int(d.get("arnoldi_order", 0)))
 
     @property
     def n_pins(self):

@@ -237,3 +237,33 @@ def test_high_fanout_net(schedule):
     for k, w in (("at", sta.AT), ("slew", sta.SLEW), ("rat", sta.RAT), ("slack", sta.SLACK)):
         assert_close(k, ctx.get_pin_state(w), ref[k])
     ctx.close()
+
+
+@pytest.mark.parametrize("case", ["small", "big", "corners", "order1", "order2"])
+def test_arnoldi_net_model_parity(case):
+    """STA_NET_ARNOLDI: sink delays from the order-q reduced model, every
+    arrival, slew, required time and slack against the FP64 oracle running
+    the same model; small trees sweep in shared memory, 20-60 node trees in
+    global scratch; every schedule gives the same bits."""
+    if case == "big":
+        d = synth.make_design(600, 8, seed=9, rc_nodes=(20, 60))
+    elif case == "corners":
+        ls, rs = synth.lut_corners()
+        d = synth.make_design(3000, 20, seed=4, n_corners=4, lut_scale=ls, rc_scale=rs)
+    else:
+        d = synth.make_design(4000, 25, seed=2, rc_nodes=(2, 16))
+    d.update(net_model=sta.NET_ARNOLDI, arnoldi_order={"order1": 1, "order2": 2}.get(case, 3))
+    d["period_ns"], _ = tune_period(d)
+    ref = oracle.sta(d)
+    outs = []
+    for sch in (sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP):
+        ctx = sta.Context(d)
+        ctx.set_schedule(sch)
+        ctx.update_timing()
+        outs.append({k: ctx.get_pin_state(w) for k, w in (("at", sta.AT), ("slew", sta.SLEW), ("rat", sta.RAT),
+                                                           ("slack", sta.SLACK))})
+        ctx.close()
+    for k in ("at", "slew", "rat", "slack"):
+        for o in outs[1:]:
+            np.testing.assert_array_equal(o[k], outs[0][k], err_msg=k)
+        assert_close(k, outs[0][k], ref[k])

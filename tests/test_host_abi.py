@@ -95,6 +95,20 @@ def test_plan_rejects_malformed_inputs(lib):
         assert ei.value.status == sta.EINVAL, i
 
 
+def test_plan_net_model_validation(lib):
+    """STA_NET_ARNOLDI needs RC trees and an order in 0..3; unknown models
+    are rejected; a valid Arnoldi design plans like its Elmore twin."""
+    d = synth.make_design(200, 6, seed=1)
+    base = sta.sta_plan(d)
+    assert sta.sta_plan(dict(d, net_model=sta.NET_ARNOLDI, arnoldi_order=2)) == base
+    for bad in (dict(d, net_model=2), dict(d, net_model=sta.NET_ARNOLDI, arnoldi_order=4),
+                dict(d, net_model=sta.NET_ARNOLDI, arnoldi_order=-1),
+                dict(synth.make_design(200, 6, seed=1, placed=True), net_model=sta.NET_ARNOLDI)):
+        with pytest.raises(sta.StaError) as ei:
+            sta.sta_plan(bad)
+        assert ei.value.status == sta.EINVAL
+
+
 def test_plan_rejects_floating_input(lib):
     lib_ = synth.make_library(0)
     b = synth.Builder(lib_)
