@@ -238,3 +238,81 @@ def objective(d: dict, w_tns: float = 1.0, w_wns: float = 1.0) -> float:
     J = np.zeros(1, np.float64)
     _check(lib.orc_objective(C.byref(s), float(w_tns), float(w_wns), _ptr(J)), "objective")
     return float(J[0])
+
+
+def report_paths(d: dict, k: int, slack_lt: float = float("inf"), corner: int = 0, res: dict | None = None):
+    """Top-k path report (Sec. III "Report options": top-k, per-endpoint
+    limit, slack threshold, CSR path arrays), per-endpoint limit 1.
+
+    The endpoints whose setup slack at ``corner`` is below ``slack_lt``, in
+    increasing slack (ties: lower endpoint index), the first ``k``; for each
+    its critical path, traced back from the endpoint at the edge with the
+    smaller late slack (ties: rise): a net sink steps to its net's driver with
+    the same edge; a gate output steps to the input arc whose late arrival +
+    NLDM delay (at that input's late slew and the output's load) is largest
+    (ties: lower input slot, then rise before fall); a flip-flop Q steps to
+    its CK (rising edge); the trace stops at a PI or CK.  Returns a list of
+    dicts: endpoint pin, slack, and the pins, edges and late arrivals from the
+    startpoint to the endpoint.  FP64, from this package's own analysis."""
+    res = res if res is not None else sta(d)
+    K = int(d.get("n_corners", 1))
+    sc = float(np.asarray(d["lut_scale"] if d.get("lut_scale") is not None else np.ones(K))[corner])
+    load, _, _ = net_delays(d, corner)
+    role = np.asarray(d["pin_role"])
+    cpp, cp = np.asarray(d["cell_pin_ptr"]), np.asarray(d["cell_pin"])
+    ctype, nin = np.asarray(d["cell_type"]), np.asarray(d["type_nin"])
+    kind = np.asarray(d["type_kind"])
+    sense = np.asarray(d["arc_sense"]).reshape(-1, 3)
+    i1 = np.asarray(d["lut_idx1"]).reshape(-1, 3, 4, 7)
+    i2 = np.asarray(d["lut_idx2"]).reshape(-1, 3, 4, 7)
+    vv = np.asarray(d["lut_val"]).reshape(-1, 3, 4, 49)
+    cell_of = -np.ones(d["n_pins"], int)
+    slot_of = -np.ones(d["n_pins"], int)
+    for c in range(d["n_cells"]):
+        for j in range(cpp[c], cpp[c + 1]):
+            cell_of[cp[j]] = c
+            slot_of[cp[j]] = j - cpp[c]
+    npp, npn = np.asarray(d["net_pin_ptr"]), np.asarray(d["net_pin"])
+    driver = -np.ones(d["n_pins"], int)
+    for n in range(d["n_nets"]):
+        driver[npn[npp[n] + 1:npp[n + 1]]] = npn[npp[n]]
+    at, slew, slack = res["at"][:, corner], res["slew"][:, corner], res["slack"][:, corner]
+    eps, es = res["endpoints"], res["ep_setup"][:, corner]
+    order = sorted((e for e in range(len(eps)) if es[e] < slack_lt), key=lambda e: (es[e], e))[:k]
+    arcs_on = {0: lambda i, o: i == o, 1: lambda i, o: i != o, 2: lambda i, o: True}
+    out = []
+    for e in order:
+        p = int(eps[e])
+        rf = 0 if slack[p, 2] <= slack[p, 3] else 1
+        pins, rfs = [], []
+        while True:
+            if len(pins) > d["n_pins"]:
+                raise RuntimeError("oracle report_paths: path longer than the design")
+            pins.append(p)
+            rfs.append(rf)
+            if driver[p] >= 0:                       # net sink: to the driver, same edge
+                p = int(driver[p])
+                continue
+            if role[p] in (0, 5):                    # PI or CK: the startpoint
+                break
+            c = cell_of[p]
+            t = ctype[c]
+            if kind[t] == 1:                         # Q: to CK (the rising-edge input slot)
+                p, rf = int(cp[cpp[c] + int(np.nonzero(sense[t] == 3)[0][0])]), 0
+                continue
+            best, arg = -np.inf, None
+            for j in range(nin[t]):
+                a = int(cp[cpp[c] + j])
+                for rfi in (0, 1):
+                    if sense[t, j] < 0 or not arcs_on[int(sense[t, j])](rfi, rf):
+                        continue
+                    dl = lut_eval(i1[t, j, rf], i2[t, j, rf], vv[t, j, rf], slew[a, 2 + rfi], load[p])[0]
+                    cand = at[a, 2 + rfi] + sc * dl
+                    if cand > best:
+                        best, arg = cand, (a, rfi)
+            p, rf = arg
+        pins.reverse()
+        rfs.reverse()
+        out.append({"endpoint": int(eps[e]), "slack": float(es[e]), "pins": np.array(pins),
+                    "rf": np.array(rfs, np.int8), "at": np.array([at[q, 2 + r] for q, r in zip(pins, rfs)])})
+    return out

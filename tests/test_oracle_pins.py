@@ -641,3 +641,63 @@ def test_arnoldi_net_model_in_the_analysis():
     assert np.all(D1[D0 > 0] < D0[D0 > 0])
     r = oracle.sta(da)
     assert np.isfinite(r["tns_setup"][0])
+
+
+# ------------------------------------------------------- top-k path report
+
+def _arc_ok(d, net, u, ru, v, rv):
+    """u -> v is a timing arc with edges ru -> rv (net arc: same edge)."""
+    role = np.asarray(d["pin_role"])
+    if net.driver.get(v) == u:
+        return ru == rv
+    c = net.cell_of[v]
+    if c < 0 or net.cell_of[u] != c:
+        return False
+    t = d["cell_type"][c]
+    se = np.asarray(d["arc_sense"]).reshape(-1, 3)[t, net.slot_of[u]]
+    if role[v] == synth.Q:
+        return se == _indep.RISE and ru == 0
+    return ru in _indep.rf_in_of(se, rv)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_paths_are_longest_paths_fixed_delay(seed):
+    """With slew-independent delays every reported path is made of timing
+    arcs with consistent edges, and it is a longest path: its arrival at the
+    endpoint equals the maximum over all enumerated paths ending there with
+    that edge, and the late arrival along it is the path's own prefix sum."""
+    d = _fixed_design(seed, n_cells=12, depth=5)
+    d["period_ns"] = 0.3
+    res = oracle.sta(d)
+    allp = _indep.enumerate_paths(d)
+    net = _indep.Net(d)
+    paths = oracle.report_paths(d, 50, res=res)
+    assert len(paths) > 0
+    for pth in paths:
+        pins, rfs, at = pth["pins"], pth["rf"], pth["at"]
+        e = pins[-1]
+        assert e == pth["endpoint"]
+        assert np.asarray(d["pin_role"])[pins[0]] in (synth.PI, synth.CK)
+        for (u, ru), (v, rv) in zip(zip(pins[:-1], rfs[:-1]), zip(pins[1:], rfs[1:])):
+            assert _arc_ok(d, net, int(u), int(ru), int(v), int(rv)), (u, v)
+        best = max(a for a, _, f in allp[e] if f == rfs[-1])
+        assert at[-1] == pytest.approx(best, abs=1e-12)
+        # every prefix is tight: arrival = predecessor's arrival + arc delay
+        for i in range(1, len(pins)):
+            v, u = int(pins[i]), int(pins[i - 1])
+            if net.driver.get(v) == u:
+                assert at[i] == pytest.approx(at[i - 1] + net.Dns[v], abs=1e-12)
+        assert pth["slack"] == pytest.approx(res["rat"][e, 0, 2 + rfs[-1]] - at[-1], abs=1e-12)
+
+
+def test_paths_order_threshold_and_count():
+    """Endpoints by increasing setup slack (ties by index), only those below
+    the threshold, at most k of them."""
+    d = synth.make_design(800, 12, seed=3, period_ns=0.9)
+    res = oracle.sta(d)
+    es = res["ep_setup"][:, 0]
+    for k, thr in ((10, np.inf), (1000, 0.0), (5, -0.2)):
+        paths = oracle.report_paths(d, k, slack_lt=thr, res=res)
+        want = sorted((e for e in range(len(es)) if es[e] < thr), key=lambda e: (es[e], e))[:k]
+        assert [p["endpoint"] for p in paths] == [int(res["endpoints"][e]) for e in want]
+        assert all(p["slack"] < thr for p in paths)
