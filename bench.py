@@ -337,6 +337,17 @@ def run_ours(a, dist: Dist):
                   "what": "sta_set_rc from pinned host R/C + sta_update_timing + endpoint slacks and "
                           "violation flags to host + sta_report_slack"}
 
+    # ---- top-k path report (1000 worst endpoints' critical paths, host arrays)
+    ctx.report_paths(1000)
+    t0 = time.perf_counter()
+    n_rep = 5
+    for _ in range(n_rep):
+        paths = ctx.report_paths(1000)
+    out["paths"] = {"k": 1000, "ms_per_report": (time.perf_counter() - t0) / n_rep * 1e3,
+                    "pins": int(sum(len(p["pins"]) for p in paths)),
+                    "what": "sta_report_paths: radix select of the 1000 worst setup endpoints, bitonic sort, "
+                            "critical-path trace, CSR arrays copied to the host"}
+
     del ctx
     torch.cuda.empty_cache()
     if not a.no_grad:

@@ -318,6 +318,32 @@ sta_status sta_get_endpoint_slack(sta_ctx *ctx, float *setup, float *hold, uint8
 sta_status sta_backward(sta_ctx *ctx, double w_tns, double w_wns, double *J_out, double *terms,
                         double *grad_xy, sta_mem mem, void *stream);
 
+/* Top-k path report (Sec. III "Report options": top-k paths with a slack
+ * threshold and a per-endpoint limit, as flattened CSR path pin arrays).
+ * Per-endpoint limit 1: the endpoints of design `design` whose setup slack
+ * at `corner` is below slack_lt (ns; +inf for no threshold), in increasing
+ * slack (ties: lower endpoint index), the first k (k <= 4096); for each its
+ * critical path, traced back from the endpoint at the edge with the smaller
+ * late slack (ties: rise): a net sink steps to its net's driver (same
+ * edge), a gate output to the input arc whose late arrival + NLDM delay is
+ * largest (ties: lower input slot, then rise), a flip-flop Q to its CK
+ * (rising edge); the path starts at a PI or CK.  Outputs (in `mem`, any of
+ * the array pointers may be NULL):
+ *   n_paths, n_pins      host int32: paths reported, pins over all paths;
+ *   path_ptr[n_paths+1]  offsets of each path in the pin arrays;
+ *   path_pin[n_pins]     caller pin ids, startpoint first, endpoint last;
+ *   path_rf[n_pins]      edge at each pin (0 rise, 1 fall);
+ *   path_at[n_pins]      late arrival at each pin (ns);
+ *   path_slack[n_paths]  setup slack of each path's endpoint (ns);
+ *   path_endpoint[n_paths] caller pin id of each endpoint.
+ * Pin arrays hold pin_capacity entries; if the report needs more, returns
+ * STA_EINVAL with n_pins set to the size needed.  Synchronises `stream`.
+ * For a batch, pin ids follow sta_get_pin_state's numbering. */
+sta_status sta_report_paths(sta_ctx *ctx, int32_t design, int32_t corner, int32_t k, float slack_lt,
+                            int32_t *n_paths, int32_t *n_pins, int32_t *path_ptr, int32_t *path_pin,
+                            int8_t *path_rf, float *path_at, float *path_slack, int32_t *path_endpoint,
+                            int32_t pin_capacity, sta_mem mem, void *stream);
+
 /* Device views in the library's internal (level-major) pin order; valid
  * until the next sta_update_timing or sta_destroy.  gpu_pin_of[p] maps a
  * caller pin id to its internal index (device int32 array). */

@@ -61,6 +61,28 @@ cudaError_t adjoint_prepare(HostSched &h);
 // The two-stage FP64 WNS/TNS reduction.
 void launch_reduce(const DevCtx &c, const HostSched &h, cudaStream_t st);
 
+// Top-k path report of one design (paths.cu): selection of the k worst
+// endpoints below a slack threshold and the trace of their critical paths.
+constexpr int kMaxPaths = 4096;   // paths one report returns at most
+struct PathJob {
+    int e0, n;                    // the design's endpoints [e0, e0 + n)
+    int corner, k, max_len;       // max_len: pins a path can hold
+    float slack_lt;
+    const int32_t *pin_item;      // [P] item of an item pin, -1 for endpoint pins
+    const int32_t *caller_pin;    // [P] internal pin -> caller pin id
+    unsigned long long *sel;      // [3] selection state: key prefix, remaining rank
+    unsigned *hist;               // [256] digit histogram (zero between passes)
+    unsigned *count;              // keys selected
+    unsigned long long *keys;     // [kMaxPaths] selected keys, sorted
+    int32_t *ptr;                 // [kMaxPaths + 1] CSR offsets
+    int32_t *pin;                 // [kMaxPaths * max_len] caller pin ids
+    int8_t *rf;                   // edges
+    float *at;                    // late arrivals
+    float *slack;                 // [kMaxPaths] setup slack of each path
+    int32_t *endpoint;            // [kMaxPaths] caller pin id of each endpoint
+};
+void launch_report_paths(const DevCtx &c, const HostSched &h, const PathJob &j, cudaStream_t st);
+
 // Device-side resizing (sta_resize_cells).
 void launch_resize(const DevCtx &c, const int32_t *item_of_cell, const int32_t *d_pin_of_cell,
                    const int32_t *fo_of_pin, const float *type_pin_cap, const int32_t *cells, const int32_t *types,

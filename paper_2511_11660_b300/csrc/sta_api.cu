@@ -46,6 +46,9 @@ struct sta_ctx {
     std::string msg;
     // caller pin -> (cell, slot) for resizing
     std::vector<int32_t> pin_cell_c, pin_slot_c;
+    // path reports (allocated at the first sta_report_paths)
+    sta::PathJob pj{};
+    int32_t path_cap = 0;   // pins the path buffers hold
 };
 
 namespace {
@@ -861,6 +864,84 @@ sta_status sta_get_endpoint_slack(sta_ctx *c, float *setup, float *hold, uint8_t
         if (vs) CK(cudaMemcpyAsync(vs, c->dc.viol_setup, EK, kind, st));
         if (vh) CK(cudaMemcpyAsync(vh, c->dc.viol_hold, EK, kind, st));
         if (mem == STA_HOST) CK(cudaStreamSynchronize(st));
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    return STA_OK;
+}
+
+sta_status sta_report_paths(sta_ctx *c, int32_t design, int32_t corner, int32_t k, float slack_lt, int32_t *n_paths,
+                            int32_t *n_pins, int32_t *path_ptr, int32_t *path_pin, int8_t *path_rf, float *path_at,
+                            float *path_slack, int32_t *path_endpoint, int32_t pin_capacity, sta_mem mem,
+                            void *stream)
+{
+    if (!c || !n_paths || !n_pins) return STA_EINVAL;
+    if (!c->updated) return fail(c, STA_ESTATE, "no analysis yet");
+    const Plan &pl = c->plan;
+    if (design < 0 || design >= pl.n_designs) return fail(c, STA_EINVAL, "design index out of range");
+    if (corner < 0 || corner >= pl.K) return fail(c, STA_EINVAL, "corner index out of range");
+    if (k < 0 || k > sta::kMaxPaths) return fail(c, STA_EINVAL, "k must be in 0..4096");
+    if (std::isnan(slack_lt)) return fail(c, STA_EINVAL, "slack threshold is NaN");
+    try {
+        CK(cudaSetDevice(c->device));
+        cudaStream_t st = as_stream(stream);
+        sta::PathJob &j = c->pj;
+        if (!j.sel) {
+            // item of every item pin, caller id of every internal pin
+            std::vector<int32_t> pin_item(pl.P, -1), caller(pl.P, 0);
+            for (int32_t g = 0; g < pl.I; ++g) {
+                const int32_t t = pl.item_type[g], p0 = pl.item_pin0[g];
+                const int32_t np = t < 0 ? 1 : (pl.type_kind[t] == 1 ? 2 : pl.type_nin[t] + 1);
+                for (int32_t i = 0; i < np; ++i) pin_item[p0 + i] = g;
+            }
+            for (int32_t p = 0; p < pl.P; ++p) caller[pl.gpu_of[p]] = p;
+            j.pin_item = upload(c, pin_item);
+            j.caller_pin = upload(c, caller);
+            j.max_len = 2 * pl.S + 3;
+            c->path_cap = sta::kMaxPaths * j.max_len;
+            j.sel = dev_alloc<unsigned long long>(c, 3);
+            j.hist = dev_alloc<unsigned>(c, 256);
+            j.count = dev_alloc<unsigned>(c, 1);
+            j.keys = dev_alloc<unsigned long long>(c, sta::kMaxPaths);
+            j.ptr = dev_alloc<int32_t>(c, sta::kMaxPaths + 1);
+            j.pin = dev_alloc<int32_t>(c, (size_t)c->path_cap);
+            j.rf = dev_alloc<int8_t>(c, (size_t)c->path_cap);
+            j.at = dev_alloc<float>(c, (size_t)c->path_cap);
+            j.slack = dev_alloc<float>(c, sta::kMaxPaths);
+            j.endpoint = dev_alloc<int32_t>(c, sta::kMaxPaths);
+        }
+        j.e0 = pl.ep_design_ptr[design];
+        j.n = pl.ep_design_ptr[design + 1] - j.e0;
+        j.corner = corner;
+        j.k = k;
+        j.slack_lt = slack_lt;
+        const unsigned long long sel0[3] = {0ull, (unsigned long long)k, 0ull};
+        CK(cudaMemcpyAsync(j.sel, sel0, sizeof(sel0), cudaMemcpyHostToDevice, st));
+        CK(cudaMemsetAsync(j.hist, 0, 256 * sizeof(unsigned), st));
+        CK(cudaMemsetAsync(j.count, 0, sizeof(unsigned), st));
+        CK(cudaMemsetAsync(j.ptr, 0, sizeof(int32_t), st));
+        if (k > 0) sta::launch_report_paths(c->dc, c->hs, j, st);
+        CK(cudaGetLastError());
+        unsigned cnt = 0;
+        CK(cudaMemcpyAsync(&cnt, j.count, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        if (k == 0) cnt = 0;
+        int32_t total = 0;
+        if (cnt > 0) CK(cudaMemcpy(&total, j.ptr + cnt, sizeof(int32_t), cudaMemcpyDeviceToHost));
+        *n_paths = (int32_t)cnt;
+        *n_pins = total;
+        if (total > pin_capacity && (path_pin || path_rf || path_at))
+            return fail(c, STA_EINVAL, "pin arrays too small for the report (n_pins holds the size needed)");
+        const cudaMemcpyKind kind = mem == STA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+        if (path_ptr) CK(cudaMemcpyAsync(path_ptr, j.ptr, (cnt + 1) * sizeof(int32_t), kind, st));
+        if (path_pin && total) CK(cudaMemcpyAsync(path_pin, j.pin, total * sizeof(int32_t), kind, st));
+        if (path_rf && total) CK(cudaMemcpyAsync(path_rf, j.rf, total * sizeof(int8_t), kind, st));
+        if (path_at && total) CK(cudaMemcpyAsync(path_at, j.at, total * sizeof(float), kind, st));
+        if (path_slack && cnt) CK(cudaMemcpyAsync(path_slack, j.slack, cnt * sizeof(float), kind, st));
+        if (path_endpoint && cnt) CK(cudaMemcpyAsync(path_endpoint, j.endpoint, cnt * sizeof(int32_t), kind, st));
+        CK(cudaStreamSynchronize(st));
+        const sta_status se = check_device_error(c);
+        if (se != STA_OK) return se;
     } catch (const CudaFail &f) {
         return from_cuda(c, f);
     }

@@ -100,6 +100,8 @@ SIGNATURES = {
     "sta_report_slack_design": (C.c_int, [_V, C.c_int32, _V, _P]),
     "sta_get_pin_state": (C.c_int, [_V, C.c_int32, _P, C.c_int, _V]),
     "sta_get_endpoint_slack": (C.c_int, [_V, _P, _P, _P, _P, C.c_int, _V]),
+    "sta_report_paths": (C.c_int, [_V, C.c_int32, C.c_int32, C.c_int32, C.c_float, _P, _P, _P, _P, _P, _P, _P, _P,
+                                   C.c_int32, C.c_int, _V]),
     "sta_backward": (C.c_int, [_V, C.c_double, C.c_double, _P, _P, _P, C.c_int, _V]),
     "sta_get_arrays": (C.c_int, [_V, C.POINTER(sta_views)]),
     "sta_stats": (C.c_int, [_V, C.POINTER(sta_plan_info)]),
@@ -337,6 +339,28 @@ class Context:
         if out is None:
             out = np.empty((self.P, self.K, 4), np.float32)
         self._chk(self.lib.sta_get_pin_state(self.h, which, _ptr(out), _mem_of(out), _stream(stream)))
+        return out
+
+    def report_paths(self, k: int, slack_lt: float = float("inf"), corner: int = 0, design: int = 0, stream=None):
+        """Top-k path report (host arrays): a list of dicts with the endpoint
+        pin, its setup slack and the path's pins, edges and late arrivals from
+        the startpoint to the endpoint."""
+        n_paths, n_pins = C.c_int32(0), C.c_int32(0)
+        cap = max(1, k) * (2 * self.stats()["n_levels"] + 3)
+        ptr = np.zeros(max(1, k) + 1, np.int32)
+        pin = np.zeros(cap, np.int32)
+        rf = np.zeros(cap, np.int8)
+        at = np.zeros(cap, np.float32)
+        slack = np.zeros(max(1, k), np.float32)
+        ep = np.zeros(max(1, k), np.int32)
+        self._chk(self.lib.sta_report_paths(self.h, design, corner, k, float(slack_lt), C.byref(n_paths),
+                                            C.byref(n_pins), _ptr(ptr), _ptr(pin), _ptr(rf), _ptr(at), _ptr(slack),
+                                            _ptr(ep), cap, HOST, _stream(stream)))
+        out = []
+        for i in range(n_paths.value):
+            b, e = ptr[i], ptr[i + 1]
+            out.append({"endpoint": int(ep[i]), "slack": float(slack[i]), "pins": pin[b:e].copy(),
+                        "rf": rf[b:e].copy(), "at": at[b:e].copy()})
         return out
 
     def get_endpoint_slack(self, device: bool = False, stream=None):

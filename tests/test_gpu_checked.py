@@ -3,7 +3,8 @@
 on the device, and a violation sets the bounds bit of the device error word,
 which the next synchronising call reports.  This runs representative cases
 through that build -- every schedule, several corners, a batch, large RC
-trees swept in global scratch, star RC and the adjoint -- in a child process
+trees swept in global scratch, star RC, the adjoint and the path report -- in
+a child process
 (the binding holds one library per process), checks them against the FP64
 oracle and requires that no check fired."""
 import os
@@ -40,6 +41,7 @@ for name, d in cases.items():
         ctx.update_timing()
         if d.get("gamma_ns", 0) > 0:
             ctx.backward(1.0, 1.0)
+        ctx.report_paths(64)
         ctx.sync()
         assert_close("at", ctx.get_pin_state(sta.AT), ref["at"])
         assert_close("slack", ctx.get_pin_state(sta.SLACK), ref["slack"])
