@@ -76,6 +76,8 @@ class _Design(C.Structure):
         ("pi_slew_ns", C.c_double), ("n_corners", C.c_int32), ("lut_scale", C.c_void_p),
         ("rc_scale", C.c_void_p), ("gamma_ns", C.c_double),
         ("net_model", C.c_int32), ("arnoldi_order", C.c_int32),
+        ("n_exc", C.c_int32), ("exc_from_ptr", C.c_void_p), ("exc_from", C.c_void_p), ("exc_to_ptr", C.c_void_p),
+        ("exc_to", C.c_void_p), ("exc_action", C.c_void_p), ("exc_mult", C.c_void_p),
     ]
 
 
@@ -86,6 +88,8 @@ _ARRAYS = {
     "net_pin": np.int32, "rc_ptr": np.int32, "rc_parent": np.int32, "rc_pin_node": np.int32,
     "rc_R": np.float32, "rc_C": np.float32, "cell_xy": np.float32, "port_xy": np.float32,
     "lut_scale": np.float32, "rc_scale": np.float32,
+    "exc_from_ptr": np.int32, "exc_from": np.int32, "exc_to_ptr": np.int32, "exc_to": np.int32,
+    "exc_action": np.int32, "exc_mult": np.float32,
 }
 _SCALARS = ("setup_ns", "hold_ns", "po_cap_pf", "r_per_um", "c_per_um", "period_ns", "clk_slew_ns",
             "pi_at_ns", "pi_slew_ns", "gamma_ns")
@@ -115,6 +119,7 @@ def _marshal(d: dict, use_rc: bool | None = None):
     s.n_nets = int(d["n_nets"])
     s.n_corners = int(d.get("n_corners", 1))
     s.net_model = int(d.get("net_model", 0))
+    s.n_exc = int(len(d["exc_action"])) if d.get("exc_action") is not None else 0
     s.arnoldi_order = int(d.get("arnoldi_order", 3))
     if d.get("lut_scale") is None:
         a = np.ones(s.n_corners, np.float32); keep.append(a); s.lut_scale = a.ctypes.data
@@ -192,12 +197,16 @@ def endpoints(d: dict) -> np.ndarray:
 
 
 def sta(d: dict, use_rc: bool | None = None) -> dict:
-    """Full FP64 analysis; see ``orc_sta`` for the array layouts."""
+    """Full FP64 analysis; see ``orc_sta`` for the array layouts.  With
+    timing-exception groups (keys exc_from_ptr, exc_from, exc_to_ptr,
+    exc_to, exc_action, exc_mult) the per-pin arrays hold one state per
+    (corner, tag): index corner * (groups + 1) + tag."""
     lib = _load()
     s, keep = _marshal(d, use_rc)
     P, K = int(d["n_pins"]), int(d.get("n_corners", 1))
+    Ks = K * (1 + s.n_exc)   # states: corner * (groups + 1) + tag
     E = len(endpoints(d))
-    arr = {k: np.zeros((max(P, 1), K, 4), np.float64) for k in ("at", "slew", "rat", "slack")}
+    arr = {k: np.zeros((max(P, 1), Ks, 4), np.float64) for k in ("at", "slew", "rat", "slack")}
     eps = np.zeros((max(E, 1), K), np.float64)
     eph = np.zeros((max(E, 1), K), np.float64)
     summ = np.zeros((K, 8), np.float64)

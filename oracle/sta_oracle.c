@@ -28,6 +28,15 @@
  *       calculator, Sec. III "Delay models"): sink delay = 50% crossing of
  *       the step response of an order-q congruence-projected model of the
  *       RC tree; the slew law of O3 is kept;
+ *   O8  timing exceptions (Sec. III names an SDC exceptions manager; the
+ *       reading is SDC's set_false_path / set_multicycle_path -setup with
+ *       -from startpoints and -to endpoints): every path carries the tag of
+ *       its startpoint's group (0 = none); arrivals and required times are
+ *       propagated per tag (slews are tag-free); an endpoint checks tag g
+ *       with group g's action when it is in the group's endpoint list (or
+ *       the list is empty) -- false path: no check; multicycle M: setup
+ *       capture edge at M * T, hold unchanged -- and the default check
+ *       otherwise; endpoint slack = min over tags;
  *   O6  log-sum-exp smoothed objective and its hand-written FP64 adjoint
  *       with respect to cell (x, y) (not in the paper; it feeds a placer the
  *       way the paper's DREAMPlace integration consumes pin slacks, Sec. IV-C).
@@ -100,6 +109,13 @@ typedef struct {
     double gamma_ns;             /* 0: hard max/min merges; > 0: log-sum-exp */
     int32_t net_model;           /* 0 Elmore; 1 Arnoldi reduced order (O7, RC trees only) */
     int32_t arnoldi_order;       /* Krylov dimension q of O7 (>= 1) */
+    /* O8 timing exceptions: group g lists startpoint pins (PI or CK)
+     * exc_from[exc_from_ptr[g] ..), endpoint pins (D or PO)
+     * exc_to[exc_to_ptr[g] ..) (none = every endpoint), an action
+     * (0 false path, 1 multicycle setup) and a multiplier */
+    int32_t n_exc;
+    const int32_t *exc_from_ptr, *exc_from, *exc_to_ptr, *exc_to, *exc_action;
+    const float *exc_mult;
 } orc_design;
 
 /* ------------------------------------------------------------------ O1 */
@@ -471,7 +487,7 @@ static double merge(const double *x, int n, int late, double gamma)
     if (n == 0) return late ? -INFINITY : INFINITY;
     double m = x[0];
     for (int i = 1; i < n; ++i) m = late ? fmax(m, x[i]) : fmin(m, x[i]);
-    if (gamma <= 0.0) return m;
+    if (gamma <= 0.0 || isinf(m)) return m;   /* no finite candidate (another tag's arrivals) */
     double s = 0.0;
     for (int i = 0; i < n; ++i) s += exp((late ? (x[i] - m) : (m - x[i])) / gamma);
     return late ? m + gamma * log(s) : m - gamma * log(s);
@@ -628,12 +644,16 @@ int orc_topo_order(const orc_design *d, int32_t *order)
 #define IX(p, k, j) ((((size_t)(p)) * (size_t)K + (size_t)(k)) * 4 + (size_t)(j))
 #define JJ(el, rf) ((el) * 2 + (rf))   /* el 0 early, 1 late; rf 0 rise, 1 fall */
 
-static void forward_corner(const orc_design *d, const pin_info *pi, const int32_t *order, int32_t k,
-                           const double *load, const double *Dn, const double *Vn,
+/* One state: k indexes the at/slew arrays of Ks states (corner * tags +
+ * tag), kc is the corner (its table scale).  src_on[p] == 0 marks a
+ * startpoint of another tag: its arrivals are absent (-inf late, +inf
+ * early); its slew is kept (slews are tag-free).  src_on may be NULL. */
+static void forward_corner(const orc_design *d, const pin_info *pi, const int32_t *order, int32_t k, int32_t Ks,
+                           int32_t kc, const int8_t *src_on, const double *load, const double *Dn, const double *Vn,
                            double *at, double *slew)
 {
-    int32_t K = d->n_corners;
-    double sc = d->lut_scale ? d->lut_scale[k] : 1.0;
+    int32_t K = Ks;
+    double sc = d->lut_scale ? d->lut_scale[kc] : 1.0;
     for (int32_t oi = 0; oi < d->n_pins; ++oi) {
         int32_t p = order[oi];
         int r = d->pin_role[p];
@@ -641,6 +661,8 @@ static void forward_corner(const orc_design *d, const pin_info *pi, const int32_
             double a = (r == R_PI) ? d->pi_at_ns : 0.0;
             double s = (r == R_PI) ? d->pi_slew_ns : d->clk_slew_ns;
             for (int j = 0; j < 4; ++j) { at[IX(p, k, j)] = a; slew[IX(p, k, j)] = s; }
+            if (src_on && !src_on[p])
+                for (int j = 0; j < 4; ++j) at[IX(p, k, j)] = j < 2 ? INFINITY : -INFINITY;
         } else if (r == R_IN || r == R_D || r == R_PO) {
             int32_t drv = d->net_pin[d->net_pin_ptr[pi->sink_net[p]]];
             for (int j = 0; j < 4; ++j) {
@@ -676,21 +698,30 @@ static void forward_corner(const orc_design *d, const pin_info *pi, const int32_
 
 /* ----------------------------------------------- O4: required times, slack */
 
-static void backward_corner(const orc_design *d, const pin_info *pi, const int32_t *order, int32_t k,
-                            const double *load, const double *Dn, const double *slew, double *rat)
+/* One state (as forward_corner).  ep_req[2p], ep_req[2p+1] replace the late
+ * and early requirements of endpoint pin p (may be NULL: the defaults). */
+static void backward_corner(const orc_design *d, const pin_info *pi, const int32_t *order, int32_t k, int32_t Ks,
+                            int32_t kc, const double *ep_req, const double *load, const double *Dn,
+                            const double *slew, double *rat)
 {
-    int32_t K = d->n_corners;
-    double sc = d->lut_scale ? d->lut_scale[k] : 1.0;
+    int32_t K = Ks;
+    double sc = d->lut_scale ? d->lut_scale[kc] : 1.0;
     for (int32_t oi = d->n_pins - 1; oi >= 0; --oi) {
         int32_t p = order[oi];
         int r = d->pin_role[p];
         double rl[2] = {INFINITY, INFINITY}, re[2] = {-INFINITY, -INFINITY};
-        if (r == R_D) {
-            rl[0] = rl[1] = d->period_ns - d->setup_ns;
-            re[0] = re[1] = d->hold_ns;
-        } else if (r == R_PO) {
-            rl[0] = rl[1] = d->period_ns;
-            re[0] = re[1] = 0.0;
+        if (r == R_D || r == R_PO) {
+            if (r == R_D) {
+                rl[0] = rl[1] = d->period_ns - d->setup_ns;
+                re[0] = re[1] = d->hold_ns;
+            } else {
+                rl[0] = rl[1] = d->period_ns;
+                re[0] = re[1] = 0.0;
+            }
+            if (ep_req) {
+                rl[0] = rl[1] = ep_req[2 * (size_t)p];
+                re[0] = re[1] = ep_req[2 * (size_t)p + 1];
+            }
         } else {
             if (pi->drv_net[p] >= 0) {
                 int32_t n = pi->drv_net[p];
@@ -726,8 +757,10 @@ static void backward_corner(const orc_design *d, const pin_info *pi, const int32
 
 /* Full analysis.  Arrays at/slew/rat/slack are [n_pins][n_corners][4] with
  * the inner index el * 2 + rf (el 0 early / hold, 1 late / setup).
+ * With exception groups (O8) the pin arrays hold n_corners * (n_exc + 1)
+ * states, state = corner * (n_exc + 1) + tag.
  * Endpoints are the DFF D pins and POs in ascending pin id; ep_setup and
- * ep_hold are [n_endpoints][n_corners] (min over rise/fall).  summary is
+ * ep_hold are [n_endpoints][n_corners] (min over rise/fall and tags).  summary is
  * [n_corners][8]: WNS setup, TNS setup, WNS hold, TNS hold, worst setup
  * slack, worst hold slack, setup violations, hold violations. */
 int orc_sta(const orc_design *d, double *at, double *slew, double *rat, double *slack,
@@ -736,35 +769,89 @@ int orc_sta(const orc_design *d, double *at, double *slew, double *rat, double *
     pin_info pi;
     int rc = build_info(d, &pi);
     if (rc) { return rc; }
-    int32_t P = d->n_pins, K = d->n_corners;
+    const int32_t P = d->n_pins, Kc = d->n_corners;
+    const int32_t G = d->n_exc > 0 ? d->n_exc : 0, Tg = G + 1, K = Kc * Tg;   /* K: states (corner, tag) */
     int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(P ? P : 1));
     double *load = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
     double *Dn = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
     double *Vn = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
-    if (!order || !load || !Dn || !Vn) { rc = ERR_NOMEM; goto done; }
+    int8_t *tag_of = (int8_t *)calloc((size_t)(P ? P : 1), 1);
+    int8_t *src_on = (int8_t *)calloc((size_t)(P ? P : 1), 1);
+    uint8_t *in_to = (uint8_t *)calloc((size_t)(P ? P : 1), 1);
+    double *ep_req = (double *)malloc(sizeof(double) * 2 * (size_t)(P ? P : 1));
+    if (!order || !load || !Dn || !Vn || !tag_of || !src_on || !in_to || !ep_req) { rc = ERR_NOMEM; goto done; }
     rc = topo_order(d, &pi, order);
     if (rc) goto done;
-    for (int32_t k = 0; k < K; ++k) {
-        rc = orc_net_delays(d, k, load, Dn, Vn);
+    /* O8: a startpoint's tag is its first group (0 = none) */
+    for (int32_t g = 0; g < G; ++g) {
+        for (int32_t i = d->exc_from_ptr[g]; i < d->exc_from_ptr[g + 1]; ++i) {
+            const int32_t p = d->exc_from[i];
+            if (p < 0 || p >= P || (d->pin_role[p] != R_PI && d->pin_role[p] != R_CK)) { rc = ERR_INVAL; goto done; }
+            if (!tag_of[p]) tag_of[p] = (int8_t)(g + 1);
+        }
+        for (int32_t i = d->exc_to_ptr[g]; i < d->exc_to_ptr[g + 1]; ++i) {
+            const int32_t p = d->exc_to[i];
+            if (p < 0 || p >= P || (d->pin_role[p] != R_D && d->pin_role[p] != R_PO)) { rc = ERR_INVAL; goto done; }
+        }
+        if (d->exc_action[g] != 0 && !(d->exc_action[g] == 1 && d->exc_mult[g] >= 1.0f)) { rc = ERR_INVAL; goto done; }
+    }
+    for (int32_t kc = 0; kc < Kc; ++kc) {
+        rc = orc_net_delays(d, kc, load, Dn, Vn);
         if (rc) goto done;
-        forward_corner(d, &pi, order, k, load, Dn, Vn, at, slew);
-        backward_corner(d, &pi, order, k, load, Dn, slew, rat);
-        for (int32_t p = 0; p < P; ++p)
-            for (int rf = 0; rf < 2; ++rf) {
-                slack[IX(p, k, JJ(0, rf))] = at[IX(p, k, JJ(0, rf))] - rat[IX(p, k, JJ(0, rf))];
-                slack[IX(p, k, JJ(1, rf))] = rat[IX(p, k, JJ(1, rf))] - at[IX(p, k, JJ(1, rf))];
+        for (int32_t g = 0; g < Tg; ++g) {
+            const int32_t k = kc * Tg + g;
+            if (G > 0) {
+                for (int32_t p = 0; p < P; ++p) src_on[p] = tag_of[p] == g;
+                /* requirements of tag g at every endpoint */
+                for (int32_t p = 0; p < P; ++p) in_to[p] = 0;
+                const int applies_all = g > 0 && d->exc_to_ptr[g] == d->exc_to_ptr[g - 1];
+                if (g > 0)
+                    for (int32_t i = d->exc_to_ptr[g - 1]; i < d->exc_to_ptr[g]; ++i) in_to[d->exc_to[i]] = 1;
+                for (int32_t p = 0; p < P; ++p) {
+                    const int r = d->pin_role[p];
+                    if (r != R_D && r != R_PO) continue;
+                    const double T = d->period_ns;
+                    double late = r == R_D ? T - d->setup_ns : T, early = r == R_D ? d->hold_ns : 0.0;
+                    if (g > 0 && (applies_all || in_to[p])) {
+                        if (d->exc_action[g - 1] == 0) {
+                            late = INFINITY;   /* false path: no check */
+                            early = -INFINITY;
+                        } else {
+                            const double M = d->exc_mult[g - 1];   /* multicycle: capture at M * T */
+                            late = r == R_D ? M * T - d->setup_ns : M * T;
+                        }
+                    }
+                    ep_req[2 * (size_t)p] = late;
+                    ep_req[2 * (size_t)p + 1] = early;
+                }
             }
-        double *sm = summary + (size_t)k * 8;
+            forward_corner(d, &pi, order, k, K, kc, G ? src_on : NULL, load, Dn, Vn, at, slew);
+            backward_corner(d, &pi, order, k, K, kc, G ? ep_req : NULL, load, Dn, slew, rat);
+            for (int32_t p = 0; p < P; ++p)
+                for (int rf = 0; rf < 2; ++rf) {
+                    slack[IX(p, k, JJ(0, rf))] = at[IX(p, k, JJ(0, rf))] - rat[IX(p, k, JJ(0, rf))];
+                    slack[IX(p, k, JJ(1, rf))] = rat[IX(p, k, JJ(1, rf))] - at[IX(p, k, JJ(1, rf))];
+                }
+        }
+        /* endpoints of corner kc: min over rise/fall and over tags */
+        double *sm = summary + (size_t)kc * 8;
         double wns_s = 0, tns_s = 0, wns_h = 0, tns_h = 0, worst_s = INFINITY, worst_h = INFINITY;
         double nv_s = 0, nv_h = 0;
         int32_t e = 0;
         for (int32_t p = 0; p < P; ++p) {
             int r = d->pin_role[p];
             if (r != R_D && r != R_PO) continue;
-            double ss = fmin(slack[IX(p, k, JJ(1, 0))], slack[IX(p, k, JJ(1, 1))]);
-            double hs = fmin(slack[IX(p, k, JJ(0, 0))], slack[IX(p, k, JJ(0, 1))]);
-            ep_setup[(size_t)e * K + k] = ss;
-            ep_hold[(size_t)e * K + k] = hs;
+            double ssm = INFINITY, hsm = INFINITY;
+            for (int32_t g = 0; g < Tg; ++g) {
+                const int32_t k = kc * Tg + g;
+                double ss = fmin(slack[IX(p, k, JJ(1, 0))], slack[IX(p, k, JJ(1, 1))]);
+                double hs = fmin(slack[IX(p, k, JJ(0, 0))], slack[IX(p, k, JJ(0, 1))]);
+                ssm = fmin(ssm, ss);
+                hsm = fmin(hsm, hs);
+            }
+            const double ss = ssm, hs = hsm;
+            ep_setup[(size_t)e * Kc + kc] = ss;
+            ep_hold[(size_t)e * Kc + kc] = hs;
             ++e;
             worst_s = fmin(worst_s, ss); worst_h = fmin(worst_h, hs);
             if (ss < 0) { tns_s += ss; nv_s += 1; wns_s = fmin(wns_s, ss); }
@@ -774,7 +861,7 @@ int orc_sta(const orc_design *d, double *at, double *slew, double *rat, double *
         sm[4] = worst_s; sm[5] = worst_h; sm[6] = nv_s; sm[7] = nv_h;
     }
 done:
-    free(order); free(load); free(Dn); free(Vn);
+    free(order); free(load); free(Dn); free(Vn); free(tag_of); free(src_on); free(in_to); free(ep_req);
     free_info(&pi);
     return rc;
 }
@@ -831,7 +918,7 @@ int orc_objective_grad(const orc_design *d, double w_tns, double w_wns, double *
         double f = d->rc_scale ? d->rc_scale[k] : 1.0;
         rc = orc_net_delays(d, k, load, Dn, Vn);
         if (rc) goto done;
-        forward_corner(d, &pi, order, k, load, Dn, Vn, at, sl);
+        forward_corner(d, &pi, order, k, K, k, NULL, load, Dn, Vn, at, sl);
         /* endpoint slacks and the objective */
         double mx = -INFINITY;
         for (int32_t p = 0; p < P; ++p) {

@@ -214,3 +214,51 @@ def enumerate_suffixes(d, corner=0):
         return out
 
     return {p: suf(p) for p in range(d["n_pins"])}
+
+
+def enumerate_paths_from(d, corner=0):
+    """Every path's (arrival, edge, startpoint pin) at every pin, for
+    slew-independent cell delays (read at the driven net's load)."""
+    net = Net(d, corner)
+    sc = float(np.asarray(d["lut_scale"])[corner])
+    role = np.asarray(d["pin_role"])
+    ctype = np.asarray(d["cell_type"])
+    cpp = np.asarray(d["cell_pin_ptr"])
+    cp = np.asarray(d["cell_pin"])
+    sense = np.asarray(d["arc_sense"]).reshape(-1, 3)
+    nin = np.asarray(d["type_nin"])
+    i1 = np.asarray(d["lut_idx1"]).reshape(-1, 3, 4, 7)
+    i2 = np.asarray(d["lut_idx2"]).reshape(-1, 3, 4, 7)
+    vv = np.asarray(d["lut_val"]).reshape(-1, 3, 4, 49)
+    memo = {}
+
+    def paths(p):
+        if p in memo:
+            return memo[p]
+        r = role[p]
+        if r == PI:
+            out = [(float(d["pi_at_ns"]), rf, p) for rf in (0, 1)]
+        elif r == CK:
+            out = [(0.0, rf, p) for rf in (0, 1)]
+        elif r in (IN, D, PO):
+            out = [(a + net.Dns[p], rf, s) for a, rf, s in paths(net.driver[p])]
+        else:
+            c = net.cell_of[p]
+            t = ctype[c]
+            l = net.load.get(p, 0.0)
+            out = []
+            for slot in range(nin[t]):
+                se = sense[t, slot]
+                if se == NONE:
+                    continue
+                for a, rf, s in paths(cp[cpp[c] + slot]):
+                    if r == Q and rf != 0:
+                        continue
+                    for rfo in (0, 1):
+                        if rf in rf_in_of(se, rfo):
+                            dl = sc * bilinear(i1[t, slot, rfo], i2[t, slot, rfo], vv[t, slot, rfo], 0.0, l)
+                            out.append((a + dl, rfo, s))
+        memo[p] = out
+        return out
+
+    return {p: paths(p) for p in range(d["n_pins"])}

@@ -38,7 +38,7 @@ MUTANTS = [
     ("fwd_slew_merge_late", "slew[IX(p, k, JJ(el, rfo))] = merge(cs, n, el, d->gamma_ns);", "slew[IX(p, k, JJ(el, rfo))] = merge(cs, n, 1, d->gamma_ns);", 0),
     ("merge_min_max_swap", "m = late ? fmax(m, x[i]) : fmin(m, x[i]);", "m = late ? fmin(m, x[i]) : fmax(m, x[i]);", 0),
     ("lse_early_sign", "return late ? m + gamma * log(s) : m - gamma * log(s);", "return m + gamma * log(s);", 0),
-    ("fwd_lut_corner", "double sc = d->lut_scale ? d->lut_scale[k] : 1.0;", "double sc = d->lut_scale ? d->lut_scale[0] : 1.0;", 0),
+    ("fwd_lut_corner", "double sc = d->lut_scale ? d->lut_scale[kc] : 1.0;", "double sc = d->lut_scale ? d->lut_scale[0] : 1.0;", 0),
     ("pi_arrival_zero", "double a = (r == R_PI) ? d->pi_at_ns : 0.0;", "double a = 0.0;", 0),
     ("clock_slew_is_pi_slew", "d->pi_slew_ns : d->clk_slew_ns", "d->pi_slew_ns : d->pi_slew_ns", 0),
     # O4 required times, slack, WNS/TNS
@@ -48,7 +48,7 @@ MUTANTS = [
     ("rat_early_net_min", "re[rf] = fmax(re[rf], rat[IX(s, k, JJ(0, rf))] - Dn[s]);", "re[rf] = fmin(re[rf], rat[IX(s, k, JJ(0, rf))] - Dn[s]);", 0),
     ("rat_cell_early_slew", "slew[IX(p, k, JJ(1, ri))], load[z], 0, 0);", "slew[IX(p, k, JJ(0, ri))], load[z], 0, 0);", 0),
     ("rat_cell_rf_index", "rat[IX(z, k, JJ(1, rfo))] - dl);", "rat[IX(z, k, JJ(1, ri))] - dl);", 0),
-    ("bwd_lut_corner", "double sc = d->lut_scale ? d->lut_scale[k] : 1.0;", "double sc = d->lut_scale ? d->lut_scale[0] : 1.0;", 1),
+    ("bwd_lut_corner", "double sc = d->lut_scale ? d->lut_scale[kc] : 1.0;", "double sc = d->lut_scale ? d->lut_scale[0] : 1.0;", 1),
     ("hold_slack_sign", "slack[IX(p, k, JJ(0, rf))] = at[IX(p, k, JJ(0, rf))] - rat[IX(p, k, JJ(0, rf))];",
      "slack[IX(p, k, JJ(0, rf))] = rat[IX(p, k, JJ(0, rf))] - at[IX(p, k, JJ(0, rf))];", 0),
     ("tns_sign", "if (ss < 0) { tns_s += ss;", "if (ss < 0) { tns_s -= ss;", 0),
@@ -70,6 +70,13 @@ MUTANTS = [
     ("arn_modal_inverse", "yinf[k] = s / lam[k];", "yinf[k] = s * lam[k];", 0),
     ("arn_half_threshold", "if (v >= 0.5 * vinf) hi = mid;", "if (v >= 0.4 * vinf) hi = mid;", 0),
     ("arn_model_switch", "if (d->net_model == 1 && d->rc_ptr) {", "if (d->net_model == 2 && d->rc_ptr) {", 0),
+    # O8 timing exceptions
+    ("exc_seed_not_masked", "if (src_on && !src_on[p])", "if (src_on && src_on[p] > 1)", 0),
+    ("exc_first_group_wins", "if (!tag_of[p]) tag_of[p] = (int8_t)(g + 1);", "tag_of[p] = (int8_t)(g + 1);", 0),
+    ("exc_false_still_checked", "late = INFINITY;   /* false path: no check */", "late = late;", 0),
+    ("exc_multicycle_edge", "late = r == R_D ? M * T - d->setup_ns : M * T;", "late = r == R_D ? M * T : M * T;", 0),
+    ("exc_to_list_ignored", "if (g > 0 && (applies_all || in_to[p])) {", "if (g > 0) {", 0),
+    ("exc_tag_max_not_min", "ssm = fmin(ssm, ss);", "ssm = fmax(ssm, ss);", 0),
     # O6 smoothed objective and its adjoint
     ("tns_softplus_sign", "tns += -g * softplus(-seed[p] / g);", "tns += -g * softplus(seed[p] / g);", 0),
     ("seed_sigmoid_sign", "w_tns * sigmoid(-s / g)", "w_tns * sigmoid(s / g)", 0),

@@ -701,3 +701,84 @@ def test_paths_order_threshold_and_count():
         want = sorted((e for e in range(len(es)) if es[e] < thr), key=lambda e: (es[e], e))[:k]
         assert [p["endpoint"] for p in paths] == [int(res["endpoints"][e]) for e in want]
         assert all(p["slack"] < thr for p in paths)
+
+
+# ------------------------------------------------------- O8 timing exceptions
+
+def _groups(d, rng, n_groups):
+    """Random exception groups: startpoints (PIs and CKs), endpoint lists
+    (sometimes empty = every endpoint), false path or multicycle."""
+    role = np.asarray(d["pin_role"])
+    starts = np.nonzero((role == synth.PI) | (role == synth.CK))[0]
+    ends = np.nonzero((role == synth.D) | (role == synth.PO))[0]
+    fp, fr, tp, to, act, mult = [0], [], [0], [], [], []
+    for g in range(n_groups):
+        fr += list(rng.choice(starts, size=max(1, len(starts) // 3), replace=False))
+        fp.append(len(fr))
+        if rng.random() < 0.7:
+            to += list(rng.choice(ends, size=max(1, len(ends) // 2), replace=False))
+        tp.append(len(to))
+        act.append(int(rng.random() < 0.5))
+        mult.append(float(rng.integers(2, 4)))
+    return dict(exc_from_ptr=np.array(fp, np.int32), exc_from=np.array(fr, np.int32),
+                exc_to_ptr=np.array(tp, np.int32), exc_to=np.array(to, np.int32),
+                exc_action=np.array(act, np.int32), exc_mult=np.array(mult, np.float32))
+
+
+@pytest.mark.parametrize("seed", range(5))
+def test_exceptions_brute_force_fixed_delay(seed):
+    """Every path tagged by its startpoint's first group: an endpoint's setup
+    slack is the minimum over the paths ending there of (requirement -
+    arrival) and its hold slack the minimum of (arrival - requirement), with
+    the tag's requirement -- the group's action when the endpoint is in its
+    list (or the list is empty): false path removes the check, multicycle M
+    moves the setup capture edge to M * T -- and the default otherwise."""
+    rng = np.random.default_rng(seed)
+    d = _fixed_design(seed, n_cells=14, depth=5)
+    d["period_ns"] = 0.35
+    d.update(_groups(d, rng, 3))
+    res = oracle.sta(d)
+    role = np.asarray(d["pin_role"])
+    first = {}
+    for g in range(3):
+        for p in d["exc_from"][d["exc_from_ptr"][g]:d["exc_from_ptr"][g + 1]]:
+            first.setdefault(int(p), g)
+    T = d["period_ns"]
+    allp = _indep.enumerate_paths_from(d)
+    for e, p in enumerate(res["endpoints"]):
+        setup = hold = np.inf
+        for a, rf, s in allp[p]:
+            late = T - d["setup_ns"] if role[p] == synth.D else T
+            early = d["hold_ns"] if role[p] == synth.D else 0.0
+            g = first.get(s)
+            if g is not None:
+                lst = d["exc_to"][d["exc_to_ptr"][g]:d["exc_to_ptr"][g + 1]]
+                if len(lst) == 0 or p in lst:
+                    if d["exc_action"][g] == 0:
+                        late, early = np.inf, -np.inf
+                    else:
+                        M = float(d["exc_mult"][g])
+                        late = M * T - d["setup_ns"] if role[p] == synth.D else M * T
+            setup = min(setup, late - a)
+            hold = min(hold, a - early)
+        assert res["ep_setup"][e, 0] == pytest.approx(setup, abs=1e-12), (e, p)
+        assert res["ep_hold"][e, 0] == pytest.approx(hold, abs=1e-12), (e, p)
+    assert res["at"].shape[1] == 4                     # one corner x (3 groups + 1) tags
+
+
+def test_exceptions_all_false_and_all_multicycle():
+    """Every startpoint in one false-path group: no check anywhere, WNS = TNS
+    = 0.  Every startpoint in one multicycle-M group: every setup slack moves
+    by exactly (M - 1) * T, hold slacks do not move."""
+    d = synth.make_design(600, 10, seed=5, period_ns=0.7)
+    role = np.asarray(d["pin_role"])
+    starts = np.nonzero((role == synth.PI) | (role == synth.CK))[0].astype(np.int32)
+    base = oracle.sta(d)
+    grp = dict(exc_from_ptr=np.array([0, len(starts)], np.int32), exc_from=starts,
+               exc_to_ptr=np.array([0, 0], np.int32), exc_to=np.zeros(0, np.int32))
+    r = oracle.sta(dict(d, exc_action=np.array([0], np.int32), exc_mult=np.array([1], np.float32), **grp))
+    assert np.all(np.isinf(r["ep_setup"])) and np.all(np.isinf(r["ep_hold"]))
+    assert r["wns_setup"][0] == 0 and r["tns_setup"][0] == 0 and r["tns_hold"][0] == 0
+    r = oracle.sta(dict(d, exc_action=np.array([1], np.int32), exc_mult=np.array([3], np.float32), **grp))
+    np.testing.assert_allclose(r["ep_setup"], base["ep_setup"] + 2 * d["period_ns"], rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(r["ep_hold"], base["ep_hold"])
