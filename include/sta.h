@@ -161,6 +161,24 @@ typedef struct {
     float gamma_ns;
     int32_t net_model;      /* STA_NET_ELMORE (0) or STA_NET_ARNOLDI (1) */
     int32_t arnoldi_order;  /* q of STA_NET_ARNOLDI: 1..3, 0 = 3 */
+    /* Timing exceptions (Sec. III: an SDC exceptions manager; this is the
+     * reading of set_false_path / set_multicycle_path -setup with -from
+     * startpoints and -to endpoints).  Group g (0 <= g < n_exc <= 7):
+     * startpoint pins exc_from[exc_from_ptr[g] .. exc_from_ptr[g+1]) (PI or
+     * CK), endpoint pins exc_to[exc_to_ptr[g] .. exc_to_ptr[g+1]) (D or PO;
+     * an empty list means every endpoint), exc_action[g] (0 false path, 1
+     * multicycle) and exc_mult[g] (the setup multiplier M >= 1).  Every path
+     * carries the tag of its startpoint's first group (0 = none); arrivals
+     * and required times are propagated per (corner, tag) state, slews are
+     * tag-free; endpoint e checks tag g with g's action when it is in g's
+     * list -- false path: no check; multicycle: setup capture edge at M * T,
+     * hold unchanged -- and the default check otherwise.  Endpoint slacks,
+     * WNS and TNS take the min over tags; per-pin arrays (sta_get_pin_state)
+     * hold n_corners * (n_exc + 1) states, state = corner * (n_exc + 1) +
+     * tag.  Not with gamma_ns > 0 or in a batch.  n_exc = 0: none. */
+    int32_t n_exc;
+    const int32_t *exc_from_ptr, *exc_from, *exc_to_ptr, *exc_to, *exc_action;
+    const float *exc_mult;
 } sta_design_desc;
 
 /* net delay calculators (sta_design_desc.net_model) */
@@ -178,6 +196,8 @@ typedef struct {
     int32_t launches_per_update;                 /* kernels one sta_update_timing launches */
     int32_t launches_per_backward;               /* kernels one sta_backward launches (differentiable
                                                     contexts, current reverse-sweep schedule; else 0) */
+    int32_t n_tags;                              /* exception tags (n_exc + 1); per-pin states =
+                                                    n_corners * n_tags */
 } sta_plan_info;
 
 /* Per-corner summary returned by sta_report_slack. */

@@ -262,9 +262,15 @@ def report_paths(d: dict, k: int, slack_lt: float = float("inf"), corner: int = 
     (ties: lower input slot, then rise before fall); a flip-flop Q steps to
     its CK (rising edge); the trace stops at a PI or CK.  Returns a list of
     dicts: endpoint pin, slack, and the pins, edges and late arrivals from the
-    startpoint to the endpoint.  FP64, from this package's own analysis."""
+    startpoint to the endpoint.  FP64, from this package's own analysis.
+
+    With timing exceptions the endpoint's slack is its minimum over the
+    exception tags, and the path is traced in the (tag, edge) state with the
+    smallest late slack (ties: lower tag, then rise) -- the path of the
+    startpoint group that sets the endpoint's slack."""
     res = res if res is not None else sta(d)
     K = int(d.get("n_corners", 1))
+    Tg = 1 + (len(d["exc_action"]) if d.get("exc_action") is not None else 0)
     sc = float(np.asarray(d["lut_scale"] if d.get("lut_scale") is not None else np.ones(K))[corner])
     load, _, _ = net_delays(d, corner)
     role = np.asarray(d["pin_role"])
@@ -285,14 +291,18 @@ def report_paths(d: dict, k: int, slack_lt: float = float("inf"), corner: int = 
     driver = -np.ones(d["n_pins"], int)
     for n in range(d["n_nets"]):
         driver[npn[npp[n] + 1:npp[n + 1]]] = npn[npp[n]]
-    at, slew, slack = res["at"][:, corner], res["slew"][:, corner], res["slack"][:, corner]
     eps, es = res["endpoints"], res["ep_setup"][:, corner]
     order = sorted((e for e in range(len(eps)) if es[e] < slack_lt), key=lambda e: (es[e], e))[:k]
     arcs_on = {0: lambda i, o: i == o, 1: lambda i, o: i != o, 2: lambda i, o: True}
     out = []
     for e in order:
         p = int(eps[e])
-        rf = 0 if slack[p, 2] <= slack[p, 3] else 1
+        best_s, st, rf = np.inf, corner * Tg, 0
+        for g in range(Tg):
+            sl = res["slack"][p, corner * Tg + g]
+            if min(sl[2], sl[3]) < best_s:
+                best_s, st, rf = min(sl[2], sl[3]), corner * Tg + g, 0 if sl[2] <= sl[3] else 1
+        at, slew = res["at"][:, st], res["slew"][:, st]
         pins, rfs = [], []
         while True:
             if len(pins) > d["n_pins"]:

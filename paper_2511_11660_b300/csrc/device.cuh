@@ -24,7 +24,10 @@ constexpr unsigned kErrResize = 4u;
 
 struct DevCtx {
     int32_t P, I, S, E, K, T, C, n_designs;
-    int32_t KL;                                 // quads per item: corners handled side by side (1, 2, 4 or 8)
+    int32_t KL;                                 // quads per item: states handled side by side (1, 2, 4 or 8)
+    int32_t Kc, Tg;                             // corners and exception tags: K = Kc * Tg states, k = corner * Tg + tag
+    const int32_t *item_tag;                    // [I] tag of a startpoint item (Tg > 1)
+    const float *ep_mult;                       // [E][Tg] setup multiplier per endpoint and tag, 0 = no check (Tg > 1)
     int64_t NN;                                 // RC nodes
     int32_t F;                                  // net sinks (fan-out entries)
     int32_t net_model, arnoldi_q;               // STA_NET_ELMORE / STA_NET_ARNOLDI and its order
@@ -123,6 +126,8 @@ struct MaxMerge {
     {
         if (!SMOOTH) {
             m = fmaxf(m, y);
+        } else if (!(y > -INFINITY)) {
+            // an absent candidate (another exception tag's arrival): no term
         } else if (y > m) {
             s = s * expf((m - y) * inv_g) + 1.f;
             m = y;

@@ -222,6 +222,7 @@ __device__ __forceinline__ bool group_all(const DevCtx &c, bool ok) { return __a
 
 struct FwdItem {
     int t, pin0, nin, kind;
+    int tag;                    // exception tag of a startpoint item (PI, flip-flop)
     int sense[3], drv[3];
     float Dn0[3], V0[3], ld0;   // net values of the lane's first corner, loaded ahead
 };
@@ -241,6 +242,7 @@ __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, co
     f.pin0 = chk(c, c.item_pin0[g], c.P);
     f.kind = f.t >= 0 ? tkind[f.t] : -1;
     f.nin = f.kind == 0 ? tnin[f.t] : 0;
+    f.tag = (c.Tg > 1 && f.kind != 0) ? c.item_tag[g] : 0;
     const int K = c.K, kq = corner_lane(c);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -287,11 +289,15 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
     const int el = q >> 1, rfo = q & 1;
     const int kq = corner_lane(c), KL = c.KL;
     const bool pub = WAIT && g != c.hold_item;
+    // a startpoint's arrival exists only in its own exception tag's states
+    // (absent elsewhere: -inf late, +inf early); slews are tag-free
+    const float absent = el ? -INFINITY : INFINITY;
     if (t < 0) {   // primary input
         for (int k = kq; k < K; k += KL) {
-            st_comp(c.at + (size_t)pin0 * K + k, q, c.pi_at);
+            const float a = (c.Tg == 1 || k % c.Tg == f.tag) ? c.pi_at : absent;
+            st_comp(c.at + (size_t)pin0 * K + k, q, a);
             st_comp(c.slew + (size_t)pin0 * K + k, q, c.pi_slew);
-            if (pub) publish_fwd(c, par, pin0, k, q, c.pi_at, c.pi_slew);
+            if (pub) publish_fwd(c, par, pin0, k, q, a, c.pi_slew);
         }
         return;
     }
@@ -302,10 +308,11 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
         for (int k = kq; k < K; k += KL) {
             const float sc = __ldg(c.lut_scale + k);
             const float ld = k != kq ? c.load[(size_t)qp * K + k] : f.ld0;
-            st_comp(c.at + (size_t)ck * K + k, q, 0.f);
+            const float ck_at = (c.Tg == 1 || k % c.Tg == f.tag) ? 0.f : absent;
+            st_comp(c.at + (size_t)ck * K + k, q, ck_at);
             st_comp(c.slew + (size_t)ck * K + k, q, cs);
             const Seg as = seg_slew<UNIFORM>(c, lut, tb, cs), bl = seg_load<UNIFORM>(c, lut, tb, ld);
-            const float a = sc * lookup<UNIFORM>(lut, tb + rfo * kLutStride, as, bl, cs, ld);
+            const float a = ck_at + sc * lookup<UNIFORM>(lut, tb + rfo * kLutStride, as, bl, cs, ld);
             const float sl = sc * lookup<UNIFORM>(lut, tb + (2 + rfo) * kLutStride, as, bl, cs, ld);
             st_comp(c.at + (size_t)qp * K + k, q, a);
             st_comp(c.slew + (size_t)qp * K + k, q, sl);
@@ -424,11 +431,16 @@ __device__ __forceinline__ void ep_run(const DevCtx &c, const EpItem &x, float a
                                        int par)
 {
     const int K = c.K, p = x.p, d = x.d;
-    const float req = q >= 2 ? (x.isD ? c.period - c.setup : c.period) : (x.isD ? c.hold : 0.f);
     const unsigned m = quad_mask();
     const int base = threadIdx.x & 28;   // first lane of the quad
     const int kq = corner_lane(c);
     for (int k = kq; k < K; k += c.KL) {
+        // requirement of state k: the exception tag's multiplier M (1 = the
+        // default check, 0 = no check) -- setup capture edge at M * T
+        const float M = c.Tg > 1 ? c.ep_mult[(size_t)e * c.Tg + k % c.Tg] : 1.f;
+        const float req = M == 0.f ? (q >= 2 ? INFINITY : -INFINITY)
+                                   : (q >= 2 ? (x.isD ? M * c.period - c.setup : M * c.period)
+                                             : (x.isD ? c.hold : 0.f));
         float ad, sd;
         if (!WAIT) {
             ad = ld_state(c.at + (size_t)d * K + k, q);

@@ -468,11 +468,17 @@ __device__ __forceinline__ void block_fold6(double v[6], double (*sh)[NT])
 __global__ void __launch_bounds__(kRedThreads) k_reduce_chunks(const DevCtx c)
 {
     __shared__ double sh[6][kRedThreads];
-    const int b = blockIdx.x, k = blockIdx.y, K = c.K;
+    const int b = blockIdx.x, k = blockIdx.y, K = c.Kc;
     const int e0 = c.red_chunk_ptr[b], e1 = c.red_chunk_ptr[b + 1];
     double v[6] = {0, 0, INFINITY, INFINITY, 0, 0};
     for (int e = e0 + threadIdx.x; e < e1; e += kRedThreads) {
-        const double ss = c.ep_setup[(size_t)e * K + k], hs = c.ep_hold[(size_t)e * K + k];
+        // the endpoint's slack at corner k: min over its exception tags
+        float fs = INFINITY, fh = INFINITY;
+        for (int g = 0; g < c.Tg; ++g) {
+            fs = fminf(fs, c.ep_setup[(size_t)e * c.K + k * c.Tg + g]);
+            fh = fminf(fh, c.ep_hold[(size_t)e * c.K + k * c.Tg + g]);
+        }
+        const double ss = fs, hs = fh;
         v[2] = fmin(v[2], ss);
         v[3] = fmin(v[3], hs);
         if (ss < 0) { v[0] += ss; v[4] += 1; }
@@ -485,7 +491,7 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_chunks(const DevCtx c)
 __global__ void __launch_bounds__(kRedThreads) k_reduce_final(const DevCtx c)
 {
     __shared__ double sh[6][kRedThreads];
-    const int d = blockIdx.x / c.K, k = blockIdx.x % c.K, K = c.K;
+    const int d = blockIdx.x / c.Kc, k = blockIdx.x % c.Kc, K = c.Kc;
     const int b0 = c.red_design_chunk[d], b1 = c.red_design_chunk[d + 1];
     double v[6] = {0, 0, INFINITY, INFINITY, 0, 0};
     for (int b = b0 + threadIdx.x; b < b1; b += kRedThreads) {
@@ -513,8 +519,8 @@ __global__ void __launch_bounds__(kRedThreads) k_reduce_final(const DevCtx c)
 
 void launch_reduce(const DevCtx &c, const HostSched &h, cudaStream_t st)
 {
-    if (h.n_red_chunks > 0) k_reduce_chunks<<<dim3(h.n_red_chunks, c.K), kRedThreads, 0, st>>>(c);
-    k_reduce_final<<<c.n_designs * c.K, kRedThreads, 0, st>>>(c);
+    if (h.n_red_chunks > 0) k_reduce_chunks<<<dim3(h.n_red_chunks, c.Kc), kRedThreads, 0, st>>>(c);
+    k_reduce_final<<<c.n_designs * c.Kc, kRedThreads, 0, st>>>(c);
 }
 
 // ------------------------------------------------------------- gathers
@@ -638,6 +644,28 @@ void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cud
 void launch_gather_pins(const float4 *arr, const int32_t *gpu_of, float4 *out, int P, int K, cudaStream_t st)
 {
     if ((long long)P * K > 0) k_gather_pins<<<nblk((long long)P * K, 256), 256, 0, st>>>(arr, gpu_of, out, P, K);
+}
+
+__global__ void k_collapse_tags(const DevCtx c, float *ep, uint8_t *viol)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t EK = (size_t)c.E * c.Kc;
+    if (i >= EK) return;
+    const size_t e = i / c.Kc, k = i % c.Kc;
+    float s = INFINITY, h = INFINITY;
+    for (int g = 0; g < c.Tg; ++g) {
+        s = fminf(s, c.ep_setup[e * c.K + k * c.Tg + g]);
+        h = fminf(h, c.ep_hold[e * c.K + k * c.Tg + g]);
+    }
+    ep[i] = s;
+    ep[EK + i] = h;
+    viol[i] = s < 0.f;
+    viol[EK + i] = h < 0.f;
+}
+
+void launch_collapse_tags(const DevCtx &c, float *ep, uint8_t *viol, cudaStream_t st)
+{
+    if ((long long)c.E * c.Kc > 0) k_collapse_tags<<<nblk((long long)c.E * c.Kc, 256), 256, 0, st>>>(c, ep, viol);
 }
 
 void launch_gather_f32(const float *src, const int32_t *idx, float *dst, int n, cudaStream_t st)

@@ -89,6 +89,9 @@ void launch_resize(const DevCtx &c, const int32_t *item_of_cell, const int32_t *
                    int n, int32_t *item_type, cudaStream_t st);
 
 void launch_gather_pins(const float4 *arr, const int32_t *gpu_of, float4 *out, int P, int K, cudaStream_t st);
+// Endpoint slacks and violation flags per corner, min over the exception
+// tags: ep[0 .. E*Kc) setup, ep[E*Kc ..) hold; viol likewise.
+void launch_collapse_tags(const DevCtx &c, float *ep, uint8_t *viol, cudaStream_t st);
 void launch_gather_f32(const float *src, const int32_t *idx, float *dst, int n, cudaStream_t st);
 
 }  // namespace sta

@@ -34,7 +34,8 @@ __device__ __forceinline__ unsigned ordered_bits(float f)
 
 __device__ __forceinline__ bool key_of(const DevCtx &c, const PathJob &j, int i, unsigned long long &key)
 {
-    const float s = c.ep_setup[(size_t)(j.e0 + i) * c.K + j.corner];
+    float s = INFINITY;   // the endpoint's slack at the corner: min over exception tags
+    for (int g = 0; g < c.Tg; ++g) s = fminf(s, c.ep_setup[(size_t)(j.e0 + i) * c.K + j.corner * c.Tg + g]);
     if (!(s < j.slack_lt)) return false;   // also drops NaN
     key = ((unsigned long long)ordered_bits(s) << 32) | (unsigned)i;
     return true;
@@ -119,9 +120,9 @@ __global__ void __launch_bounds__(1024) k_sel_sort(const PathJob j)
 
 // One step of the trace back from pin p at edge rf; false at a startpoint.
 template <bool UNIFORM>
-__device__ bool trace_step(const DevCtx &c, const PathJob &j, int &p, int &rf)
+__device__ bool trace_step(const DevCtx &c, const PathJob &j, int k, int &p, int &rf)
 {
-    const int K = c.K, k = j.corner;
+    const int K = c.K;
     const int drv = c.drv_of[p];
     if (drv >= 0) {   // net sink
         p = drv;
@@ -167,12 +168,30 @@ __device__ bool trace_step(const DevCtx &c, const PathJob &j, int &p, int &rf)
     return true;
 }
 
-__device__ __forceinline__ void path_start(const DevCtx &c, const PathJob &j, int i, int &e, int &p, int &rf)
+// the endpoint, and the (exception tag, edge) state with its smallest late
+// slack (ties: lower tag, then rise): the path is traced in that state
+__device__ __forceinline__ void path_start(const DevCtx &c, const PathJob &j, int i, int &e, int &p, int &k, int &rf)
 {
     e = j.e0 + (int)(j.keys[i] & 0xffffffffu);
     p = c.ep_pin[e];
-    const size_t o = (size_t)p * c.K + j.corner;
-    rf = ld_state(c.slack + o, 2) <= ld_state(c.slack + o, 3) ? 0 : 1;
+    float best = INFINITY;
+    k = j.corner * c.Tg;
+    rf = 0;
+    for (int g = 0; g < c.Tg; ++g) {
+        const int kk = j.corner * c.Tg + g;
+        const size_t o = (size_t)p * c.K + kk;
+        const float s0 = ld_state(c.slack + o, 2), s1 = ld_state(c.slack + o, 3);
+        const float s = fminf(s0, s1);
+        if (s < best) {
+            best = s;
+            k = kk;
+            rf = s0 <= s1 ? 0 : 1;
+        }
+    }
+    if (!(best < INFINITY)) {   // no checked state (cannot be selected): tag 0
+        const size_t o = (size_t)p * c.K + k;
+        rf = ld_state(c.slack + o, 2) <= ld_state(c.slack + o, 3) ? 0 : 1;
+    }
 }
 
 // pass 1: path lengths (pins, endpoint and startpoint included)
@@ -181,10 +200,10 @@ __global__ void k_path_len(const DevCtx c, const PathJob j)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int)*j.count) return;
-    int e, p, rf;
-    path_start(c, j, i, e, p, rf);
+    int e, p, k, rf;
+    path_start(c, j, i, e, p, k, rf);
     int len = 1;
-    while (len < j.max_len && trace_step<UNIFORM>(c, j, p, rf)) ++len;
+    while (len < j.max_len && trace_step<UNIFORM>(c, j, k, p, rf)) ++len;
     j.ptr[i + 1] = len;
 }
 
@@ -211,19 +230,21 @@ __global__ void k_path_write(const DevCtx c, const PathJob j)
 {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= (int)*j.count) return;
-    int e, p, rf;
-    path_start(c, j, i, e, p, rf);
+    int e, p, k, rf;
+    path_start(c, j, i, e, p, k, rf);
     const int b = j.ptr[i];
     int w = j.ptr[i + 1] - 1;
-    j.slack[i] = c.ep_setup[(size_t)e * c.K + j.corner];
+    float es = INFINITY;
+    for (int g = 0; g < c.Tg; ++g) es = fminf(es, c.ep_setup[(size_t)e * c.K + j.corner * c.Tg + g]);
+    j.slack[i] = es;
     j.endpoint[i] = j.caller_pin[p];
     for (;;) {
         if (w < b) break;
         j.pin[w] = j.caller_pin[p];
         j.rf[w] = (int8_t)rf;
-        j.at[w] = ld_state(c.at + (size_t)p * c.K + j.corner, 2 + rf);
+        j.at[w] = ld_state(c.at + (size_t)p * c.K + k, 2 + rf);
         --w;
-        if (!trace_step<UNIFORM>(c, j, p, rf)) break;
+        if (!trace_step<UNIFORM>(c, j, k, p, rf)) break;
     }
 }
 

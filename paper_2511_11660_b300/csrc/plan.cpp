@@ -109,17 +109,29 @@ void build(const sta_design_desc *d, Plan &pl)
     const int32_t C = d->n_cells, P = d->n_pins, N = d->n_nets;
     REQUIRE(C >= 0 && P >= 0 && N >= 0, STA_EINVAL, "negative size");
     REQUIRE(d->n_corners >= 1 && d->n_corners <= 16, STA_EINVAL, "n_corners %d out of [1, 16]", d->n_corners);
-    const int K = d->n_corners;
+    const int Kc = d->n_corners;
+    REQUIRE(d->n_exc >= 0 && d->n_exc <= 7, STA_EINVAL, "n_exc %d out of [0, 7]", d->n_exc);
+    REQUIRE(d->n_exc == 0 || (d->exc_from_ptr && d->exc_to_ptr && d->exc_action && d->exc_mult &&
+                              (d->exc_from || d->exc_from_ptr[d->n_exc] == 0) &&
+                              (d->exc_to || d->exc_to_ptr[d->n_exc] == 0)),
+            STA_EINVAL, "exception arrays NULL");
+    REQUIRE(d->n_exc == 0 || d->gamma_ns == 0.f, STA_EINVAL, "timing exceptions need gamma_ns = 0");
+    const int Tg = d->n_exc + 1, K = Kc * Tg;   // states: corner * Tg + tag
+    pl.Kc = Kc;
+    pl.Tg = Tg;
     pl.K = K;
     pl.C = C;
     pl.P = P;
     pl.lut_scale.assign(K, 1.f);
     pl.rc_scale.assign(K, 1.f);
-    for (int k = 0; k < K; ++k) {
-        if (d->lut_scale) pl.lut_scale[k] = d->lut_scale[k];
-        if (d->rc_scale) pl.rc_scale[k] = d->rc_scale[k];
-        REQUIRE(finite(pl.lut_scale[k]) && pl.lut_scale[k] > 0 && finite(pl.rc_scale[k]) && pl.rc_scale[k] > 0,
-                STA_EINVAL, "corner %d: scales must be finite and > 0", k);
+    for (int k = 0; k < Kc; ++k) {
+        const float ls = d->lut_scale ? d->lut_scale[k] : 1.f, rs = d->rc_scale ? d->rc_scale[k] : 1.f;
+        REQUIRE(finite(ls) && ls > 0 && finite(rs) && rs > 0, STA_EINVAL, "corner %d: scales must be finite and > 0",
+                k);
+        for (int g = 0; g < Tg; ++g) {
+            pl.lut_scale[k * Tg + g] = ls;
+            pl.rc_scale[k * Tg + g] = rs;
+        }
     }
     REQUIRE(finite(d->period_ns) && finite(d->clk_slew_ns) && d->clk_slew_ns >= 0 && finite(d->pi_at_ns) &&
                 finite(d->pi_slew_ns) && d->pi_slew_ns >= 0,
@@ -419,6 +431,50 @@ void build(const sta_design_desc *d, Plan &pl)
             }
         }
     }
+    // ---- timing exceptions: the tag of every startpoint item (its PI or CK
+    // pin's first group) and the setup multiplier of every (endpoint, tag)
+    pl.item_tag.clear();
+    pl.ep_mult.clear();
+    if (pl.Tg > 1) {
+        const int32_t G = pl.Tg - 1;
+        std::vector<int8_t> tag_of(P, 0);
+        std::vector<int32_t> caller_of(P, 0);
+        for (int32_t p = 0; p < P; ++p) caller_of[pl.gpu_of[p]] = p;
+        for (int32_t g = 0; g < G; ++g) {
+            REQUIRE(d->exc_from_ptr[g] >= 0 && d->exc_from_ptr[g] <= d->exc_from_ptr[g + 1] && d->exc_to_ptr[g] >= 0 &&
+                        d->exc_to_ptr[g] <= d->exc_to_ptr[g + 1],
+                    STA_EINVAL, "exception group %d: offsets not monotone", g);
+            for (int32_t i = d->exc_from_ptr[g]; i < d->exc_from_ptr[g + 1]; ++i) {
+                const int32_t p = d->exc_from[i];
+                REQUIRE(p >= 0 && p < P && (d->pin_role[p] == kPinPI || d->pin_role[p] == kPinCK), STA_EINVAL,
+                        "exception group %d: startpoint %d is not a PI or CK pin", g, p);
+                if (!tag_of[p]) tag_of[p] = (int8_t)(g + 1);
+            }
+            for (int32_t i = d->exc_to_ptr[g]; i < d->exc_to_ptr[g + 1]; ++i) {
+                const int32_t p = d->exc_to[i];
+                REQUIRE(p >= 0 && p < P && (d->pin_role[p] == kPinD || d->pin_role[p] == kPinPO), STA_EINVAL,
+                        "exception group %d: endpoint %d is not a D or PO pin", g, p);
+            }
+            REQUIRE(d->exc_action[g] == 0 || (d->exc_action[g] == 1 && finite(d->exc_mult[g]) && d->exc_mult[g] >= 1.f),
+                    STA_EINVAL, "exception group %d: action must be 0 (false path) or 1 (multicycle, M >= 1)", g);
+        }
+        pl.item_tag.assign(pl.I, 0);
+        for (int32_t g = 0; g < pl.I; ++g) {
+            const int32_t t = pl.item_type[g];
+            if (t < 0) pl.item_tag[g] = tag_of[caller_of[pl.item_pin0[g]]];
+            else if (pl.type_kind[t] == 1) pl.item_tag[g] = tag_of[d->cell_pin[d->cell_pin_ptr[pl.item_cell[g]] + 1]];
+        }
+        pl.ep_mult.assign((size_t)pl.E * pl.Tg, 1.f);
+        std::vector<uint8_t> in_to(P, 0);
+        for (int32_t g = 0; g < G; ++g) {
+            const bool all = d->exc_to_ptr[g] == d->exc_to_ptr[g + 1];
+            for (int32_t i = d->exc_to_ptr[g]; i < d->exc_to_ptr[g + 1]; ++i) in_to[d->exc_to[i]] = 1;
+            for (int32_t e = 0; e < pl.E; ++e)
+                if (all || in_to[caller_of[pl.ep_pin[e]]])
+                    pl.ep_mult[(size_t)e * pl.Tg + g + 1] = d->exc_action[g] == 0 ? 0.f : d->exc_mult[g];
+            for (int32_t i = d->exc_to_ptr[g]; i < d->exc_to_ptr[g + 1]; ++i) in_to[d->exc_to[i]] = 0;
+        }
+    }
     // ---- RC nets too large for the shared-memory sweep
     pl.n_big_nets = 0;
     if (!pl.placed)
@@ -474,8 +530,10 @@ bool same_library(const sta_library &a, const sta_library &b)
 sta_status build_batch_plan(const sta_design_desc *const *descs, int32_t n, Plan &plan, std::string &err)
 {
     if (n < 1 || !descs) { err = "empty batch"; return STA_EINVAL; }
-    for (int32_t i = 0; i < n; ++i)
+    for (int32_t i = 0; i < n; ++i) {
         if (!descs[i] || !descs[i]->lib) { err = "NULL descriptor in batch"; return STA_EINVAL; }
+        if (descs[i]->n_exc != 0) { err = "timing exceptions are not supported in a batch"; return STA_EINVAL; }
+    }
     const sta_design_desc &d0 = *descs[0];
     const bool placed = d0.rc_ptr == nullptr;
     const int K = d0.n_corners;

@@ -35,6 +35,9 @@ struct Plan {
     bool placed = false;
     float gamma = 0.f;
     int32_t net_model = STA_NET_ELMORE;      // net delay calculator
+    int32_t Kc = 1, Tg = 1;                  // corners and exception tags; K = Kc * Tg states
+    std::vector<int32_t> item_tag;           // [I] exception tag of a startpoint item (PI, flip-flop), else 0
+    std::vector<float> ep_mult;              // [E][Tg] setup multiplier of each endpoint and tag, 0 = no check
     int32_t arnoldi_q = 3;                   // order of STA_NET_ARNOLDI
     // constraints
     float period = 1.f, clk_slew = 0.02f, pi_at = 0.f, pi_slew = 0.02f;

@@ -46,6 +46,9 @@ struct sta_ctx {
     std::string msg;
     // caller pin -> (cell, slot) for resizing
     std::vector<int32_t> pin_cell_c, pin_slot_c;
+    // endpoint slacks collapsed over exception tags (allocated at first use)
+    float *d_ep_collapse = nullptr;
+    uint8_t *d_viol_collapse = nullptr;
     // path reports (allocated at the first sta_report_paths)
     sta::PathJob pj{};
     int32_t path_cap = 0;   // pins the path buffers hold
@@ -136,6 +139,8 @@ sta_status create_from_plan(sta_ctx *c, int device)
     d.S = pl.S;
     d.E = pl.E;
     d.K = pl.K;
+    d.Kc = pl.Kc;
+    d.Tg = pl.Tg;
     d.NN = pl.NN;
     d.F = (int32_t)pl.F;
     d.net_model = pl.net_model;
@@ -198,7 +203,11 @@ sta_status create_from_plan(sta_ctx *c, int device)
     d.ep_hold = dev_alloc<float>(c, EK);
     d.viol_setup = dev_alloc<uint8_t>(c, EK);
     d.viol_hold = dev_alloc<uint8_t>(c, EK);
-    d.report = dev_alloc<double>(c, (size_t)pl.n_designs * pl.K * 8);
+    d.report = dev_alloc<double>(c, (size_t)pl.n_designs * pl.Kc * 8);
+    if (pl.Tg > 1) {
+        d.item_tag = upload(c, pl.item_tag);
+        d.ep_mult = upload(c, pl.ep_mult);
+    }
     {
         // reduction chunks: <= kRedChunk endpoints, never straddling designs
         std::vector<int32_t> cp{0}, dc{0};
@@ -210,7 +219,7 @@ sta_status create_from_plan(sta_ctx *c, int device)
         c->hs.n_red_chunks = (int)cp.size() - 1;
         d.red_chunk_ptr = upload(c, cp);
         d.red_design_chunk = upload(c, dc);
-        d.red_partial = dev_alloc<double>(c, std::max<size_t>(1, cp.size() - 1) * pl.K * 6);
+        d.red_partial = dev_alloc<double>(c, std::max<size_t>(1, cp.size() - 1) * pl.Kc * 6);
     }
     d.err = dev_alloc<unsigned>(c, 1);
     CK(cudaMemset(d.err, 0, sizeof(unsigned)));
@@ -413,7 +422,8 @@ sta_status sta_plan(const sta_design_desc *desc, sta_plan_info *out)
         out->n_rc_nodes = pl.placed ? pl.F + desc->n_nets : pl.NN;
         out->n_endpoints = pl.E;
         out->n_levels = pl.S;
-        out->n_corners = pl.K;
+        out->n_corners = pl.Kc;
+        out->n_tags = pl.Tg;
         out->max_level_width = pl.max_width;
         out->n_designs = 1;
         out->device_bytes = 0;
@@ -530,19 +540,24 @@ const char *sta_last_error(const sta_ctx *c) { return c ? c->msg.c_str() : "NULL
 sta_status sta_set_corners(sta_ctx *c, const float *lut_scale, const float *rc_scale)
 {
     if (!c || !lut_scale || !rc_scale) return STA_EINVAL;
-    const int K = c->plan.K;
-    for (int k = 0; k < K; ++k)
+    const int Kc = c->plan.Kc, Tg = c->plan.Tg, K = c->plan.K;
+    for (int k = 0; k < Kc; ++k)
         if (!std::isfinite(lut_scale[k]) || !(lut_scale[k] > 0) || !std::isfinite(rc_scale[k]) || !(rc_scale[k] > 0))
             return fail(c, STA_EINVAL, "corner scales must be finite and > 0");
+    std::vector<float> ls(K), rs(K);   // every exception tag of a corner shares its scales
+    for (int k = 0; k < K; ++k) {
+        ls[k] = lut_scale[k / Tg];
+        rs[k] = rc_scale[k / Tg];
+    }
     try {
         CK(cudaSetDevice(c->device));
-        CK(cudaMemcpy(const_cast<float *>(c->dc.lut_scale), lut_scale, K * sizeof(float), cudaMemcpyHostToDevice));
-        CK(cudaMemcpy(const_cast<float *>(c->dc.rc_scale), rc_scale, K * sizeof(float), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(const_cast<float *>(c->dc.lut_scale), ls.data(), K * sizeof(float), cudaMemcpyHostToDevice));
+        CK(cudaMemcpy(const_cast<float *>(c->dc.rc_scale), rs.data(), K * sizeof(float), cudaMemcpyHostToDevice));
     } catch (const CudaFail &f) {
         return from_cuda(c, f);
     }
-    c->plan.lut_scale.assign(lut_scale, lut_scale + K);
-    c->plan.rc_scale.assign(rc_scale, rc_scale + K);
+    c->plan.lut_scale = ls;
+    c->plan.rc_scale = rs;
     return STA_OK;
 }
 
@@ -796,7 +811,7 @@ sta_status sta_report_slack_design(sta_ctx *c, int32_t d, void *stream, sta_corn
     if (d < 0 || d >= c->plan.n_designs) return fail(c, STA_EINVAL, "design index out of range");
     sta_status st = sta_sync(c, stream);
     if (st != STA_OK) return st;
-    const int K = c->plan.K;
+    const int K = c->plan.Kc;
     std::vector<double> h((size_t)K * 8);
     try {
         CK(cudaMemcpy(h.data(), c->dc.report + (size_t)d * K * 8, h.size() * sizeof(double),
@@ -857,12 +872,25 @@ sta_status sta_get_endpoint_slack(sta_ctx *c, float *setup, float *hold, uint8_t
     try {
         CK(cudaSetDevice(c->device));
         cudaStream_t st = as_stream(stream);
-        const size_t EK = (size_t)c->plan.E * c->plan.K;
+        const size_t EK = (size_t)c->plan.E * c->plan.Kc;
         const cudaMemcpyKind kind = mem == STA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
-        if (setup) CK(cudaMemcpyAsync(setup, c->dc.ep_setup, EK * sizeof(float), kind, st));
-        if (hold) CK(cudaMemcpyAsync(hold, c->dc.ep_hold, EK * sizeof(float), kind, st));
-        if (vs) CK(cudaMemcpyAsync(vs, c->dc.viol_setup, EK, kind, st));
-        if (vh) CK(cudaMemcpyAsync(vh, c->dc.viol_hold, EK, kind, st));
+        const float *es = c->dc.ep_setup, *eh = c->dc.ep_hold;
+        const uint8_t *evs = c->dc.viol_setup, *evh = c->dc.viol_hold;
+        if (c->plan.Tg > 1) {   // per corner: min over the exception tags
+            if (!c->d_ep_collapse) {
+                c->d_ep_collapse = dev_alloc<float>(c, 2 * std::max<size_t>(1, EK));
+                c->d_viol_collapse = dev_alloc<uint8_t>(c, 2 * std::max<size_t>(1, EK));
+            }
+            sta::launch_collapse_tags(c->dc, c->d_ep_collapse, c->d_viol_collapse, st);
+            es = c->d_ep_collapse;
+            eh = c->d_ep_collapse + EK;
+            evs = c->d_viol_collapse;
+            evh = c->d_viol_collapse + EK;
+        }
+        if (setup) CK(cudaMemcpyAsync(setup, es, EK * sizeof(float), kind, st));
+        if (hold) CK(cudaMemcpyAsync(hold, eh, EK * sizeof(float), kind, st));
+        if (vs) CK(cudaMemcpyAsync(vs, evs, EK, kind, st));
+        if (vh) CK(cudaMemcpyAsync(vh, evh, EK, kind, st));
         if (mem == STA_HOST) CK(cudaStreamSynchronize(st));
     } catch (const CudaFail &f) {
         return from_cuda(c, f);
@@ -879,7 +907,7 @@ sta_status sta_report_paths(sta_ctx *c, int32_t design, int32_t corner, int32_t 
     if (!c->updated) return fail(c, STA_ESTATE, "no analysis yet");
     const Plan &pl = c->plan;
     if (design < 0 || design >= pl.n_designs) return fail(c, STA_EINVAL, "design index out of range");
-    if (corner < 0 || corner >= pl.K) return fail(c, STA_EINVAL, "corner index out of range");
+    if (corner < 0 || corner >= pl.Kc) return fail(c, STA_EINVAL, "corner index out of range");
     if (k < 0 || k > sta::kMaxPaths) return fail(c, STA_EINVAL, "k must be in 0..4096");
     if (std::isnan(slack_lt)) return fail(c, STA_EINVAL, "slack threshold is NaN");
     try {
@@ -1085,7 +1113,8 @@ sta_status sta_stats(const sta_ctx *c, sta_plan_info *out)
     out->n_rc_nodes = pl.placed ? pl.F + out->n_nets : pl.NN;
     out->n_endpoints = pl.E;
     out->n_levels = pl.S;
-    out->n_corners = pl.K;
+    out->n_corners = pl.Kc;
+    out->n_tags = pl.Tg;
     out->max_level_width = pl.max_width;
     out->n_designs = pl.n_designs;
     out->device_bytes = (int64_t)c->bytes;

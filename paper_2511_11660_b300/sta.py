@@ -47,7 +47,9 @@ class sta_design_desc(C.Structure):
                 ("c_per_um", C.c_float), ("period_ns", C.c_float), ("clk_slew_ns", C.c_float),
                 ("pi_at_ns", C.c_float), ("pi_slew_ns", C.c_float), ("n_corners", C.c_int32),
                 ("lut_scale", C.c_void_p), ("rc_scale", C.c_void_p), ("gamma_ns", C.c_float),
-                ("net_model", C.c_int32), ("arnoldi_order", C.c_int32)]
+                ("net_model", C.c_int32), ("arnoldi_order", C.c_int32), ("n_exc", C.c_int32),
+                ("exc_from_ptr", C.c_void_p), ("exc_from", C.c_void_p), ("exc_to_ptr", C.c_void_p),
+                ("exc_to", C.c_void_p), ("exc_action", C.c_void_p), ("exc_mult", C.c_void_p)]
 
 
 class sta_plan_info(C.Structure):
@@ -55,7 +57,7 @@ class sta_plan_info(C.Structure):
                 ("n_cell_arcs", C.c_int64), ("n_net_arcs", C.c_int64), ("n_rc_nodes", C.c_int64),
                 ("n_endpoints", C.c_int64), ("n_levels", C.c_int32), ("n_corners", C.c_int32),
                 ("max_level_width", C.c_int32), ("n_designs", C.c_int32), ("device_bytes", C.c_int64),
-                ("launches_per_update", C.c_int32), ("launches_per_backward", C.c_int32)]
+                ("launches_per_update", C.c_int32), ("launches_per_backward", C.c_int32), ("n_tags", C.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -166,7 +168,8 @@ class Design:
             "cell_pin_ptr": np.int32, "cell_pin": np.int32, "pin_role": np.int8, "net_pin_ptr": np.int32,
             "net_pin": np.int32, "rc_ptr": np.int32, "rc_parent": np.int32, "rc_pin_node": np.int32,
             "rc_R": np.float32, "rc_C": np.float32, "cell_xy": np.float32, "port_xy": np.float32,
-            "lut_scale": np.float32, "rc_scale": np.float32}
+            "lut_scale": np.float32, "rc_scale": np.float32, "exc_from_ptr": np.int32, "exc_from": np.int32,
+            "exc_to_ptr": np.int32, "exc_to": np.int32, "exc_action": np.int32, "exc_mult": np.float32}
 
     def __init__(self, d: dict):
         self.src = d
@@ -188,7 +191,9 @@ class Design:
             float(d.get("r_per_um", 0.0)), float(d.get("c_per_um", 0.0)), float(d["period_ns"]),
             float(d["clk_slew_ns"]), float(d["pi_at_ns"]), float(d["pi_slew_ns"]), int(d.get("n_corners", 1)),
             _ptr(a["lut_scale"]), _ptr(a["rc_scale"]), float(d.get("gamma_ns", 0.0)),
-            int(d.get("net_model", 0)), int(d.get("arnoldi_order", 0)))
+            int(d.get("net_model", 0)), int(d.get("arnoldi_order", 0)),
+            0 if a["exc_action"] is None else len(a["exc_action"]), _ptr(a["exc_from_ptr"]), _ptr(a["exc_from"]),
+            _ptr(a["exc_to_ptr"]), _ptr(a["exc_to"]), _ptr(a["exc_action"]), _ptr(a["exc_mult"]))
 
     @property
     def n_pins(self):
@@ -239,6 +244,7 @@ class Context:
             raise StaError(st, self.lib.sta_plan_error().decode())
         info = self.stats()
         self.P, self.K, self.E, self.C = info["n_pins"], info["n_corners"], info["n_endpoints"], info["n_cells"]
+        self.T = info["n_tags"]
         self.device = device
 
     def _chk(self, st):
@@ -334,10 +340,11 @@ class Context:
         return [r.as_dict() for r in reps]
 
     def get_pin_state(self, which: int, out=None, stream=None):
-        """[n_pins, n_corners, 4] float32 in caller pin order; a torch CUDA
-        tensor ``out`` receives it on the device, else a numpy array."""
+        """[n_pins, n_corners * n_tags, 4] float32 in caller pin order (state
+        = corner * n_tags + exception tag); a torch CUDA tensor ``out``
+        receives it on the device, else a numpy array."""
         if out is None:
-            out = np.empty((self.P, self.K, 4), np.float32)
+            out = np.empty((self.P, self.K * self.T, 4), np.float32)
         self._chk(self.lib.sta_get_pin_state(self.h, which, _ptr(out), _mem_of(out), _stream(stream)))
         return out
 

@@ -31,7 +31,11 @@ def tol(x):
 
 
 def check_paths(d, gpu, res, k, slack_lt=np.inf, corner=0):
+    """With timing exceptions each path is checked in the (corner, tag)
+    states whose late slack at its endpoint is within tolerance of the
+    smallest: it must be valid and critical in one of them."""
     net = _indep.Net(d, corner)
+    Tg = 1 + (len(d["exc_action"]) if d.get("exc_action") is not None else 0)
     role = np.asarray(d["pin_role"])
     K = int(d.get("n_corners", 1))
     sc = float(np.asarray(d["lut_scale"] if d.get("lut_scale") is not None else np.ones(K))[corner])
@@ -40,7 +44,6 @@ def check_paths(d, gpu, res, k, slack_lt=np.inf, corner=0):
     vv = np.asarray(d["lut_val"]).reshape(-1, 3, 4, 49)
     sense = np.asarray(d["arc_sense"]).reshape(-1, 3)
     cpp, cp = np.asarray(d["cell_pin_ptr"]), np.asarray(d["cell_pin"])
-    at, slew = res["at"][:, corner], res["slew"][:, corner]
     eps, es = res["endpoints"], res["ep_setup"][:, corner]
     eligible = sorted((e for e in range(len(eps)) if es[e] < slack_lt), key=lambda e: (es[e], e))
     assert len(gpu) == min(k, len(eligible))
@@ -54,14 +57,16 @@ def check_paths(d, gpu, res, k, slack_lt=np.inf, corner=0):
         s = [p["slack"] for p in gpu]
         assert all(a <= b for a, b in zip(s, s[1:]))
 
-    def cand(v, rv, u, ru):
-        c = net.cell_of[v]
-        t = d["cell_type"][c]
-        j = net.slot_of[u]
-        dl = oracle.lut_eval(i1[t, j, rv], i2[t, j, rv], vv[t, j, rv], slew[u, 2 + ru], net.load[v])[0]
-        return at[u, 2 + ru] + sc * dl
+    def check_one(p, st):
+        at, slew = res["at"][:, st], res["slew"][:, st]
 
-    for p in gpu:
+        def cand(v, rv, u, ru):
+            c = net.cell_of[v]
+            t = d["cell_type"][c]
+            j = net.slot_of[u]
+            dl = oracle.lut_eval(i1[t, j, rv], i2[t, j, rv], vv[t, j, rv], slew[u, 2 + ru], net.load[v])[0]
+            return at[u, 2 + ru] + sc * dl
+
         pins, rfs, ats = p["pins"], p["rf"], p["at"]
         assert pins[-1] == p["endpoint"]
         assert role[pins[0]] in (synth.PI, synth.CK)
@@ -82,6 +87,21 @@ def check_paths(d, gpu, res, k, slack_lt=np.inf, corner=0):
             best = max(cand(v, rv, int(cp[cpp[c] + j]), r2) for j in range(d["type_nin"][t])
                        for r2 in _indep.rf_in_of(sense[t, j], rv))
             assert cand(v, rv, u, ru) >= best - 2 * tol(best)
+
+    for p in gpu:
+        e = int(p["endpoint"])
+        late = [float(np.min(res["slack"][e, corner * Tg + g, 2:])) for g in range(Tg)]
+        worst = min(late)
+        states = [corner * Tg + g for g in range(Tg) if late[g] <= worst + 2 * tol(worst)]
+        errors = []
+        for st in states:
+            try:
+                check_one(p, st)
+                break
+            except AssertionError as ex:
+                errors.append(ex)
+        else:
+            raise errors[0]
 
 
 @pytest.mark.parametrize("case", ["tiny", "corners", "smooth", "threshold"])

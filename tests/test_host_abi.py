@@ -109,6 +109,34 @@ def test_plan_net_model_validation(lib):
         assert ei.value.status == sta.EINVAL
 
 
+def test_plan_exception_validation(lib):
+    """Timing exceptions: n_tags = groups + 1 and the per-pin state count
+    grows with it; at most 7 groups; startpoints must be PI or CK pins,
+    endpoint lists D or PO pins; actions 0 (false path) or 1 (multicycle
+    with M >= 1); offsets monotone; not with smoothing (gamma_ns > 0)."""
+    d = synth.make_design(300, 6, seed=2, n_corners=2, lut_scale=[1.0, 1.2], rc_scale=[1.0, 1.1])
+    rng = np.random.default_rng(0)
+    g3 = synth.exception_groups(d, rng, 3)
+    info = sta.sta_plan(dict(d, **g3))
+    assert info["n_tags"] == 4 and info["n_corners"] == 2
+    assert sta.sta_plan(d)["n_tags"] == 1
+    role = np.asarray(d["pin_role"])
+    q_pin = int(np.nonzero(role == synth.Q)[0][0])
+    ck_pin = int(np.nonzero(role == synth.CK)[0][0])
+    bads = [dict(d, **synth.exception_groups(d, rng, 8)),
+            dict(d, **g3, gamma_ns=0.01),
+            dict(d, **dict(g3, exc_from=np.where(np.arange(len(g3["exc_from"])) == 0, q_pin, g3["exc_from"]))),
+            dict(d, **dict(g3, exc_action=np.array([0, 2, 1], np.int32))),
+            dict(d, **dict(g3, exc_action=np.array([1, 1, 1], np.int32), exc_mult=np.array([2, 0.5, 3], np.float32))),
+            dict(d, **dict(g3, exc_from_ptr=g3["exc_from_ptr"][[0, 2, 1, 3]]))]
+    if len(g3["exc_to"]):
+        bads.append(dict(d, **dict(g3, exc_to=np.where(np.arange(len(g3["exc_to"])) == 0, ck_pin, g3["exc_to"]))))
+    for i, bad in enumerate(bads):
+        with pytest.raises(sta.StaError) as ei:
+            sta.sta_plan(bad)
+        assert ei.value.status == sta.EINVAL, i
+
+
 def test_plan_rejects_floating_input(lib):
     lib_ = synth.make_library(0)
     b = synth.Builder(lib_)

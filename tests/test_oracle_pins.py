@@ -705,26 +705,6 @@ def test_paths_order_threshold_and_count():
 
 # ------------------------------------------------------- O8 timing exceptions
 
-def _groups(d, rng, n_groups):
-    """Random exception groups: startpoints (PIs and CKs), endpoint lists
-    (sometimes empty = every endpoint), false path or multicycle."""
-    role = np.asarray(d["pin_role"])
-    starts = np.nonzero((role == synth.PI) | (role == synth.CK))[0]
-    ends = np.nonzero((role == synth.D) | (role == synth.PO))[0]
-    fp, fr, tp, to, act, mult = [0], [], [0], [], [], []
-    for g in range(n_groups):
-        fr += list(rng.choice(starts, size=max(1, len(starts) // 3), replace=False))
-        fp.append(len(fr))
-        if rng.random() < 0.7:
-            to += list(rng.choice(ends, size=max(1, len(ends) // 2), replace=False))
-        tp.append(len(to))
-        act.append(int(rng.random() < 0.5))
-        mult.append(float(rng.integers(2, 4)))
-    return dict(exc_from_ptr=np.array(fp, np.int32), exc_from=np.array(fr, np.int32),
-                exc_to_ptr=np.array(tp, np.int32), exc_to=np.array(to, np.int32),
-                exc_action=np.array(act, np.int32), exc_mult=np.array(mult, np.float32))
-
-
 @pytest.mark.parametrize("seed", range(5))
 def test_exceptions_brute_force_fixed_delay(seed):
     """Every path tagged by its startpoint's first group: an endpoint's setup
@@ -736,7 +716,7 @@ def test_exceptions_brute_force_fixed_delay(seed):
     rng = np.random.default_rng(seed)
     d = _fixed_design(seed, n_cells=14, depth=5)
     d["period_ns"] = 0.35
-    d.update(_groups(d, rng, 3))
+    d.update(synth.exception_groups(d, rng, 3))
     res = oracle.sta(d)
     role = np.asarray(d["pin_role"])
     first = {}
@@ -782,3 +762,47 @@ def test_exceptions_all_false_and_all_multicycle():
     r = oracle.sta(dict(d, exc_action=np.array([1], np.int32), exc_mult=np.array([3], np.float32), **grp))
     np.testing.assert_allclose(r["ep_setup"], base["ep_setup"] + 2 * d["period_ns"], rtol=0, atol=1e-12)
     np.testing.assert_array_equal(r["ep_hold"], base["ep_hold"])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_exception_paths_fixed_delay(seed):
+    """With exceptions the reported path is the one that sets the endpoint's
+    slack: it starts at a startpoint s, its arrival at the endpoint is an
+    enumerated path arrival from s, and (late requirement of s's tag at the
+    endpoint) - arrival equals the endpoint's slack, the minimum over every
+    enumerated tagged path."""
+    rng = np.random.default_rng(50 + seed)
+    d = _fixed_design(seed, n_cells=14, depth=5)
+    d["period_ns"] = 0.35
+    d.update(synth.exception_groups(d, rng, 3))
+    res = oracle.sta(d)
+    role = np.asarray(d["pin_role"])
+    first = {}
+    for g in range(3):
+        for p in d["exc_from"][d["exc_from_ptr"][g]:d["exc_from_ptr"][g + 1]]:
+            first.setdefault(int(p), g)
+    T = d["period_ns"]
+
+    def late_req(p, s):
+        base = T - d["setup_ns"] if role[p] == synth.D else T
+        g = first.get(int(s))
+        if g is None:
+            return base
+        lst = d["exc_to"][d["exc_to_ptr"][g]:d["exc_to_ptr"][g + 1]]
+        if len(lst) and p not in lst:
+            return base
+        if d["exc_action"][g] == 0:
+            return np.inf
+        M = float(d["exc_mult"][g])
+        return M * T - d["setup_ns"] if role[p] == synth.D else M * T
+
+    allp = _indep.enumerate_paths_from(d)
+    paths = oracle.report_paths(d, 100, res=res)
+    assert len(paths) == int(np.sum(res["ep_setup"][:, 0] < np.inf))
+    for pth in paths:
+        e, s, rf = int(pth["endpoint"]), int(pth["pins"][0]), int(pth["rf"][-1])
+        want = min(late_req(e, s2) - a for a, _, s2 in allp[e])
+        assert pth["slack"] == pytest.approx(want, abs=1e-12)
+        arrivals = [a for a, f, s2 in allp[e] if s2 == s and f == rf]
+        assert min(abs(a - pth["at"][-1]) for a in arrivals) <= 1e-12
+        assert late_req(e, s) - pth["at"][-1] == pytest.approx(want, abs=1e-12)
