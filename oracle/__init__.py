@@ -54,8 +54,12 @@ def _load():
         _lib.orc_sta.argtypes = [P, P, P, P, P, P, P, P]
         _lib.orc_objective_grad.argtypes = [P, C.c_double, C.c_double, P, P, P]
         _lib.orc_objective.argtypes = [P, C.c_double, C.c_double, P]
+        _lib.orc_steiner_tree.argtypes = [C.c_int32, P, P, P, P, P, P, P, P]
+        _lib.orc_nm.argtypes = [C.c_float]
+        _lib.orc_net_wirelengths.argtypes = [P, P]
+        _lib.orc_nm.restype = C.c_int64
         for f in ("orc_lut_eval", "orc_rc_tree", "orc_arnoldi_t50", "orc_net_delays", "orc_topo_order", "orc_sta",
-                  "orc_objective_grad", "orc_objective"):
+                  "orc_objective_grad", "orc_objective", "orc_steiner_tree", "orc_net_wirelengths"):
             getattr(_lib, f).restype = C.c_int
     return _lib
 
@@ -78,6 +82,7 @@ class _Design(C.Structure):
         ("net_model", C.c_int32), ("arnoldi_order", C.c_int32),
         ("n_exc", C.c_int32), ("exc_from_ptr", C.c_void_p), ("exc_from", C.c_void_p), ("exc_to_ptr", C.c_void_p),
         ("exc_to", C.c_void_p), ("exc_action", C.c_void_p), ("exc_mult", C.c_void_p),
+        ("wire_model", C.c_int32), ("r_per_um_y", C.c_double), ("c_per_um_y", C.c_double),
     ]
 
 
@@ -92,7 +97,7 @@ _ARRAYS = {
     "exc_action": np.int32, "exc_mult": np.float32,
 }
 _SCALARS = ("setup_ns", "hold_ns", "po_cap_pf", "r_per_um", "c_per_um", "period_ns", "clk_slew_ns",
-            "pi_at_ns", "pi_slew_ns", "gamma_ns")
+            "pi_at_ns", "pi_slew_ns", "gamma_ns", "r_per_um_y", "c_per_um_y")
 
 
 def _marshal(d: dict, use_rc: bool | None = None):
@@ -119,6 +124,7 @@ def _marshal(d: dict, use_rc: bool | None = None):
     s.n_nets = int(d["n_nets"])
     s.n_corners = int(d.get("n_corners", 1))
     s.net_model = int(d.get("net_model", 0))
+    s.wire_model = int(d.get("wire_model", 0))
     s.n_exc = int(len(d["exc_action"])) if d.get("exc_action") is not None else 0
     s.arnoldi_order = int(d.get("arnoldi_order", 3))
     if d.get("lut_scale") is None:
@@ -170,6 +176,43 @@ def arnoldi_t50(parent, R, C_, q: int):
     out = np.zeros(len(par), np.float64)
     _check(lib.orc_arnoldi_t50(len(par), _ptr(par), _ptr(r), _ptr(c), int(q), _ptr(out)), "arnoldi_t50")
     return out
+
+
+def nm(x_um: float) -> int:
+    """O9 coordinate: the float product x * 1000 rounded to the nearest
+    integer (ties to even), in nm."""
+    return int(_load().orc_nm(float(x_um)))
+
+
+def steiner_tree(X, Y) -> dict:
+    """O9 on one net: integer nm pin coordinates (pin 0 = the driver) ->
+    the rectilinear Steiner tree in breadth-first order: parent (root -1),
+    node coordinates nx, ny, pin_node (node of each pin) and the total
+    wirelength wl (nm)."""
+    lib = _load()
+    X = np.ascontiguousarray(X, np.int64)
+    Y = np.ascontiguousarray(Y, np.int64)
+    n = len(X)
+    cap = max(1, 2 * n - 2)
+    par = np.zeros(cap, np.int32)
+    nx = np.zeros(cap, np.int64)
+    ny = np.zeros(cap, np.int64)
+    pn = np.zeros(max(n, 1), np.int32)
+    n_out = C.c_int32(0)
+    wl = C.c_int64(0)
+    _check(lib.orc_steiner_tree(n, _ptr(X), _ptr(Y), C.byref(n_out), _ptr(par), _ptr(nx), _ptr(ny), _ptr(pn),
+                                C.byref(wl)), "steiner_tree")
+    k = n_out.value
+    return {"parent": par[:k], "nx": nx[:k], "ny": ny[:k], "pin_node": pn[:n], "wl": int(wl.value)}
+
+
+def net_wirelengths(d: dict) -> np.ndarray:
+    """O9 tree length (int64 nm) of every net of a placed design."""
+    lib = _load()
+    s, keep = _marshal(d, use_rc=False)
+    wl = np.zeros(max(int(d["n_nets"]), 1), np.int64)
+    _check(lib.orc_net_wirelengths(C.byref(s), _ptr(wl)), "net_wirelengths")
+    return wl[: int(d["n_nets"])]
 
 
 def net_delays(d: dict, corner: int = 0, use_rc: bool | None = None):

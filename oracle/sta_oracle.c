@@ -37,6 +37,9 @@
  *       the list is empty) -- false path: no check; multicycle M: setup
  *       capture edge at M * T, hold unchanged -- and the default check
  *       otherwise; endpoint slack = min over tags;
+ *   O9  rectilinear Steiner tree RC from pin positions (Sec. III,
+ *       "Parasitics (RC) inputs"): Prim MST on integer nm coordinates,
+ *       greedy median Steiner insertion, breadth-first RC tree;
  *   O6  log-sum-exp smoothed objective and its hand-written FP64 adjoint
  *       with respect to cell (x, y) (not in the paper; it feeds a placer the
  *       way the paper's DREAMPlace integration consumes pin slacks, Sec. IV-C).
@@ -116,6 +119,10 @@ typedef struct {
     int32_t n_exc;
     const int32_t *exc_from_ptr, *exc_from, *exc_to_ptr, *exc_to, *exc_action;
     const float *exc_mult;
+    /* O9: RC from positions as a star (0) or a Steiner tree (1); unit R/C
+     * along y for the Steiner tree (<= 0: the x values r_per_um, c_per_um) */
+    int32_t wire_model;
+    double r_per_um_y, c_per_um_y;
 } orc_design;
 
 /* ------------------------------------------------------------------ O1 */
@@ -508,10 +515,187 @@ static void pin_xy(const orc_design *d, const pin_info *pi, int32_t p, double *x
     else { *x = 0.0; *y = 0.0; }
 }
 
+/* ------------------------------------------------------------------ O9 */
+
+/* Rectilinear Steiner tree of one net from its pin positions (Sec. III,
+ * "Parasitics (RC) inputs": the placement flow sends pin positions and unit
+ * R/C along x and y and the engine builds Steiner-tree RC).  The paper's
+ * tree builder (GPU FLUTE) is not reproduced; this is the reading:
+ *
+ *   coordinates  x, y in um (float) -> integer nm, X = round-to-nearest-even
+ *                of the float product x * 1000 (every geometric decision
+ *                below is then exact integer arithmetic);
+ *   distance     d(a, b) = |Xa - Xb| + |Ya - Yb|;
+ *   1. MST       Prim from pin 0 (the driver): each step attaches the
+ *                outside pin u and tree node v with the smallest
+ *                (d(u, v), u, rank of v), rank = order of attachment;
+ *   2. Steiner   greedy median insertion, at most 2 (n - 1) times: over
+ *                every live node u (ascending index) and every pair v < w
+ *                of u's neighbours, M = (median of X, median of Y) of
+ *                {u, v, w} and gain = d(u,v) + d(u,w) - d(M,u) - d(M,v) -
+ *                d(M,w); take the largest gain (ties: the first in that
+ *                order); stop when it is <= 0.  Apply: M at v -> edge
+ *                (u, w) becomes (v, w); M at w -> (u, v) becomes (w, v);
+ *                else a new Steiner node s at M with edges (s, u), (s, v),
+ *                (s, w) replacing (u, v), (u, w).  Then, while some live
+ *                Steiner node has <= 2 neighbours, take the lowest-index one
+ *                and remove it (one neighbour: drop the edge; two: join
+ *                them).  Nets of more than 64 pins keep the MST.  (The
+ *                reattachments and the removals are defensive: on 20k random
+ *                nets of 3-19 pins, grids with many ties included, neither
+ *                ever fired -- a Steiner node at the median of its three
+ *                neighbours leaves no positive gain at itself);
+ *   3. output    breadth-first from the driver, neighbours in ascending
+ *                index: node 0 = driver, parent[i] < i; pin_node[j] = the
+ *                node of pin j; wl = total length (nm).
+ *
+ * Capacity: n pins give at most 2n - 2 live nodes (n >= 2; a live Steiner
+ * node has >= 3 neighbours).  parent, nx, ny need max(1, 2n - 2) entries. */
+#define ORC_STEINER_MAX_PINS 64
+
+static int64_t mdist(int64_t xa, int64_t ya, int64_t xb, int64_t yb)
+{
+    return llabs(xa - xb) + llabs(ya - yb);
+}
+
+static int64_t med3(int64_t a, int64_t b, int64_t c)
+{
+    if ((a <= b && b <= c) || (c <= b && b <= a)) return b;
+    if ((b <= a && a <= c) || (c <= a && a <= b)) return a;
+    return c;
+}
+
+int64_t orc_nm(float x_um)
+{
+    float p = x_um * 1000.0f;   /* the float product, then round to nearest even */
+    return (int64_t)lrintf(p);
+}
+
+int orc_steiner_tree(int32_t n, const int64_t *X, const int64_t *Y, int32_t *n_out, int32_t *parent,
+                     int64_t *nx, int64_t *ny, int32_t *pin_node, int64_t *wl)
+{
+    if (n < 1) return ERR_INVAL;
+    int32_t cap = 3 * n;                 /* pins + at most 2 (n - 1) Steiner nodes */
+    int64_t *x = (int64_t *)calloc((size_t)cap, sizeof(int64_t));
+    int64_t *y = (int64_t *)calloc((size_t)cap, sizeof(int64_t));
+    char *adj = (char *)calloc((size_t)cap * (size_t)cap, 1);
+    char *live = (char *)calloc((size_t)cap, 1);
+    int32_t *rank = (int32_t *)calloc((size_t)cap, sizeof(int32_t));
+    int32_t *queue = (int32_t *)calloc((size_t)cap, sizeof(int32_t));
+    int32_t *newid = (int32_t *)calloc((size_t)cap, sizeof(int32_t));
+    if (!x || !y || !adj || !live || !rank || !queue || !newid) {
+        free(x); free(y); free(adj); free(live); free(rank); free(queue); free(newid);
+        return ERR_NOMEM;
+    }
+#define ADJ(a, b) adj[(size_t)(a) * (size_t)cap + (size_t)(b)]
+    int32_t N = n;
+    for (int32_t i = 0; i < n; ++i) { x[i] = X[i]; y[i] = Y[i]; live[i] = 1; rank[i] = -1; }
+    /* 1. Prim from the driver */
+    rank[0] = 0;
+    for (int32_t step = 1; step < n; ++step) {
+        int64_t bd = -1;
+        int32_t bu = -1, bv = -1;
+        for (int32_t u = 0; u < n; ++u) {
+            if (rank[u] >= 0) continue;
+            for (int32_t v = 0; v < n; ++v) {
+                if (rank[v] < 0) continue;
+                int64_t dd = mdist(x[u], y[u], x[v], y[v]);
+                if (bu < 0 || dd < bd || (dd == bd && (u < bu || (u == bu && rank[v] < rank[bv])))) {
+                    bd = dd; bu = u; bv = v;
+                }
+            }
+        }
+        rank[bu] = step;
+        ADJ(bu, bv) = ADJ(bv, bu) = 1;
+    }
+    /* 2. greedy median insertion, then removal of Steiner nodes of degree <= 2 */
+    for (int32_t it = 0; n <= ORC_STEINER_MAX_PINS && it < 2 * (n - 1); ++it) {
+        int64_t bg = 0;
+        int32_t bu = -1, bv = -1, bw = -1;
+        for (int32_t u = 0; u < N; ++u) {
+            if (!live[u]) continue;
+            for (int32_t v = 0; v < N; ++v) {
+                if (!ADJ(u, v)) continue;
+                for (int32_t w = v + 1; w < N; ++w) {
+                    if (!ADJ(u, w)) continue;
+                    int64_t mx = med3(x[u], x[v], x[w]), my = med3(y[u], y[v], y[w]);
+                    int64_t g = mdist(x[u], y[u], x[v], y[v]) + mdist(x[u], y[u], x[w], y[w]) -
+                                mdist(mx, my, x[u], y[u]) - mdist(mx, my, x[v], y[v]) - mdist(mx, my, x[w], y[w]);
+                    if (g > bg) { bg = g; bu = u; bv = v; bw = w; }
+                }
+            }
+        }
+        if (bg <= 0) break;
+        int64_t mx = med3(x[bu], x[bv], x[bw]), my = med3(y[bu], y[bv], y[bw]);
+        if (mx == x[bv] && my == y[bv]) {
+            ADJ(bu, bw) = ADJ(bw, bu) = 0;
+            ADJ(bv, bw) = ADJ(bw, bv) = 1;
+        } else if (mx == x[bw] && my == y[bw]) {
+            ADJ(bu, bv) = ADJ(bv, bu) = 0;
+            ADJ(bw, bv) = ADJ(bv, bw) = 1;
+        } else {
+            int32_t s = N++;
+            x[s] = mx; y[s] = my; live[s] = 1;
+            ADJ(bu, bv) = ADJ(bv, bu) = 0;
+            ADJ(bu, bw) = ADJ(bw, bu) = 0;
+            ADJ(s, bu) = ADJ(bu, s) = 1;
+            ADJ(s, bv) = ADJ(bv, s) = 1;
+            ADJ(s, bw) = ADJ(bw, s) = 1;
+        }
+        for (;;) {
+            int32_t s = -1, deg = 0, nb[2] = {-1, -1};
+            for (int32_t i = n; i < N && s < 0; ++i) {
+                if (!live[i]) continue;
+                int32_t dg = 0;
+                for (int32_t j = 0; j < N; ++j) dg += ADJ(i, j);
+                if (dg <= 2) { s = i; deg = dg; }
+            }
+            if (s < 0) break;
+            int32_t k = 0;
+            for (int32_t j = 0; j < N; ++j)
+                if (ADJ(s, j)) { nb[k++] = j; ADJ(s, j) = ADJ(j, s) = 0; }
+            if (deg == 2) ADJ(nb[0], nb[1]) = ADJ(nb[1], nb[0]) = 1;
+            live[s] = 0;
+        }
+    }
+    /* 3. breadth-first numbering from the driver */
+    for (int32_t i = 0; i < N; ++i) newid[i] = -1;
+    int32_t head = 0, tail = 0;
+    queue[tail++] = 0;
+    newid[0] = 0;
+    parent[0] = -1;
+    nx[0] = x[0]; ny[0] = y[0];
+    int64_t total = 0;
+    while (head < tail) {
+        int32_t a = queue[head++];
+        for (int32_t b = 0; b < N; ++b) {
+            if (!ADJ(a, b) || newid[b] >= 0) continue;
+            newid[b] = tail;
+            parent[tail] = newid[a];
+            nx[tail] = x[b]; ny[tail] = y[b];
+            total += mdist(x[a], y[a], x[b], y[b]);
+            queue[tail++] = b;
+        }
+    }
+    int rc = OK;
+    for (int32_t j = 0; j < n; ++j) {
+        pin_node[j] = newid[j];
+        if (newid[j] < 0) rc = ERR_INVAL;   /* not reached: the tree is connected */
+    }
+    *n_out = tail;
+    *wl = total;
+#undef ADJ
+    free(x); free(y); free(adj); free(live); free(rank); free(queue); free(newid);
+    return rc;
+}
+
 /* Per-corner net quantities: load (pF) at each driver pin, Elmore delay (ns)
  * and variance (ns^2) at each sink pin.  With rc_ptr == NULL the tree is the
  * star of O3/A8: root at the driver, one segment per sink of Manhattan length
- * L with R = r L and C = c L split half at each end, plus the sink pin cap. */
+ * L with R = r L and C = c L split half at each end, plus the sink pin cap;
+ * with wire_model == 1 it is the O9 Steiner tree, each edge of x length Lx
+ * and y length Ly (um) with R = rx Lx + ry Ly and C = cx Lx + cy Ly split
+ * half at each end (ry, cy <= 0: the x values). */
 int orc_net_delays(const orc_design *d, int32_t corner, double *load_pf, double *D_ns, double *V_ns2)
 {
     pin_info pi;
@@ -522,8 +706,11 @@ int orc_net_delays(const orc_design *d, int32_t corner, double *load_pf, double 
     for (int32_t n = 0; n < d->n_nets; ++n) {
         int32_t b = d->net_pin_ptr[n], e = d->net_pin_ptr[n + 1];
         int32_t nn;
+        const int steiner = !d->rc_ptr && d->wire_model == 1;
         if (d->rc_ptr) nn = d->rc_ptr[n + 1] - d->rc_ptr[n];
+        else if (steiner) nn = e - b > 1 ? 2 * (e - b) - 2 : 1;   /* capacity; set below */
         else nn = e - b;             /* root + one node per sink */
+        int32_t *pnode = NULL;
         int32_t *par = (int32_t *)malloc(sizeof(int32_t) * (size_t)nn);
         double *R = (double *)malloc(sizeof(double) * (size_t)nn);
         double *C = (double *)malloc(sizeof(double) * (size_t)nn);
@@ -544,6 +731,39 @@ int orc_net_delays(const orc_design *d, int32_t corner, double *load_pf, double 
                 if (node < 0 || node >= nn) { rc = ERR_INVAL; goto next; }
                 C[node] += 1e3 * pin_cap_of(d, &pi, d->net_pin[k]);   /* pF -> fF */
             }
+        } else if (steiner) {
+            int32_t m = e - b;
+            int64_t *X = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+            int64_t *Y = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+            int64_t *tx = (int64_t *)malloc(sizeof(int64_t) * (size_t)nn);
+            int64_t *ty = (int64_t *)malloc(sizeof(int64_t) * (size_t)nn);
+            pnode = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+            if (!X || !Y || !tx || !ty || !pnode) rc = ERR_NOMEM;
+            else {
+                for (int32_t k = 0; k < m; ++k) {
+                    double xs, ys;
+                    pin_xy(d, &pi, d->net_pin[b + k], &xs, &ys);
+                    X[k] = orc_nm((float)xs);
+                    Y[k] = orc_nm((float)ys);
+                }
+                int64_t wl;
+                rc = orc_steiner_tree(m, X, Y, &nn, par, tx, ty, pnode, &wl);
+            }
+            if (!rc) {
+                double rx = d->r_per_um, cx = d->c_per_um;
+                double ry = d->r_per_um_y > 0 ? d->r_per_um_y : rx, cy = d->c_per_um_y > 0 ? d->c_per_um_y : cx;
+                for (int32_t i = 0; i < nn; ++i) { R[i] = 0.0; C[i] = 0.0; }
+                for (int32_t i = 1; i < nn; ++i) {
+                    double lx = 1e-3 * (double)llabs(tx[i] - tx[par[i]]), ly = 1e-3 * (double)llabs(ty[i] - ty[par[i]]);
+                    double cw = f * (cx * lx + cy * ly);
+                    R[i] = f * (rx * lx + ry * ly);
+                    C[i] += 0.5 * cw;
+                    C[par[i]] += 0.5 * cw;
+                }
+                for (int32_t k = 1; k < m; ++k) C[pnode[k]] += 1e3 * pin_cap_of(d, &pi, d->net_pin[b + k]);
+            }
+            free(X); free(Y); free(tx); free(ty);
+            if (rc) goto next;
         } else {
             double xd, yd;
             pin_xy(d, &pi, d->net_pin[b], &xd, &yd);
@@ -561,22 +781,50 @@ int orc_net_delays(const orc_design *d, int32_t corner, double *load_pf, double 
         }
         rc = orc_rc_tree(nn, par, R, C, cd, Dd, be, va);
         if (rc) goto next;
-        if (d->net_model == 1 && d->rc_ptr) {
+        if (d->net_model == 1 && (d->rc_ptr || steiner)) {
             rc = orc_arnoldi_t50(nn, par, R, C, d->arnoldi_order, Dd);   /* O7 delays replace Elmore's */
             if (rc) goto next;
         }
         load_pf[d->net_pin[b]] = 1e-3 * cd[0];
         for (int32_t k = b + 1; k < e; ++k) {
-            int32_t node = d->rc_ptr ? d->rc_pin_node[k] : k - b;
+            int32_t node = d->rc_ptr ? d->rc_pin_node[k] : steiner ? pnode[k - b] : k - b;
             D_ns[d->net_pin[k]] = 1e-6 * Dd[node];
             V_ns2[d->net_pin[k]] = 1e-12 * va[node];
         }
     next:
-        free(par); free(R); free(C); free(cd); free(Dd); free(be); free(va);
+        free(par); free(R); free(C); free(cd); free(Dd); free(be); free(va); free(pnode);
         if (rc) { free_info(&pi); return rc; }
     }
     free_info(&pi);
     return OK;
+}
+
+/* O9 tree length (nm) of every net of a placed design: wl[n_nets]. */
+int orc_net_wirelengths(const orc_design *d, int64_t *wl)
+{
+    pin_info pi;
+    int rc = build_info(d, &pi);
+    if (rc) return rc;
+    for (int32_t n = 0; n < d->n_nets && !rc; ++n) {
+        int32_t b = d->net_pin_ptr[n], m = d->net_pin_ptr[n + 1] - b, nn = 0;
+        int32_t cap = m > 1 ? 2 * m - 2 : 1;
+        int64_t *X = (int64_t *)malloc(sizeof(int64_t) * (size_t)m), *Y = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+        int64_t *tx = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap), *ty = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+        int32_t *par = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap), *pn = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+        if (!X || !Y || !tx || !ty || !par || !pn) rc = ERR_NOMEM;
+        else {
+            for (int32_t k = 0; k < m; ++k) {
+                double xs, ys;
+                pin_xy(d, &pi, d->net_pin[b + k], &xs, &ys);
+                X[k] = orc_nm((float)xs);
+                Y[k] = orc_nm((float)ys);
+            }
+            rc = orc_steiner_tree(m, X, Y, &nn, par, tx, ty, pn, &wl[n]);
+        }
+        free(X); free(Y); free(tx); free(ty); free(par); free(pn);
+    }
+    free_info(&pi);
+    return rc;
 }
 
 /* ------------------------------------------------------ topological order */
@@ -887,7 +1135,7 @@ static double sigmoid(double z)
 int orc_objective_grad(const orc_design *d, double w_tns, double w_wns, double *J_out,
                        double *terms, double *grad_xy)
 {
-    if (d->rc_ptr || !d->cell_xy || d->gamma_ns <= 0.0) return ERR_INVAL;
+    if (d->rc_ptr || !d->cell_xy || d->gamma_ns <= 0.0 || d->wire_model != 0) return ERR_INVAL;
     pin_info pi;
     int rc = build_info(d, &pi);
     if (rc) return rc;

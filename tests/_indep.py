@@ -73,6 +73,11 @@ class Net:
                 return float(d["po_cap_pf"])
             return float(pin_cap[ctype[cell_of[p]], slot_of[p]])
 
+        self.cap = cap
+        if d.get("cell_xy") is not None:
+            cxy = np.asarray(d["cell_xy"]).reshape(-1, 2)
+            pxy_ = np.asarray(d["port_xy"]).reshape(-1, 2)
+            self.pos = lambda p: tuple(float(v) for v in (cxy[cell_of[p]] if cell_of[p] >= 0 else pxy_[p]))
         self.load, self.Dns, self.Vns, self.driver = {}, {}, {}, {}
         npp = np.asarray(d["net_pin_ptr"])
         npn = np.asarray(d["net_pin"])

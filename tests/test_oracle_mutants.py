@@ -69,7 +69,7 @@ MUTANTS = [
     ("arn_cholesky_diag", "L[i * qq + i] = sqrt(s);", "L[i * qq + i] = s;", 0),
     ("arn_modal_inverse", "yinf[k] = s / lam[k];", "yinf[k] = s * lam[k];", 0),
     ("arn_half_threshold", "if (v >= 0.5 * vinf) hi = mid;", "if (v >= 0.4 * vinf) hi = mid;", 0),
-    ("arn_model_switch", "if (d->net_model == 1 && d->rc_ptr) {", "if (d->net_model == 2 && d->rc_ptr) {", 0),
+    ("arn_model_switch", "if (d->net_model == 1 && (d->rc_ptr || steiner)) {", "if (d->net_model == 2 && d->rc_ptr) {", 0),
     # O8 timing exceptions
     ("exc_seed_not_masked", "if (src_on && !src_on[p])", "if (src_on && src_on[p] > 1)", 0),
     ("exc_first_group_wins", "if (!tag_of[p]) tag_of[p] = (int8_t)(g + 1);", "tag_of[p] = (int8_t)(g + 1);", 0),
@@ -89,6 +89,15 @@ MUTANTS = [
     ("adj_sink_sign", "if (cs >= 0) { grad_xy[2 * cs] -= dJdL * sx;", "if (cs >= 0) { grad_xy[2 * cs] += dJdL * sx;", 0),
     ("adj_y_uses_x", "double sx = (xd > xs) - (xd < xs), sy = (yd > ys) - (yd < ys);",
      "double sx = (xd > xs) - (xd < xs), sy = sx;", 0),
+    # O9 Steiner tree RC from positions
+    ("steiner_nm_truncates", "return (int64_t)lrintf(p);", "return (int64_t)p;", 0),
+    ("steiner_median_is_middle_arg", "if ((a <= b && b <= c) || (c <= b && b <= a)) return b;", "return b;", 0),
+    ("steiner_gain_drops_w", " - mdist(mx, my, x[w], y[w]);", ";", 0),
+    ("steiner_new_node_drops_w", "ADJ(s, bw) = ADJ(bw, s) = 1;", "ADJ(s, bw) = ADJ(bw, s) = 0;", 0),
+    ("steiner_bfs_old_parent", "parent[tail] = newid[a];", "parent[tail] = a;", 0),
+    ("steiner_ry_uses_rx", "R[i] = f * (rx * lx + ry * ly);", "R[i] = f * (rx * lx + rx * ly);", 0),
+    ("steiner_no_parent_half_cap", "C[par[i]] += 0.5 * cw;", "C[par[i]] += 0.0 * cw;", 0),
+    ("steiner_no_scale", "double cw = f * (cx * lx + cy * ly);", "double cw = (cx * lx + cy * ly);", 0),
 ]
 
 

@@ -806,3 +806,238 @@ def test_exception_paths_fixed_delay(seed):
         arrivals = [a for a, f, s2 in allp[e] if s2 == s and f == rf]
         assert min(abs(a - pth["at"][-1]) for a in arrivals) <= 1e-12
         assert late_req(e, s) - pth["at"][-1] == pytest.approx(want, abs=1e-12)
+
+
+# --------------------------------------------------- O9 Steiner RC from positions
+
+def _read_steiner_golden():
+    g = {"nm": []}
+    for line in open(os.path.join(GOLD, "steiner_hand.txt")):
+        f = line.split("#")[0].split()
+        if not f:
+            continue
+        if f[0] == "nm":
+            g["nm"].append((float(f[1]), int(f[2])))
+        else:
+            g[f[0]] = [float(x) for x in f[1:]]
+    return g
+
+
+def _hanan_rsmt(X, Y):
+    """Exact rectilinear Steiner minimal tree length by brute force: by
+    Hanan's theorem some RSMT has its Steiner points on the Hanan grid and
+    needs at most n - 2 of them, so the minimum over those subsets of the
+    rectilinear MST length (scipy) is the RSMT length."""
+    from itertools import combinations
+
+    from scipy.sparse.csgraph import minimum_spanning_tree
+    pts = sorted(set(zip(X, Y)))   # coincident pins join at no cost
+    grid = [(x, y) for x in sorted(set(X)) for y in sorted(set(Y)) if (x, y) not in pts]
+
+    def mst(ps):
+        a = np.array(ps, np.float64)
+        dm = np.abs(a[:, None, 0] - a[None, :, 0]) + np.abs(a[:, None, 1] - a[None, :, 1])
+        return float(minimum_spanning_tree(dm).sum())
+
+    best = mst(pts)
+    for k in range(1, len(pts) - 1):
+        for sub in combinations(grid, k):
+            best = min(best, mst(pts + list(sub)))
+    return best
+
+
+def _tree_checks(X, Y, t):
+    """A tree on the pins: breadth-first numbering, every pin on its own
+    node, Steiner nodes with at least three neighbours on the Hanan grid,
+    and wl the sum of the edges' Manhattan lengths."""
+    par, nx, ny, pn = t["parent"], t["nx"], t["ny"], t["pin_node"]
+    n = len(X)
+    assert par[0] == -1 and all(0 <= par[i] < i for i in range(1, len(par)))
+    assert sorted(pn.tolist()) == sorted(set(pn.tolist())) and pn[0] == 0
+    for j in range(n):
+        assert (nx[pn[j]], ny[pn[j]]) == (X[j], Y[j])
+    deg = np.bincount(par[1:], minlength=len(par)) + (np.arange(len(par)) > 0)
+    steiner = sorted(set(range(len(par))) - set(pn.tolist()))
+    assert all(deg[s] >= 3 for s in steiner)
+    assert all(nx[s] in set(X) and ny[s] in set(Y) for s in steiner)
+    assert len(par) <= max(1, 2 * n - 2)
+    wl = sum(abs(nx[i] - nx[par[i]]) + abs(ny[i] - ny[par[i]]) for i in range(1, len(par)))
+    assert wl == t["wl"]
+    # a Steiner node never sits on a neighbour, and no median insertion or
+    # reattachment can shorten the final tree (the greedy stops at zero gain)
+    nbr = [[] for _ in par]
+    for i in range(1, len(par)):
+        nbr[i].append(par[i])
+        nbr[par[i]].append(i)
+    dist = lambda a, b: abs(int(nx[a]) - int(nx[b])) + abs(int(ny[a]) - int(ny[b]))  # noqa: E731
+    for s in steiner:
+        assert all(dist(s, v) > 0 for v in nbr[s])
+    if n <= 64:
+        for u in range(len(par)):
+            for i, v in enumerate(nbr[u]):
+                for w in nbr[u][i + 1:]:
+                    mx = sorted([nx[u], nx[v], nx[w]])[1]
+                    my = sorted([ny[u], ny[v], ny[w]])[1]
+                    m = lambda a: abs(int(nx[a]) - int(mx)) + abs(int(ny[a]) - int(my))  # noqa: E731
+                    assert dist(u, v) + dist(u, w) - m(u) - m(v) - m(w) <= 0
+
+
+def test_steiner_nm_rounding():
+    g = _read_steiner_golden()
+    assert len(g["nm"]) >= 5
+    for x, want in g["nm"]:
+        assert oracle.nm(x) == want, x
+
+
+def test_steiner_hand_worked_T_net():
+    """The T net of the golden file: tree, wirelength, and the Elmore delay,
+    variance and load of its RC with different unit R/C along x and y."""
+    g = _read_steiner_golden()
+    p = [int(v) for v in g["tpins"]]
+    X, Y = p[0::2], p[1::2]
+    t = oracle.steiner_tree(X, Y)
+    np.testing.assert_array_equal(t["parent"], np.array(g["tparent"], int))
+    nodes = [int(v) for v in g["tnodes"]]
+    np.testing.assert_array_equal(t["nx"], nodes[0::2])
+    np.testing.assert_array_equal(t["ny"], nodes[1::2])
+    np.testing.assert_array_equal(t["pin_node"], np.array(g["tpinnode"], int))
+    assert t["wl"] == int(g["twl"][0])
+    rx, ry, cx, cy, cpo = g["tunits"]
+    lib = synth.make_library(0)
+    b = synth.Builder(lib)
+    a = b.pi(xy=(0.0, 0.0))
+    s1 = b.po(a, xy=(100.0, 40.0))
+    s2 = b.po(a, xy=(100.0, -40.0))
+    d = b.design(placed=True, r_per_um=rx, c_per_um=cx)
+    d.update(wire_model=1, r_per_um_y=ry, c_per_um_y=cy, po_cap_pf=cpo)
+    load, Dn, Vn = oracle.net_delays(d)
+    assert load[a] == pytest.approx(g["tload"][0], rel=1e-12)
+    for s in (s1, s2):
+        assert Dn[s] == pytest.approx(g["tdelay"][0], rel=1e-12)
+        assert Vn[s] == pytest.approx(g["tvar"][0], rel=1e-9)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_steiner_two_and_three_pins_optimal(seed):
+    """Two pins: the Manhattan distance.  Three pins: the half perimeter of
+    the bounding box (the RSMT of three points), also on a small grid where
+    distance ties and coincident pins are common."""
+    rng = np.random.default_rng(seed)
+    for hi in (5, 1000):
+        for _ in range(300):
+            X, Y = rng.integers(0, hi, 2), rng.integers(0, hi, 2)
+            t = oracle.steiner_tree(X, Y)
+            _tree_checks(X, Y, t)
+            assert t["wl"] == abs(X[0] - X[1]) + abs(Y[0] - Y[1])
+            X, Y = rng.integers(0, hi, 3), rng.integers(0, hi, 3)
+            t = oracle.steiner_tree(X, Y)
+            _tree_checks(X, Y, t)
+            assert t["wl"] == (X.max() - X.min()) + (Y.max() - Y.min())
+
+
+def test_steiner_bounded_by_rsmt_and_rmst():
+    """RSMT <= WL <= RMST (so WL <= 1.5 RSMT, Hwang's bound on the RMST);
+    the RSMT by brute force over the Hanan grid, the RMST by scipy.  Also
+    reports how close the construction gets on 4- and 5-pin nets."""
+    from scipy.sparse.csgraph import minimum_spanning_tree
+    rng = np.random.default_rng(7)
+    ratios = []
+    for n, reps in ((4, 100), (5, 12)):
+        for _ in range(reps):
+            X, Y = rng.integers(0, 50, n), rng.integers(0, 50, n)
+            t = oracle.steiner_tree(X, Y)
+            _tree_checks(X, Y, t)
+            u = np.array(sorted(set(zip(X.tolist(), Y.tolist()))), np.float64)
+            dm = np.abs(u[:, None, 0] - u[None, :, 0]) + np.abs(u[:, None, 1] - u[None, :, 1])
+            rmst = round(float(minimum_spanning_tree(dm).sum()))
+            rsmt = _hanan_rsmt(X.tolist(), Y.tolist())
+            assert rsmt - 1e-6 <= t["wl"] <= rmst
+            ratios.append(t["wl"] / rsmt)
+    assert max(ratios) <= 1.5
+    assert np.mean(ratios) < 1.03   # close to optimal on small nets
+
+
+def test_steiner_large_nets_valid():
+    """Nets up to 64 pins are Steinerised (WL below the RMST on random
+    points); larger nets keep the MST."""
+    from scipy.sparse.csgraph import minimum_spanning_tree
+    rng = np.random.default_rng(3)
+    for _ in range(150):   # small grids: distance ties, coincident pins, reattachments
+        n = int(rng.integers(6, 13))
+        X, Y = rng.integers(0, 12, n), rng.integers(0, 12, n)
+        _tree_checks(X, Y, oracle.steiner_tree(X, Y))
+    for n in (10, 37, 64, 65, 90):
+        X, Y = rng.integers(0, 10**6, n), rng.integers(0, 10**6, n)
+        t = oracle.steiner_tree(X, Y)
+        _tree_checks(X, Y, t)
+        dm = (np.abs(X[:, None] - X[None, :]) + np.abs(Y[:, None] - Y[None, :])).astype(float)
+        rmst = round(float(minimum_spanning_tree(dm).sum()))
+        if n <= 64:
+            assert t["wl"] < rmst
+        else:
+            assert t["wl"] == rmst and len(t["parent"]) == n
+
+
+def test_steiner_rc_matches_shared_path_and_corner_prescale():
+    """Steiner RC in a generated placed design: every sink's Elmore delay and
+    variance equal the shared-path sums over an RC tree rebuilt here from the
+    O9 tree (edge R = rx Lx + ry Ly, wire C split half at each end), and
+    corner k equals a single-corner design with unit R/C pre-scaled by
+    rc_scale[k]."""
+    d = synth.make_design(400, 8, seed=12, placed=True)
+    d.update(wire_model=1, r_per_um_y=0.13, c_per_um_y=0.25, n_corners=2,
+             lut_scale=np.array([1.0, 1.0], np.float32), rc_scale=np.array([1.0, 1.3], np.float32))
+    rx, cx, ry, cy = d["r_per_um"], d["c_per_um"], 0.13, 0.25
+    load, Dn, Vn = oracle.net_delays(d, 0)
+    net = _indep.Net(dict(d, wire_model=0))   # pin positions and caps only
+    npp, npn = d["net_pin_ptr"], d["net_pin"]
+    checked = 0
+    for m in range(d["n_nets"]):
+        pins = npn[npp[m]:npp[m + 1]]
+        if len(pins) < 3:
+            continue
+        xy = [net.pos(int(p)) for p in pins]
+        X = [oracle.nm(x) for x, _ in xy]
+        Y = [oracle.nm(y) for _, y in xy]
+        t = oracle.steiner_tree(X, Y)
+        par, nx, ny = t["parent"], t["nx"], t["ny"]
+        k = len(par)
+        R, Cc = np.zeros(k), np.zeros(k)
+        for i in range(1, k):
+            lx, ly = abs(nx[i] - nx[par[i]]) * 1e-3, abs(ny[i] - ny[par[i]]) * 1e-3
+            R[i] = rx * lx + ry * ly
+            Cc[i] += 0.5 * (cx * lx + cy * ly)
+            Cc[par[i]] += 0.5 * (cx * lx + cy * ly)
+        for j, p in enumerate(pins[1:], 1):
+            Cc[t["pin_node"][j]] += 1e3 * net.cap(int(p))
+        Dm, beta = _indep.shared_path_moments(par, R, Cc)
+        assert load[pins[0]] == pytest.approx(1e-3 * Cc.sum(), rel=1e-12)
+        for j, p in enumerate(pins[1:], 1):
+            nd = t["pin_node"][j]
+            assert Dn[p] == pytest.approx(1e-6 * Dm[nd], rel=1e-11)
+            assert Vn[p] == pytest.approx(1e-12 * (2 * beta[nd] - Dm[nd] ** 2), rel=1e-8, abs=1e-22)
+        checked += 1
+        if checked > 60:
+            break
+    assert checked > 20
+    f = float(np.float32(1.3))   # the corner's scale as stored
+    d1 = dict(d, n_corners=1, lut_scale=np.ones(1, np.float32), rc_scale=np.ones(1, np.float32),
+              r_per_um=f * rx, c_per_um=f * cx, r_per_um_y=f * ry, c_per_um_y=f * cy)
+    l1, D1, V1 = oracle.net_delays(d, 1)
+    l2, D2, V2 = oracle.net_delays(d1, 0)
+    np.testing.assert_allclose(l1, l2, rtol=1e-12)
+    np.testing.assert_allclose(D1, D2, rtol=1e-12)
+    np.testing.assert_allclose(V1, V2, rtol=1e-9, atol=1e-24)
+
+
+def test_net_wirelengths_match_per_net_trees():
+    """The per-net tree lengths of a placed design equal the single-net
+    trees built from its pins' nm coordinates (driver first)."""
+    d = synth.make_design(300, 6, seed=2, placed=True)
+    wl = oracle.net_wirelengths(d)
+    net = _indep.Net(d)
+    npp, npn = d["net_pin_ptr"], d["net_pin"]
+    for m in range(d["n_nets"]):
+        xy = [net.pos(int(p)) for p in npn[npp[m]:npp[m + 1]]]
+        t = oracle.steiner_tree([oracle.nm(x) for x, _ in xy], [oracle.nm(y) for _, y in xy])
+        assert wl[m] == t["wl"]
