@@ -251,7 +251,7 @@ int orc_arnoldi_t50(int32_t n, const int32_t *parent, const double *R, const dou
 {
     if (n <= 0 || parent[0] != -1 || q_in < 1) return ERR_INVAL;
     for (int32_t i = 1; i < n; ++i)
-        if (parent[i] < 0 || parent[i] >= i) return ERR_INVAL;
+        if (parent[i] < 0 || parent[i] >= i || !(R[i] > 0.0)) return ERR_INVAL;   /* G needs every R > 0 */
     t50[0] = 0.0;
     const int32_t m = n - 1;
     if (m == 0) return OK;
@@ -546,8 +546,10 @@ static void pin_xy(const orc_design *d, const pin_info *pi, int32_t p, double *x
  *                ever fired -- a Steiner node at the median of its three
  *                neighbours leaves no positive gain at itself);
  *   3. output    breadth-first from the driver, neighbours in ascending
- *                index: node 0 = driver, parent[i] < i; pin_node[j] = the
- *                node of pin j; wl = total length (nm).
+ *                index: node 0 = driver, parent[i] < i; a node at the same
+ *                point as the node it is reached from shares its RC node (no
+ *                zero-length edges); pin_node[j] = the node of pin j; wl =
+ *                total length (nm).
  *
  * Capacity: n pins give at most 2n - 2 live nodes (n >= 2; a live Steiner
  * node has >= 3 neighbours).  parent, nx, ny need max(1, 2n - 2) entries. */
@@ -666,15 +668,21 @@ int orc_steiner_tree(int32_t n, const int64_t *X, const int64_t *Y, int32_t *n_o
     parent[0] = -1;
     nx[0] = x[0]; ny[0] = y[0];
     int64_t total = 0;
+    int32_t nodes = 1;
     while (head < tail) {
         int32_t a = queue[head++];
         for (int32_t b = 0; b < N; ++b) {
             if (!ADJ(a, b) || newid[b] >= 0) continue;
-            newid[b] = tail;
-            parent[tail] = newid[a];
-            nx[tail] = x[b]; ny[tail] = y[b];
-            total += mdist(x[a], y[a], x[b], y[b]);
             queue[tail++] = b;
+            if (x[b] == x[a] && y[b] == y[a]) {   /* same point: the same RC node */
+                newid[b] = newid[a];
+                continue;
+            }
+            newid[b] = nodes;
+            parent[nodes] = newid[a];
+            nx[nodes] = x[b]; ny[nodes] = y[b];
+            total += mdist(x[a], y[a], x[b], y[b]);
+            ++nodes;
         }
     }
     int rc = OK;
@@ -682,7 +690,7 @@ int orc_steiner_tree(int32_t n, const int64_t *X, const int64_t *Y, int32_t *n_o
         pin_node[j] = newid[j];
         if (newid[j] < 0) rc = ERR_INVAL;   /* not reached: the tree is connected */
     }
-    *n_out = tail;
+    *n_out = nodes;
     *wl = total;
 #undef ADJ
     free(x); free(y); free(adj); free(live); free(rank); free(queue); free(newid);

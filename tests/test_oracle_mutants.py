@@ -94,7 +94,8 @@ MUTANTS = [
     ("steiner_median_is_middle_arg", "if ((a <= b && b <= c) || (c <= b && b <= a)) return b;", "return b;", 0),
     ("steiner_gain_drops_w", " - mdist(mx, my, x[w], y[w]);", ";", 0),
     ("steiner_new_node_drops_w", "ADJ(s, bw) = ADJ(bw, s) = 1;", "ADJ(s, bw) = ADJ(bw, s) = 0;", 0),
-    ("steiner_bfs_old_parent", "parent[tail] = newid[a];", "parent[tail] = a;", 0),
+    ("steiner_bfs_old_parent", "parent[nodes] = newid[a];", "parent[nodes] = a;", 0),
+    ("steiner_no_merge_same_point", "if (x[b] == x[a] && y[b] == y[a]) {", "if (0) {", 0),
     ("steiner_ry_uses_rx", "R[i] = f * (rx * lx + ry * ly);", "R[i] = f * (rx * lx + rx * ly);", 0),
     ("steiner_no_parent_half_cap", "C[par[i]] += 0.5 * cw;", "C[par[i]] += 0.0 * cw;", 0),
     ("steiner_no_scale", "double cw = f * (cx * lx + cy * ly);", "double cw = (cx * lx + cy * ly);", 0),

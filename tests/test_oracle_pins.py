@@ -853,9 +853,12 @@ def _tree_checks(X, Y, t):
     par, nx, ny, pn = t["parent"], t["nx"], t["ny"], t["pin_node"]
     n = len(X)
     assert par[0] == -1 and all(0 <= par[i] < i for i in range(1, len(par)))
-    assert sorted(pn.tolist()) == sorted(set(pn.tolist())) and pn[0] == 0
+    assert pn[0] == 0
     for j in range(n):
         assert (nx[pn[j]], ny[pn[j]]) == (X[j], Y[j])
+    for i in range(n):   # pins share a node exactly when they sit at the same point
+        for j in range(i + 1, n):
+            assert (pn[i] == pn[j]) == ((X[i], Y[i]) == (X[j], Y[j]))
     deg = np.bincount(par[1:], minlength=len(par)) + (np.arange(len(par)) > 0)
     steiner = sorted(set(range(len(par))) - set(pn.tolist()))
     assert all(deg[s] >= 3 for s in steiner)
@@ -870,8 +873,7 @@ def _tree_checks(X, Y, t):
         nbr[i].append(par[i])
         nbr[par[i]].append(i)
     dist = lambda a, b: abs(int(nx[a]) - int(nx[b])) + abs(int(ny[a]) - int(ny[b]))  # noqa: E731
-    for s in steiner:
-        assert all(dist(s, v) > 0 for v in nbr[s])
+    assert all(dist(i, par[i]) > 0 for i in range(1, len(par)))   # no zero-length edge
     if n <= 64:
         for u in range(len(par)):
             for i, v in enumerate(nbr[u]):
