@@ -37,6 +37,9 @@ WORKLOADS = {
     "scale": "1M cells, depth 150, RC trees of 2-10 nodes, 1 corner, clock period at the 90th percentile "
              "endpoint requirement (seed 0)",
     "mid": "200k cells, depth 150, RC trees of 2-10 nodes, 1 corner (profiler-sized; seed 0)",
+    "steiner": "1M cells, depth 150, placed in a 1000 um die, Steiner-tree RC rebuilt from the positions at every "
+               "update, 1 corner (seed 0)",
+    "steiner_mid": "200k cells, depth 150, placed, Steiner-tree RC from positions (profiler-sized; seed 0)",
     "batch": "64 designs, cells log-uniform in 5k-500k, depth 150, 4 corners, one batched context against 256 "
              "sequential plain passes (seed 0)",
     "large": "10M cells, depth 400, placed in a 1000 um die (star RC), 4 corners, 2 drive strengths, "
@@ -146,12 +149,17 @@ class ClockSampler:
 
 def byte_model(st: dict, K: int) -> dict:
     """Algorithmic (compulsory) bytes of one update per phase.
-    P pins, S net sinks (net arcs), Nn nets, N RC nodes, E endpoints, I items."""
+    P pins, S net sinks (net arcs), Nn nets, N RC nodes, E endpoints, I items.
+    Per pin and state: arrival and required time 32 B (FP64 x 4), slew and
+    slack 16 B (FP32 x 4).  Forward: every arrival and slew written once and
+    read once by its consumers (2 x 48 B); backward: arrival and slew read,
+    required time and slack written, required time read by the drivers
+    (32 + 16 + 32 + 16 + 32 B)."""
     P, S, Nn, N = st["n_pins"], st["n_net_arcs"], st["n_nets"], st["n_rc_nodes"]
     E, I = st["n_endpoints"], st["n_items"]
     net = 12 * N + 8 * S + K * (4 * Nn + 8 * S)
-    fwd = K * (64 * P + 8 * S + 4 * Nn) + 4 * S + 8 * I
-    bwd = K * (80 * P + 4 * S + 4 * Nn + 10 * E) + 4 * S + 4 * I
+    fwd = K * (96 * P + 8 * S + 4 * Nn) + 4 * S + 8 * I
+    bwd = K * (128 * P + 4 * S + 4 * Nn + 10 * E) + 4 * S + 4 * I
     red = K * 8 * E
     return {"net": net, "fwd": fwd, "bwd": bwd, "reduce": red, "total": net + fwd + bwd + red}
 
@@ -347,6 +355,53 @@ def run_ours(a, dist: Dist):
                     "pins": int(sum(len(p["pins"]) for p in paths)),
                     "what": "sta_report_paths: radix select of the 1000 worst setup endpoints, bitonic sort, "
                             "critical-path trace, CSR arrays copied to the host"}
+
+    # ---- timing exceptions: three startpoint groups (four tags per corner)
+    if d.get("exc_action") is None:
+        dx = dict(d, **synth.exception_groups(d, np.random.default_rng(a.seed), 3, div_from=5, div_to=4))
+        dx["period_ns"] = T
+        del ctx
+        torch.cuda.empty_cache()
+        ctx = sta.Context(dx, device=dev)
+        ctx.set_schedule({v: k for k, v in sched_names.items()}[schedule], 0)
+        for _ in range(3):
+            ctx.update_timing()
+        ms = _events_ms(ctx.update_timing, 10)
+        rx = ctx.report_slack()[0]
+        out["exceptions"] = {"groups": 3, "states_per_pin": ctx.stats()["n_tags"] * K, "ms_per_update": ms,
+                             "arcs_per_s": arcs / (ms * 1e-3), "wns_setup_ns": rx["wns_setup"],
+                             "setup_violations": rx["n_viol_setup"],
+                             "what": "sta_update_timing with 3 false-path / multicycle groups (1/5 of the "
+                                     "startpoints each, endpoint lists of 1/4 of the endpoints or all)"}
+
+    # ---- Steiner-tree RC from positions: a placed 1M-cell design, trees rebuilt every update
+    del ctx
+    torch.cuda.empty_cache()
+    ds = synth.make_design(1_000_000, 150, seed=a.seed, placed=True)
+    ds.update(wire_model=sta.WIRE_STEINER)
+    ctx = sta.Context(ds, device=dev)
+    ctx.set_schedule({v: k for k, v in sched_names.items()}[schedule], 0)
+    ctx.set_clock(0.0)
+    ctx.update_timing()
+    s0, _, _, _ = ctx.get_endpoint_slack()
+    ctx.set_clock(clock.period_in_gap(-s0[:, 0], min_half_gap=0.0)[0])
+    for _ in range(3):
+        ctx.update_timing()
+    ms = _events_ms(ctx.update_timing, 10)
+    ctx.set_profiling(True)
+    acc = np.zeros(4)
+    for _ in range(5):
+        ctx.update_timing()
+        ctx.sync()
+        acc += np.array(ctx.last_timings())
+    ctx.set_profiling(False)
+    wl = ctx.get_net_wirelength()
+    sst = synth.design_stats(ds)
+    out["steiner"] = {"cells": ds["n_cells"], "nets": ds["n_nets"], "ms_per_update": ms,
+                      "arcs_per_s": sst["arcs"] / (ms * 1e-3), "net_phase_ms": acc[0] / 5,
+                      "total_wirelength_m": float(wl.sum()) * 1e-9,
+                      "what": "sta_update_timing on a placed 1M-cell design with STA_WIRE_STEINER: Steiner "
+                              "trees of every net from the positions, RC sweep, forward, backward, reduction"}
 
     del ctx
     torch.cuda.empty_cache()

@@ -121,7 +121,10 @@ typedef struct {
  * gamma_ns > 0 selects log-sum-exp smoothed max/min merges (differentiable
  * mode, required for sta_backward); 0 = exact max/min.
  * Net delay calculator (Sec. III "Delay models": an Elmore calculator and
- * an Arnoldi-based reduced-order model), RC trees only for the latter:
+ * an Arnoldi-based reduced-order model), the latter on RC trees (rc_ptr)
+ * or Steiner trees (STA_WIRE_STEINER), not on stars, and with every edge
+ * R > 0 (rc_R of non-root nodes; unit R for Steiner trees, whose points at
+ * the same position share one node):
  *   STA_NET_ELMORE:  sink delay = Elmore delay (first moment of the impulse
  *     response);
  *   STA_NET_ARNOLDI: sink delay = the time the step response of an
@@ -179,7 +182,31 @@ typedef struct {
     int32_t n_exc;
     const int32_t *exc_from_ptr, *exc_from, *exc_to_ptr, *exc_to, *exc_action;
     const float *exc_mult;
+    /* RC from positions (rc_ptr == NULL; Sec. III "Parasitics (RC) inputs":
+     * pin positions and unit R/C along x and y).  wire_model:
+     *   STA_WIRE_STAR (0): one segment per sink of Manhattan length L,
+     *     R = r_per_um L, C = c_per_um L split half at each end;
+     *   STA_WIRE_STEINER (1): a rectilinear Steiner tree per net, rebuilt at
+     *     every update from the current positions -- coordinates rounded to
+     *     integer nm (the float product x * 1000, nearest, ties to even),
+     *     Prim's rectilinear MST from the driver (ties: smaller distance,
+     *     then lower pin index in net order, then the earlier-attached tree
+     *     node), then greedy median insertion: over every node u and pair of
+     *     its neighbours v < w, the Steiner point M = (median x, median y) of
+     *     {u, v, w} gains d(u,v) + d(u,w) - d(M,u) - d(M,v) - d(M,w); the
+     *     largest gain (first in (u, v, w) order) is applied while positive,
+     *     at most 2 (n - 1) times for n pins; nets of more than 64 pins keep
+     *     the MST.  Each tree edge of lengths Lx, Ly (um) has R = r_per_um Lx
+     *     + r_per_um_y Ly and wire C = c_per_um Lx + c_per_um_y Ly split half
+     *     at each end (r_per_um_y, c_per_um_y <= 0: the x values).
+     *     Positions must satisfy |x|, |y| <= 1e6 um.  Elmore or Arnoldi
+     *     (net_model) on the tree.  Not differentiable (no sta_backward). */
+    int32_t wire_model;
+    float r_per_um_y, c_per_um_y;
 } sta_design_desc;
+
+/* parasitics built from positions (sta_design_desc.wire_model) */
+enum { STA_WIRE_STAR = 0, STA_WIRE_STEINER = 1 };
 
 /* net delay calculators (sta_design_desc.net_model) */
 enum { STA_NET_ELMORE = 0, STA_NET_ARNOLDI = 1 };
@@ -319,6 +346,13 @@ sta_status sta_report_slack_design(sta_ctx *ctx, int32_t d, void *stream, sta_co
  * For a batch, pins of design d follow those of design d-1. */
 sta_status sta_get_pin_state(sta_ctx *ctx, int32_t which, float *out, sta_mem mem, void *stream);
 
+/* Steiner wirelength of every net at the last sta_update_timing:
+ * wl_nm[n_nets] (int64, nm) in the caller's net order (for a batch, nets of
+ * design d follow those of design d-1), the sum of the Manhattan lengths of
+ * the tree's edges on integer nm coordinates.  Errors: STA_ESTATE unless the
+ * context builds Steiner trees (STA_WIRE_STEINER) and has been updated. */
+sta_status sta_get_net_wirelength(sta_ctx *ctx, int64_t *wl_nm, sta_mem mem, void *stream);
+
 /* Endpoint slacks: setup[n_endpoints][n_corners] = min over rise/fall of the
  * late slack, hold likewise with the early slack, viol_* = slack < 0 as
  * 0/1 bytes.  Any output may be NULL. */
@@ -368,7 +402,10 @@ sta_status sta_report_paths(sta_ctx *ctx, int32_t design, int32_t corner, int32_
  * until the next sta_update_timing or sta_destroy.  gpu_pin_of[p] maps a
  * caller pin id to its internal index (device int32 array). */
 typedef struct {
-    const float *at, *slew, *rat, *slack;   /* [n_pins][n_corners][4] internal order */
+    const float *at;      /* [n_pins][n_corners][4][2] internal order: double-float (hi, lo), value hi + lo */
+    const float *slew;    /* [n_pins][n_corners][4] */
+    const float *rat;     /* [n_pins][n_corners][4][2] like at */
+    const float *slack;   /* [n_pins][n_corners][4] */
     const int32_t *gpu_pin_of;              /* [n_pins] */
 } sta_views;
 sta_status sta_get_arrays(sta_ctx *ctx, sta_views *out);

@@ -29,15 +29,16 @@ static inline int nblk2(long long n, int t) { return (int)((n + t - 1) / t); }
 constexpr int kDfThreadsA = 256;
 
 // Smooth min of the two edges' setup margins of endpoint e at corner k.
-// Per-endpoint terms are FP32 (the arrivals they start from are FP32); the
-// sums over endpoints and over the gradient are FP64.
+// Per-endpoint terms are FP32 (margins formed from the double-float
+// arrivals, then rounded once); the sums over endpoints and over the
+// gradient are FP64.
 __device__ __forceinline__ float ep_smooth_slack(const DevCtx &c, int e, int k, float y[2])
 {
     const int p = chk(c, c.ep_pin[e], c.P);
-    const float req = c.ep_is_d[e] ? c.period - c.setup : c.period;
-    const float4 a = c.at[(size_t)p * c.K + k];
-    y[0] = req - a.z;
-    y[1] = req - a.w;
+    const DF req = c.ep_is_d[e] ? DF(c.period) - c.setup : DF(c.period);
+    const DF4 &a = c.at[(size_t)p * c.K + k];
+    y[0] = req - a.v[2];
+    y[1] = req - a.v[3];
     const float m = fminf(y[0], y[1]);
     return m - c.gamma * logf(expf((m - y[0]) * c.inv_gamma) + expf((m - y[1]) * c.inv_gamma));
 }
@@ -165,17 +166,6 @@ __global__ void k_adj_seed(const DevCtx c)
     }
 }
 
-__device__ __forceinline__ float2 pos_of(const DevCtx &c, int p)
-{
-    const int pc = c.pin_cell[chk(c, p, c.P)];
-    if (pc >= 0) {
-        const int cc = chk(c, pc, c.C);
-        return make_float2(c.cell_xy[2 * (size_t)cc], c.cell_xy[2 * (size_t)cc + 1]);
-    }
-    const int q = -pc - 1;
-    return make_float2(c.port_xy[2 * (size_t)q], c.port_xy[2 * (size_t)q + 1]);
-}
-
 __device__ __forceinline__ float4 *abox_at(const DevCtx &c, int par, int pin, int k)
 {
     return c.abox + ((size_t)par * c.P + pin) * c.K + k;
@@ -186,7 +176,8 @@ struct AdjItem {
     // the lane's first corner, loaded ahead (written by the forward pass):
     // the output's late slew of this lane's edge, its load, the clock slew
     // (flip-flop) or the late arrival and slew of each input pin
-    float sz0, ld0, ain0[3][2], sin0[3][2];
+    float sz0, ld0, sin0[3][2];
+    DF ain0[3][2];
 };
 
 __device__ __forceinline__ AdjItem adj_prep(const DevCtx &c, const int *tnin, const int *tkind, int g, int q)
@@ -209,8 +200,8 @@ __device__ __forceinline__ AdjItem adj_prep(const DevCtx &c, const int *tnin, co
     for (int j = 0; j < 3; ++j) {
         const bool on = j < nread;
         const size_t o = (size_t)(a.pin0 + j) * K + kq;
-        a.ain0[j][0] = on ? ld_state(c.at + o, 2) : 0.f;
-        a.ain0[j][1] = on ? ld_state(c.at + o, 3) : 0.f;
+        a.ain0[j][0] = on ? ld_state_df(c.at + o, 2) : DF(0.f);
+        a.ain0[j][1] = on ? ld_state_df(c.at + o, 3) : DF(0.f);
         a.sin0[j][0] = on ? ld_state(c.slew + o, 2) : 0.f;
         a.sin0[j][1] = on ? ld_state(c.slew + o, 3) : 0.f;
     }
@@ -313,7 +304,8 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
                 interp_d(lut, tq, seg_slew<UNIFORM>(c, lut, tq, cs), seg_load<UNIFORM>(c, lut, tq, ld), ds, dl);
                 aload = abar * sc * dl;
             } else {
-                float x[6], dds[6], ddl[6];
+                float x[6];   // candidates (FP32, as the forward merge forms them)
+                float dds[6], ddl[6];
 #pragma unroll
                 for (int i = 0; i < 6; ++i) {
                     x[i] = -INFINITY;
@@ -324,7 +316,8 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
                     if (j >= nin) continue;
                     const int se = tsense[t * 3 + j];
                     const int tq = tab_off(t, j, slew_lane ? 2 + rfo : rfo);
-                    float Ain[2], Sin[2];
+                    DF Ain[2];
+                    float Sin[2];
                     if (first) {
                         Ain[0] = a.ain0[j][0];
                         Ain[1] = a.ain0[j][1];
@@ -332,8 +325,8 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
                         Sin[1] = a.sin0[j][1];
                     } else {
                         const size_t o = (size_t)(pin0 + j) * K + k;
-                        Ain[0] = ld_state(c.at + o, 2);
-                        Ain[1] = ld_state(c.at + o, 3);
+                        Ain[0] = ld_state_df(c.at + o, 2);
+                        Ain[1] = ld_state_df(c.at + o, 3);
                         Sin[0] = ld_state(c.slew + o, 2);
                         Sin[1] = ld_state(c.slew + o, 3);
                     }
@@ -344,7 +337,7 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
                         float ds, dl;
                         const float v = interp_d(lut, tq, seg_slew<UNIFORM>(c, lut, tq, s),
                                                  seg_load<UNIFORM>(c, lut, tq, ld), ds, dl);
-                        x[j * 2 + rfi] = slew_lane ? sc * v : Ain[rfi] + sc * v;
+                        x[j * 2 + rfi] = slew_lane ? sc * v : Ain[rfi].hi + sc * v;
                         dds[j * 2 + rfi] = ds;
                         ddl[j * 2 + rfi] = dl;
                     }
@@ -355,11 +348,11 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
                 for (int i = 0; i < 6; ++i) m = fmaxf(m, x[i]);
                 float zsum = 0.f;
 #pragma unroll
-                for (int i = 0; i < 6; ++i) zsum += x[i] > -INFINITY ? expf((x[i] - m) * ig) : 0.f;
+                for (int i = 0; i < 6; ++i) zsum += x[i] > -INFINITY ? expf((float)(x[i] - m) * ig) : 0.f;
 #pragma unroll
                 for (int i = 0; i < 6; ++i) {
                     if (!(x[i] > -INFINITY)) continue;
-                    const float w = abar * expf((x[i] - m) * ig) / zsum;
+                    const float w = abar * expf((float)(x[i] - m) * ig) / zsum;
                     if (!slew_lane) aAin[i] = w;
                     aSin[i] = w * sc * dds[i];
                     aload += w * sc * ddl[i];
@@ -402,12 +395,12 @@ __global__ void k_adj_star(const DevCtx c)
     if (f0 >= f1) return;
     const int K = c.K;
     const int z = chk(c, item_out_pin(c, chk_type(c, c.item_type[g]), c.item_pin0[g]), c.P);
-    const float2 pz = pos_of(c, z);
+    const float2 pz = pin_pos(c, z);
     const int cz = c.pin_cell[z];
     double gdx = 0.0, gdy = 0.0;
     for (int p = f0; p < f1; ++p) {
         const int s = chk(c, c.fo_pin[p], c.P);
-        const float2 ps = pos_of(c, s);
+        const float2 ps = pin_pos(c, s);
         const float dx = pz.x - ps.x, dy = pz.y - ps.y;
         const float L = fabsf(dx) + fabsf(dy);
         const float cp = 1e3f * c.fo_cap[p];

@@ -27,11 +27,15 @@ static inline size_t df_smem_bytes(int T) { return (size_t)T * 3 * 4 * kLutStrid
 __global__ void k_df_recover(const DevCtx c)
 {
     if (ld_volatile(c.df_state + 3) == 0u) return;
-    const float4 nan4 = make_float4(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff),
-                                    __int_as_float(0x7fffffff), __int_as_float(0x7fffffff));
+    const float4 nan4 = make_float4(nan_f(), nan_f(), nan_f(), nan_f());
+    DF4 nand;
+    for (int q = 0; q < 4; ++q) nand.v[q] = nan_df();
     const size_t stride = (size_t)gridDim.x * blockDim.x;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.fbox_len; i += stride) c.fbox[i] = nan4;
-    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.rbox_len; i += stride) c.rbox[i] = nan4;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.fbox_len; i += stride) {
+        c.fbox_a[i] = nand;
+        c.fbox_s[i] = nan4;
+    }
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < c.rbox_len; i += stride) c.rbox[i] = nand;
 }
 
 // New epoch, chunk counters at zero, abort cleared.
@@ -149,7 +153,7 @@ __global__ void __launch_bounds__(kDfThreads) k_df_backward(const DevCtx c)
         if (pending) b = bwd_prep(c, L.nin, L.kind, x, q);
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
-            float R;
+            DF R;
             if (pending && group_all(c, bwd_probe(c, b, par, q, R))) {
                 bwd_run<UNIFORM, true>(c, L.lut, L.sense, b, q, par, R);
                 pending = false;
@@ -310,11 +314,7 @@ void launch_coop_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cuda
     const size_t smem = df_smem_bytes(h.T);
     if (ev) cudaEventRecord(ev[0], st);
     k_coop_begin<<<1, 32, 0, st>>>(c);
-    if (h.placed) {
-        if (c.I > 0) launch_net_star(c, st);
-    } else if (h.rc) {
-        launch_net_tree(c, st);
-    }
+    launch_net_phase(c, h, st);
     if (ev) cudaEventRecord(ev[1], st);
     if (c.I > 0 || c.E > 0) {
         if (c.gamma > 0.f) {
@@ -339,11 +339,7 @@ void launch_dataflow_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, 
     if (ev) cudaEventRecord(ev[0], st);
     k_df_recover<<<h.df_blocks_fwd > 0 ? h.df_blocks_fwd : 1, kDfThreads, 0, st>>>(c);
     k_df_begin<<<1, 32, 0, st>>>(c);
-    if (h.placed) {
-        if (c.I > 0) launch_net_star(c, st);
-    } else if (h.rc) {
-        launch_net_tree(c, st);
-    }
+    launch_net_phase(c, h, st);
     if (ev) cudaEventRecord(ev[1], st);
     if (c.n_fwd_chunks > 0) {
         auto kf = c.gamma > 0.f ? (h.uniform ? k_df_forward<true, true> : k_df_forward<true, false>)

@@ -13,6 +13,7 @@ constexpr int kLutStride = 80;   // floats per packed table, see plan.cpp
 constexpr int kNetArnoldi = 1;     // DevCtx::net_model of the reduced-order calculator (STA_NET_ARNOLDI)
 constexpr int kRcColNodes = 16;    // RC nets up to this size are swept in shared memory (as plan.h)
 constexpr int kRcThreads = 128;    // threads (nets) per block of the RC sweep
+constexpr int kStMaxPins = 64;     // nets of more pins keep the rectilinear MST (plan.h: kSteinerMaxPins)
 constexpr int kRedThreads = 256;   // threads of the reduction kernels
 constexpr int kDfStateWords = 16;  // schedule state words (see DevCtx::df_state)
 constexpr int kRedChunk = 4096;    // endpoints per first-stage reduction block
@@ -21,6 +22,66 @@ constexpr int kRedChunk = 4096;    // endpoints per first-stage reduction block
 constexpr unsigned kErrTimeout = 1u;
 constexpr unsigned kErrBounds = 2u;
 constexpr unsigned kErrResize = 4u;
+
+// Arrival and required times are double-float values: an unevaluated sum
+// hi + lo of two FP32 numbers (|lo| <= ulp(hi) / 2), ~48 significant bits.
+// Each level adds a delay to them, and plain FP32 would round at every
+// level -- over a deep design the rounding alone reaches the 1e-4 ns parity
+// bound once arrivals pass ~20 ns -- while B300's FP64 pipe is too narrow
+// for the per-item critical path; these sums run on the FP32 pipe.  Slews,
+// slacks and every delay stay FP32.
+struct DF {
+    float hi, lo;
+    DF() = default;
+    __host__ __device__ __forceinline__ DF(float x) : hi(x), lo(0.f) {}
+    __host__ __device__ __forceinline__ DF(float h, float l) : hi(h), lo(l) {}
+};
+// a + b, b an FP32 number: the error-free sum of the high parts (Knuth's
+// two-sum), the low parts added, then renormalised (Dekker's fast two-sum).
+// Infinite sums (absent arrivals, unconstrained required times) stay exact.
+__device__ __forceinline__ DF operator+(DF a, float b)
+{
+    const float s = __fadd_rn(a.hi, b);
+    if (!isfinite(s)) return DF(s, 0.f);
+    const float bb = __fsub_rn(s, a.hi);
+    const float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    const float l = __fadd_rn(e, a.lo);
+    const float t = __fadd_rn(s, l);
+    return DF(t, __fsub_rn(l, __fsub_rn(t, s)));
+}
+__device__ __forceinline__ DF operator-(DF a, float b) { return a + (-b); }
+__device__ __forceinline__ DF operator-(DF a) { return DF(-a.hi, -a.lo); }
+// sign times a value, sign = +1 or -1 (exact)
+__device__ __forceinline__ DF operator*(float sgn, DF a) { return DF(sgn * a.hi, sgn * a.lo); }
+// a - b rounded to FP32 (slacks, smoothing exponents)
+__device__ __forceinline__ float operator-(DF a, DF b)
+{
+    return __fadd_rn(__fsub_rn(a.hi, b.hi), __fsub_rn(a.lo, b.lo));
+}
+__device__ __forceinline__ bool operator>(DF a, DF b) { return a.hi > b.hi || (a.hi == b.hi && a.lo > b.lo); }
+__device__ __forceinline__ bool operator<(DF a, DF b) { return b > a; }
+__device__ __forceinline__ DF df_max(DF a, DF b) { return b > a ? b : a; }
+__device__ __forceinline__ DF df_min(DF a, DF b) { return b < a ? b : a; }
+__device__ __forceinline__ float to_f(DF a) { return __fadd_rn(a.hi, a.lo); }
+// a * b exactly as a double-float (the product's rounding error by FMA)
+__device__ __forceinline__ DF df_mul(float a, float b)
+{
+    const float p = __fmul_rn(a, b);
+    if (!isfinite(p)) return DF(p, 0.f);
+    return DF(p) + fmaf(a, b, -p);
+}
+__device__ __forceinline__ DF shfl_xor_df(unsigned mask, DF v, int lane)
+{
+    return DF(__shfl_xor_sync(mask, v.hi, lane), __shfl_xor_sync(mask, v.lo, lane));
+}
+__device__ __forceinline__ DF shfl_df(unsigned mask, DF v, int src)
+{
+    return DF(__shfl_sync(mask, v.hi, src), __shfl_sync(mask, v.lo, src));
+}
+
+struct __align__(32) DF4 {
+    DF v[4];
+};
 
 struct DevCtx {
     int32_t P, I, S, E, K, T, C, n_designs;
@@ -41,11 +102,24 @@ struct DevCtx {
     const float *fo_cap;
     const int32_t *rc_ptr, *rc_parent;
     const float *rc_R, *rc_C;
+    // Steiner trees from positions (STA_WIRE_STEINER): the tree kernel writes
+    // the RC arrays above (through these aliases), the sinks' nodes and the
+    // live node count of every item; working storage per item
+    int32_t steiner;
+    float r_per_um_y, c_per_um_y;
+    int32_t *st_parent, *st_fo_node, *st_nlive;
+    float *st_R, *st_C;
+    int64_t *st_wl;                             // [I] tree length, nm
+    const int64_t *st_node_ptr, *st_adj_ptr;    // [I + 1] working nodes / bitset words per item
+    long long *st_x, *st_y, *st_key;            // [working nodes] coordinates (nm), Prim keys
+    int32_t *st_aux;                            // [working nodes x 3] Prim source / BFS number / queue
+    unsigned *st_adj;                           // [bitset words] adjacency rows
     const int32_t *drv_of, *pin_cell;
     const float *port_xy, *cell_xy;
     const int32_t *ep_pin, *ep_design_ptr;
     const uint8_t *ep_is_d;
-    float4 *at, *slew, *rat, *slack;            // [P*K]
+    DF4 *at, *rat;                              // [P*K] arrival and required times (double-float)
+    float4 *slew, *slack;                       // [P*K]
     float *netD, *netV, *load;                  // [P*K]
     float *ep_setup, *ep_hold;                  // [E*K]
     uint8_t *viol_setup, *viol_hold;            // [E*K]
@@ -56,9 +130,10 @@ struct DevCtx {
     unsigned *err;
     float *scratch_a, *scratch_b, *scratch_c;   // [K][NN] RC sweeps of nets larger than kRcColNodes
     // dataflow schedule: mailboxes by epoch parity, NaN until published
-    float4 *fbox;                               // [2][P][K][2] arrival, slew of driver pins
-    float4 *rbox;                               // [2][P][K]    required time of gate input pins
-    size_t fbox_len, rbox_len;                  // float4 elements of each
+    DF4 *fbox_a;                                // [2][P][K] arrival of driver pins
+    float4 *fbox_s;                             // [2][P][K] slew of driver pins
+    DF4 *rbox;                                  // [2][P][K] required time of gate input pins
+    size_t fbox_len, rbox_len;                  // records of fbox_a (= of fbox_s) and of rbox
     unsigned *df_state;                         // [kDfStateWords] [0] epoch, [1] forward chunk counter,
                                                 // [2] backward counter, [3] abort; adjoint: [4] epoch,
                                                 // [5] chunk counter, [6] abort; [7] grid-barrier arrivals
@@ -119,29 +194,42 @@ __device__ __forceinline__ float comp(const float4 &v, int i)
 // Running max of candidates y (callers pass y = x for a late max and y = -x
 // for an early min, and negate the result back).  SMOOTH replaces the max by
 // gamma * log-sum-exp(y / gamma), accumulated max-shifted.
-template <bool SMOOTH>
+template <bool SMOOTH, class T = float>
 struct MaxMerge {
-    float m = -INFINITY, s = 0.f;
-    __device__ __forceinline__ void add(float y, float inv_g)
+    T m = -INFINITY;
+    float s = 0.f;
+    __device__ __forceinline__ void add(T y, float inv_g)
     {
         if (!SMOOTH) {
-            m = fmaxf(m, y);
+            m = y > m ? y : m;
         } else if (!(y > -INFINITY)) {
             // an absent candidate (another exception tag's arrival): no term
         } else if (y > m) {
-            s = s * expf((m - y) * inv_g) + 1.f;
+            s = s * expf((float)(m - y) * inv_g) + 1.f;
             m = y;
         } else {
-            s += expf((y - m) * inv_g);
+            s += expf((float)(y - m) * inv_g);
         }
     }
-    __device__ __forceinline__ float get(float g) const { return SMOOTH ? m + g * logf(s) : m; }
+    __device__ __forceinline__ T get(float g) const { return SMOOTH ? m + g * logf(s) : m; }
 };
 
 __device__ __forceinline__ int item_out_pin(const DevCtx &c, int t, int pin0)
 {
     if (t < 0) return pin0;
     return __ldg(c.type_kind + t) == 1 ? pin0 + 1 : pin0 + __ldg(c.type_nin + t);
+}
+
+// position of a pin (um): its cell's, or its port's for a PI / PO
+__device__ __forceinline__ float2 pin_pos(const DevCtx &c, int p)
+{
+    const int pc = c.pin_cell[chk(c, p, c.P)];
+    if (pc >= 0) {
+        const int cc = chk(c, pc, c.C);
+        return make_float2(c.cell_xy[2 * (size_t)cc], c.cell_xy[2 * (size_t)cc + 1]);
+    }
+    const int q = -pc - 1;
+    return make_float2(c.port_xy[2 * (size_t)q], c.port_xy[2 * (size_t)q + 1]);
 }
 
 }  // namespace sta

@@ -21,14 +21,15 @@
 // complete (see below and dataflow.cu) and the item publishes its own
 // results there; WAIT = false relies on launch boundaries (level schedule).
 //
-// Mailboxes.  For epoch parity p, fbox[p] holds each driver pin's arrival
-// and slew and rbox[p] each gate input pin's required time.  Every float is
-// NaN until its producer stores the final value with a relaxed store, and a
-// real result is never NaN, so a reader that sees all the floats it needs
-// non-NaN has the final values: each 32-bit store is single-copy atomic, no
-// fence or flag is needed, and the poll is the data load itself.  While it
-// publishes parity p, a producer resets its own entries of parity p ^ 1 to
-// NaN for the next pass.
+// Mailboxes.  For epoch parity p, fbox_a[p] / fbox_s[p] hold each driver
+// pin's arrival (double-float) and slew (FP32) and rbox[p] each gate input
+// pin's required time (double-float).  Every float is NaN until its producer
+// stores the final value with a relaxed store, and a real result is never
+// NaN, so a reader that sees all the floats it needs non-NaN has the final
+// values: each 32-bit store is single-copy atomic, no fence or flag is
+// needed, and the poll is the data load itself.  While it publishes
+// parity p, a producer resets its own entries of parity p ^ 1 to NaN for the
+// next pass.
 #pragma once
 
 #include "device.cuh"
@@ -144,38 +145,71 @@ __device__ __forceinline__ float ld_relaxed1(const float *p)
     asm volatile("ld.relaxed.gpu.global.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
     return v;
 }
+// one double-float component (8 bytes) and a whole record (two 16-byte loads)
+__device__ __forceinline__ DF ld_relaxed_df(const DF *p)
+{
+    DF v;
+    asm volatile("ld.relaxed.gpu.global.v2.f32 {%0, %1}, [%2];" : "=f"(v.hi), "=f"(v.lo) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void ld_relaxed_df4(const DF4 *p, DF &x, DF &y, DF &z, DF &w)
+{
+    asm volatile("ld.relaxed.gpu.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(x.hi), "=f"(x.lo), "=f"(y.hi), "=f"(y.lo)
+                 : "l"(p->v)
+                 : "memory");
+    asm volatile("ld.relaxed.gpu.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(z.hi), "=f"(z.lo), "=f"(w.hi), "=f"(w.lo)
+                 : "l"(p->v + 2)
+                 : "memory");
+}
 __device__ __forceinline__ void st_relaxed(float *p, float v)
 {
     asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
 }
+__device__ __forceinline__ void st_relaxed_df(DF *p, DF v)
+{
+    asm volatile("st.relaxed.gpu.global.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.hi), "f"(v.lo) : "memory");
+}
 __device__ __forceinline__ unsigned ld_volatile(const unsigned *p) { return *(const volatile unsigned *)p; }
 __device__ __forceinline__ bool complete(float4 v) { return v.x == v.x && v.y == v.y && v.z == v.z && v.w == v.w; }
+// a published double-float: both halves non-NaN (the two 32-bit halves are
+// separate single-copy-atomic stores)
+__device__ __forceinline__ bool real_df(DF x) { return x.hi == x.hi && x.lo == x.lo; }
+__device__ __forceinline__ bool complete_df(const DF4 *p)
+{
+    DF x, y, z, w;
+    ld_relaxed_df4(p, x, y, z, w);
+    return real_df(x) && real_df(y) && real_df(z) && real_df(w);
+}
+__device__ __forceinline__ float nan_f() { return __int_as_float(0x7fffffff); }
+__device__ __forceinline__ DF nan_df() { return DF(nan_f(), nan_f()); }
 
-// mailbox records
-__device__ __forceinline__ float4 *fbox_at(const DevCtx &c, int par, int pin, int k)
+// mailbox records: [parity][pin][state]
+__device__ __forceinline__ size_t box_index(const DevCtx &c, int par, int pin, int k)
 {
-    return c.fbox + (((size_t)par * c.P + pin) * c.K + k) * 2;
+    return ((size_t)par * c.P + pin) * c.K + k;
 }
-__device__ __forceinline__ float4 *rbox_at(const DevCtx &c, int par, int pin, int k)
+__device__ __forceinline__ DF4 *fbox_a(const DevCtx &c, int par, int pin, int k) { return c.fbox_a + box_index(c, par, pin, k); }
+__device__ __forceinline__ float4 *fbox_s(const DevCtx &c, int par, int pin, int k)
 {
-    return c.rbox + ((size_t)par * c.P + pin) * c.K + k;
+    return c.fbox_s + box_index(c, par, pin, k);
 }
+__device__ __forceinline__ DF4 *rbox_at(const DevCtx &c, int par, int pin, int k) { return c.rbox + box_index(c, par, pin, k); }
 
 // Lane q publishes component q of pin's arrival and slew for parity par and
 // clears the same component of parity par ^ 1.
-__device__ __forceinline__ void publish_fwd(const DevCtx &c, int par, int pin, int k, int q, float at, float sl)
+__device__ __forceinline__ void publish_fwd(const DevCtx &c, int par, int pin, int k, int q, DF at, float sl)
 {
-    float *n = reinterpret_cast<float *>(fbox_at(c, par, pin, k));
-    float *o = reinterpret_cast<float *>(fbox_at(c, par ^ 1, pin, k));
-    st_relaxed(n + q, at);
-    st_relaxed(n + 4 + q, sl);
-    o[q] = __int_as_float(0x7fffffff);
-    o[4 + q] = __int_as_float(0x7fffffff);
+    st_relaxed_df(fbox_a(c, par, pin, k)->v + q, at);
+    st_relaxed(reinterpret_cast<float *>(fbox_s(c, par, pin, k)) + q, sl);
+    fbox_a(c, par ^ 1, pin, k)->v[q] = nan_df();
+    reinterpret_cast<float *>(fbox_s(c, par ^ 1, pin, k))[q] = nan_f();
 }
-__device__ __forceinline__ void publish_rat(const DevCtx &c, int par, int pin, int k, int q, float r)
+__device__ __forceinline__ void publish_rat(const DevCtx &c, int par, int pin, int k, int q, DF r)
 {
-    st_relaxed(reinterpret_cast<float *>(rbox_at(c, par, pin, k)) + q, r);
-    reinterpret_cast<float *>(rbox_at(c, par ^ 1, pin, k))[q] = __int_as_float(0x7fffffff);
+    st_relaxed_df(rbox_at(c, par, pin, k)->v + q, r);
+    rbox_at(c, par ^ 1, pin, k)->v[q] = nan_df();
 }
 
 // Reads of pin states (arrival, slew, required time) that another item
@@ -188,7 +222,13 @@ __device__ __forceinline__ float ld_state(const float4 *p, int q)
 {
     return __ldcg(reinterpret_cast<const float *>(p) + q);
 }
+__device__ __forceinline__ DF ld_state_df(const DF4 *p, int q)
+{
+    const float2 v = __ldcg(reinterpret_cast<const float2 *>(p->v + q));
+    return DF(v.x, v.y);
+}
 __device__ __forceinline__ void st_comp(float4 *p, int q, float v) { reinterpret_cast<float *>(p)[q] = v; }
+__device__ __forceinline__ void st_comp_df(DF4 *p, int q, DF v) { p->v[q] = v; }
 
 __device__ __forceinline__ bool arc_on(int sense, int rfi, int rfo)
 {
@@ -230,7 +270,8 @@ struct FwdItem {
 // the drivers' arrival and slew, component q of the lane's first corner, as
 // probed (the other edge comes from the partner lane q ^ 1)
 struct FwdIn {
-    float at[3], sl[3];
+    DF at[3];
+    float sl[3];
 };
 
 __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, const int *tkind, const int *tsense,
@@ -268,13 +309,11 @@ __device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         if (j < f.nin) {
-            const float *r = reinterpret_cast<const float *>(fbox_at(c, par, f.drv[j], kq));
-            in.at[j] = ld_relaxed1(r + q);
-            in.sl[j] = ld_relaxed1(r + 4 + q);
-            ok = ok && in.at[j] == in.at[j] && in.sl[j] == in.sl[j];
+            in.at[j] = ld_relaxed_df(fbox_a(c, par, f.drv[j], kq)->v + q);
+            in.sl[j] = ld_relaxed1(reinterpret_cast<const float *>(fbox_s(c, par, f.drv[j], kq)) + q);
+            ok = ok && real_df(in.at[j]) && in.sl[j] == in.sl[j];
             for (int k = kq + c.KL; k < c.K && ok; k += c.KL)
-                ok = complete(ld_relaxed4(fbox_at(c, par, f.drv[j], k))) &&
-                     complete(ld_relaxed4(fbox_at(c, par, f.drv[j], k) + 1));
+                ok = complete_df(fbox_a(c, par, f.drv[j], k)) && complete(ld_relaxed4(fbox_s(c, par, f.drv[j], k)));
         }
     }
     return ok;
@@ -294,8 +333,8 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
     const float absent = el ? -INFINITY : INFINITY;
     if (t < 0) {   // primary input
         for (int k = kq; k < K; k += KL) {
-            const float a = (c.Tg == 1 || k % c.Tg == f.tag) ? c.pi_at : absent;
-            st_comp(c.at + (size_t)pin0 * K + k, q, a);
+            const DF a((c.Tg == 1 || k % c.Tg == f.tag) ? c.pi_at : absent);
+            st_comp_df(c.at + (size_t)pin0 * K + k, q, a);
             st_comp(c.slew + (size_t)pin0 * K + k, q, c.pi_slew);
             if (pub) publish_fwd(c, par, pin0, k, q, a, c.pi_slew);
         }
@@ -308,13 +347,13 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
         for (int k = kq; k < K; k += KL) {
             const float sc = __ldg(c.lut_scale + k);
             const float ld = k != kq ? c.load[(size_t)qp * K + k] : f.ld0;
-            const float ck_at = (c.Tg == 1 || k % c.Tg == f.tag) ? 0.f : absent;
-            st_comp(c.at + (size_t)ck * K + k, q, ck_at);
+            const DF ck_at((c.Tg == 1 || k % c.Tg == f.tag) ? 0.f : absent);
+            st_comp_df(c.at + (size_t)ck * K + k, q, ck_at);
             st_comp(c.slew + (size_t)ck * K + k, q, cs);
             const Seg as = seg_slew<UNIFORM>(c, lut, tb, cs), bl = seg_load<UNIFORM>(c, lut, tb, ld);
-            const float a = ck_at + sc * lookup<UNIFORM>(lut, tb + rfo * kLutStride, as, bl, cs, ld);
+            const DF a = ck_at + sc * lookup<UNIFORM>(lut, tb + rfo * kLutStride, as, bl, cs, ld);
             const float sl = sc * lookup<UNIFORM>(lut, tb + (2 + rfo) * kLutStride, as, bl, cs, ld);
-            st_comp(c.at + (size_t)qp * K + k, q, a);
+            st_comp_df(c.at + (size_t)qp * K + k, q, a);
             st_comp(c.slew + (size_t)qp * K + k, q, sl);
             if (pub) publish_fwd(c, par, qp, k, q, a, sl);
         }
@@ -325,29 +364,34 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
     const unsigned qm = quad_mask();
     for (int k = kq; k < K; k += KL) {
         // net arcs into the input pins: this lane needs components el*2 + {0, 1}
-        float ain[3][2], sin[3][2];
+        DF ain[3][2];
+        float sin[3][2];
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             if (j < nin) {
                 const int a = pin0 + j;
-                float a0, a1, s0, s1;   // the driver's rise / fall arrival and slew at this lane's el
+                DF a0, a1;   // the driver's rise / fall arrival and slew at this lane's el
+                float s0, s1;
                 if (WAIT && k == kq) {
-                    const float ap = __shfl_xor_sync(qm, in.at[j], 1), sp = __shfl_xor_sync(qm, in.sl[j], 1);
+                    const DF ap = shfl_xor_df(qm, in.at[j], 1);
+                    const float sp = __shfl_xor_sync(qm, in.sl[j], 1);
                     a0 = rfo ? ap : in.at[j];
                     a1 = rfo ? in.at[j] : ap;
                     s0 = rfo ? sp : in.sl[j];
                     s1 = rfo ? in.sl[j] : sp;
                 } else {
-                    float4 ad, sd;
+                    float4 sd;
                     if (!WAIT) {
-                        ad = ld_state4(c.at + (size_t)f.drv[j] * K + k);
+                        a0 = ld_state_df(c.at + (size_t)f.drv[j] * K + k, el * 2);
+                        a1 = ld_state_df(c.at + (size_t)f.drv[j] * K + k, el * 2 + 1);
                         sd = ld_state4(c.slew + (size_t)f.drv[j] * K + k);
                     } else {
-                        ad = ld_relaxed4(fbox_at(c, par, f.drv[j], k));
-                        sd = ld_relaxed4(fbox_at(c, par, f.drv[j], k) + 1);
+                        DF x, y, zz, w;
+                        ld_relaxed_df4(fbox_a(c, par, f.drv[j], k), x, y, zz, w);
+                        a0 = el ? zz : x;
+                        a1 = el ? w : y;
+                        sd = ld_relaxed4(fbox_s(c, par, f.drv[j], k));
                     }
-                    a0 = el ? ad.z : ad.x;
-                    a1 = el ? ad.w : ad.y;
                     s0 = el ? sd.z : sd.x;
                     s1 = el ? sd.w : sd.y;
                 }
@@ -358,14 +402,20 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
                 sin[j][0] = sqrtf(fmaf(s0, s0, V));
                 sin[j][1] = sqrtf(fmaf(s1, s1, V));
                 // lane q stores component q of the input pin: (el, rf = q & 1)
-                st_comp(c.at + (size_t)a * K + k, q, rfo ? ain[j][1] : ain[j][0]);
+                st_comp_df(c.at + (size_t)a * K + k, q, rfo ? ain[j][1] : ain[j][0]);
                 st_comp(c.slew + (size_t)a * K + k, q, rfo ? sin[j][1] : sin[j][0]);
             }
         }
         const float sc = __ldg(c.lut_scale + k);
         const float ld = k != kq ? c.load[(size_t)z * K + k] : f.ld0;
         const Seg bl = seg_load<UNIFORM>(c, lut, tab_off(t, 0, 0), ld);
+        // Candidates are merged in FP32 -- the input arrival's high part +
+        // the arc delay -- and only the winner's sum is formed exactly: a
+        // near-tie in FP32 can pick a candidate below the true maximum by at
+        // most one FP32 rounding, and that error does not accumulate.
         MaxMerge<SMOOTH> ma, ms;
+        DF win(0.f);
+        float wd = 0.f, wy = -INFINITY;
 #pragma unroll
         for (int j = 0; j < 3; ++j) {
             if (j >= nin) continue;
@@ -377,12 +427,23 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
                 const Seg as = seg_slew<UNIFORM>(c, lut, tbj, s);
                 const float dv = lookup<UNIFORM>(lut, tbj + rfo * kLutStride, as, bl, s, ld);
                 const float sv = lookup<UNIFORM>(lut, tbj + (2 + rfo) * kLutStride, as, bl, s, ld);
-                ma.add(sgn * fmaf(sc, dv, ain[j][rfi]), c.inv_gamma);
+                const float d = sc * dv;
+                const float y = sgn * (ain[j][rfi].hi + d);
+                if (y > wy) {
+                    wy = y;
+                    win = ain[j][rfi];
+                    wd = d;
+                }
+                ma.add(y, c.inv_gamma);
                 ms.add(sgn * (sc * sv), c.inv_gamma);
             }
         }
-        const float oa = sgn * ma.get(c.gamma), os = sgn * ms.get(c.gamma);
-        st_comp(c.at + (size_t)z * K + k, q, oa);
+        // the exact winner (no finite candidate: absent, -inf late / +inf
+        // early), plus the log-sum-exp excess when smoothed
+        const float ex = SMOOTH ? c.gamma * logf(ma.s) : 0.f;
+        const DF oa = wy > -INFINITY ? (win + wd) + sgn * ex : DF(-sgn * INFINITY);
+        const float os = sgn * ms.get(c.gamma);
+        st_comp_df(c.at + (size_t)z * K + k, q, oa);
         st_comp(c.slew + (size_t)z * K + k, q, os);
         if (pub) publish_fwd(c, par, z, k, q, oa, os);
     }
@@ -411,15 +472,14 @@ __device__ __forceinline__ EpItem ep_prep(const DevCtx &c, int e)
 // the driver's arrival and slew of the lane's corners are complete; lane q
 // reads component q of its first corner (returned; the caller's group_all
 // covers the quad)
-__device__ __forceinline__ bool ep_probe(const DevCtx &c, const EpItem &x, int par, int q, float &at0, float &sl0)
+__device__ __forceinline__ bool ep_probe(const DevCtx &c, const EpItem &x, int par, int q, DF &at0, float &sl0)
 {
     const int kq = corner_lane(c);
-    const float *r = reinterpret_cast<const float *>(fbox_at(c, par, x.d, kq));
-    at0 = ld_relaxed1(r + q);
-    sl0 = ld_relaxed1(r + 4 + q);
-    bool ok = at0 == at0 && sl0 == sl0;
+    at0 = ld_relaxed_df(fbox_a(c, par, x.d, kq)->v + q);
+    sl0 = ld_relaxed1(reinterpret_cast<const float *>(fbox_s(c, par, x.d, kq)) + q);
+    bool ok = real_df(at0) && sl0 == sl0;
     for (int k = kq + c.KL; k < c.K && ok; k += c.KL)
-        ok = complete(ld_relaxed4(fbox_at(c, par, x.d, k))) && complete(ld_relaxed4(fbox_at(c, par, x.d, k) + 1));
+        ok = complete_df(fbox_a(c, par, x.d, k)) && complete(ld_relaxed4(fbox_s(c, par, x.d, k)));
     return ok;
 }
 
@@ -427,7 +487,7 @@ __device__ __forceinline__ bool ep_probe(const DevCtx &c, const EpItem &x, int p
 // capture edge T - setup, hold 0 + hold; PO: T and 0), pin and endpoint
 // slacks (min over rise/fall) and violation flags.  Lane q: component q.
 template <bool WAIT>
-__device__ __forceinline__ void ep_run(const DevCtx &c, const EpItem &x, float at0, float sl0, int e, int q,
+__device__ __forceinline__ void ep_run(const DevCtx &c, const EpItem &x, DF at0, float sl0, int e, int q,
                                        int par)
 {
     const int K = c.K, p = x.p, d = x.d;
@@ -438,25 +498,26 @@ __device__ __forceinline__ void ep_run(const DevCtx &c, const EpItem &x, float a
         // requirement of state k: the exception tag's multiplier M (1 = the
         // default check, 0 = no check) -- setup capture edge at M * T
         const float M = c.Tg > 1 ? c.ep_mult[(size_t)e * c.Tg + k % c.Tg] : 1.f;
-        const float req = M == 0.f ? (q >= 2 ? INFINITY : -INFINITY)
-                                   : (q >= 2 ? (x.isD ? M * c.period - c.setup : M * c.period)
-                                             : (x.isD ? c.hold : 0.f));
-        float ad, sd;
+        const DF req = M == 0.f ? DF(q >= 2 ? INFINITY : -INFINITY)
+                                : (q >= 2 ? (x.isD ? df_mul(M, c.period) - c.setup : df_mul(M, c.period))
+                                          : DF(x.isD ? c.hold : 0.f));
+        DF ad;
+        float sd;
         if (!WAIT) {
-            ad = ld_state(c.at + (size_t)d * K + k, q);
+            ad = ld_state_df(c.at + (size_t)d * K + k, q);
             sd = ld_state(c.slew + (size_t)d * K + k, q);
         } else if (k == kq) {
             ad = at0;
             sd = sl0;
         } else {
-            ad = comp(ld_relaxed4(fbox_at(c, par, d, k)), q);
-            sd = comp(ld_relaxed4(fbox_at(c, par, d, k) + 1), q);
+            ad = ld_relaxed_df(fbox_a(c, par, d, k)->v + q);
+            sd = ld_relaxed1(reinterpret_cast<const float *>(fbox_s(c, par, d, k)) + q);
         }
         const float Dn = k != kq ? c.netD[(size_t)p * K + k] : x.Dn0, V = k != kq ? c.netV[(size_t)p * K + k] : x.V0;
-        const float A = ad + Dn;
-        st_comp(c.at + (size_t)p * K + k, q, A);
+        const DF A = ad + Dn;
+        st_comp_df(c.at + (size_t)p * K + k, q, A);
         st_comp(c.slew + (size_t)p * K + k, q, sqrtf(fmaf(sd, sd, V)));
-        st_comp(c.rat + (size_t)p * K + k, q, req);
+        st_comp_df(c.rat + (size_t)p * K + k, q, req);
         const float sk = q >= 2 ? req - A : A - req;
         st_comp(c.slack + (size_t)p * K + k, q, sk);
         const float worst = fminf(sk, __shfl_xor_sync(m, sk, 1));   // min over the two edges
@@ -478,7 +539,8 @@ struct BwdItem {
     // states of the lane's first corner, component q, loaded ahead (written
     // by the forward pass): arrival of the output, slew and arrival of each
     // input pin (CK: the slew of the rising component of this lane's el)
-    float az0, s0[3], a0[3];
+    DF az0, a0[3];
+    float s0[3];
 };
 
 __device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, const int *tkind, int g, int q)
@@ -494,14 +556,14 @@ __device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, co
     b.f0 = chk(c, c.fo_ptr[g], (long long)c.F + 1);
     b.f1 = chk(c, c.fo_ptr[g + 1], (long long)c.F + 1);
     b.ld0 = b.t >= 0 ? c.load[(size_t)b.z * K + kq] : 0.f;
-    b.az0 = ld_state(c.at + (size_t)b.z * K + kq, q);
+    b.az0 = ld_state_df(c.at + (size_t)b.z * K + kq, q);
     const int nread = b.kind == 1 ? 1 : b.kind == 0 ? b.nin : 0;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const bool on = j < nread;
         const size_t o = (size_t)(b.pin0 + j) * K + kq;
         b.s0[j] = on ? ld_state(c.slew + o, b.kind == 1 ? (q & 2) : q) : 0.f;
-        b.a0[j] = on ? ld_state(c.at + o, q) : 0.f;
+        b.a0[j] = on ? ld_state_df(c.at + o, q) : DF(0.f);
     }
     return b;
 }
@@ -513,38 +575,49 @@ __device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, co
 // folds them: R = min (late) / max (early) over the sinks of RAT - Elmore
 // delay, component q -- the output's required time, ready for bwd_run.
 // Endpoint sinks were set by the forward pass.
-__device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int par, int q, float &R)
+__device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int par, int q, DF &R)
 {
     const int K = c.K, kq = corner_lane(c);
     const bool late = q >= 2;
     bool ok = true;
-    float r = late ? INFINITY : -INFINITY;
+    // the fold in FP32 on the high parts; the winner's difference exactly
+    float rf = late ? INFINITY : -INFINITY;
+    DF rw(rf);
+    float rd = 0.f;
     for (int p0 = b.f0; p0 < b.f1; p0 += 4) {
         int s[4];
-        float m[4], nd[4];
+        DF m[4];
+        float nd[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) s[u] = p0 + u < b.f1 ? chk(c, __ldg(c.fo_pin + p0 + u), c.P) : -1;
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (s[u] < 0) continue;
-            m[u] = s[u] < c.ep_begin ? ld_relaxed1(reinterpret_cast<const float *>(rbox_at(c, par, s[u], kq)) + q)
-                                     : ld_state(c.rat + (size_t)s[u] * K + kq, q);
+            m[u] = s[u] < c.ep_begin ? ld_relaxed_df(rbox_at(c, par, s[u], kq)->v + q)
+                                     : ld_state_df(c.rat + (size_t)s[u] * K + kq, q);
             nd[u] = __ldg(c.netD + (size_t)s[u] * K + kq);
         }
 #pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (s[u] >= 0) ok = ok && real_df(m[u]);
+        if (!ok) return false;   // no arithmetic while waiting
+#pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (s[u] < 0) continue;
-            ok = ok && m[u] == m[u];
-            const float v = m[u] - nd[u];
-            r = late ? fminf(r, v) : fmaxf(r, v);
+            const float v = m[u].hi - nd[u];
+            if (late ? v < rf : v > rf) {
+                rf = v;
+                rw = m[u];
+                rd = nd[u];
+            }
         }
     }
     for (int p = b.f0; p < b.f1 && ok; ++p) {
         const int s = chk(c, __ldg(c.fo_pin + p), c.P);
         if (s < c.ep_begin)
-            for (int k = kq + c.KL; k < K && ok; k += c.KL) ok = complete(ld_relaxed4(rbox_at(c, par, s, k)));
+            for (int k = kq + c.KL; k < K && ok; k += c.KL) ok = complete_df(rbox_at(c, par, s, k));
     }
-    R = r;
+    R = isfinite(rf) ? rw - rd : DF(rf);
     return ok;
 }
 
@@ -553,7 +626,7 @@ __device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int
 // the first corner's output required time comes folded from bwd_probe (Rpre).
 template <bool UNIFORM, bool WAIT, class L>
 __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int *tsense, const BwdItem &b, int q,
-                                        int par, float Rpre)
+                                        int par, DF Rpre)
 {
     const int t = b.t, pin0 = b.pin0, z = b.z, K = c.K;
     const int el = q >> 1, rfi = q & 1;
@@ -563,24 +636,32 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
     for (int k = kq; k < K; k += c.KL) {
         const bool first = k == kq;
         // required time of the output, component q, over its net sinks
-        float R = el ? INFINITY : -INFINITY;
+        DF R(el ? INFINITY : -INFINITY);
         if (WAIT && first) {
             R = Rpre;
         } else {
+            float rf = el ? INFINITY : -INFINITY, rd = 0.f;
+            DF rw(rf);
             for (int p = b.f0; p < b.f1; ++p) {
                 const int s = chk(c, c.fo_pin[p], c.P);
-                const float rs = (WAIT && s < c.ep_begin) ? comp(ld_relaxed4(rbox_at(c, par, s, k)), q)
-                                                          : ld_state(c.rat + (size_t)s * K + k, q);
-                const float r = rs - c.netD[(size_t)s * K + k];
-                R = el ? fminf(R, r) : fmaxf(R, r);
+                const DF rs = (WAIT && s < c.ep_begin) ? ld_relaxed_df(rbox_at(c, par, s, k)->v + q)
+                                                       : ld_state_df(c.rat + (size_t)s * K + k, q);
+                const float nd = c.netD[(size_t)s * K + k];
+                const float v = rs.hi - nd;
+                if (el ? v < rf : v > rf) {
+                    rf = v;
+                    rw = rs;
+                    rd = nd;
+                }
             }
+            if (isfinite(rf)) R = rw - rd;
         }
-        st_comp(c.rat + (size_t)z * K + k, q, R);
-        const float Az = first ? b.az0 : ld_state(c.at + (size_t)z * K + k, q);
+        st_comp_df(c.rat + (size_t)z * K + k, q, R);
+        const DF Az = first ? b.az0 : ld_state_df(c.at + (size_t)z * K + k, q);
         st_comp(c.slack + (size_t)z * K + k, q, el ? R - Az : Az - R);
         if (t < 0) continue;
         // the output's required times of both edges at this lane's el
-        const float R0 = __shfl_sync(m, R, base + el * 2), R1 = __shfl_sync(m, R, base + el * 2 + 1);
+        const DF R0 = shfl_df(m, R, base + el * 2), R1 = shfl_df(m, R, base + el * 2 + 1);
         const float sc = __ldg(c.lut_scale + k);
         const float ld = first ? b.ld0 : c.load[(size_t)z * K + k];
         if (b.kind == 1) {   // CK: only the rising edge has an arc (to both edges of Q)
@@ -590,10 +671,11 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
             const Seg as = seg_slew<UNIFORM>(c, lut, tb, s), bl = seg_load<UNIFORM>(c, lut, tb, ld);
             const float d0 = sc * lookup<UNIFORM>(lut, tb, as, bl, s, ld);
             const float d1 = sc * lookup<UNIFORM>(lut, tb + kLutStride, as, bl, s, ld);
-            float Rc = el ? fminf(R0 - d0, R1 - d1) : fmaxf(R0 - d0, R1 - d1);
-            if (rfi == 1) Rc = el ? INFINITY : -INFINITY;
-            st_comp(c.rat + (size_t)ck * K + k, q, Rc);
-            const float Ac = first ? b.a0[0] : ld_state(c.at + (size_t)ck * K + k, q);
+            const float c0 = R0.hi - d0, c1 = R1.hi - d1;
+            DF Rc = (el ? c1 < c0 : c1 > c0) ? R1 - d1 : R0 - d0;
+            if (rfi == 1) Rc = DF(el ? INFINITY : -INFINITY);
+            st_comp_df(c.rat + (size_t)ck * K + k, q, Rc);
+            const DF Ac = first ? b.a0[0] : ld_state_df(c.at + (size_t)ck * K + k, q);
             st_comp(c.slack + (size_t)ck * K + k, q, el ? Rc - Ac : Ac - Rc);
             continue;
         }
@@ -606,16 +688,24 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
             const int tbj = tab_off(t, j, 0);
             const float s = first ? b.s0[j] : ld_state(c.slew + (size_t)a * K + k, q);
             const Seg as = seg_slew<UNIFORM>(c, lut, tbj, s);
-            float acc = el ? INFINITY : -INFINITY;
+            // FP32 choice between the (at most two) arcs, the winner exactly
+            float af = el ? INFINITY : -INFINITY, ad = 0.f;
+            DF aw(af);
 #pragma unroll
             for (int rfo = 0; rfo < 2; ++rfo) {
                 if (!arc_on(se, rfi, rfo)) continue;
-                const float dv = lookup<UNIFORM>(lut, tbj + rfo * kLutStride, as, bl, s, ld);
-                const float cand = (rfo ? R1 : R0) - sc * dv;
-                acc = el ? fminf(acc, cand) : fmaxf(acc, cand);
+                const float d = sc * lookup<UNIFORM>(lut, tbj + rfo * kLutStride, as, bl, s, ld);
+                const DF Ro = rfo ? R1 : R0;
+                const float v = Ro.hi - d;
+                if (el ? v < af : v > af) {
+                    af = v;
+                    aw = Ro;
+                    ad = d;
+                }
             }
-            st_comp(c.rat + (size_t)a * K + k, q, acc);
-            const float Aa = first ? b.a0[j] : ld_state(c.at + (size_t)a * K + k, q);
+            const DF acc = isfinite(af) ? aw - ad : DF(af);
+            st_comp_df(c.rat + (size_t)a * K + k, q, acc);
+            const DF Aa = first ? b.a0[j] : ld_state_df(c.at + (size_t)a * K + k, q);
             st_comp(c.slack + (size_t)a * K + k, q, el ? acc - Aa : Aa - acc);
             if (WAIT) publish_rat(c, par, a, k, q, acc);
         }

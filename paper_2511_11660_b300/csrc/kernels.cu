@@ -266,6 +266,23 @@ __device__ void arnoldi_delays(const DevCtx &c, int n, float f, int q_req, const
     }
 }
 
+// the net values of state k (a corner's first exception tag) copied to the
+// corner's other tags
+__device__ __forceinline__ void copy_to_tags(const DevCtx &c, int z, int f0, int f1, int k)
+{
+    const int K = c.K;
+    const float ld = c.load[(size_t)z * K + k];
+    for (int g = 1; g < c.Tg; ++g) c.load[(size_t)z * K + k + g] = ld;
+    for (int q = f0; q < f1; ++q) {
+        const int s = chk(c, __ldg(c.fo_pin + q), c.P);
+        const float Dn = c.netD[(size_t)s * K + k], Vn = c.netV[(size_t)s * K + k];
+        for (int g = 1; g < c.Tg; ++g) {
+            c.netD[(size_t)s * K + k + g] = Dn;
+            c.netV[(size_t)s * K + k + g] = Vn;
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
 {
     __shared__ int8_t s_par[kRcColNodes * kRcThreads];
@@ -273,10 +290,14 @@ __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
     __shared__ float s_A[kRcColNodes * kRcThreads], s_B[kRcColNodes * kRcThreads];
     const int t = threadIdx.x;
     const int K = c.K;
+    // one thread per (net, corner); the exception tags of a corner share
+    // its net values, computed at the corner's first state and copied
     const long long gk = (long long)blockIdx.x * kRcThreads + t;
-    if (gk >= (long long)c.I * K) return;
-    const int g = (int)(gk / K), k = (int)(gk % K);
-    const int n0 = chk(c, c.rc_ptr[g], c.NN + 1), n = chk(c, c.rc_ptr[g + 1], c.NN + 1) - n0;
+    if (gk >= (long long)c.I * c.Kc) return;
+    const int g = (int)(gk / c.Kc), kc = (int)(gk % c.Kc), k = kc * c.Tg;
+    const int n0 = chk(c, c.rc_ptr[g], c.NN + 1);
+    const int n = c.steiner ? chk(c, c.st_nlive[g], chk(c, c.rc_ptr[g + 1], c.NN + 1) - n0 + 1)
+                            : chk(c, c.rc_ptr[g + 1], c.NN + 1) - n0;
     const int f0 = chk(c, c.fo_ptr[g], (long long)c.F + 1), f1 = chk(c, c.fo_ptr[g + 1], (long long)c.F + 1);
     if (n <= 0) return;
     const bool col = n <= kRcColNodes;
@@ -298,7 +319,7 @@ __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
                 s_C[i * kRcThreads + t] = cv[i];
             }
     }
-    const size_t so = (size_t)k * c.NN + n0;   // global scratch: one copy per corner
+    const size_t so = (size_t)kc * c.NN + n0;   // global scratch: one copy per corner
     const ColRef A = col ? ColRef{s_A + t, kRcThreads} : ColRef{c.scratch_a + so, 1};
     const ColRef B = col ? ColRef{s_B + t, kRcThreads} : ColRef{c.scratch_b + so, 1};
     auto par = [&](int i) -> int { return col ? s_par[i * kRcThreads + t] : chk(c, __ldg(c.rc_parent + n0 + i), i); };
@@ -363,18 +384,8 @@ __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
             for (int q = f0; q < f1; ++q) Cn[chk(c, __ldg(c.fo_node + q), n)] += 1e3f * __ldg(c.fo_cap + q);
             arnoldi_delays(c, n, f, c.arnoldi_q, A, B, Cn, par, Rv, f0, f1, K, k);
         }
+        if (c.Tg > 1) copy_to_tags(c, z, f0, f1, k);
     }
-}
-
-__device__ __forceinline__ float2 pin_pos(const DevCtx &c, int p)
-{
-    const int pc = c.pin_cell[chk(c, p, c.P)];
-    if (pc >= 0) {
-        const int cc = chk(c, pc, c.C);
-        return make_float2(c.cell_xy[2 * (size_t)cc], c.cell_xy[2 * (size_t)cc + 1]);
-    }
-    const int q = -pc - 1;
-    return make_float2(c.port_xy[2 * (size_t)q], c.port_xy[2 * (size_t)q + 1]);
 }
 
 // Star trees from positions: segment R = r L, C = c L (half at each end),
@@ -388,7 +399,7 @@ __global__ void k_net_star(const DevCtx c)
     const int z = chk(c, item_out_pin(c, chk_type(c, c.item_type[g]), c.item_pin0[g]), c.P);
     const float2 pz = pin_pos(c, z);
     const int K = c.K;
-    for (int k = 0; k < K; ++k) {
+    for (int k = 0; k < K; k += c.Tg) {   // a corner's first exception tag, copied to the others
         const float f = __ldg(c.rc_scale + k);
         const float r = f * c.r_per_um, cc = f * c.c_per_um;
         float ld = 0.f;
@@ -404,6 +415,7 @@ __global__ void k_net_star(const DevCtx c)
             ld += fmaf(cc, L, cp);
         }
         c.load[(size_t)z * K + k] = 1e-3f * ld;
+        if (c.Tg > 1) copy_to_tags(c, z, f0, f1, k);
     }
 }
 
@@ -603,17 +615,36 @@ void launch_net_star(const DevCtx &c, cudaStream_t st) { k_net_star<<<nblk(c.I, 
 
 void launch_net_tree(const DevCtx &c, cudaStream_t st)
 {
-    if (c.I > 0) k_net_tree<<<nblk((long long)c.I * c.K, kRcThreads), kRcThreads, 0, st>>>(c);
+    if (c.I > 0) k_net_tree<<<nblk((long long)c.I * c.Kc, kRcThreads), kRcThreads, 0, st>>>(c);
+}
+
+void launch_net_phase(const DevCtx &c, const HostSched &h, cudaStream_t st)
+{
+    if (h.steiner) {
+        launch_net_steiner(c, st);
+        launch_net_tree(c, st);
+    } else if (h.placed) {
+        if (c.I > 0) launch_net_star(c, st);
+    } else if (h.rc) {
+        launch_net_tree(c, st);
+    }
+}
+
+__global__ void k_gather_i64(const int64_t *src, const int32_t *idx, int64_t *out, int n)
+{
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = src[idx[i]];
+}
+
+void launch_gather_i64(const int64_t *src, const int32_t *idx, int64_t *out, int n, cudaStream_t st)
+{
+    if (n > 0) k_gather_i64<<<nblk(n, 256), 256, 0, st>>>(src, idx, out, n);
 }
 
 void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev)
 {
     if (ev) cudaEventRecord(ev[0], st);
-    if (h.placed) {
-        if (c.I > 0) launch_net_star(c, st);
-    } else if (h.rc) {
-        launch_net_tree(c, st);
-    }
+    launch_net_phase(c, h, st);
     if (ev) cudaEventRecord(ev[1], st);
     const int tpb = h.threads > 0 ? h.threads : 128;
     for (int s = 0; s < h.S; ++s) {
@@ -644,6 +675,22 @@ void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cud
 void launch_gather_pins(const float4 *arr, const int32_t *gpu_of, float4 *out, int P, int K, cudaStream_t st)
 {
     if ((long long)P * K > 0) k_gather_pins<<<nblk((long long)P * K, 256), 256, 0, st>>>(arr, gpu_of, out, P, K);
+}
+
+// The same for a double-float array (arrival or required times), rounded to FP32.
+__global__ void k_gather_pins_d(const DF4 *__restrict__ arr, const int32_t *__restrict__ gpu_of, float4 *out, int P,
+                                int K)
+{
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (size_t)P * K) return;
+    const size_t p = i / K, k = i % K;
+    const DF4 v = arr[(size_t)gpu_of[p] * K + k];
+    out[i] = make_float4(to_f(v.v[0]), to_f(v.v[1]), to_f(v.v[2]), to_f(v.v[3]));
+}
+
+void launch_gather_pins_d(const DF4 *arr, const int32_t *gpu_of, float4 *out, int P, int K, cudaStream_t st)
+{
+    if ((long long)P * K > 0) k_gather_pins_d<<<nblk((long long)P * K, 256), 256, 0, st>>>(arr, gpu_of, out, P, K);
 }
 
 __global__ void k_collapse_tags(const DevCtx c, float *ep, uint8_t *viol)

@@ -14,6 +14,7 @@ struct HostSched {
     std::vector<int32_t> stage_ptr;   // host copy of the level offsets
     bool rc = false;                  // RC trees to sweep (tree mode with nodes)
     bool placed = false;
+    bool steiner = false;             // Steiner trees built from positions before the RC sweep
     int threads = 128;                // threads per block of the level kernels
     int n_red_chunks = 0;             // first-stage reduction blocks
     bool uniform = false;             // every table shares the same slew and load axes
@@ -35,6 +36,12 @@ void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cud
 // Net delay calculation: RC trees (one thread per net) or star trees.
 void launch_net_tree(const DevCtx &c, cudaStream_t st);
 void launch_net_star(const DevCtx &c, cudaStream_t st);
+// Steiner trees from positions (steiner.cu): writes the RC arrays the tree sweep reads.
+void launch_net_steiner(const DevCtx &c, cudaStream_t st);
+// The net phase of a pass: Steiner trees + RC sweep, star trees, or RC sweep.
+void launch_net_phase(const DevCtx &c, const HostSched &h, cudaStream_t st);
+// out[i] = src[idx[i]] (int64), n entries
+void launch_gather_i64(const int64_t *src, const int32_t *idx, int64_t *out, int n, cudaStream_t st);
 
 // Dataflow schedule: one persistent kernel per pass (see dataflow.cu).
 // dataflow_prepare sizes the persistent grids (at most `requested` blocks
@@ -89,6 +96,7 @@ void launch_resize(const DevCtx &c, const int32_t *item_of_cell, const int32_t *
                    int n, int32_t *item_type, cudaStream_t st);
 
 void launch_gather_pins(const float4 *arr, const int32_t *gpu_of, float4 *out, int P, int K, cudaStream_t st);
+void launch_gather_pins_d(const DF4 *arr, const int32_t *gpu_of, float4 *out, int P, int K, cudaStream_t st);
 // Endpoint slacks and violation flags per corner, min over the exception
 // tags: ep[0 .. E*Kc) setup, ep[E*Kc ..) hold; viol likewise.
 void launch_collapse_tags(const DevCtx &c, float *ep, uint8_t *viol, cudaStream_t st);

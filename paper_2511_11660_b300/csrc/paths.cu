@@ -7,7 +7,7 @@
 // the endpoint at the edge with the smaller late slack (ties: rise):
 //   a net sink steps to its net's driver with the same edge;
 //   a gate output steps to the input arc whose late arrival + NLDM delay
-//     (the forward pass's candidate, same arithmetic) is largest (ties: lower
+//     (the forward pass's FP32 candidate, same arithmetic) is largest (ties: lower
 //     input slot, then rise before fall);
 //   a flip-flop Q steps to its CK (rising edge);
 //   the trace stops at a PI or CK.
@@ -154,7 +154,7 @@ __device__ bool trace_step(const DevCtx &c, const PathJob &j, int k, int &p, int
             const float s = ld_state(c.slew + (size_t)a * K + k, 2 + rfi);
             const Seg as = seg_slew<UNIFORM>(c, lut, tbj, s);
             const float dv = lookup<UNIFORM>(lut, tbj + rf * kLutStride, as, bl, s, ld);
-            const float cand = fmaf(sc, dv, ld_state(c.at + (size_t)a * K + k, 2 + rfi));
+            const float cand = ld_state_df(c.at + (size_t)a * K + k, 2 + rfi).hi + sc * dv;
             if (cand > best || bp < 0) {
                 best = cand;
                 bp = a;
@@ -242,7 +242,7 @@ __global__ void k_path_write(const DevCtx c, const PathJob j)
         if (w < b) break;
         j.pin[w] = j.caller_pin[p];
         j.rf[w] = (int8_t)rf;
-        j.at[w] = ld_state(c.at + (size_t)p * c.K + k, 2 + rf);
+        j.at[w] = to_f(ld_state_df(c.at + (size_t)p * c.K + k, 2 + rf));
         --w;
         if (!trace_step<UNIFORM>(c, j, k, p, rf)) break;
     }

@@ -139,7 +139,14 @@ void build(const sta_design_desc *d, Plan &pl)
     REQUIRE(finite(d->gamma_ns) && d->gamma_ns >= 0, STA_EINVAL, "gamma_ns must be finite and >= 0");
     REQUIRE(d->net_model == STA_NET_ELMORE || d->net_model == STA_NET_ARNOLDI, STA_EINVAL,
             "net_model must be STA_NET_ELMORE or STA_NET_ARNOLDI");
-    REQUIRE(d->net_model == STA_NET_ELMORE || d->rc_ptr, STA_EINVAL, "STA_NET_ARNOLDI needs RC trees (rc_ptr)");
+    REQUIRE(d->wire_model == STA_WIRE_STAR || d->wire_model == STA_WIRE_STEINER, STA_EINVAL,
+            "wire_model must be STA_WIRE_STAR or STA_WIRE_STEINER");
+    REQUIRE(d->wire_model == STA_WIRE_STAR || !d->rc_ptr, STA_EINVAL,
+            "STA_WIRE_STEINER builds RC from positions (rc_ptr must be NULL)");
+    REQUIRE(d->net_model == STA_NET_ELMORE || d->rc_ptr || d->wire_model == STA_WIRE_STEINER, STA_EINVAL,
+            "STA_NET_ARNOLDI needs RC trees (rc_ptr) or Steiner trees");
+    REQUIRE(d->wire_model == STA_WIRE_STAR || d->gamma_ns == 0.f, STA_EINVAL,
+            "Steiner trees are not differentiable: gamma_ns must be 0");
     REQUIRE(d->net_model == STA_NET_ELMORE || (d->arnoldi_order >= 0 && d->arnoldi_order <= 3), STA_EINVAL,
             "arnoldi_order must be in 0..3");
     pl.net_model = d->net_model;
@@ -152,6 +159,15 @@ void build(const sta_design_desc *d, Plan &pl)
     pl.placed = (d->rc_ptr == nullptr);
     pl.r_per_um = d->r_per_um;
     pl.c_per_um = d->c_per_um;
+    pl.steiner = pl.placed && d->wire_model == STA_WIRE_STEINER;
+    pl.n_nets = N;
+    if (pl.steiner) {
+        REQUIRE(finite(d->r_per_um_y) && finite(d->c_per_um_y), STA_EINVAL, "unit R/C along y must be finite");
+        pl.r_per_um_y = d->r_per_um_y > 0.f ? d->r_per_um_y : d->r_per_um;
+        pl.c_per_um_y = d->c_per_um_y > 0.f ? d->c_per_um_y : d->c_per_um;
+        REQUIRE(d->net_model == STA_NET_ELMORE || (d->r_per_um > 0.f && pl.r_per_um_y > 0.f), STA_EINVAL,
+                "STA_NET_ARNOLDI on Steiner trees needs unit R > 0");
+    }
     if (P > 0) REQUIRE(d->pin_role != nullptr, STA_EINVAL, "pin_role is NULL");
     if (C > 0) REQUIRE(d->cell_type && d->cell_pin_ptr && d->cell_pin, STA_EINVAL, "cell arrays NULL");
     if (N > 0) REQUIRE(d->net_pin_ptr && d->net_pin, STA_EINVAL, "net arrays NULL");
@@ -233,6 +249,8 @@ void build(const sta_design_desc *d, Plan &pl)
                             "net %d: RC node %d parent %d not before it", n, i - b, d->rc_parent[i]);
                 REQUIRE(finite(d->rc_R[i]) && d->rc_R[i] >= 0 && finite(d->rc_C[i]) && d->rc_C[i] >= 0,
                         STA_EINVAL, "net %d: negative or non-finite R/C at node %d", n, i - b);
+                if (i > b && d->net_model == STA_NET_ARNOLDI)
+                    REQUIRE(d->rc_R[i] > 0, STA_EINVAL, "net %d: STA_NET_ARNOLDI needs R > 0 (node %d)", n, i - b);
             }
             REQUIRE(d->rc_pin_node[d->net_pin_ptr[n]] == 0, STA_EINVAL, "net %d: driver must sit on node 0", n);
             for (int32_t k = d->net_pin_ptr[n] + 1; k < d->net_pin_ptr[n + 1]; ++k)
@@ -243,6 +261,17 @@ void build(const sta_design_desc *d, Plan &pl)
     } else {
         for (int64_t i = 0; i < 2LL * C; ++i)
             REQUIRE(finite(d->cell_xy[i]), STA_EINVAL, "cell_xy[%lld] not finite", (long long)i);
+        if (pl.steiner) {   // integer nm coordinates must fit: |x|, |y| <= 1e6 um
+            for (int64_t i = 0; i < 2LL * C; ++i)
+                REQUIRE(std::fabs(d->cell_xy[i]) <= 1e6f, STA_EINVAL, "cell_xy[%lld] beyond 1e6 um", (long long)i);
+            if (d->port_xy)
+                for (int32_t p = 0; p < P; ++p)
+                    if (d->pin_role[p] == kPinPI || d->pin_role[p] == kPinPO)
+                        REQUIRE(finite(d->port_xy[2 * (size_t)p]) && finite(d->port_xy[2 * (size_t)p + 1]) &&
+                                    std::fabs(d->port_xy[2 * (size_t)p]) <= 1e6f &&
+                                    std::fabs(d->port_xy[2 * (size_t)p + 1]) <= 1e6f,
+                                STA_EINVAL, "port_xy of pin %d not finite or beyond 1e6 um", p);
+        }
     }
 
     // ---- items: primary inputs (ascending pin id), then cells
@@ -394,11 +423,27 @@ void build(const sta_design_desc *d, Plan &pl)
     };
     pl.fo_ptr.assign(I + 1, 0);
     pl.rc_ptr.assign(I + 1, 0);
+    pl.net_of_item.assign(I, -1);
+    if (pl.steiner) {
+        pl.st_node_ptr.assign(I + 1, 0);
+        pl.st_adj_ptr.assign(I + 1, 0);
+    }
     for (int32_t g = 0; g < I; ++g) {
         const int32_t n = drv_net[out_pin_of_item[g]];
-        pl.fo_ptr[g + 1] = pl.fo_ptr[g] + (n >= 0 ? d->net_pin_ptr[n + 1] - d->net_pin_ptr[n] - 1 : 0);
+        pl.net_of_item[g] = n;
+        const int32_t m = n >= 0 ? d->net_pin_ptr[n + 1] - d->net_pin_ptr[n] - 1 : 0;   // sinks
+        pl.fo_ptr[g + 1] = pl.fo_ptr[g] + m;
         if (!pl.placed) pl.rc_ptr[g + 1] = pl.rc_ptr[g] + (n >= 0 ? d->rc_ptr[n + 1] - d->rc_ptr[n] : 0);
+        if (pl.steiner) {
+            // tree capacity 2 m nodes (m + 1 pins, at most m - 1 Steiner points);
+            // working storage 3 (m + 1) nodes, bitset rows for nets of <= 64 pins
+            const int64_t w = m > 0 ? 3LL * (m + 1) : 0;
+            pl.rc_ptr[g + 1] = pl.rc_ptr[g] + 2 * m;
+            pl.st_node_ptr[g + 1] = pl.st_node_ptr[g] + w;
+            pl.st_adj_ptr[g + 1] = pl.st_adj_ptr[g] + (m > 0 && m + 1 <= kSteinerMaxPins ? w * ((w + 31) / 32) : 0);
+        }
     }
+    if (pl.steiner) pl.NN = pl.rc_ptr[I];
     pl.F = pl.fo_ptr[I];
     pl.fo_pin.resize(pl.F);
     pl.fo_node.resize(pl.F);
@@ -477,7 +522,7 @@ void build(const sta_design_desc *d, Plan &pl)
     }
     // ---- RC nets too large for the shared-memory sweep
     pl.n_big_nets = 0;
-    if (!pl.placed)
+    if (!pl.placed || pl.steiner)
         for (int32_t g = 0; g < I; ++g) pl.n_big_nets += pl.rc_ptr[g + 1] - pl.rc_ptr[g] > kColNodes;
     // ---- arc count
     pl.cell_arcs = 0;
@@ -545,6 +590,8 @@ sta_status build_batch_plan(const sta_design_desc *const *descs, int32_t n, Plan
                         di.pi_at_ns == d0.pi_at_ns && di.pi_slew_ns == d0.pi_slew_ns &&
                         di.gamma_ns == d0.gamma_ns && di.r_per_um == d0.r_per_um && di.c_per_um == d0.c_per_um &&
                         di.net_model == d0.net_model && di.arnoldi_order == d0.arnoldi_order &&
+                        di.wire_model == d0.wire_model && di.r_per_um_y == d0.r_per_um_y &&
+                        di.c_per_um_y == d0.c_per_um_y &&
                         (K < 1 || K > 16 || (same_array(di.lut_scale, d0.lut_scale, (size_t)K) &&
                                              same_array(di.rc_scale, d0.rc_scale, (size_t)K)));
         if (!ok) {

@@ -20,6 +20,7 @@ constexpr int kNldm = 7;          // 7x7 NLDM tables
 constexpr int kMaxSlot = 3;       // at most three inputs per cell
 constexpr int kTabStride = 80;    // floats per packed table (see packLut)
 constexpr int kColNodes = 16;     // RC nets up to this many nodes are swept in shared memory
+constexpr int kSteinerMaxPins = 64;  // nets of more pins keep the rectilinear MST (no Steiner points)
 
 enum { kPinPI = 0, kPinPO = 1, kPinIN = 2, kPinOUT = 3, kPinD = 4, kPinCK = 5, kPinQ = 6 };
 enum { kSenseNone = -1, kSensePos = 0, kSenseNeg = 1, kSenseNon = 2, kSenseRise = 3 };
@@ -33,6 +34,12 @@ struct Plan {
     int32_t max_width = 0;
     int32_t n_designs = 1;
     bool placed = false;
+    bool steiner = false;                    // positions mode with Steiner trees (STA_WIRE_STEINER)
+    float r_per_um_y = 0.f, c_per_um_y = 0.f; // Steiner: unit R/C along y (the x values when <= 0 on input)
+    std::vector<int64_t> st_node_ptr;        // [I + 1] Steiner working nodes per item: 3 n (n = sinks + 1), 0 without sinks
+    std::vector<int64_t> st_adj_ptr;         // [I + 1] adjacency bitset words per item: 3 n x ceil(3 n / 32) (n <= 64)
+    std::vector<int32_t> net_of_item;        // [I] caller net driven by the item, -1 if none
+    int32_t n_nets = 0;
     float gamma = 0.f;
     int32_t net_model = STA_NET_ELMORE;      // net delay calculator
     int32_t Kc = 1, Tg = 1;                  // corners and exception tags; K = Kc * Tg states

@@ -32,6 +32,8 @@ struct sta_ctx {
     int32_t *d_resize_tmp = nullptr;
     int32_t resize_cap = 0;
     int32_t *d_rc_src = nullptr;
+    int32_t *d_item_of_net = nullptr;   // Steiner contexts: driving item of every caller net
+    int64_t *d_wl_tmp = nullptr;        // staging of sta_get_net_wirelength to the host
     float *d_rc_tmp = nullptr;
     float4 *d_gather_tmp = nullptr;
     cudaGraph_t graph = nullptr;
@@ -188,9 +190,9 @@ sta_status create_from_plan(sta_ctx *c, int device)
         c->d_rc_src = upload(c, src);
     }
     const size_t PK = (size_t)pl.P * pl.K;
-    d.at = dev_alloc<float4>(c, PK);
+    d.at = dev_alloc<sta::DF4>(c, PK);
     d.slew = dev_alloc<float4>(c, PK);
-    d.rat = dev_alloc<float4>(c, PK);
+    d.rat = dev_alloc<sta::DF4>(c, PK);
     d.slack = dev_alloc<float4>(c, PK);
     d.netD = dev_alloc<float>(c, PK);
     d.netV = dev_alloc<float>(c, PK);
@@ -223,16 +225,48 @@ sta_status create_from_plan(sta_ctx *c, int device)
     }
     d.err = dev_alloc<unsigned>(c, 1);
     CK(cudaMemset(d.err, 0, sizeof(unsigned)));
+    if (pl.steiner) {
+        // Steiner trees: the RC arrays are written on the device at every update
+        d.steiner = 1;
+        d.r_per_um_y = pl.r_per_um_y;
+        d.c_per_um_y = pl.c_per_um_y;
+        const size_t NN = std::max<int64_t>(1, pl.NN), WN = std::max<int64_t>(1, pl.st_node_ptr[pl.I]);
+        d.st_parent = dev_alloc<int32_t>(c, NN);
+        d.st_R = dev_alloc<float>(c, NN);
+        d.st_C = dev_alloc<float>(c, NN);
+        d.st_fo_node = dev_alloc<int32_t>(c, std::max<int64_t>(1, pl.F));
+        d.st_nlive = dev_alloc<int32_t>(c, std::max(1, pl.I));
+        d.st_wl = dev_alloc<int64_t>(c, std::max(1, pl.I));
+        CK(cudaMemset(d.st_nlive, 0, std::max(1, pl.I) * sizeof(int32_t)));
+        CK(cudaMemset(d.st_wl, 0, std::max(1, pl.I) * sizeof(int64_t)));
+        CK(cudaMemset(d.st_fo_node, 0, std::max<int64_t>(1, pl.F) * sizeof(int32_t)));
+        d.st_node_ptr = upload(c, pl.st_node_ptr);
+        d.st_adj_ptr = upload(c, pl.st_adj_ptr);
+        d.st_x = dev_alloc<long long>(c, WN);
+        d.st_y = dev_alloc<long long>(c, WN);
+        d.st_key = dev_alloc<long long>(c, WN);
+        d.st_aux = dev_alloc<int32_t>(c, 3 * WN);
+        d.st_adj = dev_alloc<unsigned>(c, std::max<int64_t>(1, pl.st_adj_ptr[pl.I]));
+        d.rc_parent = d.st_parent;
+        d.rc_R = d.st_R;
+        d.rc_C = d.st_C;
+        d.fo_node = d.st_fo_node;
+        std::vector<int32_t> item_of_net(std::max(1, pl.n_nets), -1);
+        for (int32_t g = 0; g < pl.I; ++g)
+            if (pl.net_of_item[g] >= 0) item_of_net[pl.net_of_item[g]] = g;
+        c->d_item_of_net = upload(c, item_of_net);
+    }
     if (pl.n_big_nets > 0) {
-        d.scratch_a = dev_alloc<float>(c, (size_t)pl.NN * pl.K);
-        d.scratch_b = dev_alloc<float>(c, (size_t)pl.NN * pl.K);
-        if (pl.net_model == STA_NET_ARNOLDI) d.scratch_c = dev_alloc<float>(c, (size_t)pl.NN * pl.K);
+        d.scratch_a = dev_alloc<float>(c, (size_t)pl.NN * pl.Kc);
+        d.scratch_b = dev_alloc<float>(c, (size_t)pl.NN * pl.Kc);
+        if (pl.net_model == STA_NET_ARNOLDI) d.scratch_c = dev_alloc<float>(c, (size_t)pl.NN * pl.Kc);
     }
     HostSched &h = c->hs;
     h.S = pl.S;
     h.stage_ptr = pl.stage_ptr;
     h.rc = !pl.placed && pl.NN > 0;
     h.placed = pl.placed;
+    h.steiner = pl.steiner;
     h.threads = 128;
     h.uniform = pl.uniform_axes;
     if (pl.uniform_axes) {
@@ -247,12 +281,14 @@ sta_status create_from_plan(sta_ctx *c, int device)
     }
     h.T = pl.T;
     // dataflow schedule: parity mailboxes (all NaN), epoch state, work chunks
-    d.fbox_len = 2 * 2 * (size_t)pl.P * pl.K;
+    d.fbox_len = 2 * (size_t)pl.P * pl.K;
     d.rbox_len = 2 * (size_t)pl.P * pl.K;
-    d.fbox = dev_alloc<float4>(c, d.fbox_len);
-    d.rbox = dev_alloc<float4>(c, d.rbox_len);
-    CK(cudaMemset(d.fbox, 0xFF, std::max<size_t>(1, d.fbox_len) * sizeof(float4)));
-    CK(cudaMemset(d.rbox, 0xFF, std::max<size_t>(1, d.rbox_len) * sizeof(float4)));
+    d.fbox_a = dev_alloc<sta::DF4>(c, d.fbox_len);
+    d.fbox_s = dev_alloc<float4>(c, d.fbox_len);
+    d.rbox = dev_alloc<sta::DF4>(c, d.rbox_len);
+    CK(cudaMemset(d.fbox_a, 0xFF, std::max<size_t>(1, d.fbox_len) * sizeof(sta::DF4)));   // all NaN
+    CK(cudaMemset(d.fbox_s, 0xFF, std::max<size_t>(1, d.fbox_len) * sizeof(float4)));
+    CK(cudaMemset(d.rbox, 0xFF, std::max<size_t>(1, d.rbox_len) * sizeof(sta::DF4)));
     d.df_state = dev_alloc<unsigned>(c, sta::kDfStateWords);
     CK(cudaMemset(d.df_state, 0, sta::kDfStateWords * sizeof(unsigned)));
     d.stage_ptr = upload(c, pl.stage_ptr);
@@ -328,10 +364,11 @@ int32_t launches_per_update(const sta_ctx *c)
 {
     const Plan &pl = c->plan;
     int32_t n = 0;
-    if (pl.placed) n += pl.I > 0;
+    if (pl.steiner) n += 2 * (pl.I > 0);        // Steiner trees, then the RC sweep
+    else if (pl.placed) n += pl.I > 0;
     else n += pl.NN > 0 && pl.I > 0;
     if (c->schedule == STA_SCHED_DATAFLOW) {
-        n += 1;                                  // epoch / counter reset
+        n += 2;                                  // mailbox recovery, epoch / counter reset
         n += c->dc.n_fwd_chunks > 0;
         n += c->dc.n_bwd_chunks > 0;
         n += (c->hs.n_red_chunks > 0) + 1;       // two-stage reduction
@@ -655,11 +692,11 @@ namespace {
 struct TuneKey {
     int device;
     int64_t P, I, S, K, T, E;
-    bool uniform, placed, smooth;
+    bool uniform, placed, smooth, steiner;
     bool operator<(const TuneKey &o) const
     {
-        return std::tie(device, P, I, S, K, T, E, uniform, placed, smooth) <
-               std::tie(o.device, o.P, o.I, o.S, o.K, o.T, o.E, o.uniform, o.placed, o.smooth);
+        return std::tie(device, P, I, S, K, T, E, uniform, placed, smooth, steiner) <
+               std::tie(o.device, o.P, o.I, o.S, o.K, o.T, o.E, o.uniform, o.placed, o.smooth, o.steiner);
     }
 };
 struct TuneChoice {
@@ -677,7 +714,8 @@ sta_status sta_autotune(sta_ctx *c, void *stream, int32_t trials, int32_t force,
     if (!c) return STA_EINVAL;
     if (trials < 1) trials = 1;
     const Plan &pl = c->plan;
-    const TuneKey key{c->device, pl.P, pl.I, pl.S, pl.K, pl.T, pl.E, pl.uniform_axes, pl.placed, pl.gamma > 0.f};
+    const TuneKey key{c->device, pl.P, pl.I, pl.S, pl.K, pl.T, pl.E, pl.uniform_axes, pl.placed, pl.gamma > 0.f,
+                      pl.steiner};
     TuneChoice best{-1, 0, 0.f, -1};
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
@@ -842,19 +880,23 @@ sta_status sta_get_pin_state(sta_ctx *c, int32_t which, float *out, sta_mem mem,
 {
     if (!c || !out) return STA_EINVAL;
     if (!c->updated) return fail(c, STA_ESTATE, "no analysis yet");
-    const float4 *src = which == STA_AT ? c->dc.at : which == STA_SLEW ? c->dc.slew : which == STA_RAT ? c->dc.rat
-                        : which == STA_SLACK ? c->dc.slack : nullptr;
-    if (!src) return fail(c, STA_EINVAL, "unknown array id");
+    const sta::DF4 *srcd = which == STA_AT ? c->dc.at : which == STA_RAT ? c->dc.rat : nullptr;
+    const float4 *src = which == STA_SLEW ? c->dc.slew : which == STA_SLACK ? c->dc.slack : nullptr;
+    if (!src && !srcd) return fail(c, STA_EINVAL, "unknown array id");
     try {
         CK(cudaSetDevice(c->device));
         cudaStream_t st = as_stream(stream);
         const size_t PK = (size_t)c->plan.P * c->plan.K;
+        auto gather = [&](float4 *dst) {
+            if (srcd) sta::launch_gather_pins_d(srcd, c->d_gpu_of, dst, c->plan.P, c->plan.K, st);
+            else sta::launch_gather_pins(src, c->d_gpu_of, dst, c->plan.P, c->plan.K, st);
+        };
         if (mem == STA_DEVICE) {
-            sta::launch_gather_pins(src, c->d_gpu_of, reinterpret_cast<float4 *>(out), c->plan.P, c->plan.K, st);
+            gather(reinterpret_cast<float4 *>(out));
             CK(cudaGetLastError());
         } else {
             if (!c->d_gather_tmp) c->d_gather_tmp = dev_alloc<float4>(c, PK);
-            sta::launch_gather_pins(src, c->d_gpu_of, c->d_gather_tmp, c->plan.P, c->plan.K, st);
+            gather(c->d_gather_tmp);
             CK(cudaMemcpyAsync(out, c->d_gather_tmp, PK * sizeof(float4), cudaMemcpyDeviceToHost, st));
             CK(cudaStreamSynchronize(st));
         }
@@ -1006,6 +1048,31 @@ sta_status sta_set_positions(sta_ctx *c, const float *cell_xy, sta_mem mem, void
         CK(cudaMemcpyAsync(const_cast<float *>(c->dc.cell_xy), cell_xy, 2 * (size_t)c->plan.C * sizeof(float), kind,
                            as_stream(stream)));
         if (mem == STA_HOST) CK(cudaStreamSynchronize(as_stream(stream)));
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    return STA_OK;
+}
+
+sta_status sta_get_net_wirelength(sta_ctx *c, int64_t *wl_nm, sta_mem mem, void *stream)
+{
+    if (!c || !wl_nm) return STA_EINVAL;
+    if (!c->plan.steiner) return fail(c, STA_ESTATE, "context does not build Steiner trees");
+    if (!c->updated) return fail(c, STA_ESTATE, "sta_get_net_wirelength before sta_update_timing");
+    try {
+        CK(cudaSetDevice(c->device));
+        cudaStream_t st = as_stream(stream);
+        const int32_t N = c->plan.n_nets;
+        if (N == 0) return STA_OK;
+        if (mem == STA_DEVICE) {
+            sta::launch_gather_i64(c->dc.st_wl, c->d_item_of_net, wl_nm, N, st);
+        } else {
+            if (!c->d_wl_tmp) c->d_wl_tmp = dev_alloc<int64_t>(c, N);
+            sta::launch_gather_i64(c->dc.st_wl, c->d_item_of_net, c->d_wl_tmp, N, st);
+            CK(cudaMemcpyAsync(wl_nm, c->d_wl_tmp, (size_t)N * sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+            CK(cudaStreamSynchronize(st));
+        }
+        CK(cudaGetLastError());
     } catch (const CudaFail &f) {
         return from_cuda(c, f);
     }

@@ -22,6 +22,7 @@ HOST, DEVICE = 0, 1
 AT, SLEW, RAT, SLACK = 0, 1, 2, 3
 SCHED_LEVEL, SCHED_DATAFLOW, SCHED_COOP = 0, 1, 2
 NET_ELMORE, NET_ARNOLDI = 0, 1
+WIRE_STAR, WIRE_STEINER = 0, 1
 
 
 class StaError(RuntimeError):
@@ -49,7 +50,8 @@ class sta_design_desc(C.Structure):
                 ("lut_scale", C.c_void_p), ("rc_scale", C.c_void_p), ("gamma_ns", C.c_float),
                 ("net_model", C.c_int32), ("arnoldi_order", C.c_int32), ("n_exc", C.c_int32),
                 ("exc_from_ptr", C.c_void_p), ("exc_from", C.c_void_p), ("exc_to_ptr", C.c_void_p),
-                ("exc_to", C.c_void_p), ("exc_action", C.c_void_p), ("exc_mult", C.c_void_p)]
+                ("exc_to", C.c_void_p), ("exc_action", C.c_void_p), ("exc_mult", C.c_void_p),
+                ("wire_model", C.c_int32), ("r_per_um_y", C.c_float), ("c_per_um_y", C.c_float)]
 
 
 class sta_plan_info(C.Structure):
@@ -102,6 +104,7 @@ SIGNATURES = {
     "sta_report_slack_design": (C.c_int, [_V, C.c_int32, _V, _P]),
     "sta_get_pin_state": (C.c_int, [_V, C.c_int32, _P, C.c_int, _V]),
     "sta_get_endpoint_slack": (C.c_int, [_V, _P, _P, _P, _P, C.c_int, _V]),
+    "sta_get_net_wirelength": (C.c_int, [_V, _P, C.c_int, _V]),
     "sta_report_paths": (C.c_int, [_V, C.c_int32, C.c_int32, C.c_int32, C.c_float, _P, _P, _P, _P, _P, _P, _P, _P,
                                    C.c_int32, C.c_int, _V]),
     "sta_backward": (C.c_int, [_V, C.c_double, C.c_double, _P, _P, _P, C.c_int, _V]),
@@ -193,7 +196,8 @@ class Design:
             _ptr(a["lut_scale"]), _ptr(a["rc_scale"]), float(d.get("gamma_ns", 0.0)),
             int(d.get("net_model", 0)), int(d.get("arnoldi_order", 0)),
             0 if a["exc_action"] is None else len(a["exc_action"]), _ptr(a["exc_from_ptr"]), _ptr(a["exc_from"]),
-            _ptr(a["exc_to_ptr"]), _ptr(a["exc_to"]), _ptr(a["exc_action"]), _ptr(a["exc_mult"]))
+            _ptr(a["exc_to_ptr"]), _ptr(a["exc_to"]), _ptr(a["exc_action"]), _ptr(a["exc_mult"]),
+            int(d.get("wire_model", 0)), float(d.get("r_per_um_y", 0.0)), float(d.get("c_per_um_y", 0.0)))
 
     @property
     def n_pins(self):
@@ -368,6 +372,18 @@ class Context:
             b, e = ptr[i], ptr[i + 1]
             out.append({"endpoint": int(ep[i]), "slack": float(slack[i]), "pins": pin[b:e].copy(),
                         "rf": rf[b:e].copy(), "at": at[b:e].copy()})
+        return out
+
+    def get_net_wirelength(self, device: bool = False, stream=None):
+        """Steiner wirelength (int64 nm) of every net at the last update, in
+        caller net order; a torch CUDA tensor with ``device``, else numpy."""
+        n = self.stats()["n_nets"]
+        if device:
+            import torch
+            out = torch.empty(n, dtype=torch.int64, device=torch.device("cuda", self.device))
+        else:
+            out = np.empty(n, np.int64)
+        self._chk(self.lib.sta_get_net_wirelength(self.h, _ptr(out), DEVICE if device else HOST, _stream(stream)))
         return out
 
     def get_endpoint_slack(self, device: bool = False, stream=None):

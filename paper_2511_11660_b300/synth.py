@@ -123,7 +123,8 @@ def make_design(n_cells: int, depth: int, seed: int = 0, lib: dict | None = None
                 dff_frac: float = 0.10, pi_frac: float = 0.02, po_frac: float = 0.2, placed: bool = False,
                 die_um: float = 1000.0, r_per_um: float = 0.1, c_per_um: float = 0.2,
                 period_ns: float = 1.0, n_corners: int = 1, lut_scale=None, rc_scale=None,
-                gamma_ns: float = 0.0, base_types_only: bool = True) -> dict:
+                gamma_ns: float = 0.0, base_types_only: bool = True, placement: str = "uniform",
+                local_um: float = 20.0) -> dict:
     """A random levelised netlist of ``n_cells`` cells and logic depth ``depth``.
 
     * 10% of cells are DFFs; the rest draw uniformly from the 7 gate types.
@@ -139,7 +140,12 @@ def make_design(n_cells: int, depth: int, seed: int = 0, lib: dict | None = None
     * RC per net: ``rc_nodes`` inclusive node-count range, parent of node i
       uniform in [0, i), R ~ U(5, 50) Ohm (root 0), C ~ U(0.5, 5) fF; each
       sink sits on a uniform non-root node.
-    * ``placed`` draws cell and port positions uniformly in the die.
+    * ``placed`` draws cell and port positions uniformly in the die
+      (``placement="uniform"``: every net spans the die, so path delays run
+      to ~100 ns); ``placement="local"`` then places, level by level, each
+      gate at the mean of its input drivers plus N(0, local_um^2) per axis
+      and each primary output at its driver plus the same noise (flip-flops
+      and primary inputs stay uniform), so nets are tens of um long.
     Cell ids are shuffled, so id order says nothing about level order."""
     rng = np.random.default_rng(seed)
     if lib is None:
@@ -276,6 +282,25 @@ def make_design(n_cells: int, depth: int, seed: int = 0, lib: dict | None = None
     port_xy = np.zeros((n_pins, 2), np.float32)
     ports = np.nonzero((pin_role == PI) | (pin_role == PO))[0]
     port_xy[ports] = rng.uniform(0.0, die_um, size=(len(ports), 2)).astype(np.float32)
+    if placement == "local":
+        # driver positions: PIs (ports), DFF Qs (their cells), gate outputs (their cells)
+        cell_of_lin = perm                                     # linear cell -> cell id
+        drv_xy = np.concatenate([port_xy[n_cell_pins:n_cell_pins + n_pi],
+                                 cell_xy[cell_of_lin[:n_dff]],
+                                 cell_xy[cell_of_lin[n_dff:]]]).astype(np.float64)
+        noise = rng.normal(0.0, local_um, size=(n_comb + n_po, 2))
+        gate_first = np.cumsum(nin_comb) - nin_comb
+        for k in range(1, depth + 1):
+            gs = np.nonzero(comb_level == k)[0]
+            if len(gs) == 0:
+                continue
+            acc = np.zeros((len(gs), 2))
+            for j in range(3):
+                has = nin_comb[gs] > j
+                acc[has] += drv_xy[slot_drv[gate_first[gs[has]] + j]]
+            drv_xy[n_pi + n_dff + gs] = np.clip(acc / nin_comb[gs][:, None] + noise[gs], 0.0, die_um)
+        cell_xy[cell_of_lin[n_dff:]] = drv_xy[n_pi + n_dff:].astype(np.float32)
+        port_xy[po_pin] = np.clip(drv_xy[lonely] + noise[n_comb:], 0.0, die_um).astype(np.float32)
     d.update(cell_xy=cell_xy.reshape(-1), port_xy=port_xy.reshape(-1), r_per_um=r_per_um,
              c_per_um=c_per_um, placed=placed)
     if placed:
@@ -340,8 +365,11 @@ def workload(name: str, seed: int = 0, **over) -> dict:
     """Named workloads: 'tiny' (2,000 cells, depth 30, RC trees of 2-12
     nodes), 'scale' (1M cells, depth 150, 2-10 nodes), 'mid' (the same at
     200k cells, for profiler captures), 'diff' (200k cells
-    placed in a 1000 um die, star RC from positions, gamma 0.01 ns) and
-    'large' (10M cells, depth 400, placed, 4 corners, 2 drive strengths)."""
+    placed in a 1000 um die, star RC from positions, gamma 0.01 ns),
+    'steiner' / 'steiner_mid' (1M / 200k cells placed locally in a 1000 um
+    die, Steiner-tree RC from positions) and 'large' (10M cells, depth 400,
+    placed, 4 corners, 2 drive strengths)."""
+    steiner = name in ("steiner", "steiner_mid")
     if name == "tiny":
         kw = dict(n_cells=2000, depth=30, rc_nodes=(2, 12))
     elif name == "scale":
@@ -350,6 +378,8 @@ def workload(name: str, seed: int = 0, **over) -> dict:
         kw = dict(n_cells=200_000, depth=150, rc_nodes=(2, 10))
     elif name == "diff":
         kw = dict(n_cells=200_000, depth=150, rc_nodes=(2, 10), placed=True, gamma_ns=0.01)
+    elif steiner:
+        kw = dict(n_cells=1_000_000 if name == "steiner" else 200_000, depth=150, placed=True, placement="local")
     elif name == "large":
         ls, rs = lut_corners()
         kw = dict(n_cells=10_000_000, depth=400, rc_nodes=(2, 10), placed=True, gamma_ns=0.01,
@@ -357,7 +387,10 @@ def workload(name: str, seed: int = 0, **over) -> dict:
     else:
         raise ValueError(name)
     kw.update(over)
-    return make_design(seed=seed, **kw)
+    d = make_design(seed=seed, **kw)
+    if steiner:
+        d["wire_model"] = 1   # rectilinear Steiner trees rebuilt from the positions at every update
+    return d
 
 
 def batch_workload(seed: int = 0, n_designs: int = 64, lo: int = 5_000, hi: int = 500_000, depth: int = 150,
