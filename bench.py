@@ -377,8 +377,7 @@ def run_ours(a, dist: Dist):
     # ---- Steiner-tree RC from positions: a placed 1M-cell design, trees rebuilt every update
     del ctx
     torch.cuda.empty_cache()
-    ds = synth.make_design(1_000_000, 150, seed=a.seed, placed=True)
-    ds.update(wire_model=sta.WIRE_STEINER)
+    ds = synth.workload("steiner", seed=a.seed)
     ctx = sta.Context(ds, device=dev)
     ctx.set_schedule({v: k for k, v in sched_names.items()}[schedule], 0)
     ctx.set_clock(0.0)
@@ -400,8 +399,9 @@ def run_ours(a, dist: Dist):
     out["steiner"] = {"cells": ds["n_cells"], "nets": ds["n_nets"], "ms_per_update": ms,
                       "arcs_per_s": sst["arcs"] / (ms * 1e-3), "net_phase_ms": acc[0] / 5,
                       "total_wirelength_m": float(wl.sum()) * 1e-9,
-                      "what": "sta_update_timing on a placed 1M-cell design with STA_WIRE_STEINER: Steiner "
-                              "trees of every net from the positions, RC sweep, forward, backward, reduction"}
+                      "what": "sta_update_timing on the steiner workload (1M cells placed locally, "
+                              "STA_WIRE_STEINER): Steiner trees of every net from the positions, RC sweep, forward, "
+                              "backward, reduction"}
 
     del ctx
     torch.cuda.empty_cache()

@@ -113,6 +113,9 @@ struct DevCtx {
     const int64_t *st_node_ptr, *st_adj_ptr;    // [I + 1] working nodes / bitset words per item
     long long *st_x, *st_y, *st_key;            // [working nodes] coordinates (nm), Prim keys
     int32_t *st_aux;                            // [working nodes x 3] Prim source / BFS number / queue
+    float *st_capw;                             // [working nodes] RC node capacitances being accumulated
+    const int32_t *st_items;                    // items with sinks by increasing sink count
+    int32_t st_n_items, st_small;               // their number; the first st_small have <= 8 pins
     unsigned *st_adj;                           // [bitset words] adjacency rows
     const int32_t *drv_of, *pin_cell;
     const float *port_xy, *cell_xy;

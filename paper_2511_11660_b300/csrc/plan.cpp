@@ -443,7 +443,19 @@ void build(const sta_design_desc *d, Plan &pl)
             pl.st_adj_ptr[g + 1] = pl.st_adj_ptr[g] + (m > 0 && m + 1 <= kSteinerMaxPins ? w * ((w + 31) / 32) : 0);
         }
     }
-    if (pl.steiner) pl.NN = pl.rc_ptr[I];
+    if (pl.steiner) {
+        pl.NN = pl.rc_ptr[I];
+        pl.st_items.clear();
+        for (int32_t g = 0; g < I; ++g)
+            if (pl.fo_ptr[g + 1] > pl.fo_ptr[g]) pl.st_items.push_back(g);
+        std::stable_sort(pl.st_items.begin(), pl.st_items.end(), [&](int32_t a, int32_t b) {
+            return pl.fo_ptr[a + 1] - pl.fo_ptr[a] < pl.fo_ptr[b + 1] - pl.fo_ptr[b];
+        });
+        pl.st_small = 0;
+        while (pl.st_small < (int32_t)pl.st_items.size() &&
+               pl.fo_ptr[pl.st_items[pl.st_small] + 1] - pl.fo_ptr[pl.st_items[pl.st_small]] + 1 <= kSteinerSmallPins)
+            ++pl.st_small;
+    }
     pl.F = pl.fo_ptr[I];
     pl.fo_pin.resize(pl.F);
     pl.fo_node.resize(pl.F);

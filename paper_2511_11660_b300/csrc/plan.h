@@ -21,6 +21,7 @@ constexpr int kMaxSlot = 3;       // at most three inputs per cell
 constexpr int kTabStride = 80;    // floats per packed table (see packLut)
 constexpr int kColNodes = 16;     // RC nets up to this many nodes are swept in shared memory
 constexpr int kSteinerMaxPins = 64;  // nets of more pins keep the rectilinear MST (no Steiner points)
+constexpr int kSteinerSmallPins = 8; // nets of at most this many pins are built in shared memory
 
 enum { kPinPI = 0, kPinPO = 1, kPinIN = 2, kPinOUT = 3, kPinD = 4, kPinCK = 5, kPinQ = 6 };
 enum { kSenseNone = -1, kSensePos = 0, kSenseNeg = 1, kSenseNon = 2, kSenseRise = 3 };
@@ -39,6 +40,8 @@ struct Plan {
     std::vector<int64_t> st_node_ptr;        // [I + 1] Steiner working nodes per item: 3 n (n = sinks + 1), 0 without sinks
     std::vector<int64_t> st_adj_ptr;         // [I + 1] adjacency bitset words per item: 3 n x ceil(3 n / 32) (n <= 64)
     std::vector<int32_t> net_of_item;        // [I] caller net driven by the item, -1 if none
+    std::vector<int32_t> st_items;           // items with sinks by increasing sink count (a warp's nets alike)
+    int32_t st_small = 0;                    // how many of them have at most kSteinerSmallPins pins
     int32_t n_nets = 0;
     float gamma = 0.f;
     int32_t net_model = STA_NET_ELMORE;      // net delay calculator

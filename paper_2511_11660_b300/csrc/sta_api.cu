@@ -246,6 +246,10 @@ sta_status create_from_plan(sta_ctx *c, int device)
         d.st_y = dev_alloc<long long>(c, WN);
         d.st_key = dev_alloc<long long>(c, WN);
         d.st_aux = dev_alloc<int32_t>(c, 3 * WN);
+        d.st_capw = dev_alloc<float>(c, WN);
+        d.st_items = upload(c, pl.st_items);
+        d.st_n_items = (int32_t)pl.st_items.size();
+        d.st_small = pl.st_small;
         d.st_adj = dev_alloc<unsigned>(c, std::max<int64_t>(1, pl.st_adj_ptr[pl.I]));
         d.rc_parent = d.st_parent;
         d.rc_R = d.st_R;
@@ -364,7 +368,8 @@ int32_t launches_per_update(const sta_ctx *c)
 {
     const Plan &pl = c->plan;
     int32_t n = 0;
-    if (pl.steiner) n += 2 * (pl.I > 0);        // Steiner trees, then the RC sweep
+    if (pl.steiner)   // Steiner trees (small nets, larger nets), then the RC sweep
+        n += (pl.st_small > 0) + ((int32_t)pl.st_items.size() > pl.st_small) + (pl.I > 0);
     else if (pl.placed) n += pl.I > 0;
     else n += pl.NN > 0 && pl.I > 0;
     if (c->schedule == STA_SCHED_DATAFLOW) {
