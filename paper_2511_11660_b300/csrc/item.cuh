@@ -440,8 +440,11 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
         }
         // the exact winner (no finite candidate: absent, -inf late / +inf
         // early), plus the log-sum-exp excess when smoothed
-        const float ex = SMOOTH ? c.gamma * logf(ma.s) : 0.f;
-        const DF oa = wy > -INFINITY ? (win + wd) + sgn * ex : DF(-sgn * INFINITY);
+        DF oa(-sgn * INFINITY);   // no finite candidate
+        if (wy > -INFINITY) {
+            oa = win + wd;
+            if (SMOOTH) oa = oa + sgn * (c.gamma * logf(ma.s));
+        }
         const float os = sgn * ms.get(c.gamma);
         st_comp_df(c.at + (size_t)z * K + k, q, oa);
         st_comp(c.slew + (size_t)z * K + k, q, os);
