@@ -82,6 +82,7 @@ class _Design(C.Structure):
         ("net_model", C.c_int32), ("arnoldi_order", C.c_int32),
         ("n_exc", C.c_int32), ("exc_from_ptr", C.c_void_p), ("exc_from", C.c_void_p), ("exc_to_ptr", C.c_void_p),
         ("exc_to", C.c_void_p), ("exc_action", C.c_void_p), ("exc_mult", C.c_void_p),
+        ("exc_thru_ptr", C.c_void_p), ("exc_thru_set_ptr", C.c_void_p), ("exc_thru_pin", C.c_void_p),
         ("wire_model", C.c_int32), ("r_per_um_y", C.c_double), ("c_per_um_y", C.c_double),
     ]
 
@@ -95,6 +96,7 @@ _ARRAYS = {
     "lut_scale": np.float32, "rc_scale": np.float32,
     "exc_from_ptr": np.int32, "exc_from": np.int32, "exc_to_ptr": np.int32, "exc_to": np.int32,
     "exc_action": np.int32, "exc_mult": np.float32,
+    "exc_thru_ptr": np.int32, "exc_thru_set_ptr": np.int32, "exc_thru_pin": np.int32,
 }
 _SCALARS = ("setup_ns", "hold_ns", "po_cap_pf", "r_per_um", "c_per_um", "period_ns", "clk_slew_ns",
             "pi_at_ns", "pi_slew_ns", "gamma_ns", "r_per_um_y", "c_per_um_y")
@@ -239,6 +241,35 @@ def endpoints(d: dict) -> np.ndarray:
     return np.nonzero((role == 4) | (role == 1))[0].astype(np.int32)
 
 
+def tag_layout(d: dict):
+    """O8 tags of an exception-group design: the first tag of each group and
+    the advance mask of every pin (bit t: tag t moves on to t + 1 there)."""
+    G = len(d["exc_action"]) if d.get("exc_action") is not None else 0
+    tp = d.get("exc_thru_ptr")
+    base, t = [], 1
+    for g in range(G):
+        base.append(t)
+        t += (int(tp[g + 1]) - int(tp[g]) if tp is not None else 0) + 1
+    adv = {}
+    if tp is not None:
+        tsp, tpin = d["exc_thru_set_ptr"], d["exc_thru_pin"]
+        for g in range(G):
+            for jj in range(int(tp[g + 1]) - int(tp[g])):
+                s = int(tp[g]) + jj
+                for p in tpin[tsp[s]:tsp[s + 1]]:
+                    adv[int(p)] = adv.get(int(p), 0) | (1 << (base[g] + jj))
+    return base, adv
+
+
+def n_tags(d: dict) -> int:
+    """O8 tags per corner: 1 + sum over exception groups of (through sets + 1)."""
+    if d.get("exc_action") is None:
+        return 1
+    G = len(d["exc_action"])
+    tp = d.get("exc_thru_ptr")
+    return 1 + sum((int(tp[g + 1]) - int(tp[g]) if tp is not None else 0) + 1 for g in range(G))
+
+
 def sta(d: dict, use_rc: bool | None = None) -> dict:
     """Full FP64 analysis; see ``orc_sta`` for the array layouts.  With
     timing-exception groups (keys exc_from_ptr, exc_from, exc_to_ptr,
@@ -247,7 +278,7 @@ def sta(d: dict, use_rc: bool | None = None) -> dict:
     lib = _load()
     s, keep = _marshal(d, use_rc)
     P, K = int(d["n_pins"]), int(d.get("n_corners", 1))
-    Ks = K * (1 + s.n_exc)   # states: corner * (groups + 1) + tag
+    Ks = K * n_tags(d)   # states: corner * tags + tag
     E = len(endpoints(d))
     arr = {k: np.zeros((max(P, 1), Ks, 4), np.float64) for k in ("at", "slew", "rat", "slack")}
     eps = np.zeros((max(E, 1), K), np.float64)
@@ -313,7 +344,8 @@ def report_paths(d: dict, k: int, slack_lt: float = float("inf"), corner: int = 
     startpoint group that sets the endpoint's slack."""
     res = res if res is not None else sta(d)
     K = int(d.get("n_corners", 1))
-    Tg = 1 + (len(d["exc_action"]) if d.get("exc_action") is not None else 0)
+    Tg = n_tags(d)
+    _, adv = tag_layout(d)
     sc = float(np.asarray(d["lut_scale"] if d.get("lut_scale") is not None else np.ones(K))[corner])
     load, _, _ = net_delays(d, corner)
     role = np.asarray(d["pin_role"])
@@ -345,15 +377,24 @@ def report_paths(d: dict, k: int, slack_lt: float = float("inf"), corner: int = 
             sl = res["slack"][p, corner * Tg + g]
             if min(sl[2], sl[3]) < best_s:
                 best_s, st, rf = min(sl[2], sl[3]), corner * Tg + g, 0 if sl[2] <= sl[3] else 1
-        at, slew = res["at"][:, st], res["slew"][:, st]
-        pins, rfs = [], []
+        pins, rfs, ats = [], [], []
         while True:
             if len(pins) > d["n_pins"]:
                 raise RuntimeError("oracle report_paths: path longer than the design")
+            at, slew = res["at"][:, st], res["slew"][:, st]
             pins.append(p)
             rfs.append(rf)
+            ats.append(at[p, 2 + rf])
             if driver[p] >= 0:                       # net sink: to the driver, same edge
-                p = int(driver[p])
+                # through a -through pin the path may come from the previous
+                # tag's state: the one with the larger late arrival (ties: same)
+                tg = st - corner * Tg
+                a = adv.get(p, 0)
+                stay, inflow = not (a >> tg) & 1, tg >= 1 and (a >> (tg - 1)) & 1
+                dp = int(driver[p])
+                if inflow and (not stay or res["at"][dp, st - 1, 2 + rf] > res["at"][dp, st, 2 + rf]):
+                    st -= 1
+                p = dp
                 continue
             if role[p] in (0, 5):                    # PI or CK: the startpoint
                 break
@@ -375,6 +416,7 @@ def report_paths(d: dict, k: int, slack_lt: float = float("inf"), corner: int = 
             p, rf = arg
         pins.reverse()
         rfs.reverse()
+        ats.reverse()
         out.append({"endpoint": int(eps[e]), "slack": float(es[e]), "pins": np.array(pins),
-                    "rf": np.array(rfs, np.int8), "at": np.array([at[q, 2 + r] for q, r in zip(pins, rfs)])})
+                    "rf": np.array(rfs, np.int8), "at": np.array(ats)})
     return out

@@ -36,7 +36,10 @@
  *       with group g's action when it is in the group's endpoint list (or
  *       the list is empty) -- false path: no check; multicycle M: setup
  *       capture edge at M * T, hold unchanged -- and the default check
- *       otherwise; endpoint slack = min over tags;
+ *       otherwise; endpoint slack = min over tags.  With -through, a group
+ *       has ordered through sets of gate input pins and one tag per stage:
+ *       a path of the group moves to the next stage at a pin of the next
+ *       set, and only a path through every set gets the group's action;
  *   O9  rectilinear Steiner tree RC from pin positions (Sec. III,
  *       "Parasitics (RC) inputs"): Prim MST on integer nm coordinates,
  *       greedy median Steiner insertion, breadth-first RC tree;
@@ -119,6 +122,10 @@ typedef struct {
     int32_t n_exc;
     const int32_t *exc_from_ptr, *exc_from, *exc_to_ptr, *exc_to, *exc_action;
     const float *exc_mult;
+    /* O8 -through: group g's ordered through sets are sets
+     * exc_thru_ptr[g] .. exc_thru_ptr[g+1]; set s lists gate input pins
+     * exc_thru_pin[exc_thru_set_ptr[s] .. exc_thru_set_ptr[s+1]).  NULL: none. */
+    const int32_t *exc_thru_ptr, *exc_thru_set_ptr, *exc_thru_pin;
     /* O9: RC from positions as a star (0) or a Steiner tree (1); unit R/C
      * along y for the Steiner tree (<= 0: the x values r_per_um, c_per_um) */
     int32_t wire_model;
@@ -903,11 +910,16 @@ int orc_topo_order(const orc_design *d, int32_t *order)
 /* One state: k indexes the at/slew arrays of Ks states (corner * tags +
  * tag), kc is the corner (its table scale).  src_on[p] == 0 marks a
  * startpoint of another tag: its arrivals are absent (-inf late, +inf
- * early); its slew is kept (slews are tag-free).  src_on may be NULL. */
+ * early); its slew is kept (slews are tag-free).  src_on may be NULL.
+ * adv (may be NULL) marks the through pins: bit t of adv[p] set when tag t
+ * moves on to tag t + 1 at gate input p; this state's tag is t = k - kt0
+ * (kt0: the corner's first state), and the state k - 1 (tag t - 1) must be
+ * final already. */
 static void forward_corner(const orc_design *d, const pin_info *pi, const int32_t *order, int32_t k, int32_t Ks,
-                           int32_t kc, const int8_t *src_on, const double *load, const double *Dn, const double *Vn,
-                           double *at, double *slew)
+                           int32_t kc, const int8_t *src_on, const uint32_t *adv, int32_t kt0, const double *load,
+                           const double *Dn, const double *Vn, double *at, double *slew)
 {
+    const int32_t t = k - kt0;
     int32_t K = Ks;
     double sc = d->lut_scale ? d->lut_scale[kc] : 1.0;
     for (int32_t oi = 0; oi < d->n_pins; ++oi) {
@@ -921,9 +933,16 @@ static void forward_corner(const orc_design *d, const pin_info *pi, const int32_
                 for (int j = 0; j < 4; ++j) at[IX(p, k, j)] = j < 2 ? INFINITY : -INFINITY;
         } else if (r == R_IN || r == R_D || r == R_PO) {
             int32_t drv = d->net_pin[d->net_pin_ptr[pi->sink_net[p]]];
+            /* a path in tag t stays unless p advances t; one in tag t - 1
+             * arrives in tag t when p advances t - 1 */
+            const int stay = !adv || !((adv[p] >> t) & 1u);
+            const int inflow = adv && t >= 1 && ((adv[p] >> (t - 1)) & 1u);
             for (int j = 0; j < 4; ++j) {
                 double sd = slew[IX(drv, k, j)];
-                at[IX(p, k, j)] = at[IX(drv, k, j)] + Dn[p];
+                double a = j < 2 ? INFINITY : -INFINITY;   /* absent */
+                if (stay) a = at[IX(drv, k, j)];
+                if (inflow) a = j < 2 ? fmin(a, at[IX(drv, k - 1, j)]) : fmax(a, at[IX(drv, k - 1, j)]);
+                at[IX(p, k, j)] = a + Dn[p];
                 slew[IX(p, k, j)] = sqrt(sd * sd + Vn[p]);
             }
         } else { /* R_OUT or R_Q */
@@ -955,12 +974,15 @@ static void forward_corner(const orc_design *d, const pin_info *pi, const int32_
 /* ----------------------------------------------- O4: required times, slack */
 
 /* One state (as forward_corner).  ep_req[2p], ep_req[2p+1] replace the late
- * and early requirements of endpoint pin p (may be NULL: the defaults). */
+ * and early requirements of endpoint pin p (may be NULL: the defaults).
+ * Through a sink s that advances this state's tag t, the path continues in
+ * tag t + 1: the state k + 1 must be final already. */
 static void backward_corner(const orc_design *d, const pin_info *pi, const int32_t *order, int32_t k, int32_t Ks,
-                            int32_t kc, const double *ep_req, const double *load, const double *Dn,
-                            const double *slew, double *rat)
+                            int32_t kc, const double *ep_req, const uint32_t *adv, int32_t kt0, const double *load,
+                            const double *Dn, const double *slew, double *rat)
 {
     int32_t K = Ks;
+    const int32_t t = k - kt0;
     double sc = d->lut_scale ? d->lut_scale[kc] : 1.0;
     for (int32_t oi = d->n_pins - 1; oi >= 0; --oi) {
         int32_t p = order[oi];
@@ -983,9 +1005,10 @@ static void backward_corner(const orc_design *d, const pin_info *pi, const int32
                 int32_t n = pi->drv_net[p];
                 for (int32_t q = d->net_pin_ptr[n] + 1; q < d->net_pin_ptr[n + 1]; ++q) {
                     int32_t s = d->net_pin[q];
+                    const int32_t ks = adv && ((adv[s] >> t) & 1u) ? k + 1 : k;
                     for (int rf = 0; rf < 2; ++rf) {
-                        rl[rf] = fmin(rl[rf], rat[IX(s, k, JJ(1, rf))] - Dn[s]);
-                        re[rf] = fmax(re[rf], rat[IX(s, k, JJ(0, rf))] - Dn[s]);
+                        rl[rf] = fmin(rl[rf], rat[IX(s, ks, JJ(1, rf))] - Dn[s]);
+                        re[rf] = fmax(re[rf], rat[IX(s, ks, JJ(0, rf))] - Dn[s]);
                     }
                 }
             }
@@ -1013,8 +1036,9 @@ static void backward_corner(const orc_design *d, const pin_info *pi, const int32
 
 /* Full analysis.  Arrays at/slew/rat/slack are [n_pins][n_corners][4] with
  * the inner index el * 2 + rf (el 0 early / hold, 1 late / setup).
- * With exception groups (O8) the pin arrays hold n_corners * (n_exc + 1)
- * states, state = corner * (n_exc + 1) + tag.
+ * With exception groups (O8) the pin arrays hold n_corners * tags states,
+ * state = corner * tags + tag, tags = 1 + sum over groups of (through sets
+ * + 1).
  * Endpoints are the DFF D pins and POs in ascending pin id; ep_setup and
  * ep_hold are [n_endpoints][n_corners] (min over rise/fall and tags).  summary is
  * [n_corners][8]: WNS setup, TNS setup, WNS hold, TNS hold, worst setup
@@ -1026,7 +1050,20 @@ int orc_sta(const orc_design *d, double *at, double *slew, double *rat, double *
     int rc = build_info(d, &pi);
     if (rc) { return rc; }
     const int32_t P = d->n_pins, Kc = d->n_corners;
-    const int32_t G = d->n_exc > 0 ? d->n_exc : 0, Tg = G + 1, K = Kc * Tg;   /* K: states (corner, tag) */
+    const int32_t G = d->n_exc > 0 ? d->n_exc : 0;
+    /* O8 tags: 0 = no group; group g owns tags base[g] .. base[g] + r_g, its
+     * progress through its r_g ordered through sets (base[g] + r_g: fully
+     * matched) */
+    int32_t base[33], nthru[32];
+    int32_t Tg = 1;
+    for (int32_t g = 0; g < G && g < 32; ++g) {
+        nthru[g] = d->exc_thru_ptr ? d->exc_thru_ptr[g + 1] - d->exc_thru_ptr[g] : 0;
+        if (nthru[g] < 0) { free_info(&pi); return ERR_INVAL; }
+        base[g] = Tg;
+        Tg += nthru[g] + 1;
+    }
+    if (G > 32 || Tg > 32) { free_info(&pi); return ERR_INVAL; }
+    const int32_t K = Kc * Tg;   /* K: states (corner, tag) */
     int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(P ? P : 1));
     double *load = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
     double *Dn = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
@@ -1035,7 +1072,9 @@ int orc_sta(const orc_design *d, double *at, double *slew, double *rat, double *
     int8_t *src_on = (int8_t *)calloc((size_t)(P ? P : 1), 1);
     uint8_t *in_to = (uint8_t *)calloc((size_t)(P ? P : 1), 1);
     double *ep_req = (double *)malloc(sizeof(double) * 2 * (size_t)(P ? P : 1));
-    if (!order || !load || !Dn || !Vn || !tag_of || !src_on || !in_to || !ep_req) { rc = ERR_NOMEM; goto done; }
+    uint32_t *adv = (uint32_t *)calloc((size_t)(P ? P : 1), sizeof(uint32_t));
+    int any_thru = 0;
+    if (!order || !load || !Dn || !Vn || !tag_of || !src_on || !in_to || !ep_req || !adv) { rc = ERR_NOMEM; goto done; }
     rc = topo_order(d, &pi, order);
     if (rc) goto done;
     /* O8: a startpoint's tag is its first group (0 = none) */
@@ -1043,37 +1082,60 @@ int orc_sta(const orc_design *d, double *at, double *slew, double *rat, double *
         for (int32_t i = d->exc_from_ptr[g]; i < d->exc_from_ptr[g + 1]; ++i) {
             const int32_t p = d->exc_from[i];
             if (p < 0 || p >= P || (d->pin_role[p] != R_PI && d->pin_role[p] != R_CK)) { rc = ERR_INVAL; goto done; }
-            if (!tag_of[p]) tag_of[p] = (int8_t)(g + 1);
+            if (!tag_of[p]) tag_of[p] = (int8_t)base[g];
         }
         for (int32_t i = d->exc_to_ptr[g]; i < d->exc_to_ptr[g + 1]; ++i) {
             const int32_t p = d->exc_to[i];
             if (p < 0 || p >= P || (d->pin_role[p] != R_D && d->pin_role[p] != R_PO)) { rc = ERR_INVAL; goto done; }
         }
         if (d->exc_action[g] != 0 && !(d->exc_action[g] == 1 && d->exc_mult[g] >= 1.0f)) { rc = ERR_INVAL; goto done; }
+        /* through set j + 1 of group g: tag base[g] + j moves on at its pins */
+        for (int32_t j = 0; j < nthru[g]; ++j) {
+            const int32_t s = d->exc_thru_ptr[g] + j;
+            for (int32_t i = d->exc_thru_set_ptr[s]; i < d->exc_thru_set_ptr[s + 1]; ++i) {
+                const int32_t p = d->exc_thru_pin[i];
+                if (p < 0 || p >= P || d->pin_role[p] != R_IN) { rc = ERR_INVAL; goto done; }
+                adv[p] |= 1u << (base[g] + j);
+                any_thru = 1;
+            }
+        }
     }
     for (int32_t kc = 0; kc < Kc; ++kc) {
         rc = orc_net_delays(d, kc, load, Dn, Vn);
         if (rc) goto done;
-        for (int32_t g = 0; g < Tg; ++g) {
-            const int32_t k = kc * Tg + g;
+        const int32_t kt0 = kc * Tg;
+        /* forward: tags in increasing order (a path moves from tag t to t + 1) */
+        for (int32_t t = 0; t < Tg; ++t) {
+            if (G > 0)
+                for (int32_t p = 0; p < P; ++p) src_on[p] = tag_of[p] == t;
+            forward_corner(d, &pi, order, kt0 + t, K, kc, G ? src_on : NULL, any_thru ? adv : NULL, kt0, load, Dn,
+                           Vn, at, slew);
+        }
+        /* backward: tags in decreasing order */
+        for (int32_t t = Tg - 1; t >= 0; --t) {
+            const int32_t k = kt0 + t;
             if (G > 0) {
-                for (int32_t p = 0; p < P; ++p) src_on[p] = tag_of[p] == g;
-                /* requirements of tag g at every endpoint */
+                /* requirements of tag t at every endpoint: its group's action
+                 * when t is the group's fully matched tag and the endpoint is
+                 * in the group's list (or the list is empty); else the default */
+                int32_t grp = -1;
+                for (int32_t g = 0; g < G; ++g)
+                    if (t == base[g] + nthru[g]) grp = g;
                 for (int32_t p = 0; p < P; ++p) in_to[p] = 0;
-                const int applies_all = g > 0 && d->exc_to_ptr[g] == d->exc_to_ptr[g - 1];
-                if (g > 0)
-                    for (int32_t i = d->exc_to_ptr[g - 1]; i < d->exc_to_ptr[g]; ++i) in_to[d->exc_to[i]] = 1;
+                const int applies_all = grp >= 0 && d->exc_to_ptr[grp + 1] == d->exc_to_ptr[grp];
+                if (grp >= 0)
+                    for (int32_t i = d->exc_to_ptr[grp]; i < d->exc_to_ptr[grp + 1]; ++i) in_to[d->exc_to[i]] = 1;
                 for (int32_t p = 0; p < P; ++p) {
                     const int r = d->pin_role[p];
                     if (r != R_D && r != R_PO) continue;
                     const double T = d->period_ns;
                     double late = r == R_D ? T - d->setup_ns : T, early = r == R_D ? d->hold_ns : 0.0;
-                    if (g > 0 && (applies_all || in_to[p])) {
-                        if (d->exc_action[g - 1] == 0) {
+                    if (grp >= 0 && (applies_all || in_to[p])) {
+                        if (d->exc_action[grp] == 0) {
                             late = INFINITY;   /* false path: no check */
                             early = -INFINITY;
                         } else {
-                            const double M = d->exc_mult[g - 1];   /* multicycle: capture at M * T */
+                            const double M = d->exc_mult[grp];   /* multicycle: capture at M * T */
                             late = r == R_D ? M * T - d->setup_ns : M * T;
                         }
                     }
@@ -1081,8 +1143,8 @@ int orc_sta(const orc_design *d, double *at, double *slew, double *rat, double *
                     ep_req[2 * (size_t)p + 1] = early;
                 }
             }
-            forward_corner(d, &pi, order, k, K, kc, G ? src_on : NULL, load, Dn, Vn, at, slew);
-            backward_corner(d, &pi, order, k, K, kc, G ? ep_req : NULL, load, Dn, slew, rat);
+            backward_corner(d, &pi, order, k, K, kc, G ? ep_req : NULL, any_thru ? adv : NULL, kt0, load, Dn, slew,
+                            rat);
             for (int32_t p = 0; p < P; ++p)
                 for (int rf = 0; rf < 2; ++rf) {
                     slack[IX(p, k, JJ(0, rf))] = at[IX(p, k, JJ(0, rf))] - rat[IX(p, k, JJ(0, rf))];
@@ -1117,7 +1179,7 @@ int orc_sta(const orc_design *d, double *at, double *slew, double *rat, double *
         sm[4] = worst_s; sm[5] = worst_h; sm[6] = nv_s; sm[7] = nv_h;
     }
 done:
-    free(order); free(load); free(Dn); free(Vn); free(tag_of); free(src_on); free(in_to); free(ep_req);
+    free(order); free(load); free(Dn); free(Vn); free(tag_of); free(src_on); free(in_to); free(ep_req); free(adv);
     free_info(&pi);
     return rc;
 }
@@ -1174,7 +1236,7 @@ int orc_objective_grad(const orc_design *d, double w_tns, double w_wns, double *
         double f = d->rc_scale ? d->rc_scale[k] : 1.0;
         rc = orc_net_delays(d, k, load, Dn, Vn);
         if (rc) goto done;
-        forward_corner(d, &pi, order, k, K, k, NULL, load, Dn, Vn, at, sl);
+        forward_corner(d, &pi, order, k, K, k, NULL, NULL, k, load, Dn, Vn, at, sl);
         /* endpoint slacks and the objective */
         double mx = -INFINITY;
         for (int32_t p = 0; p < P; ++p) {

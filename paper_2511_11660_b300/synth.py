@@ -315,17 +315,26 @@ def make_design(n_cells: int, depth: int, seed: int = 0, lib: dict | None = None
     return d
 
 
-def exception_groups(d: dict, rng, n_groups: int, div_from: int = 3, div_to: int = 2) -> dict:
+def exception_groups(d: dict, rng, n_groups: int, div_from: int = 3, div_to: int = 2, max_thru: int = 0,
+                     div_thru: int = 8) -> dict:
     """Random timing-exception groups for design ``d``: each group takes a
     random 1/div_from of the startpoints (PI and CK pins) and, with probability
     0.7, a random 1/div_to of the endpoints (D and PO pins; otherwise an empty
     list, i.e. every endpoint); its action is a false path or a multicycle
-    with M in {2, 3}.  Returned as the design keys exc_*."""
+    with M in {2, 3}.  With max_thru > 0 each group also gets 0..max_thru
+    ordered through sets, each a random 1/div_thru of the gate input pins.
+    Returned as the design keys exc_*."""
     role = np.asarray(d["pin_role"])
     starts = np.nonzero((role == PI) | (role == CK))[0]
     ends = np.nonzero((role == D) | (role == PO))[0]
+    ins = np.nonzero(role == IN)[0]
     fp, fr, tp, to, act, mult = [0], [], [0], [], [], []
+    thp, tsp, tpin = [0], [0], []
     for _ in range(n_groups):
+        for _ in range(int(rng.integers(0, max_thru + 1)) if max_thru > 0 else 0):
+            tpin += list(rng.choice(ins, size=max(1, len(ins) // div_thru), replace=False))
+            tsp.append(len(tpin))
+        thp.append(len(tsp) - 1)
         fr += list(rng.choice(starts, size=max(1, len(starts) // div_from), replace=False))
         fp.append(len(fr))
         if rng.random() < 0.7:
@@ -333,9 +342,13 @@ def exception_groups(d: dict, rng, n_groups: int, div_from: int = 3, div_to: int
         tp.append(len(to))
         act.append(int(rng.random() < 0.5))
         mult.append(float(rng.integers(2, 4)))
-    return dict(exc_from_ptr=np.array(fp, np.int32), exc_from=np.array(fr, np.int32),
-                exc_to_ptr=np.array(tp, np.int32), exc_to=np.array(to, np.int32),
-                exc_action=np.array(act, np.int32), exc_mult=np.array(mult, np.float32))
+    out = dict(exc_from_ptr=np.array(fp, np.int32), exc_from=np.array(fr, np.int32),
+               exc_to_ptr=np.array(tp, np.int32), exc_to=np.array(to, np.int32),
+               exc_action=np.array(act, np.int32), exc_mult=np.array(mult, np.float32))
+    if max_thru > 0:
+        out.update(exc_thru_ptr=np.array(thp, np.int32), exc_thru_set_ptr=np.array(tsp, np.int32),
+                   exc_thru_pin=np.array(tpin, np.int32))
+    return out
 
 
 def design_stats(d: dict) -> dict:

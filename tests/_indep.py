@@ -173,11 +173,13 @@ def enumerate_paths(d, corner=0, with_slew=False):
     return {p: paths(p) for p in range(d["n_pins"])}
 
 
-def enumerate_suffixes(d, corner=0):
+def enumerate_suffixes(d, corner=0, with_pins=False):
     """Every path from each pin to an endpoint, for slew-independent cell
     delays: {pin: [(delay to the endpoint, rf at the pin, endpoint pin)]}.
     Cell delays are read at the driven net's load (the tables do not depend
-    on slew); net delays are the independent Elmore sums of ``Net``."""
+    on slew); net delays are the independent Elmore sums of ``Net``.  With
+    with_pins each tuple also carries the gate input pins after the pin,
+    in order."""
     net = Net(d, corner)
     sc = float(np.asarray(d["lut_scale"])[corner])
     role = np.asarray(d["pin_role"])
@@ -200,10 +202,11 @@ def enumerate_suffixes(d, corner=0):
         r = role[p]
         out = []
         if r in (D, PO):
-            out = [(0.0, rf, p) for rf in (0, 1)]
+            out = [(0.0, rf, p, ()) for rf in (0, 1)]
         elif r in (PI, OUT, Q):
             for s in sinks_of.get(p, []):
-                out += [(dl + net.Dns[s], rf, e) for dl, rf, e in suf(s)]
+                head = (s,) if role[s] == IN else ()
+                out += [(dl + net.Dns[s], rf, e, head + ps) for dl, rf, e, ps in suf(s)]
         elif r in (IN, CK):
             c = net.cell_of[p]
             t = ctype[c]
@@ -211,19 +214,24 @@ def enumerate_suffixes(d, corner=0):
             se = sense[t, slot]
             z = cp[cpp[c] + nin[t]]
             l = net.load.get(int(z), 0.0)
-            for dl, rfo, e in suf(int(z)):
+            for dl, rfo, e, ps in suf(int(z)):
                 dc = sc * bilinear(i1[t, slot, rfo], i2[t, slot, rfo], vv[t, slot, rfo], 0.0, l)
                 for rf in rf_in_of(se, rfo):
-                    out.append((dl + dc, rf, e))
+                    out.append((dl + dc, rf, e, ps))
         memo[p] = out
         return out
 
-    return {p: suf(p) for p in range(d["n_pins"])}
+    alls = {p: suf(p) for p in range(d["n_pins"])}
+    if with_pins:
+        return alls
+    return {p: [(dl, rf, e) for dl, rf, e, _ in v] for p, v in alls.items()}
 
 
-def enumerate_paths_from(d, corner=0):
+def enumerate_paths_from(d, corner=0, with_pins=False):
     """Every path's (arrival, edge, startpoint pin) at every pin, for
-    slew-independent cell delays (read at the driven net's load)."""
+    slew-independent cell delays (read at the driven net's load).  With
+    with_pins each tuple also carries the gate input pins the path passes,
+    in order."""
     net = Net(d, corner)
     sc = float(np.asarray(d["lut_scale"])[corner])
     role = np.asarray(d["pin_role"])
@@ -242,11 +250,12 @@ def enumerate_paths_from(d, corner=0):
             return memo[p]
         r = role[p]
         if r == PI:
-            out = [(float(d["pi_at_ns"]), rf, p) for rf in (0, 1)]
+            out = [(float(d["pi_at_ns"]), rf, p, ()) for rf in (0, 1)]
         elif r == CK:
-            out = [(0.0, rf, p) for rf in (0, 1)]
+            out = [(0.0, rf, p, ()) for rf in (0, 1)]
         elif r in (IN, D, PO):
-            out = [(a + net.Dns[p], rf, s) for a, rf, s in paths(net.driver[p])]
+            out = [(a + net.Dns[p], rf, s, ps + ((p,) if r == IN else ()))
+                   for a, rf, s, ps in paths(net.driver[p])]
         else:
             c = net.cell_of[p]
             t = ctype[c]
@@ -256,14 +265,17 @@ def enumerate_paths_from(d, corner=0):
                 se = sense[t, slot]
                 if se == NONE:
                     continue
-                for a, rf, s in paths(cp[cpp[c] + slot]):
+                for a, rf, s, ps in paths(cp[cpp[c] + slot]):
                     if r == Q and rf != 0:
                         continue
                     for rfo in (0, 1):
                         if rf in rf_in_of(se, rfo):
                             dl = sc * bilinear(i1[t, slot, rfo], i2[t, slot, rfo], vv[t, slot, rfo], 0.0, l)
-                            out.append((a + dl, rfo, s))
+                            out.append((a + dl, rfo, s, ps))
         memo[p] = out
         return out
 
-    return {p: paths(p) for p in range(d["n_pins"])}
+    allp = {p: paths(p) for p in range(d["n_pins"])}
+    if with_pins:
+        return allp
+    return {p: [(a, rf, s) for a, rf, s, _ in v] for p, v in allp.items()}

@@ -31,7 +31,7 @@ MUTANTS = [
     ("rc_corner_scale", "double f = d->rc_scale ? d->rc_scale[corner] : 1.0;", "double f = 1.0;", 0),
     # O2 forward propagation
     ("wire_slew_no_var", "sqrt(sd * sd + Vn[p])", "sqrt(sd * sd)", 0),
-    ("wire_at_no_delay", "at[IX(p, k, j)] = at[IX(drv, k, j)] + Dn[p];", "at[IX(p, k, j)] = at[IX(drv, k, j)];", 0),
+    ("wire_at_no_delay", "at[IX(p, k, j)] = a + Dn[p];", "at[IX(p, k, j)] = a;", 0),
     ("neg_unate_as_pos", "case S_NEG: rf_in[0] = 1 - rf_out;", "case S_NEG: rf_in[0] = rf_out;", 0),
     ("non_unate_one_edge", "case S_NON: rf_in[0] = 0; rf_in[1] = 1; return 2;", "case S_NON: rf_in[0] = 0; rf_in[1] = 1; return 1;", 0),
     ("fwd_delay_table_rf", "sc * lut(d, t, s, rfo ? TB_DF : TB_DR, si, l, 0, 0);", "sc * lut(d, t, s, rfo ? TB_DR : TB_DF, si, l, 0, 0);", 0),
@@ -44,8 +44,8 @@ MUTANTS = [
     # O4 required times, slack, WNS/TNS
     ("setup_sign", "rl[0] = rl[1] = d->period_ns - d->setup_ns;", "rl[0] = rl[1] = d->period_ns + d->setup_ns;", 0),
     ("hold_zero", "re[0] = re[1] = d->hold_ns;", "re[0] = re[1] = 0.0;", 0),
-    ("rat_net_no_delay", "rat[IX(s, k, JJ(1, rf))] - Dn[s]);", "rat[IX(s, k, JJ(1, rf))]);", 0),
-    ("rat_early_net_min", "re[rf] = fmax(re[rf], rat[IX(s, k, JJ(0, rf))] - Dn[s]);", "re[rf] = fmin(re[rf], rat[IX(s, k, JJ(0, rf))] - Dn[s]);", 0),
+    ("rat_net_no_delay", "rat[IX(s, ks, JJ(1, rf))] - Dn[s]);", "rat[IX(s, ks, JJ(1, rf))]);", 0),
+    ("rat_early_net_min", "re[rf] = fmax(re[rf], rat[IX(s, ks, JJ(0, rf))] - Dn[s]);", "re[rf] = fmin(re[rf], rat[IX(s, ks, JJ(0, rf))] - Dn[s]);", 0),
     ("rat_cell_early_slew", "slew[IX(p, k, JJ(1, ri))], load[z], 0, 0);", "slew[IX(p, k, JJ(0, ri))], load[z], 0, 0);", 0),
     ("rat_cell_rf_index", "rat[IX(z, k, JJ(1, rfo))] - dl);", "rat[IX(z, k, JJ(1, ri))] - dl);", 0),
     ("bwd_lut_corner", "double sc = d->lut_scale ? d->lut_scale[kc] : 1.0;", "double sc = d->lut_scale ? d->lut_scale[0] : 1.0;", 1),
@@ -72,10 +72,10 @@ MUTANTS = [
     ("arn_model_switch", "if (d->net_model == 1 && (d->rc_ptr || steiner)) {", "if (d->net_model == 2 && d->rc_ptr) {", 0),
     # O8 timing exceptions
     ("exc_seed_not_masked", "if (src_on && !src_on[p])", "if (src_on && src_on[p] > 1)", 0),
-    ("exc_first_group_wins", "if (!tag_of[p]) tag_of[p] = (int8_t)(g + 1);", "tag_of[p] = (int8_t)(g + 1);", 0),
+    ("exc_first_group_wins", "if (!tag_of[p]) tag_of[p] = (int8_t)base[g];", "tag_of[p] = (int8_t)base[g];", 0),
     ("exc_false_still_checked", "late = INFINITY;   /* false path: no check */", "late = late;", 0),
     ("exc_multicycle_edge", "late = r == R_D ? M * T - d->setup_ns : M * T;", "late = r == R_D ? M * T : M * T;", 0),
-    ("exc_to_list_ignored", "if (g > 0 && (applies_all || in_to[p])) {", "if (g > 0) {", 0),
+    ("exc_to_list_ignored", "if (grp >= 0 && (applies_all || in_to[p])) {", "if (grp >= 0) {", 0),
     ("exc_tag_max_not_min", "ssm = fmin(ssm, ss);", "ssm = fmax(ssm, ss);", 0),
     # O6 smoothed objective and its adjoint
     ("tns_softplus_sign", "tns += -g * softplus(-seed[p] / g);", "tns += -g * softplus(seed[p] / g);", 0),
@@ -89,6 +89,13 @@ MUTANTS = [
     ("adj_sink_sign", "if (cs >= 0) { grad_xy[2 * cs] -= dJdL * sx;", "if (cs >= 0) { grad_xy[2 * cs] += dJdL * sx;", 0),
     ("adj_y_uses_x", "double sx = (xd > xs) - (xd < xs), sy = (yd > ys) - (yd < ys);",
      "double sx = (xd > xs) - (xd < xs), sy = sx;", 0),
+    # O8 -through stages
+    ("thru_inflow_ignored", "const int inflow = adv && t >= 1 && ((adv[p] >> (t - 1)) & 1u);", "const int inflow = 0;", 0),
+    ("thru_stay_always", "const int stay = !adv || !((adv[p] >> t) & 1u);", "const int stay = 1;", 0),
+    ("thru_bwd_same_state", "const int32_t ks = adv && ((adv[s] >> t) & 1u) ? k + 1 : k;",
+     "const int32_t ks = k;", 0),
+    ("thru_action_first_stage", "if (t == base[g] + nthru[g]) grp = g;", "if (t == base[g]) grp = g;", 0),
+    ("thru_adv_next_tag", "adv[p] |= 1u << (base[g] + j);", "adv[p] |= 1u << (base[g] + nthru[g]);", 0),
     # O9 Steiner tree RC from positions
     ("steiner_nm_truncates", "return (int64_t)lrintf(p);", "return (int64_t)p;", 0),
     ("steiner_median_is_middle_arg", "if ((a <= b && b <= c) || (c <= b && b <= a)) return b;", "return b;", 0),

@@ -764,17 +764,18 @@ def test_exceptions_all_false_and_all_multicycle():
     np.testing.assert_array_equal(r["ep_hold"], base["ep_hold"])
 
 
-@pytest.mark.parametrize("seed", range(3))
-def test_exception_paths_fixed_delay(seed):
+@pytest.mark.parametrize("seed,max_thru", [(0, 0), (1, 0), (2, 0), (3, 2), (4, 2)])
+def test_exception_paths_fixed_delay(seed, max_thru):
     """With exceptions the reported path is the one that sets the endpoint's
     slack: it starts at a startpoint s, its arrival at the endpoint is an
-    enumerated path arrival from s, and (late requirement of s's tag at the
-    endpoint) - arrival equals the endpoint's slack, the minimum over every
-    enumerated tagged path."""
+    enumerated path arrival from s, and (late requirement of its group's
+    match at the endpoint) - arrival equals the endpoint's slack, the minimum
+    over every enumerated tagged path.  With -through sets, a path's match
+    also needs its gate input pins to pass the group's sets in order."""
     rng = np.random.default_rng(50 + seed)
     d = _fixed_design(seed, n_cells=14, depth=5)
     d["period_ns"] = 0.35
-    d.update(synth.exception_groups(d, rng, 3))
+    d.update(synth.exception_groups(d, rng, 3, max_thru=max_thru, div_thru=3))
     res = oracle.sta(d)
     role = np.asarray(d["pin_role"])
     first = {}
@@ -783,10 +784,10 @@ def test_exception_paths_fixed_delay(seed):
             first.setdefault(int(p), g)
     T = d["period_ns"]
 
-    def late_req(p, s):
+    def late_req(p, s, ins):
         base = T - d["setup_ns"] if role[p] == synth.D else T
         g = first.get(int(s))
-        if g is None:
+        if g is None or (max_thru and not _through_matched(d, g, ins)):
             return base
         lst = d["exc_to"][d["exc_to_ptr"][g]:d["exc_to_ptr"][g + 1]]
         if len(lst) and p not in lst:
@@ -796,16 +797,17 @@ def test_exception_paths_fixed_delay(seed):
         M = float(d["exc_mult"][g])
         return M * T - d["setup_ns"] if role[p] == synth.D else M * T
 
-    allp = _indep.enumerate_paths_from(d)
+    allp = _indep.enumerate_paths_from(d, with_pins=True)
     paths = oracle.report_paths(d, 100, res=res)
     assert len(paths) == int(np.sum(res["ep_setup"][:, 0] < np.inf))
     for pth in paths:
         e, s, rf = int(pth["endpoint"]), int(pth["pins"][0]), int(pth["rf"][-1])
-        want = min(late_req(e, s2) - a for a, _, s2 in allp[e])
+        want = min(late_req(e, s2, ins) - a for a, _, s2, ins in allp[e])
         assert pth["slack"] == pytest.approx(want, abs=1e-12)
-        arrivals = [a for a, f, s2 in allp[e] if s2 == s and f == rf]
+        ins = tuple(int(q) for q in pth["pins"] if role[q] == synth.IN)
+        arrivals = [a for a, f, s2, ins2 in allp[e] if s2 == s and f == rf and ins2 == ins]
         assert min(abs(a - pth["at"][-1]) for a in arrivals) <= 1e-12
-        assert late_req(e, s) - pth["at"][-1] == pytest.approx(want, abs=1e-12)
+        assert late_req(e, s, ins) - pth["at"][-1] == pytest.approx(want, abs=1e-12)
 
 
 # --------------------------------------------------- O9 Steiner RC from positions
@@ -1043,3 +1045,136 @@ def test_net_wirelengths_match_per_net_trees():
         xy = [net.pos(int(p)) for p in npn[npp[m]:npp[m + 1]]]
         t = oracle.steiner_tree([oracle.nm(x) for x, _ in xy], [oracle.nm(y) for _, y in xy])
         assert wl[m] == t["wl"]
+
+
+def _through_matched(d, g, ins_pins):
+    """The path's gate input pins pass group g's through sets in order
+    (greedy earliest match, which decides a subsequence of sets)."""
+    tp, tsp, tpin = d["exc_thru_ptr"], d["exc_thru_set_ptr"], d["exc_thru_pin"]
+    j, r = 0, tp[g + 1] - tp[g]
+    for p in ins_pins:
+        if j < r:
+            s = tp[g] + j
+            if p in set(int(x) for x in tpin[tsp[s]:tsp[s + 1]]):
+                j += 1
+    return j == r
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_exceptions_through_brute_force(seed):
+    """-through: a path of group g (its startpoint's first group) gets g's
+    action only if its gate input pins pass g's through sets in order and it
+    ends in g's list; every endpoint's setup and hold slack is the minimum
+    over its enumerated paths of that path's requirement - arrival."""
+    rng = np.random.default_rng(200 + seed)
+    d = _fixed_design(seed, n_cells=16, depth=5)
+    d["period_ns"] = 0.35
+    d.update(synth.exception_groups(d, rng, 3, max_thru=2, div_thru=3))
+    assert d["exc_thru_ptr"][-1] > 0
+    res = oracle.sta(d)
+    assert res["at"].shape[1] == oracle.n_tags(d)
+    role = np.asarray(d["pin_role"])
+    first = {}
+    for g in range(3):
+        for p in d["exc_from"][d["exc_from_ptr"][g]:d["exc_from_ptr"][g + 1]]:
+            first.setdefault(int(p), g)
+    T = d["period_ns"]
+    allp = _indep.enumerate_paths_from(d, with_pins=True)
+    matched_any = 0
+    for e, p in enumerate(res["endpoints"]):
+        setup = hold = np.inf
+        for a, rf, s, ins in allp[p]:
+            late = T - d["setup_ns"] if role[p] == synth.D else T
+            early = d["hold_ns"] if role[p] == synth.D else 0.0
+            g = first.get(s)
+            if g is not None and _through_matched(d, g, ins):
+                lst = d["exc_to"][d["exc_to_ptr"][g]:d["exc_to_ptr"][g + 1]]
+                if len(lst) == 0 or p in lst:
+                    matched_any += 1
+                    if d["exc_action"][g] == 0:
+                        late, early = np.inf, -np.inf
+                    else:
+                        late = float(d["exc_mult"][g]) * T - d["setup_ns"] if role[p] == synth.D \
+                            else float(d["exc_mult"][g]) * T
+            setup = min(setup, late - a)
+            hold = min(hold, a - early)
+        assert res["ep_setup"][e, 0] == pytest.approx(setup, abs=1e-12), (e, p)
+        assert res["ep_hold"][e, 0] == pytest.approx(hold, abs=1e-12), (e, p)
+    assert matched_any > 0
+
+
+def test_exceptions_through_every_pin_equals_plain_group():
+    """A through set holding every gate input pin is passed by every path
+    that crosses a gate: with one such set, the group acts exactly like the
+    group without -through on every endpoint reached through a gate."""
+    d = synth.make_design(500, 8, seed=6, period_ns=0.7)
+    rng = np.random.default_rng(1)
+    g1 = synth.exception_groups(d, rng, 2)
+    role = np.asarray(d["pin_role"])
+    ins = np.nonzero(role == synth.IN)[0].astype(np.int32)
+    thru = dict(exc_thru_ptr=np.array([0, 1, 1], np.int32), exc_thru_set_ptr=np.array([0, len(ins)], np.int32),
+                exc_thru_pin=ins)
+    r0 = oracle.sta(dict(d, **g1))
+    r1 = oracle.sta(dict(d, **g1, **thru))
+    # endpoints driven straight from a startpoint (no gate) may differ; all others agree
+    npp, npn = d["net_pin_ptr"], d["net_pin"]
+    drv = {int(s): int(npn[npp[n]]) for n in range(d["n_nets"]) for s in npn[npp[n] + 1:npp[n + 1]]}
+    direct = np.array([role[drv[int(p)]] in (synth.PI, synth.Q) for p in r0["endpoints"]])
+    assert (~direct).sum() > 10
+    np.testing.assert_allclose(r1["ep_setup"][~direct], r0["ep_setup"][~direct], rtol=0, atol=1e-12)
+    np.testing.assert_allclose(r1["ep_hold"][~direct], r0["ep_hold"][~direct], rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_exceptions_through_required_times_brute_force(seed):
+    """Required times per tag with -through: at every pin and tag t, the late
+    required time is the minimum over the path suffixes to an endpoint of
+    (requirement of the tag the suffix ends in - suffix delay), the tag
+    advancing at each gate input of the suffix that is in its group's next
+    through set (the early one the maximum, likewise)."""
+    rng = np.random.default_rng(300 + seed)
+    d = _fixed_design(seed, n_cells=14, depth=5)
+    d["period_ns"] = 0.35
+    d.update(synth.exception_groups(d, rng, 2, max_thru=2, div_thru=3))
+    res = oracle.sta(d)
+    base, _ = oracle.tag_layout(d)
+    tp, tsp, tpin = d["exc_thru_ptr"], d["exc_thru_set_ptr"], d["exc_thru_pin"]
+    role = np.asarray(d["pin_role"])
+    T = d["period_ns"]
+    Tg = oracle.n_tags(d)
+    group_of = {}
+    for g in range(2):
+        for j in range(tp[g + 1] - tp[g] + 1):
+            group_of[base[g] + j] = (g, j)
+
+    def final(t, ins):   # (group, fully matched) after the suffix's gate inputs
+        if t == 0:
+            return None, False
+        g, j = group_of[t]
+        r = tp[g + 1] - tp[g]
+        for p in ins:
+            if j < r and p in set(int(x) for x in tpin[tsp[tp[g] + j]:tsp[tp[g] + j + 1]]):
+                j += 1
+        return g, j == r
+
+    def reqs(e, t, ins):
+        late = T - d["setup_ns"] if role[e] == synth.D else T
+        early = d["hold_ns"] if role[e] == synth.D else 0.0
+        g, full = final(t, ins)
+        if full:
+            lst = d["exc_to"][d["exc_to_ptr"][g]:d["exc_to_ptr"][g + 1]]
+            if len(lst) == 0 or e in lst:
+                if d["exc_action"][g] == 0:
+                    return np.inf, -np.inf
+                M = float(d["exc_mult"][g])
+                late = M * T - d["setup_ns"] if role[e] == synth.D else M * T
+        return late, early
+
+    suf = _indep.enumerate_suffixes(d, with_pins=True)
+    for p in range(d["n_pins"]):
+        for t in range(Tg):
+            for rf in (0, 1):
+                late = min([reqs(e, t, ins)[0] - dl for dl, r, e, ins in suf[p] if r == rf], default=np.inf)
+                early = max([reqs(e, t, ins)[1] - dl for dl, r, e, ins in suf[p] if r == rf], default=-np.inf)
+                assert res["rat"][p, t, 2 + rf] == pytest.approx(late, abs=1e-12), (p, t, rf)
+                assert res["rat"][p, t, rf] == pytest.approx(early, abs=1e-12), (p, t, rf)
