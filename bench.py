@@ -356,9 +356,11 @@ def run_ours(a, dist: Dist):
                     "what": "sta_report_paths: radix select of the 1000 worst setup endpoints, bitonic sort, "
                             "critical-path trace, CSR arrays copied to the host"}
 
-    # ---- timing exceptions: three startpoint groups (four tags per corner)
+    # ---- timing exceptions: three startpoint groups with up to two -through
+    # sets of 1/64 of the gate inputs each (one tag per group stage)
     if d.get("exc_action") is None:
-        dx = dict(d, **synth.exception_groups(d, np.random.default_rng(a.seed), 3, div_from=5, div_to=4))
+        dx = dict(d, **synth.exception_groups(d, np.random.default_rng(a.seed), 3, div_from=5, div_to=4, max_thru=2,
+                                              div_thru=64))
         dx["period_ns"] = T
         del ctx
         torch.cuda.empty_cache()
@@ -372,7 +374,8 @@ def run_ours(a, dist: Dist):
                              "arcs_per_s": arcs / (ms * 1e-3), "wns_setup_ns": rx["wns_setup"],
                              "setup_violations": rx["n_viol_setup"],
                              "what": "sta_update_timing with 3 false-path / multicycle groups (1/5 of the "
-                                     "startpoints each, endpoint lists of 1/4 of the endpoints or all)"}
+                                     "startpoints each, 0-2 ordered -through sets of 1/64 of the gate inputs, "
+                                     "endpoint lists of 1/4 of the endpoints or all)"}
 
     # ---- Steiner-tree RC from positions: a placed 1M-cell design, trees rebuilt every update
     del ctx

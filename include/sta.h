@@ -178,10 +178,19 @@ typedef struct {
      * hold unchanged -- and the default check otherwise.  Endpoint slacks,
      * WNS and TNS take the min over tags; per-pin arrays (sta_get_pin_state)
      * hold n_corners * (n_exc + 1) states, state = corner * (n_exc + 1) +
-     * tag.  Not with gamma_ns > 0 or in a batch.  n_exc = 0: none. */
+     * tag.  Not with gamma_ns > 0 or in a batch.  n_exc = 0: none.
+     * -through (Sec. IV-B: false paths through pin sequences): group g may
+     * have ordered through sets exc_thru_ptr[g] .. exc_thru_ptr[g+1]; set s
+     * lists gate input pins exc_thru_pin[exc_thru_set_ptr[s] ..
+     * exc_thru_set_ptr[s+1]).  A path of group g moves to the next stage at
+     * a pin of its next set, and only a path through every set, in order,
+     * gets the group's action (else the default check).  Tags are then one
+     * per stage: n_tags = 1 + sum over groups of (sets + 1) <= 32.
+     * exc_thru_ptr NULL: no through sets. */
     int32_t n_exc;
     const int32_t *exc_from_ptr, *exc_from, *exc_to_ptr, *exc_to, *exc_action;
     const float *exc_mult;
+    const int32_t *exc_thru_ptr, *exc_thru_set_ptr, *exc_thru_pin;
     /* RC from positions (rc_ptr == NULL; Sec. III "Parasitics (RC) inputs":
      * pin positions and unit R/C along x and y).  wire_model:
      *   STA_WIRE_STAR (0): one segment per sink of Manhattan length L,
@@ -223,8 +232,8 @@ typedef struct {
     int32_t launches_per_update;                 /* kernels one sta_update_timing launches */
     int32_t launches_per_backward;               /* kernels one sta_backward launches (differentiable
                                                     contexts, current reverse-sweep schedule; else 0) */
-    int32_t n_tags;                              /* exception tags (n_exc + 1); per-pin states =
-                                                    n_corners * n_tags */
+    int32_t n_tags;                              /* exception tags (1 + sum over groups of (through
+                                                    sets + 1)); per-pin states = n_corners * n_tags */
 } sta_plan_info;
 
 /* Per-corner summary returned by sta_report_slack. */

@@ -312,8 +312,13 @@ __device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int
             in.at[j] = ld_relaxed_df(fbox_a(c, par, f.drv[j], kq)->v + q);
             in.sl[j] = ld_relaxed1(reinterpret_cast<const float *>(fbox_s(c, par, f.drv[j], kq)) + q);
             ok = ok && real_df(in.at[j]) && in.sl[j] == in.sl[j];
-            for (int k = kq + c.KL; k < c.K && ok; k += c.KL)
-                ok = complete_df(fbox_a(c, par, f.drv[j], k)) && complete(ld_relaxed4(fbox_s(c, par, f.drv[j], k)));
+            // the lane's other states; with -through every state (a path may
+            // come in from the previous tag)
+            const int k0 = c.pin_adv ? 0 : kq + c.KL, dk = c.pin_adv ? 1 : c.KL;
+            for (int k = k0; k < c.K && ok; k += dk)
+                if (k != kq)
+                    ok = complete_df(fbox_a(c, par, f.drv[j], k)) &&
+                         complete(ld_relaxed4(fbox_s(c, par, f.drv[j], k)));
         }
     }
     return ok;
@@ -372,7 +377,31 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
                 const int a = pin0 + j;
                 DF a0, a1;   // the driver's rise / fall arrival and slew at this lane's el
                 float s0, s1;
-                if (WAIT && k == kq) {
+                const uint32_t adv = c.pin_adv ? c.pin_adv[a] : 0u;
+                if (adv) {
+                    // -through: a path in this state's tag t stays unless a
+                    // advances t; one in tag t - 1 comes in when a advances t - 1
+                    const int tg = k % c.Tg;
+                    const bool stay = !((adv >> tg) & 1u), inflow = tg >= 1 && ((adv >> (tg - 1)) & 1u);
+                    auto rd = [&](int kk, int comp) {
+                        return WAIT ? ld_relaxed_df(fbox_a(c, par, f.drv[j], kk)->v + comp)
+                                    : ld_state_df(c.at + (size_t)f.drv[j] * K + kk, comp);
+                    };
+                    a0 = a1 = DF(absent);
+                    if (stay) {
+                        a0 = rd(k, el * 2);
+                        a1 = rd(k, el * 2 + 1);
+                    }
+                    if (inflow) {
+                        const DF b0 = rd(k - 1, el * 2), b1 = rd(k - 1, el * 2 + 1);
+                        a0 = el ? df_max(a0, b0) : df_min(a0, b0);
+                        a1 = el ? df_max(a1, b1) : df_min(a1, b1);
+                    }
+                    const float4 sd = WAIT ? ld_relaxed4(fbox_s(c, par, f.drv[j], k))
+                                           : ld_state4(c.slew + (size_t)f.drv[j] * K + k);
+                    s0 = el ? sd.z : sd.x;
+                    s1 = el ? sd.w : sd.y;
+                } else if (WAIT && k == kq) {
                     const DF ap = shfl_xor_df(qm, in.at[j], 1);
                     const float sp = __shfl_xor_sync(qm, in.sl[j], 1);
                     a0 = rfo ? ap : in.at[j];
@@ -596,8 +625,10 @@ __device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (s[u] < 0) continue;
-            m[u] = s[u] < c.ep_begin ? ld_relaxed_df(rbox_at(c, par, s[u], kq)->v + q)
-                                     : ld_state_df(c.rat + (size_t)s[u] * K + kq, q);
+            // -through: a path in tag t continues in t + 1 beyond a sink that advances t
+            const int ks = (c.pin_adv && ((c.pin_adv[s[u]] >> (kq % c.Tg)) & 1u)) ? kq + 1 : kq;
+            m[u] = s[u] < c.ep_begin ? ld_relaxed_df(rbox_at(c, par, s[u], ks)->v + q)
+                                     : ld_state_df(c.rat + (size_t)s[u] * K + ks, q);
             nd[u] = __ldg(c.netD + (size_t)s[u] * K + kq);
         }
 #pragma unroll
@@ -617,8 +648,11 @@ __device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int
     }
     for (int p = b.f0; p < b.f1 && ok; ++p) {
         const int s = chk(c, __ldg(c.fo_pin + p), c.P);
-        if (s < c.ep_begin)
-            for (int k = kq + c.KL; k < K && ok; k += c.KL) ok = complete_df(rbox_at(c, par, s, k));
+        if (s < c.ep_begin) {
+            const int k0 = c.pin_adv ? 0 : kq + c.KL, dk = c.pin_adv ? 1 : c.KL;
+            for (int k = k0; k < K && ok; k += dk)
+                if (k != kq) ok = complete_df(rbox_at(c, par, s, k));
+        }
     }
     R = isfinite(rf) ? rw - rd : DF(rf);
     return ok;
@@ -647,8 +681,9 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
             DF rw(rf);
             for (int p = b.f0; p < b.f1; ++p) {
                 const int s = chk(c, c.fo_pin[p], c.P);
-                const DF rs = (WAIT && s < c.ep_begin) ? ld_relaxed_df(rbox_at(c, par, s, k)->v + q)
-                                                       : ld_state_df(c.rat + (size_t)s * K + k, q);
+                const int ks = (c.pin_adv && ((c.pin_adv[s] >> (k % c.Tg)) & 1u)) ? k + 1 : k;
+                const DF rs = (WAIT && s < c.ep_begin) ? ld_relaxed_df(rbox_at(c, par, s, ks)->v + q)
+                                                       : ld_state_df(c.rat + (size_t)s * K + ks, q);
                 const float nd = c.netD[(size_t)s * K + k];
                 const float v = rs.hi - nd;
                 if (el ? v < rf : v > rf) {

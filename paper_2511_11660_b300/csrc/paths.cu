@@ -118,13 +118,23 @@ __global__ void __launch_bounds__(1024) k_sel_sort(const PathJob j)
     if (threadIdx.x == 0) *j.count = (unsigned)m;
 }
 
-// One step of the trace back from pin p at edge rf; false at a startpoint.
+// One step of the trace back from pin p at edge rf in state k; false at a
+// startpoint.  Through a -through pin the path may come from the previous
+// tag's state: the one whose late arrival is larger (ties: the same tag).
 template <bool UNIFORM>
-__device__ bool trace_step(const DevCtx &c, const PathJob &j, int k, int &p, int &rf)
+__device__ bool trace_step(const DevCtx &c, const PathJob &j, int &k, int &p, int &rf)
 {
     const int K = c.K;
     const int drv = c.drv_of[p];
     if (drv >= 0) {   // net sink
+        if (c.pin_adv) {
+            const uint32_t adv = c.pin_adv[p];
+            const int tg = k % c.Tg;
+            const bool stay = !((adv >> tg) & 1u), inflow = tg >= 1 && ((adv >> (tg - 1)) & 1u);
+            if (inflow && (!stay || ld_state_df(c.at + (size_t)drv * K + k - 1, 2 + rf) >
+                                        ld_state_df(c.at + (size_t)drv * K + k, 2 + rf)))
+                --k;
+        }
         p = drv;
         return true;
     }

@@ -116,7 +116,19 @@ void build(const sta_design_desc *d, Plan &pl)
                               (d->exc_to || d->exc_to_ptr[d->n_exc] == 0)),
             STA_EINVAL, "exception arrays NULL");
     REQUIRE(d->n_exc == 0 || d->gamma_ns == 0.f, STA_EINVAL, "timing exceptions need gamma_ns = 0");
-    const int Tg = d->n_exc + 1, K = Kc * Tg;   // states: corner * Tg + tag
+    // tags: 0 = no group; group g owns 1 + (its through sets) tags, one per
+    // stage of its -through sequence
+    int Tg = 1;
+    if (d->n_exc > 0 && d->exc_thru_ptr) {
+        REQUIRE(d->exc_thru_set_ptr && (d->exc_thru_pin || d->exc_thru_set_ptr[d->exc_thru_ptr[d->n_exc]] == 0) &&
+                    d->exc_thru_ptr[0] == 0,
+                STA_EINVAL, "exception through arrays NULL or not starting at 0");
+        for (int g = 0; g < d->n_exc; ++g)
+            REQUIRE(d->exc_thru_ptr[g + 1] >= d->exc_thru_ptr[g], STA_EINVAL, "exception group %d: through offsets", g);
+    }
+    for (int g = 0; g < d->n_exc; ++g) Tg += 1 + (d->exc_thru_ptr ? d->exc_thru_ptr[g + 1] - d->exc_thru_ptr[g] : 0);
+    REQUIRE(Tg <= 32, STA_EINVAL, "%d exception tags (groups + their through sets) exceed 32", Tg);
+    const int K = Kc * Tg;   // states: corner * Tg + tag
     pl.Kc = Kc;
     pl.Tg = Tg;
     pl.K = K;
@@ -492,8 +504,14 @@ void build(const sta_design_desc *d, Plan &pl)
     // pin's first group) and the setup multiplier of every (endpoint, tag)
     pl.item_tag.clear();
     pl.ep_mult.clear();
+    pl.pin_adv.clear();
     if (pl.Tg > 1) {
-        const int32_t G = pl.Tg - 1;
+        const int32_t G = d->n_exc;
+        std::vector<int32_t> base(G + 1, 1), nthru(G, 0);   // first tag and through sets of each group
+        for (int32_t g = 0; g < G; ++g) {
+            nthru[g] = d->exc_thru_ptr ? d->exc_thru_ptr[g + 1] - d->exc_thru_ptr[g] : 0;
+            base[g + 1] = base[g] + nthru[g] + 1;
+        }
         std::vector<int8_t> tag_of(P, 0);
         std::vector<int32_t> caller_of(P, 0);
         for (int32_t p = 0; p < P; ++p) caller_of[pl.gpu_of[p]] = p;
@@ -505,7 +523,7 @@ void build(const sta_design_desc *d, Plan &pl)
                 const int32_t p = d->exc_from[i];
                 REQUIRE(p >= 0 && p < P && (d->pin_role[p] == kPinPI || d->pin_role[p] == kPinCK), STA_EINVAL,
                         "exception group %d: startpoint %d is not a PI or CK pin", g, p);
-                if (!tag_of[p]) tag_of[p] = (int8_t)(g + 1);
+                if (!tag_of[p]) tag_of[p] = (int8_t)base[g];
             }
             for (int32_t i = d->exc_to_ptr[g]; i < d->exc_to_ptr[g + 1]; ++i) {
                 const int32_t p = d->exc_to[i];
@@ -514,6 +532,19 @@ void build(const sta_design_desc *d, Plan &pl)
             }
             REQUIRE(d->exc_action[g] == 0 || (d->exc_action[g] == 1 && finite(d->exc_mult[g]) && d->exc_mult[g] >= 1.f),
                     STA_EINVAL, "exception group %d: action must be 0 (false path) or 1 (multicycle, M >= 1)", g);
+            // through set j + 1: the group's tag base + j moves on to base + j + 1 at its pins
+            for (int32_t j = 0; j < nthru[g]; ++j) {
+                const int32_t s = d->exc_thru_ptr[g] + j;
+                REQUIRE(d->exc_thru_set_ptr[s] >= 0 && d->exc_thru_set_ptr[s] <= d->exc_thru_set_ptr[s + 1], STA_EINVAL,
+                        "exception group %d: through set offsets not monotone", g);
+                for (int32_t i = d->exc_thru_set_ptr[s]; i < d->exc_thru_set_ptr[s + 1]; ++i) {
+                    const int32_t p = d->exc_thru_pin[i];
+                    REQUIRE(p >= 0 && p < P && d->pin_role[p] == kPinIN, STA_EINVAL,
+                            "exception group %d: through pin %d is not a gate input pin", g, p);
+                    if (pl.pin_adv.empty()) pl.pin_adv.assign(P, 0u);
+                    pl.pin_adv[pl.gpu_of[p]] |= 1u << (base[g] + j);
+                }
+            }
         }
         pl.item_tag.assign(pl.I, 0);
         for (int32_t g = 0; g < pl.I; ++g) {
@@ -526,9 +557,9 @@ void build(const sta_design_desc *d, Plan &pl)
         for (int32_t g = 0; g < G; ++g) {
             const bool all = d->exc_to_ptr[g] == d->exc_to_ptr[g + 1];
             for (int32_t i = d->exc_to_ptr[g]; i < d->exc_to_ptr[g + 1]; ++i) in_to[d->exc_to[i]] = 1;
-            for (int32_t e = 0; e < pl.E; ++e)
+            for (int32_t e = 0; e < pl.E; ++e)   // the fully matched tag gets the action
                 if (all || in_to[caller_of[pl.ep_pin[e]]])
-                    pl.ep_mult[(size_t)e * pl.Tg + g + 1] = d->exc_action[g] == 0 ? 0.f : d->exc_mult[g];
+                    pl.ep_mult[(size_t)e * pl.Tg + base[g] + nthru[g]] = d->exc_action[g] == 0 ? 0.f : d->exc_mult[g];
             for (int32_t i = d->exc_to_ptr[g]; i < d->exc_to_ptr[g + 1]; ++i) in_to[d->exc_to[i]] = 0;
         }
     }

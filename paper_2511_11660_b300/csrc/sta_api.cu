@@ -209,6 +209,7 @@ sta_status create_from_plan(sta_ctx *c, int device)
     if (pl.Tg > 1) {
         d.item_tag = upload(c, pl.item_tag);
         d.ep_mult = upload(c, pl.ep_mult);
+        d.pin_adv = pl.pin_adv.empty() ? nullptr : upload(c, pl.pin_adv);
     }
     {
         // reduction chunks: <= kRedChunk endpoints, never straddling designs

@@ -51,6 +51,7 @@ class sta_design_desc(C.Structure):
                 ("net_model", C.c_int32), ("arnoldi_order", C.c_int32), ("n_exc", C.c_int32),
                 ("exc_from_ptr", C.c_void_p), ("exc_from", C.c_void_p), ("exc_to_ptr", C.c_void_p),
                 ("exc_to", C.c_void_p), ("exc_action", C.c_void_p), ("exc_mult", C.c_void_p),
+                ("exc_thru_ptr", C.c_void_p), ("exc_thru_set_ptr", C.c_void_p), ("exc_thru_pin", C.c_void_p),
                 ("wire_model", C.c_int32), ("r_per_um_y", C.c_float), ("c_per_um_y", C.c_float)]
 
 
@@ -172,7 +173,8 @@ class Design:
             "net_pin": np.int32, "rc_ptr": np.int32, "rc_parent": np.int32, "rc_pin_node": np.int32,
             "rc_R": np.float32, "rc_C": np.float32, "cell_xy": np.float32, "port_xy": np.float32,
             "lut_scale": np.float32, "rc_scale": np.float32, "exc_from_ptr": np.int32, "exc_from": np.int32,
-            "exc_to_ptr": np.int32, "exc_to": np.int32, "exc_action": np.int32, "exc_mult": np.float32}
+            "exc_to_ptr": np.int32, "exc_to": np.int32, "exc_action": np.int32, "exc_mult": np.float32,
+            "exc_thru_ptr": np.int32, "exc_thru_set_ptr": np.int32, "exc_thru_pin": np.int32}
 
     def __init__(self, d: dict):
         self.src = d
@@ -197,6 +199,7 @@ class Design:
             int(d.get("net_model", 0)), int(d.get("arnoldi_order", 0)),
             0 if a["exc_action"] is None else len(a["exc_action"]), _ptr(a["exc_from_ptr"]), _ptr(a["exc_from"]),
             _ptr(a["exc_to_ptr"]), _ptr(a["exc_to"]), _ptr(a["exc_action"]), _ptr(a["exc_mult"]),
+            _ptr(a["exc_thru_ptr"]), _ptr(a["exc_thru_set_ptr"]), _ptr(a["exc_thru_pin"]),
             int(d.get("wire_model", 0)), float(d.get("r_per_um_y", 0.0)), float(d.get("c_per_um_y", 0.0)))
 
     @property

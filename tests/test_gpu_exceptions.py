@@ -1,5 +1,6 @@
-"""GPU timing exceptions (false paths and multicycle paths by startpoint group
-and endpoint list) against the FP64 oracle.
+"""GPU timing exceptions (false paths and multicycle paths by startpoint group,
+ordered -through sets of gate inputs and endpoint list) against the FP64
+oracle.
 
 Every per-pin array holds one state per (corner, exception tag) and is
 compared element by element (infinities equal: an absent tag's arrival is
@@ -27,7 +28,7 @@ def _lib():
     sta.load()
 
 
-def _design(case, seed, n_groups):
+def _design(case, seed, n_groups, max_thru=0):
     rng = np.random.default_rng(100 + seed)
     if case == "corners":
         ls, rs = synth.lut_corners()
@@ -38,7 +39,7 @@ def _design(case, seed, n_groups):
     else:
         d = synth.workload("tiny", seed=seed)
         d["period_ns"], _ = tune_period(d)
-    d.update(synth.exception_groups(d, rng, n_groups))
+    d.update(synth.exception_groups(d, rng, n_groups, max_thru=max_thru))
     return d
 
 
@@ -52,7 +53,7 @@ def _gpu(ctx):
 
 def check(d, g, ref):
     K = int(d.get("n_corners", 1))
-    Tg = 1 + len(d["exc_action"])
+    Tg = oracle.n_tags(d)
     for k in ("at", "slew", "rat", "slack"):
         assert g[k].shape == ref[k].shape == (d["n_pins"], K * Tg, 4)
         assert_close(k, g[k], ref[k])
@@ -74,16 +75,18 @@ def check(d, g, ref):
             1e-5 * abs(ref["tns_hold"][k])
 
 
-@pytest.mark.parametrize("case,seed,n_groups", [("tiny", 0, 1), ("tiny", 1, 3), ("tiny", 2, 7),
-                                                ("corners", 4, 3), ("placed", 5, 2)])
-def test_exceptions_parity_all_schedules(case, seed, n_groups):
-    d = _design(case, seed, n_groups)
+@pytest.mark.parametrize("case,seed,n_groups,max_thru", [("tiny", 0, 1, 0), ("tiny", 1, 3, 0), ("tiny", 2, 7, 0),
+                                                         ("corners", 4, 3, 0), ("placed", 5, 2, 0),
+                                                         ("tiny", 6, 3, 2), ("tiny", 7, 5, 3),
+                                                         ("corners", 8, 2, 2)])
+def test_exceptions_parity_all_schedules(case, seed, n_groups, max_thru):
+    d = _design(case, seed, n_groups, max_thru)
     ref = oracle.sta(d)
     # the groups must change something: some endpoint's slack differs from the unconstrained analysis
     plain = {k: v for k, v in d.items() if not k.startswith("exc_")}
     assert not np.allclose(oracle.sta(plain)["ep_setup"], ref["ep_setup"])
     ctx = sta.Context(d)
-    assert ctx.stats()["n_tags"] == n_groups + 1
+    assert ctx.stats()["n_tags"] == oracle.n_tags(d)
     for sch in SCHEDULES:
         ctx.set_schedule(sch)
         ctx.update_timing()
@@ -127,9 +130,10 @@ def test_exceptions_all_false_paths_leave_no_checks():
     ctx.close()
 
 
-@pytest.mark.parametrize("case,seed,n_groups,corner", [("tiny", 1, 3, 0), ("corners", 4, 3, 2)])
-def test_exceptions_paths(case, seed, n_groups, corner):
-    d = _design(case, seed, n_groups)
+@pytest.mark.parametrize("case,seed,n_groups,corner,max_thru", [("tiny", 1, 3, 0, 0), ("corners", 4, 3, 2, 0),
+                                                                ("tiny", 6, 3, 0, 2), ("corners", 8, 2, 1, 2)])
+def test_exceptions_paths(case, seed, n_groups, corner, max_thru):
+    d = _design(case, seed, n_groups, max_thru)
     res = oracle.sta(d)
     ctx = sta.Context(d)
     ctx.update_timing()
@@ -141,11 +145,14 @@ def test_exceptions_paths(case, seed, n_groups, corner):
     ctx.close()
 
 
-def test_exceptions_full_size():
-    """The 1M-cell workload with three exception groups (four tags)."""
+@pytest.mark.parametrize("max_thru", [0, 2])
+def test_exceptions_full_size(max_thru):
+    """The 1M-cell workload with three exception groups (four tags; with
+    through sets of 1/64 of the gate inputs, up to ten)."""
     d = synth.workload("scale", seed=0)
     d["period_ns"], _ = tune_period(d)
-    d.update(synth.exception_groups(d, np.random.default_rng(9), 3, div_from=5, div_to=4))
+    d.update(synth.exception_groups(d, np.random.default_rng(9), 3, div_from=5, div_to=4, max_thru=max_thru,
+                                    div_thru=64))
     ref = oracle.sta(d)
     ctx = sta.Context(d)
     ctx.update_timing()

@@ -35,7 +35,8 @@ def check_paths(d, gpu, res, k, slack_lt=np.inf, corner=0):
     states whose late slack at its endpoint is within tolerance of the
     smallest: it must be valid and critical in one of them."""
     net = _indep.Net(d, corner)
-    Tg = 1 + (len(d["exc_action"]) if d.get("exc_action") is not None else 0)
+    Tg = oracle.n_tags(d)
+    _, adv = oracle.tag_layout(d)
     role = np.asarray(d["pin_role"])
     K = int(d.get("n_corners", 1))
     sc = float(np.asarray(d["lut_scale"] if d.get("lut_scale") is not None else np.ones(K))[corner])
@@ -57,23 +58,40 @@ def check_paths(d, gpu, res, k, slack_lt=np.inf, corner=0):
         s = [p["slack"] for p in gpu]
         assert all(a <= b for a, b in zip(s, s[1:]))
 
-    def check_one(p, st):
-        at, slew = res["at"][:, st], res["slew"][:, st]
+    def check_one(p, st_end):
+        pins, rfs, ats = p["pins"], p["rf"], p["at"]
+        # the state at every pin: it changes only at -through pins, to the
+        # previous tag's state when that one carries the larger late arrival
+        sts = [st_end] * len(pins)
+        for i in range(len(pins) - 1, 0, -1):
+            st = sts[i]
+            v, u = int(pins[i]), int(pins[i - 1])
+            if net.driver.get(v) == u:
+                tg = st - corner * Tg
+                a = adv.get(v, 0)
+                stay, inflow = not (a >> tg) & 1, tg >= 1 and (a >> (tg - 1)) & 1
+                r = 2 + int(rfs[i])
+                a_st, a_prev = res["at"][u, st, r], res["at"][u, st - 1, r]
+                if inflow and (not stay or a_prev > a_st + (tol(a_st) if np.isfinite(a_st) else 0.0)):
+                    st -= 1
+            sts[i - 1] = st
 
-        def cand(v, rv, u, ru):
+        def cand(v, rv, u, ru, st):
+            at, slew = res["at"][:, st], res["slew"][:, st]
             c = net.cell_of[v]
             t = d["cell_type"][c]
             j = net.slot_of[u]
             dl = oracle.lut_eval(i1[t, j, rv], i2[t, j, rv], vv[t, j, rv], slew[u, 2 + ru], net.load[v])[0]
             return at[u, 2 + ru] + sc * dl
 
-        pins, rfs, ats = p["pins"], p["rf"], p["at"]
         assert pins[-1] == p["endpoint"]
         assert role[pins[0]] in (synth.PI, synth.CK)
-        for q, r, a in zip(pins, rfs, ats):
-            assert abs(a - at[q, 2 + r]) <= tol(at[q, 2 + r])
+        for q, r, a, st in zip(pins, rfs, ats, sts):
+            ref = res["at"][q, st, 2 + r]
+            assert abs(a - ref) <= tol(ref)
         for i in range(1, len(pins)):
             u, ru, v, rv = int(pins[i - 1]), int(rfs[i - 1]), int(pins[i]), int(rfs[i])
+            st = sts[i]
             if net.driver.get(v) == u:
                 assert ru == rv
                 continue
@@ -84,9 +102,9 @@ def check_paths(d, gpu, res, k, slack_lt=np.inf, corner=0):
                 assert ru == 0 and sense[t, net.slot_of[u]] == _indep.RISE
                 continue
             assert ru in _indep.rf_in_of(sense[t, net.slot_of[u]], rv)
-            best = max(cand(v, rv, int(cp[cpp[c] + j]), r2) for j in range(d["type_nin"][t])
+            best = max(cand(v, rv, int(cp[cpp[c] + j]), r2, st) for j in range(d["type_nin"][t])
                        for r2 in _indep.rf_in_of(sense[t, j], rv))
-            assert cand(v, rv, u, ru) >= best - 2 * tol(best)
+            assert cand(v, rv, u, ru, st) >= best - 2 * tol(best)
 
     for p in gpu:
         e = int(p["endpoint"])

@@ -131,6 +131,17 @@ def test_plan_exception_validation(lib):
             dict(d, **dict(g3, exc_from_ptr=g3["exc_from_ptr"][[0, 2, 1, 3]]))]
     if len(g3["exc_to"]):
         bads.append(dict(d, **dict(g3, exc_to=np.where(np.arange(len(g3["exc_to"])) == 0, ck_pin, g3["exc_to"]))))
+    # -through: the stages add tags; a through pin must be a gate input; at most 32 tags
+    gt = synth.exception_groups(d, np.random.default_rng(5), 3, max_thru=2)
+    assert sta.sta_plan(dict(d, **gt))["n_tags"] == 1 + 3 + int(gt["exc_thru_ptr"][-1])
+    out_pin = int(np.nonzero(role == synth.OUT)[0][0])
+    if len(gt["exc_thru_pin"]):
+        bads.append(dict(d, **dict(gt, exc_thru_pin=np.where(np.arange(len(gt["exc_thru_pin"])) == 0, out_pin,
+                                                                  gt["exc_thru_pin"]))))
+    many = dict(g3, exc_thru_ptr=np.array([0, 10, 20, 30], np.int32),
+                exc_thru_set_ptr=np.arange(31, dtype=np.int32),
+                exc_thru_pin=np.full(30, int(np.nonzero(role == synth.IN)[0][0]), np.int32))
+    bads.append(dict(d, **many))   # 1 + 3 * 11 = 34 tags
     for i, bad in enumerate(bads):
         with pytest.raises(sta.StaError) as ei:
             sta.sta_plan(bad)
