@@ -102,6 +102,62 @@ struct Work {
     __device__ __forceinline__ long long dist(int a, int b) const { return mdist(x(a), y(a), x(b), y(b)); }
 };
 
+// Breadth-first numbering from the driver and the RC arrays of item g's
+// tree (N working nodes; without Steiner points the MST by its sources).
+template <class TX, class TI>
+__device__ void write_tree(const DevCtx &c, int g, int f0, int n, int N, bool steinerise, const Work<TX, TI> &w)
+{
+    const int n0 = c.rc_ptr[g], tcap = c.rc_ptr[g + 1] - n0;   // 2 m nodes
+    for (int i = 0; i < N; ++i) w.set_id(i, -1);
+    int head = 0, tail = 1, nodes = 1;   // queue of working nodes; RC nodes written
+    w.set_qu(0, 0);
+    w.set_id(0, 0);
+    w.cp(0) = 0.f;
+    c.st_parent[n0] = -1;
+    c.st_R[n0] = 0.f;
+    long long total = 0;
+    const float rx = c.r_per_um, ry = c.r_per_um_y, cx = c.c_per_um, cy = c.c_per_um_y;
+    auto visit = [&](int a, int b) -> bool {
+        if (w.id(b) >= 0) return true;
+        w.set_qu(tail++, b);   // tail <= N <= cap: each working node is queued once
+        const long long ax = llabs(w.x(b) - w.x(a)), ay = llabs(w.y(b) - w.y(a));
+        const int ia = w.id(a);
+        if (ax + ay == 0) {   // the same point: the same RC node (no zero-length edge)
+            w.set_id(b, ia);
+            return true;
+        }
+        if (nodes >= tcap) {   // not reached: <= 2 n - 2 live nodes
+            atomicOr(c.err, kErrBounds);
+            return false;
+        }
+        w.set_id(b, nodes);
+        total += ax + ay;
+        const float lx = 1e-3f * (float)ax, ly = 1e-3f * (float)ay;
+        const float half = 0.5f * (cx * lx + cy * ly);
+        c.st_parent[n0 + nodes] = ia;
+        c.st_R[n0 + nodes] = rx * lx + ry * ly;
+        w.cp(nodes) = half;
+        w.cp(ia) += half;
+        ++nodes;
+        return true;
+    };
+    while (head < tail) {
+        const int a = w.qu(head++);
+        if (steinerise) {
+            for (int q = 0; q < w.W; ++q)
+                for (unsigned mk = w.wd(a, q); mk; mk &= mk - 1)
+                    if (!visit(a, q * 32 + __ffs(mk) - 1)) return;
+        } else {   // the MST by its sources: the parent (visited) and the children, ascending
+            for (int b = 0; b < n; ++b)
+                if (w.sr(b) == a && !visit(a, b)) return;
+        }
+    }
+    for (int i = 0; i < nodes; ++i) c.st_C[n0 + i] = w.cp(i);
+    for (int j = 1; j < n; ++j) c.st_fo_node[f0 + j - 1] = w.id(j);
+    c.st_nlive[g] = nodes;
+    c.st_wl[g] = total;
+}
+
 // The tree of item g's net (f0: first sink, m >= 1 sinks) in storage w.
 template <class TX, class TI>
 __device__ void steiner_net(const DevCtx &c, int g, int f0, int m, const Work<TX, TI> &w)
@@ -233,56 +289,7 @@ __device__ void steiner_net(const DevCtx &c, int g, int f0, int m, const Work<TX
         }
     }
 
-    // breadth-first numbering from the driver -> the RC tree of the net
-    const int n0 = c.rc_ptr[g], tcap = c.rc_ptr[g + 1] - n0;   // 2 m nodes
-    for (int i = 0; i < N; ++i) w.set_id(i, -1);
-    int head = 0, tail = 1, nodes = 1;   // queue of working nodes; RC nodes written
-    w.set_qu(0, 0);
-    w.set_id(0, 0);
-    w.cp(0) = 0.f;
-    c.st_parent[n0] = -1;
-    c.st_R[n0] = 0.f;
-    long long total = 0;
-    const float rx = c.r_per_um, ry = c.r_per_um_y, cx = c.c_per_um, cy = c.c_per_um_y;
-    auto visit = [&](int a, int b) -> bool {
-        if (w.id(b) >= 0) return true;
-        w.set_qu(tail++, b);   // tail <= N <= cap: each working node is queued once
-        const long long ax = llabs(w.x(b) - w.x(a)), ay = llabs(w.y(b) - w.y(a));
-        const int ia = w.id(a);
-        if (ax + ay == 0) {   // the same point: the same RC node (no zero-length edge)
-            w.set_id(b, ia);
-            return true;
-        }
-        if (nodes >= tcap) {   // not reached: <= 2 n - 2 live nodes
-            atomicOr(c.err, kErrBounds);
-            return false;
-        }
-        w.set_id(b, nodes);
-        total += ax + ay;
-        const float lx = 1e-3f * (float)ax, ly = 1e-3f * (float)ay;
-        const float half = 0.5f * (cx * lx + cy * ly);
-        c.st_parent[n0 + nodes] = ia;
-        c.st_R[n0 + nodes] = rx * lx + ry * ly;
-        w.cp(nodes) = half;
-        w.cp(ia) += half;
-        ++nodes;
-        return true;
-    };
-    while (head < tail) {
-        const int a = w.qu(head++);
-        if (steinerise) {
-            for (int q = 0; q < w.W; ++q)
-                for (unsigned mk = w.wd(a, q); mk; mk &= mk - 1)
-                    if (!visit(a, q * 32 + __ffs(mk) - 1)) return;
-        } else {   // the MST by its sources: the parent (visited) and the children, ascending
-            for (int b = 0; b < n; ++b)
-                if (w.sr(b) == a && !visit(a, b)) return;
-        }
-    }
-    for (int i = 0; i < nodes; ++i) c.st_C[n0 + i] = w.cp(i);
-    for (int j = 1; j < n; ++j) c.st_fo_node[f0 + j - 1] = w.id(j);
-    c.st_nlive[g] = nodes;
-    c.st_wl[g] = total;
+    write_tree(c, g, f0, n, N, steinerise, w);
 }
 
 // Nets of at most kSmallPins pins: working storage in shared memory, one
@@ -327,20 +334,46 @@ __device__ __forceinline__ void warp_min_key(long long &k, int &u)
     }
 }
 
+// One warp's storage in shared memory, for nets of at most kStMaxPins pins.
+constexpr int kWarpCap = 3 * kStMaxPins, kWarpW = (kWarpCap + 31) / 32;
+struct WarpSmem {
+    int32_t x[kWarpCap], y[kWarpCap];
+    long long key[kStMaxPins];
+    int16_t src[kStMaxPins], nid[kWarpCap], q[kWarpCap];
+    unsigned adj[kWarpCap * kWarpW];
+    float cap[2 * kStMaxPins];
+};
+
+template <class TX, class TI>
+__device__ void warp_net(const DevCtx &c, int g, int f0, int n, int lane, const Work<TX, TI> &w);
+
 __global__ void __launch_bounds__(32 * kWarpNets) k_net_steiner_warp(const DevCtx c)
 {
-    const int lane = threadIdx.x & 31;
-    const int i = c.st_small + blockIdx.x * kWarpNets + (threadIdx.x >> 5);
+    __shared__ WarpSmem sm[kWarpNets];
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const int i = c.st_small + blockIdx.x * kWarpNets + wi;
     if (i >= c.st_n_items) return;   // the whole warp
     const int g = chk(c, c.st_items[i], c.I);
     const int f0 = c.fo_ptr[g], m = c.fo_ptr[g + 1] - f0;
     const int n = m + 1, cap = 3 * n;
-    const long long nb = c.st_node_ptr[g];
-    int32_t *aux = c.st_aux + 3 * nb;
+    if (n <= kStMaxPins) {   // working storage in shared memory
+        WarpSmem &S = sm[wi];
+        const Work<int32_t, int16_t> w{S.x, S.y, S.key, S.src, S.nid, S.q, S.adj, S.cap, 1, (cap + 31) >> 5};
+        warp_net(c, g, f0, n, lane, w);
+    } else {                 // the MST of a large net, in global scratch
+        const long long nb = c.st_node_ptr[g];
+        int32_t *aux = c.st_aux + 3 * nb;
+        const Work<long long, int32_t> w{c.st_x + nb, c.st_y + nb, c.st_key + nb, aux, aux + cap, aux + 2 * cap,
+                                         nullptr, c.st_capw + nb, 1, (cap + 31) >> 5};
+        warp_net(c, g, f0, n, lane, w);
+    }
+}
+
+template <class TX, class TI>
+__device__ void warp_net(const DevCtx &c, int g, int f0, int n, int lane, const Work<TX, TI> &w)
+{
+    const int cap = 3 * n;
     const bool steinerise = n <= kStMaxPins;
-    const Work<long long, int32_t> w{c.st_x + nb, c.st_y + nb, c.st_key + nb, aux, aux + cap, aux + 2 * cap,
-                                     steinerise ? c.st_adj + c.st_adj_ptr[g] : nullptr, c.st_capw + nb, 1,
-                                     (cap + 31) >> 5};
     // pins (0 = the driver, then the sinks in net order), keys, adjacency
     for (int j = lane; j < n; j += 32) {
         const int p = j == 0 ? chk(c, item_out_pin(c, chk_type(c, c.item_type[g]), c.item_pin0[g]), c.P)
@@ -455,14 +488,21 @@ __global__ void __launch_bounds__(32 * kWarpNets) k_net_steiner_warp(const DevCt
                     w.link(s, bv);
                     w.link(s, bw);
                 }
-                for (;;) {   // remove Steiner nodes with <= 2 neighbours, lowest index first
-                    int s = -1, dg = 0;
-                    for (int x = n; x < N; ++x)
-                        if (w.id(x) && (dg = w.deg(x)) <= 2) {
-                            s = x;
-                            break;
-                        }
-                    if (s < 0) break;
+            }
+            N = __shfl_sync(0xffffffffu, N, 0);
+            if (__shfl_sync(0xffffffffu, err, 0)) return;
+            __syncwarp();
+            for (;;) {   // remove Steiner nodes with <= 2 neighbours, lowest index first (lanes scan)
+                int s = INT_MAX;
+                for (int x = n + lane; x < N; x += 32)
+                    if (w.id(x) && w.deg(x) <= 2) {
+                        s = x;
+                        break;
+                    }
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) s = min(s, __shfl_xor_sync(0xffffffffu, s, off));
+                if (s == INT_MAX) break;
+                if (lane == 0) {
                     int nb2[2] = {-1, -1}, k = 0;
                     for (int q = 0; q < w.W; ++q)
                         for (unsigned mk = w.wd(s, q); mk; mk &= mk - 1) {
@@ -471,66 +511,14 @@ __global__ void __launch_bounds__(32 * kWarpNets) k_net_steiner_warp(const DevCt
                             ++k;
                         }
                     for (int q = 0; q < k && q < 2; ++q) w.cut(s, nb2[q]);
-                    if (dg == 2) w.link(nb2[0], nb2[1]);
+                    if (k == 2) w.link(nb2[0], nb2[1]);
                     w.set_id(s, 0);
                 }
+                __syncwarp();
             }
-            N = __shfl_sync(0xffffffffu, N, 0);
-            if (__shfl_sync(0xffffffffu, err, 0)) return;
-            __syncwarp();
         }
     }
-    // breadth-first numbering and the RC arrays: lane 0, as steiner_net does
-    if (lane != 0) return;
-    const int n0 = c.rc_ptr[g], tcap = c.rc_ptr[g + 1] - n0;
-    for (int x = 0; x < N; ++x) w.set_id(x, -1);
-    int head = 0, tail = 1, nodes = 1;
-    w.set_qu(0, 0);
-    w.set_id(0, 0);
-    w.cp(0) = 0.f;
-    c.st_parent[n0] = -1;
-    c.st_R[n0] = 0.f;
-    long long total = 0;
-    const float rx = c.r_per_um, ry = c.r_per_um_y, cx = c.c_per_um, cy = c.c_per_um_y;
-    auto visit = [&](int a, int b) -> bool {
-        if (w.id(b) >= 0) return true;
-        w.set_qu(tail++, b);
-        const long long ax = llabs(w.x(b) - w.x(a)), ay = llabs(w.y(b) - w.y(a));
-        const int ia = w.id(a);
-        if (ax + ay == 0) {
-            w.set_id(b, ia);
-            return true;
-        }
-        if (nodes >= tcap) {
-            atomicOr(c.err, kErrBounds);
-            return false;
-        }
-        w.set_id(b, nodes);
-        total += ax + ay;
-        const float lx = 1e-3f * (float)ax, ly = 1e-3f * (float)ay;
-        const float half = 0.5f * (cx * lx + cy * ly);
-        c.st_parent[n0 + nodes] = ia;
-        c.st_R[n0 + nodes] = rx * lx + ry * ly;
-        w.cp(nodes) = half;
-        w.cp(ia) += half;
-        ++nodes;
-        return true;
-    };
-    while (head < tail) {
-        const int a = w.qu(head++);
-        if (steinerise) {
-            for (int q = 0; q < w.W; ++q)
-                for (unsigned mk = w.wd(a, q); mk; mk &= mk - 1)
-                    if (!visit(a, q * 32 + __ffs(mk) - 1)) return;
-        } else {
-            for (int b = 0; b < n; ++b)
-                if (w.sr(b) == a && !visit(a, b)) return;
-        }
-    }
-    for (int x = 0; x < nodes; ++x) c.st_C[n0 + x] = w.cp(x);
-    for (int j = 1; j < n; ++j) c.st_fo_node[f0 + j - 1] = w.id(j);
-    c.st_nlive[g] = nodes;
-    c.st_wl[g] = total;
+    if (lane == 0) write_tree(c, g, f0, n, N, steinerise, w);   // lane 0, as steiner_net does
 }
 
 }  // namespace
