@@ -99,7 +99,7 @@ __device__ __forceinline__ bool warp_idle_round(const DevCtx &c, long long &spin
     return true;
 }
 
-template <bool SMOOTH, bool UNIFORM>
+template <bool SMOOTH, bool UNIFORM, bool THRU>
 __global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
 {
     extern __shared__ float smem[];
@@ -123,8 +123,8 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
             if (pending) {
                 FwdIn in;
                 if (is_item) {
-                    if (group_all(c, fwd_probe(c, f, par, q, in))) {
-                        fwd_run<SMOOTH, UNIFORM, true>(c, L.lut, f, in, x, q, par);
+                    if (group_all(c, fwd_probe<THRU>(c, f, par, q, in))) {
+                        fwd_run<SMOOTH, UNIFORM, true, THRU>(c, L.lut, f, in, x, q, par);
                         pending = false;
                     }
                 } else if (group_all(c, ep_probe(c, e, par, q, in.at[0], in.sl[0]))) {
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
     }
 }
 
-template <bool UNIFORM>
+template <bool UNIFORM, bool THRU>
 __global__ void __launch_bounds__(kDfThreads) k_df_backward(const DevCtx c)
 {
     extern __shared__ float smem[];
@@ -154,8 +154,8 @@ __global__ void __launch_bounds__(kDfThreads) k_df_backward(const DevCtx c)
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
             DF R;
-            if (pending && group_all(c, bwd_probe(c, b, par, q, R))) {
-                bwd_run<UNIFORM, true>(c, L.lut, L.sense, b, q, par, R);
+            if (pending && group_all(c, bwd_probe<THRU>(c, b, par, q, R))) {
+                bwd_run<UNIFORM, true, THRU>(c, L.lut, L.sense, b, q, par, R);
                 pending = false;
             }
             if (__any_sync(0xffffffffu, pending) && !warp_idle_round(c, spins)) break;
@@ -179,14 +179,29 @@ static cudaError_t occupancy_blocks(F kernel, size_t smem, int *blocks)
 
 size_t dataflow_smem_bytes(int T) { return df_smem_bytes(T); }
 
+// The persistent kernels for a schedule: smoothed merges, shared table axes,
+// and -through sets each select a compiled variant.
+using DfKernel = void (*)(DevCtx);
+static DfKernel df_forward_kernel(bool smooth, bool uniform, bool thru)
+{
+    if (thru) return smooth ? (uniform ? k_df_forward<true, true, true> : k_df_forward<true, false, true>)
+                            : (uniform ? k_df_forward<false, true, true> : k_df_forward<false, false, true>);
+    return smooth ? (uniform ? k_df_forward<true, true, false> : k_df_forward<true, false, false>)
+                  : (uniform ? k_df_forward<false, true, false> : k_df_forward<false, false, false>);
+}
+static DfKernel df_backward_kernel(bool uniform, bool thru)
+{
+    if (thru) return uniform ? k_df_backward<true, true> : k_df_backward<false, true>;
+    return uniform ? k_df_backward<true, false> : k_df_backward<false, false>;
+}
+
 // Shared-memory attribute and persistent grid sizes, computed outside any
 // stream capture.  `requested` > 0 fixes the grid size.
 cudaError_t dataflow_prepare(HostSched &h, bool smooth, int requested)
 {
     const size_t smem = df_smem_bytes(h.T);
-    auto kf = smooth ? (h.uniform ? k_df_forward<true, true> : k_df_forward<true, false>)
-                     : (h.uniform ? k_df_forward<false, true> : k_df_forward<false, false>);
-    auto kb = h.uniform ? k_df_backward<true> : k_df_backward<false>;
+    auto kf = df_forward_kernel(smooth, h.uniform, h.thru);
+    auto kb = df_backward_kernel(h.uniform, h.thru);
     int bf = 0, bb = 0;
     cudaError_t e = occupancy_blocks(kf, smem, &bf);
     if (e == cudaSuccess) e = occupancy_blocks(kb, smem, &bb);
@@ -342,14 +357,11 @@ void launch_dataflow_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, 
     launch_net_phase(c, h, st);
     if (ev) cudaEventRecord(ev[1], st);
     if (c.n_fwd_chunks > 0) {
-        auto kf = c.gamma > 0.f ? (h.uniform ? k_df_forward<true, true> : k_df_forward<true, false>)
-                                : (h.uniform ? k_df_forward<false, true> : k_df_forward<false, false>);
-        kf<<<h.df_blocks_fwd, kDfThreads, smem, st>>>(c);
+        df_forward_kernel(c.gamma > 0.f, h.uniform, h.thru)<<<h.df_blocks_fwd, kDfThreads, smem, st>>>(c);
     }
     if (ev) cudaEventRecord(ev[2], st);
     if (c.n_bwd_chunks > 0) {
-        auto kb = h.uniform ? k_df_backward<true> : k_df_backward<false>;
-        kb<<<h.df_blocks_bwd, kDfThreads, smem, st>>>(c);
+        df_backward_kernel(h.uniform, h.thru)<<<h.df_blocks_bwd, kDfThreads, smem, st>>>(c);
     }
     if (ev) cudaEventRecord(ev[3], st);
     launch_reduce(c, h, st);

@@ -302,8 +302,12 @@ __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, co
 // Are the drivers' arrivals and slews of the lane's corners complete?  Lane
 // q reads component q of its first corner (returned in `in`); the caller's
 // group_all over the quad covers the four components.
+// THRU = false: the design has no -through sets (c.pin_adv is NULL); the
+// kernels compiled so carry none of their code and registers.
+template <bool THRU = true>
 __device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int par, int q, FwdIn &in)
 {
+    const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
     bool ok = true;
     const int kq = corner_lane(c);
 #pragma unroll
@@ -314,7 +318,7 @@ __device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int
             ok = ok && real_df(in.at[j]) && in.sl[j] == in.sl[j];
             // the lane's other states; with -through every state (a path may
             // come in from the previous tag)
-            const int k0 = c.pin_adv ? 0 : kq + c.KL, dk = c.pin_adv ? 1 : c.KL;
+            const int k0 = pin_adv ? 0 : kq + c.KL, dk = pin_adv ? 1 : c.KL;
             for (int k = k0; k < c.K && ok; k += dk)
                 if (k != kq)
                     ok = complete_df(fbox_a(c, par, f.drv[j], k)) &&
@@ -325,10 +329,11 @@ __device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int
 }
 
 // Lane q of the quad computes component q = el*2 + rf of the item's states.
-template <bool SMOOTH, bool UNIFORM, bool WAIT, class L>
+template <bool SMOOTH, bool UNIFORM, bool WAIT, bool THRU = true, class L>
 __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const FwdItem &f, const FwdIn &in, int g,
                                         int q, int par)
 {
+    const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
     const int K = c.K, t = f.t, pin0 = f.pin0, nin = f.nin;
     const int el = q >> 1, rfo = q & 1;
     const int kq = corner_lane(c), KL = c.KL;
@@ -377,7 +382,7 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
                 const int a = pin0 + j;
                 DF a0, a1;   // the driver's rise / fall arrival and slew at this lane's el
                 float s0, s1;
-                const uint32_t adv = c.pin_adv ? c.pin_adv[a] : 0u;
+                const uint32_t adv = pin_adv ? pin_adv[a] : 0u;
                 if (adv) {
                     // -through: a path in this state's tag t stays unless a
                     // advances t; one in tag t - 1 comes in when a advances t - 1
@@ -607,8 +612,10 @@ __device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, co
 // folds them: R = min (late) / max (early) over the sinks of RAT - Elmore
 // delay, component q -- the output's required time, ready for bwd_run.
 // Endpoint sinks were set by the forward pass.
+template <bool THRU = true>
 __device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int par, int q, DF &R)
 {
+    const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
     const int K = c.K, kq = corner_lane(c);
     const bool late = q >= 2;
     bool ok = true;
@@ -626,7 +633,7 @@ __device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int
         for (int u = 0; u < 4; ++u) {
             if (s[u] < 0) continue;
             // -through: a path in tag t continues in t + 1 beyond a sink that advances t
-            const int ks = (c.pin_adv && ((c.pin_adv[s[u]] >> (kq % c.Tg)) & 1u)) ? kq + 1 : kq;
+            const int ks = (pin_adv && ((pin_adv[s[u]] >> (kq % c.Tg)) & 1u)) ? kq + 1 : kq;
             m[u] = s[u] < c.ep_begin ? ld_relaxed_df(rbox_at(c, par, s[u], ks)->v + q)
                                      : ld_state_df(c.rat + (size_t)s[u] * K + ks, q);
             nd[u] = __ldg(c.netD + (size_t)s[u] * K + kq);
@@ -649,7 +656,7 @@ __device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int
     for (int p = b.f0; p < b.f1 && ok; ++p) {
         const int s = chk(c, __ldg(c.fo_pin + p), c.P);
         if (s < c.ep_begin) {
-            const int k0 = c.pin_adv ? 0 : kq + c.KL, dk = c.pin_adv ? 1 : c.KL;
+            const int k0 = pin_adv ? 0 : kq + c.KL, dk = pin_adv ? 1 : c.KL;
             for (int k = k0; k < K && ok; k += dk)
                 if (k != kq) ok = complete_df(rbox_at(c, par, s, k));
         }
@@ -661,10 +668,11 @@ __device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int
 // Lane q = el*2 + rfi: the output's required time (component q) over its
 // net sinks, then each input pin's over its arcs, and pin slacks.  With WAIT
 // the first corner's output required time comes folded from bwd_probe (Rpre).
-template <bool UNIFORM, bool WAIT, class L>
+template <bool UNIFORM, bool WAIT, bool THRU = true, class L>
 __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int *tsense, const BwdItem &b, int q,
                                         int par, DF Rpre)
 {
+    const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
     const int t = b.t, pin0 = b.pin0, z = b.z, K = c.K;
     const int el = q >> 1, rfi = q & 1;
     const unsigned m = quad_mask();
@@ -681,7 +689,7 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
             DF rw(rf);
             for (int p = b.f0; p < b.f1; ++p) {
                 const int s = chk(c, c.fo_pin[p], c.P);
-                const int ks = (c.pin_adv && ((c.pin_adv[s] >> (k % c.Tg)) & 1u)) ? k + 1 : k;
+                const int ks = (pin_adv && ((pin_adv[s] >> (k % c.Tg)) & 1u)) ? k + 1 : k;
                 const DF rs = (WAIT && s < c.ep_begin) ? ld_relaxed_df(rbox_at(c, par, s, ks)->v + q)
                                                        : ld_state_df(c.rat + (size_t)s * K + ks, q);
                 const float nd = c.netD[(size_t)s * K + k];

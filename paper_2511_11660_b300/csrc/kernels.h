@@ -15,6 +15,7 @@ struct HostSched {
     bool rc = false;                  // RC trees to sweep (tree mode with nodes)
     bool placed = false;
     bool steiner = false;             // Steiner trees built from positions before the RC sweep
+    bool thru = false;                // -through exception sets (the dataflow kernels' variant)
     int threads = 128;                // threads per block of the level kernels
     int n_red_chunks = 0;             // first-stage reduction blocks
     bool uniform = false;             // every table shares the same slew and load axes

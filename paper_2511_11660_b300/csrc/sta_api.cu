@@ -272,6 +272,7 @@ sta_status create_from_plan(sta_ctx *c, int device)
     h.rc = !pl.placed && pl.NN > 0;
     h.placed = pl.placed;
     h.steiner = pl.steiner;
+    h.thru = !pl.pin_adv.empty();
     h.threads = 128;
     h.uniform = pl.uniform_axes;
     if (pl.uniform_axes) {
