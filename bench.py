@@ -327,15 +327,19 @@ def run_ours(a, dist: Dist):
         h2d = XY.numel() * 4
         feed = lambda: ctx.set_positions(XY)  # noqa: E731
     E = st["n_endpoints"]
+    # page-locked host buffers for the endpoint results (direct DMA)
+    pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory().numpy()  # noqa: E731
+    ep_out = (pin((E, K), torch.float32), pin((E, K), torch.float32), pin((E, K), torch.uint8),
+              pin((E, K), torch.uint8))
     for _ in range(2):
-        feed(); ctx.update_timing(); ctx.get_endpoint_slack(); ctx.report_slack()
+        feed(); ctx.update_timing(); ctx.get_endpoint_slack(out=ep_out); ctx.report_slack()
     torch.cuda.synchronize()
     dist.barrier()
     t0 = time.perf_counter()
     for _ in range(a.steps):
         feed()
         ctx.update_timing()
-        ctx.get_endpoint_slack()
+        ctx.get_endpoint_slack(out=ep_out)
         ctx.report_slack()
     torch.cuda.synchronize()
     t_e2e = dist.max(time.perf_counter() - t0) / a.steps
@@ -343,7 +347,7 @@ def run_ours(a, dist: Dist):
                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(E * K * 10 + 64 * K),
                   "ms_per_step": t_e2e * 1e3,
                   "what": "sta_set_rc from pinned host R/C + sta_update_timing + endpoint slacks and "
-                          "violation flags to host + sta_report_slack"}
+                          "violation flags to pinned host buffers + sta_report_slack"}
 
     # ---- top-k path report (1000 worst endpoints' critical paths, host arrays)
     ctx.report_paths(1000)

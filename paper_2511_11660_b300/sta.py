@@ -389,7 +389,16 @@ class Context:
         self._chk(self.lib.sta_get_net_wirelength(self.h, _ptr(out), DEVICE if device else HOST, _stream(stream)))
         return out
 
-    def get_endpoint_slack(self, device: bool = False, stream=None):
+    def get_endpoint_slack(self, device: bool = False, stream=None, out=None):
+        """Endpoint setup and hold slacks [E, corners] and violation flags.
+        ``out``: four preallocated arrays (setup, hold, setup flags, hold
+        flags) to fill instead -- page-locked host memory makes the copies
+        direct DMA."""
+        if out is not None:
+            s, h, vs, vh = out
+            self._chk(self.lib.sta_get_endpoint_slack(self.h, _ptr(s), _ptr(h), _ptr(vs), _ptr(vh), _mem_of(s),
+                                                      _stream(stream)))
+            return s, h, vs, vh
         if device:
             import torch
             dev = torch.device("cuda", self.device)
