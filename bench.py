@@ -318,10 +318,18 @@ def run_ours(a, dist: Dist):
 
     # ---- end to end through the C ABI with host buffers
     if d.get("rc_R") is not None:
-        Rh = torch.from_numpy(np.asarray(d["rc_R"], np.float32)).pin_memory()
-        Ch = torch.from_numpy(np.asarray(d["rc_C"], np.float32)).pin_memory()
-        h2d = Rh.numel() * 4 + Ch.numel() * 4
-        feed = lambda: ctx.set_rc(Rh, Ch)  # noqa: E731
+        # two page-locked R/C sets staged in turn on a copy stream: the copy of
+        # step i + 1's parasitics runs while step i's update computes
+        rc_sets = [(torch.from_numpy(np.asarray(d["rc_R"], np.float32)).pin_memory(),
+                    torch.from_numpy(np.asarray(d["rc_C"], np.float32)).pin_memory()) for _ in range(2)]
+        h2d = rc_sets[0][0].numel() * 4 + rc_sets[0][1].numel() * 4
+        copy_stream = torch.cuda.Stream()
+        feed_i = [0]
+
+        def feed():
+            Rh, Ch = rc_sets[feed_i[0] & 1]
+            ctx.set_rc_async(Rh, Ch, stream=copy_stream)
+            feed_i[0] += 1
     else:
         XY = torch.from_numpy(np.asarray(d["cell_xy"], np.float32)).pin_memory()
         h2d = XY.numel() * 4
@@ -331,14 +339,18 @@ def run_ours(a, dist: Dist):
     pin = lambda shape, dt: torch.empty(shape, dtype=dt).pin_memory().numpy()  # noqa: E731
     ep_out = (pin((E, K), torch.float32), pin((E, K), torch.float32), pin((E, K), torch.uint8),
               pin((E, K), torch.uint8))
+    # each step: the update, the host-to-device copy of the next step's
+    # inputs (overlapping the update where the API allows it), the
+    # endpoint results back to the host
+    feed()
     for _ in range(2):
-        feed(); ctx.update_timing(); ctx.get_endpoint_slack(out=ep_out); ctx.report_slack()
+        ctx.update_timing(); feed(); ctx.get_endpoint_slack(out=ep_out); ctx.report_slack()
     torch.cuda.synchronize()
     dist.barrier()
     t0 = time.perf_counter()
     for _ in range(a.steps):
-        feed()
         ctx.update_timing()
+        feed()
         ctx.get_endpoint_slack(out=ep_out)
         ctx.report_slack()
     torch.cuda.synchronize()
@@ -346,8 +358,9 @@ def run_ours(a, dist: Dist):
     out["e2e"] = {"value": arcs * dist.world / t_e2e, "unit": UNIT,
                   "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(E * K * 10 + 64 * K),
                   "ms_per_step": t_e2e * 1e3,
-                  "what": "sta_set_rc from pinned host R/C + sta_update_timing + endpoint slacks and "
-                          "violation flags to pinned host buffers + sta_report_slack"}
+                  "what": "per step: sta_update_timing, sta_set_rc_async of the next step's R/C from "
+                          "pinned host memory on a copy stream (overlapping the update), endpoint slacks and "
+                          "violation flags to pinned host buffers, sta_report_slack"}
 
     # ---- top-k path report (1000 worst endpoints' critical paths, host arrays)
     ctx.report_paths(1000)

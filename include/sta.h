@@ -275,6 +275,18 @@ sta_status sta_create_batch(const sta_design_desc *const *descs, int32_t n_desig
  * next sta_update_timing. */
 sta_status sta_set_rc(sta_ctx *ctx, const float *R, const float *C, sta_mem mem);
 
+/* Stage new RC values for the next sta_update_timing without waiting: R and
+ * C (host, page-locked for the copies to overlap, or device; the caller's
+ * node order, n_rc_nodes floats each) are copied on `stream` into one of two
+ * staging buffers, and the next sta_update_timing, on its own stream, waits
+ * for that copy and reorders the values into place before its pass.  So the
+ * copy of the next step's parasitics can run while the current update
+ * computes.  The source buffers must stay unchanged until the copy has run
+ * (synchronise `stream`, or wait for the next update).  A later call before
+ * the next update replaces the staged values.  Errors: STA_ESTATE if the
+ * context uses positions. */
+sta_status sta_set_rc_async(sta_ctx *ctx, const float *R, const float *C, sta_mem mem, void *stream);
+
 /* Replace cell positions (positions mode): cell_xy[n_cells*2] um, copied on
  * `stream`.  Errors: STA_ESTATE if the context uses RC trees. */
 sta_status sta_set_positions(sta_ctx *ctx, const float *cell_xy, sta_mem mem, void *stream);

@@ -35,6 +35,11 @@ struct sta_ctx {
     int32_t *d_item_of_net = nullptr;   // Steiner contexts: driving item of every caller net
     int64_t *d_wl_tmp = nullptr;        // staging of sta_get_net_wirelength to the host
     float *d_rc_tmp = nullptr;
+    // sta_set_rc_async: two staging buffers (R then C), copy-done and
+    // buffer-free events, the buffer the next update applies (-1: none)
+    float *d_stage[2] = {nullptr, nullptr};
+    cudaEvent_t stage_copied[2] = {nullptr, nullptr}, stage_free[2] = {nullptr, nullptr};
+    int stage_next = 0, stage_pending = -1;
     float4 *d_gather_tmp = nullptr;
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -574,6 +579,10 @@ void sta_destroy(sta_ctx *c)
     drop_graph(c);
     for (auto &e : c->ev)
         if (e) cudaEventDestroy(e);
+    for (int b = 0; b < 2; ++b) {
+        if (c->stage_copied[b]) cudaEventDestroy(c->stage_copied[b]);
+        if (c->stage_free[b]) cudaEventDestroy(c->stage_free[b]);
+    }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (void *p : c->allocs) cudaFree(p);
     delete c;
@@ -815,6 +824,15 @@ sta_status sta_update_timing(sta_ctx *c, void *stream)
     try {
         CK(cudaSetDevice(c->device));
         cudaStream_t st = as_stream(stream);
+        if (c->stage_pending >= 0) {   // RC values staged by sta_set_rc_async: wait for the copy, reorder
+            const int b = c->stage_pending;
+            const size_t NN = (size_t)c->plan.NN;
+            CK(cudaStreamWaitEvent(st, c->stage_copied[b], 0));
+            sta::launch_gather_f32(c->d_stage[b], c->d_rc_src, const_cast<float *>(c->dc.rc_R), (int)NN, st);
+            sta::launch_gather_f32(c->d_stage[b] + NN, c->d_rc_src, const_cast<float *>(c->dc.rc_C), (int)NN, st);
+            CK(cudaEventRecord(c->stage_free[b], st));
+            c->stage_pending = -1;
+        }
         if (c->profiling) {
             // eager launches with events at the phase boundaries
             record_pass(c, st, c->ev);
@@ -1039,6 +1057,38 @@ sta_status sta_set_rc(sta_ctx *c, const float *R, const float *Cc, sta_mem mem)
         CK(cudaMemcpy(c->d_rc_tmp, Cc, NN * sizeof(float), kind));
         sta::launch_gather_f32(c->d_rc_tmp, c->d_rc_src, const_cast<float *>(c->dc.rc_C), (int)NN, 0);
         CK(cudaDeviceSynchronize());
+        c->stage_pending = -1;   // these values replace any staged ones
+    } catch (const CudaFail &f) {
+        return from_cuda(c, f);
+    }
+    return STA_OK;
+}
+
+sta_status sta_set_rc_async(sta_ctx *c, const float *R, const float *Cc, sta_mem mem, void *stream)
+{
+    if (!c || !R || !Cc) return STA_EINVAL;
+    if (c->plan.placed) return fail(c, STA_ESTATE, "context uses positions, not RC trees");
+    const size_t NN = (size_t)c->plan.NN;
+    try {
+        CK(cudaSetDevice(c->device));
+        cudaStream_t st = as_stream(stream);
+        if (!c->d_stage[0]) {
+            for (int b = 0; b < 2; ++b) {
+                c->d_stage[b] = dev_alloc<float>(c, 2 * std::max<size_t>(1, NN));
+                CK(cudaEventCreateWithFlags(&c->stage_copied[b], cudaEventDisableTiming));
+                CK(cudaEventCreateWithFlags(&c->stage_free[b], cudaEventDisableTiming));
+                CK(cudaEventRecord(c->stage_free[b], st));
+            }
+        }
+        // a buffer staged but not applied yet is replaced: reuse it
+        const int b = c->stage_pending >= 0 ? c->stage_pending : c->stage_next;
+        CK(cudaStreamWaitEvent(st, c->stage_free[b], 0));   // its last reorder has read it
+        const cudaMemcpyKind kind = mem == STA_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+        CK(cudaMemcpyAsync(c->d_stage[b], R, NN * sizeof(float), kind, st));
+        CK(cudaMemcpyAsync(c->d_stage[b] + NN, Cc, NN * sizeof(float), kind, st));
+        CK(cudaEventRecord(c->stage_copied[b], st));
+        c->stage_pending = b;
+        c->stage_next = b ^ 1;
     } catch (const CudaFail &f) {
         return from_cuda(c, f);
     }

@@ -106,6 +106,7 @@ SIGNATURES = {
     "sta_get_pin_state": (C.c_int, [_V, C.c_int32, _P, C.c_int, _V]),
     "sta_get_endpoint_slack": (C.c_int, [_V, _P, _P, _P, _P, C.c_int, _V]),
     "sta_get_net_wirelength": (C.c_int, [_V, _P, C.c_int, _V]),
+    "sta_set_rc_async": (C.c_int, [_V, _P, _P, C.c_int, _V]),
     "sta_report_paths": (C.c_int, [_V, C.c_int32, C.c_int32, C.c_int32, C.c_float, _P, _P, _P, _P, _P, _P, _P, _P,
                                    C.c_int32, C.c_int, _V]),
     "sta_backward": (C.c_int, [_V, C.c_double, C.c_double, _P, _P, _P, C.c_int, _V]),
@@ -314,6 +315,12 @@ class Context:
 
     def set_rc(self, R, Cc):
         self._chk(self.lib.sta_set_rc(self.h, _ptr(R), _ptr(Cc), _mem_of(R)))
+
+    def set_rc_async(self, R, Cc, stream=None):
+        """Stage R/C for the next update_timing; the copy runs on ``stream``
+        (page-locked host tensors or device tensors) and may overlap an
+        update in flight.  The caller keeps R and Cc unchanged until then."""
+        self._chk(self.lib.sta_set_rc_async(self.h, _ptr(R), _ptr(Cc), _mem_of(R), _stream(stream)))
 
     def set_positions(self, cell_xy, stream=None):
         mem = _mem_of(cell_xy)

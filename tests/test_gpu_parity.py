@@ -267,3 +267,48 @@ def test_arnoldi_net_model_parity(case):
         for o in outs[1:]:
             np.testing.assert_array_equal(o[k], outs[0][k], err_msg=k)
         assert_close(k, outs[0][k], ref[k])
+
+
+def test_set_rc_async_matches_set_rc():
+    """sta_set_rc_async: values staged on a copy stream are applied by the
+    next update (equal to sta_set_rc's); a later staging before the update
+    replaces an earlier one; a synchronous sta_set_rc replaces staged
+    values; updates without new staging keep the applied values."""
+    import torch
+    d = synth.make_design(2000, 12, seed=21, period_ns=1.2)
+    rng = np.random.default_rng(3)
+    sets = []
+    for _ in range(3):
+        R = (d["rc_R"] * rng.uniform(0.5, 1.5, len(d["rc_R"]))).astype(np.float32)
+        Cc = (d["rc_C"] * rng.uniform(0.5, 1.5, len(d["rc_C"]))).astype(np.float32)
+        sets.append((torch.from_numpy(R).pin_memory(), torch.from_numpy(Cc).pin_memory()))
+    ref = sta.Context(d)
+    ctx = sta.Context(d)
+    cs = torch.cuda.Stream()
+
+    def want(i):
+        ref.set_rc(sets[i][0].numpy(), sets[i][1].numpy())
+        ref.update_timing()
+        return ref.get_pin_state(sta.SLACK)
+
+    ctx.set_rc_async(*sets[0], stream=cs)
+    ctx.update_timing()
+    np.testing.assert_array_equal(ctx.get_pin_state(sta.SLACK), want(0))
+    ctx.update_timing()   # nothing staged: the same values
+    np.testing.assert_array_equal(ctx.get_pin_state(sta.SLACK), want(0))
+    ctx.set_rc_async(*sets[1], stream=cs)
+    ctx.set_rc_async(*sets[2], stream=cs)   # replaces the staged set 1
+    ctx.update_timing()
+    np.testing.assert_array_equal(ctx.get_pin_state(sta.SLACK), want(2))
+    ctx.set_rc_async(*sets[1], stream=cs)
+    cs.synchronize()
+    ctx.set_rc(sets[0][0].numpy(), sets[0][1].numpy())   # the synchronous call wins
+    ctx.update_timing()
+    np.testing.assert_array_equal(ctx.get_pin_state(sta.SLACK), want(0))
+    # alternate two staged sets while updates run, as a placement loop would
+    for i in range(6):
+        ctx.set_rc_async(*sets[i % 2], stream=cs)
+        ctx.update_timing()
+        np.testing.assert_array_equal(ctx.get_pin_state(sta.SLACK), want(i % 2))
+    ctx.close()
+    ref.close()
