@@ -440,6 +440,9 @@ class Context:
         return float(J[0]), terms, g
 
     def views(self) -> dict:
+        """Device pointers in the library's pin order: at and rat point to
+        [n_pins][states][4][2] float32 double-float pairs (value hi + lo),
+        slew and slack to [n_pins][states][4] float32."""
         v = sta_views()
         self._chk(self.lib.sta_get_arrays(self.h, C.byref(v)))
         return {k: getattr(v, k) for k, _ in v._fields_}
