@@ -3,8 +3,9 @@
 on the device, and a violation sets the bounds bit of the device error word,
 which the next synchronising call reports.  This runs representative cases
 through that build -- every schedule, several corners, a batch, large RC
-trees swept in global scratch, star RC, the adjoint and the path report -- in
-a child process
+trees swept in global scratch, star RC, Steiner trees (all three Steiner
+kernels) with the Arnoldi model, exceptions with -through sets, the adjoint
+and the path report -- in a child process
 (the binding holds one library per process), checks them against the FP64
 oracle and requires that no check fired."""
 import os
@@ -32,7 +33,26 @@ cases = {
     "corners": synth.make_design(3000, 20, seed=4, n_corners=4, lut_scale=ls, rc_scale=rs, period_ns=1.7),
     "big_rc": synth.make_design(400, 6, seed=9, rc_nodes=(20, 60)),
     "star_smooth": synth.make_design(3000, 15, seed=6, placed=True, gamma_ns=0.01, period_ns=1.5),
+    "steiner_arnoldi": dict(synth.make_design(3000, 15, seed=7, placed=True, period_ns=1.5), wire_model=1,
+                            net_model=1, arnoldi_order=3),
 }
+# exceptions with -through sets on 4 corners
+exc = synth.make_design(3000, 20, seed=8, n_corners=4, lut_scale=ls, rc_scale=rs, period_ns=1.7)
+exc.update(synth.exception_groups(exc, np.random.default_rng(8), 3, max_thru=2))
+cases["exceptions_through"] = exc
+# a net of 80 pins (minimum spanning tree only) and nets of 20-63 pins (warp kernel)
+bld = synth.Builder(synth.make_library(0))
+rng = np.random.default_rng(2)
+pi = bld.pi(xy=(10.0, 10.0))
+for _ in range(80):
+    bld.po(pi, xy=tuple(float(v) for v in rng.uniform(0, 500, 2)))
+for k in (20, 40, 63):
+    x = bld.cell("BUF", [pi], xy=tuple(float(v) for v in rng.uniform(0, 500, 2)))
+    for _ in range(k):
+        bld.po(x, xy=tuple(float(v) for v in rng.uniform(0, 500, 2)))
+fan = bld.design(placed=True, period_ns=2.0)
+fan["wire_model"] = 1
+cases["steiner_fanout"] = fan
 for name, d in cases.items():
     ref = oracle.sta(d)
     for sch in (sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP):
