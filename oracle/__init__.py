@@ -48,6 +48,7 @@ def _load():
         P = C.c_void_p
         _lib.orc_lut_eval.argtypes = [P, P, P, C.c_double, C.c_double, P]
         _lib.orc_rc_tree.argtypes = [C.c_int32, P, P, P, P, P, P, P]
+        _lib.orc_rc_tree_adjoint.argtypes = [C.c_int32, P, P, P, P, P, C.c_double, P, P]
         _lib.orc_arnoldi_t50.argtypes = [C.c_int32, P, P, P, C.c_int32, P]
         _lib.orc_net_delays.argtypes = [P, C.c_int32, P, P, P]
         _lib.orc_topo_order.argtypes = [P, P]
@@ -58,7 +59,7 @@ def _load():
         _lib.orc_nm.argtypes = [C.c_float]
         _lib.orc_net_wirelengths.argtypes = [P, P]
         _lib.orc_nm.restype = C.c_int64
-        for f in ("orc_lut_eval", "orc_rc_tree", "orc_arnoldi_t50", "orc_net_delays", "orc_topo_order", "orc_sta",
+        for f in ("orc_lut_eval", "orc_rc_tree", "orc_rc_tree_adjoint", "orc_arnoldi_t50", "orc_net_delays", "orc_topo_order", "orc_sta",
                   "orc_objective_grad", "orc_objective", "orc_steiner_tree", "orc_net_wirelengths"):
             getattr(_lib, f).restype = C.c_int
     return _lib
@@ -166,6 +167,19 @@ def rc_tree(parent, R, C_):
     outs = [np.zeros(n, np.float64) for _ in range(4)]
     _check(lib.orc_rc_tree(n, _ptr(par), _ptr(r), _ptr(c), *[_ptr(o) for o in outs]), "rc_tree")
     return tuple(outs)
+
+
+def rc_tree_adjoint(parent, R, C_, Dbar, Vbar, Lbar: float):
+    """Reverse mode of O3 on one tree: dJ/dR and dJ/dC from dJ/dD, dJ/dvar
+    (per node) and dJ/dload (the root's downstream capacitance)."""
+    lib = _load()
+    par = np.ascontiguousarray(parent, np.int32)
+    arrs = [np.ascontiguousarray(a, np.float64) for a in (R, C_, Dbar, Vbar)]
+    n = len(par)
+    Rb, Cb = np.zeros(n, np.float64), np.zeros(n, np.float64)
+    _check(lib.orc_rc_tree_adjoint(n, _ptr(par), *[_ptr(a) for a in arrs], float(Lbar), _ptr(Rb), _ptr(Cb)),
+           "rc_tree_adjoint")
+    return Rb, Cb
 
 
 def arnoldi_t50(parent, R, C_, q: int):
@@ -303,7 +317,8 @@ def sta(d: dict, use_rc: bool | None = None) -> dict:
 
 
 def objective_grad(d: dict, w_tns: float = 1.0, w_wns: float = 1.0):
-    """O6: smoothed J, per-corner (TNS_g, WNS_g) and dJ/d(cell x, y) in FP64."""
+    """O6: smoothed J, per-corner (TNS_g, WNS_g) and dJ/d(cell x, y) in FP64
+    (star or Steiner parasitics from positions; Steiner with the Elmore model)."""
     lib = _load()
     s, keep = _marshal(d, use_rc=False)
     K = int(d.get("n_corners", 1))

@@ -187,6 +187,58 @@ int orc_rc_tree(int32_t n, const int32_t *parent, const double *R, const double 
     return OK;
 }
 
+/* Reverse mode of orc_rc_tree: given Dbar_i = dJ/dD_i, Vbar_i = dJ/dvar_i
+ * and Lbar = dJ/dCdown_0 (the load), the derivatives Rbar_i = dJ/dR_i
+ * (Rbar_0 = 0) and Cbar_i = dJ/dC_i.  Each forward recurrence is taken
+ * back in the opposite order:
+ *   var_i = 2 beta_i - D_i^2          -> betabar_i = 2 Vbar_i, Dbar_i -= 2 D_i Vbar_i
+ *   beta_i = beta_parent + R_i M_i    -> betabar summed up the subtree;
+ *                                        Rbar_i += betabar_i M_i, Mbar_i = betabar_i R_i
+ *   M_i = C_i D_i + sum children M    -> Mbar summed down from the root;
+ *                                        Cbar_i += Mbar_i D_i, Dbar_i += Mbar_i C_i
+ *   D_i = D_parent + R_i Cdown_i      -> Dbar summed up the subtree;
+ *                                        Rbar_i += Dbar_i Cdown_i, Cdbar_i = Dbar_i R_i
+ *   Cdown_i = C_i + sum children      -> Cdbar summed down from the root
+ *                                        (Cdbar_0 = Lbar); Cbar_i += Cdbar_i. */
+int orc_rc_tree_adjoint(int32_t n, const int32_t *parent, const double *R, const double *C, const double *Dbar,
+                        const double *Vbar, double Lbar, double *Rbar, double *Cbar)
+{
+    if (n <= 0) return ERR_INVAL;
+    double *cd = (double *)malloc(sizeof(double) * (size_t)n), *D = (double *)malloc(sizeof(double) * (size_t)n);
+    double *be = (double *)malloc(sizeof(double) * (size_t)n), *va = (double *)malloc(sizeof(double) * (size_t)n);
+    double *M = (double *)malloc(sizeof(double) * (size_t)n), *bb = (double *)malloc(sizeof(double) * (size_t)n);
+    double *mb = (double *)malloc(sizeof(double) * (size_t)n), *db = (double *)malloc(sizeof(double) * (size_t)n);
+    double *cb = (double *)malloc(sizeof(double) * (size_t)n);
+    int rc = (!cd || !D || !be || !va || !M || !bb || !mb || !db || !cb) ? ERR_NOMEM : OK;
+    if (!rc) rc = orc_rc_tree(n, parent, R, C, cd, D, be, va);
+    if (!rc) {
+        for (int32_t i = 0; i < n; ++i) M[i] = C[i] * D[i];
+        for (int32_t i = n - 1; i >= 1; --i) M[parent[i]] += M[i];
+        for (int32_t i = 0; i < n; ++i) {
+            Rbar[i] = 0.0;
+            Cbar[i] = 0.0;
+            bb[i] = 2.0 * Vbar[i];
+        }
+        for (int32_t i = n - 1; i >= 1; --i) {
+            Rbar[i] += bb[i] * M[i];
+            bb[parent[i]] += bb[i];
+        }
+        for (int32_t i = 0; i < n; ++i) mb[i] = (i ? bb[i] * R[i] : 0.0) + (i ? mb[parent[i]] : 0.0);
+        for (int32_t i = 0; i < n; ++i) {
+            Cbar[i] += mb[i] * D[i];
+            db[i] = Dbar[i] - 2.0 * D[i] * Vbar[i] + mb[i] * C[i];
+        }
+        for (int32_t i = n - 1; i >= 1; --i) {
+            Rbar[i] += db[i] * cd[i];
+            db[parent[i]] += db[i];
+        }
+        for (int32_t i = 0; i < n; ++i) cb[i] = (i ? db[i] * R[i] + cb[parent[i]] : Lbar);
+        for (int32_t i = 0; i < n; ++i) Cbar[i] += cb[i];
+    }
+    free(cd); free(D); free(be); free(va); free(M); free(bb); free(mb); free(db); free(cb);
+    return rc;
+}
+
 /* ------------------------------------------------------------------ O7 */
 
 /* Solve G x = y for an RC tree whose root (node 0) is held at 0 V: G is the
@@ -704,6 +756,54 @@ int orc_steiner_tree(int32_t n, const int64_t *X, const int64_t *Y, int32_t *n_o
     return rc;
 }
 
+/* O9 RC tree of net n at corner RC scale f: the Steiner tree of its pins'
+ * nm coordinates (pin 0 = the driver), each edge of x length Lx and y length
+ * Ly (um) with R = f (rx Lx + ry Ly) and wire C = f (cx Lx + cy Ly) split
+ * half at each end, plus the sink pin caps (fF) at their nodes.  Arrays of
+ * max(1, 2 m - 2) entries for m pins (pnode: m); nx, ny (node coordinates,
+ * nm) may be NULL. */
+static int steiner_rc(const orc_design *d, const pin_info *pi, int32_t n, double f, int32_t *nn_out,
+                      int32_t *par, double *R, double *C, int32_t *pnode, int64_t *nx, int64_t *ny)
+{
+    int32_t b = d->net_pin_ptr[n], m = d->net_pin_ptr[n + 1] - b, cap = m > 1 ? 2 * m - 2 : 1, nn = 0;
+    int64_t *X = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+    int64_t *Y = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+    int64_t *tx = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    int64_t *ty = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+    int rc = OK;
+    if (!X || !Y || !tx || !ty) rc = ERR_NOMEM;
+    else {
+        for (int32_t k = 0; k < m; ++k) {
+            double xs, ys;
+            pin_xy(d, pi, d->net_pin[b + k], &xs, &ys);
+            X[k] = orc_nm((float)xs);
+            Y[k] = orc_nm((float)ys);
+        }
+        int64_t wl;
+        rc = orc_steiner_tree(m, X, Y, &nn, par, tx, ty, pnode, &wl);
+    }
+    if (!rc) {
+        double rx = d->r_per_um, cx = d->c_per_um;
+        double ry = d->r_per_um_y > 0 ? d->r_per_um_y : rx, cy = d->c_per_um_y > 0 ? d->c_per_um_y : cx;
+        for (int32_t i = 0; i < nn; ++i) { R[i] = 0.0; C[i] = 0.0; }
+        for (int32_t i = 1; i < nn; ++i) {
+            double lx = 1e-3 * (double)llabs(tx[i] - tx[par[i]]), ly = 1e-3 * (double)llabs(ty[i] - ty[par[i]]);
+            double cw = f * (cx * lx + cy * ly);
+            R[i] = f * (rx * lx + ry * ly);
+            C[i] += 0.5 * cw;
+            C[par[i]] += 0.5 * cw;
+        }
+        for (int32_t k = 1; k < m; ++k) C[pnode[k]] += 1e3 * pin_cap_of(d, pi, d->net_pin[b + k]);
+        for (int32_t i = 0; i < nn; ++i) {
+            if (nx) nx[i] = tx[i];
+            if (ny) ny[i] = ty[i];
+        }
+        *nn_out = nn;
+    }
+    free(X); free(Y); free(tx); free(ty);
+    return rc;
+}
+
 /* Per-corner net quantities: load (pF) at each driver pin, Elmore delay (ns)
  * and variance (ns^2) at each sink pin.  With rc_ptr == NULL the tree is the
  * star of O3/A8: root at the driver, one segment per sink of Manhattan length
@@ -747,37 +847,9 @@ int orc_net_delays(const orc_design *d, int32_t corner, double *load_pf, double 
                 C[node] += 1e3 * pin_cap_of(d, &pi, d->net_pin[k]);   /* pF -> fF */
             }
         } else if (steiner) {
-            int32_t m = e - b;
-            int64_t *X = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
-            int64_t *Y = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
-            int64_t *tx = (int64_t *)malloc(sizeof(int64_t) * (size_t)nn);
-            int64_t *ty = (int64_t *)malloc(sizeof(int64_t) * (size_t)nn);
-            pnode = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
-            if (!X || !Y || !tx || !ty || !pnode) rc = ERR_NOMEM;
-            else {
-                for (int32_t k = 0; k < m; ++k) {
-                    double xs, ys;
-                    pin_xy(d, &pi, d->net_pin[b + k], &xs, &ys);
-                    X[k] = orc_nm((float)xs);
-                    Y[k] = orc_nm((float)ys);
-                }
-                int64_t wl;
-                rc = orc_steiner_tree(m, X, Y, &nn, par, tx, ty, pnode, &wl);
-            }
-            if (!rc) {
-                double rx = d->r_per_um, cx = d->c_per_um;
-                double ry = d->r_per_um_y > 0 ? d->r_per_um_y : rx, cy = d->c_per_um_y > 0 ? d->c_per_um_y : cx;
-                for (int32_t i = 0; i < nn; ++i) { R[i] = 0.0; C[i] = 0.0; }
-                for (int32_t i = 1; i < nn; ++i) {
-                    double lx = 1e-3 * (double)llabs(tx[i] - tx[par[i]]), ly = 1e-3 * (double)llabs(ty[i] - ty[par[i]]);
-                    double cw = f * (cx * lx + cy * ly);
-                    R[i] = f * (rx * lx + ry * ly);
-                    C[i] += 0.5 * cw;
-                    C[par[i]] += 0.5 * cw;
-                }
-                for (int32_t k = 1; k < m; ++k) C[pnode[k]] += 1e3 * pin_cap_of(d, &pi, d->net_pin[b + k]);
-            }
-            free(X); free(Y); free(tx); free(ty);
+            pnode = (int32_t *)malloc(sizeof(int32_t) * (size_t)(e - b));
+            if (!pnode) rc = ERR_NOMEM;
+            else rc = steiner_rc(d, &pi, n, f, &nn, par, R, C, pnode, NULL, NULL);
             if (rc) goto next;
         } else {
             double xd, yd;
@@ -1194,18 +1266,88 @@ static double sigmoid(double z)
     return e / (1.0 + e);
 }
 
+/* Steiner partials of one corner (RC scale f): from the sinks' dJ/dD and
+ * dJ/dvar and the drivers' dJ/dload, dJ/dR and dJ/dC of every tree node
+ * (orc_rc_tree_adjoint), then dJ/dLx = f (rx Rbar_i + cx (Cbar_i +
+ * Cbar_parent) / 2) and likewise for y, then the cells.  The gradient is
+ * that of the tree held fixed: every node coordinate is the coordinate of a
+ * pin (a Steiner point takes medians of pin coordinates), it moves with the
+ * lowest-index pin of the net at that coordinate (Lx = |X_i - X_parent| in
+ * nm / 1000, nm rounding taken as the identity), and sign 0 at X_i =
+ * X_parent. */
+static int steiner_grad(const orc_design *d, const pin_info *pi, double f, const double *aD, const double *aV,
+                        const double *aload, double *grad_xy)
+{
+    double rx = d->r_per_um, cx = d->c_per_um;
+    double ry = d->r_per_um_y > 0 ? d->r_per_um_y : rx, cy = d->c_per_um_y > 0 ? d->c_per_um_y : cx;
+    int rc = OK;
+    for (int32_t n = 0; n < d->n_nets && !rc; ++n) {
+        int32_t b = d->net_pin_ptr[n], m = d->net_pin_ptr[n + 1] - b, cap = m > 1 ? 2 * m - 2 : 1, nn = 0;
+        if (m < 2) continue;
+        int32_t *par = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap), *pnode = (int32_t *)malloc(sizeof(int32_t) * (size_t)m);
+        double *R = (double *)malloc(sizeof(double) * (size_t)cap), *C = (double *)malloc(sizeof(double) * (size_t)cap);
+        double *Db = (double *)calloc((size_t)cap, sizeof(double)), *Vb = (double *)calloc((size_t)cap, sizeof(double));
+        double *Rb = (double *)malloc(sizeof(double) * (size_t)cap), *Cb = (double *)malloc(sizeof(double) * (size_t)cap);
+        int64_t *nx = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap), *ny = (int64_t *)malloc(sizeof(int64_t) * (size_t)cap);
+        int64_t *X = (int64_t *)malloc(sizeof(int64_t) * (size_t)m), *Y = (int64_t *)malloc(sizeof(int64_t) * (size_t)m);
+        if (!par || !pnode || !R || !C || !Db || !Vb || !Rb || !Cb || !nx || !ny || !X || !Y) rc = ERR_NOMEM;
+        if (!rc) rc = steiner_rc(d, pi, n, f, &nn, par, R, C, pnode, nx, ny);
+        if (!rc) {
+            for (int32_t k = 1; k < m; ++k) {
+                int32_t s = d->net_pin[b + k];
+                Db[pnode[k]] += 1e-6 * aD[s];
+                Vb[pnode[k]] += 1e-12 * aV[s];
+            }
+            rc = orc_rc_tree_adjoint(nn, par, R, C, Db, Vb, 1e-3 * aload[d->net_pin[b]], Rb, Cb);
+        }
+        if (!rc) {
+            for (int32_t k = 0; k < m; ++k) {
+                double xs, ys;
+                pin_xy(d, pi, d->net_pin[b + k], &xs, &ys);
+                X[k] = orc_nm((float)xs);
+                Y[k] = orc_nm((float)ys);
+            }
+            for (int32_t i = 1; i < nn; ++i) {
+                int32_t p = par[i];
+                double gl[2] = {f * (rx * Rb[i] + 0.5 * cx * (Cb[i] + Cb[p])), f * (ry * Rb[i] + 0.5 * cy * (Cb[i] + Cb[p]))};
+                const int64_t *co[2] = {nx, ny}, *pc[2] = {X, Y};
+                for (int ax = 0; ax < 2; ++ax) {
+                    int64_t a = co[ax][i], q = co[ax][p];
+                    double sg = (double)((a > q) - (a < q));
+                    if (sg == 0.0) continue;
+                    int32_t ka = -1, kq = -1;   /* the pins that carry the two coordinates */
+                    for (int32_t k = m - 1; k >= 0; --k) {
+                        if (pc[ax][k] == a) ka = k;
+                        if (pc[ax][k] == q) kq = k;
+                    }
+                    if (ka < 0 || kq < 0) { rc = ERR_INVAL; break; }   /* not reached */
+                    int32_t ca = pi->cell[d->net_pin[b + ka]], cq = pi->cell[d->net_pin[b + kq]];
+                    if (ca >= 0) grad_xy[2 * ca + ax] += gl[ax] * sg;
+                    if (cq >= 0) grad_xy[2 * cq + ax] -= gl[ax] * sg;
+                }
+            }
+        }
+        free(par); free(pnode); free(R); free(C); free(Db); free(Vb); free(Rb); free(Cb);
+        free(nx); free(ny); free(X); free(Y);
+    }
+    return rc;
+}
+
 /* Smoothed objective J = w_tns * TNS_g + w_wns * WNS_g summed over corners,
  * with per endpoint setup slack s_e = smin_g over rise/fall of (RAT - AT_late)
  *   TNS_g = - sum_e g * softplus(-s_e / g)
  *   WNS_g = - g * log sum_e exp(-s_e / g)
  * and its gradient with respect to every cell (x, y) (ports are fixed).  The
  * forward merges are the log-sum-exp ones of merge() with the same gamma.
- * Requires the position (star tree) parasitics and gamma_ns > 0.
+ * Requires parasitics from positions (star, or Steiner with the Elmore
+ * model) and gamma_ns > 0.
  * terms[k*2 + 0] = TNS_g, terms[k*2 + 1] = WNS_g of corner k (may be NULL). */
 int orc_objective_grad(const orc_design *d, double w_tns, double w_wns, double *J_out,
                        double *terms, double *grad_xy)
 {
-    if (d->rc_ptr || !d->cell_xy || d->gamma_ns <= 0.0 || d->wire_model != 0) return ERR_INVAL;
+    if (d->rc_ptr || !d->cell_xy || d->gamma_ns <= 0.0 || (d->wire_model != 0 && d->wire_model != 1) ||
+        (d->wire_model == 1 && d->net_model != 0))
+        return ERR_INVAL;
     pin_info pi;
     int rc = build_info(d, &pi);
     if (rc) return rc;
@@ -1321,6 +1463,11 @@ int orc_objective_grad(const orc_design *d, double w_tns, double w_wns, double *
                     }
                 }
             }
+        }
+        if (d->wire_model == 1) {
+            rc = steiner_grad(d, &pi, f, aD, aV, aload, grad_xy);
+            if (rc) goto done;
+            continue;
         }
         /* star-tree partials: D = R (C/2 + Cp), var = D^2, load = sum (cL + Cp) */
         for (int32_t n = 0; n < d->n_nets; ++n) {

@@ -106,6 +106,15 @@ MUTANTS = [
     ("steiner_ry_uses_rx", "R[i] = f * (rx * lx + ry * ly);", "R[i] = f * (rx * lx + rx * ly);", 0),
     ("steiner_no_parent_half_cap", "C[par[i]] += 0.5 * cw;", "C[par[i]] += 0.0 * cw;", 0),
     ("steiner_no_scale", "double cw = f * (cx * lx + cy * ly);", "double cw = (cx * lx + cy * ly);", 0),
+    # O6 on Steiner trees: the RC-tree adjoint and the tree-held-fixed chain to positions
+    ("rcadj_no_var_D", "db[i] = Dbar[i] - 2.0 * D[i] * Vbar[i] + mb[i] * C[i];", "db[i] = Dbar[i] + mb[i] * C[i];", 0),
+    ("rcadj_beta_factor", "bb[i] = 2.0 * Vbar[i];", "bb[i] = Vbar[i];", 0),
+    ("rcadj_no_load", "cb[i] = (i ? db[i] * R[i] + cb[parent[i]] : Lbar);", "cb[i] = (i ? db[i] * R[i] + cb[parent[i]] : 0.0);", 0),
+    ("rcadj_moment_down_order", "mb[i] = (i ? bb[i] * R[i] : 0.0) + (i ? mb[parent[i]] : 0.0);", "mb[i] = (i ? bb[i] * R[i] : 0.0);", 0),
+    ("stgrad_no_parent_cap", "0.5 * cx * (Cb[i] + Cb[p])", "0.5 * cx * Cb[i]", 0),
+    ("stgrad_y_uses_rx", "f * (ry * Rb[i] + 0.5 * cy", "f * (rx * Rb[i] + 0.5 * cy", 0),
+    ("stgrad_parent_sign", "if (cq >= 0) grad_xy[2 * cq + ax] -= gl[ax] * sg;", "if (cq >= 0) grad_xy[2 * cq + ax] += gl[ax] * sg;", 0),
+    ("stgrad_sink_var_scale", "Vb[pnode[k]] += 1e-12 * aV[s];", "Vb[pnode[k]] += 1e-6 * aV[s];", 0),
 ]
 
 

@@ -1178,3 +1178,124 @@ def test_exceptions_through_required_times_brute_force(seed):
                 early = max([reqs(e, t, ins)[1] - dl for dl, r, e, ins in suf[p] if r == rf], default=-np.inf)
                 assert res["rat"][p, t, 2 + rf] == pytest.approx(late, abs=1e-12), (p, t, rf)
                 assert res["rat"][p, t, rf] == pytest.approx(early, abs=1e-12), (p, t, rf)
+
+
+# ------------------------------------------- O6 on Steiner trees (O9 + O3)
+
+def test_rc_tree_adjoint_matches_central_differences():
+    """dJ/dR and dJ/dC of orc_rc_tree_adjoint against central differences of
+    J = sum_i (Dbar_i D_i + Vbar_i var_i) + Lbar Cdown_0 through the forward
+    orc_rc_tree, on random trees of 1-24 nodes (a chain and a star among
+    them).  J is quadratic in any single R_i or C_i, so a central difference
+    is exact up to rounding at any step."""
+    rng = np.random.default_rng(5)
+    shapes = [None] * 20 + ["chain", "star"]
+    for k, shape in enumerate(shapes):
+        n = int(rng.integers(1, 25)) if shape is None else 9
+        par, R, C_ = _random_tree(rng, n)
+        if shape == "chain":
+            par = [-1] + list(range(n - 1))
+        elif shape == "star":
+            par = [-1] + [0] * (n - 1)
+        Db, Vb = rng.normal(size=n), rng.normal(size=n)
+        Lb = float(rng.normal())
+
+        def J(R_, C2):
+            cd, D, _, var = oracle.rc_tree(par, R_, C2)
+            return float(Db @ D + Vb @ var + Lb * cd[0])
+        Rb, Cb = oracle.rc_tree_adjoint(par, R, C_, Db, Vb, Lb)
+        assert Rb[0] == 0.0
+        for i in range(n):
+            for arr, bar, skip0 in ((R, Rb, True), (C_, Cb, False)):
+                if skip0 and i == 0:
+                    continue
+                h = 0.1 * arr[i]
+                up, dn = arr.copy(), arr.copy()
+                up[i] += h
+                dn[i] -= h
+                fd = (J(up, C_) - J(dn, C_)) / (2 * h) if arr is R else (J(R, up) - J(R, dn)) / (2 * h)
+                assert bar[i] == pytest.approx(fd, rel=1e-7, abs=1e-9), (k, i)
+
+
+def _pin_positions(d):
+    """um position of every pin (cell pins at their cell, ports at port_xy)."""
+    P = int(d["n_pins"])
+    cell_of = np.full(P, -1, np.int64)
+    cp = np.asarray(d["cell_pin_ptr"])
+    for c in range(int(d["n_cells"])):
+        cell_of[np.asarray(d["cell_pin"])[cp[c]:cp[c + 1]]] = c
+    xy = np.asarray(d["cell_xy"], np.float32).reshape(-1, 2)
+    pxy = np.asarray(d["port_xy"], np.float32).reshape(-1, 2)
+    out = np.where(cell_of[:, None] >= 0, xy[np.maximum(cell_of, 0)], pxy[:P])
+    return out.astype(np.float32), cell_of
+
+
+def _net_trees(d, nets):
+    pos, _ = _pin_positions(d)
+    ptr, pins = np.asarray(d["net_pin_ptr"]), np.asarray(d["net_pin"])
+    out = []
+    for n in nets:
+        q = pins[ptr[n]:ptr[n + 1]]
+        X = [oracle.nm(float(v)) for v in pos[q, 0]]
+        Y = [oracle.nm(float(v)) for v in pos[q, 1]]
+        out.append(oracle.steiner_tree(X, Y))
+    return out
+
+
+@pytest.mark.parametrize("ry", [None, 0.3])
+def test_steiner_adjoint_matches_central_differences(ry):
+    """dJ/d(x, y) of the oracle's adjoint on Steiner-tree RC against central
+    differences of its own smoothed objective.  Positions sit at (integer +
+    1/4) nm so that a step of h = 20 nm moves every nm coordinate by exactly
+    20; a cell is checked only where the trees of all its nets keep their
+    topology at both steps (parents and pin nodes equal, every node
+    coordinate moving linearly), which is where the tree-held-fixed gradient
+    is the derivative.  With ry, unit R and C along y differ from x."""
+    d = synth.make_design(400, 12, seed=23, placed=True, placement="local", gamma_ns=0.01, period_ns=0.6)
+    d["wire_model"] = 1
+    d["r_per_um"] = 0.5
+    if ry is not None:
+        d["r_per_um_y"], d["c_per_um_y"] = ry, 0.35
+    for key in ("cell_xy", "port_xy"):
+        v = np.asarray(d[key], np.float64)
+        d[key] = ((np.round(v * 1000.0) + 0.25) / 1000.0).astype(np.float32)
+    d["gamma_ns"], d["period_ns"] = 0.0, 0.0
+    req = -oracle.sta(d)["ep_setup"][:, 0]
+    d["period_ns"], d["gamma_ns"] = float(np.quantile(req, 0.7)), 0.01
+    J, _, g = oracle.objective_grad(d)
+    _, cell_of = _pin_positions(d)
+    ptr, pins = np.asarray(d["net_pin_ptr"]), np.asarray(d["net_pin"])
+    net_of_pin = np.repeat(np.arange(int(d["n_nets"])), np.diff(ptr))
+    pin_net = np.full(int(d["n_pins"]), -1)
+    pin_net[pins] = net_of_pin
+    rng = np.random.default_rng(1)
+    cells = rng.choice(d["n_cells"], 60, replace=False)
+    h = 0.020
+    scale = np.abs(g).max()
+    checked = bad = 0
+    for c in cells:
+        nets = sorted(set(pin_net[np.nonzero(cell_of == c)[0]]) - {-1})
+        base = _net_trees(d, nets)
+        for ax in (0, 1):
+            dd = {}
+            for sgn in (1, -1):
+                dd[sgn] = dict(d)
+                xy = np.asarray(d["cell_xy"], np.float64).copy()
+                xy[2 * c + ax] += sgn * h
+                dd[sgn]["cell_xy"] = xy.astype(np.float32)
+            tp, tm = _net_trees(dd[1], nets), _net_trees(dd[-1], nets)
+            same = all(len(a["parent"]) == len(b["parent"]) == len(o["parent"]) and
+                       np.array_equal(a["parent"], o["parent"]) and np.array_equal(b["parent"], o["parent"]) and
+                       np.array_equal(a["pin_node"], o["pin_node"]) and np.array_equal(b["pin_node"], o["pin_node"]) and
+                       np.array_equal(a["nx"] + b["nx"], 2 * o["nx"]) and np.array_equal(a["ny"] + b["ny"], 2 * o["ny"])
+                       for a, b, o in zip(tp, tm, base))
+            if not same:
+                continue
+            checked += 1
+            fd = (oracle.objective(dd[1]) - oracle.objective(dd[-1])) / (2 * h)
+            if abs(fd - g[c, ax]) > 1e-5 * abs(g[c, ax]) + 1e-6 * scale:
+                bad += 1
+    assert checked >= 60, checked
+    # a cell may straddle a table breakpoint inside +-h: allow one
+    assert bad <= 1, (bad, checked)
+    assert scale > 0
