@@ -460,7 +460,8 @@ def run_grad(a, dev: int) -> dict:
     res = {}
     for name, d in (("diff_200k", synth.workload("diff", seed=a.seed)),
                     ("placed_1M", synth.make_design(1_000_000, 150, seed=a.seed, rc_nodes=(2, 10), placed=True,
-                                                    gamma_ns=0.01))):
+                                                    gamma_ns=0.01)),
+                    ("steiner_1M", dict(synth.workload("steiner", seed=a.seed), gamma_ns=0.01))):
         ctx = sta.Context(d, device=dev)
         ctx.set_schedule(sta.SCHED_DATAFLOW, 0)
         ctx.set_clock(0.0)
@@ -478,7 +479,9 @@ def run_grad(a, dev: int) -> dict:
             it()
         ms = _events_ms(it, 10)
         res[name] = {"ms_per_iter": ms, "cells": d["n_cells"], "pins": d["n_pins"],
-                     "what": "set_positions + update_timing (dataflow) + sta_backward, all on the device"}
+                     "what": "set_positions + update_timing (dataflow) + sta_backward, all on the device" +
+                             ("; Steiner trees rebuilt every iteration, gradient through the trees held fixed"
+                              if d.get("wire_model") == 1 else "")}
         ctx.close()
     return res
 

@@ -386,10 +386,16 @@ sta_status sta_get_endpoint_slack(sta_ctx *ctx, float *setup, float *hold, uint8
  *   s_e   = smooth min over rise/fall of (RAT_e - AT_late,e),
  *   TNS_g = -sum_e g * softplus(-s_e / g),  WNS_g = -g * log sum_e exp(-s_e / g)
  * and its gradient with respect to every cell position by a hand-written
- * adjoint of the forward pass (LSE merges, NLDM interpolation, star Elmore).
+ * adjoint of the forward pass (LSE merges, NLDM interpolation, Elmore delay
+ * and variance of the star or of the Steiner tree).  On Steiner trees the
+ * gradient is that of the update's trees held fixed: every tree node sits at
+ * pin coordinates (a Steiner point takes medians) and moves with the lowest
+ * pin of the net (driver first, then the sinks in net order) at that x or
+ * y; the nm rounding of positions counts as the identity.
  * J_out: 1 double (+ per-corner TNS_g, WNS_g pairs if terms != NULL);
  * grad_xy: n_cells*2 doubles.  All three in `mem`; host outputs synchronise.
- * Errors: STA_ESTATE (no prior update, or not differentiable). */
+ * Errors: STA_ESTATE (no prior update, not differentiable, or Steiner trees
+ * with STA_NET_ARNOLDI). */
 sta_status sta_backward(sta_ctx *ctx, double w_tns, double w_wns, double *J_out, double *terms,
                         double *grad_xy, sta_mem mem, void *stream);
 

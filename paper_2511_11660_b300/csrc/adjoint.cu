@@ -432,6 +432,128 @@ __global__ void k_adj_star(const DevCtx c)
     }
 }
 
+// Steiner trees, after the sweep: the tree of the update held fixed.  Per
+// corner, the reverse mode of the tree's Elmore recurrences (those of
+// k_net_tree, taken back in the opposite order)
+//   var_i = 2 beta_i - D_i^2       betabar = 2 varbar, summed up the subtree
+//   beta_i = beta_p + R_i M_i      Rbar_i += betabar_i M_i; Mbar = betabar R,
+//                                  summed down from the root
+//   M_i = C_i D_i + sum children   Cbar_i += Mbar_i D_i, Dbar_i += Mbar_i C_i
+//   D_i = D_p + R_i Cdown_i        Dbar summed up the subtree; Rbar_i +=
+//                                  Dbar_i Cdown_i; Cdownbar_i = Dbar_i R_i,
+//                                  summed down from the root (root: loadbar)
+//   Cdown_i = C_i + sum children   Cbar_i += Cdownbar_i
+// from the sinks' adjoints (Dbar = 1e-6 (dJ/dAT rise + fall), varbar =
+// 1e-12 sum over edges of dJ/dslew / (2 slew)) and the driver's load
+// adjoint (1e-3 dJ/dload); then dJ/dLx_i = f (rx Rbar_i + cx (Cbar_i +
+// Cbar_p) / 2), likewise for y, summed over corners.  Every node coordinate
+// is a pin's (Steiner points take medians); the tree writer recorded the
+// lowest net pin at it and the sign of node - parent, so Lx_i moves by +-1
+// per um of the two carrying pins' cells (nm rounding taken as the
+// identity, sign 0 at equal coordinates).  One thread per net; node arrays
+// in a shared-memory column (trees of at most kAdjColNodes nodes) or in
+// global scratch.
+constexpr int kAdjSteinerThreads = 64;
+enum { kA_PC, kA_CD, kA_D, kA_M, kA_DB, kA_VB, kA_RB, kA_BB, kA_GX, kA_GY, kAdjArrays };
+
+struct AdjNodes {
+    float *p;
+    int s;          // element stride
+    long long a;    // array stride
+    __device__ __forceinline__ float &operator()(int arr, int i) const { return p[arr * a + i * s]; }
+};
+
+__global__ void __launch_bounds__(kAdjSteinerThreads) k_adj_steiner(const DevCtx c)
+{
+    __shared__ float s_col[kAdjArrays * kAdjColNodes * kAdjSteinerThreads];
+    const int t = threadIdx.x, it = blockIdx.x * kAdjSteinerThreads + t;
+    if (it >= c.st_n_items) return;
+    const int g = chk(c, c.st_items[it], c.I);
+    const int f0 = c.fo_ptr[g], m = c.fo_ptr[g + 1] - f0;
+    const int n0 = c.rc_ptr[g], n = chk(c, c.st_nlive[g], c.rc_ptr[g + 1] - n0 + 1);
+    if (m <= 0 || n <= 1) return;
+    const AdjNodes v = n <= kAdjColNodes ? AdjNodes{s_col + t, kAdjSteinerThreads, kAdjColNodes * kAdjSteinerThreads}
+                                         : AdjNodes{c.st_abuf + n0, 1, c.NN};
+    const int *par = c.st_parent + n0;
+    for (int i = 0; i < n; ++i) {
+        v(kA_PC, i) = 0.f;
+        v(kA_GX, i) = 0.f;
+        v(kA_GY, i) = 0.f;
+    }
+    for (int p = f0; p < f0 + m; ++p) v(kA_PC, chk(c, c.st_fo_node[p], n)) += 1e3f * c.fo_cap[p];
+    const float rx = c.r_per_um, ry = c.r_per_um_y, cx = c.c_per_um, cy = c.c_per_um_y;
+    const int K = c.K;
+    for (int k = 0; k < K; ++k) {
+        const float f = __ldg(c.rc_scale + k);
+        auto Cn = [&](int i) { return f * c.st_C[n0 + i] + v(kA_PC, i); };
+        auto Rn = [&](int i) { return f * c.st_R[n0 + i]; };
+        for (int i = 0; i < n; ++i) {
+            v(kA_CD, i) = Cn(i);
+            v(kA_DB, i) = 0.f;
+            v(kA_VB, i) = 0.f;
+        }
+        for (int i = n - 1; i >= 1; --i) v(kA_CD, par[i]) += v(kA_CD, i);
+        v(kA_D, 0) = 0.f;
+        for (int i = 1; i < n; ++i) v(kA_D, i) = v(kA_D, par[i]) + Rn(i) * v(kA_CD, i);
+        for (int i = 0; i < n; ++i) v(kA_M, i) = Cn(i) * v(kA_D, i);
+        for (int i = n - 1; i >= 1; --i) v(kA_M, par[i]) += v(kA_M, i);
+        for (int p = f0; p < f0 + m; ++p) {
+            const int s = chk(c, c.fo_pin[p], c.P), q = chk(c, c.st_fo_node[p], n);
+            const float4 as = c.adj[(size_t)s * K + k], Ss = c.slew[(size_t)s * K + k];
+            v(kA_DB, q) += 1e-6f * (as.x + as.y);
+            v(kA_VB, q) += 1e-12f * (as.z / (2.f * Ss.z) + as.w / (2.f * Ss.w));
+        }
+        for (int i = 0; i < n; ++i) {
+            v(kA_BB, i) = 2.f * v(kA_VB, i);
+            v(kA_RB, i) = 0.f;
+        }
+        for (int i = n - 1; i >= 1; --i) {
+            v(kA_RB, i) += v(kA_BB, i) * v(kA_M, i);
+            v(kA_BB, par[i]) += v(kA_BB, i);
+        }
+        v(kA_M, 0) = 0.f;   // M becomes Mbar, summed down from the root
+        for (int i = 1; i < n; ++i) v(kA_M, i) = v(kA_BB, i) * Rn(i) + v(kA_M, par[i]);
+        for (int i = 0; i < n; ++i) {   // BB becomes Cbar
+            const float mb = v(kA_M, i), Di = v(kA_D, i);
+            v(kA_BB, i) = mb * Di;
+            v(kA_DB, i) += mb * Cn(i) - 2.f * Di * v(kA_VB, i);
+        }
+        for (int i = n - 1; i >= 1; --i) {
+            v(kA_RB, i) += v(kA_DB, i) * v(kA_CD, i);
+            v(kA_DB, par[i]) += v(kA_DB, i);
+        }
+        v(kA_CD, 0) = 1e-3f * c.aload[(size_t)g * K + k];   // CD becomes Cdownbar, summed down
+        v(kA_BB, 0) += v(kA_CD, 0);
+        for (int i = 1; i < n; ++i) {
+            v(kA_CD, i) = v(kA_DB, i) * Rn(i) + v(kA_CD, par[i]);
+            v(kA_BB, i) += v(kA_CD, i);
+        }
+        for (int i = 1; i < n; ++i) {
+            const float rb = v(kA_RB, i), cb = v(kA_BB, i) + v(kA_BB, par[i]);
+            v(kA_GX, i) += f * (rx * rb + 0.5f * cx * cb);
+            v(kA_GY, i) += f * (ry * rb + 0.5f * cy * cb);
+        }
+    }
+    const int z = chk(c, item_out_pin(c, chk_type(c, c.item_type[g]), c.item_pin0[g]), c.P);
+    auto cell_of = [&](int j) -> int {
+        const int p = j ? chk(c, c.fo_pin[f0 + chk(c, j - 1, m)], c.P) : z;
+        return c.pin_cell[p] >= 0 ? chk(c, c.pin_cell[p], c.C) : -1;
+    };
+    for (int i = 1; i < n; ++i) {
+        const int2 ci = c.st_src[n0 + i], cp = c.st_src[n0 + par[i]];
+        const int codes[2][2] = {{ci.x, cp.x}, {ci.y, cp.y}};
+        const float gl[2] = {v(kA_GX, i), v(kA_GY, i)};
+        for (int ax = 0; ax < 2; ++ax) {
+            const int sg = (codes[ax][0] & 3) - 1;
+            if (sg == 0) continue;
+            const double gv = (double)gl[ax] * (double)sg;
+            const int ca = cell_of(codes[ax][0] >> 2), cq = cell_of(codes[ax][1] >> 2);
+            if (ca >= 0) atomicAdd(c.grad + 2 * (size_t)ca + ax, gv);
+            if (cq >= 0) atomicAdd(c.grad + 2 * (size_t)cq + ax, -gv);
+        }
+    }
+}
+
 template <bool UNIFORM>
 __global__ void k_adj_level(const DevCtx c, int i0, int i1)
 {
@@ -536,8 +658,15 @@ void launch_adjoint(const DevCtx &c, const HostSched &h, cudaStream_t st)
             else k_adj_level<false><<<nblk2(4LL * c.KL * (i1 - i0), 128), 128, 0, st>>>(c, i0, i1);
         }
     }
-    if (c.I > 0) k_adj_star<<<nblk2(c.I, 128), 128, 0, st>>>(c);
+    if (c.steiner) {
+        if (c.st_n_items > 0)
+            k_adj_steiner<<<nblk2(c.st_n_items, kAdjSteinerThreads), kAdjSteinerThreads, 0, st>>>(c);
+    } else if (c.I > 0) {
+        k_adj_star<<<nblk2(c.I, 128), 128, 0, st>>>(c);
+    }
 }
+
+size_t steiner_adjoint_floats(int64_t NN) { return (size_t)kAdjArrays * (size_t)std::max<int64_t>(1, NN); }
 
 size_t adjoint_smem_bytes(int T) { return (size_t)T * 3 * 4 * kLutStride * sizeof(float) + (size_t)T * 5 * sizeof(int); }
 

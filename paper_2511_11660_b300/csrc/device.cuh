@@ -109,6 +109,9 @@ struct DevCtx {
     int32_t steiner;
     float r_per_um_y, c_per_um_y;
     int32_t *st_parent, *st_fo_node, *st_nlive;
+    int2 *st_src;                               // [NN] differentiable contexts: per RC node, for x and y,
+                                                // (pin << 2) | (sign of node - parent + 1), pin = the
+                                                // lowest net pin (0 = driver) at that coordinate
     float *st_R, *st_C;
     int64_t *st_wl;                             // [I] tree length, nm
     const int64_t *st_node_ptr, *st_adj_ptr;    // [I + 1] working nodes / bitset words per item
@@ -156,6 +159,8 @@ struct DevCtx {
     double *obj;                                // [K][4] max(-s/g), sum exp(-s/g - max), TNS_g, WNS_g; [4K] J
     float *aload;                               // [I][K] dJ/dload of each item's output net
     double *grad;                               // [C][2] dJ/d(x, y)
+    float *st_abuf;                             // [kAdjArrays][NN] Steiner adjoint storage of trees above
+                                                // kAdjColNodes nodes
     double w_tns, w_wns;
     // shared table axes (valid when every table has the same ones): slew and
     // load breakpoints and reciprocal segment widths

@@ -65,6 +65,10 @@ void launch_coop_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cuda
 void launch_adjoint(const DevCtx &c, const HostSched &h, cudaStream_t st);
 size_t adjoint_smem_bytes(int T);
 cudaError_t adjoint_prepare(HostSched &h);
+// Steiner contexts: trees of more than kAdjColNodes nodes keep their adjoint
+// node arrays in a device buffer of steiner_adjoint_floats(NN) floats.
+constexpr int kAdjColNodes = 16;
+size_t steiner_adjoint_floats(int64_t NN);
 
 // The two-stage FP64 WNS/TNS reduction.
 void launch_reduce(const DevCtx &c, const HostSched &h, cudaStream_t st);

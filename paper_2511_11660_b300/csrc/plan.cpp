@@ -157,8 +157,6 @@ void build(const sta_design_desc *d, Plan &pl)
             "STA_WIRE_STEINER builds RC from positions (rc_ptr must be NULL)");
     REQUIRE(d->net_model == STA_NET_ELMORE || d->rc_ptr || d->wire_model == STA_WIRE_STEINER, STA_EINVAL,
             "STA_NET_ARNOLDI needs RC trees (rc_ptr) or Steiner trees");
-    REQUIRE(d->wire_model == STA_WIRE_STAR || d->gamma_ns == 0.f, STA_EINVAL,
-            "Steiner trees are not differentiable: gamma_ns must be 0");
     REQUIRE(d->net_model == STA_NET_ELMORE || (d->arnoldi_order >= 0 && d->arnoldi_order <= 3), STA_EINVAL,
             "arnoldi_order must be in 0..3");
     pl.net_model = d->net_model;

@@ -257,6 +257,7 @@ sta_status create_from_plan(sta_ctx *c, int device)
         d.st_n_items = (int32_t)pl.st_items.size();
         d.st_small = pl.st_small;
         d.st_adj = dev_alloc<unsigned>(c, std::max<int64_t>(1, pl.st_adj_ptr[pl.I]));
+        if (pl.gamma > 0.f) d.st_src = dev_alloc<int2>(c, NN);   // read by sta_backward
         d.rc_parent = d.st_parent;
         d.rc_R = d.st_R;
         d.rc_C = d.st_C;
@@ -414,7 +415,7 @@ int32_t launches_per_backward(const sta_ctx *c)
     } else {
         for (int32_t s = 0; s < pl.S; ++s) n += pl.stage_ptr[s + 1] > pl.stage_ptr[s];
     }
-    n += pl.I > 0;                               // star segments
+    n += pl.steiner ? !pl.st_items.empty() : pl.I > 0;   // star segments or Steiner trees
     return n;
 }
 
@@ -1269,6 +1270,8 @@ sta_status sta_backward(sta_ctx *c, double w_tns, double w_wns, double *J_out, d
     if (!(c->plan.gamma > 0.f) || !c->plan.placed)
         return fail(c, STA_ESTATE, "sta_backward needs a differentiable context (gamma_ns > 0, positions)");
     if (!std::isfinite(w_tns) || !std::isfinite(w_wns)) return fail(c, STA_EINVAL, "weights must be finite");
+    if (c->plan.steiner && c->plan.net_model != STA_NET_ELMORE)
+        return fail(c, STA_ESTATE, "sta_backward on Steiner trees needs the Elmore net model");
     try {
         CK(cudaSetDevice(c->device));
         cudaStream_t st = as_stream(stream);
@@ -1282,6 +1285,12 @@ sta_status sta_backward(sta_ctx *c, double w_tns, double w_wns, double *J_out, d
             d.abox_len = 2 * (size_t)c->plan.P * K;
             d.abox = dev_alloc<float4>(c, d.abox_len);
             CK(cudaMemset(d.abox, 0xFF, std::max<size_t>(1, d.abox_len) * sizeof(float4)));
+            if (c->plan.steiner) {   // node storage for trees too large for the shared-memory column
+                int64_t big = 0;
+                for (int32_t g = 0; g < c->plan.I; ++g)
+                    big = std::max<int64_t>(big, c->plan.rc_ptr[g + 1] - c->plan.rc_ptr[g]);
+                if (big > sta::kAdjColNodes) d.st_abuf = dev_alloc<float>(c, sta::steiner_adjoint_floats(c->plan.NN));
+            }
         }
         if (!c->hs.adj_ready) {
             const cudaError_t e = sta::adjoint_prepare(c->hs);

@@ -117,6 +117,20 @@ __device__ void write_tree(const DevCtx &c, int g, int f0, int n, int N, bool st
     c.st_R[n0] = 0.f;
     long long total = 0;
     const float rx = c.r_per_um, ry = c.r_per_um_y, cx = c.c_per_um, cy = c.c_per_um_y;
+    // differentiable contexts: which pin carries each coordinate of node b
+    // (the lowest one at that value; every coordinate is a pin's), and the
+    // sign of b - a along it
+    auto src_code = [&](int b, int a, bool along_y) -> int {
+        const long long v = along_y ? w.y(b) : w.x(b), u = along_y ? w.y(a) : w.x(a);
+        int j = 0;
+        while (j < n && (along_y ? w.y(j) : w.x(j)) != v) ++j;
+        if (j >= n) {   // not reached: medians of pin coordinates
+            atomicOr(c.err, kErrBounds);
+            j = 0;
+        }
+        return (j << 2) | ((v > u) - (v < u) + 1);
+    };
+    if (c.st_src) c.st_src[n0] = make_int2(1, 1);   // the driver, sign 0
     auto visit = [&](int a, int b) -> bool {
         if (w.id(b) >= 0) return true;
         w.set_qu(tail++, b);   // tail <= N <= cap: each working node is queued once
@@ -136,6 +150,7 @@ __device__ void write_tree(const DevCtx &c, int g, int f0, int n, int N, bool st
         const float half = 0.5f * (cx * lx + cy * ly);
         c.st_parent[n0 + nodes] = ia;
         c.st_R[n0 + nodes] = rx * lx + ry * ly;
+        if (c.st_src) c.st_src[n0 + nodes] = make_int2(src_code(b, a, false), src_code(b, a, true));
         w.cp(nodes) = half;
         w.cp(ia) += half;
         ++nodes;

@@ -105,6 +105,54 @@ def test_device_outputs_and_autograd():
     ctx.close()
 
 
+def _steiner_design(case):
+    if case == "fanout":
+        # nets of 80 pins (minimum spanning tree) and 20-63 pins: trees of more
+        # than 16 nodes, whose adjoint works in global scratch
+        bld = synth.Builder(synth.make_library(0))
+        rng = np.random.default_rng(2)
+        pi = bld.pi(xy=(10.0, 10.0))
+        for _ in range(80):
+            bld.po(pi, xy=tuple(float(v) for v in rng.uniform(0, 300, 2)))
+        for k in (20, 40, 63):
+            x = bld.cell("BUF", [pi], xy=tuple(float(v) for v in rng.uniform(0, 300, 2)))
+            for _ in range(k):
+                bld.po(x, xy=tuple(float(v) for v in rng.uniform(0, 300, 2)))
+        d = bld.design(placed=True, period_ns=2.0)
+        d["gamma_ns"] = 0.01
+    else:
+        kw = {}
+        if case == "corners":
+            ls, rs = synth.lut_corners()
+            kw = dict(n_corners=4, lut_scale=ls, rc_scale=rs)
+        d = synth.make_design(3000, 20, seed=7, placed=True, placement="local", gamma_ns=0.01, **kw)
+    d["wire_model"] = 1
+    d["r_per_um"] = 0.5
+    if case == "xy":
+        d["r_per_um_y"], d["c_per_um_y"] = 0.3, 0.35
+    d["period_ns"], _ = tune_period(d, min_half_gap=0.0)
+    return d
+
+
+@pytest.mark.parametrize("case", ["local", "xy", "corners", "fanout"])
+@pytest.mark.parametrize("adj_schedule", [sta.SCHED_DATAFLOW, sta.SCHED_LEVEL], ids=["adj_dataflow", "adj_level"])
+def test_steiner_gradient(case, adj_schedule):
+    """Steiner-tree RC (STA_WIRE_STEINER) with the trees of the update held
+    fixed: J, the per-corner terms and every gradient component against the
+    oracle, whose Steiner adjoint is pinned to central differences."""
+    d = _steiner_design(case)
+    ctx = sta.Context(d)
+    ctx.set_adjoint_schedule(adj_schedule)
+    ctx.update_timing()
+    J, terms, g = ctx.backward()
+    ctx.close()
+    J0, terms0, g0 = oracle.objective_grad(d)
+    assert J == pytest.approx(J0, rel=1e-5)
+    np.testing.assert_allclose(terms, terms0, rtol=1e-5)
+    check_grad(g, g0)
+    assert np.abs(g0).max() > 0
+
+
 def test_backward_state_errors():
     d = synth.make_design(300, 5, seed=1)              # RC trees: not differentiable
     ctx = sta.Context(d)
@@ -116,6 +164,13 @@ def test_backward_state_errors():
     ctx = sta.Context(d)
     with pytest.raises(sta.StaError) as ei:
         ctx.backward()                                  # before any update
+    assert ei.value.status == sta.ESTATE
+    ctx.close()
+    d = dict(placed(300, 5, 1), wire_model=1, net_model=1)   # Steiner with Arnoldi delays
+    ctx = sta.Context(d)
+    ctx.update_timing()
+    with pytest.raises(sta.StaError) as ei:
+        ctx.backward()
     assert ei.value.status == sta.ESTATE
     ctx.close()
 

@@ -5,7 +5,7 @@ which the next synchronising call reports.  This runs representative cases
 through that build -- every schedule, several corners, a batch, large RC
 trees swept in global scratch, star RC, Steiner trees (all three Steiner
 kernels) with the Arnoldi model, exceptions with -through sets, the adjoint
-and the path report -- in a child process
+on stars and on Steiner trees, and the path report -- in a child process
 (the binding holds one library per process), checks them against the FP64
 oracle and requires that no check fired."""
 import os
@@ -53,6 +53,10 @@ for k in (20, 40, 63):
 fan = bld.design(placed=True, period_ns=2.0)
 fan["wire_model"] = 1
 cases["steiner_fanout"] = fan
+# the Steiner adjoint: trees in shared-memory columns and (the large nets) in global scratch
+cases["steiner_grad"] = dict(synth.make_design(3000, 15, seed=5, placed=True, placement="local", gamma_ns=0.01,
+                                               period_ns=1.0), wire_model=1)
+cases["steiner_fanout_grad"] = dict(fan, gamma_ns=0.01)
 for name, d in cases.items():
     ref = oracle.sta(d)
     for sch in (sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP):
