@@ -450,107 +450,158 @@ __global__ void k_adj_star(const DevCtx c)
 // is a pin's (Steiner points take medians); the tree writer recorded the
 // lowest net pin at it and the sign of node - parent, so Lx_i moves by +-1
 // per um of the two carrying pins' cells (nm rounding taken as the
-// identity, sign 0 at equal coordinates).  One thread per net; node arrays
-// in a shared-memory column (trees of at most kAdjColNodes nodes) or in
-// global scratch.
-constexpr int kAdjSteinerThreads = 64;
-enum { kA_PC, kA_CD, kA_D, kA_M, kA_DB, kA_VB, kA_RB, kA_BB, kA_GX, kA_GY, kAdjArrays };
+// identity, sign 0 at equal coordinates).  One thread per net.  The tree
+// (parents, R), the pin caps and every per-node sum sit in a shared-memory
+// column of COLN nodes, where the gradient is also summed per net pin (up to
+// COLP pins) before one FP64 atomic per pin and axis: nets of at most 9 pins
+// take 16-node columns, 64 threads a block; larger ones 128-node columns, 8
+// threads a block, largest first.  Trees beyond a column work in global
+// scratch with an atomic per contribution.
+enum { kA_PAR, kA_R, kA_PC, kA_CN, kA_CD, kA_D, kA_M, kA_DB, kA_RB, kA_BB, kAdjArrays };
 
-struct AdjNodes {
-    float *p;
-    int s;          // element stride
+// Node arrays of one net: a shared-memory column (element i of array a at
+// s_col[(a COLN + i) NT + thread]) or a row of the global scratch.
+template <int COLN, int NT>
+struct ColNodes {
+    float *p;   // s_col + thread
+    __device__ __forceinline__ float &operator()(int arr, int i) const { return p[(arr * COLN + i) * NT]; }
+};
+struct RowNodes {
+    float *p;       // scratch + first node
     long long a;    // array stride
-    __device__ __forceinline__ float &operator()(int arr, int i) const { return p[arr * a + i * s]; }
+    __device__ __forceinline__ float &operator()(int arr, int i) const { return p[arr * a + i]; }
 };
 
-__global__ void __launch_bounds__(kAdjSteinerThreads) k_adj_steiner(const DevCtx c)
+// The sweeps of one net (n tree nodes from n0, m sinks from f0); scatter(j,
+// axis, g) takes dJ/d(coordinate of net pin j).  Every input is read-only
+// here and goes through the read-only path.  Per corner: Cdown (up), D and
+// M = C D (down), the sinks' seeds, then in one upward sweep the subtree
+// sums of M and betabar with Rbar += betabar M, in one downward sweep Mbar
+// with Cbar and Dbar's M term, in one upward sweep Dbar with Rbar += Dbar
+// Cdown, and in one downward sweep Cdownbar, Cbar and the scatter.
+template <class V, class S>
+__device__ __forceinline__ void steiner_adjoint_net(const DevCtx &c, const V &v, const S &scatter, int g, int f0,
+                                                    int m, int n0, int n)
 {
-    __shared__ float s_col[kAdjArrays * kAdjColNodes * kAdjSteinerThreads];
-    const int t = threadIdx.x, it = blockIdx.x * kAdjSteinerThreads + t;
-    if (it >= c.st_n_items) return;
-    const int g = chk(c, c.st_items[it], c.I);
-    const int f0 = c.fo_ptr[g], m = c.fo_ptr[g + 1] - f0;
-    const int n0 = c.rc_ptr[g], n = chk(c, c.st_nlive[g], c.rc_ptr[g + 1] - n0 + 1);
-    if (m <= 0 || n <= 1) return;
-    const AdjNodes v = n <= kAdjColNodes ? AdjNodes{s_col + t, kAdjSteinerThreads, kAdjColNodes * kAdjSteinerThreads}
-                                         : AdjNodes{c.st_abuf + n0, 1, c.NN};
-    const int *par = c.st_parent + n0;
+    auto par = [&](int i) { return __float_as_int(v(kA_PAR, i)); };
+#pragma unroll 4
     for (int i = 0; i < n; ++i) {
+        v(kA_PAR, i) = __int_as_float(i ? chk(c, __ldg(c.st_parent + n0 + i), i) : -1);
+        v(kA_R, i) = __ldg(c.st_R + n0 + i);
         v(kA_PC, i) = 0.f;
-        v(kA_GX, i) = 0.f;
-        v(kA_GY, i) = 0.f;
     }
-    for (int p = f0; p < f0 + m; ++p) v(kA_PC, chk(c, c.st_fo_node[p], n)) += 1e3f * c.fo_cap[p];
+#pragma unroll 4
+    for (int p = f0; p < f0 + m; ++p) v(kA_PC, chk(c, __ldg(c.st_fo_node + p), n)) += 1e3f * __ldg(c.fo_cap + p);
     const float rx = c.r_per_um, ry = c.r_per_um_y, cx = c.c_per_um, cy = c.c_per_um_y;
     const int K = c.K;
     for (int k = 0; k < K; ++k) {
         const float f = __ldg(c.rc_scale + k);
-        auto Cn = [&](int i) { return f * c.st_C[n0 + i] + v(kA_PC, i); };
-        auto Rn = [&](int i) { return f * c.st_R[n0 + i]; };
+#pragma unroll 4
         for (int i = 0; i < n; ++i) {
-            v(kA_CD, i) = Cn(i);
+            const float cn = f * __ldg(c.st_C + n0 + i) + v(kA_PC, i);
+            v(kA_CN, i) = cn;
+            v(kA_CD, i) = cn;
             v(kA_DB, i) = 0.f;
-            v(kA_VB, i) = 0.f;
+            v(kA_BB, i) = 0.f;
         }
-        for (int i = n - 1; i >= 1; --i) v(kA_CD, par[i]) += v(kA_CD, i);
+        for (int i = n - 1; i >= 1; --i) v(kA_CD, par(i)) += v(kA_CD, i);
         v(kA_D, 0) = 0.f;
-        for (int i = 1; i < n; ++i) v(kA_D, i) = v(kA_D, par[i]) + Rn(i) * v(kA_CD, i);
-        for (int i = 0; i < n; ++i) v(kA_M, i) = Cn(i) * v(kA_D, i);
-        for (int i = n - 1; i >= 1; --i) v(kA_M, par[i]) += v(kA_M, i);
-        for (int p = f0; p < f0 + m; ++p) {
-            const int s = chk(c, c.fo_pin[p], c.P), q = chk(c, c.st_fo_node[p], n);
-            const float4 as = c.adj[(size_t)s * K + k], Ss = c.slew[(size_t)s * K + k];
-            v(kA_DB, q) += 1e-6f * (as.x + as.y);
-            v(kA_VB, q) += 1e-12f * (as.z / (2.f * Ss.z) + as.w / (2.f * Ss.w));
+        v(kA_M, 0) = 0.f;
+        for (int i = 1; i < n; ++i) {
+            const float Di = v(kA_D, par(i)) + f * v(kA_R, i) * v(kA_CD, i);
+            v(kA_D, i) = Di;
+            v(kA_M, i) = v(kA_CN, i) * Di;
         }
-        for (int i = 0; i < n; ++i) {
-            v(kA_BB, i) = 2.f * v(kA_VB, i);
-            v(kA_RB, i) = 0.f;
+#pragma unroll 4
+        for (int p = f0; p < f0 + m; ++p) {   // Dbar with its -2 D varbar term; BB = 2 varbar
+            const int s = chk(c, __ldg(c.fo_pin + p), c.P), q = chk(c, __ldg(c.st_fo_node + p), n);
+            const float4 as = __ldg(c.adj + (size_t)s * K + k), Ss = __ldg(c.slew + (size_t)s * K + k);
+            const float bb = 2e-12f * (as.z / (2.f * Ss.z) + as.w / (2.f * Ss.w));
+            v(kA_DB, q) += 1e-6f * (as.x + as.y) - v(kA_D, q) * bb;
+            v(kA_BB, q) += bb;
+        }
+        for (int i = n - 1; i >= 1; --i) {   // M and betabar summed up the subtree
+            const int pi = par(i);
+            const float Mi = v(kA_M, i), bi = v(kA_BB, i);
+            v(kA_M, pi) += Mi;
+            v(kA_RB, i) = bi * Mi;
+            v(kA_BB, pi) += bi;
+        }
+        v(kA_M, 0) = 0.f;    // M becomes Mbar, BB becomes Cbar
+        v(kA_BB, 0) = 0.f;
+        for (int i = 1; i < n; ++i) {
+            const float mb = v(kA_BB, i) * f * v(kA_R, i) + v(kA_M, par(i));
+            v(kA_M, i) = mb;
+            v(kA_BB, i) = mb * v(kA_D, i);
+            v(kA_DB, i) += mb * v(kA_CN, i);
         }
         for (int i = n - 1; i >= 1; --i) {
-            v(kA_RB, i) += v(kA_BB, i) * v(kA_M, i);
-            v(kA_BB, par[i]) += v(kA_BB, i);
+            const float db = v(kA_DB, i);
+            v(kA_RB, i) += db * v(kA_CD, i);
+            v(kA_DB, par(i)) += db;
         }
-        v(kA_M, 0) = 0.f;   // M becomes Mbar, summed down from the root
-        for (int i = 1; i < n; ++i) v(kA_M, i) = v(kA_BB, i) * Rn(i) + v(kA_M, par[i]);
-        for (int i = 0; i < n; ++i) {   // BB becomes Cbar
-            const float mb = v(kA_M, i), Di = v(kA_D, i);
-            v(kA_BB, i) = mb * Di;
-            v(kA_DB, i) += mb * Cn(i) - 2.f * Di * v(kA_VB, i);
-        }
-        for (int i = n - 1; i >= 1; --i) {
-            v(kA_RB, i) += v(kA_DB, i) * v(kA_CD, i);
-            v(kA_DB, par[i]) += v(kA_DB, i);
-        }
-        v(kA_CD, 0) = 1e-3f * c.aload[(size_t)g * K + k];   // CD becomes Cdownbar, summed down
+        v(kA_CD, 0) = 1e-3f * __ldg(c.aload + (size_t)g * K + k);   // CD becomes Cdownbar
         v(kA_BB, 0) += v(kA_CD, 0);
         for (int i = 1; i < n; ++i) {
-            v(kA_CD, i) = v(kA_DB, i) * Rn(i) + v(kA_CD, par[i]);
-            v(kA_BB, i) += v(kA_CD, i);
-        }
-        for (int i = 1; i < n; ++i) {
-            const float rb = v(kA_RB, i), cb = v(kA_BB, i) + v(kA_BB, par[i]);
-            v(kA_GX, i) += f * (rx * rb + 0.5f * cx * cb);
-            v(kA_GY, i) += f * (ry * rb + 0.5f * cy * cb);
+            const int pi = par(i);
+            const float cdb = v(kA_DB, i) * f * v(kA_R, i) + v(kA_CD, pi);
+            v(kA_CD, i) = cdb;
+            const float cbi = v(kA_BB, i) + cdb;
+            v(kA_BB, i) = cbi;
+            const float rb = v(kA_RB, i), cb = cbi + v(kA_BB, pi);
+            const float gl[2] = {f * (rx * rb + 0.5f * cx * cb), f * (ry * rb + 0.5f * cy * cb)};
+            const int2 ci = __ldg(c.st_src + n0 + i), cp = __ldg(c.st_src + n0 + pi);
+            const int own[2] = {ci.x, ci.y}, up[2] = {cp.x, cp.y};
+            for (int ax = 0; ax < 2; ++ax) {
+                const int sg = (own[ax] & 3) - 1;
+                if (sg == 0) continue;
+                scatter(own[ax] >> 2, ax, sg * gl[ax]);
+                scatter(up[ax] >> 2, ax, -sg * gl[ax]);
+            }
         }
     }
-    const int z = chk(c, item_out_pin(c, chk_type(c, c.item_type[g]), c.item_pin0[g]), c.P);
+}
+
+// Items i0 .. i1 - 1 of the Steiner list (by increasing pin count), the
+// last first.
+template <int COLN, int COLP, int NT>
+__global__ void __launch_bounds__(NT) k_adj_steiner(const DevCtx c, int i0, int i1)
+{
+    __shared__ float s_col[kAdjArrays * COLN * NT];
+    __shared__ float s_pin[2 * COLP * NT];
+    const int t = threadIdx.x, it = blockIdx.x * NT + t;
+    if (it >= i1 - i0) return;
+    const int g = chk(c, __ldg(c.st_items + i1 - 1 - it), c.I);
+    const int f0 = __ldg(c.fo_ptr + g), m = __ldg(c.fo_ptr + g + 1) - f0;
+    const int n0 = __ldg(c.rc_ptr + g), n = chk(c, __ldg(c.st_nlive + g), __ldg(c.rc_ptr + g + 1) - n0 + 1);
+    if (m <= 0 || n <= 1) return;
+    const int z = chk(c, item_out_pin(c, chk_type(c, __ldg(c.item_type + g)), __ldg(c.item_pin0 + g)), c.P);
     auto cell_of = [&](int j) -> int {
-        const int p = j ? chk(c, c.fo_pin[f0 + chk(c, j - 1, m)], c.P) : z;
-        return c.pin_cell[p] >= 0 ? chk(c, c.pin_cell[p], c.C) : -1;
+        const int p = j ? chk(c, __ldg(c.fo_pin + f0 + chk(c, j - 1, m)), c.P) : z;
+        const int cc = __ldg(c.pin_cell + p);
+        return cc >= 0 ? chk(c, cc, c.C) : -1;
     };
-    for (int i = 1; i < n; ++i) {
-        const int2 ci = c.st_src[n0 + i], cp = c.st_src[n0 + par[i]];
-        const int codes[2][2] = {{ci.x, cp.x}, {ci.y, cp.y}};
-        const float gl[2] = {v(kA_GX, i), v(kA_GY, i)};
-        for (int ax = 0; ax < 2; ++ax) {
-            const int sg = (codes[ax][0] & 3) - 1;
-            if (sg == 0) continue;
-            const double gv = (double)gl[ax] * (double)sg;
-            const int ca = cell_of(codes[ax][0] >> 2), cq = cell_of(codes[ax][1] >> 2);
-            if (ca >= 0) atomicAdd(c.grad + 2 * (size_t)ca + ax, gv);
-            if (cq >= 0) atomicAdd(c.grad + 2 * (size_t)cq + ax, -gv);
+    if (n <= COLN && m + 1 <= COLP) {
+        for (int j = 0; j < 2 * (m + 1); ++j) s_pin[j * NT + t] = 0.f;
+        steiner_adjoint_net(
+            c, ColNodes<COLN, NT>{s_col + t},
+            [&](int j, int ax, float gv) { s_pin[(2 * chk(c, j, m + 1) + ax) * NT + t] += gv; }, g, f0, m, n0, n);
+        for (int j = 0; j <= m; ++j) {
+            const int cc = cell_of(j);
+            if (cc < 0) continue;
+            for (int ax = 0; ax < 2; ++ax) {
+                const float gv = s_pin[(2 * j + ax) * NT + t];
+                if (gv != 0.f) atomicAdd(c.grad + 2 * (size_t)cc + ax, (double)gv);
+            }
         }
+    } else {
+        steiner_adjoint_net(
+            c, RowNodes{c.st_abuf + n0, c.NN},
+            [&](int j, int ax, float gv) {
+                const int cc = cell_of(j);
+                if (cc >= 0) atomicAdd(c.grad + 2 * (size_t)cc + ax, (double)gv);
+            },
+            g, f0, m, n0, n);
     }
 }
 
@@ -659,8 +710,10 @@ void launch_adjoint(const DevCtx &c, const HostSched &h, cudaStream_t st)
         }
     }
     if (c.steiner) {
-        if (c.st_n_items > 0)
-            k_adj_steiner<<<nblk2(c.st_n_items, kAdjSteinerThreads), kAdjSteinerThreads, 0, st>>>(c);
+        const int ns = c.st_adj_small, nl = c.st_n_items - ns;
+        if (ns > 0) k_adj_steiner<kAdjColNodes, 9, 64><<<nblk2(ns, 64), 64, 0, st>>>(c, 0, ns);
+        if (nl > 0)
+            k_adj_steiner<kAdjBigColNodes, 64, 8><<<nblk2(nl, 8), 8, 0, st>>>(c, ns, c.st_n_items);
     } else if (c.I > 0) {
         k_adj_star<<<nblk2(c.I, 128), 128, 0, st>>>(c);
     }

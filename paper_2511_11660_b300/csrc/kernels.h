@@ -65,9 +65,12 @@ void launch_coop_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cuda
 void launch_adjoint(const DevCtx &c, const HostSched &h, cudaStream_t st);
 size_t adjoint_smem_bytes(int T);
 cudaError_t adjoint_prepare(HostSched &h);
-// Steiner contexts: trees of more than kAdjColNodes nodes keep their adjoint
-// node arrays in a device buffer of steiner_adjoint_floats(NN) floats.
-constexpr int kAdjColNodes = 16;
+// Steiner contexts: the adjoint of a net's tree works in a shared-memory
+// column of kAdjColNodes nodes (nets of at most kAdjSmallPins pins) or
+// kAdjBigColNodes nodes (larger nets, at most 64 pins); trees beyond that
+// keep their node arrays in a device buffer of steiner_adjoint_floats(NN)
+// floats, needed when some net has room for kAdjBigColNodes nodes or more.
+constexpr int kAdjColNodes = 16, kAdjSmallPins = 9, kAdjBigColNodes = 128;
 size_t steiner_adjoint_floats(int64_t NN);
 
 // The two-stage FP64 WNS/TNS reduction.

@@ -256,6 +256,11 @@ sta_status create_from_plan(sta_ctx *c, int device)
         d.st_items = upload(c, pl.st_items);
         d.st_n_items = (int32_t)pl.st_items.size();
         d.st_small = pl.st_small;
+        d.st_adj_small = 0;
+        while (d.st_adj_small < d.st_n_items &&
+               pl.fo_ptr[pl.st_items[d.st_adj_small] + 1] - pl.fo_ptr[pl.st_items[d.st_adj_small]] + 1 <=
+                   sta::kAdjSmallPins)
+            ++d.st_adj_small;
         d.st_adj = dev_alloc<unsigned>(c, std::max<int64_t>(1, pl.st_adj_ptr[pl.I]));
         if (pl.gamma > 0.f) d.st_src = dev_alloc<int2>(c, NN);   // read by sta_backward
         d.rc_parent = d.st_parent;
@@ -415,7 +420,8 @@ int32_t launches_per_backward(const sta_ctx *c)
     } else {
         for (int32_t s = 0; s < pl.S; ++s) n += pl.stage_ptr[s + 1] > pl.stage_ptr[s];
     }
-    n += pl.steiner ? !pl.st_items.empty() : pl.I > 0;   // star segments or Steiner trees
+    if (pl.steiner) n += (c->dc.st_adj_small > 0) + (c->dc.st_n_items > c->dc.st_adj_small);   // Steiner trees
+    else n += pl.I > 0;                                    // star segments
     return n;
 }
 
@@ -1289,7 +1295,7 @@ sta_status sta_backward(sta_ctx *c, double w_tns, double w_wns, double *J_out, d
                 int64_t big = 0;
                 for (int32_t g = 0; g < c->plan.I; ++g)
                     big = std::max<int64_t>(big, c->plan.rc_ptr[g + 1] - c->plan.rc_ptr[g]);
-                if (big > sta::kAdjColNodes) d.st_abuf = dev_alloc<float>(c, sta::steiner_adjoint_floats(c->plan.NN));
+                if (big >= sta::kAdjBigColNodes) d.st_abuf = dev_alloc<float>(c, sta::steiner_adjoint_floats(c->plan.NN));
             }
         }
         if (!c->hs.adj_ready) {
