@@ -425,6 +425,29 @@ sta_status sta_report_paths(sta_ctx *ctx, int32_t design, int32_t corner, int32_
                             int8_t *path_rf, float *path_at, float *path_slack, int32_t *path_endpoint,
                             int32_t pin_capacity, sta_mem mem, void *stream);
 
+/* Top-k path report with a per-endpoint report limit (Sec. III "Report
+ * options": top-k, per-endpoint report limit, slack-less-than threshold):
+ * the k paths of design `design` with the smallest setup slack at `corner`
+ * below slack_lt, at most per_endpoint (1..32) of them ending at any one
+ * endpoint, in increasing slack (ties: the endpoint's place in the
+ * per-endpoint-1 order, then the path's rank there).  A path's late
+ * arrival adds, along the path, each cell arc's NLDM delay at the
+ * analysis' input slew and output load and each net's delay; relative to
+ * the critical path of sta_report_paths, a path leaves the critical fan-in
+ * at some gate outputs, each costing (critical candidate - its candidate),
+ * and its slack is its end edge's late slack plus those costs.  Only the k
+ * worst endpoints can hold one of the k worst paths; each of them is
+ * searched best-first over these deviations.  path_at holds the path's own
+ * arrivals (the analysis' arrival less the deviation costs at or above the
+ * pin); path_slack the path's slack; the other outputs as sta_report_paths
+ * (an endpoint may appear several times).  per_endpoint = 1 is
+ * sta_report_paths.  Errors: STA_EINVAL also when k * per_endpoint > 16384
+ * or, with per_endpoint > 1, the design has timing exceptions. */
+sta_status sta_report_paths_nworst(sta_ctx *ctx, int32_t design, int32_t corner, int32_t k, int32_t per_endpoint,
+                                   float slack_lt, int32_t *n_paths, int32_t *n_pins, int32_t *path_ptr,
+                                   int32_t *path_pin, int8_t *path_rf, float *path_at, float *path_slack,
+                                   int32_t *path_endpoint, int32_t pin_capacity, sta_mem mem, void *stream);
+
 /* Device views in the library's internal (level-major) pin order; valid
  * until the next sta_update_timing or sta_destroy.  gpu_pin_of[p] maps a
  * caller pin id to its internal index (device int32 array). */

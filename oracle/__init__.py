@@ -435,3 +435,145 @@ def report_paths(d: dict, k: int, slack_lt: float = float("inf"), corner: int = 
         out.append({"endpoint": int(eps[e]), "slack": float(es[e]), "pins": np.array(pins),
                     "rf": np.array(rfs, np.int8), "at": np.array(ats)})
     return out
+
+
+def report_paths_nworst(d: dict, k: int, per_endpoint: int, slack_lt: float = float("inf"), corner: int = 0,
+                        res: dict | None = None):
+    """Top-k path report with a per-endpoint limit (Sec. III "Report
+    options": top-k, per-endpoint report limit, slack-less-than threshold):
+    the k paths of smallest setup slack at ``corner`` below ``slack_lt``,
+    at most ``per_endpoint`` of them ending at any one endpoint.
+
+    A path runs from a startpoint (PI or CK) to an endpoint through timing
+    arcs; its late arrival adds, along the path, each cell arc's NLDM delay
+    at the analysis' own input slew and output load, and each net's delay.
+    Relative to the critical path of report_paths (same tie rules), a path
+    is the endpoint edge it ends on plus the gate outputs where it leaves the
+    critical fan-in: leaving it at output (p, rf) for input arc (a, rfi)
+    costs dev = cand(critical) - cand(a, rfi) >= 0 with cand = late arrival
+    of (a, rfi) + arc delay, and the path's slack is the endpoint edge's
+    slack plus the sum of its devs.  Each endpoint's paths come from a
+    best-first search over these deviation sets, every set generated once:
+    a path's children leave the critical fan-in at or above its last
+    deviation's input pin.  The endpoints considered are the k worst (no
+    other can hold one of the k worst paths); their paths are merged by
+    (slack, endpoint order, rank at the endpoint).  Returns dicts like
+    report_paths, with the pins, edges and the path's own late arrivals.
+    Without timing exceptions only."""
+    import heapq
+    if n_tags(d) != 1:
+        raise ValueError("per-endpoint limit above 1 needs a design without timing exceptions")
+    res = res if res is not None else sta(d)
+    K = int(d.get("n_corners", 1))
+    sc = float(np.asarray(d["lut_scale"] if d.get("lut_scale") is not None else np.ones(K))[corner])
+    load, _, _ = net_delays(d, corner)
+    role = np.asarray(d["pin_role"])
+    cpp, cp = np.asarray(d["cell_pin_ptr"]), np.asarray(d["cell_pin"])
+    ctype, nin = np.asarray(d["cell_type"]), np.asarray(d["type_nin"])
+    kind = np.asarray(d["type_kind"])
+    sense = np.asarray(d["arc_sense"]).reshape(-1, 3)
+    i1 = np.asarray(d["lut_idx1"]).reshape(-1, 3, 4, 7)
+    i2 = np.asarray(d["lut_idx2"]).reshape(-1, 3, 4, 7)
+    vv = np.asarray(d["lut_val"]).reshape(-1, 3, 4, 49)
+    cell_of = -np.ones(d["n_pins"], int)
+    for c in range(d["n_cells"]):
+        cell_of[cp[cpp[c]:cpp[c + 1]]] = c
+    npp, npn = np.asarray(d["net_pin_ptr"]), np.asarray(d["net_pin"])
+    driver = -np.ones(d["n_pins"], int)
+    for n in range(d["n_nets"]):
+        driver[npn[npp[n] + 1:npp[n + 1]]] = npn[npp[n]]
+    at, slew = res["at"][:, corner], res["slew"][:, corner]
+    arcs_on = {0: lambda i, o: i == o, 1: lambda i, o: i != o, 2: lambda i, o: True}
+
+    def fanin(p, rf):
+        """Candidates of node (p, rf): [(a, rfi, cand)] in tie order, or one
+        (driver / CK) step, or [] at a startpoint; and whether p is a gate output."""
+        if driver[p] >= 0:
+            return [(int(driver[p]), rf, None)], False
+        if role[p] in (0, 5):
+            return [], False
+        c = cell_of[p]
+        t = ctype[c]
+        if kind[t] == 1:
+            return [(int(cp[cpp[c] + int(np.nonzero(sense[t] == 3)[0][0])]), 0, None)], False
+        out = []
+        for j in range(nin[t]):
+            a = int(cp[cpp[c] + j])
+            for rfi in (0, 1):
+                if sense[t, j] < 0 or not arcs_on[int(sense[t, j])](rfi, rf):
+                    continue
+                dl = lut_eval(i1[t, j, rf], i2[t, j, rf], vv[t, j, rf], slew[a, 2 + rfi], load[p])[0]
+                out.append((a, rfi, at[a, 2 + rfi] + sc * dl))
+        return out, True
+
+    def critical(cands):
+        best = 0
+        for i in range(1, len(cands)):
+            if cands[i][2] > cands[best][2]:
+                best = i
+        return best
+
+    def region(p, rf):
+        """Deviations at or above node (p, rf) along the critical fan-in:
+        [(dev, (p, rf, a, rfi))]."""
+        out = []
+        while True:
+            cands, gate = fanin(p, rf)
+            if not cands:
+                return out
+            b = critical(cands) if gate else 0
+            if gate:
+                for i, (a, rfi, cand) in enumerate(cands):
+                    if i != b:
+                        out.append((cands[b][2] - cand, (p, rf, a, rfi)))
+            p, rf = cands[b][0], cands[b][1]
+
+    eps, es = res["endpoints"], res["ep_setup"][:, corner]
+    order = sorted((e for e in range(len(eps)) if es[e] < slack_lt), key=lambda e: (es[e], e))[:k]
+    found = []
+    for oi, e in enumerate(order):
+        p = int(eps[e])
+        sl = res["slack"][p, corner]
+        heap, seq = [], 0
+        for rf in (0, 1):
+            heapq.heappush(heap, (float(sl[2 + rf]), seq, rf, ()))
+            seq += 1
+        rank = 0
+        while heap and rank < per_endpoint:
+            cost, _, rf, devs = heapq.heappop(heap)
+            if not cost < slack_lt:
+                break
+            found.append((cost, oi, rank, p, rf, devs))
+            rank += 1
+            start = (p, rf) if not devs else (devs[-1][2], devs[-1][3])
+            for dv, dev in region(*start):
+                heapq.heappush(heap, (cost + dv, seq, rf, devs + (dev,)))
+                seq += 1
+    found.sort(key=lambda f: (f[0], f[1], f[2]))
+    out = []
+    for cost, _, _, p, rf, devs in found[:k]:
+        pins, rfs, ats, dsum = [], [], [], []
+        q, qrf, di, acc = p, rf, 0, 0.0
+        while True:
+            pins.append(q)
+            rfs.append(qrf)
+            cands, gate = fanin(q, qrf)
+            if not cands:
+                break
+            if gate and di < len(devs) and devs[di][0] == q and devs[di][1] == qrf:
+                b = critical(cands)
+                alt = [x for x in cands if x[0] == devs[di][2] and x[1] == devs[di][3]][0]
+                dsum.append(cands[b][2] - alt[2])
+                q, qrf = alt[0], alt[1]
+                di += 1
+                continue
+            dsum.append(0.0)
+            b = critical(cands) if gate else 0
+            q, qrf = cands[b][0], cands[b][1]
+        dsum.append(0.0)
+        # the path's arrival at a pin: the analysis' arrival less the devs taken at or above it
+        up = np.cumsum(dsum[::-1])[::-1]
+        ats = [at[x, 2 + r] - u for x, r, u in zip(pins, rfs, up[:len(pins)])]
+        out.append({"endpoint": p, "slack": cost, "pins": np.array(pins[::-1]),
+                    "rf": np.array(rfs[::-1], np.int8), "at": np.array(ats[::-1])})
+    return out

@@ -79,6 +79,17 @@ void launch_reduce(const DevCtx &c, const HostSched &h, cudaStream_t st);
 // Top-k path report of one design (paths.cu): selection of the k worst
 // endpoints below a slack threshold and the trace of their critical paths.
 constexpr int kMaxPaths = 4096;   // paths one report returns at most
+// One path at an endpoint: its end edge and deviations from the critical
+// fan-in, as a chain of records (parent = the same path without its last,
+// highest deviation).
+struct PathRec {
+    float cost;                   // the path's setup slack
+    float dv;                     // its last deviation's cost (0 at a root)
+    int parent;                   // record of the parent path, -1 at a root
+    int p, a;                     // deviation: gate output p at edge rf takes input a at edge rfi
+    int rf, rfi;                  // (root: p = the endpoint, rf = the end edge)
+    int pos, alt;                 // place of the deviation in its parent's region order
+};
 struct PathJob {
     int e0, n;                    // the design's endpoints [e0, e0 + n)
     int corner, k, max_len;       // max_len: pins a path can hold
@@ -95,7 +106,13 @@ struct PathJob {
     float *at;                    // late arrivals
     float *slack;                 // [kMaxPaths] setup slack of each path
     int32_t *endpoint;            // [kMaxPaths] caller pin id of each endpoint
+    // per-endpoint limit above 1 (sta_report_paths_nworst)
+    int per_ep;                   // paths per endpoint at most
+    PathRec *recs;                // [kMaxNworst] paths found, per_ep slots per selected endpoint
+    unsigned long long *pkeys;    // [kMaxNworst] (slack, endpoint order, rank) keys, then sorted
 };
+constexpr int kMaxPerEndpoint = 32, kMaxNworst = 16384;   // per_ep, k * per_ep
+void launch_report_paths_nworst(const DevCtx &c, const HostSched &h, const PathJob &j, cudaStream_t st);
 void launch_report_paths(const DevCtx &c, const HostSched &h, const PathJob &j, cudaStream_t st);
 
 // Device-side resizing (sta_resize_cells).

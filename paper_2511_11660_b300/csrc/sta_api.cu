@@ -972,10 +972,10 @@ sta_status sta_get_endpoint_slack(sta_ctx *c, float *setup, float *hold, uint8_t
     return STA_OK;
 }
 
-sta_status sta_report_paths(sta_ctx *c, int32_t design, int32_t corner, int32_t k, float slack_lt, int32_t *n_paths,
-                            int32_t *n_pins, int32_t *path_ptr, int32_t *path_pin, int8_t *path_rf, float *path_at,
-                            float *path_slack, int32_t *path_endpoint, int32_t pin_capacity, sta_mem mem,
-                            void *stream)
+static sta_status report_paths_impl(sta_ctx *c, int32_t design, int32_t corner, int32_t k, int32_t per_ep,
+                                    float slack_lt, int32_t *n_paths, int32_t *n_pins, int32_t *path_ptr,
+                                    int32_t *path_pin, int8_t *path_rf, float *path_at, float *path_slack,
+                                    int32_t *path_endpoint, int32_t pin_capacity, sta_mem mem, void *stream)
 {
     if (!c || !n_paths || !n_pins) return STA_EINVAL;
     if (!c->updated) return fail(c, STA_ESTATE, "no analysis yet");
@@ -1012,6 +1012,11 @@ sta_status sta_report_paths(sta_ctx *c, int32_t design, int32_t corner, int32_t 
             j.slack = dev_alloc<float>(c, sta::kMaxPaths);
             j.endpoint = dev_alloc<int32_t>(c, sta::kMaxPaths);
         }
+        if (per_ep > 1 && !j.recs) {
+            j.recs = dev_alloc<sta::PathRec>(c, sta::kMaxNworst);
+            j.pkeys = dev_alloc<unsigned long long>(c, sta::kMaxNworst);
+        }
+        j.per_ep = per_ep;
         j.e0 = pl.ep_design_ptr[design];
         j.n = pl.ep_design_ptr[design + 1] - j.e0;
         j.corner = corner;
@@ -1022,7 +1027,8 @@ sta_status sta_report_paths(sta_ctx *c, int32_t design, int32_t corner, int32_t 
         CK(cudaMemsetAsync(j.hist, 0, 256 * sizeof(unsigned), st));
         CK(cudaMemsetAsync(j.count, 0, sizeof(unsigned), st));
         CK(cudaMemsetAsync(j.ptr, 0, sizeof(int32_t), st));
-        if (k > 0) sta::launch_report_paths(c->dc, c->hs, j, st);
+        if (k > 0 && per_ep > 1) sta::launch_report_paths_nworst(c->dc, c->hs, j, st);
+        else if (k > 0) sta::launch_report_paths(c->dc, c->hs, j, st);
         CK(cudaGetLastError());
         unsigned cnt = 0;
         CK(cudaMemcpyAsync(&cnt, j.count, sizeof(unsigned), cudaMemcpyDeviceToHost, st));
@@ -1048,6 +1054,31 @@ sta_status sta_report_paths(sta_ctx *c, int32_t design, int32_t corner, int32_t 
         return from_cuda(c, f);
     }
     return STA_OK;
+}
+
+sta_status sta_report_paths(sta_ctx *c, int32_t design, int32_t corner, int32_t k, float slack_lt, int32_t *n_paths,
+                            int32_t *n_pins, int32_t *path_ptr, int32_t *path_pin, int8_t *path_rf, float *path_at,
+                            float *path_slack, int32_t *path_endpoint, int32_t pin_capacity, sta_mem mem,
+                            void *stream)
+{
+    return report_paths_impl(c, design, corner, k, 1, slack_lt, n_paths, n_pins, path_ptr, path_pin, path_rf, path_at,
+                             path_slack, path_endpoint, pin_capacity, mem, stream);
+}
+
+sta_status sta_report_paths_nworst(sta_ctx *c, int32_t design, int32_t corner, int32_t k, int32_t per_endpoint,
+                                   float slack_lt, int32_t *n_paths, int32_t *n_pins, int32_t *path_ptr,
+                                   int32_t *path_pin, int8_t *path_rf, float *path_at, float *path_slack,
+                                   int32_t *path_endpoint, int32_t pin_capacity, sta_mem mem, void *stream)
+{
+    if (!c) return STA_EINVAL;
+    if (per_endpoint < 1 || per_endpoint > sta::kMaxPerEndpoint)
+        return fail(c, STA_EINVAL, "per_endpoint must be in 1..32");
+    if (per_endpoint > 1 && (int64_t)k * per_endpoint > sta::kMaxNworst)
+        return fail(c, STA_EINVAL, "k * per_endpoint must be at most 16384");
+    if (per_endpoint > 1 && c->plan.Tg > 1)
+        return fail(c, STA_EINVAL, "a per-endpoint limit above 1 needs a design without timing exceptions");
+    return report_paths_impl(c, design, corner, k, per_endpoint, slack_lt, n_paths, n_pins, path_ptr, path_pin,
+                             path_rf, path_at, path_slack, path_endpoint, pin_capacity, mem, stream);
 }
 
 sta_status sta_set_rc(sta_ctx *c, const float *R, const float *Cc, sta_mem mem)

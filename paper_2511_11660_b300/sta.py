@@ -109,6 +109,8 @@ SIGNATURES = {
     "sta_set_rc_async": (C.c_int, [_V, _P, _P, C.c_int, _V]),
     "sta_report_paths": (C.c_int, [_V, C.c_int32, C.c_int32, C.c_int32, C.c_float, _P, _P, _P, _P, _P, _P, _P, _P,
                                    C.c_int32, C.c_int, _V]),
+    "sta_report_paths_nworst": (C.c_int, [_V, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_float, _P, _P, _P, _P,
+                                          _P, _P, _P, _P, C.c_int32, C.c_int, _V]),
     "sta_backward": (C.c_int, [_V, C.c_double, C.c_double, _P, _P, _P, C.c_int, _V]),
     "sta_get_arrays": (C.c_int, [_V, C.POINTER(sta_views)]),
     "sta_stats": (C.c_int, [_V, C.POINTER(sta_plan_info)]),
@@ -362,10 +364,12 @@ class Context:
         self._chk(self.lib.sta_get_pin_state(self.h, which, _ptr(out), _mem_of(out), _stream(stream)))
         return out
 
-    def report_paths(self, k: int, slack_lt: float = float("inf"), corner: int = 0, design: int = 0, stream=None):
+    def report_paths(self, k: int, slack_lt: float = float("inf"), corner: int = 0, design: int = 0, stream=None,
+                     per_endpoint: int = 1):
         """Top-k path report (host arrays): a list of dicts with the endpoint
-        pin, its setup slack and the path's pins, edges and late arrivals from
-        the startpoint to the endpoint."""
+        pin, the path's setup slack and the path's pins, edges and late
+        arrivals from the startpoint to the endpoint.  per_endpoint > 1:
+        sta_report_paths_nworst (up to that many paths per endpoint)."""
         n_paths, n_pins = C.c_int32(0), C.c_int32(0)
         cap = max(1, k) * (2 * self.stats()["n_levels"] + 3)
         ptr = np.zeros(max(1, k) + 1, np.int32)
@@ -374,9 +378,15 @@ class Context:
         at = np.zeros(cap, np.float32)
         slack = np.zeros(max(1, k), np.float32)
         ep = np.zeros(max(1, k), np.int32)
-        self._chk(self.lib.sta_report_paths(self.h, design, corner, k, float(slack_lt), C.byref(n_paths),
-                                            C.byref(n_pins), _ptr(ptr), _ptr(pin), _ptr(rf), _ptr(at), _ptr(slack),
-                                            _ptr(ep), cap, HOST, _stream(stream)))
+        if per_endpoint == 1:
+            self._chk(self.lib.sta_report_paths(self.h, design, corner, k, float(slack_lt), C.byref(n_paths),
+                                                C.byref(n_pins), _ptr(ptr), _ptr(pin), _ptr(rf), _ptr(at),
+                                                _ptr(slack), _ptr(ep), cap, HOST, _stream(stream)))
+        else:
+            self._chk(self.lib.sta_report_paths_nworst(self.h, design, corner, k, int(per_endpoint), float(slack_lt),
+                                                       C.byref(n_paths), C.byref(n_pins), _ptr(ptr), _ptr(pin),
+                                                       _ptr(rf), _ptr(at), _ptr(slack), _ptr(ep), cap, HOST,
+                                                       _stream(stream)))
         out = []
         for i in range(n_paths.value):
             b, e = ptr[i], ptr[i + 1]

@@ -198,3 +198,143 @@ def test_paths_full_size():
     ctx.update_timing()
     check_paths(d, ctx.report_paths(200), res, 200)
     ctx.close()
+
+
+# ------------------------------------------- per-endpoint limit above 1
+
+def check_nworst(d, gpu, want, L, res, corner=0):
+    """The report with a per-endpoint limit against the oracle's: the path
+    slacks, in order, agree within tolerance (near-ties may swap which of two
+    equally critical paths is reported, never the slack at a rank); every GPU
+    path is a chain of timing arcs with consistent edges from a startpoint to
+    its endpoint, distinct from the others, at most L per endpoint, and its
+    arrivals and slack are its own FP64 prefix sums under the oracle's
+    analysis (cell arc delays at the analysis' slews and loads)."""
+    net = _indep.Net(d, corner)
+    role = np.asarray(d["pin_role"])
+    K = int(d.get("n_corners", 1))
+    sc = float(np.asarray(d["lut_scale"] if d.get("lut_scale") is not None else np.ones(K))[corner])
+    i1 = np.asarray(d["lut_idx1"]).reshape(-1, 3, 4, 7)
+    i2 = np.asarray(d["lut_idx2"]).reshape(-1, 3, 4, 7)
+    vv = np.asarray(d["lut_val"]).reshape(-1, 3, 4, 49)
+    sense = np.asarray(d["arc_sense"]).reshape(-1, 3)
+    assert len(gpu) == len(want)
+    gs = np.array([p["slack"] for p in gpu])
+    ws = np.array([p["slack"] for p in want])
+    assert np.all(np.diff(gs) >= 0)
+    assert np.all(np.abs(gs - ws) <= ABS_TOL + REL_TOL * np.abs(ws)), np.abs(gs - ws).max()
+    seen, per_ep = set(), {}
+    for p in gpu:
+        pins, rfs, ats = p["pins"], p["rf"], p["at"]
+        key = (tuple(pins.tolist()), tuple(rfs.tolist()))
+        assert key not in seen
+        seen.add(key)
+        per_ep[p["endpoint"]] = per_ep.get(p["endpoint"], 0) + 1
+        assert pins[-1] == p["endpoint"]
+        assert role[pins[0]] in (synth.PI, synth.CK)
+        arr = float(res["at"][pins[0], corner, 2 + rfs[0]])
+        assert abs(ats[0] - arr) <= tol(arr)
+        for i in range(1, len(pins)):
+            u, ru, v, rv = int(pins[i - 1]), int(rfs[i - 1]), int(pins[i]), int(rfs[i])
+            if net.driver.get(v) == u:
+                assert ru == rv
+                arr += net.Dns[v]
+            else:
+                c = net.cell_of[v]
+                assert c >= 0 and net.cell_of[u] == c
+                t = d["cell_type"][c]
+                j = net.slot_of[u]
+                if role[v] == synth.Q:
+                    assert ru == 0 and sense[t, j] == _indep.RISE
+                else:
+                    assert ru in _indep.rf_in_of(sense[t, j], rv)
+                dl = oracle.lut_eval(i1[t, j, rv], i2[t, j, rv], vv[t, j, rv], res["slew"][u, corner, 2 + ru],
+                                     net.load[v])[0]
+                arr += sc * dl
+            assert abs(ats[i] - arr) <= tol(arr), (i, ats[i], arr)
+        ref = float(res["rat"][pins[-1], corner, 2 + rfs[-1]]) - arr
+        assert abs(p["slack"] - ref) <= tol(ref)
+    assert max(per_ep.values(), default=0) <= L
+
+
+@pytest.mark.parametrize("case", ["tiny", "corners", "threshold"])
+def test_nworst_paths_match_oracle(case):
+    corner, slack_lt = 0, np.inf
+    if case == "corners":
+        ls, rs = synth.lut_corners()
+        d = synth.make_design(3000, 20, seed=4, n_corners=4, lut_scale=ls, rc_scale=rs, period_ns=1.7)
+        corner = 3
+    else:
+        d = synth.workload("tiny", seed=1)
+        d["period_ns"], _ = tune_period(d)
+        if case == "threshold":
+            slack_lt = -0.05
+    res = oracle.sta(d)
+    ctx = sta.Context(d)
+    ctx.update_timing()
+    for k, L in ((1, 2), (40, 5), (300, 3), (64, 32)):
+        gpu = ctx.report_paths(k, slack_lt=slack_lt, corner=corner, per_endpoint=L)
+        want = oracle.report_paths_nworst(d, k, L, slack_lt=slack_lt, corner=corner, res=res)
+        check_nworst(d, gpu, want, L, res, corner)
+        assert len(gpu) > 0
+    # more paths than endpoints at the limit: some endpoint holds several
+    gpu = ctx.report_paths(100, per_endpoint=8, corner=corner, slack_lt=slack_lt)
+    assert len({p["endpoint"] for p in gpu}) < len(gpu)
+    ctx.close()
+
+
+def test_nworst_limit_one_and_errors():
+    d = synth.workload("tiny", seed=2)
+    d["period_ns"], _ = tune_period(d)
+    ctx = sta.Context(d)
+    ctx.update_timing()
+    a = ctx.report_paths(50)
+    b = ctx.report_paths(50, per_endpoint=1)
+    assert [p["endpoint"] for p in a] == [p["endpoint"] for p in b]
+    assert ctx.report_paths(0, per_endpoint=4) == []
+    assert ctx.report_paths(20, per_endpoint=4, slack_lt=-1e6) == []
+    for k, L in ((10, 0), (10, 33), (4096, 5)):
+        with pytest.raises(sta.StaError) as ei:
+            ctx.report_paths(k, per_endpoint=L)
+        assert ei.value.status == sta.EINVAL
+    ctx.close()
+    dx = dict(d, **synth.exception_groups(d, np.random.default_rng(0), 2))
+    ctx = sta.Context(dx)
+    ctx.update_timing()
+    with pytest.raises(sta.StaError) as ei:
+        ctx.report_paths(10, per_endpoint=2)
+    assert ei.value.status == sta.EINVAL
+    assert len(ctx.report_paths(10, per_endpoint=1)) == 10
+    ctx.close()
+
+
+def test_nworst_batch_design_equals_separate_context():
+    ds = synth.batch_workload(seed=1, n_designs=3, lo=800, hi=3000, depth=12)
+    b = sta.Context(None, batch=ds)
+    b.update_timing()
+    off = 0
+    for i, d in enumerate(ds):
+        c = sta.Context(d)
+        c.update_timing()
+        want = c.report_paths(60, corner=1, per_endpoint=4)
+        got = b.report_paths(60, corner=1, design=i, per_endpoint=4)
+        assert len(got) == len(want)
+        for g, w in zip(got, want):
+            assert g["endpoint"] == w["endpoint"] + off
+            np.testing.assert_array_equal(g["pins"], w["pins"] + off)
+            np.testing.assert_array_equal(g["at"], w["at"])
+        c.close()
+        off += d["n_pins"]
+    b.close()
+
+
+def test_nworst_paths_full_size():
+    """The 1M-cell workload: the 100 worst paths, up to 4 per endpoint."""
+    d = synth.workload("scale", seed=0)
+    d["period_ns"], _ = tune_period(d)
+    res = oracle.sta(d)
+    ctx = sta.Context(d)
+    ctx.update_timing()
+    gpu = ctx.report_paths(100, per_endpoint=4)
+    check_nworst(d, gpu, oracle.report_paths_nworst(d, 100, 4, res=res), 4, res)
+    ctx.close()

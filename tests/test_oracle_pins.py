@@ -1299,3 +1299,67 @@ def test_steiner_adjoint_matches_central_differences(ry):
     # a cell may straddle a table breakpoint inside +-h: allow one
     assert bad <= 1, (bad, checked)
     assert scale > 0
+
+
+# --------------------------------------- N4 top-k paths, per-endpoint limit
+
+@pytest.mark.parametrize("seed", range(4))
+def test_nworst_paths_match_brute_force_fixed_delay(seed):
+    """With slew-independent delays the report with a per-endpoint limit L is
+    fixed by exhaustive enumeration: per endpoint, every path's slack
+    (required time of its end edge - its arrival), the L smallest of each of
+    the k worst endpoints, merged by (slack, endpoint order, rank), the first
+    k.  Every reported path is made of timing arcs, distinct from the others,
+    its arrivals are its own prefix sums and its slack is required - arrival."""
+    d = _fixed_design(seed, n_cells=14, depth=5)
+    d["period_ns"] = 0.3
+    res = oracle.sta(d)
+    allp = _indep.enumerate_paths(d)
+    net = _indep.Net(d)
+    eps, es = res["endpoints"], res["ep_setup"][:, 0]
+    for k, L in ((50, 3), (12, 8), (40, 1), (5, 30)):
+        paths = oracle.report_paths_nworst(d, k, L, res=res)
+        order = sorted(range(len(eps)), key=lambda e: (es[e], e))[:k]
+        want = []
+        for oi, e in enumerate(order):
+            p = int(eps[e])
+            sl = sorted(res["rat"][p, 0, 2 + rf] - a for a, _, rf in allp[p])
+            want += [(s, oi, r, p) for r, s in enumerate(sl[:L])]
+        want.sort()
+        want = want[:k]
+        assert len(paths) == len(want)
+        for pth, (s, _, _, p) in zip(paths, want):
+            assert pth["slack"] == pytest.approx(s, abs=1e-12)
+            assert pth["endpoint"] == p
+        seen = set()
+        for pth in paths:
+            pins, rfs, at = pth["pins"], pth["rf"], pth["at"]
+            key = (tuple(pins.tolist()), tuple(rfs.tolist()))
+            assert key not in seen
+            seen.add(key)
+            assert pins[-1] == pth["endpoint"]
+            assert np.asarray(d["pin_role"])[pins[0]] in (synth.PI, synth.CK)
+            for (u, ru), (v, rv) in zip(zip(pins[:-1], rfs[:-1]), zip(pins[1:], rfs[1:])):
+                assert _arc_ok(d, net, int(u), int(ru), int(v), int(rv)), (u, v)
+            for i in range(1, len(pins)):
+                v, u = int(pins[i]), int(pins[i - 1])
+                if net.driver.get(v) == u:
+                    assert at[i] == pytest.approx(at[i - 1] + net.Dns[v], abs=1e-12)
+                else:
+                    assert at[i] >= at[i - 1]
+            assert any(abs(a - at[-1]) < 1e-12 and rf == rfs[-1] for a, _, rf in allp[int(pins[-1])])
+            e = int(pins[-1])
+            assert pth["slack"] == pytest.approx(res["rat"][e, 0, 2 + rfs[-1]] - at[-1], abs=1e-12)
+
+
+def test_nworst_limit_one_is_the_plain_report():
+    d = synth.make_design(800, 12, seed=3, period_ns=0.9)
+    res = oracle.sta(d)
+    for k, thr in ((10, np.inf), (60, 0.0)):
+        a = oracle.report_paths(d, k, slack_lt=thr, res=res)
+        b = oracle.report_paths_nworst(d, k, 1, slack_lt=thr, res=res)
+        assert [p["endpoint"] for p in a] == [p["endpoint"] for p in b]
+        for x, y in zip(a, b):
+            np.testing.assert_array_equal(x["pins"], y["pins"])
+            np.testing.assert_allclose(x["at"], y["at"], atol=1e-12)
+            assert x["slack"] == pytest.approx(y["slack"], abs=1e-12)
