@@ -28,15 +28,19 @@
  *       calculator, Sec. III "Delay models"): sink delay = 50% crossing of
  *       the step response of an order-q congruence-projected model of the
  *       RC tree; the slew law of O3 is kept;
- *   O8  timing exceptions (Sec. III names an SDC exceptions manager; the
- *       reading is SDC's set_false_path / set_multicycle_path -setup with
- *       -from startpoints and -to endpoints): every path carries the tag of
- *       its startpoint's group (0 = none); arrivals and required times are
- *       propagated per tag (slews are tag-free); an endpoint checks tag g
- *       with group g's action when it is in the group's endpoint list (or
- *       the list is empty) -- false path: no check; multicycle M: setup
- *       capture edge at M * T, hold unchanged -- and the default check
- *       otherwise; endpoint slack = min over tags.  With -through, a group
+ *   O8  timing exceptions (Sec. III names an SDC exceptions manager, Sec.
+ *       IV-B lists false and multicycle paths and min/max delays; the
+ *       reading is SDC's set_false_path / set_multicycle_path -setup /
+ *       set_max_delay / set_min_delay with -from startpoints and -to
+ *       endpoints): every path carries the tag of its startpoint's group
+ *       (0 = none); arrivals and required times are propagated per tag
+ *       (slews are tag-free); an endpoint checks tag g with group g's action
+ *       when it is in the group's endpoint list (or the list is empty) --
+ *       false path: no check; multicycle M: setup capture edge at M * T,
+ *       hold unchanged; max delay V: setup capture edge at V (the library
+ *       setup time still applies at a flip-flop), hold unchanged; min delay
+ *       V: hold edge at V (plus the hold time), setup unchanged -- and the
+ *       default check otherwise; endpoint slack = min over tags.  With -through, a group
  *       has ordered through sets of gate input pins and one tag per stage:
  *       a path of the group moves to the next stage at a pin of the next
  *       set, and only a path through every set gets the group's action;
@@ -1160,7 +1164,8 @@ int orc_sta(const orc_design *d, double *at, double *slew, double *rat, double *
             const int32_t p = d->exc_to[i];
             if (p < 0 || p >= P || (d->pin_role[p] != R_D && d->pin_role[p] != R_PO)) { rc = ERR_INVAL; goto done; }
         }
-        if (d->exc_action[g] != 0 && !(d->exc_action[g] == 1 && d->exc_mult[g] >= 1.0f)) { rc = ERR_INVAL; goto done; }
+        if (d->exc_action[g] < 0 || d->exc_action[g] > 3 || !isfinite(d->exc_mult[g]) ||
+            (d->exc_action[g] == 1 && d->exc_mult[g] < 1.0f)) { rc = ERR_INVAL; goto done; }
         /* through set j + 1 of group g: tag base[g] + j moves on at its pins */
         for (int32_t j = 0; j < nthru[g]; ++j) {
             const int32_t s = d->exc_thru_ptr[g] + j;
@@ -1206,9 +1211,15 @@ int orc_sta(const orc_design *d, double *at, double *slew, double *rat, double *
                         if (d->exc_action[grp] == 0) {
                             late = INFINITY;   /* false path: no check */
                             early = -INFINITY;
-                        } else {
+                        } else if (d->exc_action[grp] == 1) {
                             const double M = d->exc_mult[grp];   /* multicycle: capture at M * T */
                             late = r == R_D ? M * T - d->setup_ns : M * T;
+                        } else if (d->exc_action[grp] == 2) {
+                            const double V = d->exc_mult[grp];   /* max delay: capture at V */
+                            late = r == R_D ? V - d->setup_ns : V;
+                        } else {
+                            const double V = d->exc_mult[grp];   /* min delay: hold edge at V */
+                            early = r == R_D ? V + d->hold_ns : V;
                         }
                     }
                     ep_req[2 * (size_t)p] = late;

@@ -316,14 +316,18 @@ def make_design(n_cells: int, depth: int, seed: int = 0, lib: dict | None = None
 
 
 def exception_groups(d: dict, rng, n_groups: int, div_from: int = 3, div_to: int = 2, max_thru: int = 0,
-                     div_thru: int = 8) -> dict:
+                     div_thru: int = 8, actions=None) -> dict:
     """Random timing-exception groups for design ``d``: each group takes a
     random 1/div_from of the startpoints (PI and CK pins) and, with probability
     0.7, a random 1/div_to of the endpoints (D and PO pins; otherwise an empty
     list, i.e. every endpoint); its action is a false path or a multicycle
     with M in {2, 3}.  With max_thru > 0 each group also gets 0..max_thru
     ordered through sets, each a random 1/div_thru of the gate input pins.
-    Returned as the design keys exc_*."""
+    With ``actions`` (a tuple of codes) each group draws its action from it
+    instead: 0 false path, 1 multicycle (M in {2, 3}), 2 max delay (a value
+    uniform in [0.5, 1.5] periods), 3 min delay (uniform in [0, 0.3]
+    periods; the period is d["period_ns"], else 1 ns).  Returned as the
+    design keys exc_*."""
     role = np.asarray(d["pin_role"])
     starts = np.nonzero((role == PI) | (role == CK))[0]
     ends = np.nonzero((role == D) | (role == PO))[0]
@@ -340,8 +344,16 @@ def exception_groups(d: dict, rng, n_groups: int, div_from: int = 3, div_to: int
         if rng.random() < 0.7:
             to += list(rng.choice(ends, size=max(1, len(ends) // div_to), replace=False))
         tp.append(len(to))
-        act.append(int(rng.random() < 0.5))
-        mult.append(float(rng.integers(2, 4)))
+        if actions is None:
+            act.append(int(rng.random() < 0.5))
+            mult.append(float(rng.integers(2, 4)))
+        else:
+            a = int(actions[int(rng.integers(0, len(actions)))])
+            T = float(d.get("period_ns", 1.0))
+            act.append(a)
+            mult.append(float(rng.integers(2, 4)) if a == 1 else
+                        T * float(rng.uniform(0.5, 1.5)) if a == 2 else T * float(rng.uniform(0.0, 0.3)) if a == 3
+                        else 1.0)
     out = dict(exc_from_ptr=np.array(fp, np.int32), exc_from=np.array(fr, np.int32),
                exc_to_ptr=np.array(tp, np.int32), exc_to=np.array(to, np.int32),
                exc_action=np.array(act, np.int32), exc_mult=np.array(mult, np.float32))

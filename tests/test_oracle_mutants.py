@@ -106,6 +106,9 @@ MUTANTS = [
     ("steiner_ry_uses_rx", "R[i] = f * (rx * lx + ry * ly);", "R[i] = f * (rx * lx + rx * ly);", 0),
     ("steiner_no_parent_half_cap", "C[par[i]] += 0.5 * cw;", "C[par[i]] += 0.0 * cw;", 0),
     ("steiner_no_scale", "double cw = f * (cx * lx + cy * ly);", "double cw = (cx * lx + cy * ly);", 0),
+    ("exc_maxdelay_no_setup", "late = r == R_D ? V - d->setup_ns : V;", "late = V;", 0),
+    ("exc_mindelay_no_hold", "early = r == R_D ? V + d->hold_ns : V;", "early = V;", 0),
+    ("exc_maxdelay_as_multicycle", "late = r == R_D ? V - d->setup_ns : V;", "late = r == R_D ? V * T - d->setup_ns : V * T;", 0),
     # O6 on Steiner trees: the RC-tree adjoint and the tree-held-fixed chain to positions
     ("rcadj_no_var_D", "db[i] = Dbar[i] - 2.0 * D[i] * Vbar[i] + mb[i] * C[i];", "db[i] = Dbar[i] + mb[i] * C[i];", 0),
     ("rcadj_beta_factor", "bb[i] = 2.0 * Vbar[i];", "bb[i] = Vbar[i];", 0),

@@ -705,18 +705,20 @@ def test_paths_order_threshold_and_count():
 
 # ------------------------------------------------------- O8 timing exceptions
 
-@pytest.mark.parametrize("seed", range(5))
-def test_exceptions_brute_force_fixed_delay(seed):
+@pytest.mark.parametrize("seed,actions", [(0, None), (1, None), (2, None), (3, None), (4, None),
+                                          (5, (0, 1, 2, 3)), (6, (2, 3)), (7, (1, 2, 3))])
+def test_exceptions_brute_force_fixed_delay(seed, actions):
     """Every path tagged by its startpoint's first group: an endpoint's setup
     slack is the minimum over the paths ending there of (requirement -
     arrival) and its hold slack the minimum of (arrival - requirement), with
     the tag's requirement -- the group's action when the endpoint is in its
     list (or the list is empty): false path removes the check, multicycle M
-    moves the setup capture edge to M * T -- and the default otherwise."""
+    moves the setup capture edge to M * T, max delay V moves it to V, min
+    delay V moves the hold edge to V -- and the default otherwise."""
     rng = np.random.default_rng(seed)
     d = _fixed_design(seed, n_cells=14, depth=5)
     d["period_ns"] = 0.35
-    d.update(synth.exception_groups(d, rng, 3))
+    d.update(synth.exception_groups(d, rng, 3, actions=actions))
     res = oracle.sta(d)
     role = np.asarray(d["pin_role"])
     first = {}
@@ -734,11 +736,15 @@ def test_exceptions_brute_force_fixed_delay(seed):
             if g is not None:
                 lst = d["exc_to"][d["exc_to_ptr"][g]:d["exc_to_ptr"][g + 1]]
                 if len(lst) == 0 or p in lst:
-                    if d["exc_action"][g] == 0:
+                    act, v = d["exc_action"][g], float(d["exc_mult"][g])
+                    if act == 0:
                         late, early = np.inf, -np.inf
+                    elif act == 1:
+                        late = v * T - d["setup_ns"] if role[p] == synth.D else v * T
+                    elif act == 2:
+                        late = v - d["setup_ns"] if role[p] == synth.D else v
                     else:
-                        M = float(d["exc_mult"][g])
-                        late = M * T - d["setup_ns"] if role[p] == synth.D else M * T
+                        early = v + d["hold_ns"] if role[p] == synth.D else v
             setup = min(setup, late - a)
             hold = min(hold, a - early)
         assert res["ep_setup"][e, 0] == pytest.approx(setup, abs=1e-12), (e, p)
@@ -762,6 +768,14 @@ def test_exceptions_all_false_and_all_multicycle():
     r = oracle.sta(dict(d, exc_action=np.array([1], np.int32), exc_mult=np.array([3], np.float32), **grp))
     np.testing.assert_allclose(r["ep_setup"], base["ep_setup"] + 2 * d["period_ns"], rtol=0, atol=1e-12)
     np.testing.assert_array_equal(r["ep_hold"], base["ep_hold"])
+    # every startpoint in one max-delay-V group: setup slacks move by V - T; one min-delay-V group: hold by -V
+    V = np.float32(0.45)
+    r = oracle.sta(dict(d, exc_action=np.array([2], np.int32), exc_mult=np.array([V], np.float32), **grp))
+    np.testing.assert_allclose(r["ep_setup"], base["ep_setup"] + float(V) - d["period_ns"], rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(r["ep_hold"], base["ep_hold"])
+    r = oracle.sta(dict(d, exc_action=np.array([3], np.int32), exc_mult=np.array([V], np.float32), **grp))
+    np.testing.assert_allclose(r["ep_hold"], base["ep_hold"] - float(V), rtol=0, atol=1e-12)
+    np.testing.assert_array_equal(r["ep_setup"], base["ep_setup"])
 
 
 @pytest.mark.parametrize("seed,max_thru", [(0, 0), (1, 0), (2, 0), (3, 2), (4, 2)])
