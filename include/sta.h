@@ -164,18 +164,24 @@ typedef struct {
     float gamma_ns;
     int32_t net_model;      /* STA_NET_ELMORE (0) or STA_NET_ARNOLDI (1) */
     int32_t arnoldi_order;  /* q of STA_NET_ARNOLDI: 1..3, 0 = 3 */
-    /* Timing exceptions (Sec. III: an SDC exceptions manager; this is the
-     * reading of set_false_path / set_multicycle_path -setup with -from
-     * startpoints and -to endpoints).  Group g (0 <= g < n_exc <= 7):
+    /* Timing exceptions (Sec. III: an SDC exceptions manager; Sec. IV-B
+     * lists false and multicycle paths and min/max delays; this is the
+     * reading of set_false_path / set_multicycle_path -setup /
+     * set_max_delay / set_min_delay with -from startpoints and -to
+     * endpoints).  Group g (0 <= g < n_exc <= 7):
      * startpoint pins exc_from[exc_from_ptr[g] .. exc_from_ptr[g+1]) (PI or
      * CK), endpoint pins exc_to[exc_to_ptr[g] .. exc_to_ptr[g+1]) (D or PO;
      * an empty list means every endpoint), exc_action[g] (0 false path, 1
-     * multicycle) and exc_mult[g] (the setup multiplier M >= 1).  Every path
-     * carries the tag of its startpoint's first group (0 = none); arrivals
-     * and required times are propagated per (corner, tag) state, slews are
-     * tag-free; endpoint e checks tag g with g's action when it is in g's
-     * list -- false path: no check; multicycle: setup capture edge at M * T,
-     * hold unchanged -- and the default check otherwise.  Endpoint slacks,
+     * multicycle, 2 max delay, 3 min delay) and exc_mult[g] (multicycle:
+     * the setup multiplier M >= 1; max/min delay: the value V in ns).  Every
+     * path carries the tag of its startpoint's first group (0 = none);
+     * arrivals and required times are propagated per (corner, tag) state,
+     * slews are tag-free; endpoint e checks tag g with g's action when it is
+     * in g's list -- false path: no check; multicycle: setup capture edge at
+     * M * T, hold unchanged; max delay: setup capture edge at V (a
+     * flip-flop's setup time still applies), hold unchanged; min delay: hold
+     * edge at V (plus a flip-flop's hold time), setup unchanged -- and the
+     * default check otherwise.  Endpoint slacks,
      * WNS and TNS take the min over tags; per-pin arrays (sta_get_pin_state)
      * hold n_corners * (n_exc + 1) states, state = corner * (n_exc + 1) +
      * tag.  Not with gamma_ns > 0 or in a batch.  n_exc = 0: none.

@@ -89,6 +89,7 @@ struct DevCtx {
     int32_t Kc, Tg;                             // corners and exception tags: K = Kc * Tg states, k = corner * Tg + tag
     const int32_t *item_tag;                    // [I] tag of a startpoint item (Tg > 1)
     const float *ep_mult;                       // [E][Tg] setup multiplier per endpoint and tag, 0 = no check (Tg > 1)
+    const float2 *ep_off;                       // [E][Tg] late requirement offset, early requirement (Tg > 1)
     const uint32_t *pin_adv;                    // [P] bit t: tag t moves on to t + 1 at this gate input (-through; or NULL)
     int64_t NN;                                 // RC nodes
     int32_t F;                                  // net sinks (fan-out entries)

@@ -532,12 +532,17 @@ __device__ __forceinline__ void ep_run(const DevCtx &c, const EpItem &x, DF at0,
     const int base = threadIdx.x & 28;   // first lane of the quad
     const int kq = corner_lane(c);
     for (int k = kq; k < K; k += c.KL) {
-        // requirement of state k: the exception tag's multiplier M (1 = the
-        // default check, 0 = no check) -- setup capture edge at M * T
-        const float M = c.Tg > 1 ? c.ep_mult[(size_t)e * c.Tg + k % c.Tg] : 1.f;
-        const DF req = M == 0.f ? DF(q >= 2 ? INFINITY : -INFINITY)
-                                : (q >= 2 ? (x.isD ? df_mul(M, c.period) - c.setup : df_mul(M, c.period))
-                                          : DF(x.isD ? c.hold : 0.f));
+        // requirement of state k: late = M T + off.x (M = 0: off.x alone),
+        // early = off.y, from the exception tag's action (false path: no
+        // check; multicycle: M; max delay: M = 0, off.x = V - setup; min
+        // delay: off.y = V + hold); the default check without exceptions
+        float M = 1.f;
+        float2 off = make_float2(x.isD ? -c.setup : 0.f, x.isD ? c.hold : 0.f);
+        if (c.Tg > 1) {
+            M = c.ep_mult[(size_t)e * c.Tg + k % c.Tg];
+            off = c.ep_off[(size_t)e * c.Tg + k % c.Tg];
+        }
+        const DF req = q >= 2 ? (M == 0.f ? DF(off.x) : df_mul(M, c.period) + off.x) : DF(off.y);
         DF ad;
         float sd;
         if (!WAIT) {

@@ -502,6 +502,7 @@ void build(const sta_design_desc *d, Plan &pl)
     // pin's first group) and the setup multiplier of every (endpoint, tag)
     pl.item_tag.clear();
     pl.ep_mult.clear();
+    pl.ep_off.clear();
     pl.pin_adv.clear();
     if (pl.Tg > 1) {
         const int32_t G = d->n_exc;
@@ -528,8 +529,11 @@ void build(const sta_design_desc *d, Plan &pl)
                 REQUIRE(p >= 0 && p < P && (d->pin_role[p] == kPinD || d->pin_role[p] == kPinPO), STA_EINVAL,
                         "exception group %d: endpoint %d is not a D or PO pin", g, p);
             }
-            REQUIRE(d->exc_action[g] == 0 || (d->exc_action[g] == 1 && finite(d->exc_mult[g]) && d->exc_mult[g] >= 1.f),
-                    STA_EINVAL, "exception group %d: action must be 0 (false path) or 1 (multicycle, M >= 1)", g);
+            REQUIRE(d->exc_action[g] >= 0 && d->exc_action[g] <= 3 && finite(d->exc_mult[g]) &&
+                        (d->exc_action[g] != 1 || d->exc_mult[g] >= 1.f),
+                    STA_EINVAL,
+                    "exception group %d: action must be 0 (false path), 1 (multicycle, M >= 1), 2 (max delay) or "
+                    "3 (min delay) with a finite value", g);
             // through set j + 1: the group's tag base + j moves on to base + j + 1 at its pins
             for (int32_t j = 0; j < nthru[g]; ++j) {
                 const int32_t s = d->exc_thru_ptr[g] + j;
@@ -550,14 +554,42 @@ void build(const sta_design_desc *d, Plan &pl)
             if (t < 0) pl.item_tag[g] = tag_of[caller_of[pl.item_pin0[g]]];
             else if (pl.type_kind[t] == 1) pl.item_tag[g] = tag_of[d->cell_pin[d->cell_pin_ptr[pl.item_cell[g]] + 1]];
         }
+        // requirement of (endpoint, tag): late = mult * T + off[0] (mult = 0: off[0] alone), early = off[1];
+        // default: flip-flop D T - setup and hold, output port T and 0
         pl.ep_mult.assign((size_t)pl.E * pl.Tg, 1.f);
+        pl.ep_off.assign((size_t)pl.E * pl.Tg * 2, 0.f);
+        for (int32_t e = 0; e < pl.E; ++e)
+            for (int32_t t = 0; t < pl.Tg; ++t) {
+                pl.ep_off[((size_t)e * pl.Tg + t) * 2] = pl.ep_is_d[e] ? -pl.setup : 0.f;
+                pl.ep_off[((size_t)e * pl.Tg + t) * 2 + 1] = pl.ep_is_d[e] ? pl.hold : 0.f;
+            }
         std::vector<uint8_t> in_to(P, 0);
         for (int32_t g = 0; g < G; ++g) {
             const bool all = d->exc_to_ptr[g] == d->exc_to_ptr[g + 1];
+            const double v = d->exc_mult[g];
             for (int32_t i = d->exc_to_ptr[g]; i < d->exc_to_ptr[g + 1]; ++i) in_to[d->exc_to[i]] = 1;
-            for (int32_t e = 0; e < pl.E; ++e)   // the fully matched tag gets the action
-                if (all || in_to[caller_of[pl.ep_pin[e]]])
-                    pl.ep_mult[(size_t)e * pl.Tg + base[g] + nthru[g]] = d->exc_action[g] == 0 ? 0.f : d->exc_mult[g];
+            for (int32_t e = 0; e < pl.E; ++e) {   // the fully matched tag gets the action
+                if (!all && !in_to[caller_of[pl.ep_pin[e]]]) continue;
+                const size_t x = (size_t)e * pl.Tg + base[g] + nthru[g];
+                const bool isd = pl.ep_is_d[e];
+                switch (d->exc_action[g]) {
+                case 0:   // false path: no check
+                    pl.ep_mult[x] = 0.f;
+                    pl.ep_off[2 * x] = INFINITY;
+                    pl.ep_off[2 * x + 1] = -INFINITY;
+                    break;
+                case 1:   // multicycle: setup capture edge at M * T
+                    pl.ep_mult[x] = (float)v;
+                    break;
+                case 2:   // max delay: setup capture edge at v
+                    pl.ep_mult[x] = 0.f;
+                    pl.ep_off[2 * x] = (float)(isd ? v - pl.setup : v);
+                    break;
+                default:  // min delay: hold edge at v
+                    pl.ep_off[2 * x + 1] = (float)(isd ? v + pl.hold : v);
+                    break;
+                }
+            }
             for (int32_t i = d->exc_to_ptr[g]; i < d->exc_to_ptr[g + 1]; ++i) in_to[d->exc_to[i]] = 0;
         }
     }

@@ -48,6 +48,7 @@ struct Plan {
     int32_t Kc = 1, Tg = 1;                  // corners and exception tags; K = Kc * Tg states
     std::vector<int32_t> item_tag;           // [I] exception tag of a startpoint item (PI, flip-flop), else 0
     std::vector<float> ep_mult;              // [E][Tg] setup multiplier of each endpoint and tag, 0 = no check
+    std::vector<float> ep_off;               // [E][Tg][2] late requirement offset and early requirement (ns)
     std::vector<uint32_t> pin_adv;           // [P] bit t: tag t moves on to t + 1 at this gate input (empty: no -through)
     int32_t arnoldi_q = 3;                   // order of STA_NET_ARNOLDI
     // constraints

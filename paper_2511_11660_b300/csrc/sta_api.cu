@@ -214,6 +214,7 @@ sta_status create_from_plan(sta_ctx *c, int device)
     if (pl.Tg > 1) {
         d.item_tag = upload(c, pl.item_tag);
         d.ep_mult = upload(c, pl.ep_mult);
+        d.ep_off = reinterpret_cast<const float2 *>(upload(c, pl.ep_off));
         d.pin_adv = pl.pin_adv.empty() ? nullptr : upload(c, pl.pin_adv);
     }
     {

@@ -1,6 +1,6 @@
-"""GPU timing exceptions (false paths and multicycle paths by startpoint group,
-ordered -through sets of gate inputs and endpoint list) against the FP64
-oracle.
+"""GPU timing exceptions (false paths, multicycle paths and max/min delays by
+startpoint group, ordered -through sets of gate inputs and endpoint list)
+against the FP64 oracle.
 
 Every per-pin array holds one state per (corner, exception tag) and is
 compared element by element (infinities equal: an absent tag's arrival is
@@ -28,7 +28,7 @@ def _lib():
     sta.load()
 
 
-def _design(case, seed, n_groups, max_thru=0):
+def _design(case, seed, n_groups, max_thru=0, actions=None):
     rng = np.random.default_rng(100 + seed)
     if case == "corners":
         ls, rs = synth.lut_corners()
@@ -39,7 +39,7 @@ def _design(case, seed, n_groups, max_thru=0):
     else:
         d = synth.workload("tiny", seed=seed)
         d["period_ns"], _ = tune_period(d)
-    d.update(synth.exception_groups(d, rng, n_groups, max_thru=max_thru))
+    d.update(synth.exception_groups(d, rng, n_groups, max_thru=max_thru, actions=actions))
     return d
 
 
@@ -75,12 +75,17 @@ def check(d, g, ref):
             1e-5 * abs(ref["tns_hold"][k])
 
 
-@pytest.mark.parametrize("case,seed,n_groups,max_thru", [("tiny", 0, 1, 0), ("tiny", 1, 3, 0), ("tiny", 2, 7, 0),
-                                                         ("corners", 4, 3, 0), ("placed", 5, 2, 0),
-                                                         ("tiny", 6, 3, 2), ("tiny", 7, 5, 3),
-                                                         ("corners", 8, 2, 2)])
-def test_exceptions_parity_all_schedules(case, seed, n_groups, max_thru):
-    d = _design(case, seed, n_groups, max_thru)
+ALL_ACTIONS = (0, 1, 2, 3)   # false path, multicycle, max delay, min delay
+
+
+@pytest.mark.parametrize("case,seed,n_groups,max_thru,actions",
+                         [("tiny", 0, 1, 0, None), ("tiny", 1, 3, 0, None), ("tiny", 2, 7, 0, None),
+                          ("corners", 4, 3, 0, None), ("placed", 5, 2, 0, None),
+                          ("tiny", 6, 3, 2, None), ("tiny", 7, 5, 3, None),
+                          ("corners", 8, 2, 2, None), ("tiny", 9, 6, 0, ALL_ACTIONS),
+                          ("corners", 10, 4, 1, ALL_ACTIONS), ("tiny", 11, 4, 2, (2, 3))])
+def test_exceptions_parity_all_schedules(case, seed, n_groups, max_thru, actions):
+    d = _design(case, seed, n_groups, max_thru, actions)
     ref = oracle.sta(d)
     # the groups must change something: some endpoint's slack differs from the unconstrained analysis
     plain = {k: v for k, v in d.items() if not k.startswith("exc_")}
@@ -145,14 +150,15 @@ def test_exceptions_paths(case, seed, n_groups, corner, max_thru):
     ctx.close()
 
 
-@pytest.mark.parametrize("max_thru", [0, 2])
-def test_exceptions_full_size(max_thru):
+@pytest.mark.parametrize("max_thru,actions", [(0, None), (2, None), (0, ALL_ACTIONS)])
+def test_exceptions_full_size(max_thru, actions):
     """The 1M-cell workload with three exception groups (four tags; with
-    through sets of 1/64 of the gate inputs, up to ten)."""
+    through sets of 1/64 of the gate inputs, up to ten), also with max/min
+    delay actions."""
     d = synth.workload("scale", seed=0)
     d["period_ns"], _ = tune_period(d)
     d.update(synth.exception_groups(d, np.random.default_rng(9), 3, div_from=5, div_to=4, max_thru=max_thru,
-                                    div_thru=64))
+                                    div_thru=64, actions=actions))
     ref = oracle.sta(d)
     ctx = sta.Context(d)
     ctx.update_timing()

@@ -112,13 +112,15 @@ def test_plan_net_model_validation(lib):
 def test_plan_exception_validation(lib):
     """Timing exceptions: n_tags = groups + 1 and the per-pin state count
     grows with it; at most 7 groups; startpoints must be PI or CK pins,
-    endpoint lists D or PO pins; actions 0 (false path) or 1 (multicycle
-    with M >= 1); offsets monotone; not with smoothing (gamma_ns > 0)."""
+    endpoint lists D or PO pins; actions 0 (false path), 1 (multicycle
+    with M >= 1), 2 (max delay) or 3 (min delay) with a finite value;
+    offsets monotone; not with smoothing (gamma_ns > 0)."""
     d = synth.make_design(300, 6, seed=2, n_corners=2, lut_scale=[1.0, 1.2], rc_scale=[1.0, 1.1])
     rng = np.random.default_rng(0)
     g3 = synth.exception_groups(d, rng, 3)
     info = sta.sta_plan(dict(d, **g3))
     assert info["n_tags"] == 4 and info["n_corners"] == 2
+    assert sta.sta_plan(dict(d, **dict(g3, exc_action=np.array([2, 3, 1], np.int32))))["n_tags"] == 4
     assert sta.sta_plan(d)["n_tags"] == 1
     role = np.asarray(d["pin_role"])
     q_pin = int(np.nonzero(role == synth.Q)[0][0])
@@ -126,7 +128,10 @@ def test_plan_exception_validation(lib):
     bads = [dict(d, **synth.exception_groups(d, rng, 8)),
             dict(d, **g3, gamma_ns=0.01),
             dict(d, **dict(g3, exc_from=np.where(np.arange(len(g3["exc_from"])) == 0, q_pin, g3["exc_from"]))),
-            dict(d, **dict(g3, exc_action=np.array([0, 2, 1], np.int32))),
+            dict(d, **dict(g3, exc_action=np.array([0, 4, 1], np.int32))),
+            dict(d, **dict(g3, exc_action=np.array([0, -1, 1], np.int32))),
+            dict(d, **dict(g3, exc_action=np.array([2, 3, 1], np.int32), exc_mult=np.array([0.5, np.nan, 2],
+                                                                                         np.float32))),
             dict(d, **dict(g3, exc_action=np.array([1, 1, 1], np.int32), exc_mult=np.array([2, 0.5, 3], np.float32))),
             dict(d, **dict(g3, exc_from_ptr=g3["exc_from_ptr"][[0, 2, 1, 3]]))]
     if len(g3["exc_to"]):
