@@ -184,7 +184,9 @@ typedef struct {
      * default check otherwise.  Endpoint slacks,
      * WNS and TNS take the min over tags; per-pin arrays (sta_get_pin_state)
      * hold n_corners * (n_exc + 1) states, state = corner * (n_exc + 1) +
-     * tag.  Not with gamma_ns > 0 or in a batch.  n_exc = 0: none.
+     * tag.  Not with gamma_ns > 0.  In a batch the groups of every design
+     * count together (at most 7 groups and 32 tags over the batch; a group
+     * acts only on its own design's paths).  n_exc = 0: none.
      * -through (Sec. IV-B: false paths through pin sequences): group g may
      * have ordered through sets exc_thru_ptr[g] .. exc_thru_ptr[g+1]; set s
      * lists gate input pins exc_thru_pin[exc_thru_set_ptr[s] ..

@@ -650,8 +650,18 @@ sta_status build_batch_plan(const sta_design_desc *const *descs, int32_t n, Plan
     if (n < 1 || !descs) { err = "empty batch"; return STA_EINVAL; }
     for (int32_t i = 0; i < n; ++i) {
         if (!descs[i] || !descs[i]->lib) { err = "NULL descriptor in batch"; return STA_EINVAL; }
-        if (descs[i]->n_exc != 0) { err = "timing exceptions are not supported in a batch"; return STA_EINVAL; }
     }
+    // timing exceptions: the groups of every design, pins offset, in one list
+    // (a group's tag only travels on paths from its own design's startpoints,
+    // so an empty endpoint list still reaches only that design's endpoints)
+    int32_t G = 0;
+    bool any_thru = false;
+    for (int32_t i = 0; i < n; ++i) {
+        if (descs[i]->n_exc < 0) { err = "negative n_exc"; return STA_EINVAL; }
+        G += descs[i]->n_exc;
+        any_thru = any_thru || (descs[i]->n_exc > 0 && descs[i]->exc_thru_ptr);
+    }
+    if (G > 7) { err = "at most 7 timing-exception groups over the whole batch"; return STA_EINVAL; }
     const sta_design_desc &d0 = *descs[0];
     const bool placed = d0.rc_ptr == nullptr;
     const int K = d0.n_corners;
@@ -702,9 +712,44 @@ sta_status build_batch_plan(const sta_design_desc *const *descs, int32_t n, Plan
             port_xy.assign(2 * P, 0.f);
         }
         std::vector<int64_t> pin_off(n + 1, 0);
+        std::vector<int32_t> xf_ptr(1, 0), xf, xt_ptr(1, 0), xt, xact, xth_ptr(1, 0), xth_set(1, 0), xth_pin;
+        std::vector<float> xmult;
         int64_t c0 = 0, p0 = 0, n0 = 0, cp0 = 0, np0 = 0, r0 = 0;
         for (int32_t i = 0; i < n; ++i) {
             const sta_design_desc &di = *descs[i];
+            if (di.n_exc > 0) {   // the checks build_plan makes, before the arrays are read here
+                bool ok = di.exc_from_ptr && di.exc_to_ptr && di.exc_action && di.exc_mult &&
+                          (!di.exc_thru_ptr || di.exc_thru_set_ptr);
+                for (int32_t g = 0; ok && g < di.n_exc; ++g)
+                    ok = di.exc_from_ptr[g] >= 0 && di.exc_from_ptr[g] <= di.exc_from_ptr[g + 1] &&
+                         di.exc_to_ptr[g] >= 0 && di.exc_to_ptr[g] <= di.exc_to_ptr[g + 1] &&
+                         (!di.exc_thru_ptr || (di.exc_thru_ptr[g] >= 0 && di.exc_thru_ptr[g] <= di.exc_thru_ptr[g + 1]));
+                ok = ok && (di.exc_from || di.exc_from_ptr[di.n_exc] == 0) && (di.exc_to || di.exc_to_ptr[di.n_exc] == 0);
+                if (ok && di.exc_thru_ptr)
+                    for (int32_t sset = di.exc_thru_ptr[0]; ok && sset < di.exc_thru_ptr[di.n_exc]; ++sset)
+                        ok = di.exc_thru_set_ptr[sset] >= 0 && di.exc_thru_set_ptr[sset] <= di.exc_thru_set_ptr[sset + 1] &&
+                             (di.exc_thru_pin || di.exc_thru_set_ptr[sset + 1] == di.exc_thru_set_ptr[sset]);
+                if (!ok) {
+                    err = "exception arrays NULL or offsets not monotone in design " + std::to_string(i);
+                    return STA_EINVAL;
+                }
+            }
+            for (int32_t g = 0; g < di.n_exc; ++g) {
+                for (int32_t k = di.exc_from_ptr[g]; k < di.exc_from_ptr[g + 1]; ++k)
+                    xf.push_back((int32_t)(p0 + di.exc_from[k]));
+                xf_ptr.push_back((int32_t)xf.size());
+                for (int32_t k = di.exc_to_ptr[g]; k < di.exc_to_ptr[g + 1]; ++k) xt.push_back((int32_t)(p0 + di.exc_to[k]));
+                xt_ptr.push_back((int32_t)xt.size());
+                xact.push_back(di.exc_action[g]);
+                xmult.push_back(di.exc_mult[g]);
+                if (di.exc_thru_ptr)
+                    for (int32_t sset = di.exc_thru_ptr[g]; sset < di.exc_thru_ptr[g + 1]; ++sset) {
+                        for (int32_t k = di.exc_thru_set_ptr[sset]; k < di.exc_thru_set_ptr[sset + 1]; ++k)
+                            xth_pin.push_back((int32_t)(p0 + di.exc_thru_pin[k]));
+                        xth_set.push_back((int32_t)xth_pin.size());
+                    }
+                xth_ptr.push_back((int32_t)xth_set.size() - 1);
+            }
             for (int32_t c = 0; c < di.n_cells; ++c) {
                 cell_type[c0 + c] = di.cell_type[c];
                 cell_pin_ptr[c0 + c + 1] = (int32_t)(cp0 + di.cell_pin_ptr[c + 1]);
@@ -757,6 +802,16 @@ sta_status build_batch_plan(const sta_design_desc *const *descs, int32_t n, Plan
             m.cell_xy = cell_xy.data();
             m.port_xy = port_xy.data();
         }
+        m.n_exc = G;
+        m.exc_from_ptr = xf_ptr.data();
+        m.exc_from = xf.data();
+        m.exc_to_ptr = xt_ptr.data();
+        m.exc_to = xt.data();
+        m.exc_action = xact.data();
+        m.exc_mult = xmult.data();
+        m.exc_thru_ptr = any_thru ? xth_ptr.data() : nullptr;
+        m.exc_thru_set_ptr = any_thru ? xth_set.data() : nullptr;
+        m.exc_thru_pin = any_thru ? xth_pin.data() : nullptr;
         sta_status st = build_plan(&m, plan, err);
         if (st != STA_OK) return st;
         // endpoints are in ascending merged pin id: split them by design

@@ -82,3 +82,42 @@ def test_set_corners_matches_fresh_context():
     assert_close("at", ctx.get_pin_state(sta.AT), ref["at"])
     assert_close("rat", ctx.get_pin_state(sta.RAT), ref["rat"])
     ctx.close()
+
+
+def test_batch_with_exceptions_equals_separate_contexts():
+    """Designs with their own timing-exception groups (false, multicycle,
+    max/min delay, -through sets) batched together: endpoint slacks and
+    flags, the per-design report and the oracle's values agree with separate
+    contexts; each group acts on its own design's paths only."""
+    ds = designs()[:3]
+    rng = np.random.default_rng(4)
+    ds[0] = dict(ds[0], **synth.exception_groups(ds[0], rng, 2, actions=(0, 1, 2, 3)))
+    ds[2] = dict(ds[2], **synth.exception_groups(ds[2], rng, 3, max_thru=2, actions=(0, 1, 2, 3)))
+    bctx = sta.Context(None, batch=ds)
+    assert bctx.stats()["n_tags"] == 1 + sum(len(d.get("exc_action", [])) for d in ds) + \
+        int(ds[2].get("exc_thru_ptr", [0])[-1])
+    for schedule in (sta.SCHED_DATAFLOW, sta.SCHED_COOP):
+        bctx.set_schedule(schedule)
+        bctx.update_timing()
+        es, eh, vs, vh = bctx.get_endpoint_slack()
+        e0 = 0
+        for i, d in enumerate(ds):
+            ctx = sta.Context(d)
+            ctx.set_schedule(schedule)
+            ctx.update_timing()
+            s1, h1, v1, w1 = ctx.get_endpoint_slack()
+            E = len(s1)
+            np.testing.assert_array_equal(es[e0:e0 + E], s1)
+            np.testing.assert_array_equal(eh[e0:e0 + E], h1)
+            np.testing.assert_array_equal(vs[e0:e0 + E], v1)
+            assert bctx.report_slack(design=i) == ctx.report_slack()
+            ref = oracle.sta(d)
+            assert_close("ep_setup", es[e0:e0 + E], ref["ep_setup"])
+            assert_close("ep_hold", eh[e0:e0 + E], ref["ep_hold"])
+            ctx.close()
+            e0 += E
+    bctx.close()
+    many = [dict(d, **synth.exception_groups(d, rng, 3)) for d in designs()[:3]]   # 9 groups
+    with pytest.raises(sta.StaError) as ei:
+        sta.Context(None, batch=many)
+    assert ei.value.status == sta.EINVAL
