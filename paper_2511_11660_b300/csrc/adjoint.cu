@@ -453,9 +453,9 @@ __global__ void k_adj_star(const DevCtx c)
 // identity, sign 0 at equal coordinates).  One thread per net.  The tree
 // (parents, R), the pin caps and every per-node sum sit in a shared-memory
 // column of COLN nodes, where the gradient is also summed per net pin (up to
-// COLP pins) before one FP64 atomic per pin and axis: nets of at most 9 pins
-// take 16-node columns, 64 threads a block; larger ones 128-node columns, 8
-// threads a block, largest first.  Trees beyond a column work in global
+// COLP pins) before one FP64 atomic per pin and axis: nets of at most 5 pins
+// take 8-node columns and nets of 6-9 pins 16-node columns, 64 threads a
+// block; larger ones 128-node columns, 8 threads a block, largest first.  Trees beyond a column work in global
 // scratch with an atomic per contribution.
 enum { kA_PAR, kA_R, kA_PC, kA_CN, kA_CD, kA_D, kA_M, kA_DB, kA_RB, kA_BB, kAdjArrays };
 
@@ -710,8 +710,10 @@ void launch_adjoint(const DevCtx &c, const HostSched &h, cudaStream_t st)
         }
     }
     if (c.steiner) {
-        const int ns = c.st_adj_small, nl = c.st_n_items - ns;
-        if (ns > 0) k_adj_steiner<kAdjColNodes, 9, 64><<<nblk2(ns, 64), 64, 0, st>>>(c, 0, ns);
+        const int nt = c.st_adj_tiny, ns = c.st_adj_small, nl = c.st_n_items - ns;
+        if (nt > 0) k_adj_steiner<kAdjTinyColNodes, kAdjTinyPins, 64><<<nblk2(nt, 64), 64, 0, st>>>(c, 0, nt);
+        if (ns > nt)
+            k_adj_steiner<kAdjColNodes, kAdjSmallPins, 64><<<nblk2(ns - nt, 64), 64, 0, st>>>(c, nt, ns);
         if (nl > 0)
             k_adj_steiner<kAdjBigColNodes, 64, 8><<<nblk2(nl, 8), 8, 0, st>>>(c, ns, c.st_n_items);
     } else if (c.I > 0) {

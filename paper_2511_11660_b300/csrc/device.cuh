@@ -121,7 +121,7 @@ struct DevCtx {
     float *st_capw;                             // [working nodes] RC node capacitances being accumulated
     const int32_t *st_items;                    // items with sinks by increasing sink count
     int32_t st_n_items, st_small;               // their number; the first st_small have <= 8 pins
-    int32_t st_adj_small;                       // the first st_adj_small have <= 9 pins (adjoint split)
+    int32_t st_adj_tiny, st_adj_small;          // the first st_adj_tiny have <= 5 pins, st_adj_small <= 9 (adjoint)
     unsigned *st_adj;                           // [bitset words] adjacency rows
     const int32_t *drv_of, *pin_cell;
     const float *port_xy, *cell_xy;

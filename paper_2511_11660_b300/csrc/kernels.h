@@ -71,6 +71,7 @@ cudaError_t adjoint_prepare(HostSched &h);
 // keep their node arrays in a device buffer of steiner_adjoint_floats(NN)
 // floats, needed when some net has room for kAdjBigColNodes nodes or more.
 constexpr int kAdjColNodes = 16, kAdjSmallPins = 9, kAdjBigColNodes = 128;
+constexpr int kAdjTinyColNodes = 8, kAdjTinyPins = 5;   // nets of <= 5 pins: <= 8 tree nodes
 size_t steiner_adjoint_floats(int64_t NN);
 
 // The two-stage FP64 WNS/TNS reduction.

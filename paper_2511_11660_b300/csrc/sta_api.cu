@@ -257,7 +257,12 @@ sta_status create_from_plan(sta_ctx *c, int device)
         d.st_items = upload(c, pl.st_items);
         d.st_n_items = (int32_t)pl.st_items.size();
         d.st_small = pl.st_small;
-        d.st_adj_small = 0;
+        d.st_adj_tiny = 0;
+        while (d.st_adj_tiny < d.st_n_items &&
+               pl.fo_ptr[pl.st_items[d.st_adj_tiny] + 1] - pl.fo_ptr[pl.st_items[d.st_adj_tiny]] + 1 <=
+                   sta::kAdjTinyPins)
+            ++d.st_adj_tiny;
+        d.st_adj_small = d.st_adj_tiny;
         while (d.st_adj_small < d.st_n_items &&
                pl.fo_ptr[pl.st_items[d.st_adj_small] + 1] - pl.fo_ptr[pl.st_items[d.st_adj_small]] + 1 <=
                    sta::kAdjSmallPins)
@@ -421,7 +426,8 @@ int32_t launches_per_backward(const sta_ctx *c)
     } else {
         for (int32_t s = 0; s < pl.S; ++s) n += pl.stage_ptr[s + 1] > pl.stage_ptr[s];
     }
-    if (pl.steiner) n += (c->dc.st_adj_small > 0) + (c->dc.st_n_items > c->dc.st_adj_small);   // Steiner trees
+    if (pl.steiner)   // Steiner trees: three column sizes
+        n += (c->dc.st_adj_tiny > 0) + (c->dc.st_adj_small > c->dc.st_adj_tiny) + (c->dc.st_n_items > c->dc.st_adj_small);
     else n += pl.I > 0;                                    // star segments
     return n;
 }
