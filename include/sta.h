@@ -490,11 +490,14 @@ sta_status sta_last_timings(sta_ctx *ctx, float *ms4);
  * held on every GPU that loads it until the process exits; the limit is
  * ceil(n_endpoints / 4096) * n_corners <= 8192 (about 33.5 million
  * endpoint-corners), larger inputs return STA_EINVAL with a message on
- * stderr.  The first call on a device looks the array's address up
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the array: calls whose
+ * stderr.  The kernels run on the current device, which must own setup,
+ * hold, out and the stream.  The first call on a device looks the array's
+ * address up (cudaGetSymbolAddress) with that device current; make that
+ * first call before any stream capture.  The cached address does not
+ * survive cudaDeviceReset.  Every call shares the array: calls whose
  * kernels overlap on the GPU race, so serialise them (one stream).  Errors:
- * STA_EINVAL (NULL pointer, bad size), STA_ECUDA. */
+ * STA_EINVAL (NULL pointer, bad size), STA_ECUDA (a launch of this call
+ * failed). */
 sta_status sta_reduce_slack_noalloc(const float *setup, const float *hold, int64_t n_endpoints,
                                     int32_t n_corners, double *out, void *stream);
 

@@ -8,6 +8,7 @@
 // cannot tolerate the implicit device synchronisation and possible failure
 // of a cudaMalloc.  Its partial sums live in a fixed file-scope device array
 // instead of a buffer, so it needs neither cudaMalloc nor cudaFree.
+#include <atomic>
 #include <cstdio>
 
 #include "sta.h"
@@ -24,7 +25,12 @@ constexpr int kMaxDevices = 64;
 // by every GPU that loads the library until the process exits.
 static __device__ __align__(256) double g_partial[kMaxSlots * 6];
 
-double *g_partial_ptr[kMaxDevices] = {};
+// Per-device address of g_partial, looked up at the first call on that
+// device.  Atomic, so two host threads making their first call on one
+// device at once both store the same address without a data race.  The
+// cached address belongs to the device's primary context: it does not
+// survive cudaDeviceReset (or a release of the primary context).
+std::atomic<double *> g_partial_ptr[kMaxDevices] = {};
 
 template <int NT>
 __device__ __forceinline__ void fold6(double v[6], double (*sh)[NT])
@@ -102,13 +108,15 @@ cudaError_t partial_ptr(double **out)
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-    if (!g_partial_ptr[dev]) {
+    double *cached = g_partial_ptr[dev].load(std::memory_order_acquire);
+    if (!cached) {
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_partial);
         if (e != cudaSuccess) return e;
-        g_partial_ptr[dev] = static_cast<double *>(p);
+        cached = static_cast<double *>(p);
+        g_partial_ptr[dev].store(cached, std::memory_order_release);
     }
-    *out = g_partial_ptr[dev];
+    *out = cached;
     return cudaSuccess;
 }
 
@@ -118,8 +126,11 @@ extern "C" sta_status sta_reduce_slack_noalloc(const float *setup, const float *
                                                int32_t n_corners, double *out, void *stream)
 {
     if (!setup || !hold || !out || n_endpoints < 0 || n_corners < 1) return STA_EINVAL;
-    const long long nb = (n_endpoints + kChunk - 1) / kChunk;
-    if (nb * n_corners > kMaxSlots) {
+    // Size check without overflow: bound n_endpoints before rounding it up to
+    // chunks, then compare the chunk count against the slots per corner.
+    const long long max_endpoints = (long long)kMaxSlots * kChunk;
+    const long long nb = n_endpoints <= max_endpoints ? (n_endpoints + kChunk - 1) / kChunk : kMaxSlots + 1LL;
+    if (nb > kMaxSlots / n_corners) {
         std::fprintf(stderr,
                      "sta_reduce_slack_noalloc: %lld endpoints x %d corners exceeds the fixed scratch "
                      "(at most %d chunks of %d endpoints times corners)\n",
@@ -129,8 +140,21 @@ extern "C" sta_status sta_reduce_slack_noalloc(const float *setup, const float *
     double *part = nullptr;
     if (partial_ptr(&part) != cudaSuccess) return STA_ECUDA;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    if (nb > 0) k_na_chunks<<<dim3((unsigned)nb, (unsigned)n_corners), kThreads, 0, st>>>(setup, hold, n_endpoints,
-                                                                                       n_corners, part);
-    k_na_final<<<n_corners, kThreads, 0, st>>>(part, (int)nb, n_corners, out);
-    return cudaGetLastError() == cudaSuccess ? STA_OK : STA_ECUDA;
+    // Launched through cudaLaunchKernel so that each launch's own status is
+    // checked: an error left behind by unrelated earlier work is not taken
+    // (or cleared) as this call's failure.
+    long long E = n_endpoints;
+    int K = n_corners, nbi = (int)nb;
+    if (nb > 0) {
+        void *args1[] = {(void *)&setup, (void *)&hold, (void *)&E, (void *)&K, (void *)&part};
+        if (cudaLaunchKernel((const void *)k_na_chunks, dim3((unsigned)nb, (unsigned)n_corners), dim3(kThreads),
+                             args1, 0, st) != cudaSuccess)
+            return STA_ECUDA;
+    }
+    const double *cpart = part;
+    void *args2[] = {(void *)&cpart, (void *)&nbi, (void *)&K, (void *)&out};
+    if (cudaLaunchKernel((const void *)k_na_final, dim3((unsigned)n_corners), dim3(kThreads), args2, 0, st) !=
+        cudaSuccess)
+        return STA_ECUDA;
+    return STA_OK;
 }

@@ -462,9 +462,26 @@ def reduce_slack_noalloc(setup, hold, out, stream=None):
     """WNS/TNS of device endpoint slacks ``setup``/``hold`` ([E, K] float32
     CUDA tensors) into ``out`` ([K, 8] float64 CUDA tensor) without any device
     allocation (``sta_reduce_slack_noalloc``)."""
+    import torch
     lib = load()
+    for name, t, dt in (("setup", setup, torch.float32), ("hold", hold, torch.float32), ("out", out, torch.float64)):
+        if not isinstance(t, torch.Tensor) or t.device.type != "cuda":
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    if setup.dim() != 2 or setup.shape != hold.shape:
+        raise ValueError("setup and hold must both be [n_endpoints, n_corners]")
+    if setup.device != hold.device or setup.device != out.device:
+        raise ValueError("setup, hold and out must sit on one CUDA device")
     E, K = int(setup.shape[0]), int(setup.shape[1])
-    st = lib.sta_reduce_slack_noalloc(_ptr(setup), _ptr(hold), E, K, _ptr(out), _stream(stream))
+    if K < 1 or out.numel() < 8 * K:
+        raise ValueError("out must hold n_corners x 8 float64 values")
+    # the C entry point runs on the current device: make it the tensors' one
+    with torch.cuda.device(setup.device):
+        s = _stream(stream) if stream is not None else torch.cuda.current_stream(setup.device).cuda_stream
+        st = lib.sta_reduce_slack_noalloc(_ptr(setup), _ptr(hold), E, K, _ptr(out), s)
     if st != OK:
         raise StaError(st, "sta_reduce_slack_noalloc failed")
     return out

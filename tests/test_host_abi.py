@@ -269,3 +269,24 @@ def test_levels_are_longest_path_levels(lib, seed):
     got = sta.sta_plan_levels(d)
     np.testing.assert_array_equal(got, _levels_by_dfs(d))
     assert got.max() == 17
+
+
+@pytest.mark.parametrize("n_endpoints,corners", [
+    (8193 * 4096, 1),          # one chunk past the fixed scratch
+    (4096 * 4096 + 1, 2),      # 4097 chunks x 2 corners
+    (2 ** 62 + 1, 8192),       # chunks x corners would wrap a signed 64-bit product
+    (2 ** 63 - 1, 1),          # rounding up to chunks would overflow
+])
+def test_noalloc_size_check_rejects_on_the_host(lib, n_endpoints, corners):
+    # The size check runs before any CUDA call, so the dummy (never
+    # dereferenced) pointers are safe and no GPU is needed.
+    dummy = 4096
+    st = lib.sta_reduce_slack_noalloc(dummy, dummy, n_endpoints, corners, dummy, None)
+    assert st == sta.EINVAL
+
+
+def test_noalloc_rejects_bad_arguments_on_the_host(lib):
+    dummy = 4096
+    assert lib.sta_reduce_slack_noalloc(None, dummy, 10, 1, dummy, None) == sta.EINVAL
+    assert lib.sta_reduce_slack_noalloc(dummy, dummy, -1, 1, dummy, None) == sta.EINVAL
+    assert lib.sta_reduce_slack_noalloc(dummy, dummy, 10, 0, dummy, None) == sta.EINVAL

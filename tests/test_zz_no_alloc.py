@@ -47,8 +47,29 @@ def test_noalloc_rejects_oversize():
     if not torch.cuda.is_available():
         pytest.skip("needs a CUDA device")
     lib = sta.load()
-    x = torch.zeros(16, dtype=torch.float32, device="cuda")
+    n = 8193 * 4096   # 8193 chunks of 4096 endpoints: one past the fixed scratch
+    # buffers of the claimed size, so that a regression of the host-side check
+    # reads only memory it owns (a wrong status, never an out-of-range read)
+    x = torch.zeros(n, dtype=torch.float32, device="cuda")
     out = torch.zeros(8, dtype=torch.float64, device="cuda")
-    # 8193 chunks of 4096 endpoints: one past the fixed scratch; rejected on the host
-    st = lib.sta_reduce_slack_noalloc(x.data_ptr(), x.data_ptr(), 8193 * 4096, 1, out.data_ptr(), None)
+    st = lib.sta_reduce_slack_noalloc(x.data_ptr(), x.data_ptr(), n, 1, out.data_ptr(), None)
     assert st == sta.EINVAL
+    del x
+
+
+def test_noalloc_binding_checks_inputs():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("needs a CUDA device")
+    s = torch.zeros((10, 2), dtype=torch.float32, device="cuda")
+    out = torch.zeros((2, 8), dtype=torch.float64, device="cuda")
+    with pytest.raises(ValueError):
+        sta.reduce_slack_noalloc(s.double(), s, out)          # wrong dtype
+    with pytest.raises(ValueError):
+        sta.reduce_slack_noalloc(s, s[:5], out)               # shapes differ
+    with pytest.raises(ValueError):
+        sta.reduce_slack_noalloc(s, s, out[:1])               # out too short
+    with pytest.raises(ValueError):
+        sta.reduce_slack_noalloc(s.t(), s.t(), out)           # not contiguous
+    with pytest.raises(ValueError):
+        sta.reduce_slack_noalloc(s.cpu(), s, out)             # host tensor
