@@ -55,7 +55,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="scale", choices=sorted(WORKLOADS))
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--schedule", default="dataflow", choices=["level", "dataflow", "coop", "auto"],
+    ap.add_argument("--schedule", default="dataflow", choices=["level", "dataflow", "coop", "tile", "auto"],
                     help="propagation schedule; auto = sta_autotune's choice")
     ap.add_argument("--net-model", default="elmore", choices=["elmore", "arnoldi"],
                     help="net delay calculator of the scale/mid workloads (arnoldi: order-3 reduced model)")
@@ -148,13 +148,29 @@ class ClockSampler:
 
 
 def byte_model(st: dict, K: int) -> dict:
-    """Algorithmic (compulsory) bytes of one update per phase.
-    P pins, S net sinks (net arcs), Nn nets, N RC nodes, E endpoints, I items.
-    Per pin and state: arrival and required time 32 B (FP64 x 4), slew and
-    slack 16 B (FP32 x 4).  Forward: every arrival and slew written once and
-    read once by its consumers (2 x 48 B); backward: arrival and slew read,
-    required time and slack written, required time read by the drivers
-    (32 + 16 + 32 + 16 + 32 B)."""
+    """Algorithmic (compulsory) bytes of one update per kernel, FP32 pin
+    states, each element read once and written once (cache reuse of fan-in
+    gathers is not credited).  P pins, A timing arcs (cell + net), S net
+    sinks, Nn nets, N RC nodes; K corners multiply the per-pin, per-sink and
+    per-net terms.
+      net    RC read 12 B/node; load write 4 B/net; sink delay and variance write 8 B/sink
+      fwd    arrival + slew write 32 B/pin and read 32 B/pin; fan-in CSR 8 B/arc + offsets 4 B/pin;
+             net outputs read (4 B/net, 8 B/sink)
+      bwd    required time write + read 32 B/pin; slews re-read 16 B/pin; arrival and required read for
+             slack 32 B/pin, slack write 16 B/pin; fan-out CSR 8 B/arc + offsets 4 B/pin
+    Total = 168P + 16A + 12N + 16S + 8Nn per corner-scaled term."""
+    P, S, Nn, N = st["n_pins"], st["n_net_arcs"], st["n_nets"], st["n_rc_nodes"]
+    A = st["n_cell_arcs"] + st["n_net_arcs"]
+    net = 12 * N + K * (4 * Nn + 8 * S)
+    fwd = K * (64 * P + 4 * P + 4 * Nn + 8 * S) + 8 * A
+    bwd = K * (48 * P + 48 * P + 4 * P) + 8 * A
+    return {"net": net, "fwd": fwd, "bwd": bwd, "reduce": 0, "total": net + fwd + bwd}
+
+
+def storage_model(st: dict, K: int) -> dict:
+    """Bytes the implementation's own arrays move per update: arrival and
+    required times are double-float (32 B per pin and state), slews and
+    slacks FP32 (16 B), E endpoints, I items."""
     P, S, Nn, N = st["n_pins"], st["n_net_arcs"], st["n_nets"], st["n_rc_nodes"]
     E, I = st["n_endpoints"], st["n_items"]
     net = 12 * N + 8 * S + K * (4 * Nn + 8 * S)
@@ -167,8 +183,10 @@ def byte_model(st: dict, K: int) -> dict:
 # the source files that define each measured kernel (its code and everything it inlines)
 _PERSISTENT = ("dataflow.cu", "item.cuh", "device.cuh", "kernels.h")
 _LEVEL = ("kernels.cu", "item.cuh", "device.cuh", "kernels.h")
+_TILE = ("tile.cu", "item.cuh", "device.cuh", "kernels.h")
 KERNEL_SOURCES = {"k_df_forward": _PERSISTENT, "k_df_backward": _PERSISTENT, "k_coop_pass": _PERSISTENT,
-                  "k_net_tree": _LEVEL, "k_fwd_level": _LEVEL, "k_bwd_level": _LEVEL}
+                  "k_net_tree": _LEVEL, "k_fwd_level": _LEVEL, "k_bwd_level": _LEVEL,
+                  "k_tile_forward": _TILE, "k_tile_backward": _TILE}
 
 
 def kernel_source_hash(kernel: str) -> str:
@@ -221,7 +239,8 @@ def run_ours(a, dist: Dist):
         d.update(net_model=sta.NET_ARNOLDI, arnoldi_order=3)
     dstats = synth.design_stats(d)
     ctx = sta.Context(d, device=dev)
-    sched_names = {sta.SCHED_LEVEL: "level", sta.SCHED_DATAFLOW: "dataflow", sta.SCHED_COOP: "coop"}
+    sched_names = {sta.SCHED_LEVEL: "level", sta.SCHED_DATAFLOW: "dataflow", sta.SCHED_COOP: "coop",
+                   sta.SCHED_TILE: "tile"}
     if a.schedule == "auto":
         sch, par, _ = ctx.autotune(trials=5)
         schedule = sched_names[sch]
@@ -299,6 +318,9 @@ def run_ours(a, dist: Dist):
     if schedule == "dataflow":
         kern = "k_df_forward" if fwd_dominant else "k_df_backward"
         launches = 1
+    elif schedule == "tile":
+        kern = "k_tile_forward" if fwd_dominant else "k_tile_backward"
+        launches = 1
     elif schedule == "coop":
         # one launch runs both passes: its time is the forward slot
         kern, launches = "k_coop_pass", 1
@@ -308,12 +330,19 @@ def run_ours(a, dist: Dist):
         launches = st["n_levels"]
     achieved = phase_bytes / (phase_ms * 1e-3) / 1e9
     tr = measured_traffic(kern)
+    sm = storage_model(st, K)
+    if schedule == "coop":
+        storage = sm["fwd"] + sm["bwd"]
+    else:
+        storage = sm["fwd"] if fwd_dominant else sm["bwd"]
     out["roofline"] = {"bound": "hbm", "kernel": kern, "achieved": achieved, "peak": pk["hbm_gbs"],
                        "unit": "GB/s", "frac": achieved / pk["hbm_gbs"],
                        "traffic": tr, "peak_source": pk_kind + " (hbm_gbs, copy burst)",
                        "bytes_per_launch": phase_bytes / launches, "launches_per_pass": launches,
+                       "byte_model": "algorithmic: 168P + 16A + 12N + 16S + 8Nn per pass, split per kernel",
+                       "storage_bytes_per_launch": storage / launches,
                        "phase_ms": {"net": ph[0], "fwd": ph[1], "bwd": ph[2], "reduce": ph[3]},
-                       "pass_bytes_model": bm["total"],
+                       "pass_bytes_model": bm["total"], "pass_storage_bytes": sm["total"],
                        "pass_frac": bm["total"] / (ms_step * 1e-3) / 1e9 / pk["hbm_gbs"]}
 
     # ---- end to end through the C ABI with host buffers
@@ -517,7 +546,7 @@ def run_batched(a, dev: int, plain: bool = True, dist: Dist = None) -> dict:
         ds = [ds[i] for i in part]
     arcs = sum(synth.design_stats(d)["arcs"] for d in ds)
     K = ds[0]["n_corners"]
-    names = {sta.SCHED_LEVEL: "level", sta.SCHED_DATAFLOW: "dataflow", sta.SCHED_COOP: "coop"}
+    names = {sta.SCHED_LEVEL: "level", sta.SCHED_DATAFLOW: "dataflow", sta.SCHED_COOP: "coop", sta.SCHED_TILE: "tile"}
     b = sta.Context(None, batch=ds, device=dev)
     sch, par, _ = b.autotune(trials=3)
     for _ in range(3):
@@ -610,7 +639,8 @@ def run_incremental(a, dist: Dist):
     s0, _, _, _ = ctx.get_endpoint_slack()
     T = clock.period_in_gap(-s0[:, 1], min_half_gap=0.0)[0]   # corner 1 (scale 1.0)
     ctx.set_clock(T)
-    sched = {sta.SCHED_LEVEL: "level", sta.SCHED_DATAFLOW: "dataflow", sta.SCHED_COOP: "coop"}[ctx.autotune(trials=2)[0]]
+    sched = {sta.SCHED_LEVEL: "level", sta.SCHED_DATAFLOW: "dataflow", sta.SCHED_COOP: "coop",
+             sta.SCHED_TILE: "tile"}[ctx.autotune(trials=2)[0]]
     K = ctx.K
     C = d["n_cells"]
     rng = np.random.default_rng(a.seed)

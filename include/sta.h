@@ -72,7 +72,9 @@ enum { STA_AT = 0, STA_SLEW = 1, STA_RAT = 2, STA_SLACK = 3 };
 /* propagation schedules (sta_set_schedule) */
 enum { STA_SCHED_LEVEL = 0,      /* one kernel launch per level, graph-captured */
        STA_SCHED_DATAFLOW = 1,   /* one persistent kernel per pass, per-item ready flags */
-       STA_SCHED_COOP = 2 };     /* one co-resident launch for both passes, a grid barrier per level */
+       STA_SCHED_COOP = 2,       /* one co-resident launch for both passes, a grid barrier per level */
+       STA_SCHED_TILE = 3 };     /* one co-resident launch per pass; each block walks its own tile of the
+                                    graph level by level, block-local dependencies through shared memory */
 
 /*
  * Cell library.  Per type: type_nin inputs (1..3) followed by one output.
@@ -262,6 +264,30 @@ sta_status sta_plan(const sta_design_desc *desc, sta_plan_info *out);
  * inputs, primary inputs counting as level 0).  Errors as sta_plan. */
 sta_status sta_plan_levels(const sta_design_desc *desc, int32_t *cell_level);
 
+/* Partition of the graph for the tile schedule (STA_SCHED_TILE): sizes and
+ * how many dependencies stay inside a tile. */
+typedef struct {
+    int32_t n_tiles, n_steps;        /* tiles (resident blocks), steps (levels + 1) */
+    int32_t wave_items, ring_slots;  /* entries one wave of a block runs; shared-memory ring slots */
+    int32_t max_step_entries;        /* largest list of one tile at one step */
+    int32_t pad;
+    int64_t fwd_edges, fwd_local;    /* gate-input -> driver dependencies, and those read from the ring */
+    int64_t bwd_edges, bwd_local;    /* driver -> gate-input dependencies, and those read from the ring */
+    int64_t crit_edges, crit_local;  /* critical fan-in edges, and those inside one tile */
+} sta_tile_info;
+
+/* Host only, no GPU needed: build the tile schedule's partition of a design
+ * into n_tiles tiles (as sta_set_schedule(STA_SCHED_TILE, n_tiles) would),
+ * check it by replaying the kernels' ring use on the host (every entry in
+ * exactly one list at its level, every ring read finds its producer), and
+ * report its statistics.  Errors: as sta_plan; STA_EINVAL also for
+ * n_tiles < 1 or a failed check (message via sta_plan_error). */
+sta_status sta_plan_tiles(const sta_design_desc *desc, int32_t n_tiles, sta_tile_info *out);
+
+/* Statistics of the context's current tile partition (zeros unless the
+ * schedule is STA_SCHED_TILE). */
+sta_status sta_get_tile_info(const sta_ctx *ctx, sta_tile_info *out);
+
 /* Message of the last failed sta_plan / sta_create on this thread. */
 const char *sta_plan_error(void);
 
@@ -335,7 +361,15 @@ sta_status sta_resize_cells(sta_ctx *ctx, const int32_t *cells, const int32_t *t
 
 /* Select the propagation schedule (STA_SCHED_*) and its parameter: threads
  * per block for LEVEL (0 = 128); for DATAFLOW and COOP the persistent grid
- * size in blocks (0 = every block the occupancy allows on this device). */
+ * size in blocks (0 = every block the occupancy allows on this device); for
+ * TILE the number of tiles (0 = one per SM), at most the co-resident
+ * blocks of its kernels.  TILE partitions the graph on the host (every item
+ * goes to the tile of its critical fan-in while that tile's level has room,
+ * so that most level-to-level dependencies stay inside one block and pass
+ * through shared memory) and uploads the partition; it needs at most 4095
+ * levels.  Errors: STA_EINVAL (unknown schedule, parameter out of range,
+ * library too large for the shared-memory copy, too many levels or tiles),
+ * STA_ECUDA / STA_ENOMEM (set-up on the device). */
 sta_status sta_set_schedule(sta_ctx *ctx, int32_t schedule, int32_t param);
 
 /* Reverse sweep of sta_backward: STA_SCHED_DATAFLOW (one persistent kernel,

@@ -20,7 +20,7 @@ namespace sta {
 
 constexpr int kDfThreads = 256;
 
-static inline size_t df_smem_bytes(int T) { return (size_t)T * 3 * 4 * kLutStride * sizeof(float) + (size_t)T * 5 * sizeof(int); }
+static inline size_t df_smem_bytes(int T) { return smem_lib_bytes(T); }
 
 // After an aborted pass the mailboxes hold a mix of parities: reset them
 // all to NaN.  (A completed pass leaves the next parity all NaN.)
@@ -47,25 +47,6 @@ __global__ void k_df_begin(const DevCtx c)
         c.df_state[2] = 0u;
         c.df_state[3] = 0u;
     }
-}
-
-struct SmemLib {
-    LutShared lut;
-    const int *nin, *kind, *sense;
-};
-
-__device__ __forceinline__ SmemLib stage_library(const DevCtx &c, float *smem)
-{
-    const int nl = c.T * 3 * 4 * kLutStride;
-    for (int i = threadIdx.x; i < nl; i += blockDim.x) smem[i] = __ldg(c.lut + i);
-    int *ti = reinterpret_cast<int *>(smem + nl);
-    for (int i = threadIdx.x; i < c.T; i += blockDim.x) {
-        ti[i] = __ldg(c.type_nin + i);
-        ti[c.T + i] = __ldg(c.type_kind + i);
-    }
-    for (int i = threadIdx.x; i < 3 * c.T; i += blockDim.x) ti[2 * c.T + i] = __ldg(c.arc_sense + i);
-    __syncthreads();
-    return SmemLib{LutShared{smem}, ti, ti + c.T, ti + 2 * c.T};
 }
 
 // Next chunk for this warp (lane 0 takes it, all lanes get it); -1 when the
@@ -348,12 +329,17 @@ void launch_coop_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cuda
     if (ev) cudaEventRecord(ev[4], st);
 }
 
+void launch_df_reset(const DevCtx &c, int blocks, cudaStream_t st)
+{
+    k_df_recover<<<blocks > 0 ? blocks : 1, kDfThreads, 0, st>>>(c);
+    k_df_begin<<<1, 32, 0, st>>>(c);
+}
+
 void launch_dataflow_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev)
 {
     const size_t smem = df_smem_bytes(h.T);
     if (ev) cudaEventRecord(ev[0], st);
-    k_df_recover<<<h.df_blocks_fwd > 0 ? h.df_blocks_fwd : 1, kDfThreads, 0, st>>>(c);
-    k_df_begin<<<1, 32, 0, st>>>(c);
+    launch_df_reset(c, h.df_blocks_fwd, st);
     launch_net_phase(c, h, st);
     if (ev) cudaEventRecord(ev[1], st);
     if (c.n_fwd_chunks > 0) {

@@ -154,6 +154,14 @@ struct DevCtx {
     const int32_t *ep_order;                    // [E] endpoints by driver level (dataflow forward work list)
     const int32_t *fwd_chunk_lo, *fwd_chunk_hi;   // forward work: items by level, then endpoints (index I + e)
     const int32_t *bwd_chunk_lo, *bwd_chunk_hi;   // backward work: items by level, deepest first
+    // tile schedule (tile.cu): per-block lists of items and endpoints by step
+    int32_t tl_B, tl_NS, tl_R;                  // tiles, steps, ring slots per block
+    const int32_t *tl_ptr;                      // [B*NS + 1] list (b, s) = entries [tl_ptr[b*NS+s], ...+1)
+    const int32_t *tl_nitem;                    // [B*NS] items at the front of list (b, s), endpoints after
+    const int32_t *tl_rbase;                    // [B*NS] backward ring position of list (b, s)'s first item
+    const int4 *tl_fdesc;                       // [(I + E) * 2] forward descriptor of every list entry
+    const int4 *tl_bdesc;                       // [(I + E) * 4] backward descriptor of every item entry
+    const int16_t *tl_fo_ring;                  // [F] backward ring code of a fan-out entry, -1 = mailbox
     // differentiable pass (sta_backward)
     float4 *adj;                                // [P][K] late adjoints: dJ/dAT rise, fall, dJ/dslew rise, fall
     float4 *abox;                               // [2][P][K] the same for gate input pins, parity mailbox

@@ -128,6 +128,32 @@ __device__ __forceinline__ float lookup(const L &lut, int tq, Seg as, Seg bl, fl
     return interp(lut, tq, seg_slew_t(lut, tq, s), seg_load_t(lut, tq, l));
 }
 
+// The cell library (packed tables and per-type data) in shared memory, one
+// copy per block of the persistent kernels.
+struct SmemLib {
+    LutShared lut;
+    const int *nin, *kind, *sense;
+};
+
+__host__ __device__ inline size_t smem_lib_bytes(int T)
+{
+    return (size_t)T * 3 * 4 * kLutStride * sizeof(float) + (size_t)T * 5 * sizeof(int);
+}
+
+__device__ __forceinline__ SmemLib stage_library(const DevCtx &c, float *smem)
+{
+    const int nl = c.T * 3 * 4 * kLutStride;
+    for (int i = threadIdx.x; i < nl; i += blockDim.x) smem[i] = __ldg(c.lut + i);
+    int *ti = reinterpret_cast<int *>(smem + nl);
+    for (int i = threadIdx.x; i < c.T; i += blockDim.x) {
+        ti[i] = __ldg(c.type_nin + i);
+        ti[c.T + i] = __ldg(c.type_kind + i);
+    }
+    for (int i = threadIdx.x; i < 3 * c.T; i += blockDim.x) ti[2 * c.T + i] = __ldg(c.arc_sense + i);
+    __syncthreads();
+    return SmemLib{LutShared{smem}, ti, ti + c.T, ti + 2 * c.T};
+}
+
 // ------------------------------------------------------ mailbox access
 
 __device__ __forceinline__ float4 ld_relaxed4(const float4 *p)
@@ -329,9 +355,16 @@ __device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int
 }
 
 // Lane q of the quad computes component q = el*2 + rf of the item's states.
+// The lane's results of its first corner (component q of the output's
+// arrival and slew), for the tile schedule's shared-memory ring.
+struct FwdOut {
+    DF at;
+    float sl;
+};
+
 template <bool SMOOTH, bool UNIFORM, bool WAIT, bool THRU = true, class L>
 __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const FwdItem &f, const FwdIn &in, int g,
-                                        int q, int par)
+                                        int q, int par, FwdOut *first = nullptr)
 {
     const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
     const int K = c.K, t = f.t, pin0 = f.pin0, nin = f.nin;
@@ -347,6 +380,7 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
             st_comp_df(c.at + (size_t)pin0 * K + k, q, a);
             st_comp(c.slew + (size_t)pin0 * K + k, q, c.pi_slew);
             if (pub) publish_fwd(c, par, pin0, k, q, a, c.pi_slew);
+            if (first && k == kq) *first = FwdOut{a, c.pi_slew};
         }
         return;
     }
@@ -366,6 +400,7 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
             st_comp_df(c.at + (size_t)qp * K + k, q, a);
             st_comp(c.slew + (size_t)qp * K + k, q, sl);
             if (pub) publish_fwd(c, par, qp, k, q, a, sl);
+            if (first && k == kq) *first = FwdOut{a, sl};
         }
         return;
     }
@@ -483,6 +518,7 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
         st_comp_df(c.at + (size_t)z * K + k, q, oa);
         st_comp(c.slew + (size_t)z * K + k, q, os);
         if (pub) publish_fwd(c, par, z, k, q, oa, os);
+        if (first && k == kq) *first = FwdOut{oa, os};
     }
 }
 
@@ -673,9 +709,11 @@ __device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int
 // Lane q = el*2 + rfi: the output's required time (component q) over its
 // net sinks, then each input pin's over its arcs, and pin slacks.  With WAIT
 // the first corner's output required time comes folded from bwd_probe (Rpre).
+// With `first` (the tile schedule's ring), the lane's first-corner required
+// time of each input pin, component q, is returned there as well.
 template <bool UNIFORM, bool WAIT, bool THRU = true, class L>
 __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int *tsense, const BwdItem &b, int q,
-                                        int par, DF Rpre)
+                                        int par, DF Rpre, DF *first = nullptr)
 {
     const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
     const int t = b.t, pin0 = b.pin0, z = b.z, K = c.K;
@@ -684,10 +722,10 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
     const int base = threadIdx.x & 28;
     const int kq = corner_lane(c);
     for (int k = kq; k < K; k += c.KL) {
-        const bool first = k == kq;
+        const bool first_k = k == kq;
         // required time of the output, component q, over its net sinks
         DF R(el ? INFINITY : -INFINITY);
-        if (WAIT && first) {
+        if (WAIT && first_k) {
             R = Rpre;
         } else {
             float rf = el ? INFINITY : -INFINITY, rd = 0.f;
@@ -708,16 +746,16 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
             if (isfinite(rf)) R = rw - rd;
         }
         st_comp_df(c.rat + (size_t)z * K + k, q, R);
-        const DF Az = first ? b.az0 : ld_state_df(c.at + (size_t)z * K + k, q);
+        const DF Az = first_k ? b.az0 : ld_state_df(c.at + (size_t)z * K + k, q);
         st_comp(c.slack + (size_t)z * K + k, q, el ? R - Az : Az - R);
         if (t < 0) continue;
         // the output's required times of both edges at this lane's el
         const DF R0 = shfl_df(m, R, base + el * 2), R1 = shfl_df(m, R, base + el * 2 + 1);
         const float sc = __ldg(c.lut_scale + k);
-        const float ld = first ? b.ld0 : c.load[(size_t)z * K + k];
+        const float ld = first_k ? b.ld0 : c.load[(size_t)z * K + k];
         if (b.kind == 1) {   // CK: only the rising edge has an arc (to both edges of Q)
             const int ck = pin0;
-            const float s = first ? b.s0[0] : ld_state(c.slew + (size_t)ck * K + k, el * 2);
+            const float s = first_k ? b.s0[0] : ld_state(c.slew + (size_t)ck * K + k, el * 2);
             const int tb = tab_off(t, 1, 0);
             const Seg as = seg_slew<UNIFORM>(c, lut, tb, s), bl = seg_load<UNIFORM>(c, lut, tb, ld);
             const float d0 = sc * lookup<UNIFORM>(lut, tb, as, bl, s, ld);
@@ -726,7 +764,7 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
             DF Rc = (el ? c1 < c0 : c1 > c0) ? R1 - d1 : R0 - d0;
             if (rfi == 1) Rc = DF(el ? INFINITY : -INFINITY);
             st_comp_df(c.rat + (size_t)ck * K + k, q, Rc);
-            const DF Ac = first ? b.a0[0] : ld_state_df(c.at + (size_t)ck * K + k, q);
+            const DF Ac = first_k ? b.a0[0] : ld_state_df(c.at + (size_t)ck * K + k, q);
             st_comp(c.slack + (size_t)ck * K + k, q, el ? Rc - Ac : Ac - Rc);
             continue;
         }
@@ -737,7 +775,7 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
             const int a = pin0 + j;
             const int se = tsense[t * 3 + j];
             const int tbj = tab_off(t, j, 0);
-            const float s = first ? b.s0[j] : ld_state(c.slew + (size_t)a * K + k, q);
+            const float s = first_k ? b.s0[j] : ld_state(c.slew + (size_t)a * K + k, q);
             const Seg as = seg_slew<UNIFORM>(c, lut, tbj, s);
             // FP32 choice between the (at most two) arcs, the winner exactly
             float af = el ? INFINITY : -INFINITY, ad = 0.f;
@@ -756,9 +794,10 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
             }
             const DF acc = isfinite(af) ? aw - ad : DF(af);
             st_comp_df(c.rat + (size_t)a * K + k, q, acc);
-            const DF Aa = first ? b.a0[j] : ld_state_df(c.at + (size_t)a * K + k, q);
+            const DF Aa = first_k ? b.a0[j] : ld_state_df(c.at + (size_t)a * K + k, q);
             st_comp(c.slack + (size_t)a * K + k, q, el ? acc - Aa : Aa - acc);
             if (WAIT) publish_rat(c, par, a, k, q, acc);
+            if (first && first_k) first[j] = acc;
         }
     }
 }

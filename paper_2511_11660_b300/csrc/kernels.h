@@ -26,6 +26,7 @@ struct HostSched {
     bool adj_level = false;           // reverse sweep forced to one launch per level
     bool adj_ready = false;           // adjoint_prepare has run for the current choice
     int coop_blocks = 0;              // co-resident grid of the cooperative schedule
+    int tile_blocks = 0;              // tiles (co-resident blocks) of the tile schedule
 };
 
 // Net delays, forward levels, endpoints, backward levels, reduction.  With
@@ -58,6 +59,20 @@ void launch_dataflow_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, 
 // blocks when > 0) outside stream capture.
 cudaError_t coop_prepare(HostSched &h, bool smooth, int requested);
 void launch_coop_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev = nullptr);
+
+// Tile schedule (tile.cu): one co-resident launch per pass, each block
+// walking its own tile of the partition (tile.cpp) step by step.
+// tile_prepare gives the largest co-resident grid of the tile kernels
+// (outside stream capture); the DevCtx tl_* arrays must hold a partition
+// for c.tl_B <= that many tiles.
+int tile_threads();
+int tile_ring_slots(int KL);
+int tile_max_steps();
+cudaError_t tile_prepare(HostSched &h, bool smooth, int NS, int *max_blocks);
+void launch_tile_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cudaEvent_t *ev = nullptr);
+// Mailbox recovery after an aborted pass and a new epoch (dataflow and tile
+// schedules), on a grid of `blocks` blocks.
+void launch_df_reset(const DevCtx &c, int blocks, cudaStream_t st);
 
 // Smoothed objective and its reverse sweep to cell positions (adjoint.cu):
 // a persistent dataflow sweep when adjoint_prepare gave it a grid

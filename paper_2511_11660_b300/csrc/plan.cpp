@@ -349,9 +349,18 @@ void build(const sta_design_desc *d, Plan &pl)
         throw Fail{STA_ECYCLE, "combinational loop through cell " + std::to_string(bad)};
     }
     pl.S = (int32_t)pl.stage_ptr.size() - 1;
-    // items inside one level keep ascending original order
+    // Items inside one level are grouped by cell type (primary inputs first),
+    // in ascending original order within a type: the kernels run 8 / KL
+    // consecutive items per warp, and items of one type take the same
+    // branches (input count, arc senses), so a warp does not pay for the
+    // arcs of every type in the level.
     for (int32_t s = 0; s < pl.S; ++s)
-        std::sort(order.begin() + pl.stage_ptr[s], order.begin() + pl.stage_ptr[s + 1]);
+        std::sort(order.begin() + pl.stage_ptr[s], order.begin() + pl.stage_ptr[s + 1],
+                  [&](int32_t a, int32_t b) {
+                      const int32_t ta = a < nPI ? -1 : d->cell_type[a - nPI];
+                      const int32_t tb = b < nPI ? -1 : d->cell_type[b - nPI];
+                      return ta != tb ? ta < tb : a < b;
+                  });
     pl.max_width = 0;
     for (int32_t s = 0; s < pl.S; ++s) pl.max_width = std::max(pl.max_width, pl.stage_ptr[s + 1] - pl.stage_ptr[s]);
 

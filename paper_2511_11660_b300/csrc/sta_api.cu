@@ -13,6 +13,7 @@
 #include "kernels.h"
 #include "plan.h"
 #include "sta.h"
+#include "tile.h"
 
 using sta::DevCtx;
 using sta::HostSched;
@@ -59,11 +60,19 @@ struct sta_ctx {
     // path reports (allocated at the first sta_report_paths)
     sta::PathJob pj{};
     int32_t path_cap = 0;   // pins the path buffers hold
+    // tile schedule: the partition's device arrays (rebuilt when the tile
+    // count changes) and its statistics
+    std::vector<void *> tile_allocs;
+    size_t tile_bytes = 0;
+    sta::TilePlan tile_stats;   // sizes and statistics only (vectors cleared after the upload)
 };
 
 namespace {
 
 thread_local std::string g_plan_err;
+
+// quads per item: states handled side by side (1, 2, 4 or 8)
+int32_t quads_per_item(int32_t K) { return K >= 8 ? 8 : K >= 4 ? 4 : K >= 2 ? 2 : 1; }
 
 struct CudaFail {
     cudaError_t e;
@@ -119,7 +128,61 @@ void record_pass(sta_ctx *c, cudaStream_t st, cudaEvent_t *ev = nullptr)
 {
     if (c->schedule == STA_SCHED_DATAFLOW) sta::launch_dataflow_pass(c->dc, c->hs, st, ev);
     else if (c->schedule == STA_SCHED_COOP) sta::launch_coop_pass(c->dc, c->hs, st, ev);
+    else if (c->schedule == STA_SCHED_TILE) sta::launch_tile_pass(c->dc, c->hs, st, ev);
     else sta::launch_level_pass(c->dc, c->hs, st, ev);
+}
+
+void free_tiles(sta_ctx *c)
+{
+    for (void *p : c->tile_allocs) cudaFree(p);
+    c->tile_allocs.clear();
+    c->bytes -= c->tile_bytes;
+    c->tile_bytes = 0;
+    c->dc.tl_B = 0;
+}
+
+template <class T>
+T *tile_upload(sta_ctx *c, const std::vector<T> &v)
+{
+    void *p = nullptr;
+    const size_t b = std::max<size_t>(v.size() * sizeof(T), 16);
+    CK(cudaMalloc(&p, b));
+    c->tile_allocs.push_back(p);
+    c->tile_bytes += b;
+    c->bytes += b;
+    if (!v.empty()) CK(cudaMemcpy(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return static_cast<T *>(p);
+}
+
+// Partition the graph into B tiles and upload the lists, descriptors and
+// ring codes (tile.cpp).
+void build_tiles(sta_ctx *c, int B)
+{
+    if (c->dc.tl_B == B) return;
+    free_tiles(c);
+    sta::TilePlan tp;
+    const int W = sta::tile_threads() / (4 * c->dc.KL);
+    sta::build_tile_plan(c->plan, B, W, sta::tile_ring_slots(c->dc.KL), tp);
+    sta::DevCtx &d = c->dc;
+    d.tl_ptr = tile_upload(c, tp.ptr);
+    d.tl_nitem = tile_upload(c, tp.nitem);
+    d.tl_rbase = tile_upload(c, tp.rbase);
+    d.tl_fdesc = reinterpret_cast<const int4 *>(tile_upload(c, tp.fdesc));
+    d.tl_bdesc = reinterpret_cast<const int4 *>(tile_upload(c, tp.bdesc));
+    d.tl_fo_ring = tile_upload(c, tp.fo_ring);
+    d.tl_NS = tp.NS;
+    d.tl_R = tp.R;
+    d.tl_B = B;
+    c->hs.tile_blocks = B;
+    tp.ptr.clear();
+    tp.nitem.clear();
+    tp.rbase.clear();
+    tp.item.clear();
+    tp.fdesc.clear();
+    tp.bdesc.clear();
+    tp.fo_ring.clear();
+    tp.tile_of.clear();
+    c->tile_stats = std::move(tp);
 }
 
 void ensure_graph(sta_ctx *c)
@@ -320,7 +383,7 @@ sta_status create_from_plan(sta_ctx *c, int device)
     d.spin_limit = 1LL << 23;
     {
         // a warp works on 8 / KL items, 4 * KL lanes each (KL corners side by side)
-        d.KL = pl.K >= 8 ? 8 : pl.K >= 4 ? 4 : pl.K >= 2 ? 2 : 1;
+        d.KL = quads_per_item(pl.K);
         const int32_t kChunkItems = 8 / d.KL;
         // Forward work list: the item chunks of each level, and after the
         // chunks of level s the endpoints whose driver sits at level
@@ -400,6 +463,12 @@ int32_t launches_per_update(const sta_ctx *c)
     }
     if (c->schedule == STA_SCHED_COOP) {
         n += 2;                                  // barrier reset, all levels in one launch
+        n += (c->hs.n_red_chunks > 0) + 1;       // two-stage reduction
+        return n;
+    }
+    if (c->schedule == STA_SCHED_TILE) {
+        n += 2;                                  // mailbox recovery, epoch reset
+        n += (pl.I > 0 || pl.E > 0) + (pl.I > 0);   // forward, backward
         n += (c->hs.n_red_chunks > 0) + 1;       // two-stage reduction
         return n;
     }
@@ -495,6 +564,60 @@ sta_status sta_plan(const sta_design_desc *desc, sta_plan_info *out)
 }
 
 const char *sta_plan_error(void) { return g_plan_err.c_str(); }
+
+namespace {
+void fill_tile_info(const sta::TilePlan &tp, sta_tile_info *out)
+{
+    std::memset(out, 0, sizeof(*out));
+    out->n_tiles = tp.B;
+    out->n_steps = tp.NS;
+    out->wave_items = tp.W;
+    out->ring_slots = tp.R;
+    out->max_step_entries = tp.max_step_items;
+    out->fwd_edges = tp.fwd_edges;
+    out->fwd_local = tp.fwd_local;
+    out->bwd_edges = tp.bwd_edges;
+    out->bwd_local = tp.bwd_local;
+    out->crit_edges = tp.crit_edges;
+    out->crit_local = tp.crit_local;
+}
+}  // namespace
+
+sta_status sta_plan_tiles(const sta_design_desc *desc, int32_t n_tiles, sta_tile_info *out)
+{
+    if (n_tiles < 1) {
+        g_plan_err = "n_tiles must be >= 1";
+        return STA_EINVAL;
+    }
+    Plan pl;
+    std::string err;
+    const sta_status st = sta::build_plan(desc, pl, err);
+    if (st != STA_OK) {
+        g_plan_err = err;
+        return st;
+    }
+    const int32_t KL = quads_per_item(pl.K);
+    sta::TilePlan tp;
+    sta::build_tile_plan(pl, n_tiles, sta::tile_threads() / (4 * KL), sta::tile_ring_slots(KL), tp);
+    const std::string bad = sta::check_tile_plan(pl, tp);
+    if (!bad.empty()) {
+        g_plan_err = "tile partition check failed: " + bad;
+        return STA_EINVAL;
+    }
+    if (out) fill_tile_info(tp, out);
+    return STA_OK;
+}
+
+sta_status sta_get_tile_info(const sta_ctx *c, sta_tile_info *out)
+{
+    if (!c || !out) return STA_EINVAL;
+    if (c->schedule != STA_SCHED_TILE) {
+        std::memset(out, 0, sizeof(*out));
+        return STA_OK;
+    }
+    fill_tile_info(c->tile_stats, out);
+    return STA_OK;
+}
 
 sta_status sta_plan_levels(const sta_design_desc *desc, int32_t *cell_level)
 {
@@ -599,6 +722,7 @@ void sta_destroy(sta_ctx *c)
     }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     for (void *p : c->allocs) cudaFree(p);
+    for (void *p : c->tile_allocs) cudaFree(p);
     delete c;
 }
 
@@ -646,8 +770,11 @@ sta_status sta_set_clock(sta_ctx *c, float period_ns)
 sta_status sta_set_schedule(sta_ctx *c, int32_t schedule, int32_t param)
 {
     if (!c) return STA_EINVAL;
-    if (schedule != STA_SCHED_LEVEL && schedule != STA_SCHED_DATAFLOW && schedule != STA_SCHED_COOP)
+    if (schedule != STA_SCHED_LEVEL && schedule != STA_SCHED_DATAFLOW && schedule != STA_SCHED_COOP &&
+        schedule != STA_SCHED_TILE)
         return fail(c, STA_EINVAL, "unknown schedule");
+    if (schedule == STA_SCHED_TILE && c->plan.S + 1 > sta::tile_max_steps())
+        return fail(c, STA_EINVAL, "too many levels for the tile schedule");
     if (schedule == STA_SCHED_LEVEL && param != 0 && (param < 32 || param > 1024 || param % 32))
         return fail(c, STA_EINVAL, "threads per block must be a multiple of 32 in [32, 1024]");
     if (schedule != STA_SCHED_LEVEL && (param < 0 || param > 65535))
@@ -669,6 +796,27 @@ sta_status sta_set_schedule(sta_ctx *c, int32_t schedule, int32_t param)
         if (e != cudaSuccess) {
             c->schedule = STA_SCHED_LEVEL;
             return fail(c, STA_ECUDA, std::string("cooperative set-up: ") + cudaGetErrorString(e));
+        }
+    } else if (schedule == STA_SCHED_TILE) {
+        int max_blocks = 0, sms = 0;
+        cudaError_t e = sta::tile_prepare(c->hs, c->dc.gamma > 0.f, c->plan.S + 1, &max_blocks);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, c->device);
+        if (e != cudaSuccess) {
+            c->schedule = STA_SCHED_LEVEL;
+            return fail(c, STA_ECUDA, std::string("tile set-up: ") + cudaGetErrorString(e));
+        }
+        const int B = param > 0 ? param : std::min(sms, max_blocks);
+        if (B > max_blocks) {
+            c->schedule = STA_SCHED_LEVEL;
+            return fail(c, STA_EINVAL, "more tiles than co-resident blocks of the tile kernels (" +
+                                           std::to_string(max_blocks) + ")");
+        }
+        try {
+            build_tiles(c, B);
+        } catch (const CudaFail &f) {
+            c->schedule = STA_SCHED_LEVEL;
+            free_tiles(c);
+            return from_cuda(c, f);
         }
     } else {
         const cudaError_t e = sta::dataflow_prepare(c->hs, c->dc.gamma > 0.f, param);
@@ -761,7 +909,8 @@ sta_status sta_autotune(sta_ctx *c, void *stream, int32_t trials, int32_t force,
             std::vector<std::pair<int, int>> cand = {{STA_SCHED_LEVEL, 64}, {STA_SCHED_LEVEL, 128},
                                                      {STA_SCHED_LEVEL, 256}, {STA_SCHED_DATAFLOW, 0},
                                                      {STA_SCHED_DATAFLOW, sms}, {STA_SCHED_DATAFLOW, 2 * sms},
-                                                     {STA_SCHED_COOP, 0}, {STA_SCHED_COOP, sms}};
+                                                     {STA_SCHED_COOP, 0}, {STA_SCHED_COOP, sms},
+                                                     {STA_SCHED_TILE, sms}, {STA_SCHED_TILE, 2 * sms}};
             cudaEvent_t e0, e1;
             CK(cudaEventCreate(&e0));
             CK(cudaEventCreate(&e1));

@@ -20,7 +20,7 @@ from .build import LIB
 OK, EINVAL, ECYCLE, ENOMEM, ECUDA, ETIMEOUT, ESTATE = range(7)
 HOST, DEVICE = 0, 1
 AT, SLEW, RAT, SLACK = 0, 1, 2, 3
-SCHED_LEVEL, SCHED_DATAFLOW, SCHED_COOP = 0, 1, 2
+SCHED_LEVEL, SCHED_DATAFLOW, SCHED_COOP, SCHED_TILE = 0, 1, 2, 3
 NET_ELMORE, NET_ARNOLDI = 0, 1
 WIRE_STAR, WIRE_STEINER = 0, 1
 
@@ -66,6 +66,16 @@ class sta_plan_info(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class sta_tile_info(C.Structure):
+    _fields_ = [("n_tiles", C.c_int32), ("n_steps", C.c_int32), ("wave_items", C.c_int32),
+                ("ring_slots", C.c_int32), ("max_step_entries", C.c_int32), ("pad", C.c_int32),
+                ("fwd_edges", C.c_int64), ("fwd_local", C.c_int64), ("bwd_edges", C.c_int64),
+                ("bwd_local", C.c_int64), ("crit_edges", C.c_int64), ("crit_local", C.c_int64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
 class sta_corner_report(C.Structure):
     _fields_ = [("wns_setup", C.c_double), ("tns_setup", C.c_double), ("wns_hold", C.c_double),
                 ("tns_hold", C.c_double), ("worst_setup", C.c_double), ("worst_hold", C.c_double),
@@ -86,6 +96,8 @@ SIGNATURES = {
     "sta_plan": (C.c_int, [_P, C.POINTER(sta_plan_info)]),
     "sta_plan_error": (C.c_char_p, []),
     "sta_plan_levels": (C.c_int, [_P, _P]),
+    "sta_plan_tiles": (C.c_int, [_P, C.c_int32, C.POINTER(sta_tile_info)]),
+    "sta_get_tile_info": (C.c_int, [_V, C.POINTER(sta_tile_info)]),
     "sta_create": (C.c_int, [_P, C.c_int, C.POINTER(C.c_void_p)]),
     "sta_create_batch": (C.c_int, [_P, C.c_int32, C.c_int, C.POINTER(C.c_void_p)]),
     "sta_set_rc": (C.c_int, [_V, _P, _P, C.c_int]),
@@ -225,6 +237,18 @@ def sta_plan(design) -> dict:
     return info.as_dict()
 
 
+def sta_plan_tiles(design, n_tiles: int) -> dict:
+    """Host-only: the tile schedule's partition into ``n_tiles`` tiles,
+    checked by replaying the kernels' ring use; its statistics."""
+    lib = load()
+    dd = design if isinstance(design, Design) else Design(design)
+    info = sta_tile_info()
+    st = lib.sta_plan_tiles(C.byref(dd.desc), int(n_tiles), C.byref(info))
+    if st != OK:
+        raise StaError(st, lib.sta_plan_error().decode())
+    return info.as_dict()
+
+
 def sta_plan_levels(design) -> np.ndarray:
     """Host-only: propagation level of every cell."""
     lib = load()
@@ -275,6 +299,12 @@ class Context:
     def stats(self) -> dict:
         info = sta_plan_info()
         self._chk(self.lib.sta_stats(self.h, C.byref(info)))
+        return info.as_dict()
+
+    def tile_info(self) -> dict:
+        """Statistics of the current tile partition (zeros unless SCHED_TILE)."""
+        info = sta_tile_info()
+        self._chk(self.lib.sta_get_tile_info(self.h, C.byref(info)))
         return info.as_dict()
 
     def set_schedule(self, schedule: int, param: int = 0):

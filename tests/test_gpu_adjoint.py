@@ -55,7 +55,8 @@ def test_objective_and_gradient_small(w):
     check_grad(g, g0)
 
 
-@pytest.mark.parametrize("schedule", [sta.SCHED_DATAFLOW, sta.SCHED_COOP], ids=["dataflow", "coop"])
+@pytest.mark.parametrize("schedule", [sta.SCHED_DATAFLOW, sta.SCHED_COOP, sta.SCHED_TILE],
+                         ids=["dataflow", "coop", "tile"])
 def test_every_forward_schedule_gives_the_same_gradient(schedule):
     d = placed(2000, 15, 4)
     a = gpu_grad(d, schedule=schedule)

@@ -30,7 +30,7 @@ def designs(corners=2):
             for i, (n, dep) in enumerate([(300, 8), (2000, 25), (800, 12), (5000, 30), (40, 3)])]
 
 
-@pytest.mark.parametrize("schedule", [sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP])
+@pytest.mark.parametrize("schedule", [sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP, sta.SCHED_TILE])
 def test_batch_equals_separate_contexts(schedule):
     ds = designs()
     bctx = sta.Context(None, batch=ds)
@@ -96,7 +96,7 @@ def test_batch_with_exceptions_equals_separate_contexts():
     bctx = sta.Context(None, batch=ds)
     assert bctx.stats()["n_tags"] == 1 + sum(len(d.get("exc_action", [])) for d in ds) + \
         int(ds[2].get("exc_thru_ptr", [0])[-1])
-    for schedule in (sta.SCHED_DATAFLOW, sta.SCHED_COOP):
+    for schedule in (sta.SCHED_DATAFLOW, sta.SCHED_COOP, sta.SCHED_TILE):
         bctx.set_schedule(schedule)
         bctx.update_timing()
         es, eh, vs, vh = bctx.get_endpoint_slack()

@@ -59,7 +59,7 @@ cases["steiner_grad"] = dict(synth.make_design(3000, 15, seed=5, placed=True, pl
 cases["steiner_fanout_grad"] = dict(fan, gamma_ns=0.01)
 for name, d in cases.items():
     ref = oracle.sta(d)
-    for sch in (sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP):
+    for sch in (sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP, sta.SCHED_TILE):
         ctx = sta.Context(d)
         ctx.set_schedule(sch)
         ctx.update_timing()
@@ -72,7 +72,7 @@ for name, d in cases.items():
         ctx.close()
 batch = synth.batch_workload(seed=0, n_designs=3, lo=500, hi=3000, depth=12)
 b = sta.Context(None, batch=batch)
-for sch in (sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP):
+for sch in (sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP, sta.SCHED_TILE):
     b.set_schedule(sch)
     b.update_timing()
     b.sync()

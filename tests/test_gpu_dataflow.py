@@ -71,7 +71,11 @@ def _case(case):
 CASES = ["tiny", "corners", "star", "smooth", "fixed", "big_rc"]
 
 
-@pytest.mark.parametrize("schedule", [sta.SCHED_DATAFLOW, sta.SCHED_COOP], ids=["dataflow", "coop"])
+PERSISTENT = [sta.SCHED_DATAFLOW, sta.SCHED_COOP, sta.SCHED_TILE]
+PERSISTENT_IDS = ["dataflow", "coop", "tile"]
+
+
+@pytest.mark.parametrize("schedule", PERSISTENT, ids=PERSISTENT_IDS)
 @pytest.mark.parametrize("case", CASES)
 def test_persistent_schedules_match_level_and_oracle(case, schedule):
     d = _case(case)
@@ -81,17 +85,19 @@ def test_persistent_schedules_match_level_and_oracle(case, schedule):
     check_all(d, g, ref, exact_viol=case in ("tiny", "star", "smooth") and _hold_margin_ok(ref))
 
 
-@pytest.mark.parametrize("schedule", [sta.SCHED_DATAFLOW, sta.SCHED_COOP], ids=["dataflow", "coop"])
+@pytest.mark.parametrize("schedule", PERSISTENT, ids=PERSISTENT_IDS)
 @pytest.mark.parametrize("blocks", [1, 3, 148])
 def test_small_persistent_grids_make_progress(blocks, schedule):
     """One resident block (8 warps) must still finish: dataflow chunks are
     taken in order and only wait for earlier chunks; the cooperative grid
-    strides over every level whatever its size."""
+    strides over every level whatever its size; a tile schedule of one
+    tile runs every level in one block (many waves per level, most ring
+    slots overwritten before use, so most reads go through the mailbox)."""
     d = synth.make_design(5000, 40, seed=11, period_ns=2.5)
     same(run(d, schedule, blocks), run(d, sta.SCHED_LEVEL))
 
 
-@pytest.mark.parametrize("schedule", [sta.SCHED_DATAFLOW, sta.SCHED_COOP], ids=["dataflow", "coop"])
+@pytest.mark.parametrize("schedule", PERSISTENT, ids=PERSISTENT_IDS)
 def test_degenerate_designs_persistent(schedule):
     lib = synth.make_library(1)
     b = synth.Builder(lib)
@@ -113,10 +119,11 @@ def test_degenerate_designs_persistent(schedule):
     same(run(d, schedule), run(d, sta.SCHED_LEVEL))
 
 
-def test_repeated_dataflow_updates_are_identical():
+@pytest.mark.parametrize("schedule", [sta.SCHED_DATAFLOW, sta.SCHED_TILE], ids=["dataflow", "tile"])
+def test_repeated_dataflow_updates_are_identical(schedule):
     d = synth.workload("tiny", seed=2)
     ctx = sta.Context(d)
-    ctx.set_schedule(sta.SCHED_DATAFLOW)
+    ctx.set_schedule(schedule)
     ctx.update_timing()
     first = {k: ctx.get_pin_state(w).copy() for k, w in ARRAYS}
     for _ in range(3):
@@ -126,11 +133,12 @@ def test_repeated_dataflow_updates_are_identical():
     ctx.close()
 
 
-def test_wait_limit_reports_timeout_and_context_recovers():
+@pytest.mark.parametrize("schedule", [sta.SCHED_DATAFLOW, sta.SCHED_TILE], ids=["dataflow", "tile"])
+def test_wait_limit_reports_timeout_and_context_recovers(schedule):
     d = synth.workload("tiny", seed=0)
     ref = oracle.sta(d)
     ctx = sta.Context(d)
-    ctx.set_schedule(sta.SCHED_DATAFLOW)
+    ctx.set_schedule(schedule)
     ctx.update_timing()
     ctx.sync()
     # a gate of level 1: its output flag is withheld, its fan-out waits run out
@@ -176,16 +184,31 @@ def test_coop_barrier_wait_limit_reports_timeout_and_context_recovers():
 
 
 def test_scale_design_persistent_full_size():
-    """The 1M-cell workload under the dataflow and cooperative schedules,
-    against the oracle and bit-identical to the level schedule."""
+    """The 1M-cell workload under the dataflow, cooperative and tile
+    schedules, against the oracle and bit-identical to the level schedule."""
     d = synth.workload("scale", seed=0)
     d["period_ns"], _ = tune_period(d)
     lv = run(d, sta.SCHED_LEVEL)
     ref = oracle.sta(d)
-    for schedule in (sta.SCHED_DATAFLOW, sta.SCHED_COOP):
+    for schedule in (sta.SCHED_DATAFLOW, sta.SCHED_COOP, sta.SCHED_TILE):
         g = run(d, schedule)
         same(g, lv)
         check_all(d, g, ref, exact_viol=_hold_margin_ok(ref))
+
+
+def test_tile_schedule_rejects_more_tiles_than_resident_blocks():
+    d = synth.make_design(2000, 20, seed=3)
+    ctx = sta.Context(d)
+    with pytest.raises(sta.StaError) as ei:
+        ctx.set_schedule(sta.SCHED_TILE, 60000)
+    assert ei.value.status == sta.EINVAL
+    # the context still works on another schedule
+    ctx.set_schedule(sta.SCHED_TILE, 0)
+    ctx.update_timing()
+    ctx.sync()
+    info = ctx.tile_info()
+    assert info["n_tiles"] > 0 and info["crit_local"] <= info["crit_edges"]
+    ctx.close()
 
 
 def test_autotune_selects_a_schedule_and_keeps_results():
@@ -194,7 +217,7 @@ def test_autotune_selects_a_schedule_and_keeps_results():
     ref = oracle.sta(d)
     ctx = sta.Context(d)
     sch, par, ms = ctx.autotune(trials=3)
-    assert sch in (sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP) and ms > 0
+    assert sch in (sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP, sta.SCHED_TILE) and ms > 0
     assert_close("at", ctx.get_pin_state(sta.AT), ref["at"])
     assert_close("slack", ctx.get_pin_state(sta.SLACK), ref["slack"])
     t0 = time.perf_counter()

@@ -17,7 +17,7 @@ from tests.test_gpu_paths import check_paths
 
 pytestmark = pytest.mark.gpu
 
-SCHEDULES = [sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP]
+SCHEDULES = [sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP, sta.SCHED_TILE]
 
 
 @pytest.fixture(scope="module", autouse=True)

@@ -216,7 +216,7 @@ def test_scale_design_sampled_full_size():
     print("1M parity max abs err", {k: v[0] for k, v in errs.items()})
 
 
-@pytest.mark.parametrize("schedule", [sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP])
+@pytest.mark.parametrize("schedule", [sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP, sta.SCHED_TILE])
 def test_high_fanout_net(schedule):
     """One primary input drives 1,500 gates (more sinks than a shared-memory
     RC tile holds, so its net is swept in global scratch) and a long fan-out
@@ -256,7 +256,7 @@ def test_arnoldi_net_model_parity(case):
     d["period_ns"], _ = tune_period(d)
     ref = oracle.sta(d)
     outs = []
-    for sch in (sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP):
+    for sch in (sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP, sta.SCHED_TILE):
         ctx = sta.Context(d)
         ctx.set_schedule(sch)
         ctx.update_timing()

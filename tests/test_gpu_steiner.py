@@ -14,7 +14,7 @@ from tests.test_gpu_parity import _hold_margin_ok, check_all
 
 pytestmark = pytest.mark.gpu
 
-SCHEDULES = [sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP]
+SCHEDULES = [sta.SCHED_LEVEL, sta.SCHED_DATAFLOW, sta.SCHED_COOP, sta.SCHED_TILE]
 
 
 @pytest.fixture(scope="module", autouse=True)

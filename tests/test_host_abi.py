@@ -290,3 +290,48 @@ def test_noalloc_rejects_bad_arguments_on_the_host(lib):
     assert lib.sta_reduce_slack_noalloc(None, dummy, 10, 1, dummy, None) == sta.EINVAL
     assert lib.sta_reduce_slack_noalloc(dummy, dummy, -1, 1, dummy, None) == sta.EINVAL
     assert lib.sta_reduce_slack_noalloc(dummy, dummy, 10, 0, dummy, None) == sta.EINVAL
+
+
+@pytest.mark.parametrize("case", ["tiny", "corners", "exceptions", "placed", "one_level"])
+@pytest.mark.parametrize("n_tiles", [1, 3, 148])
+def test_tile_partition_replays_clean(lib, case, n_tiles):
+    """The tile schedule's partition (host): every item and endpoint in one
+    list at its level, and every shared-memory ring read finds its producer
+    when the kernels' writes are replayed wave by wave (sta_plan_tiles fails
+    otherwise)."""
+    if case == "tiny":
+        d = synth.workload("tiny", seed=0)
+    elif case == "corners":
+        ls, rs = synth.lut_corners()
+        d = synth.make_design(5000, 25, seed=4, n_corners=4, lut_scale=ls, rc_scale=rs)
+    elif case == "exceptions":
+        d = synth.make_design(4000, 20, seed=2)
+        d.update(synth.exception_groups(d, np.random.default_rng(1), 3, div_from=5, div_to=4, max_thru=2,
+                                        div_thru=16))
+    elif case == "placed":
+        d = synth.make_design(6000, 30, seed=7, placed=True)
+    else:
+        d = synth.make_design(3000, 1, seed=5)
+    info = sta.sta_plan_tiles(d, n_tiles)
+    assert info["n_tiles"] == n_tiles
+    assert info["n_steps"] == sta.sta_plan(d)["n_levels"] + 1
+    assert 0 <= info["fwd_local"] <= info["fwd_edges"]
+    assert 0 <= info["bwd_local"] <= info["bwd_edges"]
+    assert 0 <= info["crit_local"] <= info["crit_edges"]
+    assert info["wave_items"] * info["ring_slots"] > 0
+
+
+def test_tile_partition_keeps_critical_edges_local(lib):
+    """On the 60k-cell generator design with one tile per SM, almost every
+    critical fan-in edge (the one that sets an item's level) stays inside
+    its tile, and the step lists stay within one wave of 64 items."""
+    d = synth.make_design(60000, 60, seed=1)
+    info = sta.sta_plan_tiles(d, 148)
+    assert info["crit_local"] >= 0.95 * info["crit_edges"]
+    assert info["fwd_local"] >= 0.4 * info["fwd_edges"]
+
+
+def test_tile_partition_rejects_bad_tile_count(lib):
+    d = synth.workload("tiny", seed=0)
+    with pytest.raises(sta.StaError):
+        sta.sta_plan_tiles(d, 0)
