@@ -134,9 +134,12 @@ def make_design(n_cells: int, depth: int, seed: int = 0, lib: dict | None = None
       the DFF Q pins.  DFF D pins are driven from any level.
     * Every driver draws a weight from a geometric law of mean
       ``fanout_mean`` and is picked with probability proportional to it.
-    * A driver nobody picked drives a primary output (so every net has a sink;
-      all last-level outputs become POs); ``po_frac * n_cells`` further
-      drivers get an extra primary output (observation points).
+    * A cell output nobody picked drives a primary output (all last-level
+      outputs become POs); ``po_frac * n_cells`` further cell outputs get an
+      extra primary output (observation points).  No primary output is fed
+      straight from a primary input (its hold slack would be the bare net
+      delay, inside the tolerance of zero); a primary input nobody picked
+      has no sinks.
     * RC per net: ``rc_nodes`` inclusive node-count range, parent of node i
       uniform in [0, i), R ~ U(5, 50) Ohm (root 0), C ~ U(0.5, 5) fF; each
       sink sits on a uniform non-root node.
@@ -210,10 +213,17 @@ def make_design(n_cells: int, depth: int, seed: int = 0, lib: dict | None = None
     sink_pin = np.concatenate([gate_pin0[g_of_slot] + slot_of, dff_pin0]).astype(np.int64)
     sink_drv = np.concatenate([slot_drv, d_drv]).astype(np.int64)
     fan = np.bincount(sink_drv, minlength=n_drv)
-    lonely = np.nonzero(fan == 0)[0]
-    # observation points: extra primary outputs on random drivers
+    # A cell output nobody picked drives a primary output; a primary input
+    # nobody picked stays a port without sinks.  No primary output hangs
+    # straight off a primary input: such a feed-through's hold slack would be
+    # its net delay alone (~1e-4 ns), inside the FP32 tolerance of zero, and
+    # its hold violation flag would not be well defined.
+    lonely = np.nonzero(fan[n_pi:] == 0)[0] + n_pi
+    # observation points: extra primary outputs on random cell outputs
     n_tap = int(round(po_frac * n_cells))
-    taps = rng.choice(n_drv, size=min(n_tap, n_drv), replace=False) if n_tap > 0 else np.zeros(0, np.int64)
+    n_cell_drv = n_drv - n_pi
+    taps = (rng.choice(n_cell_drv, size=min(n_tap, n_cell_drv), replace=False) + n_pi if n_tap > 0 and n_cell_drv > 0
+            else np.zeros(0, np.int64))
     lonely = np.concatenate([lonely, np.setdiff1d(taps, lonely)])
     n_po = len(lonely)
     po_pin = n_cell_pins + n_pi + np.arange(n_po)

@@ -279,3 +279,125 @@ def enumerate_paths_from(d, corner=0, with_pins=False):
     if with_pins:
         return allp
     return {p: [(a, rf, s) for a, rf, s, _ in v] for p, v in allp.items()}
+
+
+def _lse(xs, gamma, late):
+    """gamma * log sum exp(x / gamma) (late) or its mirror -gamma * log sum
+    exp(-x / gamma) (early), by numpy's logaddexp over the listed values."""
+    x = np.asarray(xs, np.float64)
+    return gamma * np.logaddexp.reduce(x / gamma) if late else -gamma * np.logaddexp.reduce(-x / gamma)
+
+
+def smoothed_forward(d, gamma, corner=0):
+    """Arrival and slew of every pin, [pin][4] with index el*2 + rf, when every
+    fan-in merge (arrival and slew) is the smooth max / min of the
+    differentiable reading: each gate output lists all its arc candidates
+    (input arrival + NLDM delay at the input slew and the output load, and
+    the NLDM slew) and merges them at once with ``_lse``; net arcs add the
+    shared-path Elmore delay and combine slews as sqrt(s^2 + var)."""
+    net = Net(d, corner)
+    sc = float(np.asarray(d["lut_scale"])[corner])
+    role = np.asarray(d["pin_role"])
+    ctype = np.asarray(d["cell_type"])
+    cpp = np.asarray(d["cell_pin_ptr"])
+    cp = np.asarray(d["cell_pin"])
+    sense = np.asarray(d["arc_sense"]).reshape(-1, 3)
+    nin = np.asarray(d["type_nin"])
+    i1 = np.asarray(d["lut_idx1"]).reshape(-1, 3, 4, 7)
+    i2 = np.asarray(d["lut_idx2"]).reshape(-1, 3, 4, 7)
+    vv = np.asarray(d["lut_val"]).reshape(-1, 3, 4, 49)
+    memo = {}
+
+    def st(p):
+        if p in memo:
+            return memo[p]
+        r = role[p]
+        if r == PI:
+            out = (np.full(4, float(d["pi_at_ns"])), np.full(4, float(d["pi_slew_ns"])))
+        elif r == CK:
+            out = (np.zeros(4), np.full(4, float(d["clk_slew_ns"])))
+        elif r in (IN, D, PO):
+            a, s = st(net.driver[p])
+            out = (a + net.Dns[p], np.sqrt(s * s + net.Vns[p]))
+        else:
+            c = net.cell_of[p]
+            t = ctype[c]
+            l = net.load.get(p, 0.0)
+            at, sl = np.zeros(4), np.zeros(4)
+            for el in (0, 1):
+                for rfo in (0, 1):
+                    ca, cs = [], []
+                    for slot in range(nin[t]):
+                        se = sense[t, slot]
+                        if se == NONE:
+                            continue
+                        aa, ss = st(int(cp[cpp[c] + slot]))
+                        for rfi in rf_in_of(se, rfo):
+                            s_in = ss[el * 2 + rfi]
+                            ca.append(aa[el * 2 + rfi] + sc * bilinear(i1[t, slot, rfo], i2[t, slot, rfo],
+                                                                       vv[t, slot, rfo], s_in, l))
+                            cs.append(sc * bilinear(i1[t, slot, 2 + rfo], i2[t, slot, 2 + rfo],
+                                                    vv[t, slot, 2 + rfo], s_in, l))
+                    at[el * 2 + rfo] = _lse(ca, gamma, el == 1)
+                    sl[el * 2 + rfo] = _lse(cs, gamma, el == 1)
+            out = (at, sl)
+        memo[p] = out
+        return out
+
+    res = [st(p) for p in range(d["n_pins"])]
+    return np.array([r[0] for r in res]), np.array([r[1] for r in res])
+
+
+def enumerate_paths_at_slews(d, slew, corner=0):
+    """Every path's (late arrival, edge) at every pin when each cell arc's
+    delay is read at the slew the analysis computed for the arc's input pin
+    and edge (``slew`` [pin][4], late components used) and the output load:
+    path delays are then additive, and the latest path to a pin is its
+    graph-based arrival."""
+    net = Net(d, corner)
+    sc = float(np.asarray(d["lut_scale"])[corner])
+    role = np.asarray(d["pin_role"])
+    ctype = np.asarray(d["cell_type"])
+    cpp = np.asarray(d["cell_pin_ptr"])
+    cp = np.asarray(d["cell_pin"])
+    sense = np.asarray(d["arc_sense"]).reshape(-1, 3)
+    nin = np.asarray(d["type_nin"])
+    i1 = np.asarray(d["lut_idx1"]).reshape(-1, 3, 4, 7)
+    i2 = np.asarray(d["lut_idx2"]).reshape(-1, 3, 4, 7)
+    vv = np.asarray(d["lut_val"]).reshape(-1, 3, 4, 49)
+    slew = np.asarray(slew, np.float64)
+    memo = {}
+
+    def paths(p):
+        if p in memo:
+            return memo[p]
+        r = role[p]
+        if r == PI:
+            out = [(float(d["pi_at_ns"]), rf) for rf in (0, 1)]
+        elif r == CK:
+            out = [(0.0, rf) for rf in (0, 1)]
+        elif r in (IN, D, PO):
+            out = [(a + net.Dns[p], rf) for a, rf in paths(net.driver[p])]
+        else:
+            c = net.cell_of[p]
+            t = ctype[c]
+            l = net.load.get(p, 0.0)
+            out = []
+            for slot in range(nin[t]):
+                se = sense[t, slot]
+                if se == NONE:
+                    continue
+                a_pin = int(cp[cpp[c] + slot])
+                for a, rf in paths(a_pin):
+                    if r == Q and rf != 0:
+                        continue
+                    for rfo in (0, 1):
+                        if rf not in rf_in_of(se, rfo):
+                            continue
+                        dl = sc * bilinear(i1[t, slot, rfo], i2[t, slot, rfo], vv[t, slot, rfo],
+                                           slew[a_pin, 2 + rf], l)
+                        out.append((a + dl, rfo))
+        memo[p] = out
+        return out
+
+    return {p: paths(p) for p in range(d["n_pins"])}

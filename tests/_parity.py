@@ -37,6 +37,24 @@ def assert_close(name, gpu, ref, abs_tol=ABS_TOL, rel_tol=REL_TOL):
     return ea, er
 
 
+VIOL_MARGIN = ABS_TOL   # ns
+
+
+def assert_viol_defined(ref, margin: float = VIOL_MARGIN):
+    """Endpoint violation sets are well defined when every finite endpoint
+    slack of the oracle lies farther than the tolerance from zero: a GPU
+    value within tolerance then has the same sign (|err| <= max(1e-4, 1e-5
+    |ref|) < |ref|), so the sets must agree bit for bit.  Fails (it does not
+    skip) when a design or clock period breaks that."""
+    for key in ("ep_setup", "ep_hold"):
+        v = np.asarray(ref[key], np.float64)
+        v = v[np.isfinite(v)]
+        if v.size:
+            worst = float(np.abs(v).min())
+            assert worst > margin, ("%s: an endpoint slack %.3g ns from zero, within the %.0e ns tolerance: "
+                                    "the violation set is not well defined for this design" % (key, worst, margin))
+
+
 def tune_period(d: dict, bands=((0.89, 0.91), (0.88, 0.92), (0.87, 0.93), (0.85, 0.95)),
                 min_half_gap: float = 1e-4):
     """Clock period in the widest gap between consecutive endpoint setup

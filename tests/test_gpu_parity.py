@@ -11,7 +11,7 @@ import pytest
 
 import oracle
 from paper_2511_11660_b300 import sta, synth
-from tests._parity import assert_close, tune_period
+from tests._parity import assert_close, assert_viol_defined, tune_period
 
 pytestmark = pytest.mark.gpu
 
@@ -38,7 +38,12 @@ def run_both(d, schedule=None, param=0):
     return out, ref
 
 
-def check_all(d, g, ref, exact_viol=True):
+def check_all(d, g, ref, exact_viol=True, require_margin=True):
+    """Every per-pin array and endpoint slack within tolerance, the FP64
+    reductions, and (exact_viol) the setup and hold violation flags and
+    counts bit for bit -- after asserting that the oracle's endpoint slacks
+    keep clear of zero (require_margin), so that the sets are well
+    defined."""
     errs = {}
     for k in ("at", "slew", "rat", "slack"):
         errs[k] = assert_close(k, g[k], ref[k])
@@ -58,15 +63,13 @@ def check_all(d, g, ref, exact_viol=True):
         assert abs(rep["tns_setup"] - ref["tns_setup"][k]) <= nv * 1e-4 + 1e-5 * abs(ref["tns_setup"][k])
         assert abs(rep["wns_setup"] - ref["wns_setup"][k]) <= 1e-4 + 1e-5 * abs(ref["wns_setup"][k])
         if exact_viol:
+            if require_margin:
+                assert_viol_defined(ref)
             np.testing.assert_array_equal(g["viol_setup"][:, k], (ref["ep_setup"][:, k] < 0).astype(np.uint8))
             np.testing.assert_array_equal(g["viol_hold"][:, k], (ref["ep_hold"][:, k] < 0).astype(np.uint8))
             assert rep["n_viol_setup"] == ref["n_viol_setup"][k]
             assert rep["n_viol_hold"] == ref["n_viol_hold"][k]
     return errs
-
-
-def _hold_margin_ok(ref, margin=2e-4):
-    return bool(np.all(np.abs(ref["ep_hold"]) > margin))
 
 
 @pytest.mark.parametrize("seed", [0, 1, 2])
@@ -75,7 +78,7 @@ def test_tiny_design_parity(seed):
     d["period_ns"], half = tune_period(d)
     g, ref = run_both(d)
     assert 0.05 < ref["n_viol_setup"][0] / len(ref["endpoints"]) < 0.2
-    check_all(d, g, ref, exact_viol=_hold_margin_ok(ref))
+    check_all(d, g, ref)
 
 
 @pytest.mark.parametrize("threads", [32, 64, 256])
@@ -84,28 +87,28 @@ def test_block_sizes_and_ragged_levels(threads):
     d = synth.make_design(6001, 9, seed=7)
     d["period_ns"], _ = tune_period(d)
     g, ref = run_both(d, sta.SCHED_LEVEL, threads)
-    check_all(d, g, ref, exact_viol=_hold_margin_ok(ref))
+    check_all(d, g, ref)
 
 
 def test_multi_corner_parity():
     ls, rs = synth.lut_corners()
     d = synth.make_design(3000, 20, seed=4, n_corners=4, lut_scale=ls, rc_scale=rs, period_ns=1.7)
     g, ref = run_both(d)
-    check_all(d, g, ref, exact_viol=False)
+    check_all(d, g, ref)
 
 
 def test_star_rc_from_positions_parity():
     d = synth.make_design(3000, 15, seed=5, placed=True)
     d["period_ns"], _ = tune_period(d)
     g, ref = run_both(d)
-    check_all(d, g, ref, exact_viol=_hold_margin_ok(ref))
+    check_all(d, g, ref)
 
 
 def test_smoothed_merges_parity():
     d = synth.make_design(3000, 15, seed=6, gamma_ns=0.01)
     d["period_ns"], _ = tune_period(d)
     g, ref = run_both(d)
-    check_all(d, g, ref, exact_viol=_hold_margin_ok(ref))
+    check_all(d, g, ref)
 
 
 def test_large_rc_trees_use_global_sweeps():
@@ -118,17 +121,18 @@ def test_large_rc_trees_use_global_sweeps():
     d["rc_R"] = (d["rc_R"] * 0.1).astype(np.float32)
     d["rc_C"] = (d["rc_C"] * 0.01).astype(np.float32)
     g, ref = run_both(d)
-    check_all(d, g, ref, exact_viol=False)
+    check_all(d, g, ref)
 
 
 def test_degenerate_designs():
     lib = synth.make_library(1)
-    # PI straight to PO
+    # PI straight to PO: its hold slack is the bare net delay, near zero, so
+    # the flags are compared without the margin precondition
     b = synth.Builder(lib)
     b.po(b.pi())
     d = b.design(period_ns=0.3)
     g, ref = run_both(d)
-    check_all(d, g, ref)
+    check_all(d, g, ref, require_margin=False)
     # flip-flop ring with one gate: Q -> INV -> D of itself, plus an unused output
     b = synth.Builder(lib)
     x = b.pi()
@@ -147,10 +151,10 @@ def test_single_cell_and_fixed_delay():
     lib = synth.make_library(2, fixed_delay=True)
     d = synth.make_design(1, 1, seed=3, lib=lib)
     g, ref = run_both(d)
-    check_all(d, g, ref, exact_viol=False)
+    check_all(d, g, ref)
     d = synth.make_design(800, 40, seed=3, lib=lib)
     g, ref = run_both(d)
-    check_all(d, g, ref, exact_viol=False)
+    check_all(d, g, ref)
 
 
 def test_repeated_updates_are_identical():
@@ -205,12 +209,14 @@ def test_set_rc_and_set_cell_types_match_fresh_contexts():
 
 
 def test_scale_design_sampled_full_size():
-    """The 1M-cell workload (depth 150, 2-10 RC nodes) in the launch
-    configuration the benchmark times: full comparison with the oracle."""
+    """The 1M-cell workload (depth 150, 2-10 RC nodes) on the default (level)
+    schedule: full comparison with the oracle, violation sets bit for bit.
+    The schedule the benchmark times is checked at this size in
+    test_gpu_dataflow.py."""
     d = synth.workload("scale", seed=0)
     d["period_ns"], half = tune_period(d)
     g, ref = run_both(d)
-    errs = check_all(d, g, ref, exact_viol=_hold_margin_ok(ref))
+    errs = check_all(d, g, ref)
     frac = ref["n_viol_setup"][0] / len(ref["endpoints"])
     assert 0.05 < frac < 0.15
     print("1M parity max abs err", {k: v[0] for k, v in errs.items()})

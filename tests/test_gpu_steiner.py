@@ -10,7 +10,7 @@ import pytest
 import oracle
 from paper_2511_11660_b300 import sta, synth
 from tests._parity import tune_period
-from tests.test_gpu_parity import _hold_margin_ok, check_all
+from tests.test_gpu_parity import check_all
 
 pytestmark = pytest.mark.gpu
 
@@ -77,7 +77,7 @@ def test_steiner_parity_all_schedules(case):
         ctx.set_schedule(sch)
         ctx.update_timing()
         np.testing.assert_array_equal(ctx.get_net_wirelength(), wl)
-        check_all(d, _gpu(ctx), ref, exact_viol=_hold_margin_ok(ref))
+        check_all(d, _gpu(ctx), ref)
     ctx.close()
 
 
@@ -122,6 +122,8 @@ def test_steiner_positions_update_and_device_output():
     ctx.update_timing()
     d2 = dict(d, cell_xy=xy)
     np.testing.assert_array_equal(ctx.get_net_wirelength(device=True).cpu().numpy(), oracle.net_wirelengths(d2))
+    # randomly moved cells: a position-update test, whose endpoint slacks are
+    # not placed in a gap, so the flags are left out
     check_all(d2, _gpu(ctx), oracle.sta(d2), exact_viol=False)
     ctx.close()
 

@@ -118,6 +118,24 @@ MUTANTS = [
     ("stgrad_y_uses_rx", "f * (ry * Rb[i] + 0.5 * cy", "f * (rx * Rb[i] + 0.5 * cy", 0),
     ("stgrad_parent_sign", "if (cq >= 0) grad_xy[2 * cq + ax] -= gl[ax] * sg;", "if (cq >= 0) grad_xy[2 * cq + ax] += gl[ax] * sg;", 0),
     ("stgrad_sink_var_scale", "Vb[pnode[k]] += 1e-12 * aV[s];", "Vb[pnode[k]] += 1e-6 * aV[s];", 0),
+    # O6 smoothed merges with several candidates (a single candidate is unchanged by each)
+    ("lse_half_gamma", "return late ? m + gamma * log(s) : m - gamma * log(s);",
+     "return late ? m + 0.5 * gamma * log(s) : m - 0.5 * gamma * log(s);", 0),
+    ("lse_max_only", "for (int i = 0; i < n; ++i) s += exp((late ? (x[i] - m) : (m - x[i])) / gamma);",
+     "for (int i = 0; i < n; ++i) s += (x[i] == m);", 0),
+    ("lse_flipped_offsets", "s += exp((late ? (x[i] - m) : (m - x[i])) / gamma);",
+     "s += exp((late ? (m - x[i]) : (x[i] - m)) / gamma);", 0),
+]
+
+# Mutants of the Python side of the oracle (oracle/__init__.py): the path
+# reports with a per-endpoint limit
+PY_SRC = os.path.join(ROOT, "oracle", "__init__.py")
+PY_MUTANTS = [
+    # the arc delay at the early slew instead of the late one: invisible when delays do not depend on slew
+    ("nworst_early_slew", "slew[a, 2 + rfi], load[p])[0]", "slew[a, rfi], load[p])[0]", 0),
+    ("nworst_input_load", "slew[a, 2 + rfi], load[p])[0]", "slew[a, 2 + rfi], load[a])[0]", 0),
+    ("nworst_endpoint_edge", "heapq.heappush(heap, (float(sl[2 + rf]), seq, rf, ()))",
+     "heapq.heappush(heap, (float(sl[2]), seq, rf, ()))", 0),
 ]
 
 
@@ -130,11 +148,12 @@ def _mutate(text: str, old: str, new: str, nth: int) -> str:
 
 
 def test_mutation_sites_exist():
-    text = open(SRC).read()
-    names = [m[0] for m in MUTANTS]
-    assert len(set(names)) == len(names)
-    for _, old, new, nth in MUTANTS:
-        assert _mutate(text, old, new, nth) != text
+    for src, muts in ((SRC, MUTANTS), (PY_SRC, PY_MUTANTS)):
+        text = open(src).read()
+        names = [m[0] for m in muts]
+        assert len(set(names)) == len(names)
+        for _, old, new, nth in muts:
+            assert _mutate(text, old, new, nth) != text
 
 
 @pytest.mark.parametrize("name,old,new,nth", MUTANTS, ids=[m[0] for m in MUTANTS])
@@ -146,5 +165,17 @@ def test_pins_reject_mutant(name, old, new, nth, tmp_path):
                         "-x", "-q", "-p", "tests._oracle_mutant"],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert "liboracle_mutant" not in r.stderr or r.returncode != 4, r.stderr[-2000:]
+    assert r.returncode == 1, "mutant %s survived the pins (exit %d):\n%s" % (name, r.returncode,
+                                                                            r.stdout[-1500:])
+
+
+@pytest.mark.parametrize("name,old,new,nth", PY_MUTANTS, ids=[m[0] for m in PY_MUTANTS])
+def test_pins_reject_python_mutant(name, old, new, nth, tmp_path):
+    src = tmp_path / "oracle_mutant.py"
+    src.write_text(_mutate(open(PY_SRC).read(), old, new, nth))
+    env = dict(os.environ, ORACLE_MUTANT_PY=str(src))
+    r = subprocess.run([sys.executable, "-m", "pytest", os.path.join(ROOT, "tests", "test_oracle_pins.py"),
+                        "-x", "-q", "-p", "tests._oracle_mutant"],
+                       cwd=ROOT, env=env, capture_output=True, text=True, timeout=300)
     assert r.returncode == 1, "mutant %s survived the pins (exit %d):\n%s" % (name, r.returncode,
                                                                             r.stdout[-1500:])

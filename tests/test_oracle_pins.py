@@ -472,6 +472,44 @@ def test_adjoint_single_path_closed_form():
     assert grad[0, 0] == pytest.approx(fd, rel=1e-6)
 
 
+def _multi_fanin_design(gamma):
+    """Gates with two to four arc candidates per output edge: NAND2 (two
+    inputs, negative unate), XOR2 (non-unate: two edges per input), AOI21,
+    MUX2 (unate data inputs, non-unate select) and a NOR2 after a flip-flop;
+    slew-dependent tables (noise on)."""
+    lib = synth.make_library(3)
+    b = synth.Builder(lib)
+    a, bb, c0 = b.pi(), b.pi(), b.pi()
+    n1 = b.cell("NAND2", [a, bb])
+    x1 = b.cell("XOR2", [n1, c0])
+    o1 = b.cell("AOI21", [x1, n1, a])
+    m1 = b.cell("MUX2", [o1, x1, bb])
+    q = b.cell("DFF", [m1])
+    z = b.cell("NOR2", [q, o1])
+    b.po(z)
+    b.po(m1)
+    return b.design(period_ns=1.0, gamma_ns=gamma, default_R=40.0, default_C=3.0)
+
+
+@pytest.mark.parametrize("gamma", [0.01, 0.003])
+def test_smoothed_merges_match_independent_log_sum_exp(gamma):
+    """Reading (differentiable mode, gamma > 0): every fan-in merge of
+    arrivals and of slews is gamma log-sum-exp over the arc candidates
+    (late; early the mirror).  Recomputed on gates with two to four
+    candidates per edge by listing every candidate with the independent net
+    sums and bilinear form and merging all at once with numpy's logaddexp --
+    not the oracle's running max-shifted sum -- on a hand-built design and a
+    generated one.  The smoothing is visible: the hard merges differ by far
+    more than the tolerance."""
+    for d in (_multi_fanin_design(gamma), synth.make_design(300, 10, seed=4, gamma_ns=gamma)):
+        r = oracle.sta(d)
+        at, sl = _indep.smoothed_forward(d, gamma)
+        np.testing.assert_allclose(r["at"][:, 0, :], at, rtol=1e-12, atol=1e-14)
+        np.testing.assert_allclose(r["slew"][:, 0, :], sl, rtol=1e-12, atol=1e-14)
+        hard = oracle.sta(dict(d, gamma_ns=0.0))
+        assert np.max(np.abs(hard["at"][:, 0, :] - r["at"][:, 0, :])) > 1e-3
+
+
 @pytest.mark.parametrize("resistive", [False, True])
 def test_adjoint_matches_central_differences(resistive):
     """dJ/d(x, y) of the oracle's adjoint against central differences of its
@@ -1364,6 +1402,44 @@ def test_nworst_paths_match_brute_force_fixed_delay(seed):
             assert any(abs(a - at[-1]) < 1e-12 and rf == rfs[-1] for a, _, rf in allp[int(pins[-1])])
             e = int(pins[-1])
             assert pth["slack"] == pytest.approx(res["rat"][e, 0, 2 + rfs[-1]] - at[-1], abs=1e-12)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_nworst_paths_match_brute_force_slew_dependent(seed):
+    """Reading 15 on slew-dependent tables: a path's arrival adds each cell
+    arc's delay at the analysis' own input slew (late, the path's edge at
+    the arc's input) and the output load, so path delays are additive and
+    plain enumeration fixes the report: every path to each endpoint, summed
+    with the independent net sums and bilinear form, ranked per endpoint,
+    the L smallest of each of the k worst endpoints merged by (slack,
+    endpoint order, rank).  The best-first search of the oracle must give
+    the same slacks and endpoints rank by rank."""
+    d = synth.make_design(14, 5, seed=seed, rc_nodes=(2, 5), pi_frac=0.3)
+    d["period_ns"] = 0.3
+    res = oracle.sta(d)
+    allp = _indep.enumerate_paths_at_slews(d, res["slew"][:, 0])
+    eps, es = res["endpoints"], res["ep_setup"][:, 0]
+    # the graph-based arrival is the latest enumerated path at every endpoint edge
+    for e in range(len(eps)):
+        p = int(eps[e])
+        for rf in (0, 1):
+            vals = [a for a, r in allp[p] if r == rf]
+            if vals:
+                assert res["at"][p, 0, 2 + rf] == pytest.approx(max(vals), abs=1e-12)
+    for k, L in ((50, 3), (12, 8), (40, 1), (5, 30)):
+        paths = oracle.report_paths_nworst(d, k, L, res=res)
+        order = sorted(range(len(eps)), key=lambda e: (es[e], e))[:k]
+        want = []
+        for oi, e in enumerate(order):
+            p = int(eps[e])
+            sl = sorted(res["rat"][p, 0, 2 + rf] - a for a, rf in allp[p])
+            want += [(s, oi, r, p) for r, s in enumerate(sl[:L])]
+        want.sort()
+        want = want[:k]
+        assert len(paths) == len(want)
+        for pth, (s, _, _, p) in zip(paths, want):
+            assert pth["slack"] == pytest.approx(s, abs=1e-12)
+            assert pth["endpoint"] == p
 
 
 def test_nworst_limit_one_is_the_plain_report():
