@@ -30,10 +30,11 @@ ERRORS = {0: "ok", 1: "invalid input", 2: "combinational cycle", 3: "out of memo
 
 
 def build(force: bool = False) -> str:
-    """Compile ``sta_oracle.c`` into ``liboracle.so`` (gcc -O2, plain C)."""
+    """Compile ``sta_oracle.c`` into ``liboracle.so`` (gcc -O3, plain C; OpenMP
+    only in the timed baseline ``orc_sta_timed``)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + ".tmp%d" % os.getpid()
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O3", "-std=c11", "-fopenmp", "-shared", "-fPIC", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -53,6 +54,7 @@ def _load():
         _lib.orc_net_delays.argtypes = [P, C.c_int32, P, P, P]
         _lib.orc_topo_order.argtypes = [P, P]
         _lib.orc_sta.argtypes = [P, P, P, P, P, P, P, P]
+        _lib.orc_sta_timed.argtypes = [P, C.c_int32, C.c_int32, P, P]
         _lib.orc_objective_grad.argtypes = [P, C.c_double, C.c_double, P, P, P]
         _lib.orc_objective.argtypes = [P, C.c_double, C.c_double, P]
         _lib.orc_steiner_tree.argtypes = [C.c_int32, P, P, P, P, P, P, P, P]
@@ -60,6 +62,7 @@ def _load():
         _lib.orc_net_wirelengths.argtypes = [P, P]
         _lib.orc_nm.restype = C.c_int64
         for f in ("orc_lut_eval", "orc_rc_tree", "orc_rc_tree_adjoint", "orc_arnoldi_t50", "orc_net_delays", "orc_topo_order", "orc_sta",
+                  "orc_sta_timed",
                   "orc_objective_grad", "orc_objective", "orc_steiner_tree", "orc_net_wirelengths"):
             getattr(_lib, f).restype = C.c_int
     return _lib
@@ -282,6 +285,23 @@ def n_tags(d: dict) -> int:
     G = len(d["exc_action"])
     tp = d.get("exc_thru_ptr")
     return 1 + sum((int(tp[g + 1]) - int(tp[g]) if tp is not None else 0) + 1 for g in range(G))
+
+
+def sta_timed(d: dict, n_threads: int = 1, reps: int = 3):
+    """The plain analysis (no exception groups) timed ``reps`` times on
+    ``n_threads`` host threads (OpenMP over the nets and over the pins of a
+    level; the serial result).  Only net delays through WNS/TNS are timed:
+    validation, the topological order and its levels are prepared once
+    outside.  Returns (seconds per run [reps], summary [n_corners][8] as in
+    ``sta``)."""
+    lib = _load()
+    s, keep = _marshal(d, None)
+    K = int(d.get("n_corners", 1))
+    secs = np.zeros(max(int(reps), 1), np.float64)
+    summ = np.zeros((K, 8), np.float64)
+    rc = lib.orc_sta_timed(C.byref(s), int(n_threads), int(reps), _ptr(secs), _ptr(summ))
+    _check(rc, "sta_timed")
+    return secs, summ
 
 
 def sta(d: dict, use_rc: bool | None = None) -> dict:

@@ -64,7 +64,9 @@
  * early <= late, WNS/TNS definitions, and the adjoint against central finite
  * differences of this file's own smoothed forward pass.
  */
+#define _POSIX_C_SOURCE 200809L   /* clock_gettime */
 #include <math.h>
+#include <time.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -815,6 +817,9 @@ static int steiner_rc(const orc_design *d, const pin_info *pi, int32_t n, double
  * with wire_model == 1 it is the O9 Steiner tree, each edge of x length Lx
  * and y length Ly (um) with R = rx Lx + ry Ly and C = cx Lx + cy Ly split
  * half at each end (ry, cy <= 0: the x values). */
+static int net_delays_one(const orc_design *d, const pin_info *pi_, int32_t n, double f, double *load_pf,
+                          double *D_ns, double *V_ns2);
+
 int orc_net_delays(const orc_design *d, int32_t corner, double *load_pf, double *D_ns, double *V_ns2)
 {
     pin_info pi;
@@ -822,7 +827,19 @@ int orc_net_delays(const orc_design *d, int32_t corner, double *load_pf, double 
     if (rc) return rc;
     for (int32_t p = 0; p < d->n_pins; ++p) { load_pf[p] = 0.0; D_ns[p] = 0.0; V_ns2[p] = 0.0; }
     double f = d->rc_scale ? d->rc_scale[corner] : 1.0;
-    for (int32_t n = 0; n < d->n_nets; ++n) {
+    for (int32_t n = 0; n < d->n_nets && !rc; ++n) rc = net_delays_one(d, &pi, n, f, load_pf, D_ns, V_ns2);
+    free_info(&pi);
+    return rc;
+}
+
+/* Net n's driver load, sink delays and variances (corner scale f applied to
+ * R and C); writes only the pins of net n. */
+static int net_delays_one(const orc_design *d, const pin_info *pi_, int32_t n, double f, double *load_pf,
+                          double *D_ns, double *V_ns2)
+{
+    int rc = OK;
+    pin_info pi = *pi_;
+    {
         int32_t b = d->net_pin_ptr[n], e = d->net_pin_ptr[n + 1];
         int32_t nn;
         const int steiner = !d->rc_ptr && d->wire_model == 1;
@@ -884,10 +901,8 @@ int orc_net_delays(const orc_design *d, int32_t corner, double *load_pf, double 
         }
     next:
         free(par); free(R); free(C); free(cd); free(Dd); free(be); free(va); free(pnode);
-        if (rc) { free_info(&pi); return rc; }
     }
-    free_info(&pi);
-    return OK;
+    return rc;
 }
 
 /* O9 tree length (nm) of every net of a placed design: wl[n_nets]. */
@@ -983,7 +998,7 @@ int orc_topo_order(const orc_design *d, int32_t *order)
 #define IX(p, k, j) ((((size_t)(p)) * (size_t)K + (size_t)(k)) * 4 + (size_t)(j))
 #define JJ(el, rf) ((el) * 2 + (rf))   /* el 0 early, 1 late; rf 0 rise, 1 fall */
 
-/* One state: k indexes the at/slew arrays of Ks states (corner * tags +
+/* Pin p of one state (its fan-ins final): k indexes the at/slew arrays of Ks states (corner * tags +
  * tag), kc is the corner (its table scale).  src_on[p] == 0 marks a
  * startpoint of another tag: its arrivals are absent (-inf late, +inf
  * early); its slew is kept (slews are tag-free).  src_on may be NULL.
@@ -991,15 +1006,14 @@ int orc_topo_order(const orc_design *d, int32_t *order)
  * moves on to tag t + 1 at gate input p; this state's tag is t = k - kt0
  * (kt0: the corner's first state), and the state k - 1 (tag t - 1) must be
  * final already. */
-static void forward_corner(const orc_design *d, const pin_info *pi, const int32_t *order, int32_t k, int32_t Ks,
-                           int32_t kc, const int8_t *src_on, const uint32_t *adv, int32_t kt0, const double *load,
-                           const double *Dn, const double *Vn, double *at, double *slew)
+static void forward_pin(const orc_design *d, const pin_info *pi, int32_t p, int32_t k, int32_t Ks, int32_t kc,
+                        const int8_t *src_on, const uint32_t *adv, int32_t kt0, const double *load, const double *Dn,
+                        const double *Vn, double *at, double *slew)
 {
     const int32_t t = k - kt0;
     int32_t K = Ks;
     double sc = d->lut_scale ? d->lut_scale[kc] : 1.0;
-    for (int32_t oi = 0; oi < d->n_pins; ++oi) {
-        int32_t p = order[oi];
+    {
         int r = d->pin_role[p];
         if (r == R_PI || r == R_CK) {
             double a = (r == R_PI) ? d->pi_at_ns : 0.0;
@@ -1047,21 +1061,29 @@ static void forward_corner(const orc_design *d, const pin_info *pi, const int32_
     }
 }
 
+/* One state over every pin in topological order (see forward_pin). */
+static void forward_corner(const orc_design *d, const pin_info *pi, const int32_t *order, int32_t k, int32_t Ks,
+                           int32_t kc, const int8_t *src_on, const uint32_t *adv, int32_t kt0, const double *load,
+                           const double *Dn, const double *Vn, double *at, double *slew)
+{
+    for (int32_t oi = 0; oi < d->n_pins; ++oi)
+        forward_pin(d, pi, order[oi], k, Ks, kc, src_on, adv, kt0, load, Dn, Vn, at, slew);
+}
+
 /* ----------------------------------------------- O4: required times, slack */
 
-/* One state (as forward_corner).  ep_req[2p], ep_req[2p+1] replace the late
+/* Pin p of one state (as forward_pin; its fan-outs final).  ep_req[2p], ep_req[2p+1] replace the late
  * and early requirements of endpoint pin p (may be NULL: the defaults).
  * Through a sink s that advances this state's tag t, the path continues in
  * tag t + 1: the state k + 1 must be final already. */
-static void backward_corner(const orc_design *d, const pin_info *pi, const int32_t *order, int32_t k, int32_t Ks,
-                            int32_t kc, const double *ep_req, const uint32_t *adv, int32_t kt0, const double *load,
-                            const double *Dn, const double *slew, double *rat)
+static void backward_pin(const orc_design *d, const pin_info *pi, int32_t p, int32_t k, int32_t Ks, int32_t kc,
+                         const double *ep_req, const uint32_t *adv, int32_t kt0, const double *load, const double *Dn,
+                         const double *slew, double *rat)
 {
     int32_t K = Ks;
     const int32_t t = k - kt0;
     double sc = d->lut_scale ? d->lut_scale[kc] : 1.0;
-    for (int32_t oi = d->n_pins - 1; oi >= 0; --oi) {
-        int32_t p = order[oi];
+    {
         int r = d->pin_role[p];
         double rl[2] = {INFINITY, INFINITY}, re[2] = {-INFINITY, -INFINITY};
         if (r == R_D || r == R_PO) {
@@ -1108,6 +1130,15 @@ static void backward_corner(const orc_design *d, const pin_info *pi, const int32
         rat[IX(p, k, JJ(0, 0))] = re[0]; rat[IX(p, k, JJ(0, 1))] = re[1];
         rat[IX(p, k, JJ(1, 0))] = rl[0]; rat[IX(p, k, JJ(1, 1))] = rl[1];
     }
+}
+
+/* One state over every pin in reverse topological order (see backward_pin). */
+static void backward_corner(const orc_design *d, const pin_info *pi, const int32_t *order, int32_t k, int32_t Ks,
+                            int32_t kc, const double *ep_req, const uint32_t *adv, int32_t kt0, const double *load,
+                            const double *Dn, const double *slew, double *rat)
+{
+    for (int32_t oi = d->n_pins - 1; oi >= 0; --oi)
+        backward_pin(d, pi, order[oi], k, Ks, kc, ep_req, adv, kt0, load, Dn, slew, rat);
 }
 
 /* Full analysis.  Arrays at/slew/rat/slack are [n_pins][n_corners][4] with
@@ -1263,6 +1294,121 @@ int orc_sta(const orc_design *d, double *at, double *slew, double *rat, double *
     }
 done:
     free(order); free(load); free(Dn); free(Vn); free(tag_of); free(src_on); free(in_to); free(ep_req); free(adv);
+    free_info(&pi);
+    return rc;
+}
+
+/* ------------------------------------------------ timed baseline (O2-O4) */
+
+static double wall_s(void)
+{
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+/* The plain analysis of orc_sta (no exception groups) repeated `reps` times
+ * with each run's wall time in secs[reps]: net delays, forward arrivals and
+ * slews, backward required times, pin slacks, endpoint slacks and WNS/TNS.
+ * Validation, the topological order and its level buckets are prepared
+ * once, outside the timed runs.  One thread walks the depth-first order
+ * of orc_sta.  With n_threads > 1 the nets and the pins of one level are
+ * split over OpenMP threads: a pin's level is one more
+ * than its deepest fan-in's, so a level's pins read only values of earlier
+ * levels (forward) or later ones (backward) and write only their own: the
+ * results equal the serial analysis.  summary[n_corners][8] as orc_sta
+ * (last run).  Returns ERR_INVAL with exception groups. */
+int orc_sta_timed(const orc_design *d, int32_t n_threads, int32_t reps, double *secs, double *summary)
+{
+    if (d->n_exc > 0 || reps < 1) return ERR_INVAL;
+    pin_info pi;
+    int rc = build_info(d, &pi);
+    if (rc) return rc;
+    const int32_t P = d->n_pins, K = d->n_corners, nt = n_threads > 0 ? n_threads : 1;
+    const size_t PK4 = (size_t)(P ? P : 1) * (size_t)K * 4;
+    int32_t *order = (int32_t *)malloc(sizeof(int32_t) * (size_t)(P ? P : 1));
+    int32_t *lev = (int32_t *)calloc((size_t)(P ? P : 1), sizeof(int32_t));
+    int32_t *lv_pins = (int32_t *)malloc(sizeof(int32_t) * (size_t)(P ? P : 1));
+    int32_t *lv_ptr = NULL;
+    double *at = (double *)malloc(sizeof(double) * PK4), *slew = (double *)malloc(sizeof(double) * PK4);
+    double *rat = (double *)malloc(sizeof(double) * PK4), *slack = (double *)malloc(sizeof(double) * PK4);
+    double *load = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    double *Dn = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    double *Vn = (double *)malloc(sizeof(double) * (size_t)(P ? P : 1));
+    int32_t L = 0;
+    if (!order || !lev || !lv_pins || !at || !slew || !rat || !slack || !load || !Dn || !Vn) { rc = ERR_NOMEM; goto done; }
+    rc = topo_order(d, &pi, order);
+    if (rc) goto done;
+    for (int32_t oi = 0; oi < P; ++oi) {
+        const int32_t p = order[oi];
+        int32_t fi[MAXSLOT + 1];
+        const int nf = fanins(d, &pi, p, fi);
+        for (int i = 0; i < nf; ++i) lev[p] = lev[p] > lev[fi[i]] + 1 ? lev[p] : lev[fi[i]] + 1;
+        L = L > lev[p] + 1 ? L : lev[p] + 1;
+    }
+    lv_ptr = (int32_t *)calloc((size_t)L + 1, sizeof(int32_t));
+    if (!lv_ptr) { rc = ERR_NOMEM; goto done; }
+    for (int32_t p = 0; p < P; ++p) ++lv_ptr[lev[p] + 1];
+    for (int32_t l = 0; l < L; ++l) lv_ptr[l + 1] += lv_ptr[l];
+    {
+        int32_t *fill = (int32_t *)malloc(sizeof(int32_t) * (size_t)(L ? L : 1));
+        if (!fill) { rc = ERR_NOMEM; goto done; }
+        for (int32_t l = 0; l < L; ++l) fill[l] = lv_ptr[l];
+        for (int32_t p = 0; p < P; ++p) lv_pins[fill[lev[p]]++] = p;
+        free(fill);
+    }
+    for (int32_t rep = 0; rep < reps; ++rep) {
+        const double t0 = wall_s();
+        for (int32_t kc = 0; kc < K && !rc; ++kc) {
+            const double f = d->rc_scale ? d->rc_scale[kc] : 1.0;
+            int bad = 0;
+#pragma omp parallel for num_threads(nt) schedule(static)
+            for (int32_t p = 0; p < P; ++p) { load[p] = 0.0; Dn[p] = 0.0; Vn[p] = 0.0; }
+#pragma omp parallel for num_threads(nt) schedule(dynamic, 512) reduction(| : bad)
+            for (int32_t n = 0; n < d->n_nets; ++n) bad |= net_delays_one(d, &pi, n, f, load, Dn, Vn) != OK;
+            if (bad) { rc = ERR_INVAL; break; }
+            if (nt == 1) {   /* one thread: the analysis' own depth-first order */
+                forward_corner(d, &pi, order, kc, K, kc, NULL, NULL, kc, load, Dn, Vn, at, slew);
+                backward_corner(d, &pi, order, kc, K, kc, NULL, NULL, kc, load, Dn, slew, rat);
+            } else {
+                for (int32_t l = 0; l < L; ++l) {
+#pragma omp parallel for num_threads(nt) schedule(static)
+                    for (int32_t i = lv_ptr[l]; i < lv_ptr[l + 1]; ++i)
+                        forward_pin(d, &pi, lv_pins[i], kc, K, kc, NULL, NULL, kc, load, Dn, Vn, at, slew);
+                }
+                for (int32_t l = L - 1; l >= 0; --l) {
+#pragma omp parallel for num_threads(nt) schedule(static)
+                    for (int32_t i = lv_ptr[l]; i < lv_ptr[l + 1]; ++i)
+                        backward_pin(d, &pi, lv_pins[i], kc, K, kc, NULL, NULL, kc, load, Dn, slew, rat);
+                }
+            }
+#pragma omp parallel for num_threads(nt) schedule(static)
+            for (int32_t p = 0; p < P; ++p)
+                for (int rf = 0; rf < 2; ++rf) {
+                    slack[IX(p, kc, JJ(0, rf))] = at[IX(p, kc, JJ(0, rf))] - rat[IX(p, kc, JJ(0, rf))];
+                    slack[IX(p, kc, JJ(1, rf))] = rat[IX(p, kc, JJ(1, rf))] - at[IX(p, kc, JJ(1, rf))];
+                }
+            /* endpoint slacks and the FP64 sums, in pin order as orc_sta */
+            double wns_s = 0, tns_s = 0, wns_h = 0, tns_h = 0, worst_s = INFINITY, worst_h = INFINITY;
+            double nv_s = 0, nv_h = 0;
+            for (int32_t p = 0; p < P; ++p) {
+                const int r = d->pin_role[p];
+                if (r != R_D && r != R_PO) continue;
+                const double ss = fmin(slack[IX(p, kc, JJ(1, 0))], slack[IX(p, kc, JJ(1, 1))]);
+                const double hs = fmin(slack[IX(p, kc, JJ(0, 0))], slack[IX(p, kc, JJ(0, 1))]);
+                worst_s = fmin(worst_s, ss); worst_h = fmin(worst_h, hs);
+                if (ss < 0) { tns_s += ss; nv_s += 1; wns_s = fmin(wns_s, ss); }
+                if (hs < 0) { tns_h += hs; nv_h += 1; wns_h = fmin(wns_h, hs); }
+            }
+            double *sm = summary + (size_t)kc * 8;
+            sm[0] = wns_s; sm[1] = tns_s; sm[2] = wns_h; sm[3] = tns_h;
+            sm[4] = worst_s; sm[5] = worst_h; sm[6] = nv_s; sm[7] = nv_h;
+        }
+        secs[rep] = wall_s() - t0;
+    }
+done:
+    free(order); free(lev); free(lv_pins); free(lv_ptr); free(at); free(slew); free(rat); free(slack);
+    free(load); free(Dn); free(Vn);
     free_info(&pi);
     return rc;
 }

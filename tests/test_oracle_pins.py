@@ -1453,3 +1453,21 @@ def test_nworst_limit_one_is_the_plain_report():
             np.testing.assert_array_equal(x["pins"], y["pins"])
             np.testing.assert_allclose(x["at"], y["at"], atol=1e-12)
             assert x["slack"] == pytest.approx(y["slack"], abs=1e-12)
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_timed_baseline_is_the_same_analysis(threads):
+    """The timed CPU baseline (net delays through WNS/TNS over level buckets,
+    OpenMP over a level's pins) reports exactly what the serial analysis
+    reports, for any thread count, on one and several corners."""
+    ls, rs = synth.lut_corners()
+    for d in (synth.workload("tiny", seed=1),
+              synth.make_design(3000, 20, seed=4, n_corners=4, lut_scale=ls, rc_scale=rs, period_ns=1.7),
+              synth.make_design(2000, 15, seed=5, placed=True)):
+        r = oracle.sta(d)
+        secs, summ = oracle.sta_timed(d, threads, 2)
+        assert len(secs) == 2 and np.all(secs > 0)
+        keys = ("wns_setup", "tns_setup", "wns_hold", "tns_hold", "worst_setup", "worst_hold")
+        for k in range(int(d.get("n_corners", 1))):
+            want = [r[x][k] for x in keys] + [r["n_viol_setup"][k], r["n_viol_hold"][k]]
+            np.testing.assert_array_equal(summ[k], np.array(want, np.float64))
