@@ -1423,12 +1423,15 @@ sta_status sta_stats(const sta_ctx *c, sta_plan_info *out)
     std::memset(out, 0, sizeof(*out));
     out->n_pins = pl.P;
     out->n_cells = pl.C;
-    out->n_nets = 0;
-    for (int32_t g = 0; g < pl.I; ++g) out->n_nets += pl.fo_ptr[g + 1] > pl.fo_ptr[g];
+    // every caller net (as sta_plan; sta_get_net_wirelength writes one value
+    // per net), sinkless ones included
+    out->n_nets = pl.n_nets;
+    int64_t nets_with_sinks = 0;
+    for (int32_t g = 0; g < pl.I; ++g) nets_with_sinks += pl.fo_ptr[g + 1] > pl.fo_ptr[g];
     out->n_items = pl.I;
     out->n_cell_arcs = pl.cell_arcs;
     out->n_net_arcs = pl.F;
-    out->n_rc_nodes = pl.placed ? pl.F + out->n_nets : pl.NN;
+    out->n_rc_nodes = pl.placed ? pl.F + nets_with_sinks : pl.NN;
     out->n_endpoints = pl.E;
     out->n_levels = pl.S;
     out->n_corners = pl.Kc;

@@ -427,7 +427,7 @@ class Context:
     def get_net_wirelength(self, device: bool = False, stream=None):
         """Steiner wirelength (int64 nm) of every net at the last update, in
         caller net order; a torch CUDA tensor with ``device``, else numpy."""
-        n = self.stats()["n_nets"]
+        n = self.stats()["n_nets"]   # every caller net: the count the library writes
         if device:
             import torch
             out = torch.empty(n, dtype=torch.int64, device=torch.device("cuda", self.device))

@@ -178,9 +178,19 @@ def test_backward_state_errors():
 
 def test_diff_workload_200k_against_oracle_and_differences():
     """The 200k-cell placed workload (star RC, gamma 0.01 ns): J and every
-    gradient component against the FP64 oracle, and central differences
-    (h = 1e-3 um) of the oracle's objective on sampled cells against the GPU
-    gradient."""
+    gradient component against the FP64 oracle, then central differences
+    (h = 1e-3 um) of the oracle's objective on 100 uniformly random cells
+    and 20 of the 200 with the largest gradients (both axes) against the GPU
+    gradient, with the per-component bound
+    |g - fd| <= 1e-3 max|g*| + 1e-3 |fd|.  A component whose one-sided
+    differences within +-h disagree by more than that bound has crossed a
+    kink (a Manhattan |dx| = 0) or a table breakpoint, where the derivative
+    is not defined at this resolution: it is counted as excluded, and at
+    most 5% may be."""
+    import multiprocessing as mp
+    import os
+
+    from tests import _fd
     d = synth.workload("diff", seed=0)
     d["period_ns"], _ = tune_period(d, min_half_gap=0.0)
     J, terms, g = gpu_grad(d)
@@ -188,25 +198,40 @@ def test_diff_workload_200k_against_oracle_and_differences():
     assert J == pytest.approx(J0, rel=1e-5)
     rel = check_grad(g, g0)
     rng = np.random.default_rng(0)
+    cells = rng.choice(d["n_cells"], 100, replace=False)
+    # most random cells barely touch the critical endpoints (their gradient
+    # is exponentially small under the smoothing): 20 more from the 200
+    # largest gradients exercise large components too
     big = np.argsort(-np.abs(g0).max(1))[:200]
-    cells = rng.choice(big, 6, replace=False)
+    cells = np.concatenate([cells, rng.choice(np.setdiff1d(big, cells), 20, replace=False)])
     h = 1e-3
+    tasks = [(0, 0, 0.0)] + [(int(c), ax, sg * h) for c in cells for ax in (0, 1) for sg in (1.0, -1.0)]
+    workers = max(1, min(16, (os.cpu_count() or 1)))
+    with mp.get_context("spawn").Pool(workers, initializer=_fd.init, initargs=("diff", 0, d["period_ns"])) as pool:
+        res = pool.map(_fd.objective_at, tasks, chunksize=4)
+    Jc = res[0][0]
+    assert Jc == pytest.approx(J0, rel=1e-12)
     scale = np.abs(g0).max()
-    for cidx in cells:
+    excluded, checked, worst, nonzero = 0, 0, 0.0, 0
+    for i, c in enumerate(cells):
         for ax in (0, 1):
-            xy = d["cell_xy"].astype(np.float64)
-            vals = []
-            for sgn in (1, -1):
-                dd = dict(d)
-                x2 = xy.copy()
-                x2[2 * cidx + ax] += sgn * h
-                dd["cell_xy"] = x2.astype(np.float32)
-                vals.append(oracle.objective(dd))
-            v0 = float(d["cell_xy"][2 * cidx + ax])
-            step = float(np.float32(v0 + h)) - float(np.float32(v0 - h))
-            fd = (vals[0] - vals[1]) / step
-            assert abs(fd - g[cidx, ax]) <= 1e-3 * scale + 1e-2 * abs(fd), (cidx, ax, fd, g[cidx, ax])
-    print("200k gradient: max error / max|g| = %.2e" % rel)
+            (jp, xp), (jm, xm) = res[1 + 4 * i + 2 * ax], res[2 + 4 * i + 2 * ax]
+            x0 = float(d["cell_xy"][2 * c + ax])
+            fd = (jp - jm) / (xp - xm)
+            fwd, bwd = (jp - Jc) / (xp - x0), (Jc - jm) / (x0 - xm)
+            bound = 1e-3 * scale + 1e-3 * abs(fd)
+            if abs(fwd - bwd) > bound:
+                excluded += 1
+                continue
+            checked += 1
+            nonzero += abs(fd) > 1e-6 * scale
+            err = abs(fd - g[c, ax])
+            worst = max(worst, err / bound)
+            assert err <= bound, (int(c), ax, fd, float(g[c, ax]), err, bound)
+    assert excluded <= 12, excluded
+    assert nonzero >= 30, nonzero
+    print("200k gradient: max error / max|g| = %.2e; central differences on %d components (%d above 1e-6 max|g|, "
+          "%d excluded), worst error / bound = %.3f" % (rel, checked, nonzero, excluded, worst))
 
 
 def test_large_library_uses_level_sweeps():
