@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--batch-designs", type=int, default=64)
     ap.add_argument("--batch-hi", type=int, default=500_000, help="largest design of the batch (cells)")
     ap.add_argument("--no-grad", action="store_true", help="skip the gradient timing")
+    ap.add_argument("--no-large", action="store_true",
+                    help="skip the 10M-cell x 4-corner incremental differentiable loop")
     return ap.parse_args()
 
 
@@ -474,6 +476,8 @@ def run_ours(a, dist: Dist):
         out["grad"] = run_grad(a, dev)
     if not a.no_batch:
         out["batched"] = run_batched(a, dev)
+    if not a.no_large:
+        out["large"] = incremental_loop(a, dev)
 
     # ---- the FP64 oracle on the host cores (rank 0, one GPU only)
     if dist.rank == 0 and dist.world == 1:
@@ -635,36 +639,37 @@ def cpu_baseline(d: dict, T: float) -> dict:
 
 # ------------------------------------------------------------- reference
 
-def run_incremental(a, dist: Dist):
-    """The large incremental differentiable loop: per iteration move 1% of the
-    cells by U(-5, 5) um and resize 1% to the other drive strength, then
-    set_positions + set_cell_types + update_timing + sta_backward."""
+def incremental_loop(a, dev: int, n_iter: int = 20) -> dict:
+    """The large incremental differentiable loop on 10M cells x 4 corners:
+    per iteration move 1% of the cells by U(-5, 5) um and resize 1% to the
+    other drive strength, then set_positions + resize_cells + update_timing
+    + sta_backward, all on the device.  Returns ms per iteration (wall and
+    device), per-call times and the memory the context holds."""
     import torch
     from paper_2511_11660_b300 import clock, sta, synth
-    torch.cuda.set_device(dist.local)
     t0 = time.perf_counter()
     d = make_workload("large", a.seed)
     t_gen = time.perf_counter() - t0
     st_d = synth.design_stats(d)
     t0 = time.perf_counter()
-    ctx = sta.Context(d, device=dist.local)
+    ctx = sta.Context(d, device=dev)
     t_create = time.perf_counter() - t0
     ctx.set_clock(0.0)
     ctx.update_timing()
     s0, _, _, _ = ctx.get_endpoint_slack()
     T = clock.period_in_gap(-s0[:, 1], min_half_gap=0.0)[0]   # corner 1 (scale 1.0)
     ctx.set_clock(T)
-    sched = {sta.SCHED_LEVEL: "level", sta.SCHED_DATAFLOW: "dataflow", sta.SCHED_COOP: "coop",
-             sta.SCHED_TILE: "tile"}[ctx.autotune(trials=2)[0]]
+    names = {sta.SCHED_LEVEL: "level", sta.SCHED_DATAFLOW: "dataflow", sta.SCHED_COOP: "coop", sta.SCHED_TILE: "tile"}
+    sch, par, _ = ctx.autotune(trials=1)
     K = ctx.K
     C = d["n_cells"]
     rng = np.random.default_rng(a.seed)
     xy = torch.tensor(np.asarray(d["cell_xy"], np.float32), device="cuda")
     types = np.asarray(d["cell_type"], np.int32).copy()
     grad = torch.empty((C, 2), dtype=torch.float64, device="cuda")
-    n_iter = 20
     walls, devs = [], []
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rz_d = ty_d = None
     for it in range(n_iter + 2):
         mv = torch.from_numpy(rng.choice(C, C // 100, replace=False)).cuda()
         dxy = torch.from_numpy(rng.uniform(-5, 5, size=(C // 100, 2)).astype(np.float32)).cuda()
@@ -687,25 +692,46 @@ def run_incremental(a, dist: Dist):
             devs.append(e0.elapsed_time(e1))
     # one more iteration, each call timed on its own
     parts = {}
-    for name, fn in (("set_positions", lambda: ctx.set_positions(xy)), ("resize_cells", lambda: ctx.resize_cells(rz_d, ty_d)),
+    for name, fn in (("set_positions", lambda: ctx.set_positions(xy)),
+                     ("resize_cells", lambda: ctx.resize_cells(rz_d, ty_d)),
                      ("update_timing", lambda: ctx.update_timing()),
                      ("backward", lambda: ctx.backward(1.0, 1.0, grad_out=grad))):
         parts[name] = _events_ms(fn, 1)
     stats = ctx.stats()
     rep = ctx.report_slack()
+    ctx.close()
+    del ctx
+    torch.cuda.empty_cache()
+    return {"ms_per_iter": float(np.median(walls) * 1e3), "device_ms_per_iter": float(np.median(devs)),
+            "iterations": n_iter, "ms_by_call": parts, "cells": st_d["cells"], "pins": st_d["pins"],
+            "arcs": st_d["arcs"], "corners": K, "levels": stats["n_levels"], "period_ns": T,
+            "schedule": "%s (%d)" % (names[sch], par), "device_bytes": stats["device_bytes"],
+            "generate_s": t_gen, "create_s": t_create,
+            "arc_corners_per_s": st_d["arcs"] * K / np.median(walls),
+            "wns_setup_ns_by_corner": [r["wns_setup"] for r in rep],
+            "gpu_launches_per_iter": stats["launches_per_update"] + stats["launches_per_backward"] + 2,
+            "what": "per iteration: 1% of the cells moved by U(-5, 5) um and 1% resized (LUTs x0.7), then "
+                    "set_positions + resize_cells + update_timing + sta_backward (gamma 0.01 ns), all on the "
+                    "device; median of %d iterations after 2 warm-up" % n_iter}
+
+
+def run_incremental(a, dist: Dist):
+    """--workload large: the incremental loop as its own JSON line."""
+    import torch
+    torch.cuda.set_device(dist.local)
+    r = incremental_loop(a, dist.local)
     out = {"metric": "grad ms/iter, incremental differentiable STA (10M cells, 4 corners)",
-           "value": float(np.median(walls) * 1e3), "unit": "ms/iter", "n_gpus": 1, "steps": n_iter, "warmup": 2,
-           "ms_per_step": float(np.median(walls) * 1e3), "higher_is_better": False, "scaling": "weak",
+           "value": r["ms_per_iter"], "unit": "ms/iter", "n_gpus": 1, "steps": r["iterations"], "warmup": 2,
+           "ms_per_step": r["ms_per_iter"], "higher_is_better": False, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-           "config": {"workload": "large: " + WORKLOADS["large"], "cells": st_d["cells"], "pins": st_d["pins"],
-                      "arcs": st_d["arcs"], "corners": K, "levels": stats["n_levels"], "period_ns": T,
-                      "schedule": sched,
-                      "device_bytes": stats["device_bytes"], "generate_s": t_gen, "create_s": t_create,
-                      "wns_setup_ns_by_corner": [r["wns_setup"] for r in rep]},
-           "device_ms_per_iter": float(np.median(devs)), "ms_by_call": parts,
-           "arc_corners_per_s": st_d["arcs"] * K / np.median(walls),
-           # per iteration: update + backward + the two resize kernels (set_positions is a copy)
-           "gpu_launches": n_iter * (stats["launches_per_update"] + stats["launches_per_backward"] + 2)}
+           "config": {"workload": "large: " + WORKLOADS["large"], "cells": r["cells"], "pins": r["pins"],
+                      "arcs": r["arcs"], "corners": r["corners"], "levels": r["levels"],
+                      "period_ns": r["period_ns"], "schedule": r["schedule"], "device_bytes": r["device_bytes"],
+                      "generate_s": r["generate_s"], "create_s": r["create_s"],
+                      "wns_setup_ns_by_corner": r["wns_setup_ns_by_corner"]},
+           "device_ms_per_iter": r["device_ms_per_iter"], "ms_by_call": r["ms_by_call"],
+           "arc_corners_per_s": r["arc_corners_per_s"],
+           "gpu_launches": r["iterations"] * r["gpu_launches_per_iter"]}
     print(json.dumps(out))
 
 

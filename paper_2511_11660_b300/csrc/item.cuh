@@ -489,18 +489,27 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
         for (int j = 0; j < 3; ++j) {
             if (j >= nin) continue;
             const int tbj = tab_off(t, j, 0);
+            // the input edges with an arc to output edge rfo, in increasing
+            // order: the one edge of a unate arc (rfo, or its opposite), both
+            // of a non-unate one -- the same candidates in the same order as
+            // testing arc_on for rfi = 0, 1, but without lanes of one quad
+            // (which differ in rfo) diverging on a unate arc
+            const int se = f.sense[j];
+            const int n_rfi = se == kSenseNonC ? 2 : (se == kSensePosC || se == kSenseNegC) ? 1 : 0;
 #pragma unroll
-            for (int rfi = 0; rfi < 2; ++rfi) {
-                if (!arc_on(f.sense[j], rfi, rfo)) continue;
-                const float s = sin[j][rfi];
+            for (int r = 0; r < 2; ++r) {
+                if (r >= n_rfi) break;
+                const int rfi = se == kSenseNonC ? r : (se == kSenseNegC ? 1 - rfo : rfo);
+                const float s = rfi ? sin[j][1] : sin[j][0];
+                const DF ai = rfi ? ain[j][1] : ain[j][0];
                 const Seg as = seg_slew<UNIFORM>(c, lut, tbj, s);
                 const float dv = lookup<UNIFORM>(lut, tbj + rfo * kLutStride, as, bl, s, ld);
                 const float sv = lookup<UNIFORM>(lut, tbj + (2 + rfo) * kLutStride, as, bl, s, ld);
                 const float d = sc * dv;
-                const float y = sgn * (ain[j][rfi].hi + d);
+                const float y = sgn * (ai.hi + d);
                 if (y > wy) {
                     wy = y;
-                    win = ain[j][rfi];
+                    win = ai;
                     wd = d;
                 }
                 ma.add(y, c.inv_gamma);
@@ -777,12 +786,17 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
             const int tbj = tab_off(t, j, 0);
             const float s = first_k ? b.s0[j] : ld_state(c.slew + (size_t)a * K + k, q);
             const Seg as = seg_slew<UNIFORM>(c, lut, tbj, s);
-            // FP32 choice between the (at most two) arcs, the winner exactly
+            // FP32 choice between the (at most two) arcs, the winner exactly;
+            // the output edges with an arc from input edge rfi in increasing
+            // order (one for a unate arc, both for a non-unate one: no lane
+            // divergence inside a quad)
             float af = el ? INFINITY : -INFINITY, ad = 0.f;
             DF aw(af);
+            const int n_rfo = se == kSenseNonC ? 2 : (se == kSensePosC || se == kSenseNegC) ? 1 : 0;
 #pragma unroll
-            for (int rfo = 0; rfo < 2; ++rfo) {
-                if (!arc_on(se, rfi, rfo)) continue;
+            for (int r = 0; r < 2; ++r) {
+                if (r >= n_rfo) break;
+                const int rfo = se == kSenseNonC ? r : (se == kSenseNegC ? 1 - rfi : rfi);
                 const float d = sc * lookup<UNIFORM>(lut, tbj + rfo * kLutStride, as, bl, s, ld);
                 const DF Ro = rfo ? R1 : R0;
                 const float v = Ro.hi - d;
