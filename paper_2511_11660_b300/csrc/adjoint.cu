@@ -330,16 +330,28 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
                         Sin[0] = ld_state(c.slew + o, 2);
                         Sin[1] = ld_state(c.slew + o, 3);
                     }
+                    // the input edges with an arc to rfo (one for a unate arc,
+                    // both for a non-unate one): no divergence between the
+                    // quad's lanes of different rfo
+                    const int n_rfi = se == kSenseNonC ? 2 : (se == kSensePosC || se == kSenseNegC) ? 1 : 0;
 #pragma unroll
-                    for (int rfi = 0; rfi < 2; ++rfi) {
-                        if (!arc_on(se, rfi, rfo)) continue;
-                        const float s = Sin[rfi];
+                    for (int r = 0; r < 2; ++r) {
+                        if (r >= n_rfi) break;
+                        const int rfi = se == kSenseNonC ? r : (se == kSenseNegC ? 1 - rfo : rfo);
+                        const float s = rfi ? Sin[1] : Sin[0];
                         float ds, dl;
                         const float v = interp_d(lut, tq, seg_slew<UNIFORM>(c, lut, tq, s),
                                                  seg_load<UNIFORM>(c, lut, tq, ld), ds, dl);
-                        x[j * 2 + rfi] = slew_lane ? sc * v : Ain[rfi].hi + sc * v;
-                        dds[j * 2 + rfi] = ds;
-                        ddl[j * 2 + rfi] = dl;
+                        const float xv = slew_lane ? sc * v : (rfi ? Ain[1] : Ain[0]).hi + sc * v;
+                        if (rfi) {
+                            x[j * 2 + 1] = xv;
+                            dds[j * 2 + 1] = ds;
+                            ddl[j * 2 + 1] = dl;
+                        } else {
+                            x[j * 2] = xv;
+                            dds[j * 2] = ds;
+                            ddl[j * 2] = dl;
+                        }
                     }
                 }
                 // softmax weights of the log-sum-exp merge
@@ -611,7 +623,7 @@ __global__ void k_adj_level(const DevCtx c, int i0, int i1)
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int g = i0 + tid / (4 * c.KL);
     if (g < i1)
-        adj_run<UNIFORM, false>(c, LutGlobal{c.lut}, c.arc_sense, adj_prep(c, c.type_nin, c.type_kind, g, tid & 3), g,
+        adj_run<UNIFORM, false>(c, LutGlobal{c.lut, c.lut_scale}, c.arc_sense, adj_prep(c, c.type_nin, c.type_kind, g, tid & 3), g,
                                 tid & 3, 0, 0.f);
 }
 
@@ -649,7 +661,7 @@ __global__ void __launch_bounds__(kDfThreadsA) k_df_adjoint(const DevCtx c)
     }
     for (int i = threadIdx.x; i < 3 * c.T; i += blockDim.x) ti[2 * c.T + i] = __ldg(c.arc_sense + i);
     __syncthreads();
-    const LutShared lut{smem};
+    const LutShared lut{smem, c.lut_scale, c.lut_scale};   // table scales read from global memory here
     const int par = (int)(ld_volatile(c.df_state + 4) & 1u);
     const int lane = threadIdx.x & 31, q = lane & 3;
     for (;;) {

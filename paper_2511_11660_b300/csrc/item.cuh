@@ -40,13 +40,20 @@ namespace sta {
 
 // Table reads: from global memory through the read-only cache, or from a
 // shared-memory copy of the packed library.
+// sc(k) is state k's table scale (the corner's LUT factor).
+constexpr int kSmemScales = 64;   // states whose table scale the shared copy holds
 struct LutGlobal {
     const float *base;
+    const float *scale;   // [K] in global memory
     __device__ __forceinline__ float operator[](int off) const { return __ldg(base + off); }
+    __device__ __forceinline__ float sc(int k) const { return __ldg(scale + k); }
 };
 struct LutShared {
-    const float *base;   // points into shared memory
+    const float *base;    // points into shared memory
+    const float *scale;   // the first kSmemScales states' scales, in shared memory
+    const float *gscale;  // [K] in global memory (states beyond the shared copy)
     __device__ __forceinline__ float operator[](int off) const { return base[off]; }
+    __device__ __forceinline__ float sc(int k) const { return k < kSmemScales ? scale[k] : __ldg(gscale + k); }
 };
 
 struct Seg {
@@ -135,9 +142,11 @@ struct SmemLib {
     const int *nin, *kind, *sense;
 };
 
+// tables, then per-type data (5 ints a type), then the states' table scales
 __host__ __device__ inline size_t smem_lib_bytes(int T)
 {
-    return (size_t)T * 3 * 4 * kLutStride * sizeof(float) + (size_t)T * 5 * sizeof(int);
+    return (size_t)T * 3 * 4 * kLutStride * sizeof(float) + (size_t)T * 5 * sizeof(int) +
+           (size_t)kSmemScales * sizeof(float);
 }
 
 __device__ __forceinline__ SmemLib stage_library(const DevCtx &c, float *smem)
@@ -150,8 +159,10 @@ __device__ __forceinline__ SmemLib stage_library(const DevCtx &c, float *smem)
         ti[c.T + i] = __ldg(c.type_kind + i);
     }
     for (int i = threadIdx.x; i < 3 * c.T; i += blockDim.x) ti[2 * c.T + i] = __ldg(c.arc_sense + i);
+    float *sc = reinterpret_cast<float *>(ti + 5 * c.T);
+    for (int i = threadIdx.x; i < kSmemScales && i < c.K; i += blockDim.x) sc[i] = __ldg(c.lut_scale + i);
     __syncthreads();
-    return SmemLib{LutShared{smem}, ti, ti + c.T, ti + 2 * c.T};
+    return SmemLib{LutShared{smem, sc, c.lut_scale}, ti, ti + c.T, ti + 2 * c.T};
 }
 
 // ------------------------------------------------------ mailbox access
@@ -389,7 +400,7 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
         const float cs = c.clk_slew;
         const int tb = tab_off(t, 1, 0);
         for (int k = kq; k < K; k += KL) {
-            const float sc = __ldg(c.lut_scale + k);
+            const float sc = lut.sc(k);
             const float ld = k != kq ? c.load[(size_t)qp * K + k] : f.ld0;
             const DF ck_at((c.Tg == 1 || k % c.Tg == f.tag) ? 0.f : absent);
             st_comp_df(c.at + (size_t)ck * K + k, q, ck_at);
@@ -475,7 +486,7 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
                 st_comp(c.slew + (size_t)a * K + k, q, rfo ? sin[j][1] : sin[j][0]);
             }
         }
-        const float sc = __ldg(c.lut_scale + k);
+        const float sc = lut.sc(k);
         const float ld = k != kq ? c.load[(size_t)z * K + k] : f.ld0;
         const Seg bl = seg_load<UNIFORM>(c, lut, tab_off(t, 0, 0), ld);
         // Candidates are merged in FP32 -- the input arrival's high part +
@@ -760,7 +771,7 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
         if (t < 0) continue;
         // the output's required times of both edges at this lane's el
         const DF R0 = shfl_df(m, R, base + el * 2), R1 = shfl_df(m, R, base + el * 2 + 1);
-        const float sc = __ldg(c.lut_scale + k);
+        const float sc = lut.sc(k);
         const float ld = first_k ? b.ld0 : c.load[(size_t)z * K + k];
         if (b.kind == 1) {   // CK: only the rising edge has an arc (to both edges of Q)
             const int ck = pin0;

@@ -430,7 +430,7 @@ __global__ void k_fwd_level(const DevCtx c, int i0, int i1)
     const int g = i0 + tid / (4 * c.KL);
     if (g < i1) {
         const FwdItem f = fwd_prep(c, c.type_nin, c.type_kind, c.arc_sense, g);
-        fwd_run<SMOOTH, UNIFORM, false>(c, LutGlobal{c.lut}, f, FwdIn{}, g, tid & 3, 0);
+        fwd_run<SMOOTH, UNIFORM, false>(c, LutGlobal{c.lut, c.lut_scale}, f, FwdIn{}, g, tid & 3, 0);
     }
 }
 
@@ -446,7 +446,7 @@ __global__ void k_bwd_level(const DevCtx c, int i0, int i1)
 {
     const int tid = blockIdx.x * blockDim.x + threadIdx.x;
     const int g = i0 + tid / (4 * c.KL);
-    if (g < i1) bwd_run<UNIFORM, false>(c, LutGlobal{c.lut}, c.arc_sense,
+    if (g < i1) bwd_run<UNIFORM, false>(c, LutGlobal{c.lut, c.lut_scale}, c.arc_sense,
                                         bwd_prep(c, c.type_nin, c.type_kind, g, tid & 3), tid & 3, 0, 0.f);
 }
 

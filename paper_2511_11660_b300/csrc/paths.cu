@@ -127,7 +127,7 @@ __device__ int gate_cands(const DevCtx &c, int k, int t, int pin0, int p, int rf
 {
     const int K = c.K;
     const int nin = __ldg(c.type_nin + t);
-    const LutGlobal lut{c.lut};
+    const LutGlobal lut{c.lut, c.lut_scale};
     const float sc = __ldg(c.lut_scale + k);
     const float ld = c.load[(size_t)p * K + k];
     const Seg bl = seg_load<UNIFORM>(c, lut, tab_off(t, 0, 0), ld);
