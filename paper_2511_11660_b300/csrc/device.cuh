@@ -11,7 +11,7 @@ namespace sta {
 
 constexpr int kLutStride = 80;   // floats per packed table, see plan.cpp
 constexpr int kNetArnoldi = 1;     // DevCtx::net_model of the reduced-order calculator (STA_NET_ARNOLDI)
-constexpr int kRcColNodes = 16;    // RC nets up to this size are swept in shared memory (as plan.h)
+constexpr int kRcColNodes = 10;    // RC nets up to this size are swept in shared memory (as plan.h)
 constexpr int kRcThreads = 128;    // threads (nets) per block of the RC sweep
 constexpr int kStMaxPins = 64;     // nets of more pins keep the rectilinear MST (plan.h: kSteinerMaxPins)
 constexpr int kRedThreads = 256;   // threads of the reduction kernels

@@ -19,7 +19,7 @@ namespace sta {
 constexpr int kNldm = 7;          // 7x7 NLDM tables
 constexpr int kMaxSlot = 3;       // at most three inputs per cell
 constexpr int kTabStride = 80;    // floats per packed table (see packLut)
-constexpr int kColNodes = 16;     // RC nets up to this many nodes are swept in shared memory
+constexpr int kColNodes = 10;     // RC nets up to this many nodes are swept in shared memory
 constexpr int kSteinerMaxPins = 64;  // nets of more pins keep the rectilinear MST (no Steiner points)
 constexpr int kSteinerSmallPins = 8; // nets of at most this many pins are built in shared memory
 
