@@ -134,9 +134,9 @@ __global__ void __launch_bounds__(kDfThreads) k_df_backward(const DevCtx c)
         if (pending) b = bwd_prep(c, L.nin, L.kind, x, q);
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
-            DF R;
-            if (pending && group_all(c, bwd_probe<THRU>(c, b, par, q, R))) {
-                bwd_run<UNIFORM, true, THRU>(c, L.lut, L.sense, b, q, par, R);
+            Fold4 fo;
+            if (pending && group_all(c, bwd_probe_split<THRU>(c, b, par, q, fo))) {
+                bwd_run<UNIFORM, true, THRU>(c, L.lut, L.sense, b, q, par, quad_fold(fo, q));
                 pending = false;
             }
             if (__any_sync(0xffffffffu, pending) && !warp_idle_round(c, spins)) break;

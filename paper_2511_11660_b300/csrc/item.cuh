@@ -726,6 +726,125 @@ __device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int
     return ok;
 }
 
+// The backward fold split over the quad instead of over components: lane q
+// folds fan-out entries q, q + 4, q + 8, ... for all four components (one
+// 32-byte read per sink), keeping per component the extreme of RAT - Elmore
+// delay, the entry index that holds it (the first on ties, as the sequential
+// fold) and the winner's operands; quad_fold then reduces the four lanes.
+// A driver with many sinks waits for a quarter of the round trips.
+struct Fold4 {
+    float v[4];
+    int idx[4];
+    DF rw[4];
+    float rd[4];
+};
+
+// Reduce the quad's folds (every lane of the quad calls it): per component
+// the extreme value, lowest entry on ties; lane q returns component q's
+// required time (infinite when no sink constrains it).
+__device__ __forceinline__ DF quad_fold(Fold4 &f, int q)
+{
+    const unsigned m = quad_mask();
+    const int base = threadIdx.x & 28;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+        for (int off = 1; off <= 2; off <<= 1) {
+            const float ov = __shfl_xor_sync(m, f.v[j], off);
+            const int oi = __shfl_xor_sync(m, f.idx[j], off);
+            const bool take = (j >= 2 ? ov < f.v[j] : ov > f.v[j]) || (ov == f.v[j] && oi < f.idx[j]);
+            if (take) {
+                f.v[j] = ov;
+                f.idx[j] = oi;
+            }
+        }
+    }
+    DF rw(0.f);
+    float rd = 0.f, rf = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int src = base + (f.idx[j] == 0x7fffffff ? 0 : (f.idx[j] & 3));
+        const DF w = shfl_df(m, f.rw[j], src);
+        const float dd = __shfl_sync(m, f.rd[j], src);
+        if (j == q) {
+            rw = w;
+            rd = dd;
+            rf = f.v[j];
+        }
+    }
+    return isfinite(rf) ? rw - rd : DF(rf);
+}
+
+// bwd_probe with the fold split over the quad (Fold4): lane q reads all
+// four components of fan-out entries q, q + 4, ... (four at a time, their
+// loads in flight together) for the lane's first corner.  The caller's
+// group_all covers the quad, then quad_fold gives each lane its component's
+// required time -- the same value as bwd_probe's.
+template <bool THRU = true>
+__device__ __forceinline__ bool bwd_probe_split(const DevCtx &c, const BwdItem &b, int par, int q, Fold4 &f)
+{
+    const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
+    const int K = c.K, kq = corner_lane(c);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        f.v[j] = j >= 2 ? INFINITY : -INFINITY;
+        f.idx[j] = 0x7fffffff;
+        f.rw[j] = DF(f.v[j]);
+        f.rd[j] = 0.f;
+    }
+    const int nfo = b.f1 - b.f0;
+    for (int e0 = q; e0 < nfo; e0 += 16) {
+        int s[4];
+        DF m[4][4];
+        float nd[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int e = e0 + 4 * u;
+            s[u] = e < nfo ? chk(c, __ldg(c.fo_pin + b.f0 + e), c.P) : -1;
+            nd[u] = 0.f;
+            if (s[u] < 0) continue;
+            const int ks = (pin_adv && ((pin_adv[s[u]] >> (kq % c.Tg)) & 1u)) ? kq + 1 : kq;
+            if (s[u] < c.ep_begin) {
+                ld_relaxed_df4(rbox_at(c, par, s[u], ks), m[u][0], m[u][1], m[u][2], m[u][3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) m[u][j] = ld_state_df(c.rat + (size_t)s[u] * K + ks, j);
+            }
+            nd[u] = __ldg(c.netD + (size_t)s[u] * K + kq);
+        }
+        bool ok = true;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (s[u] >= 0) ok = ok && real_df(m[u][0]) && real_df(m[u][1]) && real_df(m[u][2]) && real_df(m[u][3]);
+        if (!ok) return false;   // no arithmetic while waiting
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (s[u] < 0) continue;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const float val = m[u][j].hi - nd[u];
+                if (j >= 2 ? val < f.v[j] : val > f.v[j]) {
+                    f.v[j] = val;
+                    f.idx[j] = e0 + 4 * u;
+                    f.rw[j] = m[u][j];
+                    f.rd[j] = nd[u];
+                }
+            }
+        }
+    }
+    // the lane's other states of its gate-input sinks
+    if (K > c.KL || pin_adv) {
+        for (int e = q; e < nfo; e += 4) {
+            const int s = chk(c, __ldg(c.fo_pin + b.f0 + e), c.P);
+            if (s >= c.ep_begin) continue;
+            const int k0 = pin_adv ? 0 : kq + c.KL, dk = pin_adv ? 1 : c.KL;
+            for (int k = k0; k < K; k += dk)
+                if (k != kq && !complete_df(rbox_at(c, par, s, k))) return false;
+        }
+    }
+    return true;
+}
+
 // Lane q = el*2 + rfi: the output's required time (component q) over its
 // net sinks, then each input pin's over its arcs, and pin slacks.  With WAIT
 // the first corner's output required time comes folded from bwd_probe (Rpre).

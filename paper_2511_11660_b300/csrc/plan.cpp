@@ -349,18 +349,51 @@ void build(const sta_design_desc *d, Plan &pl)
         throw Fail{STA_ECYCLE, "combinational loop through cell " + std::to_string(bad)};
     }
     pl.S = (int32_t)pl.stage_ptr.size() - 1;
-    // Items inside one level are grouped by cell type (primary inputs first),
-    // in ascending original order within a type: the kernels run 8 / KL
-    // consecutive items per warp, and items of one type take the same
-    // branches (input count, arc senses), so a warp does not pay for the
-    // arcs of every type in the level.
-    for (int32_t s = 0; s < pl.S; ++s)
-        std::sort(order.begin() + pl.stage_ptr[s], order.begin() + pl.stage_ptr[s + 1],
-                  [&](int32_t a, int32_t b) {
-                      const int32_t ta = a < nPI ? -1 : d->cell_type[a - nPI];
-                      const int32_t tb = b < nPI ? -1 : d->cell_type[b - nPI];
-                      return ta != tb ? ta < tb : a < b;
-                  });
+    // Items inside one level are grouped by cell type (primary inputs first):
+    // the kernels run 8 / KL consecutive items per warp, and items of one type
+    // take the same branches (input count, arc senses), so a warp does not
+    // pay for the arcs of every type in the level.  Within a type, items are
+    // ordered by the position of their critical fan-in (the driver item of
+    // the highest level) in the previous levels' order, then by original
+    // index: items whose inputs complete together share a warp.
+    std::vector<int32_t> pos_of(I, -1);
+    for (int32_t s = 0; s < pl.S; ++s) {
+        std::vector<int32_t> key(pl.stage_ptr[s + 1] - pl.stage_ptr[s]);
+        for (int32_t i = pl.stage_ptr[s]; i < pl.stage_ptr[s + 1]; ++i) {
+            const int32_t it = order[i];
+            int32_t best = -1, best_lv = -1;
+            if (it >= nPI) {
+                const int32_t c = it - nPI, t = d->cell_type[c];
+                if (pl.type_kind[t] != 1)
+                    for (int sl = 0; sl < pl.type_nin[t]; ++sl) {
+                        const int32_t a = d->cell_pin[d->cell_pin_ptr[c] + sl];
+                        const int32_t h = item_of(d->net_pin[d->net_pin_ptr[sink_net[a]]]);
+                        if (level[h] > best_lv) {
+                            best_lv = level[h];
+                            best = pos_of[h];
+                        }
+                    }
+            }
+            key[i - pl.stage_ptr[s]] = best;
+        }
+        std::vector<int32_t> idx(key.size());
+        for (size_t i = 0; i < idx.size(); ++i) idx[i] = (int32_t)i;
+        const int32_t base = pl.stage_ptr[s];
+        std::sort(idx.begin(), idx.end(), [&](int32_t x, int32_t y) {
+            const int32_t a = order[base + x], b = order[base + y];
+            const int32_t ta = a < nPI ? -1 : d->cell_type[a - nPI];
+            const int32_t tb = b < nPI ? -1 : d->cell_type[b - nPI];
+            if (ta != tb) return ta < tb;
+            if (key[x] != key[y]) return key[x] < key[y];
+            return a < b;
+        });
+        std::vector<int32_t> sorted(idx.size());
+        for (size_t i = 0; i < idx.size(); ++i) sorted[i] = order[base + idx[i]];
+        for (size_t i = 0; i < idx.size(); ++i) {
+            order[base + i] = sorted[i];
+            pos_of[sorted[i]] = base + (int32_t)i;
+        }
+    }
     pl.max_width = 0;
     for (int32_t s = 0; s < pl.S; ++s) pl.max_width = std::max(pl.max_width, pl.stage_ptr[s + 1] - pl.stage_ptr[s]);
 

@@ -397,16 +397,6 @@ __device__ __forceinline__ void tile_bwd_load(const DevCtx &c, const SmemLib &L,
     }
 }
 
-// The lane's part of the fold: per component c the extreme of RAT - delay
-// over its sinks (entries q, q + 4, ...), the entry index that holds it and
-// the winner's operands.  False while some sink is not yet published.
-struct Fold4 {
-    float v[4];
-    int idx[4];
-    DF rw[4];
-    float rd[4];
-};
-
 template <bool THRU>
 __device__ __forceinline__ bool tile_bwd_probe(const DevCtx &c, TileBwd &u, int par, int q, const DF *ring_r, Fold4 &f)
 {
@@ -471,42 +461,6 @@ __device__ __forceinline__ bool tile_bwd_probe(const DevCtx &c, TileBwd &u, int 
         }
     }
     return ok;
-}
-
-// Reduce the quad's folds (every lane of the quad calls it): per component
-// the extreme value, lowest entry on ties; lane q returns component q's
-// required time (infinite when no sink constrains it).
-__device__ __forceinline__ DF quad_fold(Fold4 &f, int q)
-{
-    const unsigned m = quad_mask();
-    const int base = threadIdx.x & 28;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-#pragma unroll
-        for (int off = 1; off <= 2; off <<= 1) {
-            const float ov = __shfl_xor_sync(m, f.v[j], off);
-            const int oi = __shfl_xor_sync(m, f.idx[j], off);
-            const bool take = (j >= 2 ? ov < f.v[j] : ov > f.v[j]) || (ov == f.v[j] && oi < f.idx[j]);
-            if (take) {
-                f.v[j] = ov;
-                f.idx[j] = oi;
-            }
-        }
-    }
-    DF rw(0.f);
-    float rd = 0.f, rf = 0.f;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int src = base + (f.idx[j] == 0x7fffffff ? 0 : (f.idx[j] & 3));
-        const DF w = shfl_df(m, f.rw[j], src);
-        const float dd = __shfl_sync(m, f.rd[j], src);
-        if (j == q) {
-            rw = w;
-            rd = dd;
-            rf = f.v[j];
-        }
-    }
-    return isfinite(rf) ? rw - rd : DF(rf);
 }
 
 __device__ __forceinline__ void bwd_wave_next(const int *nit, int W, Wave &w)
