@@ -174,9 +174,9 @@ __device__ __forceinline__ float4 *abox_at(const DevCtx &c, int par, int pin, in
 struct AdjItem {
     int t, pin0, kind, nin, z, f0, f1;
     // the lane's first corner, loaded ahead (written by the forward pass):
-    // the output's late slew of this lane's edge, its load, the clock slew
+    // the output's late slews (rise, fall), its load, the clock slew
     // (flip-flop) or the late arrival and slew of each input pin
-    float sz0, ld0, sin0[3][2];
+    float sz0[2], ld0, sin0[3][2];
     DF ain0[3][2];
 };
 
@@ -193,7 +193,8 @@ __device__ __forceinline__ AdjItem adj_prep(const DevCtx &c, const int *tnin, co
     a.z = chk(c, a.z, c.P);
     a.f0 = chk(c, c.fo_ptr[g], (long long)c.F + 1);
     a.f1 = chk(c, c.fo_ptr[g + 1], (long long)c.F + 1);
-    a.sz0 = ld_state(c.slew + (size_t)a.z * K + kq, 2 + (q >> 1));
+    a.sz0[0] = ld_state(c.slew + (size_t)a.z * K + kq, 2);
+    a.sz0[1] = ld_state(c.slew + (size_t)a.z * K + kq, 3);
     a.ld0 = a.t >= 0 ? c.load[(size_t)a.z * K + kq] : 0.f;
     const int nread = a.kind == 1 ? 1 : a.nin;
 #pragma unroll
@@ -209,47 +210,77 @@ __device__ __forceinline__ AdjItem adj_prep(const DevCtx &c, const int *tnin, co
 }
 
 // Lane q of a quad works on output edge rf = q >> 1, arrivals (q & 1 == 0)
-// or slews (q & 1 == 1).  Are the adjoints of every gate-input sink of the
-// item's net complete (all the lane's corners)?  For the lane's first corner
-// the same pass gathers the lane's adjoint of the output: the sum over the
+// or slews (q & 1 == 1); its adjoint of the output is the sum over the net's
 // sinks of dJ/dAT (arrival lanes) or of dJ/dslew * slew_z / slew_sink (slew
-// lanes, through slew_sink = sqrt(slew_z^2 + var)).  Sinks are read four at a
-// time, one component each; the caller's group_all covers the quad.
-// Endpoint sinks were seeded by an earlier launch.
-__device__ __forceinline__ bool adj_probe(const DevCtx &c, const AdjItem &a, int par, int q, float &abar)
+// lanes, through slew_sink = sqrt(slew_z^2 + var)).  Every schedule sums in
+// one order: the entries of each residue class mod 4 in increasing order,
+// then (class 0 + class 1) + (class 2 + class 3).
+__device__ __forceinline__ float4 adj_sink_terms(const DevCtx &c, int s, int k, float4 as, float szr, float szf)
+{
+    const float ssr = ld_state(c.slew + (size_t)s * c.K + k, 2), ssf = ld_state(c.slew + (size_t)s * c.K + k, 3);
+    return make_float4(as.x, as.y, as.z * szr / ssr, as.w * szf / ssf);
+}
+
+// Are the adjoints of every gate-input sink of the item's net complete (all
+// the lane's corners)?  The quad splits the sinks: lane q reads the whole
+// adjoint record of fan-out entries q, q + 4, ... (first corner) and sums
+// each component over them (`part`, its residue class); adj_quad_sum then
+// combines the classes.  Endpoint sinks were seeded by an earlier launch.
+__device__ __forceinline__ bool adj_probe(const DevCtx &c, const AdjItem &a, int par, int q, float4 &part)
 {
     const int K = c.K, kq = corner_lane(c);
-    const int rf = q >> 1;
-    const bool slew_lane = (q & 1) != 0;
-    const int comp_q = slew_lane ? 2 + rf : rf;   // dJ/dAT rise, fall; dJ/dslew rise, fall
+    const int nfo = a.f1 - a.f0;
     bool ok = true;
-    float acc = 0.f;
-    for (int p0 = a.f0; p0 < a.f1; p0 += 4) {
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int e0 = q; e0 < nfo && ok; e0 += 16) {
         int s[4];
-        float v[4], ss[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) s[u] = p0 + u < a.f1 ? chk(c, __ldg(c.fo_pin + p0 + u), c.P) : -1;
+        float4 v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
+            const int e = e0 + 4 * u;
+            s[u] = e < nfo ? chk(c, __ldg(c.fo_pin + a.f0 + e), c.P) : -1;
             if (s[u] < 0) continue;
-            v[u] = s[u] < c.ep_begin ? ld_relaxed1(reinterpret_cast<const float *>(abox_at(c, par, s[u], kq)) + comp_q)
-                                     : ld_state(c.adj + (size_t)s[u] * K + kq, comp_q);
-            ss[u] = slew_lane ? ld_state(c.slew + (size_t)s[u] * K + kq, 2 + rf) : 1.f;
+            v[u] = s[u] < c.ep_begin ? ld_relaxed4(abox_at(c, par, s[u], kq)) : c.adj[(size_t)s[u] * K + kq];
         }
 #pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (s[u] >= 0) ok = ok && complete(v[u]);
+        if (!ok) break;
+#pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (s[u] < 0) continue;
-            ok = ok && v[u] == v[u];
-            acc += slew_lane ? v[u] * a.sz0 / ss[u] : v[u];
+            const float4 tm = adj_sink_terms(c, s[u], kq, v[u], a.sz0[0], a.sz0[1]);
+            acc.x += tm.x;
+            acc.y += tm.y;
+            acc.z += tm.z;
+            acc.w += tm.w;
         }
     }
-    for (int p = a.f0; p < a.f1 && ok; ++p) {
-        const int s = chk(c, __ldg(c.fo_pin + p), c.P);
+    for (int e = q; e < nfo && ok; e += 4) {
+        const int s = chk(c, __ldg(c.fo_pin + a.f0 + e), c.P);
         if (s < c.ep_begin)
             for (int k = kq + c.KL; k < K && ok; k += c.KL) ok = complete(ld_relaxed4(abox_at(c, par, s, k)));
     }
-    abar = acc;
+    part = acc;
     return ok;
+}
+
+// The quad's residue-class sums combined, lane q's component (every lane
+// of the quad calls it).
+__device__ __forceinline__ float adj_quad_sum(float4 part, int q)
+{
+    const unsigned m = quad_mask();
+    const int base = threadIdx.x & 28;
+    float r = 0.f;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const float pj = j == 0 ? part.x : j == 1 ? part.y : j == 2 ? part.z : part.w;
+        const float c0 = __shfl_sync(m, pj, base), c1 = __shfl_sync(m, pj, base + 1);
+        const float c2 = __shfl_sync(m, pj, base + 2), c3 = __shfl_sync(m, pj, base + 3);
+        const float tot = (c0 + c1) + (c2 + c3);
+        if (j == (q >> 1) + 2 * (q & 1)) r = tot;
+    }
+    return r;
 }
 
 __device__ __forceinline__ float quad_sum(float v)
@@ -282,14 +313,21 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
         if (WAIT && first) {
             abar = abar0;
         } else {
-            const float szq = first ? a.sz0 : ld_state(c.slew + (size_t)z * K + k, 2 + rfo);
-            abar = 0.f;
-            for (int p = a.f0; p < a.f1; ++p) {
-                const int s = chk(c, c.fo_pin[p], c.P);
-                const float4 as = (WAIT && s < c.ep_begin) ? ld_relaxed4(abox_at(c, par, s, k)) : c.adj[(size_t)s * K + k];
-                if (slew_lane) abar += (rfo ? as.w : as.z) * szq / ld_state(c.slew + (size_t)s * K + k, 2 + rfo);
-                else abar += rfo ? as.y : as.x;
+            const float szr = first ? a.sz0[0] : ld_state(c.slew + (size_t)z * K + k, 2);
+            const float szf = first ? a.sz0[1] : ld_state(c.slew + (size_t)z * K + k, 3);
+            const int j = rfo + 2 * (slew_lane ? 1 : 0);   // component: dJ/dAT rise, fall, dJ/dslew rise, fall
+            float cls[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r) {
+                cls[r] = 0.f;
+                for (int p = a.f0 + r; p < a.f1; p += 4) {
+                    const int s = chk(c, c.fo_pin[p], c.P);
+                    const float4 as = (WAIT && s < c.ep_begin) ? ld_relaxed4(abox_at(c, par, s, k)) : c.adj[(size_t)s * K + k];
+                    const float4 tm = adj_sink_terms(c, s, k, as, szr, szf);
+                    cls[r] += j == 0 ? tm.x : j == 1 ? tm.y : j == 2 ? tm.z : tm.w;
+                }
             }
+            abar = (cls[0] + cls[1]) + (cls[2] + cls[3]);
         }
         // through the output merges and the NLDM lookups
         float aload = 0.f;
@@ -675,9 +713,9 @@ __global__ void __launch_bounds__(kDfThreadsA) k_df_adjoint(const DevCtx c)
         if (pending) it = adj_prep(c, ti, ti + c.T, x, q);
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
-            float abar;
-            if (pending && group_all(c, adj_probe(c, it, par, q, abar))) {
-                adj_run<UNIFORM, true>(c, lut, ti + 2 * c.T, it, x, q, par, abar);
+            float4 part;
+            if (pending && group_all(c, adj_probe(c, it, par, q, part))) {
+                adj_run<UNIFORM, true>(c, lut, ti + 2 * c.T, it, x, q, par, adj_quad_sum(part, q));
                 pending = false;
             }
             if (__any_sync(0xffffffffu, pending)) {
