@@ -710,7 +710,7 @@ def incremental_loop(a, dev: int, n_iter: int = 20) -> dict:
             "arc_corners_per_s": st_d["arcs"] * K / np.median(walls),
             "wns_setup_ns_by_corner": [r["wns_setup"] for r in rep],
             "gpu_launches_per_iter": stats["launches_per_update"] + stats["launches_per_backward"] + 2,
-            "what": "per iteration: 1% of the cells moved by U(-5, 5) um and 1% resized (LUTs x0.7), then "
+            "what": "per iteration: 1%% of the cells moved by U(-5, 5) um and 1%% resized (LUTs x0.7), then "
                     "set_positions + resize_cells + update_timing + sta_backward (gamma 0.01 ns), all on the "
                     "device; median of %d iterations after 2 warm-up" % n_iter}
 
