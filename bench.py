@@ -637,7 +637,7 @@ def cpu_baseline(d: dict, T: float) -> dict:
                              "runs_s": [round(float(x), 4) for x in sn]}}
 
 
-# ------------------------------------------------------------- reference
+# ---------------------------------------------------------- incremental
 
 def incremental_loop(a, dev: int, n_iter: int = 20) -> dict:
     """The large incremental differentiable loop on 10M cells x 4 corners:
@@ -734,6 +734,8 @@ def run_incremental(a, dist: Dist):
            "gpu_launches": r["iterations"] * r["gpu_launches_per_iter"]}
     print(json.dumps(out))
 
+
+# ------------------------------------------------------------- reference
 
 def run_reference(a, dist: Dist):
     """The FP64 oracle timed on the host cores on this arm's workload: each
