@@ -265,11 +265,12 @@ __device__ __forceinline__ bool adj_probe(const DevCtx &c, const AdjItem &a, int
     return ok;
 }
 
-// The quad's residue-class sums combined, lane q's component (every lane
-// of the quad calls it).
-__device__ __forceinline__ float adj_quad_sum(float4 part, int q)
+// The quad's residue-class sums combined, lane q's component.  Every lane
+// of mask m calls it: the quad's own lanes, or the whole warp when the
+// caller keeps it converged (cheaper shuffles; each quad still sums only
+// its own lanes).
+__device__ __forceinline__ float adj_quad_sum(float4 part, int q, unsigned m = quad_mask())
 {
-    const unsigned m = quad_mask();
     const int base = threadIdx.x & 28;
     float r = 0.f;
 #pragma unroll
@@ -713,10 +714,17 @@ __global__ void __launch_bounds__(kDfThreadsA) k_df_adjoint(const DevCtx c)
         if (pending) it = adj_prep(c, ti, ti + c.T, x, q);
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
-            float4 part;
-            if (pending && group_all(c, adj_probe(c, it, par, q, part))) {
-                adj_run<UNIFORM, true>(c, lut, ti + 2 * c.T, it, x, q, par, adj_quad_sum(part, q));
-                pending = false;
+            float4 part = make_float4(0.f, 0.f, 0.f, 0.f);
+            bool ok = false;
+            if (pending) ok = adj_probe(c, it, par, q, part);
+            const bool go = group_all_warp(c, ok) && pending;   // the whole warp votes
+            if (__any_sync(0xffffffffu, go)) {
+                // every lane sums (full-warp shuffles); the ready groups use it
+                const float sum = adj_quad_sum(part, q, 0xffffffffu);
+                if (go) {
+                    adj_run<UNIFORM, true>(c, lut, ti + 2 * c.T, it, x, q, par, sum);
+                    pending = false;
+                }
             }
             if (__any_sync(0xffffffffu, pending)) {
                 if (++spins >= c.spin_limit) {

@@ -101,17 +101,14 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
         }
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
-            if (pending) {
-                FwdIn in;
-                if (is_item) {
-                    if (group_all(c, fwd_probe<THRU>(c, f, par, q, in))) {
-                        fwd_run<SMOOTH, UNIFORM, true, THRU>(c, L.lut, f, in, x, q, par);
-                        pending = false;
-                    }
-                } else if (group_all(c, ep_probe(c, e, par, q, in.at[0], in.sl[0]))) {
-                    ep_run<true>(c, e, in.at[0], in.sl[0], c.ep_order[chk(c, x - c.I, c.E)], q, par);
-                    pending = false;
-                }
+            FwdIn in;
+            bool ok = false;
+            if (pending)
+                ok = is_item ? fwd_probe<THRU, true>(c, f, par, q, in) : ep_probe(c, e, par, q, in.at[0], in.sl[0]);
+            if (group_all_warp(c, ok) && pending) {   // the whole warp votes
+                if (is_item) fwd_run<SMOOTH, UNIFORM, true, THRU, true>(c, L.lut, f, in, x, q, par);
+                else ep_run<true>(c, e, in.at[0], in.sl[0], c.ep_order[chk(c, x - c.I, c.E)], q, par);
+                pending = false;
             }
             if (__any_sync(0xffffffffu, pending) && !warp_idle_round(c, spins)) break;
         }
@@ -135,9 +132,17 @@ __global__ void __launch_bounds__(kDfThreads) k_df_backward(const DevCtx c)
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
             Fold4 fo;
-            if (pending && group_all(c, bwd_probe_split<THRU>(c, b, par, q, fo))) {
-                bwd_run<UNIFORM, true, THRU>(c, L.lut, L.sense, b, q, par, quad_fold(fo, q));
-                pending = false;
+            bool ok = false;
+            if (pending) ok = bwd_probe_split<THRU>(c, b, par, q, fo);
+            else fold4_clear(fo);
+            const bool go = group_all_warp(c, ok) && pending;   // the whole warp votes
+            if (__any_sync(0xffffffffu, go)) {
+                // every lane folds (full-warp shuffles); the ready groups use it
+                const DF Rz = quad_fold(fo, q, 0xffffffffu);
+                if (go) {
+                    bwd_run<UNIFORM, true, THRU>(c, L.lut, L.sense, b, q, par, Rz);
+                    pending = false;
+                }
             }
             if (__any_sync(0xffffffffu, pending) && !warp_idle_round(c, spins)) break;
         }

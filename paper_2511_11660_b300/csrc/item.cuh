@@ -200,6 +200,18 @@ __device__ __forceinline__ void ld_relaxed_df4(const DF4 *p, DF &x, DF &y, DF &z
                  : "l"(p->v + 2)
                  : "memory");
 }
+// two adjacent double-float components (16 bytes) and two adjacent floats
+__device__ __forceinline__ void ld_relaxed_df2(const DF *p, DF &a, DF &b)
+{
+    asm volatile("ld.relaxed.gpu.global.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(a.hi), "=f"(a.lo), "=f"(b.hi), "=f"(b.lo)
+                 : "l"(p)
+                 : "memory");
+}
+__device__ __forceinline__ void ld_relaxed2(const float *p, float &a, float &b)
+{
+    asm volatile("ld.relaxed.gpu.global.v2.f32 {%0, %1}, [%2];" : "=f"(a), "=f"(b) : "l"(p) : "memory");
+}
 __device__ __forceinline__ void st_relaxed(float *p, float v)
 {
     asm volatile("st.relaxed.gpu.global.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
@@ -289,6 +301,15 @@ __device__ __forceinline__ unsigned group_mask(const DevCtx &c)
 }
 // every lane of the item's group agrees
 __device__ __forceinline__ bool group_all(const DevCtx &c, bool ok) { return __all_sync(group_mask(c), ok); }
+// The same answer from one ballot of the whole warp, for callers that keep
+// all 32 lanes converged (lanes without an item vote false).  A vote over
+// the group's lanes alone costs several times a full-warp ballot when every
+// group of the warp votes at once.
+__device__ __forceinline__ bool group_all_warp(const DevCtx &c, bool ok)
+{
+    const unsigned gm = group_mask(c);
+    return (__ballot_sync(0xffffffffu, ok) & gm) == gm;
+}
 
 // ------------------------------------------------------------- forward
 //
@@ -305,10 +326,13 @@ struct FwdItem {
 };
 
 // the drivers' arrival and slew, component q of the lane's first corner, as
-// probed (the other edge comes from the partner lane q ^ 1)
+// probed; with PAIR the probe also returns the other edge of the same
+// early/late half (component q ^ 1), else it comes from the partner lane
 struct FwdIn {
     DF at[3];
     float sl[3];
+    DF atp[3];
+    float slp[3];
 };
 
 __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, const int *tkind, const int *tsense,
@@ -341,7 +365,7 @@ __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, co
 // group_all over the quad covers the four components.
 // THRU = false: the design has no -through sets (c.pin_adv is NULL); the
 // kernels compiled so carry none of their code and registers.
-template <bool THRU = true>
+template <bool THRU = true, bool PAIR = false>
 __device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int par, int q, FwdIn &in)
 {
     const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
@@ -350,9 +374,22 @@ __device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         if (j < f.nin) {
-            in.at[j] = ld_relaxed_df(fbox_a(c, par, f.drv[j], kq)->v + q);
-            in.sl[j] = ld_relaxed1(reinterpret_cast<const float *>(fbox_s(c, par, f.drv[j], kq)) + q);
-            ok = ok && real_df(in.at[j]) && in.sl[j] == in.sl[j];
+            if (PAIR) {
+                // both edges of the lane's early/late half in one load each
+                DF a0, a1;
+                float s0, s1;
+                ld_relaxed_df2(fbox_a(c, par, f.drv[j], kq)->v + (q & 2), a0, a1);
+                ld_relaxed2(reinterpret_cast<const float *>(fbox_s(c, par, f.drv[j], kq)) + (q & 2), s0, s1);
+                in.at[j] = (q & 1) ? a1 : a0;
+                in.atp[j] = (q & 1) ? a0 : a1;
+                in.sl[j] = (q & 1) ? s1 : s0;
+                in.slp[j] = (q & 1) ? s0 : s1;
+                ok = ok && real_df(a0) && real_df(a1) && s0 == s0 && s1 == s1;
+            } else {
+                in.at[j] = ld_relaxed_df(fbox_a(c, par, f.drv[j], kq)->v + q);
+                in.sl[j] = ld_relaxed1(reinterpret_cast<const float *>(fbox_s(c, par, f.drv[j], kq)) + q);
+                ok = ok && real_df(in.at[j]) && in.sl[j] == in.sl[j];
+            }
             // the lane's other states; with -through every state (a path may
             // come in from the previous tag)
             const int k0 = pin_adv ? 0 : kq + c.KL, dk = pin_adv ? 1 : c.KL;
@@ -373,7 +410,7 @@ struct FwdOut {
     float sl;
 };
 
-template <bool SMOOTH, bool UNIFORM, bool WAIT, bool THRU = true, class L>
+template <bool SMOOTH, bool UNIFORM, bool WAIT, bool THRU = true, bool PAIR = false, class L>
 __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const FwdItem &f, const FwdIn &in, int g,
                                         int q, int par, FwdOut *first = nullptr)
 {
@@ -453,8 +490,8 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
                     s0 = el ? sd.z : sd.x;
                     s1 = el ? sd.w : sd.y;
                 } else if (WAIT && k == kq) {
-                    const DF ap = shfl_xor_df(qm, in.at[j], 1);
-                    const float sp = __shfl_xor_sync(qm, in.sl[j], 1);
+                    const DF ap = PAIR ? in.atp[j] : shfl_xor_df(qm, in.at[j], 1);
+                    const float sp = PAIR ? in.slp[j] : __shfl_xor_sync(qm, in.sl[j], 1);
                     a0 = rfo ? ap : in.at[j];
                     a1 = rfo ? in.at[j] : ap;
                     s0 = rfo ? sp : in.sl[j];
@@ -739,12 +776,24 @@ struct Fold4 {
     float rd[4];
 };
 
-// Reduce the quad's folds (every lane of the quad calls it): per component
-// the extreme value, lowest entry on ties; lane q returns component q's
-// required time (infinite when no sink constrains it).
-__device__ __forceinline__ DF quad_fold(Fold4 &f, int q)
+__device__ __forceinline__ void fold4_clear(Fold4 &f)
 {
-    const unsigned m = quad_mask();
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        f.v[j] = j >= 2 ? INFINITY : -INFINITY;
+        f.idx[j] = 0x7fffffff;
+        f.rw[j] = DF(f.v[j]);
+        f.rd[j] = 0.f;
+    }
+}
+
+// Reduce the quad's folds: per component the extreme value, lowest entry on
+// ties; lane q returns component q's required time (infinite when no sink
+// constrains it).  Every lane of mask m calls it: the quad's own lanes, or
+// the whole warp (m = all lanes) when the caller keeps it converged, which
+// makes the shuffles cheaper; each quad still reduces only its own lanes.
+__device__ __forceinline__ DF quad_fold(Fold4 &f, int q, unsigned m = quad_mask())
+{
     const int base = threadIdx.x & 28;
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
@@ -785,13 +834,7 @@ __device__ __forceinline__ bool bwd_probe_split(const DevCtx &c, const BwdItem &
 {
     const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
     const int K = c.K, kq = corner_lane(c);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        f.v[j] = j >= 2 ? INFINITY : -INFINITY;
-        f.idx[j] = 0x7fffffff;
-        f.rw[j] = DF(f.v[j]);
-        f.rd[j] = 0.f;
-    }
+    fold4_clear(f);
     const int nfo = b.f1 - b.f0;
     for (int e0 = q; e0 < nfo; e0 += 16) {
         int s[4];

@@ -259,8 +259,8 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_forward(const DevCtx c
         bool pending = has(w0) && !bad;
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
+            bool ok = pending;
             if (pending) {
-                bool ok = true;
                 if (cur.id < c.I) {
 #pragma unroll
                     for (int j = 0; j < 3; ++j)
@@ -271,26 +271,26 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_forward(const DevCtx c
                     ok = tile_fwd_input<false>(c, cur.f.drv[0], cur.ring[0], par, q, ring_at, ring_sl, cur.in.at[0],
                                                cur.in.sl[0]);
                 }
-                if (group_all(c, ok)) {
-                    if (cur.id < c.I) {
-                        FwdOut o;
-                        fwd_run<SMOOTH, UNIFORM, true, THRU>(c, L.lut, cur.f, cur.in, cur.id, q, par, &o);
-                        // a held test item leaves its slot NaN: its consumers then wait on the mailbox
-                        const int rs = (((x - base) % R) * KL + kq) * 4 + q;
-                        const bool held = cur.id == c.hold_item;
-                        ring_at[rs] = held ? nan_df() : o.at;
-                        ring_sl[rs] = held ? nan_f() : o.sl;
-                    } else {
-                        EpItem ep;
-                        ep.p = cur.f.pin0;
-                        ep.d = cur.f.drv[0];
-                        ep.isD = cur.f.tag != 0;
-                        ep.Dn0 = cur.f.Dn0[0];
-                        ep.V0 = cur.f.V0[0];
-                        ep_run<true>(c, ep, cur.in.at[0], cur.in.sl[0], cur.f.t, q, par);
-                    }
-                    pending = false;
+            }
+            if (group_all_warp(c, ok) && pending) {   // the whole warp votes
+                if (cur.id < c.I) {
+                    FwdOut o;
+                    fwd_run<SMOOTH, UNIFORM, true, THRU>(c, L.lut, cur.f, cur.in, cur.id, q, par, &o);
+                    // a held test item leaves its slot NaN: its consumers then wait on the mailbox
+                    const int rs = (((x - base) % R) * KL + kq) * 4 + q;
+                    const bool held = cur.id == c.hold_item;
+                    ring_at[rs] = held ? nan_df() : o.at;
+                    ring_sl[rs] = held ? nan_f() : o.sl;
+                } else {
+                    EpItem ep;
+                    ep.p = cur.f.pin0;
+                    ep.d = cur.f.drv[0];
+                    ep.isD = cur.f.tag != 0;
+                    ep.Dn0 = cur.f.Dn0[0];
+                    ep.V0 = cur.f.V0[0];
+                    ep_run<true>(c, ep, cur.in.at[0], cur.in.sl[0], cur.f.t, q, par);
                 }
+                pending = false;
             }
             if (__any_sync(0xffffffffu, pending) && !tile_idle_round(c, spins, &s_abort)) {
                 bad = true;
@@ -403,13 +403,7 @@ __device__ __forceinline__ bool tile_bwd_probe(const DevCtx &c, TileBwd &u, int 
     const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
     const BwdItem &b = u.b;
     const int K = c.K, kq = corner_lane(c);
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        f.v[j] = j >= 2 ? INFINITY : -INFINITY;
-        f.idx[j] = 0x7fffffff;
-        f.rw[j] = DF(f.v[j]);
-        f.rd[j] = 0.f;
-    }
+    fold4_clear(f);
     auto fold = [&](int e, const DF (&m)[4], float nd) {
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
@@ -514,8 +508,13 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_backward(const DevCtx 
         long long spins = 0;
         while (__any_sync(0xffffffffu, pending)) {
             Fold4 fo;
-            if (pending && group_all(c, tile_bwd_probe<THRU>(c, cur, par, q, ring_r, fo))) {
-                const DF Rz = quad_fold(fo, q);
+            bool ok = false;
+            if (pending) ok = tile_bwd_probe<THRU>(c, cur, par, q, ring_r, fo);
+            else fold4_clear(fo);
+            const bool go = group_all_warp(c, ok) && pending;   // the whole warp votes
+            // every lane folds (full-warp shuffles); the ready groups use it
+            const DF Rz = __any_sync(0xffffffffu, go) ? quad_fold(fo, q, 0xffffffffu) : DF(0.f);
+            if (go) {
                 DF first[3];
                 bwd_run<UNIFORM, true, THRU>(c, L.lut, L.sense, cur.b, q, par, Rz, first);
                 if (cur.b.kind == 0) {
