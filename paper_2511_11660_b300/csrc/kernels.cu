@@ -283,18 +283,92 @@ __device__ __forceinline__ void copy_to_tags(const DevCtx &c, int z, int f0, int
     }
 }
 
+// The Elmore sweeps of one net (load, D, second moment, variance).  Node
+// columns A and B and the net's parents, R and C sit in shared memory (node
+// i at element i * kRcThreads of each column) when the net fits there
+// (col), else in global memory (the scratch columns, the plan's RC arrays).
+// SH: every net of the warp fits, so the sweeps use shared-memory accesses
+// only; otherwise each thread picks its own columns (generic accesses, the
+// warp's nets of both kinds in one pass).
+template <bool SH>
+__device__ __forceinline__ void rc_elmore(const DevCtx &c, float *sA, float *sB, const int8_t *spar, const float *sR,
+                                          const float *sC, float *gA, float *gB, bool col, int n0, int n, int f0,
+                                          int f1, int z, int k, float f)
+{
+    constexpr int S = kRcThreads;
+    const int K = c.K;
+    const bool sh = SH || col;
+    auto A = [&](int i) -> float & { return sh ? sA[i * S] : gA[i]; };
+    auto B = [&](int i) -> float & { return sh ? sB[i * S] : gB[i]; };
+    auto par = [&](int i) -> int { return sh ? spar[i * S] : chk(c, __ldg(c.rc_parent + n0 + i), i); };
+    auto Rv = [&](int i) -> float { return sh ? sR[i * S] : __ldg(c.rc_R + n0 + i); };
+    auto Cv = [&](int i) -> float { return sh ? sC[i * S] : __ldg(c.rc_C + n0 + i); };
+    // every rounding is spelled out (products, sums, one FMA per node in
+    // the D and beta sweeps), not left to the compiler's contraction
+    for (int i = 0; i < n; ++i) {
+        const float ci = __fmul_rn(f, Cv(i));
+        A(i) = ci;
+        B(i) = ci;
+    }
+    for (int q0 = f0; q0 < f1; q0 += 4) {
+        int nd[4];
+        float cp[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (q0 + u < f1) {
+                nd[u] = chk(c, __ldg(c.fo_node + q0 + u), n);
+                cp[u] = __fmul_rn(1e3f, __ldg(c.fo_cap + q0 + u));
+            }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (q0 + u < f1) {
+                A(nd[u]) = __fadd_rn(A(nd[u]), cp[u]);
+                B(nd[u]) = __fadd_rn(B(nd[u]), cp[u]);             // node capacitance
+            }
+    }
+    for (int i = n - 1; i > 0; --i) A(par(i)) = __fadd_rn(A(par(i)), A(i));   // Cdown
+    c.load[(size_t)z * K + k] = __fmul_rn(1e-3f, A(0));
+    A(0) = 0.f;
+    B(0) = 0.f;
+    for (int i = 1; i < n; ++i) {
+        const float d = fmaf(__fmul_rn(f, Rv(i)), A(i), A(par(i)));   // Elmore D
+        A(i) = d;
+        B(i) = __fmul_rn(B(i), d);                                     // C_i D_i
+    }
+    for (int i = n - 1; i > 0; --i) B(par(i)) = __fadd_rn(B(par(i)), B(i));   // M
+    B(0) = 0.f;
+    for (int i = 1; i < n; ++i) B(i) = fmaf(__fmul_rn(f, Rv(i)), B(i), B(par(i)));   // beta
+    for (int q0 = f0; q0 < f1; q0 += 4) {
+        int nd[4], sp[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (q0 + u < f1) {
+                nd[u] = chk(c, __ldg(c.fo_node + q0 + u), n);
+                sp[u] = chk(c, __ldg(c.fo_pin + q0 + u), c.P);
+            }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+            if (q0 + u < f1) {
+                const float Dn = A(nd[u]);
+                c.netD[(size_t)sp[u] * K + k] = __fmul_rn(1e-6f, Dn);
+                c.netV[(size_t)sp[u] * K + k] = __fmul_rn(1e-12f, fmaxf(fmaf(-Dn, Dn, __fmul_rn(2.f, B(nd[u]))), 0.f));
+            }
+    }
+}
+
 __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
 {
     __shared__ int8_t s_par[kRcColNodes * kRcThreads];
     __shared__ float s_R[kRcColNodes * kRcThreads], s_C[kRcColNodes * kRcThreads];
     __shared__ float s_A[kRcColNodes * kRcThreads], s_B[kRcColNodes * kRcThreads];
     const int t = threadIdx.x;
-    const int K = c.K;
     // one thread per (net, corner); the exception tags of a corner share
     // its net values, computed at the corner's first state and copied
     const long long gk = (long long)blockIdx.x * kRcThreads + t;
     if (gk >= (long long)c.I * c.Kc) return;
-    const int g = (int)(gk / c.Kc), kc = (int)(gk % c.Kc), k = kc * c.Tg;
+    // (net, corner) from the thread index: I * Kc < 2^31 (checked at set-up)
+    const unsigned u = (unsigned)gk, nk = (unsigned)c.Kc;
+    const int g = nk == 1u ? (int)u : (int)(u / nk), kc = nk == 1u ? 0 : (int)(u % nk), k = kc * c.Tg;
     const int n0 = chk(c, c.rc_ptr[g], c.NN + 1);
     const int n = c.steiner ? chk(c, c.st_nlive[g], chk(c, c.rc_ptr[g + 1], c.NN + 1) - n0 + 1)
                             : chk(c, c.rc_ptr[g + 1], c.NN + 1) - n0;
@@ -320,72 +394,26 @@ __global__ void __launch_bounds__(kRcThreads) k_net_tree(const DevCtx c)
             }
     }
     const size_t so = (size_t)kc * c.NN + n0;   // global scratch: one copy per corner
-    const ColRef A = col ? ColRef{s_A + t, kRcThreads} : ColRef{c.scratch_a + so, 1};
-    const ColRef B = col ? ColRef{s_B + t, kRcThreads} : ColRef{c.scratch_b + so, 1};
-    auto par = [&](int i) -> int { return col ? s_par[i * kRcThreads + t] : chk(c, __ldg(c.rc_parent + n0 + i), i); };
-    auto Rv = [&](int i) -> float { return col ? s_R[i * kRcThreads + t] : __ldg(c.rc_R + n0 + i); };
-    auto Cv = [&](int i) -> float { return col ? s_C[i * kRcThreads + t] : __ldg(c.rc_C + n0 + i); };
     const int z = chk(c, item_out_pin(c, chk_type(c, c.item_type[g]), c.item_pin0[g]), c.P);
-    {
-        const float f = __ldg(c.rc_scale + k);
-        for (int i = 0; i < n; ++i) {
-            const float ci = f * Cv(i);
-            A[i] = ci;
-            B[i] = ci;
-        }
-        for (int q0 = f0; q0 < f1; q0 += 4) {
-            int nd[4];
-            float cp[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (q0 + u < f1) {
-                    nd[u] = chk(c, __ldg(c.fo_node + q0 + u), n);
-                    cp[u] = 1e3f * __ldg(c.fo_cap + q0 + u);
-                }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (q0 + u < f1) {
-                    A[nd[u]] += cp[u];
-                    B[nd[u]] += cp[u];                                   // node capacitance
-                }
-        }
-        for (int i = n - 1; i > 0; --i) A[par(i)] += A[i];              // Cdown
-        c.load[(size_t)z * K + k] = 1e-3f * A[0];
-        A[0] = 0.f;
-        B[0] = 0.f;
-        for (int i = 1; i < n; ++i) {
-            const float d = A[par(i)] + f * Rv(i) * A[i];               // Elmore D
-            A[i] = d;
-            B[i] *= d;                                                   // C_i D_i
-        }
-        for (int i = n - 1; i > 0; --i) B[par(i)] += B[i];              // M
-        B[0] = 0.f;
-        for (int i = 1; i < n; ++i) B[i] = B[par(i)] + f * Rv(i) * B[i];   // beta
-        for (int q0 = f0; q0 < f1; q0 += 4) {
-            int nd[4], sp[4];
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (q0 + u < f1) {
-                    nd[u] = chk(c, __ldg(c.fo_node + q0 + u), n);
-                    sp[u] = chk(c, __ldg(c.fo_pin + q0 + u), c.P);
-                }
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-                if (q0 + u < f1) {
-                    const float Dn = A[nd[u]];
-                    c.netD[(size_t)sp[u] * K + k] = 1e-6f * Dn;
-                    c.netV[(size_t)sp[u] * K + k] = 1e-12f * fmaxf(2.f * B[nd[u]] - Dn * Dn, 0.f);
-                }
-        }
-        if (c.net_model == kNetArnoldi && n > 1) {
-            // node capacitance again (wire * f + sink pins), in the C column
-            const ColRef Cn = col ? ColRef{s_C + t, kRcThreads} : ColRef{c.scratch_c + so, 1};
-            for (int i = 0; i < n; ++i) Cn[i] = f * Cv(i);
-            for (int q = f0; q < f1; ++q) Cn[chk(c, __ldg(c.fo_node + q), n)] += 1e3f * __ldg(c.fo_cap + q);
-            arnoldi_delays(c, n, f, c.arnoldi_q, A, B, Cn, par, Rv, f0, f1, K, k);
-        }
-        if (c.Tg > 1) copy_to_tags(c, z, f0, f1, k);
+    const float f = __ldg(c.rc_scale + k);
+    if (__all_sync(__activemask(), col))
+        rc_elmore<true>(c, s_A + t, s_B + t, s_par + t, s_R + t, s_C + t, nullptr, nullptr, true, n0, n, f0, f1, z, k, f);
+    else
+        rc_elmore<false>(c, s_A + t, s_B + t, s_par + t, s_R + t, s_C + t, c.scratch_a + so, c.scratch_b + so, col, n0,
+                         n, f0, f1, z, k, f);
+    if (c.net_model == kNetArnoldi && n > 1) {
+        const ColRef A = col ? ColRef{s_A + t, kRcThreads} : ColRef{c.scratch_a + so, 1};
+        const ColRef B = col ? ColRef{s_B + t, kRcThreads} : ColRef{c.scratch_b + so, 1};
+        auto par = [&](int i) -> int { return col ? s_par[i * kRcThreads + t] : chk(c, __ldg(c.rc_parent + n0 + i), i); };
+        auto Rv = [&](int i) -> float { return col ? s_R[i * kRcThreads + t] : __ldg(c.rc_R + n0 + i); };
+        auto Cv = [&](int i) -> float { return col ? s_C[i * kRcThreads + t] : __ldg(c.rc_C + n0 + i); };
+        // node capacitance again (wire * f + sink pins), in the C column
+        const ColRef Cn = col ? ColRef{s_C + t, kRcThreads} : ColRef{c.scratch_c + so, 1};
+        for (int i = 0; i < n; ++i) Cn[i] = f * Cv(i);
+        for (int q = f0; q < f1; ++q) Cn[chk(c, __ldg(c.fo_node + q), n)] += 1e3f * __ldg(c.fo_cap + q);
+        arnoldi_delays(c, n, f, c.arnoldi_q, A, B, Cn, par, Rv, f0, f1, c.K, k);
     }
+    if (c.Tg > 1) copy_to_tags(c, z, f0, f1, k);
 }
 
 // Star trees from positions: segment R = r L, C = c L (half at each end),

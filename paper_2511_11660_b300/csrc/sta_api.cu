@@ -201,6 +201,9 @@ sta_status create_from_plan(sta_ctx *c, int device)
 {
     Plan &pl = c->plan;
     c->device = device;
+    // the RC sweep numbers its (net, corner) threads in 32 bits
+    if ((long long)pl.I * pl.Kc >= (1LL << 31))
+        return fail(c, STA_EINVAL, "too many items x corners (must be below 2^31)");
     CK(cudaSetDevice(device));
     CK(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
     DevCtx &d = c->dc;
