@@ -55,9 +55,10 @@ __device__ __forceinline__ int next_chunk(const DevCtx &c, int counter, int n_ch
 {
     int ch = 0;
     if ((threadIdx.x & 31) == 0) ch = (int)atomicAdd(c.df_state + counter, 1u);
+    const unsigned aborted = ld_volatile(c.df_state + 3);   // read while the claim is in flight
     ch = __shfl_sync(0xffffffffu, ch, 0);
     if (ch >= n_chunks) return -1;
-    if (ld_volatile(c.df_state + 3)) return -1;
+    if (aborted) return -1;
     return ch;
 }
 

@@ -676,6 +676,9 @@ struct BwdItem {
     // input pin (CK: the slew of the rising component of this lane's el)
     DF az0, a0[3];
     float s0[3];
+    // sink pins of the fan-out entries q, q + 4, q + 8, q + 12 (-1: none),
+    // the ones the lane's probe reads first
+    int sk[4];
 };
 
 __device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, const int *tkind, int g, int q)
@@ -690,6 +693,11 @@ __device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, co
     b.z = chk(c, b.t < 0 ? b.pin0 : (b.kind == 1 ? b.pin0 + 1 : b.pin0 + b.nin), c.P);
     b.f0 = chk(c, c.fo_ptr[g], (long long)c.F + 1);
     b.f1 = chk(c, c.fo_ptr[g + 1], (long long)c.F + 1);
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int e = q + 4 * u;
+        b.sk[u] = e < b.f1 - b.f0 ? chk(c, __ldg(c.fo_pin + b.f0 + e), c.P) : -1;
+    }
     b.ld0 = b.t >= 0 ? c.load[(size_t)b.z * K + kq] : 0.f;
     b.az0 = ld_state_df(c.at + (size_t)b.z * K + kq, q);
     const int nread = b.kind == 1 ? 1 : b.kind == 0 ? b.nin : 0;
@@ -843,7 +851,8 @@ __device__ __forceinline__ bool bwd_probe_split(const DevCtx &c, const BwdItem &
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             const int e = e0 + 4 * u;
-            s[u] = e < nfo ? chk(c, __ldg(c.fo_pin + b.f0 + e), c.P) : -1;
+            // the first group's sinks were read ahead
+            s[u] = e0 == q ? b.sk[u] : e < nfo ? chk(c, __ldg(c.fo_pin + b.f0 + e), c.P) : -1;
             nd[u] = 0.f;
             if (s[u] < 0) continue;
             const int ks = (pin_adv && ((pin_adv[s[u]] >> (kq % c.Tg)) & 1u)) ? kq + 1 : kq;
