@@ -391,15 +391,20 @@ sta_status sta_set_wait_limit(sta_ctx *ctx, int64_t polls);
  * operation. */
 sta_status sta_debug_hold_cell(sta_ctx *ctx, int32_t cell);
 
-/* Full analysis on `stream`: net delay calculation, forward arrival/slew
+/* Full analysis on `stream` (Sec. III: the engine's graph-based analysis
+ * with the "Delay models" paragraph's NLDM cell delays and Elmore or
+ * Arnoldi net delays): net delay calculation, forward arrival/slew
  * propagation, endpoint required times, backward required-time propagation,
- * pin and endpoint slacks, FP64 WNS/TNS.  Asynchronous. */
+ * pin and endpoint slacks, FP64 WNS/TNS.  Asynchronous; errors of the
+ * device work surface at the next synchronising call. */
 sta_status sta_update_timing(sta_ctx *ctx, void *stream);
 
 /* Wait for the context's work on `stream` and surface device errors. */
 sta_status sta_sync(sta_ctx *ctx, void *stream);
 
-/* Synchronise and fill reports[n_corners] (design 0 of a batch). */
+/* Synchronise and fill reports[n_corners] (design 0 of a batch): WNS/TNS
+ * and worst slacks per corner, the WNS/TNS of Sec. III "Report options".
+ * Caller owns `reports` (host memory). */
 sta_status sta_report_slack(sta_ctx *ctx, void *stream, sta_corner_report *reports);
 /* Same for design `d` of a batch context. */
 sta_status sta_report_slack_design(sta_ctx *ctx, int32_t d, void *stream, sta_corner_report *reports);
@@ -422,8 +427,9 @@ sta_status sta_get_net_wirelength(sta_ctx *ctx, int64_t *wl_nm, sta_mem mem, voi
 sta_status sta_get_endpoint_slack(sta_ctx *ctx, float *setup, float *hold, uint8_t *viol_setup,
                                   uint8_t *viol_hold, sta_mem mem, void *stream);
 
-/* Differentiable mode (gamma_ns > 0, positions): after sta_update_timing,
- * compute the smoothed objective
+/* Differentiable mode (gamma_ns > 0, positions; the timing feedback a
+ * timing-driven placer takes from the engine, Sec. IV-C): after
+ * sta_update_timing, compute the smoothed objective
  *   J = w_tns * TNS_g + w_wns * WNS_g,  summed over corners, with
  *   s_e   = smooth min over rise/fall of (RAT_e - AT_late,e),
  *   TNS_g = -sum_e g * softplus(-s_e / g),  WNS_g = -g * log sum_e exp(-s_e / g)
