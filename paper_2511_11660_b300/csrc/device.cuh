@@ -16,7 +16,8 @@ constexpr int kRcThreads = 128;    // threads (nets) per block of the RC sweep
 constexpr int kStMaxPins = 64;     // nets of more pins keep the rectilinear MST (plan.h: kSteinerMaxPins)
 constexpr int kRedThreads = 256;   // threads of the reduction kernels
 constexpr int kDfStateWords = 16;  // schedule state words (see DevCtx::df_state)
-constexpr int kRedChunk = 4096;    // endpoints per first-stage reduction block
+constexpr int kRedChunk = 1024;    // endpoints per first-stage reduction block
+static_assert(kRedChunk % kRedThreads == 0, "a reduction thread folds a whole number of endpoints");
 
 // device error word bits (sta_sync maps them to sta_status)
 constexpr unsigned kErrTimeout = 1u;

@@ -486,74 +486,116 @@ __global__ void k_bwd_level(const DevCtx c, int i0, int i1)
 // partials (TNS setup, TNS hold, worst setup, worst hold, violation counts).
 // Stage 2: one block per (design, corner) folds that design's chunks into
 // WNS = min(0, worst), TNS = sum of negatives.
+// The partials of a reduction: TNS setup and hold (FP64 sums of FP32
+// slacks), worst setup and hold (FP32, exact), violation counts (integers).
+// Only the sums take FP64 arithmetic, B300's FP64 pipe being narrow.
+struct Fold6 {
+    double ts, th;
+    float ms, mh;
+    int ns, nh;
+};
+__device__ __forceinline__ Fold6 fold6_init() { return Fold6{0.0, 0.0, INFINITY, INFINITY, 0, 0}; }
+__device__ __forceinline__ void fold6_add(Fold6 &a, const Fold6 &b)
+{
+    a.ts += b.ts;
+    a.th += b.th;
+    a.ms = fminf(a.ms, b.ms);
+    a.mh = fminf(a.mh, b.mh);
+    a.ns += b.ns;
+    a.nh += b.nh;
+}
+// A block's partials folded in a fixed order: a butterfly across each warp
+// (every lane ends with the same value: each step combines the same two
+// operands), then thread 0 folds the warps' values in warp order; its
+// return value is the block's result.
 template <int NT>
-__device__ __forceinline__ void block_fold6(double v[6], double (*sh)[NT])
+__device__ __forceinline__ Fold6 block_fold6(Fold6 f, Fold6 *sh)
 {
 #pragma unroll
-    for (int q = 0; q < 6; ++q) sh[q][threadIdx.x] = v[q];
-    __syncthreads();
-    for (int w = NT / 2; w > 0; w >>= 1) {
-        if (threadIdx.x < w) {
-            sh[0][threadIdx.x] += sh[0][threadIdx.x + w];
-            sh[1][threadIdx.x] += sh[1][threadIdx.x + w];
-            sh[2][threadIdx.x] = fmin(sh[2][threadIdx.x], sh[2][threadIdx.x + w]);
-            sh[3][threadIdx.x] = fmin(sh[3][threadIdx.x], sh[3][threadIdx.x + w]);
-            sh[4][threadIdx.x] += sh[4][threadIdx.x + w];
-            sh[5][threadIdx.x] += sh[5][threadIdx.x + w];
-        }
-        __syncthreads();
+    for (int off = 16; off > 0; off >>= 1) {
+        Fold6 o;
+        o.ts = __shfl_xor_sync(0xffffffffu, f.ts, off);
+        o.th = __shfl_xor_sync(0xffffffffu, f.th, off);
+        o.ms = __shfl_xor_sync(0xffffffffu, f.ms, off);
+        o.mh = __shfl_xor_sync(0xffffffffu, f.mh, off);
+        o.ns = __shfl_xor_sync(0xffffffffu, f.ns, off);
+        o.nh = __shfl_xor_sync(0xffffffffu, f.nh, off);
+        fold6_add(f, o);
     }
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = f;
+    __syncthreads();
+    Fold6 r = sh[0];
+    if (threadIdx.x == 0)
+        for (int w = 1; w < NT / 32; ++w) fold6_add(r, sh[w]);
+    return r;
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_reduce_chunks(const DevCtx c)
 {
-    __shared__ double sh[6][kRedThreads];
+    __shared__ Fold6 sh[kRedThreads / 32];
     const int b = blockIdx.x, k = blockIdx.y, K = c.Kc;
     const int e0 = c.red_chunk_ptr[b], e1 = c.red_chunk_ptr[b + 1];
-    double v[6] = {0, 0, INFINITY, INFINITY, 0, 0};
-    for (int e = e0 + threadIdx.x; e < e1; e += kRedThreads) {
+    // thread t folds endpoints e0 + t + i * kRedThreads in increasing i; every
+    // slack is loaded first, so the loads are in flight together
+    constexpr int kPer = kRedChunk / kRedThreads;
+    float fsv[kPer], fhv[kPer];
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        const int e = e0 + threadIdx.x + i * kRedThreads;
         // the endpoint's slack at corner k: min over its exception tags
         float fs = INFINITY, fh = INFINITY;
-        for (int g = 0; g < c.Tg; ++g) {
-            fs = fminf(fs, c.ep_setup[(size_t)e * c.K + k * c.Tg + g]);
-            fh = fminf(fh, c.ep_hold[(size_t)e * c.K + k * c.Tg + g]);
-        }
-        const double ss = fs, hs = fh;
-        v[2] = fmin(v[2], ss);
-        v[3] = fmin(v[3], hs);
-        if (ss < 0) { v[0] += ss; v[4] += 1; }
-        if (hs < 0) { v[1] += hs; v[5] += 1; }
+        if (e < e1)
+            for (int g = 0; g < c.Tg; ++g) {
+                fs = fminf(fs, c.ep_setup[(size_t)e * c.K + k * c.Tg + g]);
+                fh = fminf(fh, c.ep_hold[(size_t)e * c.K + k * c.Tg + g]);
+            }
+        fsv[i] = fs;
+        fhv[i] = fh;
     }
-    block_fold6<kRedThreads>(v, sh);
-    if (threadIdx.x < 6) c.red_partial[((size_t)b * K + k) * 6 + threadIdx.x] = sh[threadIdx.x][0];
+    Fold6 f = fold6_init();
+#pragma unroll
+    for (int i = 0; i < kPer; ++i) {
+        if (e0 + (int)threadIdx.x + i * kRedThreads >= e1) break;
+        const float fs = fsv[i], fh = fhv[i];
+        f.ms = fminf(f.ms, fs);
+        f.mh = fminf(f.mh, fh);
+        if (fs < 0.f) { f.ts += (double)fs; ++f.ns; }
+        if (fh < 0.f) { f.th += (double)fh; ++f.nh; }
+    }
+    f = block_fold6<kRedThreads>(f, sh);
+    if (threadIdx.x == 0) {
+        double *o = c.red_partial + ((size_t)b * K + k) * 6;
+        o[0] = f.ts;
+        o[1] = f.th;
+        o[2] = f.ms;
+        o[3] = f.mh;
+        o[4] = f.ns;
+        o[5] = f.nh;
+    }
 }
 
 __global__ void __launch_bounds__(kRedThreads) k_reduce_final(const DevCtx c)
 {
-    __shared__ double sh[6][kRedThreads];
+    __shared__ Fold6 sh[kRedThreads / 32];
     const int d = blockIdx.x / c.Kc, k = blockIdx.x % c.Kc, K = c.Kc;
     const int b0 = c.red_design_chunk[d], b1 = c.red_design_chunk[d + 1];
-    double v[6] = {0, 0, INFINITY, INFINITY, 0, 0};
+    Fold6 f = fold6_init();
     for (int b = b0 + threadIdx.x; b < b1; b += kRedThreads) {
         const double *p = c.red_partial + ((size_t)b * K + k) * 6;
-        v[0] += p[0];
-        v[1] += p[1];
-        v[2] = fmin(v[2], p[2]);
-        v[3] = fmin(v[3], p[3]);
-        v[4] += p[4];
-        v[5] += p[5];
+        // minima and counts were stored from FP32 values and integers: exact
+        fold6_add(f, Fold6{p[0], p[1], (float)p[2], (float)p[3], (int)p[4], (int)p[5]});
     }
-    block_fold6<kRedThreads>(v, sh);
+    f = block_fold6<kRedThreads>(f, sh);
     if (threadIdx.x == 0) {
         double *o = c.report + ((size_t)d * K + k) * 8;
-        o[0] = fmin(0.0, sh[2][0]);
-        o[1] = sh[0][0];
-        o[2] = fmin(0.0, sh[3][0]);
-        o[3] = sh[1][0];
-        o[4] = sh[2][0];
-        o[5] = sh[3][0];
-        o[6] = sh[4][0];
-        o[7] = sh[5][0];
+        o[0] = fmin(0.0, (double)f.ms);
+        o[1] = f.ts;
+        o[2] = fmin(0.0, (double)f.mh);
+        o[3] = f.th;
+        o[4] = f.ms;
+        o[5] = f.mh;
+        o[6] = f.ns;
+        o[7] = f.nh;
     }
 }
 
