@@ -287,9 +287,6 @@ __device__ __forceinline__ bool arc_on(int sense, int rfi, int rfo)
 // lanes of the quad that owns this lane
 __device__ __forceinline__ unsigned quad_mask() { return 0xFu << (threadIdx.x & 28); }
 
-// every lane of the quad agrees
-__device__ __forceinline__ bool quad_all(bool ok) { return __all_sync(quad_mask(), ok); }
-
 // Corners are spread over c.KL quads: an item owns 4 * KL consecutive lanes,
 // and the quad with corner offset kq handles corners kq, kq + KL, ...
 __device__ __forceinline__ int corner_lane(const DevCtx &c) { return (threadIdx.x >> 2) & (c.KL - 1); }
@@ -299,12 +296,10 @@ __device__ __forceinline__ unsigned group_mask(const DevCtx &c)
     if (w >= 32) return 0xffffffffu;
     return ((1u << w) - 1u) << ((threadIdx.x & 31) & ~(w - 1));
 }
-// every lane of the item's group agrees
-__device__ __forceinline__ bool group_all(const DevCtx &c, bool ok) { return __all_sync(group_mask(c), ok); }
-// The same answer from one ballot of the whole warp, for callers that keep
-// all 32 lanes converged (lanes without an item vote false).  A vote over
-// the group's lanes alone costs several times a full-warp ballot when every
-// group of the warp votes at once.
+// Does every lane of the item's group agree?  One ballot of the whole warp:
+// callers keep all 32 lanes converged (lanes without an item vote false).  A
+// vote over each group's own lanes (a 4-lane mask) costs many times a
+// full-warp ballot when every group of the warp votes at once.
 __device__ __forceinline__ bool group_all_warp(const DevCtx &c, bool ok)
 {
     const unsigned gm = group_mask(c);
@@ -361,8 +356,9 @@ __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, co
 }
 
 // Are the drivers' arrivals and slews of the lane's corners complete?  Lane
-// q reads component q of its first corner (returned in `in`); the caller's
-// group_all over the quad covers the four components.
+// q reads component q of its first corner (returned in `in`; with PAIR also
+// the other edge of its early/late half); the caller's group vote
+// (group_all_warp) over the quad covers the four components.
 // THRU = false: the design has no -through sets (c.pin_adv is NULL); the
 // kernels compiled so carry none of their code and registers.
 template <bool THRU = true, bool PAIR = false>
@@ -600,8 +596,8 @@ __device__ __forceinline__ EpItem ep_prep(const DevCtx &c, int e)
 }
 
 // the driver's arrival and slew of the lane's corners are complete; lane q
-// reads component q of its first corner (returned; the caller's group_all
-// covers the quad)
+// reads component q of its first corner (returned; the caller's group vote,
+// group_all_warp, covers the quad)
 __device__ __forceinline__ bool ep_probe(const DevCtx &c, const EpItem &x, int par, int q, DF &at0, float &sl0)
 {
     const int kq = corner_lane(c);
@@ -712,8 +708,8 @@ __device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, co
 }
 
 // Are the required times of every sink of the item's net complete (all the
-// lane's corners)?  Lane q reads component q only: the caller's group_all
-// over the quad covers the four.  Sinks are read four at a time, their
+// lane's corners)?  Lane q reads component q only: the caller's group vote
+// (group_all_warp) over the quad covers the four.  Sinks are read four at a time, their
 // loads in flight together.  For the lane's first corner the same pass
 // folds them: R = min (late) / max (early) over the sinks of RAT - Elmore
 // delay, component q -- the output's required time, ready for bwd_run.
@@ -835,7 +831,7 @@ __device__ __forceinline__ DF quad_fold(Fold4 &f, int q, unsigned m = quad_mask(
 // bwd_probe with the fold split over the quad (Fold4): lane q reads all
 // four components of fan-out entries q, q + 4, ... (four at a time, their
 // loads in flight together) for the lane's first corner.  The caller's
-// group_all covers the quad, then quad_fold gives each lane its component's
+// group vote covers the quad, then quad_fold gives each lane its component's
 // required time -- the same value as bwd_probe's.
 template <bool THRU = true>
 __device__ __forceinline__ bool bwd_probe_split(const DevCtx &c, const BwdItem &b, int par, int q, Fold4 &f)
