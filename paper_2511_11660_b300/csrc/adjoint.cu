@@ -297,9 +297,21 @@ __device__ __forceinline__ float quad_sum(float v)
 // of the slews (q & 1 == 1, slew tables), for the quad's corners; the quad
 // sums the partials.  The segment gradients are summed over corners (and the
 // driver's over all its segments) before the FP64 atomics.
-template <bool UNIFORM, bool WAIT, class Lut>
+// The lane's partials of one item for its first corner, before the quad
+// sums: the load adjoint and the adjoints of each input candidate's arrival
+// (aAin) and slew (aSin).
+struct AdjPart {
+    float aload, aAin[6], aSin[6];
+};
+
+// SPLIT (one corner per lane group, K == KL, with WAIT): adj_run stops
+// before the quad sums and returns the lane's partials in *part; the caller
+// sums them over the quad with the whole warp converged (adj_part_sum) and
+// stores them (adj_store).  The sums and the stores are the ones adj_run
+// makes itself otherwise.
+template <bool UNIFORM, bool WAIT, bool SPLIT = false, class Lut>
 __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const int *tsense, const AdjItem &a, int g,
-                                        int q, int par, float abar0)
+                                        int q, int par, float abar0, AdjPart *part = nullptr)
 {
     const int t = a.t, pin0 = a.pin0, z = a.z, K = c.K, nin = a.nin;
     const int kq = corner_lane(c), KL = c.KL;
@@ -410,6 +422,15 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
                 }
             }
         }
+        if (SPLIT) {
+            part->aload = aload;
+#pragma unroll
+            for (int i = 0; i < 6; ++i) {
+                part->aAin[i] = aAin[i];
+                part->aSin[i] = aSin[i];
+            }
+            return;
+        }
         aload = quad_sum(aload);
         if (q == 0) c.aload[(size_t)g * K + k] = aload;
         if (a.kind == 0) {
@@ -429,6 +450,39 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
                 }
             }
         }
+    }
+}
+
+// The quad sums of the partials (every lane of mask m calls it: the whole
+// warp, converged), in quad_sum's order.
+__device__ __forceinline__ void adj_part_sum(AdjPart &p, unsigned m)
+{
+    p.aload += __shfl_xor_sync(m, p.aload, 1);
+    p.aload += __shfl_xor_sync(m, p.aload, 2);
+#pragma unroll
+    for (int i = 0; i < 6; ++i) {
+        p.aAin[i] += __shfl_xor_sync(m, p.aAin[i], 1);
+        p.aAin[i] += __shfl_xor_sync(m, p.aAin[i], 2);
+        p.aSin[i] += __shfl_xor_sync(m, p.aSin[i], 1);
+        p.aSin[i] += __shfl_xor_sync(m, p.aSin[i], 2);
+    }
+}
+
+// adj_run's stores of the summed partials (first corner; the dataflow sweep)
+__device__ __forceinline__ void adj_store(const DevCtx &c, const AdjItem &a, int g, int q, int par, const AdjPart &p)
+{
+    const int K = c.K, k = corner_lane(c);
+    if (q == 0) c.aload[(size_t)g * K + k] = p.aload;
+    if (a.kind != 0) return;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        if (j >= a.nin) continue;
+        const float v = q == 0 ? p.aAin[j * 2] : q == 1 ? p.aAin[j * 2 + 1] : q == 2 ? p.aSin[j * 2] : p.aSin[j * 2 + 1];
+        reinterpret_cast<float *>(c.adj + (size_t)(a.pin0 + j) * K + k)[q] = v;
+        float *n = reinterpret_cast<float *>(abox_at(c, par, a.pin0 + j, k));
+        float *o = reinterpret_cast<float *>(abox_at(c, par ^ 1, a.pin0 + j, k));
+        st_relaxed(n + q, v);
+        o[q] = __int_as_float(0x7fffffff);
     }
 }
 
@@ -721,7 +775,17 @@ __global__ void __launch_bounds__(kDfThreadsA) k_df_adjoint(const DevCtx c)
             if (__any_sync(0xffffffffu, go)) {
                 // every lane sums (full-warp shuffles); the ready groups use it
                 const float sum = adj_quad_sum(part, q, 0xffffffffu);
-                if (go) {
+                if (c.K == c.KL) {
+                    // one corner per group: the quad sums of the item's
+                    // partials also run converged
+                    AdjPart ap{};
+                    if (go) adj_run<UNIFORM, true, true>(c, lut, ti + 2 * c.T, it, x, q, par, sum, &ap);
+                    adj_part_sum(ap, 0xffffffffu);
+                    if (go) {
+                        adj_store(c, it, x, q, par, ap);
+                        pending = false;
+                    }
+                } else if (go) {
                     adj_run<UNIFORM, true>(c, lut, ti + 2 * c.T, it, x, q, par, sum);
                     pending = false;
                 }
