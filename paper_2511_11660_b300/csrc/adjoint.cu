@@ -491,49 +491,53 @@ __device__ __forceinline__ void adj_store(const DevCtx &c, const AdjItem &a, int
 // D = r L (c L / 2 + Cpin) and variance D^2) and the driver's load adjoint
 // (load = sum of c L + Cpin), summed over corners, then to the two cells'
 // positions through L = |dx| + |dy| (sign 0 at dx = 0).  One thread per
-// item's net; the driver cell gets one atomic pair per net.
+// fan-out entry (segment); each segment adds its share to both cells.
 __global__ void k_adj_star(const DevCtx c)
 {
-    const int g = blockIdx.x * blockDim.x + threadIdx.x;
-    if (g >= c.I) return;
-    const int f0 = chk(c, c.fo_ptr[g], (long long)c.F + 1), f1 = chk(c, c.fo_ptr[g + 1], (long long)c.F + 1);
-    if (f0 >= f1) return;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= c.F) return;
     const int K = c.K;
-    const int z = chk(c, item_out_pin(c, chk_type(c, c.item_type[g]), c.item_pin0[g]), c.P);
-    const float2 pz = pin_pos(c, z);
-    const int cz = c.pin_cell[z];
-    double gdx = 0.0, gdy = 0.0;
-    for (int p = f0; p < f1; ++p) {
-        const int s = chk(c, c.fo_pin[p], c.P);
-        const float2 ps = pin_pos(c, s);
-        const float dx = pz.x - ps.x, dy = pz.y - ps.y;
-        const float L = fabsf(dx) + fabsf(dy);
-        const float cp = 1e3f * c.fo_cap[p];
-        float dJdL = 0.f;
-        for (int k = 0; k < K; ++k) {
-            const float fk = __ldg(c.rc_scale + k);
-            const float r = fk * c.r_per_um, cc = fk * c.c_per_um;
-            const float4 as = c.adj[(size_t)s * K + k];
-            const float4 Ss = c.slew[(size_t)s * K + k];
-            const float Draw = r * L * (0.5f * cc * L + cp);
-            const float dDdL = r * (cc * L + cp);
-            const float Dbar = as.x + as.y;
-            const float Vbar = as.z / (2.f * Ss.z) + as.w / (2.f * Ss.w);
-            dJdL += Dbar * 1e-6f * dDdL + Vbar * 1e-12f * 2.f * Draw * dDdL + c.aload[(size_t)g * K + k] * 1e-3f * cc;
+    // every input of this kernel is read-only here (read-only loads)
+    auto pos = [&](int cell_or_port) -> float2 {
+        if (cell_or_port >= 0) {
+            const int cc = chk(c, cell_or_port, c.C);
+            return make_float2(__ldg(c.cell_xy + 2 * (size_t)cc), __ldg(c.cell_xy + 2 * (size_t)cc + 1));
         }
-        const double gx = (double)dJdL * (double)((dx > 0.f) - (dx < 0.f));
-        const double gy = (double)dJdL * (double)((dy > 0.f) - (dy < 0.f));
-        gdx += gx;
-        gdy += gy;
-        const int cs = c.pin_cell[s] >= 0 ? chk(c, c.pin_cell[s], c.C) : -1;
-        if (cs >= 0) {
-            atomicAdd(c.grad + 2 * (size_t)cs, -gx);
-            atomicAdd(c.grad + 2 * (size_t)cs + 1, -gy);
-        }
+        const int q = -cell_or_port - 1;
+        return make_float2(__ldg(c.port_xy + 2 * (size_t)q), __ldg(c.port_xy + 2 * (size_t)q + 1));
+    };
+    const int g = chk(c, __ldg(c.fo_item + p), c.I);
+    const int s = chk(c, __ldg(c.fo_pin + p), c.P);
+    const int z = chk(c, __ldg(c.drv_of + s), c.P);   // the net's driver: the item's output pin
+    const int cz = __ldg(c.pin_cell + z), csp = __ldg(c.pin_cell + s);
+    const float2 pz = pos(cz), ps = pos(csp);
+    const float dx = pz.x - ps.x, dy = pz.y - ps.y;
+    const float L = fabsf(dx) + fabsf(dy);
+    const float cp = 1e3f * __ldg(c.fo_cap + p);
+    float dJdL = 0.f;
+    for (int k = 0; k < K; ++k) {
+        const float fk = __ldg(c.rc_scale + k);
+        const float r = fk * c.r_per_um, cc = fk * c.c_per_um;
+        const float4 as = __ldg(c.adj + (size_t)s * K + k);
+        const float2 Ss = __ldg(reinterpret_cast<const float2 *>(c.slew + (size_t)s * K + k) + 1);   // late
+        const float Draw = r * L * (0.5f * cc * L + cp);
+        const float dDdL = r * (cc * L + cp);
+        const float Dbar = as.x + as.y;
+        const float Vbar = as.z / (2.f * Ss.x) + as.w / (2.f * Ss.y);
+        dJdL += Dbar * 1e-6f * dDdL + Vbar * 1e-12f * 2.f * Draw * dDdL + __ldg(c.aload + (size_t)g * K + k) * 1e-3f * cc;
+    }
+    // the sign products are exact in FP32 (a sign is -1, 0 or 1)
+    const double gx = (double)(dJdL * (float)((dx > 0.f) - (dx < 0.f)));
+    const double gy = (double)(dJdL * (float)((dy > 0.f) - (dy < 0.f)));
+    if (csp >= 0) {
+        const int cs = chk(c, csp, c.C);
+        atomicAdd(c.grad + 2 * (size_t)cs, -gx);
+        atomicAdd(c.grad + 2 * (size_t)cs + 1, -gy);
     }
     if (cz >= 0) {
-        atomicAdd(c.grad + 2 * (size_t)cz, gdx);
-        atomicAdd(c.grad + 2 * (size_t)cz + 1, gdy);
+        const int cd = chk(c, cz, c.C);
+        atomicAdd(c.grad + 2 * (size_t)cd, gx);
+        atomicAdd(c.grad + 2 * (size_t)cd + 1, gy);
     }
 }
 
@@ -839,7 +843,7 @@ void launch_adjoint(const DevCtx &c, const HostSched &h, cudaStream_t st)
         if (nl > 0)
             k_adj_steiner<kAdjBigColNodes, 64, 8><<<nblk2(nl, 8), 8, 0, st>>>(c, ns, c.st_n_items);
     } else if (c.I > 0) {
-        k_adj_star<<<nblk2(c.I, 128), 128, 0, st>>>(c);
+        if (c.F > 0) k_adj_star<<<nblk2(c.F, 256), 256, 0, st>>>(c);
     }
 }
 

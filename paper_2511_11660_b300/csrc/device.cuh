@@ -102,6 +102,7 @@ struct DevCtx {
     const float *lut_scale, *rc_scale;          // [K]
     const int32_t *item_pin0, *item_type, *item_cell;
     const int32_t *fo_ptr, *fo_pin, *fo_node;   // sinks of each item's output net
+    const int32_t *fo_item;                     // [F] item of each fan-out entry (differentiable star RC)
     const float *fo_cap;
     const int32_t *rc_ptr, *rc_parent;
     const float *rc_R, *rc_C;

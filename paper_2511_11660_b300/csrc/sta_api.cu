@@ -1481,6 +1481,12 @@ sta_status sta_backward(sta_ctx *c, double w_tns, double w_wns, double *J_out, d
             d.obj = dev_alloc<double>(c, 4 * (size_t)K + 1);
             d.grad = dev_alloc<double>(c, 2 * (size_t)c->plan.C);
             d.aload = dev_alloc<float>(c, (size_t)c->plan.I * K);
+            if (!c->plan.steiner) {   // the star segments' kernel runs one thread per fan-out entry
+                std::vector<int32_t> fo_item(c->plan.F);
+                for (int32_t g = 0; g < c->plan.I; ++g)
+                    for (int64_t p = c->plan.fo_ptr[g]; p < c->plan.fo_ptr[g + 1]; ++p) fo_item[p] = g;
+                d.fo_item = upload(c, fo_item);
+            }
             d.abox_len = 2 * (size_t)c->plan.P * K;
             d.abox = dev_alloc<float4>(c, d.abox_len);
             CK(cudaMemset(d.abox, 0xFF, std::max<size_t>(1, d.abox_len) * sizeof(float4)));
