@@ -431,16 +431,40 @@ __global__ void k_net_star(const DevCtx c)
         const float f = __ldg(c.rc_scale + k);
         const float r = f * c.r_per_um, cc = f * c.c_per_um;
         float ld = 0.f;
-        for (int q = f0; q < f1; ++q) {
-            const int s = chk(c, c.fo_pin[q], c.P);
-            const float2 ps = pin_pos(c, s);
-            const float L = fabsf(pz.x - ps.x) + fabsf(pz.y - ps.y);
-            const float cp = 1e3f * c.fo_cap[q];
-            const float Dr = r * L * fmaf(0.5f * cc, L, cp);
-            const float Dn = 1e-6f * Dr;
-            c.netD[(size_t)s * K + k] = Dn;
-            c.netV[(size_t)s * K + k] = Dn * Dn;
-            ld += fmaf(cc, L, cp);
+        // four sinks at a time, their (read-only) loads in flight together;
+        // the load is summed in net order as before
+        for (int q0 = f0; q0 < f1; q0 += 4) {
+            int s[4];
+            float L[4], cp[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                s[u] = q0 + u < f1 ? chk(c, __ldg(c.fo_pin + q0 + u), c.P) : -1;
+                cp[u] = q0 + u < f1 ? 1e3f * __ldg(c.fo_cap + q0 + u) : 0.f;
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                L[u] = 0.f;
+                if (s[u] < 0) continue;
+                const int pc = __ldg(c.pin_cell + s[u]);
+                float2 ps;
+                if (pc >= 0) {
+                    const int cl = chk(c, pc, c.C);
+                    ps = make_float2(__ldg(c.cell_xy + 2 * (size_t)cl), __ldg(c.cell_xy + 2 * (size_t)cl + 1));
+                } else {
+                    const int pq = -pc - 1;
+                    ps = make_float2(__ldg(c.port_xy + 2 * (size_t)pq), __ldg(c.port_xy + 2 * (size_t)pq + 1));
+                }
+                L[u] = fabsf(pz.x - ps.x) + fabsf(pz.y - ps.y);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                if (s[u] < 0) continue;
+                const float Dr = r * L[u] * fmaf(0.5f * cc, L[u], cp[u]);
+                const float Dn = 1e-6f * Dr;
+                c.netD[(size_t)s[u] * K + k] = Dn;
+                c.netV[(size_t)s[u] * K + k] = Dn * Dn;
+                ld += fmaf(cc, L[u], cp[u]);
+            }
         }
         c.load[(size_t)z * K + k] = 1e-3f * ld;
         if (c.Tg > 1) copy_to_tags(c, z, f0, f1, k);
