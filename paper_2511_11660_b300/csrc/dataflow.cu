@@ -101,11 +101,13 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
             else e = ep_prep(c, c.ep_order[chk(c, x - c.I, c.E)]);
         }
         long long spins = 0;
+        FwdIn in;
+        unsigned seen = 0;   // inputs found complete (values kept in `in`)
         while (__any_sync(0xffffffffu, pending)) {
-            FwdIn in;
             bool ok = false;
             if (pending)
-                ok = is_item ? fwd_probe<THRU, true>(c, f, par, q, in) : ep_probe(c, e, par, q, in.at[0], in.sl[0]);
+                ok = is_item ? fwd_probe<THRU, true>(c, f, par, q, in, &seen)
+                             : ep_probe(c, e, par, q, in.at[0], in.sl[0]);
             if (group_all_warp(c, ok) && pending) {   // the whole warp votes
                 if (is_item) fwd_run<SMOOTH, UNIFORM, true, THRU, true>(c, L.lut, f, in, x, q, par);
                 else ep_run<true>(c, e, in.at[0], in.sl[0], c.ep_order[chk(c, x - c.I, c.E)], q, par);

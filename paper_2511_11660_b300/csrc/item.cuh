@@ -358,11 +358,16 @@ __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, co
 // Are the drivers' arrivals and slews of the lane's corners complete?  Lane
 // q reads component q of its first corner (returned in `in`; with PAIR also
 // the other edge of its early/late half); the caller's group vote
-// (group_all_warp) over the quad covers the four components.
+// (group_all_warp) over the quad covers the four components.  With `seen`
+// (the caller keeps `in` across its polling rounds), an input found complete
+// is marked and not read again: a published value is final for the pass, so
+// later rounds read only the inputs still pending (one corner per lane group
+// and no -through sets, where the first corner's values are all there is).
 // THRU = false: the design has no -through sets (c.pin_adv is NULL); the
 // kernels compiled so carry none of their code and registers.
 template <bool THRU = true, bool PAIR = false>
-__device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int par, int q, FwdIn &in)
+__device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int par, int q, FwdIn &in,
+                                          unsigned *seen = nullptr)
 {
     const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
     bool ok = true;
@@ -370,6 +375,7 @@ __device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         if (j < f.nin) {
+            if (seen && ((*seen >> j) & 1u)) continue;   // complete in an earlier round: kept
             if (PAIR) {
                 // both edges of the lane's early/late half in one load each
                 DF a0, a1;
@@ -380,7 +386,9 @@ __device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int
                 in.atp[j] = (q & 1) ? a0 : a1;
                 in.sl[j] = (q & 1) ? s1 : s0;
                 in.slp[j] = (q & 1) ? s0 : s1;
-                ok = ok && real_df(a0) && real_df(a1) && s0 == s0 && s1 == s1;
+                const bool cj = real_df(a0) && real_df(a1) && s0 == s0 && s1 == s1;
+                if (seen && cj && c.K == c.KL && !pin_adv) *seen |= 1u << j;
+                ok = ok && cj;
             } else {
                 in.at[j] = ld_relaxed_df(fbox_a(c, par, f.drv[j], kq)->v + q);
                 in.sl[j] = ld_relaxed1(reinterpret_cast<const float *>(fbox_s(c, par, f.drv[j], kq)) + q);
