@@ -771,10 +771,16 @@ __global__ void __launch_bounds__(kDfThreadsA) k_df_adjoint(const DevCtx c)
         AdjItem it{};
         if (pending) it = adj_prep(c, ti, ti + c.T, x, q);
         long long spins = 0;
+        // the lane's share of the sinks summed (`part`), kept once every one
+        // of them was complete: a published adjoint is final for the sweep
+        float4 part = make_float4(0.f, 0.f, 0.f, 0.f);
+        bool lane_done = false;
         while (__any_sync(0xffffffffu, pending)) {
-            float4 part = make_float4(0.f, 0.f, 0.f, 0.f);
             bool ok = false;
-            if (pending) ok = adj_probe(c, it, par, q, part);
+            if (pending) {
+                ok = lane_done || adj_probe(c, it, par, q, part);
+                lane_done = ok;
+            }
             const bool go = group_all_warp(c, ok) && pending;   // the whole warp votes
             if (__any_sync(0xffffffffu, go)) {
                 // every lane sums (full-warp shuffles); the ready groups use it
