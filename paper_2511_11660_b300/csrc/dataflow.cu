@@ -97,8 +97,8 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
         FwdItem f{};
         EpItem e{};
         if (pending) {
-            if (is_item) f = fwd_prep(c, L.nin, L.kind, L.sense, x);
-            else e = ep_prep(c, c.ep_order[chk(c, x - c.I, c.E)]);
+            if (is_item) f = fwd_prep<true>(c, L.nin, L.kind, L.sense, x);
+            else e = ep_prep<true>(c, c.ep_order[chk(c, x - c.I, c.E)]);
         }
         long long spins = 0;
         FwdIn in;

@@ -101,6 +101,8 @@ struct DevCtx {
     const int32_t *type_nin, *type_kind, *arc_sense;
     const float *lut_scale, *rc_scale;          // [K]
     const int32_t *item_pin0, *item_type, *item_cell;
+    const int32_t *item_drv;                    // [I][3] the item driving each gate input (0 where none)
+    const int32_t *ep_drv;                      // [E] the item driving each endpoint
     const int32_t *fo_ptr, *fo_pin, *fo_node;   // sinks of each item's output net
     const int32_t *fo_item;                     // [F] item of each fan-out entry (differentiable star RC)
     const float *fo_cap;

@@ -239,21 +239,28 @@ __device__ __forceinline__ size_t box_index(const DevCtx &c, int par, int pin, i
 {
     return ((size_t)par * c.P + pin) * c.K + k;
 }
-__device__ __forceinline__ DF4 *fbox_a(const DevCtx &c, int par, int pin, int k) { return c.fbox_a + box_index(c, par, pin, k); }
-__device__ __forceinline__ float4 *fbox_s(const DevCtx &c, int par, int pin, int k)
+// forward mailbox records: [parity][driver item][state], dense over the
+// items (only item outputs are published), so the entries a level polls sit
+// close together
+__device__ __forceinline__ size_t fbox_index(const DevCtx &c, int par, int slot, int k)
 {
-    return c.fbox_s + box_index(c, par, pin, k);
+    return ((size_t)par * c.I + slot) * c.K + k;
+}
+__device__ __forceinline__ DF4 *fbox_a(const DevCtx &c, int par, int slot, int k) { return c.fbox_a + fbox_index(c, par, slot, k); }
+__device__ __forceinline__ float4 *fbox_s(const DevCtx &c, int par, int slot, int k)
+{
+    return c.fbox_s + fbox_index(c, par, slot, k);
 }
 __device__ __forceinline__ DF4 *rbox_at(const DevCtx &c, int par, int pin, int k) { return c.rbox + box_index(c, par, pin, k); }
 
-// Lane q publishes component q of pin's arrival and slew for parity par and
-// clears the same component of parity par ^ 1.
-__device__ __forceinline__ void publish_fwd(const DevCtx &c, int par, int pin, int k, int q, DF at, float sl)
+// Lane q publishes component q of item g's output arrival and slew for
+// parity par and clears the same component of parity par ^ 1.
+__device__ __forceinline__ void publish_fwd(const DevCtx &c, int par, int g, int k, int q, DF at, float sl)
 {
-    st_relaxed_df(fbox_a(c, par, pin, k)->v + q, at);
-    st_relaxed(reinterpret_cast<float *>(fbox_s(c, par, pin, k)) + q, sl);
-    fbox_a(c, par ^ 1, pin, k)->v[q] = nan_df();
-    reinterpret_cast<float *>(fbox_s(c, par ^ 1, pin, k))[q] = nan_f();
+    st_relaxed_df(fbox_a(c, par, g, k)->v + q, at);
+    st_relaxed(reinterpret_cast<float *>(fbox_s(c, par, g, k)) + q, sl);
+    fbox_a(c, par ^ 1, g, k)->v[q] = nan_df();
+    reinterpret_cast<float *>(fbox_s(c, par ^ 1, g, k))[q] = nan_f();
 }
 __device__ __forceinline__ void publish_rat(const DevCtx &c, int par, int pin, int k, int q, DF r)
 {
@@ -316,7 +323,8 @@ __device__ __forceinline__ bool group_all_warp(const DevCtx &c, bool ok)
 struct FwdItem {
     int t, pin0, nin, kind;
     int tag;                    // exception tag of a startpoint item (PI, flip-flop)
-    int sense[3], drv[3];
+    int sense[3];
+    int drv[3];                 // each input's driver: its item (BYITEM: the mailbox index) or its pin
     float Dn0[3], V0[3], ld0;   // net values of the lane's first corner, loaded ahead
 };
 
@@ -330,6 +338,9 @@ struct FwdIn {
     float slp[3];
 };
 
+// BYITEM (the schedules that read the drivers from the mailboxes): drv
+// holds the driver items; otherwise the driver pins (their pin states).
+template <bool BYITEM = false>
 __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, const int *tkind, const int *tsense,
                                             int g)
 {
@@ -346,7 +357,7 @@ __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, co
         const bool on = j < f.nin;
         f.sense[j] = on ? tsense[f.t * 3 + j] : -1;
         const int a = on ? chk(c, f.pin0 + j, c.P) : 0;
-        f.drv[j] = on ? chk(c, c.drv_of[a], c.P) : 0;
+        f.drv[j] = on ? (BYITEM ? chk(c, c.item_drv[(size_t)g * 3 + j], c.I) : chk(c, c.drv_of[a], c.P)) : 0;
         f.Dn0[j] = on ? c.netD[(size_t)a * K + kq] : 0.f;
         f.V0[j] = on ? c.netV[(size_t)a * K + kq] : 0.f;
     }
@@ -431,7 +442,7 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
             const DF a((c.Tg == 1 || k % c.Tg == f.tag) ? c.pi_at : absent);
             st_comp_df(c.at + (size_t)pin0 * K + k, q, a);
             st_comp(c.slew + (size_t)pin0 * K + k, q, c.pi_slew);
-            if (pub) publish_fwd(c, par, pin0, k, q, a, c.pi_slew);
+            if (pub) publish_fwd(c, par, g, k, q, a, c.pi_slew);
             if (first && k == kq) *first = FwdOut{a, c.pi_slew};
         }
         return;
@@ -451,7 +462,7 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
             const float sl = sc * lookup<UNIFORM>(lut, tb + (2 + rfo) * kLutStride, as, bl, cs, ld);
             st_comp_df(c.at + (size_t)qp * K + k, q, a);
             st_comp(c.slew + (size_t)qp * K + k, q, sl);
-            if (pub) publish_fwd(c, par, qp, k, q, a, sl);
+            if (pub) publish_fwd(c, par, g, k, q, a, sl);
             if (first && k == kq) *first = FwdOut{a, sl};
         }
         return;
@@ -578,7 +589,7 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
         const float os = sgn * ms.get(c.gamma);
         st_comp_df(c.at + (size_t)z * K + k, q, oa);
         st_comp(c.slew + (size_t)z * K + k, q, os);
-        if (pub) publish_fwd(c, par, z, k, q, oa, os);
+        if (pub) publish_fwd(c, par, g, k, q, oa, os);
         if (first && k == kq) *first = FwdOut{oa, os};
     }
 }
@@ -586,17 +597,18 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
 // ------------------------------------------------------------ endpoints
 
 struct EpItem {
-    int p, d;
+    int p, d;   // the endpoint pin; its driver's item (BYITEM) or pin
     bool isD;
     float Dn0, V0;
 };
 
+template <bool BYITEM = false>
 __device__ __forceinline__ EpItem ep_prep(const DevCtx &c, int e)
 {
     EpItem x;
     e = chk(c, e, c.E);
     x.p = chk(c, c.ep_pin[e], c.P);
-    x.d = chk(c, c.drv_of[x.p], c.P);
+    x.d = BYITEM ? chk(c, c.ep_drv[e], c.I) : chk(c, c.drv_of[x.p], c.P);
     x.isD = c.ep_is_d[e] != 0;
     x.Dn0 = c.netD[(size_t)x.p * c.K + corner_lane(c)];
     x.V0 = c.netV[(size_t)x.p * c.K + corner_lane(c)];

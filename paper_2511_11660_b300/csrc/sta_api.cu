@@ -370,7 +370,7 @@ sta_status create_from_plan(sta_ctx *c, int device)
     }
     h.T = pl.T;
     // dataflow schedule: parity mailboxes (all NaN), epoch state, work chunks
-    d.fbox_len = 2 * (size_t)pl.P * pl.K;
+    d.fbox_len = 2 * (size_t)pl.I * pl.K;   // forward mailboxes: one record per item output
     d.rbox_len = 2 * (size_t)pl.P * pl.K;
     d.fbox_a = dev_alloc<sta::DF4>(c, d.fbox_len);
     d.fbox_s = dev_alloc<float4>(c, d.fbox_len);
@@ -400,6 +400,23 @@ sta_status create_from_plan(sta_ctx *c, int device)
         for (int32_t g = 0; g < pl.I; ++g) {
             const int32_t t = pl.item_type[g], p0 = pl.item_pin0[g];
             out_item[t < 0 ? p0 : (pl.type_kind[t] == 1 ? p0 + 1 : p0 + pl.type_nin[t])] = g;
+        }
+        {   // the mailbox index (driver item) of every gate input and endpoint
+            std::vector<int32_t> idrv((size_t)pl.I * 3, 0), edrv(pl.E, 0);
+            for (int32_t g = 0; g < pl.I; ++g) {
+                const int32_t t = pl.item_type[g];
+                if (t < 0 || pl.type_kind[t] != 0) continue;
+                for (int32_t j = 0; j < pl.type_nin[t] && j < 3; ++j) {
+                    const int32_t dp = pl.drv_of[pl.item_pin0[g] + j];
+                    idrv[(size_t)g * 3 + j] = dp >= 0 && out_item[dp] >= 0 ? out_item[dp] : 0;
+                }
+            }
+            for (int32_t e = 0; e < pl.E; ++e) {
+                const int32_t dp = pl.drv_of[pl.ep_pin[e]];
+                edrv[e] = dp >= 0 && out_item[dp] >= 0 ? out_item[dp] : 0;
+            }
+            d.item_drv = upload(c, idrv);
+            d.ep_drv = upload(c, edrv);
         }
         std::vector<int32_t> ep_level(pl.E), ep_order(pl.E);
         for (int32_t e = 0; e < pl.E; ++e) {

@@ -210,10 +210,10 @@ void build_tile_plan(const Plan &pl, int32_t B, int32_t W, int32_t R, TilePlan &
         dsc[2] = pl.item_type[g];
         for (int32_t j = 0; j < 3; ++j) {
             const int32_t a = pl.item_pin0[g] + j;
-            const int32_t d = j < nin ? pl.drv_of[a] : 0;
-            dsc[3 + j] = d;
+            const int32_t h0 = j < nin ? drv_item(a) : -1;
+            dsc[3 + j] = h0 >= 0 ? h0 : 0;   // the driver's item: its mailbox index
             if (j < nin) {
-                const int32_t h = drv_item(a);
+                const int32_t h = h0;
                 ring[j] = fwd_code(h, b, s);
                 ++tp.fwd_edges;
                 tp.fwd_local += ring[j] >= 0;
@@ -231,7 +231,7 @@ void build_tile_plan(const Plan &pl, int32_t B, int32_t W, int32_t R, TilePlan &
         const int32_t p = pl.ep_pin[e];
         dsc[0] = I + e;
         dsc[1] = p;
-        dsc[2] = pl.drv_of[p];
+        dsc[2] = ep_drv[e] >= 0 ? ep_drv[e] : 0;   // the driver's item
         dsc[3] = pl.ep_is_d[e];
         dsc[4] = e;
         const int32_t ring = fwd_code(ep_drv[e], ep_tile[e], ep_at[e]);
@@ -299,6 +299,11 @@ std::string check_tile_plan(const Plan &pl, const TilePlan &tp)
         out_item[out_pin_of(pl, g)] = g;
         for (int32_t j = 0; j < nin_of(pl, g); ++j) item_of_in[pl.item_pin0[g] + j] = g;
     }
+    // the mailbox index a descriptor holds for a driven pin: the driver's item
+    auto drv_mbox = [&](int32_t pin) {
+        const int32_t d = pl.drv_of[pin];
+        return d >= 0 && out_item[d] >= 0 ? out_item[d] : 0;
+    };
     std::vector<char> seen((size_t)I + E, 0);
     for (int32_t b = 0; b < B; ++b)
         for (int32_t s = 0; s < NS; ++s) {
@@ -344,18 +349,18 @@ std::string check_tile_plan(const Plan &pl, const TilePlan &tp)
                     codes[2] = (int16_t)(d[7] & 0xffff);
                     for (int32_t j = 0; j < n; ++j) {
                         drv[j] = d[3 + j];
-                        if (drv[j] != pl.drv_of[pl.item_pin0[id] + j]) return "descriptor driver";
+                        if (drv[j] != drv_mbox(pl.item_pin0[id] + j)) return "descriptor driver";
                     }
                 } else {
                     n = 1;
                     codes[0] = (int16_t)(d[6] & 0xffff);
                     drv[0] = d[2];
-                    if (drv[0] != pl.drv_of[pl.ep_pin[id - I]]) return "endpoint driver";
+                    if (drv[0] != drv_mbox(pl.ep_pin[id - I])) return "endpoint driver";
                 }
                 for (int32_t j = 0; j < n; ++j) {
                     if (codes[j] < 0) continue;
                     if (codes[j] >= R) return "ring code out of range";
-                    const int32_t h = out_item[drv[j]];
+                    const int32_t h = drv[j];
                     if (ring[codes[j]] != h || after[codes[j]] != h) return "forward ring read of a stale slot";
                 }
             }

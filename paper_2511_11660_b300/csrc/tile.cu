@@ -146,7 +146,7 @@ __device__ __forceinline__ void tile_fwd_load(const DevCtx &c, const SmemLib &L,
             const bool on = j < f.nin;
             f.sense[j] = on ? L.sense[f.t * 3 + j] : -1;
             const int a = on ? chk(c, f.pin0 + j, c.P) : 0;
-            f.drv[j] = on ? chk(c, drv[j], c.P) : 0;
+            f.drv[j] = on ? chk(c, drv[j], c.I) : 0;   // the driver's item (mailbox index)
             f.Dn0[j] = on ? c.netD[(size_t)a * K + kq] : 0.f;
             f.V0[j] = on ? c.netV[(size_t)a * K + kq] : 0.f;
             u.in.at[j] = nan_df();
@@ -161,7 +161,7 @@ __device__ __forceinline__ void tile_fwd_load(const DevCtx &c, const SmemLib &L,
     } else {
         f.t = chk(c, d1.x, c.E);
         f.pin0 = chk(c, d0.y, c.P);
-        f.drv[0] = chk(c, d0.z, c.P);
+        f.drv[0] = chk(c, d0.z, c.I);   // the driver's item (mailbox index)
         f.tag = d0.w != 0;
         f.nin = 1;
         f.Dn0[0] = c.netD[(size_t)f.pin0 * K + kq];
