@@ -168,7 +168,7 @@ __global__ void k_adj_seed(const DevCtx c)
 
 __device__ __forceinline__ float4 *abox_at(const DevCtx &c, int par, int pin, int k)
 {
-    return c.abox + ((size_t)par * c.P + pin) * c.K + k;
+    return c.abox + ((((size_t)pin * c.K + k) << 1) | (size_t)par);   // [pin][state][parity], as rbox
 }
 
 struct AdjItem {

@@ -21,8 +21,8 @@
 // complete (see below and dataflow.cu) and the item publishes its own
 // results there; WAIT = false relies on launch boundaries (level schedule).
 //
-// Mailboxes.  For epoch parity p, fbox_a[p] / fbox_s[p] hold each driver
-// pin's arrival (double-float) and slew (FP32) and rbox[p] each gate input
+// Mailboxes.  For epoch parity p, fbox_a[p] / fbox_s[p] hold each item's
+// output arrival (double-float) and slew (FP32) and rbox each gate input
 // pin's required time (double-float).  Every float is NaN until its producer
 // stores the final value with a relaxed store, and a real result is never
 // NaN, so a reader that sees all the floats it needs non-NaN has the final
@@ -234,10 +234,14 @@ __device__ __forceinline__ bool complete_df(const DF4 *p)
 __device__ __forceinline__ float nan_f() { return __int_as_float(0x7fffffff); }
 __device__ __forceinline__ DF nan_df() { return DF(nan_f(), nan_f()); }
 
-// mailbox records: [parity][pin][state]
+// required-time mailbox records: [pin][state][parity] -- a record's two
+// parities side by side, so the reset of parity p ^ 1 falls in the line of
+// the store to p (the forward records below stay [parity][item][state]: an
+// item's readers are its neighbours' readers too, and interleaving would
+// spread them over twice the lines)
 __device__ __forceinline__ size_t box_index(const DevCtx &c, int par, int pin, int k)
 {
-    return ((size_t)par * c.P + pin) * c.K + k;
+    return (((size_t)pin * c.K + k) << 1) | (size_t)par;
 }
 // forward mailbox records: [parity][driver item][state], dense over the
 // items (only item outputs are published), so the entries a level polls sit
