@@ -103,6 +103,7 @@ struct DevCtx {
     const int32_t *item_pin0, *item_type, *item_cell;
     const int32_t *item_drv;                    // [I][3] the item driving each gate input (0 where none)
     const int32_t *ep_drv;                      // [E] the item driving each endpoint
+    const int32_t *pin_fo;                      // [P] a gate input's entry in its driver's fan-out list (-1: none)
     const int32_t *fo_ptr, *fo_pin, *fo_node;   // sinks of each item's output net
     const int32_t *fo_item;                     // [F] item of each fan-out entry (differentiable star RC)
     const float *fo_cap;
@@ -145,7 +146,7 @@ struct DevCtx {
     // dataflow schedule: mailboxes by epoch parity, NaN until published
     DF4 *fbox_a;                                // [2][P][K] arrival of driver pins
     float4 *fbox_s;                             // [2][P][K] slew of driver pins
-    DF4 *rbox;                                  // [2][P][K] required time of gate input pins
+    DF4 *rbox;                                  // [F][K][2] required time of gate input pins, by fan-out entry
     size_t fbox_len, rbox_len;                  // records of fbox_a (= of fbox_s) and of rbox
     unsigned *df_state;                         // [kDfStateWords] [0] epoch, [1] forward chunk counter,
                                                 // [2] backward counter, [3] abort; adjoint: [4] epoch,
@@ -168,7 +169,7 @@ struct DevCtx {
     const int16_t *tl_fo_ring;                  // [F] backward ring code of a fan-out entry, -1 = mailbox
     // differentiable pass (sta_backward)
     float4 *adj;                                // [P][K] late adjoints: dJ/dAT rise, fall, dJ/dslew rise, fall
-    float4 *abox;                               // [2][P][K] the same for gate input pins, parity mailbox
+    float4 *abox;                               // [P][K][2] the same for gate input pins, parity mailbox
     size_t abox_len;
     double *obj;                                // [K][4] max(-s/g), sum exp(-s/g - max), TNS_g, WNS_g; [4K] J
     float *aload;                               // [I][K] dJ/dload of each item's output net

@@ -255,7 +255,9 @@ __device__ __forceinline__ float4 *fbox_s(const DevCtx &c, int par, int slot, in
 {
     return c.fbox_s + fbox_index(c, par, slot, k);
 }
-__device__ __forceinline__ DF4 *rbox_at(const DevCtx &c, int par, int pin, int k) { return c.rbox + box_index(c, par, pin, k); }
+// a gate input's required-time record, by its entry fe in its driver's
+// fan-out list (c.pin_fo): a driver reads its sinks' records contiguously
+__device__ __forceinline__ DF4 *rbox_at(const DevCtx &c, int par, int fe, int k) { return c.rbox + box_index(c, par, fe, k); }
 
 // Lane q publishes component q of item g's output arrival and slew for
 // parity par and clears the same component of parity par ^ 1.
@@ -266,10 +268,10 @@ __device__ __forceinline__ void publish_fwd(const DevCtx &c, int par, int g, int
     fbox_a(c, par ^ 1, g, k)->v[q] = nan_df();
     reinterpret_cast<float *>(fbox_s(c, par ^ 1, g, k))[q] = nan_f();
 }
-__device__ __forceinline__ void publish_rat(const DevCtx &c, int par, int pin, int k, int q, DF r)
+__device__ __forceinline__ void publish_rat(const DevCtx &c, int par, int fe, int k, int q, DF r)
 {
-    st_relaxed_df(rbox_at(c, par, pin, k)->v + q, r);
-    rbox_at(c, par ^ 1, pin, k)->v[q] = nan_df();
+    st_relaxed_df(rbox_at(c, par, fe, k)->v + q, r);
+    rbox_at(c, par ^ 1, fe, k)->v[q] = nan_df();
 }
 
 // Reads of pin states (arrival, slew, required time) that another item
@@ -699,6 +701,9 @@ struct BwdItem {
     // sink pins of the fan-out entries q, q + 4, q + 8, q + 12 (-1: none),
     // the ones the lane's probe reads first
     int sk[4];
+    // each gate input's entry in its driver's fan-out list: where its
+    // required time is published
+    int fin[3];
 };
 
 __device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, const int *tkind, int g, int q)
@@ -720,6 +725,9 @@ __device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, co
     }
     b.ld0 = b.t >= 0 ? c.load[(size_t)b.z * K + kq] : 0.f;
     b.az0 = ld_state_df(c.at + (size_t)b.z * K + kq, q);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        b.fin[j] = (b.kind == 0 && j < b.nin) ? chk(c, c.pin_fo[b.pin0 + j], (long long)c.F) : 0;
     const int nread = b.kind == 1 ? 1 : b.kind == 0 ? b.nin : 0;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -729,66 +737,6 @@ __device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, co
         b.a0[j] = on ? ld_state_df(c.at + o, q) : DF(0.f);
     }
     return b;
-}
-
-// Are the required times of every sink of the item's net complete (all the
-// lane's corners)?  Lane q reads component q only: the caller's group vote
-// (group_all_warp) over the quad covers the four.  Sinks are read four at a time, their
-// loads in flight together.  For the lane's first corner the same pass
-// folds them: R = min (late) / max (early) over the sinks of RAT - Elmore
-// delay, component q -- the output's required time, ready for bwd_run.
-// Endpoint sinks were set by the forward pass.
-template <bool THRU = true>
-__device__ __forceinline__ bool bwd_probe(const DevCtx &c, const BwdItem &b, int par, int q, DF &R)
-{
-    const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
-    const int K = c.K, kq = corner_lane(c);
-    const bool late = q >= 2;
-    bool ok = true;
-    // the fold in FP32 on the high parts; the winner's difference exactly
-    float rf = late ? INFINITY : -INFINITY;
-    DF rw(rf);
-    float rd = 0.f;
-    for (int p0 = b.f0; p0 < b.f1; p0 += 4) {
-        int s[4];
-        DF m[4];
-        float nd[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) s[u] = p0 + u < b.f1 ? chk(c, __ldg(c.fo_pin + p0 + u), c.P) : -1;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (s[u] < 0) continue;
-            // -through: a path in tag t continues in t + 1 beyond a sink that advances t
-            const int ks = (pin_adv && ((pin_adv[s[u]] >> (kq % c.Tg)) & 1u)) ? kq + 1 : kq;
-            m[u] = s[u] < c.ep_begin ? ld_relaxed_df(rbox_at(c, par, s[u], ks)->v + q)
-                                     : ld_state_df(c.rat + (size_t)s[u] * K + ks, q);
-            nd[u] = __ldg(c.netD + (size_t)s[u] * K + kq);
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-            if (s[u] >= 0) ok = ok && real_df(m[u]);
-        if (!ok) return false;   // no arithmetic while waiting
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            if (s[u] < 0) continue;
-            const float v = m[u].hi - nd[u];
-            if (late ? v < rf : v > rf) {
-                rf = v;
-                rw = m[u];
-                rd = nd[u];
-            }
-        }
-    }
-    for (int p = b.f0; p < b.f1 && ok; ++p) {
-        const int s = chk(c, __ldg(c.fo_pin + p), c.P);
-        if (s < c.ep_begin) {
-            const int k0 = pin_adv ? 0 : kq + c.KL, dk = pin_adv ? 1 : c.KL;
-            for (int k = k0; k < K && ok; k += dk)
-                if (k != kq) ok = complete_df(rbox_at(c, par, s, k));
-        }
-    }
-    R = isfinite(rf) ? rw - rd : DF(rf);
-    return ok;
 }
 
 // The backward fold split over the quad instead of over components: lane q
@@ -852,11 +800,14 @@ __device__ __forceinline__ DF quad_fold(Fold4 &f, int q, unsigned m = quad_mask(
     return isfinite(rf) ? rw - rd : DF(rf);
 }
 
-// bwd_probe with the fold split over the quad (Fold4): lane q reads all
+// Are the required times of every sink of the item's net complete (all the
+// lane's corners)?  The fold split over the quad (Fold4): lane q reads all
 // four components of fan-out entries q, q + 4, ... (four at a time, their
-// loads in flight together) for the lane's first corner.  The caller's
-// group vote covers the quad, then quad_fold gives each lane its component's
-// required time -- the same value as bwd_probe's.
+// loads in flight together) for the lane's first corner.  The caller's group
+// vote covers the quad, then quad_fold gives each lane its component's
+// required time: R = min (late) / max (early) over the sinks of RAT - Elmore
+// delay, the first extreme in fan-out order, its difference formed exactly.
+// Endpoint sinks were set by the forward pass.
 template <bool THRU = true>
 __device__ __forceinline__ bool bwd_probe_split(const DevCtx &c, const BwdItem &b, int par, int q, Fold4 &f)
 {
@@ -877,7 +828,7 @@ __device__ __forceinline__ bool bwd_probe_split(const DevCtx &c, const BwdItem &
             if (s[u] < 0) continue;
             const int ks = (pin_adv && ((pin_adv[s[u]] >> (kq % c.Tg)) & 1u)) ? kq + 1 : kq;
             if (s[u] < c.ep_begin) {
-                ld_relaxed_df4(rbox_at(c, par, s[u], ks), m[u][0], m[u][1], m[u][2], m[u][3]);
+                ld_relaxed_df4(rbox_at(c, par, b.f0 + e, ks), m[u][0], m[u][1], m[u][2], m[u][3]);
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) m[u][j] = ld_state_df(c.rat + (size_t)s[u] * K + ks, j);
@@ -911,7 +862,7 @@ __device__ __forceinline__ bool bwd_probe_split(const DevCtx &c, const BwdItem &
             if (s >= c.ep_begin) continue;
             const int k0 = pin_adv ? 0 : kq + c.KL, dk = pin_adv ? 1 : c.KL;
             for (int k = k0; k < K; k += dk)
-                if (k != kq && !complete_df(rbox_at(c, par, s, k))) return false;
+                if (k != kq && !complete_df(rbox_at(c, par, b.f0 + e, k))) return false;
         }
     }
     return true;
@@ -919,7 +870,7 @@ __device__ __forceinline__ bool bwd_probe_split(const DevCtx &c, const BwdItem &
 
 // Lane q = el*2 + rfi: the output's required time (component q) over its
 // net sinks, then each input pin's over its arcs, and pin slacks.  With WAIT
-// the first corner's output required time comes folded from bwd_probe (Rpre).
+// the first corner's output required time comes folded from the probe (Rpre).
 // With `first` (the tile schedule's ring), the lane's first-corner required
 // time of each input pin, component q, is returned there as well.
 template <bool UNIFORM, bool WAIT, bool THRU = true, class L>
@@ -944,7 +895,7 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
             for (int p = b.f0; p < b.f1; ++p) {
                 const int s = chk(c, c.fo_pin[p], c.P);
                 const int ks = (pin_adv && ((pin_adv[s] >> (k % c.Tg)) & 1u)) ? k + 1 : k;
-                const DF rs = (WAIT && s < c.ep_begin) ? ld_relaxed_df(rbox_at(c, par, s, ks)->v + q)
+                const DF rs = (WAIT && s < c.ep_begin) ? ld_relaxed_df(rbox_at(c, par, p, ks)->v + q)
                                                        : ld_state_df(c.rat + (size_t)s * K + ks, q);
                 const float nd = c.netD[(size_t)s * K + k];
                 const float v = rs.hi - nd;
@@ -1012,7 +963,7 @@ __device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int
             st_comp_df(c.rat + (size_t)a * K + k, q, acc);
             const DF Aa = first_k ? b.a0[j] : ld_state_df(c.at + (size_t)a * K + k, q);
             st_comp(c.slack + (size_t)a * K + k, q, el ? acc - Aa : Aa - acc);
-            if (WAIT) publish_rat(c, par, a, k, q, acc);
+            if (WAIT) publish_rat(c, par, b.fin[j], k, q, acc);
             if (first && first_k) first[j] = acc;
         }
     }

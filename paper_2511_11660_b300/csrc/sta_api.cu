@@ -371,7 +371,7 @@ sta_status create_from_plan(sta_ctx *c, int device)
     h.T = pl.T;
     // dataflow schedule: parity mailboxes (all NaN), epoch state, work chunks
     d.fbox_len = 2 * (size_t)pl.I * pl.K;   // forward mailboxes: one record per item output
-    d.rbox_len = 2 * (size_t)pl.P * pl.K;
+    d.rbox_len = 2 * (size_t)std::max<int64_t>(pl.F, 1) * pl.K;   // one record per fan-out entry
     d.fbox_a = dev_alloc<sta::DF4>(c, d.fbox_len);
     d.fbox_s = dev_alloc<float4>(c, d.fbox_len);
     d.rbox = dev_alloc<sta::DF4>(c, d.rbox_len);
@@ -417,6 +417,18 @@ sta_status create_from_plan(sta_ctx *c, int device)
             }
             d.item_drv = upload(c, idrv);
             d.ep_drv = upload(c, edrv);
+            // the required-time mailbox of a gate input is its entry in its
+            // driver's fan-out list: a driver's sinks are then contiguous
+            std::vector<int32_t> pfo(pl.P, -1);
+            for (int64_t q = 0; q < pl.F; ++q)
+                if (pl.fo_pin[q] < pl.P - pl.E) pfo[pl.fo_pin[q]] = (int32_t)q;
+            for (int32_t g = 0; g < pl.I; ++g) {   // every gate input is driven (the plan requires it)
+                const int32_t t = pl.item_type[g];
+                if (t < 0 || pl.type_kind[t] != 0) continue;
+                for (int32_t j = 0; j < pl.type_nin[t]; ++j)
+                    if (pfo[pl.item_pin0[g] + j] < 0) return fail(c, STA_EINVAL, "internal: an undriven gate input");
+            }
+            d.pin_fo = upload(c, pfo);
         }
         std::vector<int32_t> ep_level(pl.E), ep_order(pl.E);
         for (int32_t e = 0; e < pl.E; ++e) {

@@ -307,7 +307,7 @@ __global__ void __launch_bounds__(kTileThreads, 1) k_tile_forward(const DevCtx c
 // ------------------------------------------------------------- backward
 //
 // The output's required time is a fold over the net's sinks (item.cuh,
-// bwd_probe: min (late) / max (early) of RAT - Elmore delay, the first
+// bwd_probe_split: min (late) / max (early) of RAT - Elmore delay, the first
 // extreme in fan-out order wins, and the winner's difference is formed
 // exactly).  Here the quad splits the sinks instead of the components:
 // lane q folds fan-out entries q, q + 4, q + 8, ... for all four components
@@ -336,10 +336,10 @@ __device__ __forceinline__ void tile_bwd_desc(const DevCtx &c, int x, int4 (&d)[
 
 __device__ __forceinline__ int i4(const int4 &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; }
 
-// all four components of a sink's required time at state ks: the ring
-// (first corner, code >= 0), else the mailbox (gate input) or the endpoint's
-// required time
-__device__ __forceinline__ void sink_rat4(const DevCtx &c, int s, int code, int ks, int par, const DF *ring_r,
+// all four components of the required time of sink s (fan-out entry fe) at
+// state ks: the ring (first corner, code >= 0), else the mailbox (gate
+// input) or the endpoint's required time
+__device__ __forceinline__ void sink_rat4(const DevCtx &c, int fe, int s, int code, int ks, int par, const DF *ring_r,
                                           DF (&m)[4])
 {
     const int kq = corner_lane(c);
@@ -348,7 +348,7 @@ __device__ __forceinline__ void sink_rat4(const DevCtx &c, int s, int code, int 
 #pragma unroll
         for (int j = 0; j < 4; ++j) m[j] = r[j];
     } else if (s < c.ep_begin) {
-        ld_relaxed_df4(rbox_at(c, par, s, ks), m[0], m[1], m[2], m[3]);
+        ld_relaxed_df4(rbox_at(c, par, fe, ks), m[0], m[1], m[2], m[3]);
     } else {
 #pragma unroll
         for (int j = 0; j < 4; ++j) m[j] = ld_state_df(c.rat + (size_t)s * c.K + ks, j);
@@ -370,6 +370,9 @@ __device__ __forceinline__ void tile_bwd_load(const DevCtx &c, const SmemLib &L,
     b.f1 = chk(c, d[0].w, (long long)c.F + 1);
     b.ld0 = b.t >= 0 ? c.load[(size_t)b.z * K + kq] : 0.f;
     b.az0 = ld_state_df(c.at + (size_t)b.z * K + kq, q);
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+        b.fin[j] = (b.kind == 0 && j < b.nin) ? chk(c, c.pin_fo[b.pin0 + j], (long long)c.F) : 0;
     const int nread = b.kind == 1 ? 1 : b.kind == 0 ? b.nin : 0;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -392,7 +395,7 @@ __device__ __forceinline__ void tile_bwd_load(const DevCtx &c, const SmemLib &L,
         if (u.sk[v] >= 0) {
             u.nd[v] = __ldg(c.netD + (size_t)u.sk[v] * K + kq);
             // -through sinks pick their state at use; ring sinks are read after the barrier
-            if (!THRU && u.cd[v] < 0) sink_rat4(c, u.sk[v], -1, kq, par, nullptr, u.m[v]);
+            if (!THRU && u.cd[v] < 0) sink_rat4(c, b.f0 + e, u.sk[v], -1, kq, par, nullptr, u.m[v]);
         }
     }
 }
@@ -423,7 +426,7 @@ __device__ __forceinline__ bool tile_bwd_probe(const DevCtx &c, TileBwd &u, int 
         if (u.sk[v] < 0) continue;
         const int ks = state_of(u.sk[v]);
         const bool have = real_df(u.m[v][0]) && real_df(u.m[v][1]) && real_df(u.m[v][2]) && real_df(u.m[v][3]);
-        if (!have || (u.cd[v] >= 0 && ks == kq)) sink_rat4(c, u.sk[v], u.cd[v], ks, par, ring_r, u.m[v]);
+        if (!have || (u.cd[v] >= 0 && ks == kq)) sink_rat4(c, b.f0 + q + 4 * v, u.sk[v], u.cd[v], ks, par, ring_r, u.m[v]);
         const bool rdy = real_df(u.m[v][0]) && real_df(u.m[v][1]) && real_df(u.m[v][2]) && real_df(u.m[v][3]);
         ok = ok && rdy;
     }
@@ -438,7 +441,7 @@ __device__ __forceinline__ bool tile_bwd_probe(const DevCtx &c, TileBwd &u, int 
         int code = (int)__ldg(c.tl_fo_ring + p);
         if (code >= 0) code = chk(c, code, 4 * c.tl_R);
         DF m[4];
-        sink_rat4(c, s, code, state_of(s), par, ring_r, m);
+        sink_rat4(c, p, s, code, state_of(s), par, ring_r, m);
         if (!(real_df(m[0]) && real_df(m[1]) && real_df(m[2]) && real_df(m[3]))) return false;
         fold(e, m, __ldg(c.netD + (size_t)s * K + kq));
     }
@@ -450,7 +453,7 @@ __device__ __forceinline__ bool tile_bwd_probe(const DevCtx &c, TileBwd &u, int 
             if (s < c.ep_begin && __ldg(c.tl_fo_ring + p) < 0) {
                 const int k0 = pin_adv ? 0 : kq + c.KL, dk = pin_adv ? 1 : c.KL;
                 for (int k = k0; k < K && ok; k += dk)
-                    if (k != kq) ok = complete_df(rbox_at(c, par, s, k));
+                    if (k != kq) ok = complete_df(rbox_at(c, par, p, k));
             }
         }
     }
