@@ -44,6 +44,18 @@ __device__ __forceinline__ float ep_smooth_slack(const DevCtx &c, int e, int k, 
 }
 
 // softplus(z) = max(z, 0) + log1p(exp(-|z|))
+// x / y by the hardware's approximate division (div.approx: within 2 ulp for
+// |y| below 2^126; the divisors here are slews in ns and softmax sums >= 1).
+// An IEEE division costs many times more on a path that every level waits
+// on.  The quotient is an asm result, so the compiler cannot fuse it into a
+// later add: every schedule rounds it alike.
+__device__ __forceinline__ float div_hw(float x, float y)
+{
+    float r;
+    asm("div.approx.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(x), "f"(y));
+    return r;
+}
+
 __device__ __forceinline__ float softplus_f(float z) { return fmaxf(z, 0.f) + log1pf(expf(-fabsf(z))); }
 
 template <int NT>
@@ -218,7 +230,7 @@ __device__ __forceinline__ AdjItem adj_prep(const DevCtx &c, const int *tnin, co
 __device__ __forceinline__ float4 adj_sink_terms(const DevCtx &c, int s, int k, float4 as, float szr, float szf)
 {
     const float ssr = ld_state(c.slew + (size_t)s * c.K + k, 2), ssf = ld_state(c.slew + (size_t)s * c.K + k, 3);
-    return make_float4(as.x, as.y, as.z * szr / ssr, as.w * szf / ssf);
+    return make_float4(as.x, as.y, div_hw(as.z * szr, ssr), div_hw(as.w * szf, ssf));
 }
 
 // Are the adjoints of every gate-input sink of the item's net complete (all
@@ -409,13 +421,17 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
                 float m = -INFINITY;
 #pragma unroll
                 for (int i = 0; i < 6; ++i) m = fmaxf(m, x[i]);
-                float zsum = 0.f;
+                float zsum = 0.f, ex[6];
 #pragma unroll
-                for (int i = 0; i < 6; ++i) zsum += x[i] > -INFINITY ? expf((float)(x[i] - m) * ig) : 0.f;
+                for (int i = 0; i < 6; ++i) {
+                    ex[i] = x[i] > -INFINITY ? expf((float)(x[i] - m) * ig) : 0.f;
+                    zsum += ex[i];
+                }
+                const float az = div_hw(abar, zsum);   // zsum >= 1 (the max's own term)
 #pragma unroll
                 for (int i = 0; i < 6; ++i) {
                     if (!(x[i] > -INFINITY)) continue;
-                    const float w = abar * expf((float)(x[i] - m) * ig) / zsum;
+                    const float w = az * ex[i];
                     if (!slew_lane) aAin[i] = w;
                     aSin[i] = w * sc * dds[i];
                     aload += w * sc * ddl[i];

@@ -228,14 +228,21 @@ struct MaxMerge {
             m = y > m ? y : m;
         } else if (!(y > -INFINITY)) {
             // an absent candidate (another exception tag's arrival): no term
-        } else if (y > m) {
-            s = s * expf((float)(m - y) * inv_g) + 1.f;
-            m = y;
         } else {
-            s += expf((float)(y - m) * inv_g);
+            // one exponential of -|y - m| / gamma, whichever of the two is
+            // larger, and selects: no branch on the values, which differ
+            // between the lanes of a warp (-|y - m| is m - y, or y - m,
+            // exactly: IEEE subtraction rounds symmetrically).  The hardware
+            // exponential (__expf) errs by a few ulp near 0 and more only
+            // where the term is negligible beside s >= 1.
+            const float e = __expf(-fabsf((float)(y - m)) * inv_g);
+            const bool up = y > m;
+            s = up ? s * e + 1.f : s + e;
+            m = up ? y : m;
         }
     }
-    __device__ __forceinline__ T get(float g) const { return SMOOTH ? m + g * logf(s) : m; }
+    // __logf of s in [1, candidates]: absolute error below 1e-6, times gamma
+    __device__ __forceinline__ T get(float g) const { return SMOOTH ? m + g * __logf(s) : m; }
 };
 
 __device__ __forceinline__ int item_out_pin(const DevCtx &c, int t, int pin0)

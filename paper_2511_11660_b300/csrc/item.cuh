@@ -320,6 +320,16 @@ __device__ __forceinline__ bool group_all_warp(const DevCtx &c, bool ok)
 }
 
 // ------------------------------------------------------------- forward
+
+// The slew degraded by a net, sqrt(s^2 + V): the hardware square root
+// (sqrt.approx, relative error within 2^-23 by the PTX ISA) in place of the
+// IEEE-rounded one, whose longer sequence every level of the pass waits on.
+__device__ __forceinline__ float sqrt_hw(float x)
+{
+    float r;
+    asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
 //
 // Each item is processed in three steps: prep (loads that do not depend on
 // this pass's results), probe (are the inputs' results complete?  only in
@@ -537,8 +547,8 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
                 const float V = k != kq ? c.netV[(size_t)a * K + k] : f.V0[j];
                 ain[j][0] = a0 + Dn;
                 ain[j][1] = a1 + Dn;
-                sin[j][0] = sqrtf(fmaf(s0, s0, V));
-                sin[j][1] = sqrtf(fmaf(s1, s1, V));
+                sin[j][0] = sqrt_hw(fmaf(s0, s0, V));
+                sin[j][1] = sqrt_hw(fmaf(s1, s1, V));
                 // lane q stores component q of the input pin: (el, rf = q & 1)
                 st_comp_df(c.at + (size_t)a * K + k, q, rfo ? ain[j][1] : ain[j][0]);
                 st_comp(c.slew + (size_t)a * K + k, q, rfo ? sin[j][1] : sin[j][0]);
@@ -590,7 +600,7 @@ __device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const Fwd
         DF oa(-sgn * INFINITY);   // no finite candidate
         if (wy > -INFINITY) {
             oa = win + wd;
-            if (SMOOTH) oa = oa + sgn * (c.gamma * logf(ma.s));
+            if (SMOOTH) oa = oa + sgn * (c.gamma * __logf(ma.s));
         }
         const float os = sgn * ms.get(c.gamma);
         st_comp_df(c.at + (size_t)z * K + k, q, oa);
@@ -673,7 +683,7 @@ __device__ __forceinline__ void ep_run(const DevCtx &c, const EpItem &x, DF at0,
         const float Dn = k != kq ? c.netD[(size_t)p * K + k] : x.Dn0, V = k != kq ? c.netV[(size_t)p * K + k] : x.V0;
         const DF A = ad + Dn;
         st_comp_df(c.at + (size_t)p * K + k, q, A);
-        st_comp(c.slew + (size_t)p * K + k, q, sqrtf(fmaf(sd, sd, V)));
+        st_comp(c.slew + (size_t)p * K + k, q, sqrt_hw(fmaf(sd, sd, V)));
         st_comp_df(c.rat + (size_t)p * K + k, q, req);
         const float sk = q >= 2 ? req - A : A - req;
         st_comp(c.slack + (size_t)p * K + k, q, sk);
