@@ -227,10 +227,18 @@ __device__ __forceinline__ AdjItem adj_prep(const DevCtx &c, const int *tnin, co
 // lanes, through slew_sink = sqrt(slew_z^2 + var)).  Every schedule sums in
 // one order: the entries of each residue class mod 4 in increasing order,
 // then (class 0 + class 1) + (class 2 + class 3).
-__device__ __forceinline__ float4 adj_sink_terms(const DevCtx &c, int s, int k, float4 as, float szr, float szf)
+// A gate input's mailbox record (`scaled`) carries dJ/dslew / slew_sink
+// already, divided by the item that published it: the gather then needs
+// neither the sink's slew nor a division.  From the adjoint array (endpoints,
+// the level sweep) the same quotient is formed here from the same operands.
+__device__ __forceinline__ float4 adj_sink_terms(const DevCtx &c, int s, int k, float4 as, float szr, float szf,
+                                                 bool scaled)
 {
-    const float ssr = ld_state(c.slew + (size_t)s * c.K + k, 2), ssf = ld_state(c.slew + (size_t)s * c.K + k, 3);
-    return make_float4(as.x, as.y, div_hw(as.z * szr, ssr), div_hw(as.w * szf, ssf));
+    if (!scaled) {
+        as.z = div_hw(as.z, ld_state(c.slew + (size_t)s * c.K + k, 2));
+        as.w = div_hw(as.w, ld_state(c.slew + (size_t)s * c.K + k, 3));
+    }
+    return make_float4(as.x, as.y, __fmul_rn(as.z, szr), __fmul_rn(as.w, szf));
 }
 
 // Are the adjoints of every gate-input sink of the item's net complete (all
@@ -261,7 +269,7 @@ __device__ __forceinline__ bool adj_probe(const DevCtx &c, const AdjItem &a, int
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
             if (s[u] < 0) continue;
-            const float4 tm = adj_sink_terms(c, s[u], kq, v[u], a.sz0[0], a.sz0[1]);
+            const float4 tm = adj_sink_terms(c, s[u], kq, v[u], a.sz0[0], a.sz0[1], s[u] < c.ep_begin);
             acc.x += tm.x;
             acc.y += tm.y;
             acc.z += tm.z;
@@ -348,7 +356,7 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
                 for (int p = a.f0 + r; p < a.f1; p += 4) {
                     const int s = chk(c, c.fo_pin[p], c.P);
                     const float4 as = (WAIT && s < c.ep_begin) ? ld_relaxed4(abox_at(c, par, s, k)) : c.adj[(size_t)s * K + k];
-                    const float4 tm = adj_sink_terms(c, s, k, as, szr, szf);
+                    const float4 tm = adj_sink_terms(c, s, k, as, szr, szf, WAIT && s < c.ep_begin);
                     cls[r] += j == 0 ? tm.x : j == 1 ? tm.y : j == 2 ? tm.z : tm.w;
                 }
             }
@@ -459,9 +467,11 @@ __device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const i
                 const float v = q == 0 ? aAin[j * 2] : q == 1 ? aAin[j * 2 + 1] : q == 2 ? aSin[j * 2] : aSin[j * 2 + 1];
                 reinterpret_cast<float *>(c.adj + (size_t)(pin0 + j) * K + k)[q] = v;
                 if (WAIT) {
+                    // the slew lanes publish dJ/dslew / slew of the pin (adj_sink_terms)
+                    const float pv = q >= 2 ? div_hw(v, ld_state(c.slew + (size_t)(pin0 + j) * K + k, q)) : v;
                     float *n = reinterpret_cast<float *>(abox_at(c, par, pin0 + j, k));
                     float *o = reinterpret_cast<float *>(abox_at(c, par ^ 1, pin0 + j, k));
-                    st_relaxed(n + q, v);
+                    st_relaxed(n + q, pv);
                     o[q] = __int_as_float(0x7fffffff);
                 }
             }
@@ -495,9 +505,11 @@ __device__ __forceinline__ void adj_store(const DevCtx &c, const AdjItem &a, int
         if (j >= a.nin) continue;
         const float v = q == 0 ? p.aAin[j * 2] : q == 1 ? p.aAin[j * 2 + 1] : q == 2 ? p.aSin[j * 2] : p.aSin[j * 2 + 1];
         reinterpret_cast<float *>(c.adj + (size_t)(a.pin0 + j) * K + k)[q] = v;
+        // the slew lanes publish dJ/dslew / slew of the pin (adj_sink_terms)
+        const float pv = q >= 2 ? div_hw(v, q == 2 ? a.sin0[j][0] : a.sin0[j][1]) : v;
         float *n = reinterpret_cast<float *>(abox_at(c, par, a.pin0 + j, k));
         float *o = reinterpret_cast<float *>(abox_at(c, par ^ 1, a.pin0 + j, k));
-        st_relaxed(n + q, v);
+        st_relaxed(n + q, pv);
         o[q] = __int_as_float(0x7fffffff);
     }
 }
