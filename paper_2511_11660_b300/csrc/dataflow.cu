@@ -252,8 +252,11 @@ __global__ void k_coop_begin(const DevCtx c)
     }
 }
 
+// Four blocks a SM (64 registers a thread): a level's items are independent
+// after the barrier, so more warps in flight hide more load latency (64
+// designs x 4 corners: 14.6 -> 11.9 ms an update).
 template <bool SMOOTH, bool UNIFORM>
-__global__ void __launch_bounds__(kDfThreads) k_coop_pass(const DevCtx c)
+__global__ void __launch_bounds__(kDfThreads, 4) k_coop_pass(const DevCtx c)
 {
     extern __shared__ float smem[];
     __shared__ int abort_flag;
