@@ -81,8 +81,8 @@ __device__ __forceinline__ bool warp_idle_round(const DevCtx &c, long long &spin
     return true;
 }
 
-template <bool SMOOTH, bool UNIFORM, bool THRU>
-__global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
+template <bool SMOOTH, bool UNIFORM, bool THRU, class Ctx = DevCtx>
+__global__ void __launch_bounds__(kDfThreads) k_df_forward(const Ctx c)
 {
     extern __shared__ float smem[];
     const SmemLib L = stage_library(c, smem);
@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
     for (;;) {
         const int ch = next_chunk(c, 1, c.n_fwd_chunks);
         if (ch < 0) break;
-        const int x = c.fwd_chunk_lo[ch] + lane / (4 * c.KL);
+        const int x = c.fwd_chunk_lo[ch] + lane / (4 * nKL(c));
         bool pending = x < c.fwd_chunk_hi[ch];
         const bool is_item = x < c.I;   // else position x - I of the endpoint order
         FwdItem f{};
@@ -118,8 +118,8 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const DevCtx c)
     }
 }
 
-template <bool UNIFORM, bool THRU>
-__global__ void __launch_bounds__(kDfThreads) k_df_backward(const DevCtx c)
+template <bool UNIFORM, bool THRU, class Ctx = DevCtx>
+__global__ void __launch_bounds__(kDfThreads) k_df_backward(const Ctx c)
 {
     extern __shared__ float smem[];
     const SmemLib L = stage_library(c, smem);
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kDfThreads) k_df_backward(const DevCtx c)
     for (;;) {
         const int ch = next_chunk(c, 2, c.n_bwd_chunks);
         if (ch < 0) break;
-        const int x = c.bwd_chunk_lo[ch] + lane / (4 * c.KL);
+        const int x = c.bwd_chunk_lo[ch] + lane / (4 * nKL(c));
         bool pending = x < c.bwd_chunk_hi[ch];
         BwdItem b{};
         if (pending) b = bwd_prep(c, L.nin, L.kind, x, q);
@@ -183,17 +183,32 @@ static DfKernel df_backward_kernel(bool uniform, bool thru)
     if (thru) return uniform ? k_df_backward<true, true> : k_df_backward<false, true>;
     return uniform ? k_df_backward<true, false> : k_df_backward<false, false>;
 }
+// the builds for one state a pin (DevCtxOne; no -through sets then)
+using DfKernelOne = void (*)(DevCtxOne);
+static DfKernelOne df_forward_kernel_one(bool smooth, bool uniform)
+{
+    return smooth ? (uniform ? k_df_forward<true, true, false, DevCtxOne> : k_df_forward<true, false, false, DevCtxOne>)
+                  : (uniform ? k_df_forward<false, true, false, DevCtxOne> : k_df_forward<false, false, false, DevCtxOne>);
+}
+static DfKernelOne df_backward_kernel_one(bool uniform)
+{
+    return uniform ? k_df_backward<true, false, DevCtxOne> : k_df_backward<false, false, DevCtxOne>;
+}
 
 // Shared-memory attribute and persistent grid sizes, computed outside any
 // stream capture.  `requested` > 0 fixes the grid size.
 cudaError_t dataflow_prepare(HostSched &h, bool smooth, int requested)
 {
     const size_t smem = df_smem_bytes(h.T);
-    auto kf = df_forward_kernel(smooth, h.uniform, h.thru);
-    auto kb = df_backward_kernel(h.uniform, h.thru);
     int bf = 0, bb = 0;
-    cudaError_t e = occupancy_blocks(kf, smem, &bf);
-    if (e == cudaSuccess) e = occupancy_blocks(kb, smem, &bb);
+    cudaError_t e;
+    if (h.one) {
+        e = occupancy_blocks(df_forward_kernel_one(smooth, h.uniform), smem, &bf);
+        if (e == cudaSuccess) e = occupancy_blocks(df_backward_kernel_one(h.uniform), smem, &bb);
+    } else {
+        e = occupancy_blocks(df_forward_kernel(smooth, h.uniform, h.thru), smem, &bf);
+        if (e == cudaSuccess) e = occupancy_blocks(df_backward_kernel(h.uniform, h.thru), smem, &bb);
+    }
     if (e != cudaSuccess) return e;
     h.df_blocks_fwd = requested > 0 ? std::min(requested, bf) : bf;
     h.df_blocks_bwd = requested > 0 ? std::min(requested, bb) : bb;
@@ -353,12 +368,15 @@ void launch_dataflow_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, 
     launch_df_reset(c, h.df_blocks_fwd, st);
     launch_net_phase(c, h, st);
     if (ev) cudaEventRecord(ev[1], st);
+    const DevCtxOne c1{c};   // the same context, for the one-state builds
     if (c.n_fwd_chunks > 0) {
-        df_forward_kernel(c.gamma > 0.f, h.uniform, h.thru)<<<h.df_blocks_fwd, kDfThreads, smem, st>>>(c);
+        if (h.one) df_forward_kernel_one(c.gamma > 0.f, h.uniform)<<<h.df_blocks_fwd, kDfThreads, smem, st>>>(c1);
+        else df_forward_kernel(c.gamma > 0.f, h.uniform, h.thru)<<<h.df_blocks_fwd, kDfThreads, smem, st>>>(c);
     }
     if (ev) cudaEventRecord(ev[2], st);
     if (c.n_bwd_chunks > 0) {
-        df_backward_kernel(h.uniform, h.thru)<<<h.df_blocks_bwd, kDfThreads, smem, st>>>(c);
+        if (h.one) df_backward_kernel_one(h.uniform)<<<h.df_blocks_bwd, kDfThreads, smem, st>>>(c1);
+        else df_backward_kernel(h.uniform, h.thru)<<<h.df_blocks_bwd, kDfThreads, smem, st>>>(c);
     }
     if (ev) cudaEventRecord(ev[3], st);
     launch_reduce(c, h, st);

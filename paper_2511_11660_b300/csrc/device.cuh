@@ -182,6 +182,18 @@ struct DevCtx {
     float ax1[7], ax2[7], iw1[6], iw2[6];
 };
 
+// A context with one state per pin and one corner per lane group (K = KL =
+// 1: one corner, no exception tags), known at compile time.  The per-item
+// functions read the state counts through nK / nKL, so the kernels built for
+// this type carry no other-states loops, checks or index arithmetic: a
+// polling round and an item's run issue fewer instructions.  Made by copying
+// a DevCtx whose K and KL are 1.
+struct DevCtxOne : DevCtx {};
+__device__ __forceinline__ int nK(const DevCtx &c) { return c.K; }
+__device__ __forceinline__ int nK(const DevCtxOne &) { return 1; }
+__device__ __forceinline__ int nKL(const DevCtx &c) { return c.KL; }
+__device__ __forceinline__ int nKL(const DevCtxOne &) { return 1; }
+
 // Debug builds (-DSTA_CHECKS) range-check every index a kernel derives from
 // plan data: out of range records kErrBounds in the device error word and
 // yields 0 (or -1 for a cell type), so the access that follows stays in

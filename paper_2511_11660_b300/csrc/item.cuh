@@ -239,36 +239,43 @@ __device__ __forceinline__ DF nan_df() { return DF(nan_f(), nan_f()); }
 // the store to p (the forward records below stay [parity][item][state]: an
 // item's readers are its neighbours' readers too, and interleaving would
 // spread them over twice the lines)
-__device__ __forceinline__ size_t box_index(const DevCtx &c, int par, int pin, int k)
+template <class Ctx>
+__device__ __forceinline__ size_t box_index(const Ctx &c, int par, int pin, int k)
 {
-    return (((size_t)pin * c.K + k) << 1) | (size_t)par;
+    return (((size_t)pin * nK(c) + k) << 1) | (size_t)par;
 }
 // forward mailbox records: [parity][driver item][state], dense over the
 // items (only item outputs are published), so the entries a level polls sit
 // close together
-__device__ __forceinline__ size_t fbox_index(const DevCtx &c, int par, int slot, int k)
+template <class Ctx>
+__device__ __forceinline__ size_t fbox_index(const Ctx &c, int par, int slot, int k)
 {
-    return ((size_t)par * c.I + slot) * c.K + k;
+    return ((size_t)par * c.I + slot) * nK(c) + k;
 }
-__device__ __forceinline__ DF4 *fbox_a(const DevCtx &c, int par, int slot, int k) { return c.fbox_a + fbox_index(c, par, slot, k); }
-__device__ __forceinline__ float4 *fbox_s(const DevCtx &c, int par, int slot, int k)
+template <class Ctx>
+__device__ __forceinline__ DF4 *fbox_a(const Ctx &c, int par, int slot, int k) { return c.fbox_a + fbox_index(c, par, slot, k); }
+template <class Ctx>
+__device__ __forceinline__ float4 *fbox_s(const Ctx &c, int par, int slot, int k)
 {
     return c.fbox_s + fbox_index(c, par, slot, k);
 }
 // a gate input's required-time record, by its entry fe in its driver's
 // fan-out list (c.pin_fo): a driver reads its sinks' records contiguously
-__device__ __forceinline__ DF4 *rbox_at(const DevCtx &c, int par, int fe, int k) { return c.rbox + box_index(c, par, fe, k); }
+template <class Ctx>
+__device__ __forceinline__ DF4 *rbox_at(const Ctx &c, int par, int fe, int k) { return c.rbox + box_index(c, par, fe, k); }
 
 // Lane q publishes component q of item g's output arrival and slew for
 // parity par and clears the same component of parity par ^ 1.
-__device__ __forceinline__ void publish_fwd(const DevCtx &c, int par, int g, int k, int q, DF at, float sl)
+template <class Ctx>
+__device__ __forceinline__ void publish_fwd(const Ctx &c, int par, int g, int k, int q, DF at, float sl)
 {
     st_relaxed_df(fbox_a(c, par, g, k)->v + q, at);
     st_relaxed(reinterpret_cast<float *>(fbox_s(c, par, g, k)) + q, sl);
     fbox_a(c, par ^ 1, g, k)->v[q] = nan_df();
     reinterpret_cast<float *>(fbox_s(c, par ^ 1, g, k))[q] = nan_f();
 }
-__device__ __forceinline__ void publish_rat(const DevCtx &c, int par, int fe, int k, int q, DF r)
+template <class Ctx>
+__device__ __forceinline__ void publish_rat(const Ctx &c, int par, int fe, int k, int q, DF r)
 {
     st_relaxed_df(rbox_at(c, par, fe, k)->v + q, r);
     rbox_at(c, par ^ 1, fe, k)->v[q] = nan_df();
@@ -302,10 +309,12 @@ __device__ __forceinline__ unsigned quad_mask() { return 0xFu << (threadIdx.x & 
 
 // Corners are spread over c.KL quads: an item owns 4 * KL consecutive lanes,
 // and the quad with corner offset kq handles corners kq, kq + KL, ...
-__device__ __forceinline__ int corner_lane(const DevCtx &c) { return (threadIdx.x >> 2) & (c.KL - 1); }
-__device__ __forceinline__ unsigned group_mask(const DevCtx &c)
+template <class Ctx>
+__device__ __forceinline__ int corner_lane(const Ctx &c) { return (threadIdx.x >> 2) & (nKL(c) - 1); }
+template <class Ctx>
+__device__ __forceinline__ unsigned group_mask(const Ctx &c)
 {
-    const int w = 4 * c.KL;
+    const int w = 4 * nKL(c);
     if (w >= 32) return 0xffffffffu;
     return ((1u << w) - 1u) << ((threadIdx.x & 31) & ~(w - 1));
 }
@@ -313,7 +322,8 @@ __device__ __forceinline__ unsigned group_mask(const DevCtx &c)
 // callers keep all 32 lanes converged (lanes without an item vote false).  A
 // vote over each group's own lanes (a 4-lane mask) costs many times a
 // full-warp ballot when every group of the warp votes at once.
-__device__ __forceinline__ bool group_all_warp(const DevCtx &c, bool ok)
+template <class Ctx>
+__device__ __forceinline__ bool group_all_warp(const Ctx &c, bool ok)
 {
     const unsigned gm = group_mask(c);
     return (__ballot_sync(0xffffffffu, ok) & gm) == gm;
@@ -356,8 +366,8 @@ struct FwdIn {
 
 // BYITEM (the schedules that read the drivers from the mailboxes): drv
 // holds the driver items; otherwise the driver pins (their pin states).
-template <bool BYITEM = false>
-__device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, const int *tkind, const int *tsense,
+template <bool BYITEM = false, class Ctx = DevCtx>
+__device__ __forceinline__ FwdItem fwd_prep(const Ctx &c, const int *tnin, const int *tkind, const int *tsense,
                                             int g)
 {
     FwdItem f;
@@ -367,7 +377,7 @@ __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, co
     f.kind = f.t >= 0 ? tkind[f.t] : -1;
     f.nin = f.kind == 0 ? tnin[f.t] : 0;
     f.tag = (c.Tg > 1 && f.kind != 0) ? c.item_tag[g] : 0;
-    const int K = c.K, kq = corner_lane(c);
+    const int K = nK(c), kq = corner_lane(c);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
         const bool on = j < f.nin;
@@ -392,8 +402,8 @@ __device__ __forceinline__ FwdItem fwd_prep(const DevCtx &c, const int *tnin, co
 // and no -through sets, where the first corner's values are all there is).
 // THRU = false: the design has no -through sets (c.pin_adv is NULL); the
 // kernels compiled so carry none of their code and registers.
-template <bool THRU = true, bool PAIR = false>
-__device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int par, int q, FwdIn &in,
+template <bool THRU = true, bool PAIR = false, class Ctx = DevCtx>
+__device__ __forceinline__ bool fwd_probe(const Ctx &c, const FwdItem &f, int par, int q, FwdIn &in,
                                           unsigned *seen = nullptr)
 {
     const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
@@ -414,7 +424,7 @@ __device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int
                 in.sl[j] = (q & 1) ? s1 : s0;
                 in.slp[j] = (q & 1) ? s0 : s1;
                 const bool cj = real_df(a0) && real_df(a1) && s0 == s0 && s1 == s1;
-                if (seen && cj && c.K == c.KL && !pin_adv) *seen |= 1u << j;
+                if (seen && cj && nK(c) == nKL(c) && !pin_adv) *seen |= 1u << j;
                 ok = ok && cj;
             } else {
                 in.at[j] = ld_relaxed_df(fbox_a(c, par, f.drv[j], kq)->v + q);
@@ -423,8 +433,8 @@ __device__ __forceinline__ bool fwd_probe(const DevCtx &c, const FwdItem &f, int
             }
             // the lane's other states; with -through every state (a path may
             // come in from the previous tag)
-            const int k0 = pin_adv ? 0 : kq + c.KL, dk = pin_adv ? 1 : c.KL;
-            for (int k = k0; k < c.K && ok; k += dk)
+            const int k0 = pin_adv ? 0 : kq + nKL(c), dk = pin_adv ? 1 : nKL(c);
+            for (int k = k0; k < nK(c) && ok; k += dk)
                 if (k != kq)
                     ok = complete_df(fbox_a(c, par, f.drv[j], k)) &&
                          complete(ld_relaxed4(fbox_s(c, par, f.drv[j], k)));
@@ -441,14 +451,14 @@ struct FwdOut {
     float sl;
 };
 
-template <bool SMOOTH, bool UNIFORM, bool WAIT, bool THRU = true, bool PAIR = false, class L>
-__device__ __forceinline__ void fwd_run(const DevCtx &c, const L &lut, const FwdItem &f, const FwdIn &in, int g,
+template <bool SMOOTH, bool UNIFORM, bool WAIT, bool THRU = true, bool PAIR = false, class L, class Ctx = DevCtx>
+__device__ __forceinline__ void fwd_run(const Ctx &c, const L &lut, const FwdItem &f, const FwdIn &in, int g,
                                         int q, int par, FwdOut *first = nullptr)
 {
     const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
-    const int K = c.K, t = f.t, pin0 = f.pin0, nin = f.nin;
+    const int K = nK(c), t = f.t, pin0 = f.pin0, nin = f.nin;
     const int el = q >> 1, rfo = q & 1;
-    const int kq = corner_lane(c), KL = c.KL;
+    const int kq = corner_lane(c), KL = nKL(c);
     const bool pub = WAIT && g != c.hold_item;
     // a startpoint's arrival exists only in its own exception tag's states
     // (absent elsewhere: -inf late, +inf early); slews are tag-free
@@ -618,29 +628,30 @@ struct EpItem {
     float Dn0, V0;
 };
 
-template <bool BYITEM = false>
-__device__ __forceinline__ EpItem ep_prep(const DevCtx &c, int e)
+template <bool BYITEM = false, class Ctx = DevCtx>
+__device__ __forceinline__ EpItem ep_prep(const Ctx &c, int e)
 {
     EpItem x;
     e = chk(c, e, c.E);
     x.p = chk(c, c.ep_pin[e], c.P);
     x.d = BYITEM ? chk(c, c.ep_drv[e], c.I) : chk(c, c.drv_of[x.p], c.P);
     x.isD = c.ep_is_d[e] != 0;
-    x.Dn0 = c.netD[(size_t)x.p * c.K + corner_lane(c)];
-    x.V0 = c.netV[(size_t)x.p * c.K + corner_lane(c)];
+    x.Dn0 = c.netD[(size_t)x.p * nK(c) + corner_lane(c)];
+    x.V0 = c.netV[(size_t)x.p * nK(c) + corner_lane(c)];
     return x;
 }
 
 // the driver's arrival and slew of the lane's corners are complete; lane q
 // reads component q of its first corner (returned; the caller's group vote,
 // group_all_warp, covers the quad)
-__device__ __forceinline__ bool ep_probe(const DevCtx &c, const EpItem &x, int par, int q, DF &at0, float &sl0)
+template <class Ctx>
+__device__ __forceinline__ bool ep_probe(const Ctx &c, const EpItem &x, int par, int q, DF &at0, float &sl0)
 {
     const int kq = corner_lane(c);
     at0 = ld_relaxed_df(fbox_a(c, par, x.d, kq)->v + q);
     sl0 = ld_relaxed1(reinterpret_cast<const float *>(fbox_s(c, par, x.d, kq)) + q);
     bool ok = real_df(at0) && sl0 == sl0;
-    for (int k = kq + c.KL; k < c.K && ok; k += c.KL)
+    for (int k = kq + nKL(c); k < nK(c) && ok; k += nKL(c))
         ok = complete_df(fbox_a(c, par, x.d, k)) && complete(ld_relaxed4(fbox_s(c, par, x.d, k)));
     return ok;
 }
@@ -648,15 +659,15 @@ __device__ __forceinline__ bool ep_probe(const DevCtx &c, const EpItem &x, int p
 // Arrival through the net, required times of the ideal clock (D: setup
 // capture edge T - setup, hold 0 + hold; PO: T and 0), pin and endpoint
 // slacks (min over rise/fall) and violation flags.  Lane q: component q.
-template <bool WAIT>
-__device__ __forceinline__ void ep_run(const DevCtx &c, const EpItem &x, DF at0, float sl0, int e, int q,
+template <bool WAIT, class Ctx = DevCtx>
+__device__ __forceinline__ void ep_run(const Ctx &c, const EpItem &x, DF at0, float sl0, int e, int q,
                                        int par)
 {
-    const int K = c.K, p = x.p, d = x.d;
+    const int K = nK(c), p = x.p, d = x.d;
     const unsigned m = quad_mask();
     const int base = threadIdx.x & 28;   // first lane of the quad
     const int kq = corner_lane(c);
-    for (int k = kq; k < K; k += c.KL) {
+    for (int k = kq; k < K; k += nKL(c)) {
         // requirement of state k: late = M T + off.x (M = 0: off.x alone),
         // early = off.y, from the exception tag's action (false path: no
         // check; multicycle: M; max delay: M = 0, off.x = V - setup; min
@@ -716,10 +727,11 @@ struct BwdItem {
     int fin[3];
 };
 
-__device__ __forceinline__ BwdItem bwd_prep(const DevCtx &c, const int *tnin, const int *tkind, int g, int q)
+template <class Ctx>
+__device__ __forceinline__ BwdItem bwd_prep(const Ctx &c, const int *tnin, const int *tkind, int g, int q)
 {
     BwdItem b;
-    const int K = c.K, kq = corner_lane(c);
+    const int K = nK(c), kq = corner_lane(c);
     g = chk(c, g, c.I);
     b.t = chk_type(c, c.item_type[g]);
     b.pin0 = chk(c, c.item_pin0[g], c.P);
@@ -818,11 +830,11 @@ __device__ __forceinline__ DF quad_fold(Fold4 &f, int q, unsigned m = quad_mask(
 // required time: R = min (late) / max (early) over the sinks of RAT - Elmore
 // delay, the first extreme in fan-out order, its difference formed exactly.
 // Endpoint sinks were set by the forward pass.
-template <bool THRU = true>
-__device__ __forceinline__ bool bwd_probe_split(const DevCtx &c, const BwdItem &b, int par, int q, Fold4 &f)
+template <bool THRU = true, class Ctx = DevCtx>
+__device__ __forceinline__ bool bwd_probe_split(const Ctx &c, const BwdItem &b, int par, int q, Fold4 &f)
 {
     const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
-    const int K = c.K, kq = corner_lane(c);
+    const int K = nK(c), kq = corner_lane(c);
     fold4_clear(f);
     const int nfo = b.f1 - b.f0;
     for (int e0 = q; e0 < nfo; e0 += 16) {
@@ -866,11 +878,11 @@ __device__ __forceinline__ bool bwd_probe_split(const DevCtx &c, const BwdItem &
         }
     }
     // the lane's other states of its gate-input sinks
-    if (K > c.KL || pin_adv) {
+    if (K > nKL(c) || pin_adv) {
         for (int e = q; e < nfo; e += 4) {
             const int s = chk(c, __ldg(c.fo_pin + b.f0 + e), c.P);
             if (s >= c.ep_begin) continue;
-            const int k0 = pin_adv ? 0 : kq + c.KL, dk = pin_adv ? 1 : c.KL;
+            const int k0 = pin_adv ? 0 : kq + nKL(c), dk = pin_adv ? 1 : nKL(c);
             for (int k = k0; k < K; k += dk)
                 if (k != kq && !complete_df(rbox_at(c, par, b.f0 + e, k))) return false;
         }
@@ -883,17 +895,17 @@ __device__ __forceinline__ bool bwd_probe_split(const DevCtx &c, const BwdItem &
 // the first corner's output required time comes folded from the probe (Rpre).
 // With `first` (the tile schedule's ring), the lane's first-corner required
 // time of each input pin, component q, is returned there as well.
-template <bool UNIFORM, bool WAIT, bool THRU = true, class L>
-__device__ __forceinline__ void bwd_run(const DevCtx &c, const L &lut, const int *tsense, const BwdItem &b, int q,
+template <bool UNIFORM, bool WAIT, bool THRU = true, class L, class Ctx = DevCtx>
+__device__ __forceinline__ void bwd_run(const Ctx &c, const L &lut, const int *tsense, const BwdItem &b, int q,
                                         int par, DF Rpre, DF *first = nullptr)
 {
     const uint32_t *pin_adv = THRU ? c.pin_adv : nullptr;
-    const int t = b.t, pin0 = b.pin0, z = b.z, K = c.K;
+    const int t = b.t, pin0 = b.pin0, z = b.z, K = nK(c);
     const int el = q >> 1, rfi = q & 1;
     const unsigned m = quad_mask();
     const int base = threadIdx.x & 28;
     const int kq = corner_lane(c);
-    for (int k = kq; k < K; k += c.KL) {
+    for (int k = kq; k < K; k += nKL(c)) {
         const bool first_k = k == kq;
         // required time of the output, component q, over its net sinks
         DF R(el ? INFINITY : -INFINITY);

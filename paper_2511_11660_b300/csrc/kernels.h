@@ -25,6 +25,7 @@ struct HostSched {
     int adj_blocks = 0;               // persistent grid of the dataflow adjoint (0 = level sweep)
     bool adj_level = false;           // reverse sweep forced to one launch per level
     bool adj_ready = false;           // adjoint_prepare has run for the current choice
+    bool one = false;                 // one state a pin, one corner a lane group: the DevCtxOne kernels
     int coop_blocks = 0;              // co-resident grid of the cooperative schedule
     int tile_blocks = 0;              // tiles (co-resident blocks) of the tile schedule
 };

@@ -387,6 +387,7 @@ sta_status create_from_plan(sta_ctx *c, int device)
     {
         // a warp works on 8 / KL items, 4 * KL lanes each (KL corners side by side)
         d.KL = quads_per_item(pl.K);
+        h.one = d.K == 1 && d.KL == 1 && !h.thru;
         const int32_t kChunkItems = 8 / d.KL;
         // Forward work list: the item chunks of each level, and after the
         // chunks of level s the endpoints whose driver sits at level
