@@ -178,9 +178,10 @@ __global__ void k_adj_seed(const DevCtx c)
     }
 }
 
-__device__ __forceinline__ float4 *abox_at(const DevCtx &c, int par, int pin, int k)
+template <class Ctx>
+__device__ __forceinline__ float4 *abox_at(const Ctx &c, int par, int pin, int k)
 {
-    return c.abox + ((((size_t)pin * c.K + k) << 1) | (size_t)par);   // [pin][state][parity], as rbox
+    return c.abox + ((((size_t)pin * nK(c) + k) << 1) | (size_t)par);   // [pin][state][parity], as rbox
 }
 
 struct AdjItem {
@@ -192,10 +193,11 @@ struct AdjItem {
     DF ain0[3][2];
 };
 
-__device__ __forceinline__ AdjItem adj_prep(const DevCtx &c, const int *tnin, const int *tkind, int g, int q)
+template <class Ctx>
+__device__ __forceinline__ AdjItem adj_prep(const Ctx &c, const int *tnin, const int *tkind, int g, int q)
 {
     AdjItem a;
-    const int K = c.K, kq = corner_lane(c);
+    const int K = nK(c), kq = corner_lane(c);
     g = chk(c, g, c.I);
     a.t = chk_type(c, c.item_type[g]);
     a.pin0 = chk(c, c.item_pin0[g], c.P);
@@ -231,12 +233,13 @@ __device__ __forceinline__ AdjItem adj_prep(const DevCtx &c, const int *tnin, co
 // already, divided by the item that published it: the gather then needs
 // neither the sink's slew nor a division.  From the adjoint array (endpoints,
 // the level sweep) the same quotient is formed here from the same operands.
-__device__ __forceinline__ float4 adj_sink_terms(const DevCtx &c, int s, int k, float4 as, float szr, float szf,
+template <class Ctx>
+__device__ __forceinline__ float4 adj_sink_terms(const Ctx &c, int s, int k, float4 as, float szr, float szf,
                                                  bool scaled)
 {
     if (!scaled) {
-        as.z = div_hw(as.z, ld_state(c.slew + (size_t)s * c.K + k, 2));
-        as.w = div_hw(as.w, ld_state(c.slew + (size_t)s * c.K + k, 3));
+        as.z = div_hw(as.z, ld_state(c.slew + (size_t)s * nK(c) + k, 2));
+        as.w = div_hw(as.w, ld_state(c.slew + (size_t)s * nK(c) + k, 3));
     }
     return make_float4(as.x, as.y, __fmul_rn(as.z, szr), __fmul_rn(as.w, szf));
 }
@@ -246,9 +249,10 @@ __device__ __forceinline__ float4 adj_sink_terms(const DevCtx &c, int s, int k, 
 // adjoint record of fan-out entries q, q + 4, ... (first corner) and sums
 // each component over them (`part`, its residue class); adj_quad_sum then
 // combines the classes.  Endpoint sinks were seeded by an earlier launch.
-__device__ __forceinline__ bool adj_probe(const DevCtx &c, const AdjItem &a, int par, int q, float4 &part)
+template <class Ctx>
+__device__ __forceinline__ bool adj_probe(const Ctx &c, const AdjItem &a, int par, int q, float4 &part)
 {
-    const int K = c.K, kq = corner_lane(c);
+    const int K = nK(c), kq = corner_lane(c);
     const int nfo = a.f1 - a.f0;
     bool ok = true;
     float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -279,7 +283,7 @@ __device__ __forceinline__ bool adj_probe(const DevCtx &c, const AdjItem &a, int
     for (int e = q; e < nfo && ok; e += 4) {
         const int s = chk(c, __ldg(c.fo_pin + a.f0 + e), c.P);
         if (s < c.ep_begin)
-            for (int k = kq + c.KL; k < K && ok; k += c.KL) ok = complete(ld_relaxed4(abox_at(c, par, s, k)));
+            for (int k = kq + nKL(c); k < K && ok; k += nKL(c)) ok = complete(ld_relaxed4(abox_at(c, par, s, k)));
     }
     part = acc;
     return ok;
@@ -329,12 +333,12 @@ struct AdjPart {
 // sums them over the quad with the whole warp converged (adj_part_sum) and
 // stores them (adj_store).  The sums and the stores are the ones adj_run
 // makes itself otherwise.
-template <bool UNIFORM, bool WAIT, bool SPLIT = false, class Lut>
-__device__ __forceinline__ void adj_run(const DevCtx &c, const Lut &lut, const int *tsense, const AdjItem &a, int g,
+template <bool UNIFORM, bool WAIT, bool SPLIT = false, class Lut, class Ctx = DevCtx>
+__device__ __forceinline__ void adj_run(const Ctx &c, const Lut &lut, const int *tsense, const AdjItem &a, int g,
                                         int q, int par, float abar0, AdjPart *part = nullptr)
 {
-    const int t = a.t, pin0 = a.pin0, z = a.z, K = c.K, nin = a.nin;
-    const int kq = corner_lane(c), KL = c.KL;
+    const int t = a.t, pin0 = a.pin0, z = a.z, K = nK(c), nin = a.nin;
+    const int kq = corner_lane(c), KL = nKL(c);
     const float ig = c.inv_gamma;
     const int rfo = q >> 1;
     const bool slew_lane = (q & 1) != 0;
@@ -495,9 +499,10 @@ __device__ __forceinline__ void adj_part_sum(AdjPart &p, unsigned m)
 }
 
 // adj_run's stores of the summed partials (first corner; the dataflow sweep)
-__device__ __forceinline__ void adj_store(const DevCtx &c, const AdjItem &a, int g, int q, int par, const AdjPart &p)
+template <class Ctx>
+__device__ __forceinline__ void adj_store(const Ctx &c, const AdjItem &a, int g, int q, int par, const AdjPart &p)
 {
-    const int K = c.K, k = corner_lane(c);
+    const int K = nK(c), k = corner_lane(c);
     if (q == 0) c.aload[(size_t)g * K + k] = p.aload;
     if (a.kind != 0) return;
 #pragma unroll
@@ -773,8 +778,8 @@ __global__ void k_adj_begin(const DevCtx c)
     }
 }
 
-template <bool UNIFORM>
-__global__ void __launch_bounds__(kDfThreadsA) k_df_adjoint(const DevCtx c)
+template <bool UNIFORM, class Ctx = DevCtx>
+__global__ void __launch_bounds__(kDfThreadsA) k_df_adjoint(const Ctx c)
 {
     extern __shared__ float smem[];
     const int nl = c.T * 3 * 4 * kLutStride;
@@ -794,7 +799,7 @@ __global__ void __launch_bounds__(kDfThreadsA) k_df_adjoint(const DevCtx c)
         if (lane == 0) ch = (int)atomicAdd(c.df_state + 5, 1u);
         ch = __shfl_sync(0xffffffffu, ch, 0);
         if (ch >= c.n_bwd_chunks || ld_volatile(c.df_state + 6)) break;
-        const int x = c.bwd_chunk_lo[ch] + lane / (4 * c.KL);
+        const int x = c.bwd_chunk_lo[ch] + lane / (4 * nKL(c));
         bool pending = x < c.bwd_chunk_hi[ch];
         AdjItem it{};
         if (pending) it = adj_prep(c, ti, ti + c.T, x, q);
@@ -813,7 +818,7 @@ __global__ void __launch_bounds__(kDfThreadsA) k_df_adjoint(const DevCtx c)
             if (__any_sync(0xffffffffu, go)) {
                 // every lane sums (full-warp shuffles); the ready groups use it
                 const float sum = adj_quad_sum(part, q, 0xffffffffu);
-                if (c.K == c.KL) {
+                if (nK(c) == nKL(c)) {
                     // one corner per group: the quad sums of the item's
                     // partials also run converged
                     AdjPart ap{};
@@ -859,8 +864,15 @@ void launch_adjoint(const DevCtx &c, const HostSched &h, cudaStream_t st)
         k_adj_recover<<<h.adj_blocks, kDfThreadsA, 0, st>>>(c);
         k_adj_begin<<<1, 32, 0, st>>>(c);
         const size_t smem = adjoint_smem_bytes(h.T);
-        if (h.uniform) k_df_adjoint<true><<<h.adj_blocks, kDfThreadsA, smem, st>>>(c);
-        else k_df_adjoint<false><<<h.adj_blocks, kDfThreadsA, smem, st>>>(c);
+        if (h.one) {
+            const DevCtxOne c1{c};   // the same context, for the one-state builds
+            if (h.uniform) k_df_adjoint<true, DevCtxOne><<<h.adj_blocks, kDfThreadsA, smem, st>>>(c1);
+            else k_df_adjoint<false, DevCtxOne><<<h.adj_blocks, kDfThreadsA, smem, st>>>(c1);
+        } else if (h.uniform) {
+            k_df_adjoint<true><<<h.adj_blocks, kDfThreadsA, smem, st>>>(c);
+        } else {
+            k_df_adjoint<false><<<h.adj_blocks, kDfThreadsA, smem, st>>>(c);
+        }
     } else {
         for (int s = h.S - 1; s >= 0; --s) {
             const int i0 = h.stage_ptr[s], i1 = h.stage_ptr[s + 1];
@@ -892,12 +904,15 @@ cudaError_t adjoint_prepare(HostSched &h)
         h.adj_blocks = 0;
         return cudaSuccess;
     }
-    auto k = h.uniform ? k_df_adjoint<true> : k_df_adjoint<false>;
     int dev = 0, sms = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kDfThreadsA, smem);
+    auto occ = [&](auto k) {
+        if (e == cudaSuccess) e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kDfThreadsA, smem);
+    };
+    if (h.one) occ(h.uniform ? k_df_adjoint<true, DevCtxOne> : k_df_adjoint<false, DevCtxOne>);
+    else occ(h.uniform ? k_df_adjoint<true> : k_df_adjoint<false>);
     if (e != cudaSuccess) return e;
     h.adj_blocks = std::max(1, per_sm) * sms;
     return cudaSuccess;
