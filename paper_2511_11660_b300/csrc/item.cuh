@@ -355,8 +355,9 @@ struct FwdItem {
 };
 
 // the drivers' arrival and slew, component q of the lane's first corner, as
-// probed; with PAIR the probe also returns the other edge of the same
-// early/late half (component q ^ 1), else it comes from the partner lane
+// probed, else it comes from the partner lane; with PAIR the probe returns
+// both edges of the lane's early/late half instead, rise in at / sl and fall
+// in atp / slp (components el*2 and el*2 + 1, as fwd_run takes them)
 struct FwdIn {
     DF at[3];
     float sl[3];
@@ -419,10 +420,10 @@ __device__ __forceinline__ bool fwd_probe(const Ctx &c, const FwdItem &f, int pa
                 float s0, s1;
                 ld_relaxed_df2(fbox_a(c, par, f.drv[j], kq)->v + (q & 2), a0, a1);
                 ld_relaxed2(reinterpret_cast<const float *>(fbox_s(c, par, f.drv[j], kq)) + (q & 2), s0, s1);
-                in.at[j] = (q & 1) ? a1 : a0;
-                in.atp[j] = (q & 1) ? a0 : a1;
-                in.sl[j] = (q & 1) ? s1 : s0;
-                in.slp[j] = (q & 1) ? s0 : s1;
+                in.at[j] = a0;
+                in.atp[j] = a1;
+                in.sl[j] = s0;
+                in.slp[j] = s1;
                 const bool cj = real_df(a0) && real_df(a1) && s0 == s0 && s1 == s1;
                 if (seen && cj && nK(c) == nKL(c) && !pin_adv) *seen |= 1u << j;
                 ok = ok && cj;
@@ -530,9 +531,14 @@ __device__ __forceinline__ void fwd_run(const Ctx &c, const L &lut, const FwdIte
                                            : ld_state4(c.slew + (size_t)f.drv[j] * K + k);
                     s0 = el ? sd.z : sd.x;
                     s1 = el ? sd.w : sd.y;
+                } else if (WAIT && PAIR && k == kq) {
+                    a0 = in.at[j];
+                    a1 = in.atp[j];
+                    s0 = in.sl[j];
+                    s1 = in.slp[j];
                 } else if (WAIT && k == kq) {
-                    const DF ap = PAIR ? in.atp[j] : shfl_xor_df(qm, in.at[j], 1);
-                    const float sp = PAIR ? in.slp[j] : __shfl_xor_sync(qm, in.sl[j], 1);
+                    const DF ap = shfl_xor_df(qm, in.at[j], 1);
+                    const float sp = __shfl_xor_sync(qm, in.sl[j], 1);
                     a0 = rfo ? ap : in.at[j];
                     a1 = rfo ? in.at[j] : ap;
                     s0 = rfo ? sp : in.sl[j];
