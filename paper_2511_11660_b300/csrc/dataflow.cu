@@ -81,8 +81,10 @@ __device__ __forceinline__ bool warp_idle_round(const DevCtx &c, long long &spin
     return true;
 }
 
+// Two blocks a SM (at most 128 registers a thread): the item slots in flight
+// set the pace at 1M cells, so no build may grow past them.
 template <bool SMOOTH, bool UNIFORM, bool THRU, class Ctx = DevCtx>
-__global__ void __launch_bounds__(kDfThreads) k_df_forward(const Ctx c)
+__global__ void __launch_bounds__(kDfThreads, 2) k_df_forward(const Ctx c)
 {
     extern __shared__ float smem[];
     const SmemLib L = stage_library(c, smem);
@@ -93,24 +95,16 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const Ctx c)
         if (ch < 0) break;
         const int x = c.fwd_chunk_lo[ch] + lane / (4 * nKL(c));
         bool pending = x < c.fwd_chunk_hi[ch];
-        const bool is_item = x < c.I;   // else position x - I of the endpoint order
         FwdItem f{};
-        EpItem e{};
-        if (pending) {
-            if (is_item) f = fwd_prep<true>(c, L.nin, L.kind, L.sense, x);
-            else e = ep_prep<true>(c, c.ep_order[chk(c, x - c.I, c.E)]);
-        }
+        if (pending) f = fwd_prep<true>(c, L.nin, L.kind, L.sense, x);
         long long spins = 0;
         FwdIn in;
         unsigned seen = 0;   // inputs found complete (values kept in `in`)
         while (__any_sync(0xffffffffu, pending)) {
             bool ok = false;
-            if (pending)
-                ok = is_item ? fwd_probe<THRU, true>(c, f, par, q, in, &seen)
-                             : ep_probe(c, e, par, q, in.at[0], in.sl[0]);
+            if (pending) ok = fwd_probe<THRU, true>(c, f, par, q, in, &seen);
             if (group_all_warp(c, ok) && pending) {   // the whole warp votes
-                if (is_item) fwd_run<SMOOTH, UNIFORM, true, THRU, true>(c, L.lut, f, in, x, q, par);
-                else ep_run<true>(c, e, in.at[0], in.sl[0], c.ep_order[chk(c, x - c.I, c.E)], q, par);
+                fwd_run<SMOOTH, UNIFORM, true, THRU, true>(c, L.lut, f, in, x, q, par);
                 pending = false;
             }
             if (__any_sync(0xffffffffu, pending) && !warp_idle_round(c, spins)) break;
@@ -119,7 +113,7 @@ __global__ void __launch_bounds__(kDfThreads) k_df_forward(const Ctx c)
 }
 
 template <bool UNIFORM, bool THRU, class Ctx = DevCtx>
-__global__ void __launch_bounds__(kDfThreads) k_df_backward(const Ctx c)
+__global__ void __launch_bounds__(kDfThreads, 2) k_df_backward(const Ctx c)
 {
     extern __shared__ float smem[];
     const SmemLib L = stage_library(c, smem);
@@ -373,6 +367,7 @@ void launch_dataflow_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, 
         if (h.one) df_forward_kernel_one(c.gamma > 0.f, h.uniform)<<<h.df_blocks_fwd, kDfThreads, smem, st>>>(c1);
         else df_forward_kernel(c.gamma > 0.f, h.uniform, h.thru)<<<h.df_blocks_fwd, kDfThreads, smem, st>>>(c);
     }
+    launch_endpoints(c, st);   // every driver is final: no polling
     if (ev) cudaEventRecord(ev[2], st);
     if (c.n_bwd_chunks > 0) {
         if (h.one) df_backward_kernel_one(h.uniform)<<<h.df_blocks_bwd, kDfThreads, smem, st>>>(c1);

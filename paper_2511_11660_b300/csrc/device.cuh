@@ -102,7 +102,6 @@ struct DevCtx {
     const float *lut_scale, *rc_scale;          // [K]
     const int32_t *item_pin0, *item_type, *item_cell;
     const int32_t *item_drv;                    // [I][3] the item driving each gate input (0 where none)
-    const int32_t *ep_drv;                      // [E] the item driving each endpoint
     const int32_t *pin_fo;                      // [P] a gate input's entry in its driver's fan-out list (-1: none)
     const int32_t *fo_ptr, *fo_pin, *fo_node;   // sinks of each item's output net
     const int32_t *fo_item;                     // [F] item of each fan-out entry (differentiable star RC)
@@ -156,7 +155,6 @@ struct DevCtx {
     long long spin_limit;                       // polls before a wait gives up
     int32_t n_fwd_chunks, n_bwd_chunks;
     const int32_t *stage_ptr;                   // [S+1] item offsets of the levels (cooperative schedule)
-    const int32_t *ep_order;                    // [E] endpoints by driver level (dataflow forward work list)
     const int32_t *fwd_chunk_lo, *fwd_chunk_hi;   // forward work: items by level, then endpoints (index I + e)
     const int32_t *bwd_chunk_lo, *bwd_chunk_hi;   // backward work: items by level, deepest first
     // tile schedule (tile.cu): per-block lists of items and endpoints by step

@@ -629,37 +629,22 @@ __device__ __forceinline__ void fwd_run(const Ctx &c, const L &lut, const FwdIte
 // ------------------------------------------------------------ endpoints
 
 struct EpItem {
-    int p, d;   // the endpoint pin; its driver's item (BYITEM) or pin
+    int p, d;   // the endpoint pin; its driver: pin, or (WAIT, the tile schedule) driver item
     bool isD;
     float Dn0, V0;
 };
 
-template <bool BYITEM = false, class Ctx = DevCtx>
+template <class Ctx>
 __device__ __forceinline__ EpItem ep_prep(const Ctx &c, int e)
 {
     EpItem x;
     e = chk(c, e, c.E);
     x.p = chk(c, c.ep_pin[e], c.P);
-    x.d = BYITEM ? chk(c, c.ep_drv[e], c.I) : chk(c, c.drv_of[x.p], c.P);
+    x.d = chk(c, c.drv_of[x.p], c.P);
     x.isD = c.ep_is_d[e] != 0;
     x.Dn0 = c.netD[(size_t)x.p * nK(c) + corner_lane(c)];
     x.V0 = c.netV[(size_t)x.p * nK(c) + corner_lane(c)];
     return x;
-}
-
-// the driver's arrival and slew of the lane's corners are complete; lane q
-// reads component q of its first corner (returned; the caller's group vote,
-// group_all_warp, covers the quad)
-template <class Ctx>
-__device__ __forceinline__ bool ep_probe(const Ctx &c, const EpItem &x, int par, int q, DF &at0, float &sl0)
-{
-    const int kq = corner_lane(c);
-    at0 = ld_relaxed_df(fbox_a(c, par, x.d, kq)->v + q);
-    sl0 = ld_relaxed1(reinterpret_cast<const float *>(fbox_s(c, par, x.d, kq)) + q);
-    bool ok = real_df(at0) && sl0 == sl0;
-    for (int k = kq + nKL(c); k < nK(c) && ok; k += nKL(c))
-        ok = complete_df(fbox_a(c, par, x.d, k)) && complete(ld_relaxed4(fbox_s(c, par, x.d, k)));
-    return ok;
 }
 
 // Arrival through the net, required times of the ideal clock (D: setup

@@ -497,6 +497,11 @@ __global__ void k_endpoints(const DevCtx c)
     if (e < c.E) ep_run<false>(c, ep_prep(c, e), 0.f, 0.f, e, tid & 3, 0);
 }
 
+void launch_endpoints(const DevCtx &c, cudaStream_t st)
+{
+    if (c.E > 0) k_endpoints<<<nblk(4LL * c.KL * c.E, 256), 256, 0, st>>>(c);
+}
+
 template <bool UNIFORM>
 __global__ void __maxnreg__(64) k_bwd_level(const DevCtx c, int i0, int i1)
 {
@@ -757,7 +762,7 @@ void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cud
             else k_fwd_level<false, false><<<grid, tpb, 0, st>>>(c, i0, i1);
         }
     }
-    if (c.E > 0) k_endpoints<<<nblk(4LL * c.KL * c.E, 256), 256, 0, st>>>(c);
+    launch_endpoints(c, st);
     if (ev) cudaEventRecord(ev[2], st);
     for (int s = h.S - 1; s >= 0; --s) {
         const int i0 = h.stage_ptr[s], i1 = h.stage_ptr[s + 1];

@@ -38,6 +38,8 @@ void launch_level_pass(const DevCtx &c, const HostSched &h, cudaStream_t st, cud
 
 // Net delay calculation: RC trees (one thread per net) or star trees.
 void launch_net_tree(const DevCtx &c, cudaStream_t st);
+// Every endpoint at once, after a forward pass (the level and dataflow schedules).
+void launch_endpoints(const DevCtx &c, cudaStream_t st);
 void launch_net_star(const DevCtx &c, cudaStream_t st);
 // Steiner trees from positions (steiner.cu): writes the RC arrays the tree sweep reads.
 void launch_net_steiner(const DevCtx &c, cudaStream_t st);
