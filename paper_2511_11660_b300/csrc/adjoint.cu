@@ -799,8 +799,9 @@ __global__ void __launch_bounds__(kDfThreadsA) k_df_adjoint(const Ctx c)
         if (lane == 0) ch = (int)atomicAdd(c.df_state + 5, 1u);
         ch = __shfl_sync(0xffffffffu, ch, 0);
         if (ch >= c.n_bwd_chunks || ld_volatile(c.df_state + 6)) break;
-        const int x = c.bwd_chunk_lo[ch] + lane / (4 * nKL(c));
-        bool pending = x < c.bwd_chunk_hi[ch];
+        const int pos = c.bwd_chunk_lo[ch] + lane / (4 * nKL(c));
+        bool pending = pos < c.bwd_chunk_hi[ch];
+        const int x = pending ? chk(c, c.bwd_order[chk(c, pos, c.I)], c.I) : 0;
         AdjItem it{};
         if (pending) it = adj_prep(c, ti, ti + c.T, x, q);
         long long spins = 0;

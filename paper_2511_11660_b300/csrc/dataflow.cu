@@ -122,8 +122,9 @@ __global__ void __launch_bounds__(kDfThreads, 2) k_df_backward(const Ctx c)
     for (;;) {
         const int ch = next_chunk(c, 2, c.n_bwd_chunks);
         if (ch < 0) break;
-        const int x = c.bwd_chunk_lo[ch] + lane / (4 * nKL(c));
-        bool pending = x < c.bwd_chunk_hi[ch];
+        const int pos = c.bwd_chunk_lo[ch] + lane / (4 * nKL(c));
+        bool pending = pos < c.bwd_chunk_hi[ch];
+        const int x = pending ? chk(c, c.bwd_order[chk(c, pos, c.I)], c.I) : 0;
         BwdItem b{};
         if (pending) b = bwd_prep(c, L.nin, L.kind, x, q);
         long long spins = 0;

@@ -156,7 +156,8 @@ struct DevCtx {
     int32_t n_fwd_chunks, n_bwd_chunks;
     const int32_t *stage_ptr;                   // [S+1] item offsets of the levels (cooperative schedule)
     const int32_t *fwd_chunk_lo, *fwd_chunk_hi;   // forward work: items by level, then endpoints (index I + e)
-    const int32_t *bwd_chunk_lo, *bwd_chunk_hi;   // backward work: items by level, deepest first
+    const int32_t *bwd_chunk_lo, *bwd_chunk_hi;   // backward work: positions of bwd_order, deepest level first
+    const int32_t *bwd_order;                   // [I] items in backward work order
     // tile schedule (tile.cu): per-block lists of items and endpoints by step
     int32_t tl_B, tl_NS, tl_R;                  // tiles, steps, ring slots per block
     const int32_t *tl_ptr;                      // [B*NS + 1] list (b, s) = entries [tl_ptr[b*NS+s], ...+1)

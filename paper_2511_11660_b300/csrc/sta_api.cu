@@ -429,11 +429,45 @@ sta_status create_from_plan(sta_ctx *c, int device)
                 flo.push_back(g);
                 fhi.push_back(std::min(g + kChunkItems, pl.stage_ptr[s + 1]));
             }
-        for (int32_t s = pl.S - 1; s >= 0; --s)
-            for (int32_t g = pl.stage_ptr[s]; g < pl.stage_ptr[s + 1]; g += kChunkItems) {
-                blo.push_back(g);
-                bhi.push_back(std::min(g + kChunkItems, pl.stage_ptr[s + 1]));
+        // Backward work order: levels deepest first; inside a level the items
+        // by cell type (a warp's lanes take the same table branch), then by
+        // the position of their last sink item (the one taken last, whose
+        // required time completes last; items whose sinks are all endpoints
+        // first), so that a chunk's items tend to become ready together.
+        std::vector<int32_t> pin_item(pl.P, -1), bpos(pl.I, -1), bord;
+        bord.reserve(pl.I);
+        for (int32_t g = 0; g < pl.I; ++g) {
+            const int32_t t = pl.item_type[g], p0 = pl.item_pin0[g];
+            const int32_t z = t < 0 ? p0 : (pl.type_kind[t] == 1 ? p0 + 1 : p0 + pl.type_nin[t]);
+            for (int32_t p = p0; p <= z; ++p) pin_item[p] = g;
+        }
+        std::vector<std::pair<int64_t, int32_t>> key;
+        for (int32_t s = pl.S - 1; s >= 0; --s) {
+            key.clear();
+            for (int32_t g = pl.stage_ptr[s]; g < pl.stage_ptr[s + 1]; ++g) {
+                int32_t k = -1;
+                for (int32_t q = pl.fo_ptr[g]; q < pl.fo_ptr[g + 1]; ++q) {
+                    const int32_t sp = pl.fo_pin[q];
+                    if (sp < pl.P - pl.E && pin_item[sp] >= 0) k = std::max(k, bpos[pin_item[sp]]);
+                }
+                key.emplace_back(((int64_t)(pl.item_type[g] + 1) << 32) + (k + 1), g);
             }
+            std::stable_sort(key.begin(), key.end(),
+                             [](const std::pair<int64_t, int32_t> &a, const std::pair<int64_t, int32_t> &b) {
+                                 return a.first < b.first;
+                             });
+            const int32_t first = (int32_t)bord.size();
+            for (const auto &kg : key) {
+                bpos[kg.second] = (int32_t)bord.size();
+                bord.push_back(kg.second);
+            }
+            const int32_t last = (int32_t)bord.size();
+            for (int32_t x = first; x < last; x += kChunkItems) {
+                blo.push_back(x);
+                bhi.push_back(std::min(x + kChunkItems, last));
+            }
+        }
+        d.bwd_order = upload(c, bord);
         d.n_fwd_chunks = (int32_t)flo.size();
         d.n_bwd_chunks = (int32_t)blo.size();
         d.fwd_chunk_lo = upload(c, flo);
